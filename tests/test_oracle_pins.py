@@ -175,9 +175,12 @@ def test_merge_golden(case):
     # classify via the exported model (Alg. 3 on the re-imported tree)
     mask = oracle.classify(model, probes, case["d"], FRAME)
     assert mask.ravel().tolist() == [e for _, e in case["probes"]]
-    # and Check Color on the merged tree itself
-    _, mask2 = oracle.run(train, case["d"], case["T"], FRAME, 0, probes)
-    assert mask2.ravel().tolist() == [e for _, e in case["probes"]]
+    # and Check Color on the merged tree itself: one test frame per probe colour
+    test = np.empty((len(case["probes"]), case["H"], case["W"], 3), np.uint8)
+    test[...] = probes.reshape(-1, 1, 1, 3)
+    _, mask2 = oracle.run(train, case["d"], case["T"], FRAME, 0, test)
+    assert mask2.reshape(len(case["probes"]), -1).min(axis=1).tolist() == [e for _, e in case["probes"]]
+    assert mask2.reshape(len(case["probes"]), -1).max(axis=1).tolist() == [e for _, e in case["probes"]]
 
 
 # ---- invariants against the set-based restatement ------------------------------
