@@ -1,0 +1,447 @@
+#!/usr/bin/env python3
+"""Benchmark of the octree background model's hot path on GB300.
+
+One step = the whole path over one batch of synthetic input: build the merged
+model from N training frames (S1-S3) and classify F test frames (S1, S4),
+through the C ABI (ocq_build_model + ocq_classify), inputs resident in HBM.
+Workload: 1920x1080 RGB8, one region per pixel location, depth 3, N = 50,
+T = 10, F = 1000 (6.5 GB of frames per step, far above the 129 MB L2, so no
+L2 flush is needed between steps).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "classify+build Mpixel/s at 1080p, % HBM roofline; batched vs plain; p99 ms"
+UNIT = "Mpixel/s"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline budget (oracle)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=None, help="override F (test frames)")
+    return ap.parse_args(argv)
+
+
+# ---- multi-GPU plumbing (host logic; tested with gloo on CPU) -------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def shard_stream_id(rank: int, world: int) -> int:
+    """Weak scaling: every rank runs the full per-GPU workload on its own camera
+    stream (seeded by rank); streams share no data, so there is no collective
+    on the data path."""
+    return rank
+
+
+def aggregate(values_ms, units_per_rank):
+    """Whole-job throughput: units of all ranks / the slowest rank's time."""
+    t = max(values_ms)
+    return sum(units_per_rank) / (t / 1e3), t
+
+
+class Dist:
+    def __init__(self, world, backend):
+        self.world = world
+        self.on = world > 1
+        if self.on:
+            import torch.distributed as dist
+
+            dist.init_process_group(backend=backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.on:
+            self.dist.barrier()
+
+    def max(self, x: float, device) -> float:
+        if not self.on:
+            return x
+        import torch
+
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def gather_sum(self, x: float, device) -> float:
+        if not self.on:
+            return x
+        import torch
+
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.on:
+            self.dist.destroy_process_group()
+
+
+# ---- clocks -----------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled while the GPU is busy."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 20):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="ocq_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", str(self.period)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        self.t0 = time.time()
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.remove(self.path)
+        return self.summarise(rows)
+
+    @staticmethod
+    def summarise(rows):
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max([num(r[3]) for r in rows if num(r[3]) is not None], default=None)}
+
+
+# ---- roofline bookkeeping -----------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def classify_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1412_1945_gb300", "csrc")
+    for name in ("classify.cu", "pixels.cuh", "ocq_internal.cuh"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current classify sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d[kernel][workload]
+        if e.get("source_hash") != classify_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except (KeyError, ValueError, TypeError):
+        return None
+
+
+# ---- CPU oracle timing -----------------------------------------------------------
+
+def oracle_throughput(wl, budget_s: float, seed: int = 7, max_chunks: int = 10_000):
+    """The oracle as it stands (single thread) on random pixel locations of the
+    workload, every training and test frame of each: Mpixel/s of (N+F) x k."""
+    import numpy as np
+
+    import ocq_synth
+    import oracle
+
+    oracle.build()
+    sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, wl.F, wl.seed, wl.stream)
+    rng = np.random.default_rng(seed)
+    k = 64
+    done_px, spent = 0, 0.0
+    locs = 0
+    for _ in range(max_chunks):
+        idx = rng.integers(0, wl.H * wl.W, size=k)
+        tr = ocq_synth.fill_pixels_host(sc, 0, wl.N, idx)
+        te = ocq_synth.fill_pixels_host(sc, wl.N, wl.F, idx)
+        t0 = time.perf_counter()
+        oracle.run(tr, wl.depth, wl.T, wl.region, wl.block, te)
+        dt = time.perf_counter() - t0
+        spent += dt
+        done_px += (wl.N + wl.F) * k
+        locs += k
+        if spent >= budget_s:
+            break
+        k = int(min(4096, max(64, k * 2))) if dt < 0.5 else k
+    return done_px / spent / 1e6, locs, spent
+
+
+# ---- our arm ---------------------------------------------------------------------
+
+def workload_for(args, stream_id):
+    from dataclasses import replace
+
+    from ocq_synth import configs
+
+    wl = replace(configs.PIXEL_1080P, stream=stream_id)
+    if args.frames is not None:
+        wl = replace(wl, F=args.frames)
+    return wl
+
+
+def config_dict(wl, world):
+    return {"workload": wl.name, "H": wl.H, "W": wl.W, "train_frames": wl.N, "test_frames": wl.F,
+            "region": "pixel", "depth": wl.depth, "T": wl.T, "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2 (frames of one step = %.2f GB)" % ((wl.N + wl.F) * wl.H * wl.W * 3 / 1e9)}
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = Dist(world, "nccl")
+    import ocq_synth
+    import paper_1412_1945_gb300 as ocq
+
+    ocq.load()
+    wl = workload_for(args, shard_stream_id(rank, world))
+    H, W, N, F = wl.H, wl.W, wl.N, wl.F
+    hw = H * W
+    sc = ocq_synth.make_scene(wl.scene_kind, H, W, N, F, wl.seed, wl.stream)
+    train = torch.empty((N, H, W, 3), dtype=torch.uint8, device=dev)
+    test = torch.empty((F, H, W, 3), dtype=torch.uint8, device=dev)
+    mask = torch.empty((F, H, W), dtype=torch.uint8, device=dev)
+    ocq_synth.fill_device(sc, 0, N, train)
+    ocq_synth.fill_device(sc, N, F, test)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        m = ocq.ocq.ocq_build_model(train, N, H, W, wl.region, wl.block, wl.depth, wl.T, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        ocq.ocq.ocq_classify(m, test, F, mask, stream)
+        if ev is not None:
+            ev[2].record(stream)
+        m.free()
+
+    for _ in range(args.warmup):
+        step()
+    ocq.device_status()
+    sampler = ClockSampler(local)
+    sampler.start()
+    # keep the GPU busy while the sampler starts up, then time
+    for _ in range(max(1, args.warmup)):
+        step()
+    dist.barrier()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = ocq.ocq.ocq_kernel_launches()
+    start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    launches = ocq.ocq.ocq_kernel_launches() - l0
+    clocks = sampler.stop()
+    ocq.device_status()
+    total_ms = start.elapsed_time(end)
+    build_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    cls_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    max_ms = dist.max(total_ms, dev)
+    px_per_step = (N + F) * hw
+    value = px_per_step * args.steps * world / (max_ms / 1e3) / 1e6
+
+    # roofline of the dominant kernel (classify: tiled per-pixel kernel, one launch)
+    model_bytes = ocq.ocq.ocq_model_footprint(H, W, wl.region, wl.block, wl.depth)
+    cls_bytes = F * hw * 4 + model_bytes
+    peak, peak_kind = measured_peaks()
+    achieved = cls_bytes / (cls_ms / 1e3) / 1e9
+    build_bytes = N * hw * 3 + model_bytes
+
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": config_dict(wl, world),
+        "roofline": {"bound": "hbm", "kernel": "classify_pixel_tiled_kernel", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": profiled_traffic("classify_pixel_tiled_kernel", wl.name),
+                     "algorithmic_bytes_per_launch": cls_bytes, "peak_source": peak_kind},
+        "build": {"ms": round(build_ms, 4), "mpixel_s": round(N * hw / (build_ms / 1e3) / 1e6, 1),
+                  "gbs": round(build_bytes / (build_ms / 1e3) / 1e9, 1),
+                  "hbm_frac": round(build_bytes / (build_ms / 1e3) / 1e9 / peak, 4)},
+        "classify": {"ms": round(cls_ms, 4), "mpixel_s": round(F * hw / (cls_ms / 1e3) / 1e6, 1),
+                     "gbs": round(achieved, 1), "hbm_frac": round(achieved / peak, 4)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    if not args.no_e2e:
+        result["e2e"] = e2e_measure(ocq, wl, train, test, mask, stream, args, dist, dev, world)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, locs, spent = oracle_throughput(wl, args.cpu_seconds)
+        result["cpu_baseline"] = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": f"{locs} random pixel locations x all {N}+{F} frames "
+                                            f"({spent:.1f} s single-threaded pointer-octree oracle)"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    dist.close()
+
+
+def e2e_measure(ocq, wl, train, test, mask, stream, args, dist, dev, world):
+    import torch
+
+    H, W, N, F = wl.H, wl.W, wl.N, wl.F
+    hw = H * W
+    h_train = torch.empty(train.shape, dtype=torch.uint8, pin_memory=True)
+    h_test = torch.empty(test.shape, dtype=torch.uint8, pin_memory=True)
+    h_mask = torch.empty(mask.shape, dtype=torch.uint8, pin_memory=True)
+    h_train.copy_(train)
+    h_test.copy_(test)
+    torch.cuda.synchronize()
+
+    def call():
+        ocq.ocq.ocq_detect_host(h_train, N, h_test, F, H, W, wl.region, wl.block, wl.depth, wl.T, h_mask, stream)
+
+    call()  # warm-up (allocator pools, streams)
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        call()
+    dt = time.perf_counter() - t0
+    dt = dist.max(dt, dev)
+    ok = bool((h_mask[: min(F, 4)].to(dev) == mask[: min(F, 4)]).all().item())
+    return {"value": round((N + F) * hw * args.e2e_steps * world / dt / 1e6, 1), "unit": UNIT,
+            "h2d_bytes_per_step": (N + F) * hw * 3, "d2h_bytes_per_step": F * hw,
+            "steps": args.e2e_steps, "ms_per_step": round(dt / args.e2e_steps * 1e3, 3),
+            "api": "ocq_detect_host (page-locked host buffers)", "masks_match_device_path": ok}
+
+
+# ---- reference arm (the CPU oracle) ------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = workload_for(args, 0)
+    import numpy as np
+
+    import ocq_synth
+    import oracle
+
+    oracle.build()
+    sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, wl.F, wl.seed, wl.stream)
+    rng = np.random.default_rng(11)
+    # size one step so that warmup + steps take about 90 s in all
+    k = 16
+    idx = rng.integers(0, wl.H * wl.W, size=k)
+    tr = ocq_synth.fill_pixels_host(sc, 0, wl.N, idx)
+    te = ocq_synth.fill_pixels_host(sc, wl.N, wl.F, idx)
+    t0 = time.perf_counter()
+    oracle.run(tr, wl.depth, wl.T, wl.region, wl.block, te)
+    per_loc = (time.perf_counter() - t0) / k
+    budget = 90.0 / max(1, args.steps + args.warmup)
+    k = int(max(1, min(20000, budget / max(per_loc, 1e-7))))
+
+    def one_step():
+        idx = rng.integers(0, wl.H * wl.W, size=k)
+        tr = ocq_synth.fill_pixels_host(sc, 0, wl.N, idx)
+        te = ocq_synth.fill_pixels_host(sc, wl.N, wl.F, idx)
+        t = time.perf_counter()
+        oracle.run(tr, wl.depth, wl.T, wl.region, wl.block, te)
+        return time.perf_counter() - t
+
+    for _ in range(args.warmup):
+        one_step()
+    spent = sum(one_step() for _ in range(args.steps))
+    value = (wl.N + wl.F) * k * args.steps / spent / 1e6
+    sample = (f"{k} random pixel locations x all {wl.N}+{wl.F} frames per step "
+              f"(single-threaded pointer-octree oracle, inputs generated outside the timed region)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(spent / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": config_dict(wl, world),
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

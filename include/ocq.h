@@ -1,0 +1,169 @@
+/*
+ * ocq -- GB300 (sm_103a) library for the octree colour-quantisation background
+ * model of "Background Modeling Using Octree Color Quantization" (arXiv 1412.1945).
+ *
+ * The method (paper Sec. 2-4):
+ *   S1  each RGB8 pixel is quantised to its octree path: at level l (bit 7-l)
+ *       the child index is (red bit << 2) | (green bit << 1) | blue bit
+ *       (Alg. 1, with the printed "red[i] + green[i] + blue[i]" read as bit
+ *       concatenation); pruning the tree at height d keeps the top d levels
+ *       (Sec. 2).  The path code is the d child indices read as base-8 digits
+ *       from the root (index of level 0 most significant).
+ *   S2  one tree per training frame and region records which leaves occur
+ *       (Store Color, Alg. 1; regions Sec. 3 and Sec. 4).
+ *   S3  the N per-frame trees are merged keeping the leaves present in at least
+ *       T of them (Merge Trees, Alg. 2, with the fraction test count/N >= t
+ *       taken as the integer test count >= T, T = ceil(t*N)).
+ *   S4  a pixel of an incoming frame is background when its leaf is in its
+ *       region's merged tree, else foreground (Check Color, Alg. 3; Sec. 4).
+ *
+ * Conventions for every entry point:
+ *   - Frames are HWC RGB8 with no row padding: byte ((f*H + y)*W + x)*3 + c.
+ *     Masks are u8, one byte per pixel, 1 = foreground, 0 = background.
+ *   - Buffers called "device" must be device-accessible memory of the current
+ *     CUDA device; the caller owns them.  Nothing is retained after the call
+ *     except inside an ocq_model (library-owned, freed by ocq_model_free).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued asynchronously on it; argument errors are returned
+ *     synchronously before anything is enqueued; errors of enqueued work are
+ *     reported by a later call (OCQ_ECUDA) or by the caller's synchronisation.
+ *   - Nothing throws across this interface.  ocq_last_error() gives a message
+ *     for the calling thread's last failure.
+ *   - Domain: 1 <= depth <= 8; 1 <= T <= N <= 65535; H, W >= 1; H*W*N and
+ *     H*W*F below 2^40; block >= 1 for block regions (partial edge blocks allowed).
+ */
+#ifndef OCQ_H
+#define OCQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OCQ_OK = 0,
+  OCQ_EINVAL = 1,   /* bad argument (null pointer, size or parameter out of domain) */
+  OCQ_ENOMEM = 2,   /* device allocation failed or footprint above the budget */
+  OCQ_ECUDA = 3,    /* a CUDA call failed (message in ocq_last_error) */
+  OCQ_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+  OCQ_EBUSY = 5,    /* no capacity right now (serving admission); retry later */
+  OCQ_ENOTSUP = 6   /* valid request this build does not handle */
+} ocq_status;
+
+/* Region geometry (Sec. 3 "subdivide a video into multiple regions"; Sec. 4).
+ * FRAME: one region.  BLOCK: b x b blocks numbered row-major,
+ * r = (y/b)*ceil(W/b) + x/b, partial blocks at the right/bottom edges.
+ * PIXEL: one region per pixel location, r = y*W + x. */
+typedef enum { OCQ_REGION_FRAME = 0, OCQ_REGION_BLOCK = 1, OCQ_REGION_PIXEL = 2 } ocq_region_kind;
+
+typedef struct {
+  int32_t kind;  /* ocq_region_kind */
+  int32_t block; /* b for OCQ_REGION_BLOCK, ignored otherwise */
+} ocq_region;
+
+/* Opaque, device-resident merged model (library-owned). */
+typedef struct ocq_model ocq_model;
+
+/* Header of a model.  The exported bitset holds `regions` rows of
+ * `words_per_region` u64 words; leaf path code c of a row is bit c%64 of word
+ * c/64 (words_per_region = max(1, 8^depth/64)). */
+typedef struct {
+  int32_t H, W;
+  int32_t region_kind, block;
+  int32_t depth, T, N;
+  int32_t reserved;
+  int64_t regions;
+  int64_t words_per_region;
+} ocq_model_info;
+
+/* Human-readable name of a status code (static string). */
+const char *ocq_status_str(ocq_status s);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char *ocq_last_error(void);
+
+/* Library version string (static). */
+const char *ocq_version(void);
+
+/* Number of regions of an H x W frame for `region`, or -1 if invalid. */
+int64_t ocq_region_count(int H, int W, ocq_region region);
+
+/* Device bytes an ocq_model of this geometry occupies (0 if invalid). */
+size_t ocq_model_footprint(int H, int W, ocq_region region, int depth);
+
+/*
+ * S1 alone (Alg. 1 walk, Sec. 2 pruning): path code of each of `npix` pixels.
+ * rgb: device, npix*3 bytes.  codes: device, npix u32 (code < 8^depth).
+ */
+ocq_status ocq_path_code(const uint8_t *rgb, int64_t npix, int depth, uint32_t *codes, void *stream);
+
+/*
+ * S2 alone (Alg. 1, one tree per frame and region): the leaf set of every
+ * frame's per-region tree, as a bitset in the exported layout.
+ * frames: device, n*H*W*3.  occ: device, n * regions * words_per_region u64,
+ * frame-major (row index f*regions + r).  Every word is written.
+ */
+ocq_status ocq_occupancy(const uint8_t *frames, int n, int H, int W, ocq_region region, int depth,
+                         uint64_t *occ, void *stream);
+
+/*
+ * S1-S3 (Sec. 3, Alg. 1 + Alg. 2): build the merged model of N training
+ * frames.  frames: device, N*H*W*3 bytes.  On success *out owns a new
+ * device-resident model, ready for use on `stream` once the enqueued work has
+ * run.  Allocation uses stream-ordered device memory.
+ */
+ocq_status ocq_build_model(const uint8_t *frames, int N, int H, int W, ocq_region region, int depth, int T,
+                           void *stream, ocq_model **out);
+
+/*
+ * S4 (Sec. 4, Alg. 3): classify F frames against `model`.
+ * frames: device, F*H*W*3 bytes of the model's H x W.  mask: device, F*H*W
+ * bytes, every byte written (1 = foreground).
+ */
+ocq_status ocq_classify(const ocq_model *model, const uint8_t *frames, int F, uint8_t *mask, void *stream);
+
+/* Header of a model (host struct filled synchronously). */
+ocq_status ocq_model_get_info(const ocq_model *model, ocq_model_info *info);
+
+/* Writes the model as a bitset in the exported layout (see ocq_model_info) to
+ * device buffer `dst` of `words` u64 (must be >= regions*words_per_region). */
+ocq_status ocq_model_export(const ocq_model *model, uint64_t *dst, size_t words, void *stream);
+
+/* Creates a model from an exported bitset `src` (device) and its header
+ * (H, W, region_kind, block, depth are required; T and N are recorded). */
+ocq_status ocq_model_import(const uint64_t *src, const ocq_model_info *info, void *stream, ocq_model **out);
+
+/* Frees a model (stream-ordered on the stream it was created on); NULL is ignored. */
+void ocq_model_free(ocq_model *model);
+
+/* Synchronises `stream`, then reports whether a kernel of this library on the
+ * current device gave up a bounded wait (a bulk copy that did not arrive within
+ * one second): OCQ_ETIMEOUT if so (the record is cleared), else OCQ_OK. */
+ocq_status ocq_device_status(void *stream);
+
+/*
+ * End to end from HOST memory (Sec. 3-4: build on the first N frames, then
+ * detect foreground in the next F): copies the N training frames to the device,
+ * builds the model (as ocq_build_model), streams the F test frames through
+ * device chunk buffers with copy-in, classification and mask copy-out
+ * overlapped on three streams, and writes the F*H*W mask bytes to `mask`.
+ * train: host, N*H*W*3 bytes; test: host, F*H*W*3; mask: host, F*H*W.
+ * Page-locked host buffers give full copy bandwidth; pageable ones work too.
+ * Synchronous: returns after every mask byte is in host memory.  If
+ * out_model is not NULL it receives the model (caller frees), else the model
+ * is freed.
+ */
+ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int F, int H, int W, ocq_region region,
+                           int depth, int T, uint8_t *mask, void *stream, ocq_model **out_model);
+
+/* Number of kernels this library has launched in this process (all devices).
+ * Lets a caller count the device work a call sequence issued. */
+uint64_t ocq_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCQ_H */

@@ -73,6 +73,9 @@ def _load_host():
             lib.ocq_synth_fill_host.restype = ctypes.c_int
             lib.ocq_synth_fill_host.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                                 ctypes.c_void_p, ctypes.c_void_p]
+            lib.ocq_synth_fill_pixels_host.restype = ctypes.c_int
+            lib.ocq_synth_fill_pixels_host.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
             _host_lib = lib
     return _host_lib
 
@@ -107,6 +110,20 @@ def fill_host(scene: np.ndarray, frame0: int, nframes: int, with_gt: bool = Fals
     if rc != 0:
         raise RuntimeError("ocq_synth_fill_host failed")
     return (rgb, gt) if with_gt else rgb
+
+
+def fill_pixels_host(scene: np.ndarray, frame0: int, nframes: int, idx) -> np.ndarray:
+    """Render only the pixel locations ``idx`` (row-major indices) of frames
+    [frame0, frame0+nframes): returns ``uint8[nframes, 1, len(idx), 3]``, a
+    1-row frame that per-pixel regions treat exactly like the full frame."""
+    lib = _load_host()
+    scene = np.ascontiguousarray(scene, dtype=np.int32)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.empty((nframes, 1, idx.size, 3), dtype=np.uint8)
+    if lib.ocq_synth_fill_pixels_host(scene.ctypes.data, frame0, nframes, idx.ctypes.data, idx.size,
+                                      out.ctypes.data) != 0:
+        raise RuntimeError("ocq_synth_fill_pixels_host failed")
+    return out
 
 
 def fill_device(scene: np.ndarray, frame0: int, nframes: int, out, gt=None, stream=None):

@@ -1,0 +1,243 @@
+// C-ABI entry points: argument validation, model ownership, dispatch.
+// The compute lives in build.cu, classify.cu and transform.cu.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ocq_internal.cuh"
+
+namespace ocq {
+
+static thread_local char g_err[512];
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+ocq_status cuda_status(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return OCQ_OK;
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return OCQ_ENOMEM;
+  return OCQ_ECUDA;
+}
+
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+int64_t region_count(int H, int W, int kind, int block) {
+  if (H < 1 || W < 1) return -1;
+  if (kind == OCQ_REGION_FRAME) return 1;
+  if (kind == OCQ_REGION_BLOCK) {
+    if (block < 1) return -1;
+    return (int64_t)((H + block - 1) / block) * ((W + block - 1) / block);
+  }
+  if (kind == OCQ_REGION_PIXEL) return (int64_t)H * W;
+  return -1;
+}
+
+static const int64_t kMaxPixels = (int64_t)1 << 40;
+
+static ocq_status check_geometry(int H, int W, ocq_region region, int depth) {
+  if (H < 1 || W < 1) {
+    set_error("H and W must be >= 1 (got %d x %d)", H, W);
+    return OCQ_EINVAL;
+  }
+  if (depth < 1 || depth > 8) {
+    set_error("depth must be in [1, 8] (got %d)", depth);
+    return OCQ_EINVAL;
+  }
+  if (region_count(H, W, region.kind, region.block) < 1) {
+    set_error("invalid region (kind %d, block %d)", region.kind, region.block);
+    return OCQ_EINVAL;
+  }
+  return OCQ_OK;
+}
+
+static ocq_model *new_model(int H, int W, ocq_region region, int depth, int T, int N, cudaStream_t st,
+                            ocq_status *rc) {
+  ocq_model *m = new (std::nothrow) ocq_model();
+  if (!m) {
+    set_error("host allocation failed");
+    *rc = OCQ_ENOMEM;
+    return nullptr;
+  }
+  m->H = H, m->W = W, m->kind = region.kind, m->block = region.kind == OCQ_REGION_BLOCK ? region.block : 0;
+  m->depth = depth, m->T = T, m->N = N;
+  m->R = region_count(H, W, region.kind, region.block);
+  m->wpr = wpr32(depth);
+  m->bytes = (size_t)m->R * (size_t)m->wpr * sizeof(uint32_t);
+  m->stream = st;
+  cudaGetDevice(&m->device);
+  void *p = nullptr;
+  *rc = cuda_status(cudaMallocAsync(&p, m->bytes, st), "allocating the model");
+  if (*rc != OCQ_OK) {
+    delete m;
+    return nullptr;
+  }
+  m->bits = (uint32_t *)p;
+  return m;
+}
+
+}  // namespace ocq
+
+using namespace ocq;
+
+extern "C" {
+
+const char *ocq_status_str(ocq_status s) {
+  switch (s) {
+    case OCQ_OK: return "OCQ_OK";
+    case OCQ_EINVAL: return "OCQ_EINVAL";
+    case OCQ_ENOMEM: return "OCQ_ENOMEM";
+    case OCQ_ECUDA: return "OCQ_ECUDA";
+    case OCQ_ETIMEOUT: return "OCQ_ETIMEOUT";
+    case OCQ_EBUSY: return "OCQ_EBUSY";
+    case OCQ_ENOTSUP: return "OCQ_ENOTSUP";
+  }
+  return "OCQ_UNKNOWN";
+}
+
+const char *ocq_last_error(void) { return g_err; }
+
+uint64_t ocq_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *ocq_version(void) { return "ocq 0.1 (sm_103a)"; }
+
+int64_t ocq_region_count(int H, int W, ocq_region region) { return region_count(H, W, region.kind, region.block); }
+
+size_t ocq_model_footprint(int H, int W, ocq_region region, int depth) {
+  if (check_geometry(H, W, region, depth) != OCQ_OK) return 0;
+  return (size_t)region_count(H, W, region.kind, region.block) * (size_t)wpr32(depth) * sizeof(uint32_t);
+}
+
+ocq_status ocq_path_code(const uint8_t *rgb, int64_t npix, int depth, uint32_t *codes, void *stream) {
+  g_err[0] = 0;
+  if (npix < 0 || npix >= kMaxPixels || depth < 1 || depth > 8 || (npix > 0 && (!rgb || !codes))) {
+    set_error("ocq_path_code: bad arguments");
+    return OCQ_EINVAL;
+  }
+  if (npix == 0) return OCQ_OK;
+  return launch_path_code(rgb, npix, depth, codes, (cudaStream_t)stream);
+}
+
+ocq_status ocq_occupancy(const uint8_t *frames, int n, int H, int W, ocq_region region, int depth, uint64_t *occ,
+                         void *stream) {
+  g_err[0] = 0;
+  ocq_status rc = check_geometry(H, W, region, depth);
+  if (rc != OCQ_OK) return rc;
+  if (n < 0 || (n > 0 && (!frames || !occ)) || (int64_t)n * H * W >= kMaxPixels) {
+    set_error("ocq_occupancy: bad frame count or pointers");
+    return OCQ_EINVAL;
+  }
+  if (n == 0) return OCQ_OK;
+  return launch_occupancy(frames, n, H, W, region.kind, region.kind == OCQ_REGION_BLOCK ? region.block : 0, depth,
+                          occ, (cudaStream_t)stream);
+}
+
+ocq_status ocq_build_model(const uint8_t *frames, int N, int H, int W, ocq_region region, int depth, int T,
+                           void *stream, ocq_model **out) {
+  g_err[0] = 0;
+  if (!out) {
+    set_error("ocq_build_model: out is NULL");
+    return OCQ_EINVAL;
+  }
+  *out = nullptr;
+  ocq_status rc = check_geometry(H, W, region, depth);
+  if (rc != OCQ_OK) return rc;
+  if (!frames || N < 1 || N > 65535 || T < 1 || T > N || (int64_t)N * H * W >= kMaxPixels) {
+    set_error("ocq_build_model: need frames != NULL and 1 <= T <= N <= 65535 (N=%d, T=%d)", N, T);
+    return OCQ_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  ocq_model *m = new_model(H, W, region, depth, T, N, st, &rc);
+  if (!m) return rc;
+  rc = launch_build(frames, N, m, st);
+  if (rc != OCQ_OK) {
+    ocq_model_free(m);
+    return rc;
+  }
+  *out = m;
+  return OCQ_OK;
+}
+
+ocq_status ocq_classify(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, void *stream) {
+  g_err[0] = 0;
+  if (!m || F < 0 || (F > 0 && (!frames || !mask)) || (int64_t)F * m->H * m->W >= kMaxPixels) {
+    set_error("ocq_classify: bad arguments");
+    return OCQ_EINVAL;
+  }
+  if (F == 0) return OCQ_OK;
+  return launch_classify(m, frames, F, mask, (cudaStream_t)stream);
+}
+
+ocq_status ocq_model_get_info(const ocq_model *m, ocq_model_info *info) {
+  g_err[0] = 0;
+  if (!m || !info) {
+    set_error("ocq_model_get_info: NULL argument");
+    return OCQ_EINVAL;
+  }
+  memset(info, 0, sizeof *info);
+  info->H = m->H, info->W = m->W, info->region_kind = m->kind, info->block = m->block;
+  info->depth = m->depth, info->T = m->T, info->N = m->N;
+  info->regions = m->R;
+  info->words_per_region = wpr64(m->depth);
+  return OCQ_OK;
+}
+
+ocq_status ocq_model_export(const ocq_model *m, uint64_t *dst, size_t words, void *stream) {
+  g_err[0] = 0;
+  if (!m || !dst || words < (size_t)m->R * (size_t)wpr64(m->depth)) {
+    set_error("ocq_model_export: NULL argument or destination too small");
+    return OCQ_EINVAL;
+  }
+  return launch_export(m->bits, m->R, m->depth, dst, (cudaStream_t)stream);
+}
+
+ocq_status ocq_model_import(const uint64_t *src, const ocq_model_info *info, void *stream, ocq_model **out) {
+  g_err[0] = 0;
+  if (!out || !src || !info) {
+    set_error("ocq_model_import: NULL argument");
+    return OCQ_EINVAL;
+  }
+  *out = nullptr;
+  ocq_region region = {info->region_kind, info->block};
+  ocq_status rc = check_geometry(info->H, info->W, region, info->depth);
+  if (rc != OCQ_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  ocq_model *m = new_model(info->H, info->W, region, info->depth, info->T, info->N, st, &rc);
+  if (!m) return rc;
+  rc = launch_import(src, m->R, m->depth, m->bits, st);
+  if (rc != OCQ_OK) {
+    ocq_model_free(m);
+    return rc;
+  }
+  *out = m;
+  return OCQ_OK;
+}
+
+void ocq_model_free(ocq_model *m) {
+  if (!m) return;
+  if (m->bits) cudaFreeAsync(m->bits, m->stream);
+  delete m;
+}
+
+/* Synchronises `stream` and reports (then clears) a bounded-wait timeout
+ * recorded by a kernel on the current device: OCQ_ETIMEOUT if one occurred. */
+ocq_status ocq_device_status(void *stream) {
+  g_err[0] = 0;
+  return device_status((cudaStream_t)stream);
+}
+
+}  // extern "C"

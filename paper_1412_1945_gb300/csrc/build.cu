@@ -1,0 +1,442 @@
+// S2 (per-frame leaf sets, Alg. 1 per frame and region) and S3 (merge by
+// frequency, Alg. 2) on the GPU.
+//
+// Merge Trees keeps a leaf exactly when at least T of the N per-frame trees
+// contain it (every tree holding a leaf holds all its ancestors, so the
+// level-by-level test never rejects an ancestor of a kept leaf).  The kernels
+// therefore count, per region and leaf, the frames whose tree holds the leaf,
+// and compare with T:
+//   * whole-frame regions (and large-depth blocks): per-frame leaf bitsets in
+//     global scratch, folded into bit-sliced counters (32 leaves per word);
+//   * block regions, depth <= 5: one CTA per block, per-frame bitset and
+//     bit-sliced counters in shared memory;
+//   * pixel regions, depth <= 3: one thread per pixel location with private
+//     byte (or u16) counters for all 8^d leaves in shared memory;
+//   * pixel regions, depth >= 4: per-thread counters for 512-leaf chunks, only
+//     for chunks the pixel's N colours touch.
+#include <cstdint>
+
+#include "pixels.cuh"
+
+namespace ocq {
+
+static int bit_length(uint32_t v) {
+  int n = 0;
+  while (v) ++n, v >>= 1;
+  return n;
+}
+
+template <int MAXP>
+__device__ __forceinline__ void planes_add_reg(uint32_t (&pl)[MAXP], int P, uint32_t x) {
+#pragma unroll
+  for (int k = 0; k < MAXP; ++k) {
+    if (k < P) {
+      uint32_t t = pl[k] & x;
+      pl[k] ^= x;
+      x = t;
+    }
+  }
+}
+
+template <int MAXP>
+__device__ __forceinline__ uint32_t planes_ge_reg(const uint32_t (&pl)[MAXP], int P, uint32_t T) {
+  uint32_t gt = 0, eq = 0xFFFFFFFFu;
+#pragma unroll
+  for (int k = MAXP - 1; k >= 0; --k) {
+    if (k < P) {
+      const uint32_t c = pl[k];
+      if ((T >> k) & 1u) {
+        eq &= c;
+      } else {
+        gt |= eq & c;
+        eq &= ~c;
+      }
+    }
+  }
+  return gt | eq;
+}
+
+// ---- dense per-frame occupancy ----------------------------------------------
+
+// Whole-frame regions, depth <= 6: CTA (x, y) marks the leaves of pixel chunk x
+// of frame f0 + y in a shared bitset, then ORs it into occ[y].
+template <int D>
+__global__ void __launch_bounds__(256) occ_frame_kernel(const uint8_t *__restrict__ frames, int64_t hw, int f0,
+                                                        int64_t chunk, uint32_t *__restrict__ occ) {
+  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  __shared__ uint32_t seen[WPR];
+  for (int i = threadIdx.x; i < WPR; i += blockDim.x) seen[i] = 0;
+  __syncthreads();
+  const uint8_t *fr = frames + (int64_t)(f0 + blockIdx.y) * hw * 3;
+  const int64_t p0 = (int64_t)blockIdx.x * chunk;
+  const int64_t p1 = p0 + chunk < hw ? p0 + chunk : hw;
+  cta_for_codes<D>(fr, p0, p1, [&](uint32_t q, int64_t) {
+    const uint32_t m = 1u << (q & 31);
+    if (!(seen[q >> 5] & m)) atomicOr(&seen[q >> 5], m);
+  });
+  __syncthreads();
+  uint32_t *dst = occ + (int64_t)blockIdx.y * WPR;
+  for (int i = threadIdx.x; i < WPR; i += blockDim.x)
+    if (seen[i]) atomicOr(&dst[i], seen[i]);
+}
+
+// Any region kind and depth: one thread per pixel, global atomics into
+// occ[(f - f0) * R + r][...].
+__global__ void occ_global_kernel(const uint8_t *__restrict__ frames, int H, int W, int kind, int block, int d,
+                                  int f0, int nf, int64_t R, int64_t wpr, uint32_t *__restrict__ occ) {
+  const int64_t hw = (int64_t)H * W;
+  const int64_t npix = hw * nf;
+  const int bw = kind == OCQ_REGION_BLOCK ? (W + block - 1) / block : 1;
+  const uint8_t *base = frames + (int64_t)f0 * hw * 3;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = i / hw, p = i - f * hw;
+    const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
+    const uint8_t *px = base + i * 3;
+    const uint32_t q = planar_code_rt(__ldg(px), __ldg(px + 1), __ldg(px + 2), d);
+    uint32_t *word = occ + (f * R + region_of(y, x, W, kind, block, bw)) * wpr + (q >> 5);
+    const uint32_t m = 1u << (q & 31);
+    if (!(*(volatile uint32_t *)word & m)) atomicOr(word, m);
+  }
+}
+
+// Folds nb frames of occupancy words into bit-sliced counters; on the last
+// batch writes count >= T into the model.
+__global__ void planes_merge_kernel(const uint32_t *__restrict__ occ, int nb, int64_t nwords,
+                                    uint32_t *__restrict__ planes, int P, int first, int last, uint32_t T,
+                                    uint32_t *__restrict__ model) {
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwords; w += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t pl[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) pl[k] = (!first && k < P) ? planes[k * nwords + w] : 0u;
+    for (int f = 0; f < nb; ++f) planes_add_reg<16>(pl, P, __ldg(occ + f * nwords + w));
+    if (last) {
+      model[w] = planes_ge_reg<16>(pl, P, T);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (k < P) planes[k * nwords + w] = pl[k];
+    }
+  }
+}
+
+// ---- block regions, depth <= 5 -----------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(256) build_block_kernel(const uint8_t *__restrict__ frames, int N, int H, int W,
+                                                          int b, int bw, int P, uint32_t T,
+                                                          uint32_t *__restrict__ model) {
+  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  extern __shared__ uint32_t sm[];
+  uint32_t *seen = sm;         // [WPR]
+  uint32_t *planes = sm + WPR; // [P][WPR]
+  for (int i = threadIdx.x; i < WPR * (P + 1); i += blockDim.x) sm[i] = 0;
+  const int64_t r = blockIdx.x;
+  const int y0 = (int)(r / bw) * b, x0 = (int)(r % bw) * b;
+  const int h = min(b, H - y0), w = min(b, W - x0);
+  const int npx = h * w;
+  const int64_t hw = (int64_t)H * W;
+  __syncthreads();
+  for (int f = 0; f < N; ++f) {
+    const uint8_t *fr = frames + (int64_t)f * hw * 3;
+    for (int i = threadIdx.x; i < npx; i += blockDim.x) {
+      const int y = y0 + i / w, x = x0 + i % w;
+      const uint8_t *px = fr + ((int64_t)y * W + x) * 3;
+      const uint32_t q = planar_code_rt(__ldg(px), __ldg(px + 1), __ldg(px + 2), D);
+      const uint32_t m = 1u << (q & 31);
+      if (!(seen[q >> 5] & m)) atomicOr(&seen[q >> 5], m);
+    }
+    __syncthreads();
+    for (int wd = threadIdx.x; wd < WPR; wd += blockDim.x) {
+      uint32_t x = seen[wd];
+      if (x) {
+        for (int k = 0; k < P && x; ++k) {
+          const uint32_t t = planes[k * WPR + wd] & x;
+          planes[k * WPR + wd] ^= x;
+          x = t;
+        }
+        seen[wd] = 0;
+      }
+    }
+    __syncthreads();
+  }
+  for (int wd = threadIdx.x; wd < WPR; wd += blockDim.x) {
+    uint32_t gt = 0, eq = 0xFFFFFFFFu;
+    for (int k = P - 1; k >= 0; --k) {
+      const uint32_t c = planes[k * WPR + wd];
+      if ((T >> k) & 1u) {
+        eq &= c;
+      } else {
+        gt |= eq & c;
+        eq &= ~c;
+      }
+    }
+    model[r * WPR + wd] = gt | eq;
+  }
+}
+
+// ---- pixel regions, depth <= 3 -------------------------------------------------
+// Thread t of a 128-thread CTA owns pixel location p and a private column of
+// counter words cnt[k * 128 + t] (4 u8 or 2 u16 counters per word).
+template <int D, bool WIDE>
+__global__ void __launch_bounds__(128) build_pixel_counters_kernel(const uint8_t *__restrict__ frames, int N,
+                                                                   int64_t hw, uint32_t T,
+                                                                   uint32_t *__restrict__ model) {
+  constexpr int NC = 1 << (3 * D);
+  constexpr int CPW = WIDE ? 2 : 4;
+  constexpr int BITS = 32 / CPW;
+  constexpr int NW = (NC + CPW - 1) / CPW;
+  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  extern __shared__ uint32_t cnt[];
+  const int t = threadIdx.x;
+  const int64_t p = (int64_t)blockIdx.x * 128 + t;
+  if (p >= hw) return;  // columns are private: no CTA-wide synchronisation below
+#pragma unroll 8
+  for (int k = 0; k < NW; ++k) cnt[k * 128 + t] = 0;
+  const uint8_t *px = frames + p * 3;
+  const int64_t fstride = hw * 3;
+  int f = 0;
+  for (; f + 4 <= N; f += 4) {
+    uint32_t q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint8_t *s = px + (int64_t)(f + u) * fstride;
+      q[u] = planar_code_rt(__ldg(s), __ldg(s + 1), __ldg(s + 2), D);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cnt[(q[u] / CPW) * 128 + t] += 1u << ((q[u] % CPW) * BITS);
+  }
+  for (; f < N; ++f) {
+    const uint8_t *s = px + (int64_t)f * fstride;
+    const uint32_t q = planar_code_rt(__ldg(s), __ldg(s + 1), __ldg(s + 2), D);
+    cnt[(q / CPW) * 128 + t] += 1u << ((q % CPW) * BITS);
+  }
+  uint32_t out[WPR];
+#pragma unroll
+  for (int w = 0; w < WPR; ++w) out[w] = 0;
+#pragma unroll
+  for (int k = 0; k < NW; ++k) {
+    const uint32_t v = cnt[k * 128 + t];
+    uint32_t bits;
+    if constexpr (WIDE) {
+      const uint32_t ge = __vcmpgeu2(v, T * 0x00010001u);
+      bits = ((ge >> 15) & 1u) | ((ge >> 30) & 2u);
+    } else {
+      const uint32_t ge = __vcmpgeu4(v, T * 0x01010101u);
+      bits = ((ge >> 7) & 1u) | ((ge >> 14) & 2u) | ((ge >> 21) & 4u) | ((ge >> 28) & 8u);
+    }
+    const int c0 = k * CPW;  // first leaf of this counter word
+    if (c0 < NC) out[c0 >> 5] |= bits << (c0 & 31);
+  }
+  if (NC < 32) out[0] &= (NC < 32 ? ((1u << NC) - 1u) : 0xFFFFFFFFu);
+  uint32_t *dst = model + p * WPR;
+#pragma unroll
+  for (int w = 0; w < WPR; ++w) dst[w] = out[w];
+}
+
+// ---- pixel regions, depth >= 4 --------------------------------------------------
+// Counts leaves chunk by chunk (512 leaves, u16 counters in a private column
+// of 256 words) for the chunks the pixel's training colours touch.  `touched`
+// is a per-pixel chunk bitmap in global scratch (depth >= 6) or a register.
+template <int D>
+__global__ void __launch_bounds__(64) build_pixel_chunked_kernel(const uint8_t *__restrict__ frames, int N,
+                                                                 int64_t hw, uint32_t T, uint32_t *__restrict__ model,
+                                                                 uint32_t *__restrict__ touched_g) {
+  constexpr int NCH = 1 << (3 * D - 9);
+  constexpr int WPR = 1 << (3 * D - 5);
+  constexpr int TW = NCH / 32 > 0 ? NCH / 32 : 1;  // touched words per pixel (global form)
+  extern __shared__ uint32_t cnt[];                 // [256][64]
+  const int t = threadIdx.x;
+  const int64_t p = (int64_t)blockIdx.x * 64 + t;
+  if (p >= hw) return;
+  const uint8_t *px = frames + p * 3;
+  const int64_t fstride = hw * 3;
+  uint64_t touched = 0;
+  uint32_t *tg = touched_g ? touched_g + p * TW : nullptr;
+  for (int f = 0; f < N; ++f) {
+    const uint8_t *s = px + (int64_t)f * fstride;
+    const uint32_t q = planar_code_rt(__ldg(s), __ldg(s + 1), __ldg(s + 2), D);
+    const uint32_t c = q >> 9;
+    if constexpr (NCH <= 64)
+      touched |= 1ull << c;
+    else
+      tg[c >> 5] |= 1u << (c & 31);
+  }
+  uint32_t *row = model + p * WPR;
+  int tw = 0;
+  uint32_t cur = 0;
+  while (true) {
+    int c;
+    if constexpr (NCH <= 64) {
+      if (!touched) break;
+      c = __ffsll((long long)touched) - 1;
+      touched &= touched - 1;
+    } else {
+      while (!cur && tw < TW) cur = tg[tw++];
+      if (!cur) break;
+      c = (tw - 1) * 32 + __ffs(cur) - 1;
+      cur &= cur - 1;
+    }
+    for (int k = 0; k < 256; ++k) cnt[k * 64 + t] = 0;
+    for (int f = 0; f < N; ++f) {
+      const uint8_t *s = px + (int64_t)f * fstride;
+      const uint32_t q = planar_code_rt(__ldg(s), __ldg(s + 1), __ldg(s + 2), D);
+      if ((int)(q >> 9) == c) cnt[((q & 511u) >> 1) * 64 + t] += 1u << ((q & 1u) * 16);
+    }
+    for (int w = 0; w < 16; ++w) {
+      uint32_t out = 0;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const uint32_t ge = __vcmpgeu2(cnt[(w * 16 + k) * 64 + t], T * 0x00010001u);
+        out |= (((ge >> 15) & 1u) | ((ge >> 30) & 2u)) << (2 * k);
+      }
+      row[c * 16 + w] = out;
+    }
+  }
+}
+
+// ---- host dispatch ----------------------------------------------------------------
+
+static unsigned grid_cap(int64_t work, int threads, int per_sm) {
+  int64_t b = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  if (b > cap) b = cap;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <int D>
+static void launch_occ_frame(const uint8_t *frames, int64_t hw, int f0, int nf, uint32_t *occ, cudaStream_t st) {
+  const int64_t chunk = 256 * 16 * 4;  // pixels per CTA (multiple of 16)
+  dim3 grid((unsigned)((hw + chunk - 1) / chunk), (unsigned)nf);
+  occ_frame_kernel<D><<<grid, 256, 0, st>>>(frames, hw, f0, chunk, occ);
+  count_launch();
+}
+
+static ocq_status build_dense(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  const int P = bit_length((uint32_t)N);
+  const int64_t nwords = m->R * m->wpr;
+  const int64_t hw = (int64_t)m->H * m->W;
+  const int64_t budget = (int64_t)512 << 20;
+  int nb = N;
+  if ((int64_t)N * nwords * 4 > budget) nb = (int)(budget / (nwords * 4) > 0 ? budget / (nwords * 4) : 1);
+  if (nb > N) nb = N;
+  const bool multi = nb < N;
+  uint32_t *occ = nullptr, *planes = nullptr;
+  ocq_status rc = cuda_status(cudaMallocAsync((void **)&occ, (size_t)nb * nwords * 4, st), "build scratch");
+  if (rc != OCQ_OK) return rc;
+  if (multi) {
+    rc = cuda_status(cudaMallocAsync((void **)&planes, (size_t)P * nwords * 4, st), "build counters");
+    if (rc != OCQ_OK) {
+      cudaFreeAsync(occ, st);
+      return rc;
+    }
+  }
+  for (int f0 = 0; f0 < N && rc == OCQ_OK; f0 += nb) {
+    const int nf = N - f0 < nb ? N - f0 : nb;
+    rc = cuda_status(cudaMemsetAsync(occ, 0, (size_t)nf * nwords * 4, st), "clear occupancy");
+    if (rc != OCQ_OK) break;
+    if (m->kind == OCQ_REGION_FRAME && m->depth <= 6) {
+      switch (m->depth) {
+        case 1: launch_occ_frame<1>(frames, hw, f0, nf, occ, st); break;
+        case 2: launch_occ_frame<2>(frames, hw, f0, nf, occ, st); break;
+        case 3: launch_occ_frame<3>(frames, hw, f0, nf, occ, st); break;
+        case 4: launch_occ_frame<4>(frames, hw, f0, nf, occ, st); break;
+        case 5: launch_occ_frame<5>(frames, hw, f0, nf, occ, st); break;
+        default: launch_occ_frame<6>(frames, hw, f0, nf, occ, st); break;
+      }
+    } else {
+      occ_global_kernel<<<grid_cap(hw * nf, 256, 16), 256, 0, st>>>(frames, m->H, m->W, m->kind, m->block, m->depth,
+                                                                     f0, nf, m->R, m->wpr, occ);
+      count_launch();
+    }
+    rc = cuda_status(cudaGetLastError(), "occupancy kernel");
+    if (rc != OCQ_OK) break;
+    planes_merge_kernel<<<grid_cap(nwords, 256, 8), 256, 0, st>>>(occ, nf, nwords, planes, P, f0 == 0,
+                                                                   f0 + nf >= N, (uint32_t)m->T, m->bits);
+    count_launch();
+    rc = cuda_status(cudaGetLastError(), "planes_merge_kernel");
+  }
+  cudaFreeAsync(occ, st);
+  if (planes) cudaFreeAsync(planes, st);
+  return rc;
+}
+
+template <int D>
+static ocq_status launch_block(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  const int P = bit_length((uint32_t)N);
+  const size_t smem = (size_t)WPR * (P + 1) * 4;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(build_block_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int bw = (m->W + m->block - 1) / m->block;
+  build_block_kernel<D><<<(unsigned)m->R, 256, smem, st>>>(frames, N, m->H, m->W, m->block, bw, P, (uint32_t)m->T,
+                                                            m->bits);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "build_block_kernel");
+}
+
+template <int D, bool WIDE>
+static ocq_status launch_pixel_counters(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  constexpr int NC = 1 << (3 * D);
+  constexpr int CPW = WIDE ? 2 : 4;
+  constexpr int NW = (NC + CPW - 1) / CPW;
+  const size_t smem = (size_t)NW * 128 * 4;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(build_pixel_counters_kernel<D, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+  const int64_t hw = (int64_t)m->H * m->W;
+  build_pixel_counters_kernel<D, WIDE>
+      <<<(unsigned)((hw + 127) / 128), 128, smem, st>>>(frames, N, hw, (uint32_t)m->T, m->bits);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "build_pixel_counters_kernel");
+}
+
+template <int D>
+static ocq_status launch_pixel_chunked(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  constexpr int NCH = 1 << (3 * D - 9);
+  const int64_t hw = (int64_t)m->H * m->W;
+  ocq_status rc = cuda_status(cudaMemsetAsync(m->bits, 0, m->bytes, st), "clear model");
+  if (rc != OCQ_OK) return rc;
+  uint32_t *touched = nullptr;
+  if (NCH > 64) {
+    const size_t tb = (size_t)hw * (NCH / 32) * 4;
+    rc = cuda_status(cudaMallocAsync((void **)&touched, tb, st), "chunk bitmap");
+    if (rc != OCQ_OK) return rc;
+    rc = cuda_status(cudaMemsetAsync(touched, 0, tb, st), "clear chunk bitmap");
+  }
+  if (rc == OCQ_OK) {
+    const size_t smem = 256 * 64 * 4;
+    cudaFuncSetAttribute(build_pixel_chunked_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    build_pixel_chunked_kernel<D><<<(unsigned)((hw + 63) / 64), 64, smem, st>>>(frames, N, hw, (uint32_t)m->T,
+                                                                                 m->bits, touched);
+    count_launch();
+    rc = cuda_status(cudaGetLastError(), "build_pixel_chunked_kernel");
+  }
+  if (touched) cudaFreeAsync(touched, st);
+  return rc;
+}
+
+ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  const int d = m->depth;
+  if (m->kind == OCQ_REGION_FRAME || (m->kind == OCQ_REGION_BLOCK && d >= 6)) return build_dense(frames, N, m, st);
+  if (m->kind == OCQ_REGION_BLOCK) {
+    switch (d) {
+      case 1: return launch_block<1>(frames, N, m, st);
+      case 2: return launch_block<2>(frames, N, m, st);
+      case 3: return launch_block<3>(frames, N, m, st);
+      case 4: return launch_block<4>(frames, N, m, st);
+      default: return launch_block<5>(frames, N, m, st);
+    }
+  }
+  const bool wide = N > 255;
+  switch (d) {
+    case 1: return wide ? launch_pixel_counters<1, true>(frames, N, m, st) : launch_pixel_counters<1, false>(frames, N, m, st);
+    case 2: return wide ? launch_pixel_counters<2, true>(frames, N, m, st) : launch_pixel_counters<2, false>(frames, N, m, st);
+    case 3: return wide ? launch_pixel_counters<3, true>(frames, N, m, st) : launch_pixel_counters<3, false>(frames, N, m, st);
+    case 4: return launch_pixel_chunked<4>(frames, N, m, st);
+    case 5: return launch_pixel_chunked<5>(frames, N, m, st);
+    case 6: return launch_pixel_chunked<6>(frames, N, m, st);
+    case 7: return launch_pixel_chunked<7>(frames, N, m, st);
+    default: return launch_pixel_chunked<8>(frames, N, m, st);
+  }
+}
+
+}  // namespace ocq

@@ -1,0 +1,401 @@
+// S4: Check Color (Alg. 3) for every pixel of incoming frames (Sec. 4).
+// A pixel is background when the bit of its leaf is set in its region's row.
+//
+// Kernels:
+//   classify_generic_kernel      any region/depth: per-pixel global lookups.
+//   classify_frame_kernel<D>     whole-frame regions, depth <= 6: the one row
+//                                lives in shared memory (replicated per lane
+//                                for depth <= 4 so lookups never conflict),
+//                                frames stream through 16-byte loads.
+//   classify_pixel_tiled_kernel  pixel regions, depth <= 3: temporal blocking.
+//                                A CTA keeps the rows of a tile of pixel
+//                                locations in shared memory (lane-interleaved:
+//                                each lane's rows sit in its own bank) and
+//                                streams that tile of many frames through a
+//                                ring of stages filled by bulk asynchronous
+//                                copies (cp.async.bulk + mbarrier), so each
+//                                row is read from HBM about once per launch.
+#include <cstdint>
+
+#include "pixels.cuh"
+
+namespace ocq {
+
+// Set when a bounded wait gives up; read and cleared by device_status().
+__device__ unsigned int g_classify_timeout;
+
+// ---- generic ---------------------------------------------------------------------
+__global__ void classify_generic_kernel(const uint8_t *__restrict__ frames, int F, int H, int W, int kind, int block,
+                                        int d, int64_t wpr, const uint32_t *__restrict__ model,
+                                        uint8_t *__restrict__ mask, int64_t pb, int64_t pe) {
+  const int64_t hw = (int64_t)H * W;
+  const int64_t n = pe - pb;
+  const int64_t total = n * F;
+  const int bw = kind == OCQ_REGION_BLOCK ? (W + block - 1) / block : 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = i / n;
+    const int64_t p = pb + (i - f * n);
+    const int64_t g = f * hw + p;
+    const uint8_t *px = frames + g * 3;
+    const uint32_t q = planar_code_rt(__ldg(px), __ldg(px + 1), __ldg(px + 2), d);
+    const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
+    const uint32_t word = __ldg(model + region_of(y, x, W, kind, block, bw) * wpr + (q >> 5));
+    mask[g] = (uint8_t)(((word >> (q & 31)) & 1u) ^ 1u);
+  }
+}
+
+// Four pixels' background bits (bit 0 of each of f0..f3) -> four mask bytes.
+__device__ __forceinline__ uint32_t pack_mask4(uint32_t f0, uint32_t f1, uint32_t f2, uint32_t f3) {
+  const uint32_t lo = __byte_perm(f0, f1, 0x0040);
+  const uint32_t hi = __byte_perm(f2, f3, 0x0040);
+  const uint32_t v = __byte_perm(lo, hi, 0x5410);
+  return ~v & 0x01010101u;
+}
+
+// ---- whole-frame regions ------------------------------------------------------------
+template <int D>
+__global__ void __launch_bounds__(256) classify_frame_kernel(const uint8_t *__restrict__ frames, int64_t npix,
+                                                             const uint32_t *__restrict__ model,
+                                                             uint8_t *__restrict__ mask) {
+  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  constexpr int REP = D <= 4 ? 32 : 1;
+  extern __shared__ uint32_t row[];  // [WPR][REP]
+  for (int i = threadIdx.x; i < WPR * REP; i += blockDim.x) row[i] = __ldg(model + i / REP);
+  __syncthreads();
+  const int rep = REP == 32 ? (threadIdx.x & 31) : 0;
+  const bool vec = ((reinterpret_cast<uintptr_t>(frames) | reinterpret_cast<uintptr_t>(mask)) & 15) == 0;
+  int64_t tail = 0;
+  if (vec) {
+    const int64_t ng = npix >> 4;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+      uint32_t w[12];
+      load_group_masked<D, true>(frames + g * 48, w);
+      uint32_t fbit[16];
+      static_for<0, 16>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const uint32_t q = planar_from_masked<D>(group_pixel<k>(w));
+        const uint32_t v = row[(q >> 5) * REP + rep];
+        fbit[k] = __funnelshift_r(v, v, q);
+      });
+      uint4 o;
+      o.x = pack_mask4(fbit[0], fbit[1], fbit[2], fbit[3]);
+      o.y = pack_mask4(fbit[4], fbit[5], fbit[6], fbit[7]);
+      o.z = pack_mask4(fbit[8], fbit[9], fbit[10], fbit[11]);
+      o.w = pack_mask4(fbit[12], fbit[13], fbit[14], fbit[15]);
+      st_stream16(mask + g * 16, o);
+    }
+    tail = ng << 4;
+  }
+  for (int64_t p = tail + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t *px = frames + p * 3;
+    const uint32_t q = planar_code_rt(px[0], px[1], px[2], D);
+    mask[p] = (uint8_t)(((row[(q >> 5) * REP + rep] >> (q & 31)) & 1u) ^ 1u);
+  }
+}
+
+// ---- pixel regions: temporal blocking with bulk async copies --------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for phase `parity` of `bar` to complete; gives up after `limit_ns`.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (true) {
+    for (int i = 0; i < 64; ++i)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
+static constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
+
+template <int D, int NW, int PPT, int S>
+struct TiledCfg {
+  static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  static constexpr int THREADS = NW * 32;
+  static constexpr int TILE = THREADS * PPT;       // pixel locations per tile
+  static constexpr int STAGE = TILE * 3;           // bytes of one frame's tile
+  static constexpr int MODEL_WORDS = TILE * WPR;
+  static constexpr size_t SMEM = (size_t)MODEL_WORDS * 4 + (size_t)S * STAGE + (size_t)S * 8;
+  static_assert(STAGE % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static_assert(PPT == 8 || PPT == 16, "8 or 16 pixels per thread");
+};
+
+// Work item u = tile * F + f; CTA b handles u in [b*U/G, (b+1)*U/G), i.e. a run
+// of frames of one tile, then of the next, reloading the tile's rows at each
+// tile change.  Requires: frames and mask 16-byte aligned, H*W % 16 == 0.
+template <int D, int NW, int PPT, int S>
+__global__ void __launch_bounds__(NW * 32, 1)
+    classify_pixel_tiled_kernel(const uint8_t *__restrict__ frames, int F, int64_t hw, int64_t ntiles,
+                                const uint32_t *__restrict__ model, uint8_t *__restrict__ mask) {
+  using C = TiledCfg<D, NW, PPT, S>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint32_t *msm = reinterpret_cast<uint32_t *>(smem);
+  uint8_t *stages = smem + (size_t)C::MODEL_WORDS * 4;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stages + (size_t)S * C::STAGE);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const int64_t U = ntiles * (int64_t)F;
+  const int64_t u_begin = U * blockIdx.x / gridDim.x;
+  const int64_t u_end = U * (blockIdx.x + 1) / gridDim.x;
+  uint64_t kc = 0;  // copies consumed so far (stage = kc % S, phase = (kc / S) & 1)
+
+  for (int64_t u = u_begin; u < u_end;) {
+    const int64_t tile = u / F;
+    const int fa = (int)(u - tile * F);
+    const int nfr = (int)((u_end - u) < (int64_t)(F - fa) ? (u_end - u) : (int64_t)(F - fa));
+    const int64_t p_tile = tile * C::TILE;
+
+    // Rows of this tile -> shared memory, word w of pixel (warp, lane, j) at
+    // ((warp*PPT + j)*WPR + w)*32 + lane.
+    {
+      const uint32_t *src = model + (p_tile + (int64_t)tid * PPT) * C::WPR;
+      if constexpr (C::WPR % 4 == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+#pragma unroll 4
+        for (int i = 0; i < PPT * C::WPR / 4; ++i) {
+          const uint4 v = __ldg(s4 + i);
+          const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int idx = i * 4 + e, j = idx / C::WPR, w = idx % C::WPR;
+            msm[((warp * PPT + j) * C::WPR + w) * 32 + lane] = vv[e];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int idx = 0; idx < PPT * C::WPR; ++idx) {
+          const int j = idx / C::WPR, w = idx % C::WPR;
+          msm[((warp * PPT + j) * C::WPR + w) * 32 + lane] = __ldg(src + idx);
+        }
+      }
+    }
+    __syncthreads();
+
+    if (tid == 0) {
+      const int pre = nfr < S ? nfr : S;
+      for (int i = 0; i < pre; ++i) {
+        const int s = (int)((kc + i) % S);
+        const uint32_t bar = smem_addr(&bars[s]);
+        mbar_expect_tx(bar, C::STAGE);
+        bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE), frames + ((int64_t)(fa + i) * hw + p_tile) * 3, C::STAGE,
+                 bar);
+      }
+    }
+
+    for (int i = 0; i < nfr; ++i) {
+      const uint64_t k = kc + i;
+      const int s = (int)(k % S);
+      const uint32_t parity = (uint32_t)((k / S) & 1);
+      const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), parity, kWaitLimitNs);
+      const uint8_t *stage = stages + (size_t)s * C::STAGE;
+      const int64_t f = fa + i;
+      uint32_t fbit[PPT];
+      if constexpr (PPT == 16) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(stage + tid * 48);
+        uint32_t w[12];
+        const uint4 a = src[0], b = src[1], c = src[2];
+        w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w, w[4] = b.x, w[5] = b.y;
+        w[6] = b.z, w[7] = b.w, w[8] = c.x, w[9] = c.y, w[10] = c.z, w[11] = c.w;
+#pragma unroll
+        for (int e = 0; e < 12; ++e) w[e] = (w[e] >> (8 - D)) & byte_mask(D);
+        static_for<0, 16>([&](auto jc) {
+          constexpr int j = decltype(jc)::value;
+          const uint32_t q = planar_from_masked<D>(group_pixel<j>(w));
+          const uint32_t v = msm[((warp * PPT + j) * C::WPR + (q >> 5)) * 32 + lane];
+          fbit[j] = __funnelshift_r(v, v, q);
+        });
+      } else {
+        const uint2 *src = reinterpret_cast<const uint2 *>(stage + tid * 24);
+        uint32_t w[12];
+        const uint2 a = src[0], b = src[1], c = src[2];
+        w[0] = a.x, w[1] = a.y, w[2] = b.x, w[3] = b.y, w[4] = c.x, w[5] = c.y;
+        w[6] = w[7] = w[8] = w[9] = w[10] = w[11] = 0;
+#pragma unroll
+        for (int e = 0; e < 6; ++e) w[e] = (w[e] >> (8 - D)) & byte_mask(D);
+        static_for<0, 8>([&](auto jc) {
+          constexpr int j = decltype(jc)::value;
+          const uint32_t q = planar_from_masked<D>(group_pixel<j>(w));
+          const uint32_t v = msm[((warp * PPT + j) * C::WPR + (q >> 5)) * 32 + lane];
+          fbit[j] = __funnelshift_r(v, v, q);
+        });
+      }
+      uint8_t *dst = mask + f * hw + p_tile + (int64_t)tid * PPT;
+      if constexpr (PPT == 16) {
+        uint4 o;
+        o.x = pack_mask4(fbit[0], fbit[1], fbit[2], fbit[3]);
+        o.y = pack_mask4(fbit[4], fbit[5], fbit[6], fbit[7]);
+        o.z = pack_mask4(fbit[8], fbit[9], fbit[10], fbit[11]);
+        o.w = pack_mask4(fbit[12], fbit[13], fbit[14], fbit[15]);
+        st_stream16(dst, o);
+      } else {
+        uint2 o;
+        o.x = pack_mask4(fbit[0], fbit[1], fbit[2], fbit[3]);
+        o.y = pack_mask4(fbit[4], fbit[5], fbit[6], fbit[7]);
+        asm volatile("st.global.cs.v2.u32 [%0], {%1,%2};" ::"l"(dst), "r"(o.x), "r"(o.y) : "memory");
+      }
+      // Stage s is consumed by every thread; refill it with frame i + S.
+      if (__syncthreads_or(!ok)) {
+        // A copy did not arrive in time: record it, let every copy this CTA
+        // still has in flight land (bounded), and leave.
+        if (tid == 0) {
+          atomicExch(&g_classify_timeout, 1u);
+          const int inflight = (nfr - i) < S ? (nfr - i) : S;
+          for (int j = 0; j < inflight; ++j) {
+            const uint64_t kk = k + j;
+            mbar_wait_bounded(smem_addr(&bars[kk % S]), (uint32_t)((kk / S) & 1), kWaitLimitNs);
+          }
+        }
+        __syncthreads();
+        return;
+      }
+      if (tid == 0 && i + S < nfr) {
+        const uint32_t bar = smem_addr(&bars[s]);
+        mbar_expect_tx(bar, C::STAGE);
+        bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE), frames + ((int64_t)(fa + i + S) * hw + p_tile) * 3,
+                 C::STAGE, bar);
+      }
+    }
+    kc += nfr;
+    u += nfr;
+    __syncthreads();  // all reads of this tile's rows are done before the next reload
+  }
+}
+
+// ---- host dispatch -----------------------------------------------------------------------
+
+static unsigned grid_cap(int64_t work, int threads, int per_sm) {
+  int64_t b = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  if (b > cap) b = cap;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+static ocq_status launch_generic(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, int64_t pb,
+                                 int64_t pe, cudaStream_t st) {
+  if (pe <= pb) return OCQ_OK;
+  classify_generic_kernel<<<grid_cap((pe - pb) * F, 256, 16), 256, 0, st>>>(
+      frames, F, m->H, m->W, m->kind, m->block, m->depth, m->wpr, m->bits, mask, pb, pe);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "classify_generic_kernel");
+}
+
+template <int D>
+static ocq_status launch_frame(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st) {
+  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  constexpr int REP = D <= 4 ? 32 : 1;
+  const size_t smem = (size_t)WPR * REP * 4;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(classify_frame_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t npix = (int64_t)F * m->H * m->W;
+  const int per_sm = smem > 64 * 1024 ? 1 : 4;
+  classify_frame_kernel<D><<<grid_cap((npix + 15) / 16, 256, per_sm), 256, smem, st>>>(frames, npix, m->bits, mask);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "classify_frame_kernel");
+}
+
+template <int D, int NW, int PPT, int S>
+static ocq_status launch_tiled(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st) {
+  using C = TiledCfg<D, NW, PPT, S>;
+  const int64_t hw = (int64_t)m->H * m->W;
+  const int64_t ntiles = hw / C::TILE;
+  ocq_status rc = OCQ_OK;
+  if (ntiles > 0) {
+    auto kern = classify_pixel_tiled_kernel<D, NW, PPT, S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return cuda_status(e, "classify_pixel_tiled_kernel smem");
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS, C::SMEM);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sm_count() * per_sm;
+    const int64_t U = ntiles * F;
+    if (grid > U) grid = U;
+    kern<<<(unsigned)grid, C::THREADS, C::SMEM, st>>>(frames, F, hw, ntiles, m->bits, mask);
+    count_launch();
+    rc = cuda_status(cudaGetLastError(), "classify_pixel_tiled_kernel");
+  }
+  if (rc == OCQ_OK) rc = launch_generic(m, frames, F, mask, ntiles * C::TILE, hw, st);
+  return rc;
+}
+
+ocq_status launch_classify(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st) {
+  const int64_t hw = (int64_t)m->H * m->W;
+  const int d = m->depth;
+  if (m->kind == OCQ_REGION_FRAME && d <= 6) {
+    switch (d) {
+      case 1: return launch_frame<1>(m, frames, F, mask, st);
+      case 2: return launch_frame<2>(m, frames, F, mask, st);
+      case 3: return launch_frame<3>(m, frames, F, mask, st);
+      case 4: return launch_frame<4>(m, frames, F, mask, st);
+      case 5: return launch_frame<5>(m, frames, F, mask, st);
+      default: return launch_frame<6>(m, frames, F, mask, st);
+    }
+  }
+  const bool aligned = ((reinterpret_cast<uintptr_t>(frames) | reinterpret_cast<uintptr_t>(mask)) & 15) == 0;
+  if (m->kind == OCQ_REGION_PIXEL && d <= 3 && aligned && hw % 16 == 0) {
+    switch (d) {
+      case 1: return launch_tiled<1, 4, 8, 12>(m, frames, F, mask, st);
+      case 2: return launch_tiled<2, 4, 8, 12>(m, frames, F, mask, st);
+      default: return launch_tiled<3, 4, 8, 12>(m, frames, F, mask, st);
+    }
+  }
+  return launch_generic(m, frames, F, mask, 0, hw, st);
+}
+
+ocq_status device_status(cudaStream_t st) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e, "stream synchronise");
+  unsigned int flag = 0, zero = 0;
+  e = cudaMemcpyFromSymbol(&flag, g_classify_timeout, sizeof flag);
+  if (e != cudaSuccess) return cuda_status(e, "reading the device status");
+  if (flag) {
+    cudaMemcpyToSymbol(g_classify_timeout, &zero, sizeof zero);
+    set_error("a bounded device wait timed out");
+    return OCQ_ETIMEOUT;
+  }
+  return OCQ_OK;
+}
+
+}  // namespace ocq

@@ -1,0 +1,141 @@
+// S1 as a standalone kernel, S2 per-frame occupancy, and the translation
+// between the library's planar leaf order and the path-code order of the
+// public bitset layout (export / import).
+#include "ocq_internal.cuh"
+
+namespace ocq {
+
+// ---- S1: path code per pixel (Alg. 1 walk, pruned at depth d, Sec. 2) --------
+__global__ void path_code_kernel(const uint8_t *__restrict__ rgb, int64_t npix, int d, uint32_t *__restrict__ codes) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t r = rgb[3 * i], g = rgb[3 * i + 1], b = rgb[3 * i + 2];
+    uint32_t c = 0;
+    for (int l = 0; l < d; ++l) {  // level l reads bit 7-l of each channel
+      const int bit = 7 - l;
+      c = (c << 3) | (((r >> bit) & 1u) << 2) | (((g >> bit) & 1u) << 1) | ((b >> bit) & 1u);
+    }
+    codes[i] = c;
+  }
+}
+
+static unsigned grid_for(int64_t work, int threads, int per_sm = 16) {
+  int64_t b = (work + threads - 1) / threads;
+  int64_t cap = (int64_t)sm_count() * per_sm;
+  if (b > cap) b = cap;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+ocq_status launch_path_code(const uint8_t *rgb, int64_t npix, int depth, uint32_t *codes, cudaStream_t st) {
+  path_code_kernel<<<grid_for(npix, 256), 256, 0, st>>>(rgb, npix, depth, codes);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "path_code_kernel");
+}
+
+// ---- planar <-> path translation ------------------------------------------------
+
+// Output word k of a region row in the public layout: bits of path codes
+// 64k .. 64k+63 (fewer when d <= 1).
+__global__ void export_kernel(const uint32_t *__restrict__ bits, int64_t R, int d, int64_t wpr_in, int64_t wpr_out,
+                              uint64_t *__restrict__ dst) {
+  extern __shared__ uint16_t lut[];  // path code -> planar code, when 8^d <= 32768
+  const uint32_t ncodes = 1u << (3 * d);
+  const bool use_lut = d <= 5;
+  if (use_lut)
+    for (uint32_t c = threadIdx.x; c < ncodes; c += blockDim.x) lut[c] = (uint16_t)path_to_planar(c, d);
+  __syncthreads();
+  const int64_t total = R * wpr_out;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / wpr_out, k = i % wpr_out;
+    const uint32_t *row = bits + r * wpr_in;
+    uint64_t out = 0;
+    const uint32_t c0 = (uint32_t)(k * 64);
+    const uint32_t n = ncodes < 64 ? ncodes : 64;
+    for (uint32_t j = 0; j < n; ++j) {
+      const uint32_t q = use_lut ? lut[c0 + j] : path_to_planar(c0 + j, d);
+      out |= (uint64_t)((__ldg(row + (q >> 5)) >> (q & 31)) & 1u) << j;
+    }
+    dst[i] = out;
+  }
+}
+
+// Internal word w of a region row: bits of planar codes 32w .. 32w+31.
+__global__ void import_kernel(const uint64_t *__restrict__ src, int64_t R, int d, int64_t wpr_in, int64_t wpr_out,
+                              uint32_t *__restrict__ bits) {
+  extern __shared__ uint16_t lut[];  // planar code -> path code
+  const uint32_t ncodes = 1u << (3 * d);
+  const bool use_lut = d <= 5;
+  if (use_lut)
+    for (uint32_t q = threadIdx.x; q < ncodes; q += blockDim.x) lut[q] = (uint16_t)planar_to_path(q, d);
+  __syncthreads();
+  const int64_t total = R * wpr_out;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / wpr_out, w = i % wpr_out;
+    const uint64_t *row = src + r * wpr_in;
+    uint32_t out = 0;
+    const uint32_t q0 = (uint32_t)(w * 32);
+    const uint32_t n = ncodes < 32 ? ncodes : 32;
+    for (uint32_t j = 0; j < n; ++j) {
+      const uint32_t c = use_lut ? lut[q0 + j] : planar_to_path(q0 + j, d);
+      out |= (uint32_t)((__ldg(row + (c >> 6)) >> (c & 63)) & 1u) << j;
+    }
+    bits[i] = out;
+  }
+}
+
+static size_t lut_bytes(int d) { return d <= 5 ? ((size_t)1 << (3 * d)) * sizeof(uint16_t) : 0; }
+
+ocq_status launch_export(const uint32_t *bits, int64_t R, int depth, uint64_t *dst, cudaStream_t st) {
+  const int64_t total = R * wpr64(depth);
+  const size_t smem = lut_bytes(depth);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(export_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  export_kernel<<<grid_for(total, 256, 4), 256, smem, st>>>(bits, R, depth, wpr32(depth), wpr64(depth), dst);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "export_kernel");
+}
+
+ocq_status launch_import(const uint64_t *src, int64_t R, int depth, uint32_t *bits, cudaStream_t st) {
+  const int64_t total = R * wpr32(depth);
+  const size_t smem = lut_bytes(depth);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(import_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  import_kernel<<<grid_for(total, 256, 4), 256, smem, st>>>(src, R, depth, wpr64(depth), wpr32(depth), bits);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "import_kernel");
+}
+
+// ---- S2 standalone: per-frame, per-region leaf sets ----------------------------
+__global__ void occupancy_kernel(const uint8_t *__restrict__ frames, int64_t npix, int H, int W, int kind, int block,
+                                 int d, int64_t R, int64_t wpr, uint32_t *__restrict__ occ) {
+  const int64_t hw = (int64_t)H * W;
+  const int bw = kind == OCQ_REGION_BLOCK ? (W + block - 1) / block : 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = i / hw, p = i % hw;
+    const int y = (int)(p / W), x = (int)(p % W);
+    const uint32_t q = planar_code_rt(frames[3 * i], frames[3 * i + 1], frames[3 * i + 2], d);
+    uint32_t *word = occ + (f * R + region_of(y, x, W, kind, block, bw)) * wpr + (q >> 5);
+    const uint32_t m = 1u << (q & 31);
+    if (!(*(volatile uint32_t *)word & m)) atomicOr(word, m);
+  }
+}
+
+ocq_status launch_occupancy(const uint8_t *frames, int n, int H, int W, int kind, int block, int depth, uint64_t *occ,
+                            cudaStream_t st) {
+  const int64_t R = region_count(H, W, kind, block);
+  const int64_t rows = (int64_t)n * R;
+  const size_t bytes = (size_t)rows * (size_t)wpr32(depth) * sizeof(uint32_t);
+  uint32_t *tmp = nullptr;
+  ocq_status rc = cuda_status(cudaMallocAsync((void **)&tmp, bytes, st), "occupancy scratch");
+  if (rc != OCQ_OK) return rc;
+  rc = cuda_status(cudaMemsetAsync(tmp, 0, bytes, st), "occupancy scratch clear");
+  if (rc == OCQ_OK) {
+    const int64_t npix = (int64_t)n * H * W;
+    occupancy_kernel<<<grid_for(npix, 256), 256, 0, st>>>(frames, npix, H, W, kind, block, depth, R, wpr32(depth),
+                                                           tmp);
+    count_launch();
+    rc = cuda_status(cudaGetLastError(), "occupancy_kernel");
+  }
+  if (rc == OCQ_OK) rc = launch_export(tmp, rows, depth, occ, st);
+  cudaFreeAsync(tmp, st);
+  return rc;
+}
+
+}  // namespace ocq

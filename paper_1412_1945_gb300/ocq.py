@@ -1,0 +1,228 @@
+"""Thin ctypes binding of ``libocq.so`` (``include/ocq.h``).
+
+Functions keep the C names and argument order.  Pointer arguments accept a
+CUDA tensor (its ``data_ptr()``), a plain integer address, or None.  A
+``stream`` argument accepts a ``torch.cuda.Stream``, a raw ``cudaStream_t``
+integer, or None for the current torch stream.  Non-OK statuses raise
+``OcqError``.  Every computation runs in the CUDA library; there is no other
+code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "libocq.so")
+
+OCQ_OK, OCQ_EINVAL, OCQ_ENOMEM, OCQ_ECUDA, OCQ_ETIMEOUT, OCQ_EBUSY, OCQ_ENOTSUP = range(7)
+OCQ_REGION_FRAME, OCQ_REGION_BLOCK, OCQ_REGION_PIXEL = 0, 1, 2
+
+_lock = threading.Lock()
+_lib = None
+
+
+class OcqError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+STATUS_NAMES = {0: "OCQ_OK", 1: "OCQ_EINVAL", 2: "OCQ_ENOMEM", 3: "OCQ_ECUDA", 4: "OCQ_ETIMEOUT",
+                5: "OCQ_EBUSY", 6: "OCQ_ENOTSUP"}
+
+
+class ocq_region(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("block", ctypes.c_int32)]
+
+
+class ocq_model_info(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("region_kind", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("depth", ctypes.c_int32), ("T", ctypes.c_int32),
+                ("N", ctypes.c_int32), ("reserved", ctypes.c_int32), ("regions", ctypes.c_int64),
+                ("words_per_region", ctypes.c_int64)]
+
+
+# name -> (restype, argtypes)
+_vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+SIGNATURES = {
+    "ocq_status_str": (ctypes.c_char_p, [_i32]),
+    "ocq_last_error": (ctypes.c_char_p, []),
+    "ocq_version": (ctypes.c_char_p, []),
+    "ocq_region_count": (_i64, [_i32, _i32, ocq_region]),
+    "ocq_model_footprint": (_sz, [_i32, _i32, ocq_region, _i32]),
+    "ocq_path_code": (_i32, [_vp, _i64, _i32, _vp, _vp]),
+    "ocq_occupancy": (_i32, [_vp, _i32, _i32, _i32, ocq_region, _i32, _vp, _vp]),
+    "ocq_build_model": (_i32, [_vp, _i32, _i32, _i32, ocq_region, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
+    "ocq_classify": (_i32, [_vp, _vp, _i32, _vp, _vp]),
+    "ocq_model_get_info": (_i32, [_vp, ctypes.POINTER(ocq_model_info)]),
+    "ocq_model_export": (_i32, [_vp, _vp, _sz, _vp]),
+    "ocq_model_import": (_i32, [_vp, ctypes.POINTER(ocq_model_info), _vp, ctypes.POINTER(_vp)]),
+    "ocq_model_free": (None, [_vp]),
+    "ocq_device_status": (_i32, [_vp]),
+    "ocq_detect_host": (_i32, [_vp, _i32, _vp, _i32, _i32, _i32, ocq_region, _i32, _i32, _vp, _vp,
+                               ctypes.POINTER(_vp)]),
+    "ocq_kernel_launches": (ctypes.c_uint64, []),
+}
+
+
+def load(path: str | None = None):
+    """Load ``libocq.so``.  Raises when it is missing: there is no fallback."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or SO
+            if not os.path.exists(p):
+                raise RuntimeError(f"{p} is missing: build it with __graft_entry__.build() "
+                                   "(the octree library has no CPU fallback)")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _s(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(rc: int):
+    if rc != OCQ_OK:
+        raise OcqError(rc, load().ocq_last_error().decode(errors="replace"))
+
+
+def _region(kind, block=0):
+    if isinstance(kind, ocq_region):
+        return kind
+    return ocq_region(int(kind), int(block))
+
+
+class Model:
+    """Owns an ``ocq_model*``; freed by ``free()`` or when garbage-collected."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    @property
+    def info(self) -> ocq_model_info:
+        return ocq_model_get_info(self)
+
+    def free(self):
+        if self.handle:
+            load().ocq_model_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _h(model):
+    return model.handle if isinstance(model, Model) else model
+
+
+def ocq_status_str(s: int) -> str:
+    return load().ocq_status_str(s).decode()
+
+
+def ocq_last_error() -> str:
+    return load().ocq_last_error().decode(errors="replace")
+
+
+def ocq_version() -> str:
+    return load().ocq_version().decode()
+
+
+def ocq_region_count(H, W, kind, block=0) -> int:
+    return int(load().ocq_region_count(H, W, _region(kind, block)))
+
+
+def ocq_model_footprint(H, W, kind, block, depth) -> int:
+    return int(load().ocq_model_footprint(H, W, _region(kind, block), depth))
+
+
+def ocq_path_code(rgb, npix, depth, codes, stream=None):
+    _check(load().ocq_path_code(_p(rgb), npix, depth, _p(codes), _s(stream)))
+
+
+def ocq_occupancy(frames, n, H, W, kind, block, depth, occ, stream=None):
+    _check(load().ocq_occupancy(_p(frames), n, H, W, _region(kind, block), depth, _p(occ), _s(stream)))
+
+
+def ocq_build_model(frames, N, H, W, kind, block, depth, T, stream=None) -> Model:
+    out = ctypes.c_void_p()
+    _check(load().ocq_build_model(_p(frames), N, H, W, _region(kind, block), depth, T, _s(stream),
+                                  ctypes.byref(out)))
+    return Model(out.value)
+
+
+def ocq_classify(model, frames, F, mask, stream=None):
+    _check(load().ocq_classify(_h(model), _p(frames), F, _p(mask), _s(stream)))
+
+
+def ocq_model_get_info(model) -> ocq_model_info:
+    info = ocq_model_info()
+    _check(load().ocq_model_get_info(_h(model), ctypes.byref(info)))
+    return info
+
+
+def ocq_model_export(model, dst, words, stream=None):
+    _check(load().ocq_model_export(_h(model), _p(dst), words, _s(stream)))
+
+
+def ocq_model_import(src, info: ocq_model_info, stream=None) -> Model:
+    out = ctypes.c_void_p()
+    _check(load().ocq_model_import(_p(src), ctypes.byref(info), _s(stream), ctypes.byref(out)))
+    return Model(out.value)
+
+
+def ocq_model_free(model):
+    if isinstance(model, Model):
+        model.free()
+    elif model:
+        load().ocq_model_free(model)
+
+
+def ocq_device_status(stream=None):
+    _check(load().ocq_device_status(_s(stream)))
+
+
+def _hp(x):
+    """Host pointer of a numpy array / CPU tensor / integer address."""
+    if x is None or isinstance(x, int):
+        return x
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def ocq_detect_host(train, N, test, F, H, W, kind, block, depth, T, mask, stream=None, keep_model=False):
+    """Host buffers in, host masks out (see ocq.h).  Returns the Model when
+    ``keep_model``, else None."""
+    out = ctypes.c_void_p()
+    _check(load().ocq_detect_host(_hp(train), N, _hp(test), F, H, W, _region(kind, block), depth, T, _hp(mask),
+                                  _s(stream), ctypes.byref(out) if keep_model else None))
+    return Model(out.value) if keep_model else None
+
+
+def ocq_kernel_launches() -> int:
+    return int(load().ocq_kernel_launches())

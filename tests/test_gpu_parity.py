@@ -1,0 +1,220 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Everything here is integer work, so the bar is bit-exact: exported model
+bitsets and foreground masks must equal the oracle's element by element.
+"""
+import numpy as np
+import pytest
+
+import ocq_synth
+import oracle
+from ocq_synth import configs
+
+pytestmark = pytest.mark.gpu
+FRAME, BLOCK, PIXEL = 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def ocq(cuda_ready):
+    return cuda_ready
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+
+    return torch
+
+
+def to_dev(a, torch):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_model_and_mask(ocq, torch, train, test, d, T, kind, block):
+    tr = to_dev(train, torch)
+    m = ocq.build_model(tr, d, T, kind, block)
+    words = ocq.export_model(m).cpu().numpy().view(np.uint64)
+    mask = None
+    if test is not None:
+        mask = ocq.classify(m, to_dev(test, torch)).cpu().numpy()
+    ocq.device_status()
+    m.free()
+    return words, mask
+
+
+# ---- S1 -------------------------------------------------------------------------
+
+def test_path_code_all_colours(ocq, torch):
+    v = np.arange(1 << 24, dtype=np.uint32)
+    rgb = np.stack([(v >> 16) & 255, (v >> 8) & 255, v & 255], axis=1).astype(np.uint8)
+    dev = to_dev(rgb, torch)
+    for d in range(1, 9):
+        got = ocq.path_code(dev, d).cpu().numpy().view(np.uint32)
+        assert (got == oracle.leaf_codes(rgb, d)).all(), d
+
+
+# ---- S2 -------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,block", [(FRAME, 0), (BLOCK, 5), (PIXEL, 0)])
+@pytest.mark.parametrize("d", [1, 3, 5, 8])
+def test_occupancy_matches_per_frame_trees(ocq, torch, kind, block, d):
+    g = np.random.default_rng(40 + d)
+    frames = g.integers(0, 256, size=(3, 13, 19, 3), dtype=np.uint8)
+    occ = ocq.occupancy(to_dev(frames, torch), d, kind, block).cpu().numpy().view(np.uint64)
+    for f in range(3):
+        # a per-frame tree's leaf set is the merge of that one tree with T = 1
+        expect = oracle.build_model(frames[f:f + 1], d, 1, kind, block)
+        assert (occ[f] == expect).all(), f
+
+
+# ---- S1-S4 on small random shapes ------------------------------------------------
+
+CASES = []
+for kind, block in [(FRAME, 0), (BLOCK, 1), (BLOCK, 4), (BLOCK, 7), (PIXEL, 0)]:
+    for d in range(1, 9):
+        CASES.append((kind, block, d))
+
+
+@pytest.mark.parametrize("kind,block,d", CASES)
+def test_build_classify_random(ocq, torch, kind, block, d):
+    g = np.random.default_rng(1000 + 17 * kind + block * 3 + d)
+    H, W = int(g.integers(5, 23)), int(g.integers(5, 29))
+    N = int(g.integers(1, 9))
+    palette = g.integers(0, 256, size=(7, 3), dtype=np.uint8)
+    train = palette[g.integers(0, 7, size=(N, H, W))]
+    train[:, ::3] = g.integers(0, 256, size=train[:, ::3].shape, dtype=np.uint8)
+    test = np.concatenate([palette[g.integers(0, 7, size=(3, H, W))],
+                           g.integers(0, 256, size=(2, H, W, 3), dtype=np.uint8)])
+    for T in sorted({1, (N + 1) // 2, N}):
+        words, mask = gpu_model_and_mask(ocq, torch, train, test, d, T, kind, block)
+        ow, om = oracle.run(train, d, T, kind, block, test)
+        assert (words == ow).all(), ("model", T)
+        assert (mask == om).all(), ("mask", T)
+
+
+@pytest.mark.parametrize("H,W", [(48, 64), (52, 80), (29, 37), (16, 1024), (1, 2049)])
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_pixel_tiles_and_ragged_tail(ocq, torch, H, W, d):
+    """Pixel regions, depth <= 3: the tiled kernel (full tiles) plus the
+    remainder, and the generic path when H*W is not a multiple of 16."""
+    sc = ocq_synth.make_scene("bimodal", H, W, 12, 9, seed=77 + d)
+    frames = ocq_synth.fill_host(sc, 0, 21)
+    train, test = frames[:12], frames[12:]
+    words, mask = gpu_model_and_mask(ocq, torch, train, test, d, 3, PIXEL, 0)
+    ow, om = oracle.run(train, d, 3, PIXEL, 0, test)
+    assert (words == ow).all()
+    assert (mask == om).all()
+
+
+def test_pixel_wide_counters(ocq, torch):
+    """N > 255 switches the per-pixel counters to 16 bits."""
+    g = np.random.default_rng(5)
+    palette = g.integers(0, 256, size=(3, 3), dtype=np.uint8)
+    train = palette[g.integers(0, 3, size=(300, 4, 8))]
+    test = palette[g.integers(0, 3, size=(2, 4, 8))]
+    for T in (1, 97, 150, 300):
+        words, mask = gpu_model_and_mask(ocq, torch, train, test, 3, T, PIXEL, 0)
+        ow, om = oracle.run(train, 3, T, PIXEL, 0, test)
+        assert (words == ow).all() and (mask == om).all(), T
+
+
+def test_constant_frames_edge_cases(ocq, torch):
+    train = np.zeros((4, 6, 7, 3), np.uint8)
+    train[...] = (10, 200, 30)
+    test = np.zeros((2, 6, 7, 3), np.uint8)
+    test[0] = (10, 200, 30)
+    test[1] = (200, 10, 30)
+    for kind, block in [(FRAME, 0), (BLOCK, 3), (PIXEL, 0)]:
+        words, mask = gpu_model_and_mask(ocq, torch, train, test, 4, 4, kind, block)
+        ow, om = oracle.run(train, 4, 4, kind, block, test)
+        assert (words == ow).all() and (mask == om).all()
+        assert not mask[0].any() and mask[1].all()
+
+
+def test_export_import_roundtrip(ocq, torch):
+    g = np.random.default_rng(9)
+    train = g.integers(0, 256, size=(5, 9, 11, 3), dtype=np.uint8)
+    test = g.integers(0, 256, size=(3, 9, 11, 3), dtype=np.uint8)
+    for kind, block in [(FRAME, 0), (BLOCK, 4), (PIXEL, 0)]:
+        for d in (1, 2, 3, 5):
+            m = ocq.build_model(to_dev(train, torch), d, 2, kind, block)
+            words = ocq.export_model(m)
+            m2 = ocq.import_model(words, 9, 11, kind, block, d)
+            assert (ocq.export_model(m2).cpu() == words.cpu()).all()
+            t = to_dev(test, torch)
+            assert (ocq.classify(m2, t).cpu() == ocq.classify(m, t).cpu()).all()
+            # classify of an oracle-made model imported into the library
+            ow = oracle.build_model(train, d, 2, kind, block)
+            m3 = ocq.import_model(to_dev(ow.view(np.int64), torch), 9, 11, kind, block, d)
+            assert (ocq.classify(m3, t).cpu().numpy() == oracle.classify(ow, test, d, kind, block)).all()
+            m.free(), m2.free(), m3.free()
+
+
+# ---- the preset workloads -----------------------------------------------------------
+
+def _workload_frames(wl, n_test=None):
+    sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, wl.F, wl.seed, wl.stream)
+    F = wl.F if n_test is None else n_test
+    frames = ocq_synth.fill_host(sc, 0, wl.N + F)
+    return frames[:wl.N], frames[wl.N:]
+
+
+def test_tiny_frame_preset(ocq, torch):
+    wl = configs.TINY_FRAME
+    train, test = _workload_frames(wl)
+    words, mask = gpu_model_and_mask(ocq, torch, train, test, wl.depth, wl.T, wl.region, wl.block)
+    ow, om = oracle.run(train, wl.depth, wl.T, wl.region, wl.block, test)
+    assert (words == ow).all() and (mask == om).all()
+
+
+def test_block_preset(ocq, torch):
+    wl = configs.BLOCKS_320x240
+    train, test = _workload_frames(wl)
+    words, mask = gpu_model_and_mask(ocq, torch, train, test, wl.depth, wl.T, wl.region, wl.block)
+    ow, om = oracle.run(train, wl.depth, wl.T, wl.region, wl.block, test)
+    assert (words == ow).all() and (mask == om).all()
+
+
+def test_pixel_1080p_full_size_sampled(ocq, torch):
+    """The 1920x1080 per-pixel preset at full size (50 training + 1000 test
+    frames, generated on the device), in the bench's launch configuration;
+    the oracle checks every frame at sampled pixel locations, including the
+    first and last pixel of tiles and of the frame."""
+    wl = configs.PIXEL_1080P
+    H, W, N, F = wl.H, wl.W, wl.N, wl.F
+    sc = ocq_synth.make_scene(wl.scene_kind, H, W, N, F, wl.seed)
+    train = torch.empty((N, H, W, 3), dtype=torch.uint8, device="cuda")
+    test = torch.empty((F, H, W, 3), dtype=torch.uint8, device="cuda")
+    ocq_synth.fill_device(sc, 0, N, train)
+    ocq_synth.fill_device(sc, N, F, test)
+    m = ocq.build_model(train, wl.depth, wl.T, wl.region, wl.block)
+    mask = ocq.classify(m, test)
+    ocq.device_status()
+    words = ocq.export_model(m)
+    g = np.random.default_rng(123)
+    hw = H * W
+    picks = set(g.integers(0, hw, size=600).tolist())
+    for t in (0, 1, 1023, 1024, 2047, 2048, hw // 2, hw - 1025, hw - 1024, hw - 1):
+        picks.add(t)
+    idx = np.array(sorted(picks), np.int64)
+    ys, xs = idx // W, idx % W
+    tr = train[:, ys, xs].cpu().numpy()[:, None]        # [N, 1, k, 3]
+    te = test[:, ys, xs].cpu().numpy()[:, None]         # [F, 1, k, 3]
+    ow, om = oracle.run(tr, wl.depth, wl.T, PIXEL, 0, te)
+    gw = words[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint64)
+    assert (gw == ow).all()
+    gm = mask[:, ys, xs].cpu().numpy()
+    assert (gm == om[:, 0]).all()
+    # the synthetic truth: pixels the foreground discs never cover are mostly background
+    assert mask.float().mean().item() < 0.5
+    m.free()
+
+
+def test_synth_device_matches_host(ocq, torch):
+    for wl in (configs.TINY_FRAME, configs.BLOCKS_320x240):
+        sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, wl.F, wl.seed)
+        host, gt = ocq_synth.fill_host(sc, wl.N - 2, 5, with_gt=True)
+        dev = torch.empty(host.shape, dtype=torch.uint8, device="cuda")
+        dgt = torch.empty(gt.shape, dtype=torch.uint8, device="cuda")
+        ocq_synth.fill_device(sc, wl.N - 2, 5, dev, dgt)
+        assert (dev.cpu().numpy() == host).all() and (dgt.cpu().numpy() == gt).all()
