@@ -32,26 +32,28 @@ ocq_status launch_path_code(const uint8_t *rgb, int64_t npix, int depth, uint32_
 }
 
 // ---- planar <-> path translation ------------------------------------------------
+// Both orders are permutations of the same 3d bits, so for codes a, b with
+// disjoint bits perm(a | b) = perm(a) | perm(b).  A 64-bit output word holds path
+// codes 64k | j (j < 64): its planar codes are path_to_planar(64k) | off[j],
+// with the 64-entry table off[j] = path_to_planar(j).  Likewise for import.
 
 // Output word k of a region row in the public layout: bits of path codes
 // 64k .. 64k+63 (fewer when d <= 1).
 __global__ void export_kernel(const uint32_t *__restrict__ bits, int64_t R, int d, int64_t wpr_in, int64_t wpr_out,
                               uint64_t *__restrict__ dst) {
-  extern __shared__ uint16_t lut[];  // path code -> planar code, when 8^d <= 32768
+  __shared__ uint32_t off[64];
   const uint32_t ncodes = 1u << (3 * d);
-  const bool use_lut = d <= 5;
-  if (use_lut)
-    for (uint32_t c = threadIdx.x; c < ncodes; c += blockDim.x) lut[c] = (uint16_t)path_to_planar(c, d);
+  const uint32_t n = ncodes < 64 ? ncodes : 64;
+  if (threadIdx.x < 64) off[threadIdx.x] = threadIdx.x < n ? path_to_planar(threadIdx.x, d) : 0u;
   __syncthreads();
   const int64_t total = R * wpr_out;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / wpr_out, k = i % wpr_out;
     const uint32_t *row = bits + r * wpr_in;
+    const uint32_t base = path_to_planar((uint32_t)(k * 64), d);
     uint64_t out = 0;
-    const uint32_t c0 = (uint32_t)(k * 64);
-    const uint32_t n = ncodes < 64 ? ncodes : 64;
     for (uint32_t j = 0; j < n; ++j) {
-      const uint32_t q = use_lut ? lut[c0 + j] : path_to_planar(c0 + j, d);
+      const uint32_t q = base | off[j];
       out |= (uint64_t)((__ldg(row + (q >> 5)) >> (q & 31)) & 1u) << j;
     }
     dst[i] = out;
@@ -61,43 +63,35 @@ __global__ void export_kernel(const uint32_t *__restrict__ bits, int64_t R, int 
 // Internal word w of a region row: bits of planar codes 32w .. 32w+31.
 __global__ void import_kernel(const uint64_t *__restrict__ src, int64_t R, int d, int64_t wpr_in, int64_t wpr_out,
                               uint32_t *__restrict__ bits) {
-  extern __shared__ uint16_t lut[];  // planar code -> path code
+  __shared__ uint32_t off[32];
   const uint32_t ncodes = 1u << (3 * d);
-  const bool use_lut = d <= 5;
-  if (use_lut)
-    for (uint32_t q = threadIdx.x; q < ncodes; q += blockDim.x) lut[q] = (uint16_t)planar_to_path(q, d);
+  const uint32_t n = ncodes < 32 ? ncodes : 32;
+  if (threadIdx.x < 32) off[threadIdx.x] = threadIdx.x < n ? planar_to_path(threadIdx.x, d) : 0u;
   __syncthreads();
   const int64_t total = R * wpr_out;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / wpr_out, w = i % wpr_out;
     const uint64_t *row = src + r * wpr_in;
+    const uint32_t base = planar_to_path((uint32_t)(w * 32), d);
     uint32_t out = 0;
-    const uint32_t q0 = (uint32_t)(w * 32);
-    const uint32_t n = ncodes < 32 ? ncodes : 32;
     for (uint32_t j = 0; j < n; ++j) {
-      const uint32_t c = use_lut ? lut[q0 + j] : planar_to_path(q0 + j, d);
+      const uint32_t c = base | off[j];
       out |= (uint32_t)((__ldg(row + (c >> 6)) >> (c & 63)) & 1u) << j;
     }
     bits[i] = out;
   }
 }
 
-static size_t lut_bytes(int d) { return d <= 5 ? ((size_t)1 << (3 * d)) * sizeof(uint16_t) : 0; }
-
 ocq_status launch_export(const uint32_t *bits, int64_t R, int depth, uint64_t *dst, cudaStream_t st) {
   const int64_t total = R * wpr64(depth);
-  const size_t smem = lut_bytes(depth);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(export_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  export_kernel<<<grid_for(total, 256, 4), 256, smem, st>>>(bits, R, depth, wpr32(depth), wpr64(depth), dst);
+  export_kernel<<<grid_for(total, 256, 8), 256, 0, st>>>(bits, R, depth, wpr32(depth), wpr64(depth), dst);
   count_launch();
   return cuda_status(cudaGetLastError(), "export_kernel");
 }
 
 ocq_status launch_import(const uint64_t *src, int64_t R, int depth, uint32_t *bits, cudaStream_t st) {
   const int64_t total = R * wpr32(depth);
-  const size_t smem = lut_bytes(depth);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(import_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  import_kernel<<<grid_for(total, 256, 4), 256, smem, st>>>(src, R, depth, wpr64(depth), wpr32(depth), bits);
+  import_kernel<<<grid_for(total, 256, 8), 256, 0, st>>>(src, R, depth, wpr64(depth), wpr32(depth), bits);
   count_launch();
   return cuda_status(cudaGetLastError(), "import_kernel");
 }

@@ -59,7 +59,8 @@ def test_path_code_all_colours(ocq, torch):
 @pytest.mark.parametrize("d", [1, 3, 5, 8])
 def test_occupancy_matches_per_frame_trees(ocq, torch, kind, block, d):
     g = np.random.default_rng(40 + d)
-    frames = g.integers(0, 256, size=(3, 13, 19, 3), dtype=np.uint8)
+    H, W = (5, 3) if (kind == PIXEL and d >= 6) else (13, 19)
+    frames = g.integers(0, 256, size=(3, H, W, 3), dtype=np.uint8)
     occ = ocq.occupancy(to_dev(frames, torch), d, kind, block).cpu().numpy().view(np.uint64)
     for f in range(3):
         # a per-frame tree's leaf set is the merge of that one tree with T = 1
@@ -79,6 +80,8 @@ for kind, block in [(FRAME, 0), (BLOCK, 1), (BLOCK, 4), (BLOCK, 7), (PIXEL, 0)]:
 def test_build_classify_random(ocq, torch, kind, block, d):
     g = np.random.default_rng(1000 + 17 * kind + block * 3 + d)
     H, W = int(g.integers(5, 23)), int(g.integers(5, 29))
+    if d >= 6 and kind != FRAME:  # rows of 8^d bits: keep the models small
+        H, W = int(g.integers(2, 9)), int(g.integers(2, 9))
     N = int(g.integers(1, 9))
     palette = g.integers(0, 256, size=(7, 3), dtype=np.uint8)
     train = palette[g.integers(0, 7, size=(N, H, W))]
