@@ -158,6 +158,24 @@ ocq_status ocq_device_status(void *stream);
 ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int F, int H, int W, ocq_region region,
                            int depth, int T, uint8_t *mask, void *stream, ocq_model **out_model);
 
+/*
+ * Tuning interface (no counterpart in the paper; it selects between kernel
+ * variants that compute identical results).  `kernel` names a tunable kernel:
+ *   OCQ_TUNE_CLASSIFY_PIXEL  per-pixel classify, depth <= 3; params =
+ *                            {warps per CTA, pixels per thread, stages, frames per stage}
+ *   OCQ_TUNE_BUILD_PIXEL     per-pixel build, depth <= 3; params =
+ *                            {pixels (threads) per CTA, frames per stage, stages, 0}
+ * ocq_tune_count: number of variants (-1 for an unknown kernel).
+ * ocq_tune_select: process-wide choice used by later calls (not thread-safe
+ * against concurrent calls of the same kernel).  ocq_tune_describe writes 4
+ * int32 parameters (n >= 4).
+ */
+enum { OCQ_TUNE_CLASSIFY_PIXEL = 0, OCQ_TUNE_BUILD_PIXEL = 1 };
+int ocq_tune_count(int kernel);
+int ocq_tune_selected(int kernel);
+ocq_status ocq_tune_select(int kernel, int variant);
+ocq_status ocq_tune_describe(int kernel, int variant, int32_t *params, int n);
+
 /* Number of kernels this library has launched in this process (all devices).
  * Lets a caller count the device work a call sequence issued. */
 uint64_t ocq_kernel_launches(void);

@@ -237,7 +237,53 @@ void ocq_model_free(ocq_model *m) {
  * recorded by a kernel on the current device: OCQ_ETIMEOUT if one occurred. */
 ocq_status ocq_device_status(void *stream) {
   g_err[0] = 0;
-  return device_status((cudaStream_t)stream);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_status(e, "stream synchronise");
+  const bool c = classify_take_timeout();
+  const bool b = build_take_timeout();
+  if (c || b) {
+    set_error("a bounded device wait timed out (%s)", c ? "classify" : "build");
+    return OCQ_ETIMEOUT;
+  }
+  return OCQ_OK;
+}
+
+int ocq_tune_count(int kernel) {
+  if (kernel == OCQ_TUNE_CLASSIFY_PIXEL) return classify_variant_count();
+  if (kernel == OCQ_TUNE_BUILD_PIXEL) return build_variant_count();
+  return -1;
+}
+
+int ocq_tune_selected(int kernel) {
+  if (kernel == OCQ_TUNE_CLASSIFY_PIXEL) return classify_variant_selected();
+  if (kernel == OCQ_TUNE_BUILD_PIXEL) return build_variant_selected();
+  return -1;
+}
+
+ocq_status ocq_tune_select(int kernel, int variant) {
+  g_err[0] = 0;
+  bool ok = false;
+  if (kernel == OCQ_TUNE_CLASSIFY_PIXEL) ok = classify_variant_select(variant);
+  if (kernel == OCQ_TUNE_BUILD_PIXEL) ok = build_variant_select(variant);
+  if (!ok) {
+    set_error("ocq_tune_select: no variant %d of kernel %d", variant, kernel);
+    return OCQ_EINVAL;
+  }
+  return OCQ_OK;
+}
+
+ocq_status ocq_tune_describe(int kernel, int variant, int32_t *params, int n) {
+  g_err[0] = 0;
+  if (!params || n < 4 || variant < 0 || variant >= ocq_tune_count(kernel)) {
+    set_error("ocq_tune_describe: bad arguments");
+    return OCQ_EINVAL;
+  }
+  params[0] = params[1] = params[2] = params[3] = 0;
+  if (kernel == OCQ_TUNE_CLASSIFY_PIXEL)
+    classify_variant_describe(variant, &params[0], &params[1], &params[2], &params[3]);
+  else
+    build_variant_describe(variant, &params[0], &params[1], &params[2]);
+  return OCQ_OK;
 }
 
 }  // extern "C"

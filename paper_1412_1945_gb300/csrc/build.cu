@@ -16,9 +16,13 @@
 //     for chunks the pixel's N colours touch.
 #include <cstdint>
 
+#include "async_copy.cuh"
 #include "pixels.cuh"
 
 namespace ocq {
+
+// Set when a bounded wait gives up; read and cleared by build_take_timeout().
+__device__ unsigned int g_build_timeout;
 
 static int bit_length(uint32_t v) {
   int n = 0;
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(256) build_block_kernel(const uint8_t *__restr
 // counter words cnt[k * 128 + t] (4 u8 or 2 u16 counters per word).
 template <int D, bool WIDE>
 __global__ void __launch_bounds__(128) build_pixel_counters_kernel(const uint8_t *__restrict__ frames, int N,
-                                                                   int64_t hw, uint32_t T,
+                                                                   int64_t hw, int64_t p_begin, uint32_t T,
                                                                    uint32_t *__restrict__ model) {
   constexpr int NC = 1 << (3 * D);
   constexpr int CPW = WIDE ? 2 : 4;
@@ -187,7 +191,7 @@ __global__ void __launch_bounds__(128) build_pixel_counters_kernel(const uint8_t
   constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
   extern __shared__ uint32_t cnt[];
   const int t = threadIdx.x;
-  const int64_t p = (int64_t)blockIdx.x * 128 + t;
+  const int64_t p = p_begin + (int64_t)blockIdx.x * 128 + t;
   if (p >= hw) return;  // columns are private: no CTA-wide synchronisation below
 #pragma unroll 8
   for (int k = 0; k < NW; ++k) cnt[k * 128 + t] = 0;
@@ -230,6 +234,134 @@ __global__ void __launch_bounds__(128) build_pixel_counters_kernel(const uint8_t
   uint32_t *dst = model + p * WPR;
 #pragma unroll
   for (int w = 0; w < WPR; ++w) dst[w] = out[w];
+}
+
+// Same counting with the frames staged by bulk asynchronous copies.  A
+// persistent CTA of NT threads owns NT-pixel tiles; thread 0 streams each
+// tile's rows of FPS frames per stage into a ring of S stages (mbarrier
+// completion, bounded waits) while every thread counts its pixel from shared
+// memory.  Counters are CB-bit (4 or 8) and saturate at T, which keeps the
+// test count >= T exact.  A per-pixel "touched" bitset records which leaves
+// occurred, so the end of a tile visits only those leaves, and leaves their
+// counters at zero for the next tile.  Requires frames 16-byte aligned and
+// H*W % 16 == 0; covers full tiles only.
+template <int D, int CB, int NT, int FPS, int S>
+struct StagedBuildCfg {
+  static constexpr int NC = 1 << (3 * D);
+  static constexpr int CPW = 32 / CB;                  // counters per word
+  static constexpr int CW = (NC + CPW - 1) / CPW;      // counter words per pixel
+  static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  static constexpr int ROW = NT * 3;                   // bytes of one frame's tile
+  static constexpr int STAGE = ROW * FPS;
+  static constexpr size_t SMEM = ((size_t)CW + WPR) * NT * 4 + (size_t)S * STAGE + (size_t)S * 8;
+  static_assert(ROW % 16 == 0, "bulk copies move multiples of 16 bytes");
+};
+
+template <int D, int CB, int NT, int FPS, int S>
+__global__ void __launch_bounds__(NT) build_pixel_staged_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
+                                                                int64_t ntiles, uint32_t T,
+                                                                uint32_t *__restrict__ model) {
+  using C = StagedBuildCfg<D, CB, NT, FPS, S>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // [CW][NT]
+  uint32_t *touched = cnt + C::CW * NT;                // [WPR][NT]
+  uint8_t *stages = reinterpret_cast<uint8_t *>(touched + C::WPR * NT);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stages + (size_t)S * C::STAGE);
+  const int t = threadIdx.x;
+  constexpr uint32_t CMASK = (1u << CB) - 1u;
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+#pragma unroll 8
+  for (int c = 0; c < C::CW; ++c) cnt[c * NT + t] = 0;
+  __syncthreads();
+  const int G = (N + FPS - 1) / FPS;  // stages per tile
+  const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = my_tiles * G;
+
+  auto issue = [&](int64_t k) {
+    const int64_t i = k / G;
+    const int g = (int)(k - i * G);
+    const int64_t tile = blockIdx.x + i * gridDim.x;
+    const int f0 = g * FPS;
+    const int nf = N - f0 < FPS ? N - f0 : FPS;
+    const int s = (int)(k % S);
+    const uint32_t bar = smem_addr(&bars[s]);
+    mbar_expect_tx(bar, (uint32_t)(nf * C::ROW));
+    for (int j = 0; j < nf; ++j)
+      bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)j * C::ROW),
+               frames + ((int64_t)(f0 + j) * hw + tile * NT) * 3, C::ROW, bar);
+  };
+  if (t == 0)
+    for (int64_t k = 0; k < total && k < S; ++k) issue(k);
+
+  for (int64_t k = 0; k < total; ++k) {
+    const int64_t i = k / G;
+    const int g = (int)(k - i * G);
+    if (g == 0) {
+#pragma unroll
+      for (int w = 0; w < C::WPR; ++w) touched[w * NT + t] = 0;
+    }
+    const int s = (int)(k % S);
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)((k / S) & 1), kWaitLimitNs);
+    const uint8_t *stage = stages + (size_t)s * C::STAGE + 3 * t;
+    const int nf = N - g * FPS < FPS ? N - g * FPS : FPS;
+#pragma unroll
+    for (int j = 0; j < FPS; ++j) {
+      if (j < nf) {
+        const uint8_t *px = stage + j * C::ROW;
+        const uint32_t y = (uint32_t)px[0] | ((uint32_t)px[1] << 8) | ((uint32_t)px[2] << 16);
+        const uint32_t q = planar_code<D>(y);
+        uint32_t *cw = &cnt[(q / C::CPW) * NT + t];
+        const uint32_t sh = (q % C::CPW) * CB;
+        const uint32_t v = *cw;
+        const uint32_t c = (v >> sh) & CMASK;
+        if (c < T) *cw = v + (1u << sh);
+        if (c == 0) touched[(q >> 5) * NT + t] |= 1u << (q & 31);
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicExch(&g_build_timeout, 1u);
+        for (int64_t kk = k; kk < total && kk < k + S; ++kk)
+          mbar_wait_bounded(smem_addr(&bars[kk % S]), (uint32_t)((kk / S) & 1), kWaitLimitNs);
+      }
+      __syncthreads();
+      return;
+    }
+    if (t == 0 && k + S < total) issue(k + S);
+    if (g == G - 1) {
+      const int64_t p = (blockIdx.x + i * gridDim.x) * NT + t;
+      // the touched word w is replaced by model word w of this pixel
+#pragma unroll 1
+      for (int w = 0; w < C::WPR; ++w) {
+        const uint32_t tb = touched[w * NT + t];
+        uint32_t o = 0;
+        for (uint32_t x = tb; x; x &= x - 1) {
+          const uint32_t b = __ffs(x) - 1;
+          const uint32_t q = (uint32_t)w * 32u + b;
+          const uint32_t c = (cnt[(q / C::CPW) * NT + t] >> ((q % C::CPW) * CB)) & CMASK;
+          o |= (uint32_t)(c >= T) << b;
+        }
+        for (uint32_t x = tb; x; x &= x - 1) {  // leave the counters at zero
+          const uint32_t q = (uint32_t)w * 32u + (__ffs(x) - 1);
+          cnt[(q / C::CPW) * NT + t] = 0;
+        }
+        touched[w * NT + t] = o;
+      }
+      uint32_t *dst = model + p * C::WPR;
+      if constexpr (C::WPR % 4 == 0) {
+#pragma unroll
+        for (int w = 0; w < C::WPR; w += 4)
+          *reinterpret_cast<uint4 *>(dst + w) = make_uint4(touched[w * NT + t], touched[(w + 1) * NT + t],
+                                                           touched[(w + 2) * NT + t], touched[(w + 3) * NT + t]);
+      } else {
+#pragma unroll
+        for (int w = 0; w < C::WPR; ++w) dst[w] = touched[w * NT + t];
+      }
+    }
+  }
 }
 
 // ---- pixel regions, depth >= 4 --------------------------------------------------
@@ -374,7 +506,8 @@ static ocq_status launch_block(const uint8_t *frames, int N, ocq_model *m, cudaS
 }
 
 template <int D, bool WIDE>
-static ocq_status launch_pixel_counters(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+static ocq_status launch_pixel_counters(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st,
+                                        int64_t p_begin = 0) {
   constexpr int NC = 1 << (3 * D);
   constexpr int CPW = WIDE ? 2 : 4;
   constexpr int NW = (NC + CPW - 1) / CPW;
@@ -383,10 +516,36 @@ static ocq_status launch_pixel_counters(const uint8_t *frames, int N, ocq_model 
     cudaFuncSetAttribute(build_pixel_counters_kernel<D, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
   const int64_t hw = (int64_t)m->H * m->W;
+  const int64_t n = hw - p_begin;
+  if (n <= 0) return OCQ_OK;
   build_pixel_counters_kernel<D, WIDE>
-      <<<(unsigned)((hw + 127) / 128), 128, smem, st>>>(frames, N, hw, (uint32_t)m->T, m->bits);
+      <<<(unsigned)((n + 127) / 128), 128, smem, st>>>(frames, N, hw, p_begin, (uint32_t)m->T, m->bits);
   count_launch();
   return cuda_status(cudaGetLastError(), "build_pixel_counters_kernel");
+}
+
+template <int D, int CB, int NT, int FPS, int S>
+static ocq_status launch_pixel_staged(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  using C = StagedBuildCfg<D, CB, NT, FPS, S>;
+  const int64_t hw = (int64_t)m->H * m->W;
+  constexpr bool fits = C::SMEM <= 227 * 1024;
+  const int64_t ntiles = fits ? hw / NT : 0;
+  if (ntiles > 0) {
+    auto kern = build_pixel_staged_kernel<D, CB, NT, FPS, S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return cuda_status(e, "build_pixel_staged_kernel smem");
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, C::SMEM);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sm_count() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    kern<<<(unsigned)grid, NT, C::SMEM, st>>>(frames, N, hw, ntiles, (uint32_t)m->T, m->bits);
+    count_launch();
+    ocq_status rc = cuda_status(cudaGetLastError(), "build_pixel_staged_kernel");
+    if (rc != OCQ_OK) return rc;
+  }
+  if (N > 255) return launch_pixel_counters<D, true>(frames, N, m, st, ntiles * NT);
+  return launch_pixel_counters<D, false>(frames, N, m, st, ntiles * NT);
 }
 
 template <int D>
@@ -414,6 +573,51 @@ static ocq_status launch_pixel_chunked(const uint8_t *frames, int N, ocq_model *
   return rc;
 }
 
+// ---- tunable variants ------------------------------------------------------------
+using BuildFn = ocq_status (*)(const uint8_t *, int, ocq_model *, cudaStream_t);
+struct BuildVariant {
+  int nt, fps, stages;
+  BuildFn fn[2][3];  // [4-bit, 8-bit counters][depth 1, 2, 3]
+};
+#define OCQ_BV(NT, F, S)                                                                              \
+  {                                                                                                  \
+    NT, F, S, {                                                                                      \
+      {launch_pixel_staged<1, 4, NT, F, S>, launch_pixel_staged<2, 4, NT, F, S>,                     \
+       launch_pixel_staged<3, 4, NT, F, S>},                                                         \
+          {launch_pixel_staged<1, 8, NT, F, S>, launch_pixel_staged<2, 8, NT, F, S>,                 \
+           launch_pixel_staged<3, 8, NT, F, S>}                                                      \
+    }                                                                                                \
+  }
+static const BuildVariant kBuildVariants[] = {OCQ_BV(128, 8, 3), OCQ_BV(256, 4, 4), OCQ_BV(512, 4, 3),
+                                              OCQ_BV(128, 16, 2), OCQ_BV(256, 8, 3), OCQ_BV(128, 4, 6)};
+#undef OCQ_BV
+static int g_build_variant = 0;
+
+int build_variant_count() { return (int)(sizeof kBuildVariants / sizeof kBuildVariants[0]); }
+int build_variant_selected() { return g_build_variant; }
+bool build_variant_select(int v) {
+  if (v < 0 || v >= build_variant_count()) return false;
+  g_build_variant = v;
+  return true;
+}
+void build_variant_describe(int v, int *nt, int *fps, int *stages) {
+  *nt = kBuildVariants[v].nt;
+  *fps = kBuildVariants[v].fps;
+  *stages = kBuildVariants[v].stages;
+}
+
+// 4-bit counters saturating at T when T <= 15, else 8-bit (T <= 255).
+static ocq_status launch_build_pixel_staged(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  return kBuildVariants[g_build_variant].fn[m->T <= 15 ? 0 : 1][m->depth - 1](frames, N, m, st);
+}
+
+bool build_take_timeout() {
+  unsigned int flag = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&flag, g_build_timeout, sizeof flag) != cudaSuccess) return false;
+  if (flag) cudaMemcpyToSymbol(g_build_timeout, &zero, sizeof zero);
+  return flag != 0;
+}
+
 ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
   const int d = m->depth;
   if (m->kind == OCQ_REGION_FRAME || (m->kind == OCQ_REGION_BLOCK && d >= 6)) return build_dense(frames, N, m, st);
@@ -427,6 +631,9 @@ ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t
     }
   }
   const bool wide = N > 255;
+  const bool staged_ok = m->T <= 255 && ((reinterpret_cast<uintptr_t>(frames) & 15) == 0) &&
+                         ((int64_t)m->H * m->W) % 16 == 0;
+  if (staged_ok && d <= 3) return launch_build_pixel_staged(frames, N, m, st);
   switch (d) {
     case 1: return wide ? launch_pixel_counters<1, true>(frames, N, m, st) : launch_pixel_counters<1, false>(frames, N, m, st);
     case 2: return wide ? launch_pixel_counters<2, true>(frames, N, m, st) : launch_pixel_counters<2, false>(frames, N, m, st);

@@ -17,6 +17,7 @@
 //                                row is read from HBM about once per launch.
 #include <cstdint>
 
+#include "async_copy.cuh"
 #include "pixels.cuh"
 
 namespace ocq {
@@ -96,75 +97,74 @@ __global__ void __launch_bounds__(256) classify_frame_kernel(const uint8_t *__re
 
 // ---- pixel regions: temporal blocking with bulk async copies --------------------------
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Waits for phase `parity` of `bar` to complete; gives up after `limit_ns`.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = global_ns();
-  while (true) {
-    for (int i = 0; i < 64; ++i)
-      if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > limit_ns) return false;
-  }
-}
-
-static constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
-
-template <int D, int NW, int PPT, int S>
+template <int D, int NW, int PPT, int S, int FPS>
 struct TiledCfg {
   static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
   static constexpr int THREADS = NW * 32;
   static constexpr int TILE = THREADS * PPT;       // pixel locations per tile
-  static constexpr int STAGE = TILE * 3;           // bytes of one frame's tile
+  static constexpr int FRAME_BYTES = TILE * 3;     // one frame's tile
+  static constexpr int STAGE = FRAME_BYTES * FPS;  // one stage holds FPS frames
   static constexpr int MODEL_WORDS = TILE * WPR;
   static constexpr size_t SMEM = (size_t)MODEL_WORDS * 4 + (size_t)S * STAGE + (size_t)S * 8;
-  static_assert(STAGE % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static_assert(FRAME_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
   static_assert(PPT == 8 || PPT == 16, "8 or 16 pixels per thread");
 };
 
+// Classifies one frame of the tile from shared memory: thread (warp, lane)
+// handles pixels (warp*32 + lane)*PPT + j of the tile.
+template <int D, int NW, int PPT, int S, int FPS>
+__device__ __forceinline__ void classify_tile_frame(const uint8_t *__restrict__ src, const uint32_t *__restrict__ mrow,
+                                                    uint8_t *__restrict__ dst) {
+  using C = TiledCfg<D, NW, PPT, S, FPS>;
+  const int tid = threadIdx.x;
+  uint32_t fbit[PPT];
+  uint32_t w[12];
+  if constexpr (PPT == 16) {
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src + tid * 48);
+    const uint4 a = s4[0], b = s4[1], c = s4[2];
+    w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w, w[4] = b.x, w[5] = b.y;
+    w[6] = b.z, w[7] = b.w, w[8] = c.x, w[9] = c.y, w[10] = c.z, w[11] = c.w;
+#pragma unroll
+    for (int e = 0; e < 12; ++e) w[e] = (w[e] >> (8 - D)) & byte_mask(D);
+  } else {
+    const uint2 *s2 = reinterpret_cast<const uint2 *>(src + tid * 24);
+    const uint2 a = s2[0], b = s2[1], c = s2[2];
+    w[0] = a.x, w[1] = a.y, w[2] = b.x, w[3] = b.y, w[4] = c.x, w[5] = c.y;
+    w[6] = w[7] = w[8] = w[9] = w[10] = w[11] = 0;
+#pragma unroll
+    for (int e = 0; e < 6; ++e) w[e] = (w[e] >> (8 - D)) & byte_mask(D);
+  }
+  // mrow points at word 0 of pixel j=0 for this lane; pixel j's word q>>5 is at
+  // mrow[(j*WPR + (q>>5))*32]
+  static_for<0, PPT>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    const uint32_t q = planar_from_masked<D>(group_pixel<j>(w));
+    const uint32_t v = mrow[(j * C::WPR + (q >> 5)) * 32];
+    fbit[j] = __funnelshift_r(v, v, q);
+  });
+  if constexpr (PPT == 16) {
+    uint4 o;
+    o.x = pack_mask4(fbit[0], fbit[1], fbit[2], fbit[3]);
+    o.y = pack_mask4(fbit[4], fbit[5], fbit[6], fbit[7]);
+    o.z = pack_mask4(fbit[8], fbit[9], fbit[10], fbit[11]);
+    o.w = pack_mask4(fbit[12], fbit[13], fbit[14], fbit[15]);
+    st_stream16(dst + tid * 16, o);
+  } else {
+    const uint32_t x = pack_mask4(fbit[0], fbit[1], fbit[2], fbit[3]);
+    const uint32_t y = pack_mask4(fbit[4], fbit[5], fbit[6], fbit[7]);
+    asm volatile("st.global.cs.v2.u32 [%0], {%1,%2};" ::"l"(dst + tid * 8), "r"(x), "r"(y) : "memory");
+  }
+}
+
 // Work item u = tile * F + f; CTA b handles u in [b*U/G, (b+1)*U/G), i.e. a run
 // of frames of one tile, then of the next, reloading the tile's rows at each
-// tile change.  Requires: frames and mask 16-byte aligned, H*W % 16 == 0.
-template <int D, int NW, int PPT, int S>
+// tile change.  Frames move in groups of FPS per stage.  Requires: frames and
+// mask 16-byte aligned, H*W % 16 == 0.
+template <int D, int NW, int PPT, int S, int FPS>
 __global__ void __launch_bounds__(NW * 32, 1)
     classify_pixel_tiled_kernel(const uint8_t *__restrict__ frames, int F, int64_t hw, int64_t ntiles,
                                 const uint32_t *__restrict__ model, uint8_t *__restrict__ mask) {
-  using C = TiledCfg<D, NW, PPT, S>;
+  using C = TiledCfg<D, NW, PPT, S, FPS>;
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t *msm = reinterpret_cast<uint32_t *>(smem);
   uint8_t *stages = smem + (size_t)C::MODEL_WORDS * 4;
@@ -180,12 +180,14 @@ __global__ void __launch_bounds__(NW * 32, 1)
   const int64_t U = ntiles * (int64_t)F;
   const int64_t u_begin = U * blockIdx.x / gridDim.x;
   const int64_t u_end = U * (blockIdx.x + 1) / gridDim.x;
-  uint64_t kc = 0;  // copies consumed so far (stage = kc % S, phase = (kc / S) & 1)
+  const uint32_t *mrow = msm + warp * PPT * C::WPR * 32 + lane;
+  uint64_t kc = 0;  // stages consumed so far (stage = kc % S, phase = (kc / S) & 1)
 
   for (int64_t u = u_begin; u < u_end;) {
     const int64_t tile = u / F;
     const int fa = (int)(u - tile * F);
     const int nfr = (int)((u_end - u) < (int64_t)(F - fa) ? (u_end - u) : (int64_t)(F - fa));
+    const int ngroups = (nfr + FPS - 1) / FPS;
     const int64_t p_tile = tile * C::TILE;
 
     // Rows of this tile -> shared memory, word w of pixel (warp, lane, j) at
@@ -214,75 +216,41 @@ __global__ void __launch_bounds__(NW * 32, 1)
     }
     __syncthreads();
 
+    auto issue = [&](int g) {  // group g of this run -> stage (kc + g) % S
+      const int s = (int)((kc + g) % S);
+      const int f0 = fa + g * FPS;
+      const int nf = (nfr - g * FPS) < FPS ? (nfr - g * FPS) : FPS;
+      const uint32_t bar = smem_addr(&bars[s]);
+      mbar_expect_tx(bar, (uint32_t)(nf * C::FRAME_BYTES));
+      for (int i = 0; i < nf; ++i)
+        bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)i * C::FRAME_BYTES),
+                 frames + ((int64_t)(f0 + i) * hw + p_tile) * 3, C::FRAME_BYTES, bar);
+    };
     if (tid == 0) {
-      const int pre = nfr < S ? nfr : S;
-      for (int i = 0; i < pre; ++i) {
-        const int s = (int)((kc + i) % S);
-        const uint32_t bar = smem_addr(&bars[s]);
-        mbar_expect_tx(bar, C::STAGE);
-        bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE), frames + ((int64_t)(fa + i) * hw + p_tile) * 3, C::STAGE,
-                 bar);
-      }
+      const int pre = ngroups < S ? ngroups : S;
+      for (int g = 0; g < pre; ++g) issue(g);
     }
 
-    for (int i = 0; i < nfr; ++i) {
-      const uint64_t k = kc + i;
+    for (int g = 0; g < ngroups; ++g) {
+      const uint64_t k = kc + g;
       const int s = (int)(k % S);
-      const uint32_t parity = (uint32_t)((k / S) & 1);
-      const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), parity, kWaitLimitNs);
+      const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)((k / S) & 1), kWaitLimitNs);
       const uint8_t *stage = stages + (size_t)s * C::STAGE;
-      const int64_t f = fa + i;
-      uint32_t fbit[PPT];
-      if constexpr (PPT == 16) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(stage + tid * 48);
-        uint32_t w[12];
-        const uint4 a = src[0], b = src[1], c = src[2];
-        w[0] = a.x, w[1] = a.y, w[2] = a.z, w[3] = a.w, w[4] = b.x, w[5] = b.y;
-        w[6] = b.z, w[7] = b.w, w[8] = c.x, w[9] = c.y, w[10] = c.z, w[11] = c.w;
+      const int f0 = fa + g * FPS;
+      const int nf = (nfr - g * FPS) < FPS ? (nfr - g * FPS) : FPS;
 #pragma unroll
-        for (int e = 0; e < 12; ++e) w[e] = (w[e] >> (8 - D)) & byte_mask(D);
-        static_for<0, 16>([&](auto jc) {
-          constexpr int j = decltype(jc)::value;
-          const uint32_t q = planar_from_masked<D>(group_pixel<j>(w));
-          const uint32_t v = msm[((warp * PPT + j) * C::WPR + (q >> 5)) * 32 + lane];
-          fbit[j] = __funnelshift_r(v, v, q);
-        });
-      } else {
-        const uint2 *src = reinterpret_cast<const uint2 *>(stage + tid * 24);
-        uint32_t w[12];
-        const uint2 a = src[0], b = src[1], c = src[2];
-        w[0] = a.x, w[1] = a.y, w[2] = b.x, w[3] = b.y, w[4] = c.x, w[5] = c.y;
-        w[6] = w[7] = w[8] = w[9] = w[10] = w[11] = 0;
-#pragma unroll
-        for (int e = 0; e < 6; ++e) w[e] = (w[e] >> (8 - D)) & byte_mask(D);
-        static_for<0, 8>([&](auto jc) {
-          constexpr int j = decltype(jc)::value;
-          const uint32_t q = planar_from_masked<D>(group_pixel<j>(w));
-          const uint32_t v = msm[((warp * PPT + j) * C::WPR + (q >> 5)) * 32 + lane];
-          fbit[j] = __funnelshift_r(v, v, q);
-        });
+      for (int i = 0; i < FPS; ++i) {
+        if (i < nf)
+          classify_tile_frame<D, NW, PPT, S, FPS>(stage + (size_t)i * C::FRAME_BYTES, mrow,
+                                                  mask + (int64_t)(f0 + i) * hw + p_tile);
       }
-      uint8_t *dst = mask + f * hw + p_tile + (int64_t)tid * PPT;
-      if constexpr (PPT == 16) {
-        uint4 o;
-        o.x = pack_mask4(fbit[0], fbit[1], fbit[2], fbit[3]);
-        o.y = pack_mask4(fbit[4], fbit[5], fbit[6], fbit[7]);
-        o.z = pack_mask4(fbit[8], fbit[9], fbit[10], fbit[11]);
-        o.w = pack_mask4(fbit[12], fbit[13], fbit[14], fbit[15]);
-        st_stream16(dst, o);
-      } else {
-        uint2 o;
-        o.x = pack_mask4(fbit[0], fbit[1], fbit[2], fbit[3]);
-        o.y = pack_mask4(fbit[4], fbit[5], fbit[6], fbit[7]);
-        asm volatile("st.global.cs.v2.u32 [%0], {%1,%2};" ::"l"(dst), "r"(o.x), "r"(o.y) : "memory");
-      }
-      // Stage s is consumed by every thread; refill it with frame i + S.
+      // Stage s is consumed by every thread; refill it with group g + S.
       if (__syncthreads_or(!ok)) {
         // A copy did not arrive in time: record it, let every copy this CTA
         // still has in flight land (bounded), and leave.
         if (tid == 0) {
           atomicExch(&g_classify_timeout, 1u);
-          const int inflight = (nfr - i) < S ? (nfr - i) : S;
+          const int inflight = (ngroups - g) < S ? (ngroups - g) : S;
           for (int j = 0; j < inflight; ++j) {
             const uint64_t kk = k + j;
             mbar_wait_bounded(smem_addr(&bars[kk % S]), (uint32_t)((kk / S) & 1), kWaitLimitNs);
@@ -291,14 +259,9 @@ __global__ void __launch_bounds__(NW * 32, 1)
         __syncthreads();
         return;
       }
-      if (tid == 0 && i + S < nfr) {
-        const uint32_t bar = smem_addr(&bars[s]);
-        mbar_expect_tx(bar, C::STAGE);
-        bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE), frames + ((int64_t)(fa + i + S) * hw + p_tile) * 3,
-                 C::STAGE, bar);
-      }
+      if (tid == 0 && g + S < ngroups) issue(g + S);
     }
-    kc += nfr;
+    kc += ngroups;
     u += nfr;
     __syncthreads();  // all reads of this tile's rows are done before the next reload
   }
@@ -336,14 +299,14 @@ static ocq_status launch_frame(const ocq_model *m, const uint8_t *frames, int F,
   return cuda_status(cudaGetLastError(), "classify_frame_kernel");
 }
 
-template <int D, int NW, int PPT, int S>
+template <int D, int NW, int PPT, int S, int FPS>
 static ocq_status launch_tiled(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st) {
-  using C = TiledCfg<D, NW, PPT, S>;
+  using C = TiledCfg<D, NW, PPT, S, FPS>;
   const int64_t hw = (int64_t)m->H * m->W;
   const int64_t ntiles = hw / C::TILE;
   ocq_status rc = OCQ_OK;
   if (ntiles > 0) {
-    auto kern = classify_pixel_tiled_kernel<D, NW, PPT, S>;
+    auto kern = classify_pixel_tiled_kernel<D, NW, PPT, S, FPS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return cuda_status(e, "classify_pixel_tiled_kernel smem");
     int per_sm = 0;
@@ -360,6 +323,36 @@ static ocq_status launch_tiled(const ocq_model *m, const uint8_t *frames, int F,
   return rc;
 }
 
+// ---- tunable variants of the per-pixel tiled kernel ---------------------------------
+using ClassifyFn = ocq_status (*)(const ocq_model *, const uint8_t *, int, uint8_t *, cudaStream_t);
+struct ClassifyVariant {
+  int nw, ppt, stages, fps;
+  ClassifyFn fn[3];  // depth 1, 2, 3
+};
+#define OCQ_CV(NW, PPT, S, FPS)                                                          \
+  {                                                                                      \
+    NW, PPT, S, FPS, {                                                                   \
+      launch_tiled<1, NW, PPT, S, FPS>, launch_tiled<2, NW, PPT, S, FPS>, launch_tiled<3, NW, PPT, S, FPS> \
+    }                                                                                    \
+  }
+static const ClassifyVariant kClassifyVariants[] = {
+    OCQ_CV(4, 8, 4, 4), OCQ_CV(4, 8, 12, 1), OCQ_CV(4, 8, 6, 2), OCQ_CV(2, 16, 4, 4),
+    OCQ_CV(8, 8, 4, 2), OCQ_CV(4, 16, 3, 2), OCQ_CV(8, 8, 3, 4), OCQ_CV(4, 8, 3, 6)};
+#undef OCQ_CV
+static int g_classify_variant = 0;
+
+int classify_variant_count() { return (int)(sizeof kClassifyVariants / sizeof kClassifyVariants[0]); }
+int classify_variant_selected() { return g_classify_variant; }
+bool classify_variant_select(int v) {
+  if (v < 0 || v >= classify_variant_count()) return false;
+  g_classify_variant = v;
+  return true;
+}
+void classify_variant_describe(int v, int *nw, int *ppt, int *stages, int *fps) {
+  *nw = kClassifyVariants[v].nw, *ppt = kClassifyVariants[v].ppt;
+  *stages = kClassifyVariants[v].stages, *fps = kClassifyVariants[v].fps;
+}
+
 ocq_status launch_classify(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st) {
   const int64_t hw = (int64_t)m->H * m->W;
   const int d = m->depth;
@@ -374,28 +367,16 @@ ocq_status launch_classify(const ocq_model *m, const uint8_t *frames, int F, uin
     }
   }
   const bool aligned = ((reinterpret_cast<uintptr_t>(frames) | reinterpret_cast<uintptr_t>(mask)) & 15) == 0;
-  if (m->kind == OCQ_REGION_PIXEL && d <= 3 && aligned && hw % 16 == 0) {
-    switch (d) {
-      case 1: return launch_tiled<1, 4, 8, 12>(m, frames, F, mask, st);
-      case 2: return launch_tiled<2, 4, 8, 12>(m, frames, F, mask, st);
-      default: return launch_tiled<3, 4, 8, 12>(m, frames, F, mask, st);
-    }
-  }
+  if (m->kind == OCQ_REGION_PIXEL && d <= 3 && aligned && hw % 16 == 0)
+    return kClassifyVariants[g_classify_variant].fn[d - 1](m, frames, F, mask, st);
   return launch_generic(m, frames, F, mask, 0, hw, st);
 }
 
-ocq_status device_status(cudaStream_t st) {
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_status(e, "stream synchronise");
+bool classify_take_timeout() {
   unsigned int flag = 0, zero = 0;
-  e = cudaMemcpyFromSymbol(&flag, g_classify_timeout, sizeof flag);
-  if (e != cudaSuccess) return cuda_status(e, "reading the device status");
-  if (flag) {
-    cudaMemcpyToSymbol(g_classify_timeout, &zero, sizeof zero);
-    set_error("a bounded device wait timed out");
-    return OCQ_ETIMEOUT;
-  }
-  return OCQ_OK;
+  if (cudaMemcpyFromSymbol(&flag, g_classify_timeout, sizeof flag) != cudaSuccess) return false;
+  if (flag) cudaMemcpyToSymbol(g_classify_timeout, &zero, sizeof zero);
+  return flag != 0;
 }
 
 }  // namespace ocq

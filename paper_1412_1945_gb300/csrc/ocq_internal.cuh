@@ -150,6 +150,18 @@ ocq_status launch_occupancy(const uint8_t *frames, int n, int H, int W, int kind
                             uint64_t *occ, cudaStream_t st);
 ocq_status launch_export(const uint32_t *bits, int64_t R, int depth, uint64_t *dst, cudaStream_t st);
 ocq_status launch_import(const uint64_t *src, int64_t R, int depth, uint32_t *bits, cudaStream_t st);
-ocq_status device_status(cudaStream_t st);
+bool classify_take_timeout();
+bool build_take_timeout();
+
+// Kernel variants the tuner can choose between (per-pixel tiled classify,
+// staged per-pixel build).
+int classify_variant_count();
+int classify_variant_selected();
+bool classify_variant_select(int v);
+void classify_variant_describe(int v, int *nw, int *ppt, int *stages, int *fps);
+int build_variant_count();
+int build_variant_selected();
+bool build_variant_select(int v);
+void build_variant_describe(int v, int *nt, int *fps, int *stages);
 
 }  // namespace ocq

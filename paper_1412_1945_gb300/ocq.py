@@ -64,7 +64,13 @@ SIGNATURES = {
     "ocq_detect_host": (_i32, [_vp, _i32, _vp, _i32, _i32, _i32, ocq_region, _i32, _i32, _vp, _vp,
                                ctypes.POINTER(_vp)]),
     "ocq_kernel_launches": (ctypes.c_uint64, []),
+    "ocq_tune_count": (_i32, [_i32]),
+    "ocq_tune_selected": (_i32, [_i32]),
+    "ocq_tune_select": (_i32, [_i32, _i32]),
+    "ocq_tune_describe": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_int32), _i32]),
 }
+
+OCQ_TUNE_CLASSIFY_PIXEL, OCQ_TUNE_BUILD_PIXEL = 0, 1
 
 
 def load(path: str | None = None):
@@ -226,3 +232,22 @@ def ocq_detect_host(train, N, test, F, H, W, kind, block, depth, T, mask, stream
 
 def ocq_kernel_launches() -> int:
     return int(load().ocq_kernel_launches())
+
+
+
+def ocq_tune_count(kernel: int) -> int:
+    return int(load().ocq_tune_count(kernel))
+
+
+def ocq_tune_selected(kernel: int) -> int:
+    return int(load().ocq_tune_selected(kernel))
+
+
+def ocq_tune_select(kernel: int, variant: int):
+    _check(load().ocq_tune_select(kernel, variant))
+
+
+def ocq_tune_describe(kernel: int, variant: int):
+    buf = (ctypes.c_int32 * 4)()
+    _check(load().ocq_tune_describe(kernel, variant, buf, 4))
+    return list(buf)

@@ -221,3 +221,40 @@ def test_synth_device_matches_host(ocq, torch):
         dgt = torch.empty(gt.shape, dtype=torch.uint8, device="cuda")
         ocq_synth.fill_device(sc, wl.N - 2, 5, dev, dgt)
         assert (dev.cpu().numpy() == host).all() and (dgt.cpu().numpy() == gt).all()
+
+
+def test_pixel_staged_counter_widths(ocq, torch):
+    """Staged per-pixel build with 4-bit (T <= 15) and 8-bit (T <= 255)
+    counters saturating at T, also with N > 255."""
+    g = np.random.default_rng(21)
+    palette = g.integers(0, 256, size=(4, 3), dtype=np.uint8)
+    train = palette[g.integers(0, 4, size=(300, 16, 32))]
+    train[:, :, ::5] = g.integers(0, 256, size=train[:, :, ::5].shape, dtype=np.uint8)
+    test = palette[g.integers(0, 4, size=(3, 16, 32))]
+    for T in (1, 14, 15, 16, 90, 255):
+        words, mask = gpu_model_and_mask(ocq, torch, train, test, 3, T, PIXEL, 0)
+        ow, om = oracle.run(train, 3, T, PIXEL, 0, test)
+        assert (words == ow).all() and (mask == om).all(), T
+
+
+@pytest.mark.parametrize("H,W", [(64, 96), (50, 80)])
+def test_every_tuning_variant(ocq, torch, H, W):
+    """Each selectable kernel variant of the per-pixel build and classify gives
+    the oracle's result (several tiles of every tile size, plus a ragged rest)."""
+    O = ocq.ocq
+    sc = ocq_synth.make_scene("bimodal", H, W, 20, 11, seed=5)
+    frames = ocq_synth.fill_host(sc, 0, 31)
+    train, test = frames[:20], frames[20:]
+    for d in (1, 2, 3):
+        for T in (4, 17):
+            ow, om = oracle.run(train, d, T, PIXEL, 0, test)
+            for kernel in (O.OCQ_TUNE_BUILD_PIXEL, O.OCQ_TUNE_CLASSIFY_PIXEL):
+                saved = O.ocq_tune_selected(kernel)
+                try:
+                    for v in range(O.ocq_tune_count(kernel)):
+                        O.ocq_tune_select(kernel, v)
+                        words, mask = gpu_model_and_mask(ocq, torch, train, test, d, T, PIXEL, 0)
+                        assert (words == ow).all(), (kernel, v, d, T)
+                        assert (mask == om).all(), (kernel, v, d, T)
+                finally:
+                    O.ocq_tune_select(kernel, saved)
