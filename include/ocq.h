@@ -164,7 +164,8 @@ ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int
  *   OCQ_TUNE_CLASSIFY_PIXEL  per-pixel classify, depth <= 3; params =
  *                            {warps per CTA, pixels per thread, stages, frames per stage}
  *   OCQ_TUNE_BUILD_PIXEL     per-pixel build, depth <= 3; params =
- *                            {pixels (threads) per CTA, frames per stage, stages, 0}
+ *                            {pixels (threads) per CTA, frames per stage, stages,
+ *                             1 if a stage is one 2-D tensor copy}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 4

@@ -63,7 +63,7 @@ def build(verbose: bool = False, extra_flags=()) -> str:
     stamp = SO + ".stamp"
     if jobs or not os.path.exists(SO) or not os.path.exists(stamp) or open(stamp).read() != link_tag:
         tmp = SO + ".tmp"
-        cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcuda"]
+        cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

@@ -282,7 +282,7 @@ ocq_status ocq_tune_describe(int kernel, int variant, int32_t *params, int n) {
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL)
     classify_variant_describe(variant, &params[0], &params[1], &params[2], &params[3]);
   else
-    build_variant_describe(variant, &params[0], &params[1], &params[2]);
+    build_variant_describe(variant, &params[0], &params[1], &params[2], &params[3]);
   return OCQ_OK;
 }
 

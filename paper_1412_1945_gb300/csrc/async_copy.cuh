@@ -54,6 +54,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   }
 }
 
+// 2-D tiled tensor copy (TMA): box at element coordinates (x, y) of the tensor
+// described by `tmap` (a __grid_constant__ kernel parameter) -> shared `dst`.
+__device__ __forceinline__ void tensor2d_g2s(uint32_t dst, const void *tmap, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
 static constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per wait
 
 }  // namespace ocq

@@ -14,7 +14,11 @@
 //     byte (or u16) counters for all 8^d leaves in shared memory;
 //   * pixel regions, depth >= 4: per-thread counters for 512-leaf chunks, only
 //     for chunks the pixel's N colours touch.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstdint>
+#include <cstring>
 
 #include "async_copy.cuh"
 #include "pixels.cuh"
@@ -245,6 +249,8 @@ __global__ void __launch_bounds__(128) build_pixel_counters_kernel(const uint8_t
 // occurred, so the end of a tile visits only those leaves, and leaves their
 // counters at zero for the next tile.  Requires frames 16-byte aligned and
 // H*W % 16 == 0; covers full tiles only.
+// TENSOR: each stage is one 2-D tensor copy (TMA) of a box of FPS frame rows x
+// ROW bytes, instead of FPS row copies.
 template <int D, int CB, int NT, int FPS, int S>
 struct StagedBuildCfg {
   static constexpr int NC = 1 << (3 * D);
@@ -253,19 +259,21 @@ struct StagedBuildCfg {
   static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
   static constexpr int ROW = NT * 3;                   // bytes of one frame's tile
   static constexpr int STAGE = ROW * FPS;
-  static constexpr size_t SMEM = ((size_t)CW + WPR) * NT * 4 + (size_t)S * STAGE + (size_t)S * 8;
-  static_assert(ROW % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static constexpr size_t STATE = ((size_t)CW + WPR) * NT * 4;
+  static constexpr size_t SMEM = STATE + 128 + (size_t)S * STAGE + (size_t)S * 8;
+  static_assert(ROW % 128 == 0 && STAGE % 128 == 0, "stages stay 128-byte aligned");
 };
 
-template <int D, int CB, int NT, int FPS, int S>
+template <int D, int CB, int NT, int FPS, int S, bool TENSOR>
 __global__ void __launch_bounds__(NT) build_pixel_staged_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
                                                                 int64_t ntiles, uint32_t T,
-                                                                uint32_t *__restrict__ model) {
+                                                                uint32_t *__restrict__ model,
+                                                                const __grid_constant__ CUtensorMap tmap) {
   using C = StagedBuildCfg<D, CB, NT, FPS, S>;
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // [CW][NT]
   uint32_t *touched = cnt + C::CW * NT;                // [WPR][NT]
-  uint8_t *stages = reinterpret_cast<uint8_t *>(touched + C::WPR * NT);
+  uint8_t *stages = smem + ((C::STATE + (128 - (smem_addr(smem) + C::STATE) % 128) % 128));
   uint64_t *bars = reinterpret_cast<uint64_t *>(stages + (size_t)S * C::STAGE);
   const int t = threadIdx.x;
   constexpr uint32_t CMASK = (1u << CB) - 1u;
@@ -288,10 +296,16 @@ __global__ void __launch_bounds__(NT) build_pixel_staged_kernel(const uint8_t *_
     const int nf = N - f0 < FPS ? N - f0 : FPS;
     const int s = (int)(k % S);
     const uint32_t bar = smem_addr(&bars[s]);
-    mbar_expect_tx(bar, (uint32_t)(nf * C::ROW));
-    for (int j = 0; j < nf; ++j)
-      bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)j * C::ROW),
-               frames + ((int64_t)(f0 + j) * hw + tile * NT) * 3, C::ROW, bar);
+    if constexpr (TENSOR) {
+      // rows past frame N-1 are filled with zeros and still count as bytes
+      mbar_expect_tx(bar, (uint32_t)C::STAGE);
+      tensor2d_g2s(smem_addr(stages + (size_t)s * C::STAGE), &tmap, (int)(tile * (C::ROW / 4)), f0, bar);
+    } else {
+      mbar_expect_tx(bar, (uint32_t)(nf * C::ROW));
+      for (int j = 0; j < nf; ++j)
+        bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)j * C::ROW),
+                 frames + ((int64_t)(f0 + j) * hw + tile * NT) * 3, C::ROW, bar);
+    }
   };
   if (t == 0)
     for (int64_t k = 0; k < total && k < S; ++k) issue(k);
@@ -524,14 +538,50 @@ static ocq_status launch_pixel_counters(const uint8_t *frames, int N, ocq_model 
   return cuda_status(cudaGetLastError(), "build_pixel_counters_kernel");
 }
 
-template <int D, int CB, int NT, int FPS, int S>
+// Tensor map of the training frames as a 2-D array of u32: (H*W*3/4) x N,
+// rows H*W*3 bytes apart, box (NT*3/4) x FPS.
+// The driver's encoder is looked up through the runtime, so the library does
+// not link libcuda directly (it loads on machines without a GPU driver).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+static bool encode_frames_map(CUtensorMap *map, const uint8_t *frames, int N, int64_t hw, int nt, int fps) {
+  memset(map, 0, sizeof *map);
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)(hw * 3 / 4), (cuuint64_t)N};
+  const cuuint64_t strides[1] = {(cuuint64_t)(hw * 3)};
+  const cuuint32_t box[2] = {(cuuint32_t)(nt * 3 / 4), (cuuint32_t)fps};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, (void *)frames, dims, strides, box, estr,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int D, int CB, int NT, int FPS, int S, bool TENSOR = false>
 static ocq_status launch_pixel_staged(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
   using C = StagedBuildCfg<D, CB, NT, FPS, S>;
   const int64_t hw = (int64_t)m->H * m->W;
-  constexpr bool fits = C::SMEM <= 227 * 1024;
+  constexpr bool fits = C::SMEM <= 227 * 1024 && (!TENSOR || (NT * 3 / 4 <= 256 && FPS <= 256));
   const int64_t ntiles = fits ? hw / NT : 0;
+  CUtensorMap map;
+  memset(&map, 0, sizeof map);
+  if (TENSOR && ntiles > 0 && !encode_frames_map(&map, frames, N, hw, NT, FPS)) {
+    set_error("cuTensorMapEncodeTiled failed for the training frames");
+    return OCQ_ECUDA;
+  }
   if (ntiles > 0) {
-    auto kern = build_pixel_staged_kernel<D, CB, NT, FPS, S>;
+    auto kern = build_pixel_staged_kernel<D, CB, NT, FPS, S, TENSOR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return cuda_status(e, "build_pixel_staged_kernel smem");
     int per_sm = 0;
@@ -539,7 +589,7 @@ static ocq_status launch_pixel_staged(const uint8_t *frames, int N, ocq_model *m
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)sm_count() * per_sm;
     if (grid > ntiles) grid = ntiles;
-    kern<<<(unsigned)grid, NT, C::SMEM, st>>>(frames, N, hw, ntiles, (uint32_t)m->T, m->bits);
+    kern<<<(unsigned)grid, NT, C::SMEM, st>>>(frames, N, hw, ntiles, (uint32_t)m->T, m->bits, map);
     count_launch();
     ocq_status rc = cuda_status(cudaGetLastError(), "build_pixel_staged_kernel");
     if (rc != OCQ_OK) return rc;
@@ -576,20 +626,21 @@ static ocq_status launch_pixel_chunked(const uint8_t *frames, int N, ocq_model *
 // ---- tunable variants ------------------------------------------------------------
 using BuildFn = ocq_status (*)(const uint8_t *, int, ocq_model *, cudaStream_t);
 struct BuildVariant {
-  int nt, fps, stages;
+  int nt, fps, stages, tensor;
   BuildFn fn[2][3];  // [4-bit, 8-bit counters][depth 1, 2, 3]
 };
-#define OCQ_BV(NT, F, S)                                                                              \
+#define OCQ_BV(NT, F, S, TS)                                                                          \
   {                                                                                                  \
-    NT, F, S, {                                                                                      \
-      {launch_pixel_staged<1, 4, NT, F, S>, launch_pixel_staged<2, 4, NT, F, S>,                     \
-       launch_pixel_staged<3, 4, NT, F, S>},                                                         \
-          {launch_pixel_staged<1, 8, NT, F, S>, launch_pixel_staged<2, 8, NT, F, S>,                 \
-           launch_pixel_staged<3, 8, NT, F, S>}                                                      \
+    NT, F, S, TS, {                                                                                  \
+      {launch_pixel_staged<1, 4, NT, F, S, TS>, launch_pixel_staged<2, 4, NT, F, S, TS>,             \
+       launch_pixel_staged<3, 4, NT, F, S, TS>},                                                     \
+          {launch_pixel_staged<1, 8, NT, F, S, TS>, launch_pixel_staged<2, 8, NT, F, S, TS>,         \
+           launch_pixel_staged<3, 8, NT, F, S, TS>}                                                  \
     }                                                                                                \
   }
-static const BuildVariant kBuildVariants[] = {OCQ_BV(128, 8, 3), OCQ_BV(256, 4, 4), OCQ_BV(512, 4, 3),
-                                              OCQ_BV(128, 16, 2), OCQ_BV(256, 8, 3), OCQ_BV(128, 4, 6)};
+static const BuildVariant kBuildVariants[] = {
+    OCQ_BV(128, 16, 2, false), OCQ_BV(128, 24, 3, false), OCQ_BV(128, 32, 2, false), OCQ_BV(256, 10, 4, false),
+    OCQ_BV(128, 16, 3, true),  OCQ_BV(128, 32, 2, true),  OCQ_BV(256, 16, 3, true),  OCQ_BV(128, 8, 6, true)};
 #undef OCQ_BV
 static int g_build_variant = 0;
 
@@ -600,10 +651,11 @@ bool build_variant_select(int v) {
   g_build_variant = v;
   return true;
 }
-void build_variant_describe(int v, int *nt, int *fps, int *stages) {
+void build_variant_describe(int v, int *nt, int *fps, int *stages, int *tensor) {
   *nt = kBuildVariants[v].nt;
   *fps = kBuildVariants[v].fps;
   *stages = kBuildVariants[v].stages;
+  *tensor = kBuildVariants[v].tensor;
 }
 
 // 4-bit counters saturating at T when T <= 15, else 8-bit (T <= 255).

@@ -162,6 +162,6 @@ void classify_variant_describe(int v, int *nw, int *ppt, int *stages, int *fps);
 int build_variant_count();
 int build_variant_selected();
 bool build_variant_select(int v);
-void build_variant_describe(int v, int *nt, int *fps, int *stages);
+void build_variant_describe(int v, int *nt, int *fps, int *stages, int *tensor);
 
 }  // namespace ocq
