@@ -178,29 +178,36 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def classify_source_hash():
+KERNEL_SOURCES = ("classify.cu", "build.cu", "pixels.cuh", "ocq_internal.cuh", "async_copy.cuh")
+
+
+def kernel_source_hash():
+    """Hash of the sources of the measured kernels (ties a committed ncu figure
+    to the code it was taken on)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1412_1945_gb300", "csrc")
-    for name in ("classify.cu", "pixels.cuh", "ocq_internal.cuh"):
+    for name in KERNEL_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current classify sources (else None)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes (read + write) per launch from the committed ncu summary
+    ``profiles/traffic.md``, if it was taken on the current kernel sources
+    (else None).  Rows: ``| kernel | workload | source hash | bytes |``."""
+    p = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(p):
         return None
-    try:
-        d = json.load(open(p))
-        e = d[kernel][workload]
-        if e.get("source_hash") != classify_source_hash():
-            return None
-        return float(e["dram_bytes_per_launch"])
-    except (KeyError, ValueError, TypeError):
-        return None
+    want = kernel_source_hash()
+    for line in open(p):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel and cells[1] == workload and cells[2] == want:
+            try:
+                return float(cells[3])
+            except ValueError:
+                return None
+    return None
 
 
 # ---- CPU oracle timing -----------------------------------------------------------
@@ -332,6 +339,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": "classify_pixel_tiled_kernel", "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": profiled_traffic("classify_pixel_tiled_kernel", wl.name),
+                     "source_hash": kernel_source_hash(),
                      "algorithmic_bytes_per_launch": cls_bytes, "peak_source": peak_kind},
         "build": {"ms": round(build_ms, 4), "mpixel_s": round(N * hw / (build_ms / 1e3) / 1e6, 1),
                   "gbs": round(build_bytes / (build_ms / 1e3) / 1e9, 1),

@@ -165,7 +165,10 @@ ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int
  *                            {warps per CTA, pixels per thread, stages, frames per stage}
  *   OCQ_TUNE_BUILD_PIXEL     per-pixel build, depth <= 3; params =
  *                            {pixels (threads) per CTA, frames per stage, stages,
- *                             1 if a stage is one 2-D tensor copy}
+ *                             kind: 0 saturating counters, row copies; 1 the same with
+ *                             one 2-D tensor copy per stage; 2 byte counters bumped
+ *                             by shared-memory reductions; 3 saturating counters fed by
+ *                             direct loads, frames per stage = frames prefetched}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 4

@@ -378,6 +378,190 @@ __global__ void __launch_bounds__(NT) build_pixel_staged_kernel(const uint8_t *_
   }
 }
 
+// Byte counters bumped with shared-memory reductions (red.shared.add, no
+// return value), so successive frames of one pixel do not form a
+// read-modify-write chain.  Counts stay <= N <= 255.  Each thread keeps a
+// 16-bit mask of the model words (32 leaves each) its pixel touched; at the
+// end of a tile only those words' counters are read, thresholded and zeroed.
+// Same staging, alignment and coverage rules as build_pixel_staged_kernel.
+template <int D, int NT, int FPS, int S>
+struct RedBuildCfg {
+  static constexpr int NC = 1 << (3 * D);
+  static constexpr int CW = (NC + 3) / 4;  // u8 counter words per pixel
+  static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  static constexpr int ROW = NT * 3;
+  static constexpr int STAGE = ROW * FPS;
+  static constexpr size_t STATE = (size_t)CW * NT * 4;
+  static constexpr size_t SMEM = STATE + 128 + (size_t)S * STAGE + (size_t)S * 8;
+  static_assert(ROW % 128 == 0, "stages stay 128-byte aligned");
+};
+
+__device__ __forceinline__ void red_add_shared(uint32_t *p, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
+
+template <int D, int NT, int FPS, int S>
+__global__ void __launch_bounds__(NT) build_pixel_red_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
+                                                             int64_t ntiles, uint32_t T,
+                                                             uint32_t *__restrict__ model) {
+  using C = RedBuildCfg<D, NT, FPS, S>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // [CW][NT]
+  uint8_t *stages = smem + ((C::STATE + (128 - (smem_addr(smem) + C::STATE) % 128) % 128));
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stages + (size_t)S * C::STAGE);
+  const int t = threadIdx.x;
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+#pragma unroll 8
+  for (int c = 0; c < C::CW; ++c) cnt[c * NT + t] = 0;
+  __syncthreads();
+  const int G = (N + FPS - 1) / FPS;
+  const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t total = my_tiles * G;
+  auto issue = [&](int64_t k) {
+    const int64_t i = k / G;
+    const int g = (int)(k - i * G);
+    const int64_t tile = blockIdx.x + i * gridDim.x;
+    const int f0 = g * FPS;
+    const int nf = N - f0 < FPS ? N - f0 : FPS;
+    const int s = (int)(k % S);
+    const uint32_t bar = smem_addr(&bars[s]);
+    mbar_expect_tx(bar, (uint32_t)(nf * C::ROW));
+    for (int j = 0; j < nf; ++j)
+      bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)j * C::ROW),
+               frames + ((int64_t)(f0 + j) * hw + tile * NT) * 3, C::ROW, bar);
+  };
+  if (t == 0)
+    for (int64_t k = 0; k < total && k < S; ++k) issue(k);
+
+  uint32_t words = 0;  // model words (32 leaves each) this pixel touched in the current tile
+  for (int64_t k = 0; k < total; ++k) {
+    const int64_t i = k / G;
+    const int g = (int)(k - i * G);
+    const int s = (int)(k % S);
+    const bool ok = mbar_wait_bounded(smem_addr(&bars[s]), (uint32_t)((k / S) & 1), kWaitLimitNs);
+    const uint8_t *stage = stages + (size_t)s * C::STAGE + 3 * t;
+    const int nf = N - g * FPS < FPS ? N - g * FPS : FPS;
+#pragma unroll
+    for (int j = 0; j < FPS; ++j) {
+      if (j < nf) {
+        const uint8_t *px = stage + j * C::ROW;
+        const uint32_t y = (uint32_t)px[0] | ((uint32_t)px[1] << 8) | ((uint32_t)px[2] << 16);
+        const uint32_t q = planar_code<D>(y);
+        red_add_shared(&cnt[(q >> 2) * NT + t], 1u << ((q & 3u) * 8));
+        words |= 1u << (q >> 5);
+      }
+    }
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicExch(&g_build_timeout, 1u);
+        for (int64_t kk = k; kk < total && kk < k + S; ++kk)
+          mbar_wait_bounded(smem_addr(&bars[kk % S]), (uint32_t)((kk / S) & 1), kWaitLimitNs);
+      }
+      __syncthreads();
+      return;
+    }
+    if (t == 0 && k + S < total) issue(k + S);
+    if (g == G - 1) {
+      uint32_t *dst = model + ((blockIdx.x + i * gridDim.x) * NT + t) * C::WPR;
+      if constexpr (C::WPR % 4 == 0) {
+#pragma unroll
+        for (int w = 0; w < C::WPR; w += 4) *reinterpret_cast<uint4 *>(dst + w) = make_uint4(0, 0, 0, 0);
+      } else {
+#pragma unroll
+        for (int w = 0; w < C::WPR; ++w) dst[w] = 0;
+      }
+      for (; words; words &= words - 1) {
+        const int w = __ffs(words) - 1;
+        uint32_t o = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (w * 8 + c < C::CW) {
+            uint32_t *cp = &cnt[(w * 8 + c) * NT + t];
+            const uint32_t v = *cp;
+            if (v) {
+              const uint32_t ge = __vcmpgeu4(v, T * 0x01010101u);
+              o |= (((ge >> 7) & 1u) | ((ge >> 14) & 2u) | ((ge >> 21) & 4u) | ((ge >> 28) & 8u)) << (4 * c);
+              *cp = 0;
+            }
+          }
+        }
+        dst[w] = o;
+      }
+    }
+  }
+}
+
+// Direct-load form: one CTA of NT threads per NT-pixel tile, no staging ring.
+// Each thread prefetches its pixel's bytes of PF frames into registers, then
+// counts them in its private column of CB-bit counters (saturating at T) and
+// sets the leaf's bit in a private "kept" row the moment its count reaches T.
+// All shared memory is counter state, so a SM keeps many pixels in flight.
+template <int D, int CB, int NT, int PF>
+struct DirectBuildCfg {
+  static constexpr int NC = 1 << (3 * D);
+  static constexpr int CPW = 32 / CB;
+  static constexpr int CW = (NC + CPW - 1) / CPW;
+  static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  static constexpr size_t SMEM = ((size_t)CW + WPR) * NT * 4;
+};
+
+template <int D, int CB, int NT, int PF>
+__global__ void __launch_bounds__(NT) build_pixel_direct_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
+                                                                int64_t p_begin, uint32_t T,
+                                                                uint32_t *__restrict__ model) {
+  using C = DirectBuildCfg<D, CB, NT, PF>;
+  extern __shared__ uint32_t sm[];
+  uint32_t *cnt = sm;                    // [CW][NT]
+  uint32_t *kept = sm + C::CW * NT;      // [WPR][NT]
+  constexpr uint32_t CMASK = (1u << CB) - 1u;
+  const int t = threadIdx.x;
+  const int64_t p = p_begin + (int64_t)blockIdx.x * NT + t;
+  if (p >= hw) return;  // columns are private: no CTA-wide synchronisation
+#pragma unroll 8
+  for (int c = 0; c < C::CW; ++c) cnt[c * NT + t] = 0;
+#pragma unroll
+  for (int w = 0; w < C::WPR; ++w) kept[w * NT + t] = 0;
+  const uint8_t *px = frames + p * 3;
+  const int64_t fstride = hw * 3;
+  for (int f0 = 0; f0 < N; f0 += PF) {
+    uint32_t y[PF];
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (f0 + j < N) {
+        const uint8_t *s = px + (int64_t)(f0 + j) * fstride;
+        y[j] = (uint32_t)__ldg(s) | ((uint32_t)__ldg(s + 1) << 8) | ((uint32_t)__ldg(s + 2) << 16);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (f0 + j < N) {
+        const uint32_t q = planar_code<D>(y[j]);
+        uint32_t *cw = &cnt[(q / C::CPW) * NT + t];
+        const uint32_t sh = (q % C::CPW) * CB;
+        const uint32_t v = *cw;
+        const uint32_t c = (v >> sh) & CMASK;
+        if (c < T) {
+          *cw = v + (1u << sh);
+          if (c + 1 == T) kept[(q >> 5) * NT + t] |= 1u << (q & 31);
+        }
+      }
+    }
+  }
+  uint32_t *dst = model + p * C::WPR;
+  if constexpr (C::WPR % 4 == 0) {
+#pragma unroll
+    for (int w = 0; w < C::WPR; w += 4)
+      *reinterpret_cast<uint4 *>(dst + w) =
+          make_uint4(kept[w * NT + t], kept[(w + 1) * NT + t], kept[(w + 2) * NT + t], kept[(w + 3) * NT + t]);
+  } else {
+#pragma unroll
+    for (int w = 0; w < C::WPR; ++w) dst[w] = kept[w * NT + t];
+  }
+}
+
 // ---- pixel regions, depth >= 4 --------------------------------------------------
 // Counts leaves chunk by chunk (512 leaves, u16 counters in a private column
 // of 256 words) for the chunks the pixel's training colours touch.  `touched`
@@ -623,6 +807,44 @@ static ocq_status launch_pixel_chunked(const uint8_t *frames, int N, ocq_model *
   return rc;
 }
 
+template <int D, int CB, int NT, int PF>
+static ocq_status launch_pixel_direct(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  using C = DirectBuildCfg<D, CB, NT, PF>;
+  const int64_t hw = (int64_t)m->H * m->W;
+  auto kern = build_pixel_direct_kernel<D, CB, NT, PF>;
+  if (C::SMEM > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return cuda_status(e, "build_pixel_direct_kernel smem");
+  }
+  kern<<<(unsigned)((hw + NT - 1) / NT), NT, C::SMEM, st>>>(frames, N, hw, 0, (uint32_t)m->T, m->bits);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "build_pixel_direct_kernel");
+}
+
+template <int D, int NT, int FPS, int S>
+static ocq_status launch_pixel_red(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  using C = RedBuildCfg<D, NT, FPS, S>;
+  if (N > 255) return launch_pixel_counters<D, true>(frames, N, m, st, 0);
+  const int64_t hw = (int64_t)m->H * m->W;
+  constexpr bool fits = C::SMEM <= 227 * 1024;
+  const int64_t ntiles = fits ? hw / NT : 0;
+  if (ntiles > 0) {
+    auto kern = build_pixel_red_kernel<D, NT, FPS, S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess) return cuda_status(e, "build_pixel_red_kernel smem");
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, C::SMEM);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sm_count() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    kern<<<(unsigned)grid, NT, C::SMEM, st>>>(frames, N, hw, ntiles, (uint32_t)m->T, m->bits);
+    count_launch();
+    ocq_status rc = cuda_status(cudaGetLastError(), "build_pixel_red_kernel");
+    if (rc != OCQ_OK) return rc;
+  }
+  return launch_pixel_counters<D, false>(frames, N, m, st, ntiles * NT);
+}
+
 // ---- tunable variants ------------------------------------------------------------
 using BuildFn = ocq_status (*)(const uint8_t *, int, ocq_model *, cudaStream_t);
 struct BuildVariant {
@@ -638,10 +860,29 @@ struct BuildVariant {
            launch_pixel_staged<3, 8, NT, F, S, TS>}                                                  \
     }                                                                                                \
   }
-static const BuildVariant kBuildVariants[] = {
-    OCQ_BV(128, 16, 2, false), OCQ_BV(128, 24, 3, false), OCQ_BV(128, 32, 2, false), OCQ_BV(256, 10, 4, false),
-    OCQ_BV(128, 16, 3, true),  OCQ_BV(128, 32, 2, true),  OCQ_BV(256, 16, 3, true),  OCQ_BV(128, 8, 6, true)};
+#define OCQ_RV(NT, F, S)                                                                              \
+  {                                                                                                  \
+    NT, F, S, 2, {                                                                                   \
+      {launch_pixel_red<1, NT, F, S>, launch_pixel_red<2, NT, F, S>, launch_pixel_red<3, NT, F, S>}, \
+          {launch_pixel_red<1, NT, F, S>, launch_pixel_red<2, NT, F, S>, launch_pixel_red<3, NT, F, S>} \
+    }                                                                                                \
+  }
+#define OCQ_DV(NT, PF)                                                                                 \
+  {                                                                                                   \
+    NT, PF, 0, 3, {                                                                                   \
+      {launch_pixel_direct<1, 4, NT, PF>, launch_pixel_direct<2, 4, NT, PF>,                          \
+       launch_pixel_direct<3, 4, NT, PF>},                                                            \
+          {launch_pixel_direct<1, 8, NT, PF>, launch_pixel_direct<2, 8, NT, PF>,                      \
+           launch_pixel_direct<3, 8, NT, PF>}                                                         \
+    }                                                                                                 \
+  }
+// kind (4th field): 0 row copies, 1 2-D tensor copies, 2 byte counters bumped
+// by shared reductions, 3 direct loads (frames per stage = prefetched frames)
+static const BuildVariant kBuildVariants[] = {OCQ_RV(128, 8, 3), OCQ_RV(128, 16, 2), OCQ_BV(128, 16, 2, false),
+                                              OCQ_BV(128, 32, 2, true), OCQ_DV(64, 32)};
+#undef OCQ_DV
 #undef OCQ_BV
+#undef OCQ_RV
 static int g_build_variant = 0;
 
 int build_variant_count() { return (int)(sizeof kBuildVariants / sizeof kBuildVariants[0]); }

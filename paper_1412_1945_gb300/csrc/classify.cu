@@ -335,11 +335,10 @@ struct ClassifyVariant {
       launch_tiled<1, NW, PPT, S, FPS>, launch_tiled<2, NW, PPT, S, FPS>, launch_tiled<3, NW, PPT, S, FPS> \
     }                                                                                    \
   }
-static const ClassifyVariant kClassifyVariants[] = {
-    OCQ_CV(4, 8, 4, 4), OCQ_CV(4, 8, 12, 1), OCQ_CV(4, 8, 6, 2), OCQ_CV(2, 16, 4, 4),
-    OCQ_CV(8, 8, 4, 2), OCQ_CV(4, 16, 3, 2), OCQ_CV(8, 8, 3, 4), OCQ_CV(4, 8, 3, 6)};
+static const ClassifyVariant kClassifyVariants[] = {OCQ_CV(8, 8, 3, 4), OCQ_CV(4, 8, 4, 4), OCQ_CV(4, 8, 12, 1),
+                                                    OCQ_CV(4, 8, 6, 2), OCQ_CV(2, 16, 4, 4), OCQ_CV(8, 8, 4, 2)};
 #undef OCQ_CV
-static int g_classify_variant = 6;
+static int g_classify_variant = 0;
 
 int classify_variant_count() { return (int)(sizeof kClassifyVariants / sizeof kClassifyVariants[0]); }
 int classify_variant_selected() { return g_classify_variant; }
