@@ -162,17 +162,19 @@ ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int
  * Tuning interface (no counterpart in the paper; it selects between kernel
  * variants that compute identical results).  `kernel` names a tunable kernel:
  *   OCQ_TUNE_CLASSIFY_PIXEL  per-pixel classify, depth <= 3; params =
- *                            {warps per CTA, pixels per thread, stages, frames per stage}
+ *                            {warps per CTA, pixels per thread, stages, frames per stage,
+ *                             1 if a dedicated copy warp feeds the stages}
  *   OCQ_TUNE_BUILD_PIXEL     per-pixel build, depth <= 3; params =
  *                            {pixels (threads) per CTA, frames per stage, stages,
  *                             kind: 0 saturating counters, row copies; 1 the same with
  *                             one 2-D tensor copy per stage; 2 byte counters bumped
  *                             by shared-memory reductions; 3 saturating counters fed by
- *                             direct loads, frames per stage = frames prefetched}
+ *                             direct loads, frames per stage = frames prefetched;
+ *                             4 as 2 with a dedicated copy warp}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
- * against concurrent calls of the same kernel).  ocq_tune_describe writes 4
- * int32 parameters (n >= 4).
+ * against concurrent calls of the same kernel).  ocq_tune_describe writes 5
+ * int32 parameters (n >= 5).
  */
 enum { OCQ_TUNE_CLASSIFY_PIXEL = 0, OCQ_TUNE_BUILD_PIXEL = 1 };
 int ocq_tune_count(int kernel);

@@ -274,13 +274,13 @@ ocq_status ocq_tune_select(int kernel, int variant) {
 
 ocq_status ocq_tune_describe(int kernel, int variant, int32_t *params, int n) {
   g_err[0] = 0;
-  if (!params || n < 4 || variant < 0 || variant >= ocq_tune_count(kernel)) {
+  if (!params || n < 5 || variant < 0 || variant >= ocq_tune_count(kernel)) {
     set_error("ocq_tune_describe: bad arguments");
     return OCQ_EINVAL;
   }
-  params[0] = params[1] = params[2] = params[3] = 0;
+  params[0] = params[1] = params[2] = params[3] = params[4] = 0;
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL)
-    classify_variant_describe(variant, &params[0], &params[1], &params[2], &params[3]);
+    classify_variant_describe(variant, &params[0], &params[1], &params[2], &params[3], &params[4]);
   else
     build_variant_describe(variant, &params[0], &params[1], &params[2], &params[3]);
   return OCQ_OK;

@@ -54,6 +54,15 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Named barrier over `count` threads (a subset of the CTA).
+__device__ __forceinline__ void named_sync(uint32_t id, uint32_t count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // 2-D tiled tensor copy (TMA): box at element coordinates (x, y) of the tensor
 // described by `tmap` (a __grid_constant__ kernel parameter) -> shared `dst`.
 __device__ __forceinline__ void tensor2d_g2s(uint32_t dst, const void *tmap, int x, int y, uint32_t bar) {

@@ -821,6 +821,151 @@ static ocq_status launch_pixel_direct(const uint8_t *frames, int N, ocq_model *m
   return cuda_status(cudaGetLastError(), "build_pixel_direct_kernel");
 }
 
+// Warp-specialised form of build_pixel_red_kernel: NT counting threads plus
+// one copy warp.  The copy warp refills stage s as soon as every counting
+// warp has signalled (mbarrier "empty[s]") that it is done with it; counting
+// warps wait only on "full[s]".  No CTA-wide barrier in the steady state.
+template <int D, int NT, int FPS, int S>
+__global__ void __launch_bounds__(NT + 32) build_pixel_ws_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
+                                                                 int64_t ntiles, uint32_t T,
+                                                                 uint32_t *__restrict__ model) {
+  using C = RedBuildCfg<D, NT, FPS, S>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // [CW][NT]
+  uint8_t *stages = smem + ((C::STATE + (128 - (smem_addr(smem) + C::STATE) % 128) % 128));
+  uint64_t *full = reinterpret_cast<uint64_t *>(stages + (size_t)S * C::STAGE);
+  uint64_t *empty = full + S;
+  const int t = threadIdx.x;
+  constexpr int NCW = NT / 32;  // counting warps
+  if (t == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_addr(&full[s]), 1);
+      mbar_init(smem_addr(&empty[s]), NCW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (t < NT) {
+#pragma unroll 8
+    for (int c = 0; c < C::CW; ++c) cnt[c * NT + t] = 0;
+  }
+  __syncthreads();
+  const int G = (N + FPS - 1) / FPS;  // stages per tile
+  const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  if (t >= NT) {  // ---- copy warp ----
+    if (t != NT) return;
+    int s = 0;
+    uint32_t round = 0;  // fills of stage s so far / S ... tracked per ring turn
+    bool ok = true;
+    for (int64_t i = 0; i < my_tiles && ok; ++i) {
+      const int64_t tile = blockIdx.x + i * gridDim.x;
+      const uint8_t *base = frames + tile * NT * 3;
+      for (int g = 0; g < G; ++g) {
+        if (round > 0) {  // wait until the counting warps released this stage's previous fill
+          if (!mbar_wait_bounded(smem_addr(&empty[s]), (round - 1) & 1, kWaitLimitNs)) {
+            atomicExch(&g_build_timeout, 1u);
+            ok = false;
+            break;
+          }
+        }
+        const int f0 = g * FPS;
+        const int nf = N - f0 < FPS ? N - f0 : FPS;
+        const uint32_t bar = smem_addr(&full[s]);
+        mbar_expect_tx(bar, (uint32_t)(nf * C::ROW));
+        for (int j = 0; j < nf; ++j)
+          bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)j * C::ROW), base + (int64_t)(f0 + j) * hw * 3,
+                   C::ROW, bar);
+        if (++s == S) s = 0, ++round;
+      }
+    }
+    // let the last fills land before this CTA can retire
+    for (int k = 0; k < S; ++k) {
+      const uint32_t fills = round + (k < s ? 1u : 0u);
+      if (fills > 0) mbar_wait_bounded(smem_addr(&full[k]), (fills - 1) & 1, kWaitLimitNs);
+    }
+    return;
+  }
+
+  // ---- counting threads ----
+  const int lane = t & 31;
+  int s = 0;
+  uint32_t round = 0;
+  for (int64_t i = 0; i < my_tiles; ++i) {
+    uint32_t words = 0;  // model words (32 leaves each) this pixel touched
+    for (int g = 0; g < G; ++g) {
+      if (!mbar_wait_bounded(smem_addr(&full[s]), round & 1, kWaitLimitNs)) {
+        atomicExch(&g_build_timeout, 1u);
+        return;
+      }
+      const uint8_t *stage = stages + (size_t)s * C::STAGE + 3 * t;
+      const int nf = N - g * FPS < FPS ? N - g * FPS : FPS;
+#pragma unroll
+      for (int j = 0; j < FPS; ++j) {
+        if (j < nf) {
+          const uint8_t *px = stage + j * C::ROW;
+          const uint32_t y = (uint32_t)px[0] | ((uint32_t)px[1] << 8) | ((uint32_t)px[2] << 16);
+          const uint32_t q = planar_code<D>(y);
+          red_add_shared(&cnt[(q >> 2) * NT + t], 1u << ((q & 3u) * 8));
+          words |= 1u << (q >> 5);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
+      if (++s == S) s = 0, ++round;
+    }
+    uint32_t *dst = model + ((blockIdx.x + i * gridDim.x) * NT + t) * C::WPR;
+    if constexpr (C::WPR % 4 == 0) {
+#pragma unroll
+      for (int w = 0; w < C::WPR; w += 4) *reinterpret_cast<uint4 *>(dst + w) = make_uint4(0, 0, 0, 0);
+    } else {
+#pragma unroll
+      for (int w = 0; w < C::WPR; ++w) dst[w] = 0;
+    }
+    for (; words; words &= words - 1) {
+      const int w = __ffs(words) - 1;
+      uint32_t o = 0;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (w * 8 + c < C::CW) {
+          uint32_t *cp = &cnt[(w * 8 + c) * NT + t];
+          const uint32_t v = *cp;
+          if (v) {
+            const uint32_t ge = __vcmpgeu4(v, T * 0x01010101u);
+            o |= (((ge >> 7) & 1u) | ((ge >> 14) & 2u) | ((ge >> 21) & 4u) | ((ge >> 28) & 8u)) << (4 * c);
+            *cp = 0;
+          }
+        }
+      }
+      dst[w] = o;
+    }
+  }
+}
+
+template <int D, int NT, int FPS, int S>
+static ocq_status launch_pixel_ws(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  using C = RedBuildCfg<D, NT, FPS, S>;
+  if (N > 255) return launch_pixel_counters<D, true>(frames, N, m, st, 0);
+  const int64_t hw = (int64_t)m->H * m->W;
+  const size_t smem = C::SMEM + (size_t)S * 8;  // + the empty barriers
+  const bool fits = smem <= 227 * 1024;
+  const int64_t ntiles = fits ? hw / NT : 0;
+  if (ntiles > 0) {
+    auto kern = build_pixel_ws_kernel<D, NT, FPS, S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e, "build_pixel_ws_kernel smem");
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT + 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sm_count() * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    kern<<<(unsigned)grid, NT + 32, smem, st>>>(frames, N, hw, ntiles, (uint32_t)m->T, m->bits);
+    count_launch();
+    ocq_status rc = cuda_status(cudaGetLastError(), "build_pixel_ws_kernel");
+    if (rc != OCQ_OK) return rc;
+  }
+  return launch_pixel_counters<D, false>(frames, N, m, st, ntiles * NT);
+}
+
 template <int D, int NT, int FPS, int S>
 static ocq_status launch_pixel_red(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
   using C = RedBuildCfg<D, NT, FPS, S>;
@@ -878,8 +1023,17 @@ struct BuildVariant {
   }
 // kind (4th field): 0 row copies, 1 2-D tensor copies, 2 byte counters bumped
 // by shared reductions, 3 direct loads (frames per stage = prefetched frames)
-static const BuildVariant kBuildVariants[] = {OCQ_RV(128, 8, 3), OCQ_RV(128, 16, 2), OCQ_BV(128, 16, 2, false),
-                                              OCQ_BV(128, 32, 2, true), OCQ_DV(64, 32)};
+#define OCQ_WV(NT, F, S)                                                                              \
+  {                                                                                                  \
+    NT, F, S, 4, {                                                                                   \
+      {launch_pixel_ws<1, NT, F, S>, launch_pixel_ws<2, NT, F, S>, launch_pixel_ws<3, NT, F, S>},    \
+          {launch_pixel_ws<1, NT, F, S>, launch_pixel_ws<2, NT, F, S>, launch_pixel_ws<3, NT, F, S>} \
+    }                                                                                                \
+  }
+static const BuildVariant kBuildVariants[] = {OCQ_WV(128, 8, 3),  OCQ_WV(128, 4, 5),  OCQ_WV(128, 16, 2),
+                                              OCQ_WV(256, 4, 4),  OCQ_RV(128, 8, 3),  OCQ_RV(128, 16, 2),
+                                              OCQ_BV(128, 16, 2, false), OCQ_BV(128, 32, 2, true), OCQ_DV(64, 32)};
+#undef OCQ_WV
 #undef OCQ_DV
 #undef OCQ_BV
 #undef OCQ_RV

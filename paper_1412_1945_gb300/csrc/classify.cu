@@ -267,6 +267,129 @@ __global__ void __launch_bounds__(NW * 32, 1)
   }
 }
 
+// Warp-specialised form: NW classifying warps plus one copy warp.  The copy
+// warp streams every group of the CTA's work range, refilling a stage as soon
+// as all classifying warps have released it (mbarrier "empty"); classifying
+// warps wait only on "full".  At a tile change the classifying warps (named
+// barrier 1, the copy warp is not part of it) reload the tile's rows.  A
+// timed-out wait raises a shared abort flag; the warps then run to the end
+// without waiting, so no barrier is left short of arrivals.
+template <int D, int NW, int PPT, int S, int FPS>
+__global__ void __launch_bounds__(NW * 32 + 32, 1)
+    classify_pixel_ws_kernel(const uint8_t *__restrict__ frames, int F, int64_t hw, int64_t ntiles,
+                             const uint32_t *__restrict__ model, uint8_t *__restrict__ mask) {
+  using C = TiledCfg<D, NW, PPT, S, FPS>;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint32_t *msm = reinterpret_cast<uint32_t *>(smem);
+  uint8_t *stages = smem + (size_t)C::MODEL_WORDS * 4;
+  uint64_t *full = reinterpret_cast<uint64_t *>(stages + (size_t)S * C::STAGE);
+  uint64_t *empty = full + S;
+  __shared__ volatile int abort_flag;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_addr(&full[s]), 1);
+      mbar_init(smem_addr(&empty[s]), NW);
+    }
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t U = ntiles * (int64_t)F;
+  const int64_t u_begin = U * blockIdx.x / gridDim.x;
+  const int64_t u_end = U * (blockIdx.x + 1) / gridDim.x;
+
+  if (tid >= NW * 32) {  // ---- copy warp ----
+    if (tid != NW * 32) return;
+    int s = 0;
+    uint32_t round = 0;
+    for (int64_t u = u_begin; u < u_end && !abort_flag;) {
+      const int64_t tile = u / F;
+      const int fa = (int)(u - tile * F);
+      const int nfr = (int)((u_end - u) < (int64_t)(F - fa) ? (u_end - u) : (int64_t)(F - fa));
+      const uint8_t *base = frames + tile * C::TILE * 3;
+      for (int g = 0; g * FPS < nfr; ++g) {
+        if (round > 0 && !mbar_wait_bounded(smem_addr(&empty[s]), (round - 1) & 1, kWaitLimitNs)) {
+          atomicExch(&g_classify_timeout, 1u);
+          abort_flag = 1;
+          break;
+        }
+        const int f0 = fa + g * FPS;
+        const int nf = (nfr - g * FPS) < FPS ? (nfr - g * FPS) : FPS;
+        const uint32_t bar = smem_addr(&full[s]);
+        mbar_expect_tx(bar, (uint32_t)(nf * C::FRAME_BYTES));
+        for (int i = 0; i < nf; ++i)
+          bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)i * C::FRAME_BYTES),
+                   base + (int64_t)(f0 + i) * hw * 3, C::FRAME_BYTES, bar);
+        if (++s == S) s = 0, ++round;
+      }
+      u += nfr;
+    }
+    for (int k = 0; k < S; ++k) {  // let the last fills land before the CTA can retire
+      const uint32_t fills = round + (k < s ? 1u : 0u);
+      if (fills > 0) mbar_wait_bounded(smem_addr(&full[k]), (fills - 1) & 1, kWaitLimitNs);
+    }
+    return;
+  }
+
+  // ---- classifying warps ----
+  const int lane = tid & 31, warp = tid >> 5;
+  const uint32_t *mrow = msm + warp * PPT * C::WPR * 32 + lane;
+  int s = 0;
+  uint32_t round = 0;
+  for (int64_t u = u_begin; u < u_end;) {
+    const int64_t tile = u / F;
+    const int fa = (int)(u - tile * F);
+    const int nfr = (int)((u_end - u) < (int64_t)(F - fa) ? (u_end - u) : (int64_t)(F - fa));
+    const int64_t p_tile = tile * C::TILE;
+    named_sync(1, NW * 32);  // every warp is done with the previous tile's rows
+    {
+      const uint32_t *src = model + (p_tile + (int64_t)tid * PPT) * C::WPR;
+      if constexpr (C::WPR % 4 == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+#pragma unroll 4
+        for (int i = 0; i < PPT * C::WPR / 4; ++i) {
+          const uint4 v = __ldg(s4 + i);
+          const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int idx = i * 4 + e, j = idx / C::WPR, w = idx % C::WPR;
+            msm[((warp * PPT + j) * C::WPR + w) * 32 + lane] = vv[e];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int idx = 0; idx < PPT * C::WPR; ++idx) {
+          const int j = idx / C::WPR, w = idx % C::WPR;
+          msm[((warp * PPT + j) * C::WPR + w) * 32 + lane] = __ldg(src + idx);
+        }
+      }
+    }
+    named_sync(1, NW * 32);
+    for (int g = 0; g * FPS < nfr; ++g) {
+      const int f0 = fa + g * FPS;
+      const int nf = (nfr - g * FPS) < FPS ? (nfr - g * FPS) : FPS;
+      if (!abort_flag) {
+        if (mbar_wait_bounded(smem_addr(&full[s]), round & 1, kWaitLimitNs)) {
+          const uint8_t *stage = stages + (size_t)s * C::STAGE;
+#pragma unroll
+          for (int i = 0; i < FPS; ++i)
+            if (i < nf)
+              classify_tile_frame<D, NW, PPT, S, FPS>(stage + (size_t)i * C::FRAME_BYTES, mrow,
+                                                      mask + (int64_t)(f0 + i) * hw + p_tile);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
+        } else {
+          atomicExch(&g_classify_timeout, 1u);
+          abort_flag = 1;
+        }
+      }
+      if (++s == S) s = 0, ++round;
+    }
+    u += nfr;
+  }
+}
+
 // ---- host dispatch -----------------------------------------------------------------------
 
 static unsigned grid_cap(int64_t work, int threads, int per_sm) {
@@ -323,22 +446,57 @@ static ocq_status launch_tiled(const ocq_model *m, const uint8_t *frames, int F,
   return rc;
 }
 
+template <int D, int NW, int PPT, int S, int FPS>
+static ocq_status launch_tiled_ws(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st) {
+  using C = TiledCfg<D, NW, PPT, S, FPS>;
+  const int64_t hw = (int64_t)m->H * m->W;
+  const size_t smem = C::SMEM + (size_t)S * 8;
+  const int64_t ntiles = smem <= 227 * 1024 ? hw / C::TILE : 0;
+  ocq_status rc = OCQ_OK;
+  if (ntiles > 0) {
+    auto kern = classify_pixel_ws_kernel<D, NW, PPT, S, FPS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e, "classify_pixel_ws_kernel smem");
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS + 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sm_count() * per_sm;
+    const int64_t U = ntiles * F;
+    if (grid > U) grid = U;
+    kern<<<(unsigned)grid, C::THREADS + 32, smem, st>>>(frames, F, hw, ntiles, m->bits, mask);
+    count_launch();
+    rc = cuda_status(cudaGetLastError(), "classify_pixel_ws_kernel");
+  }
+  if (rc == OCQ_OK) rc = launch_generic(m, frames, F, mask, ntiles * C::TILE, hw, st);
+  return rc;
+}
+
 // ---- tunable variants of the per-pixel tiled kernel ---------------------------------
 using ClassifyFn = ocq_status (*)(const ocq_model *, const uint8_t *, int, uint8_t *, cudaStream_t);
 struct ClassifyVariant {
-  int nw, ppt, stages, fps;
+  int nw, ppt, stages, fps, ws;
   ClassifyFn fn[3];  // depth 1, 2, 3
 };
 #define OCQ_CV(NW, PPT, S, FPS)                                                          \
   {                                                                                      \
-    NW, PPT, S, FPS, {                                                                   \
+    NW, PPT, S, FPS, 0, {                                                                \
       launch_tiled<1, NW, PPT, S, FPS>, launch_tiled<2, NW, PPT, S, FPS>, launch_tiled<3, NW, PPT, S, FPS> \
     }                                                                                    \
   }
-static const ClassifyVariant kClassifyVariants[] = {OCQ_CV(8, 8, 3, 4), OCQ_CV(4, 8, 4, 4), OCQ_CV(4, 8, 12, 1),
-                                                    OCQ_CV(4, 8, 6, 2), OCQ_CV(2, 16, 4, 4), OCQ_CV(8, 8, 4, 2)};
+#define OCQ_WV(NW, PPT, S, FPS)                                                          \
+  {                                                                                      \
+    NW, PPT, S, FPS, 1, {                                                                \
+      launch_tiled_ws<1, NW, PPT, S, FPS>, launch_tiled_ws<2, NW, PPT, S, FPS>,           \
+          launch_tiled_ws<3, NW, PPT, S, FPS>                                            \
+    }                                                                                    \
+  }
+// ws (5th field): 1 = a dedicated copy warp with full/empty mbarriers
+static const ClassifyVariant kClassifyVariants[] = {
+    OCQ_CV(8, 8, 3, 4), OCQ_CV(4, 8, 4, 4), OCQ_CV(4, 8, 12, 1), OCQ_CV(8, 8, 4, 2),
+    OCQ_WV(8, 8, 3, 4), OCQ_WV(4, 8, 4, 4), OCQ_WV(8, 8, 6, 2), OCQ_WV(4, 8, 8, 2), OCQ_WV(4, 8, 3, 5)};
 #undef OCQ_CV
-static int g_classify_variant = 0;
+#undef OCQ_WV
+static int g_classify_variant = 5;
 
 int classify_variant_count() { return (int)(sizeof kClassifyVariants / sizeof kClassifyVariants[0]); }
 int classify_variant_selected() { return g_classify_variant; }
@@ -347,9 +505,10 @@ bool classify_variant_select(int v) {
   g_classify_variant = v;
   return true;
 }
-void classify_variant_describe(int v, int *nw, int *ppt, int *stages, int *fps) {
+void classify_variant_describe(int v, int *nw, int *ppt, int *stages, int *fps, int *ws) {
   *nw = kClassifyVariants[v].nw, *ppt = kClassifyVariants[v].ppt;
   *stages = kClassifyVariants[v].stages, *fps = kClassifyVariants[v].fps;
+  *ws = kClassifyVariants[v].ws;
 }
 
 ocq_status launch_classify(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st) {

@@ -158,7 +158,7 @@ bool build_take_timeout();
 int classify_variant_count();
 int classify_variant_selected();
 bool classify_variant_select(int v);
-void classify_variant_describe(int v, int *nw, int *ppt, int *stages, int *fps);
+void classify_variant_describe(int v, int *nw, int *ppt, int *stages, int *fps, int *ws);
 int build_variant_count();
 int build_variant_selected();
 bool build_variant_select(int v);

@@ -248,6 +248,6 @@ def ocq_tune_select(kernel: int, variant: int):
 
 
 def ocq_tune_describe(kernel: int, variant: int):
-    buf = (ctypes.c_int32 * 4)()
-    _check(load().ocq_tune_describe(kernel, variant, buf, 4))
+    buf = (ctypes.c_int32 * 5)()
+    _check(load().ocq_tune_describe(kernel, variant, buf, 5))
     return list(buf)
