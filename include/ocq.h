@@ -182,6 +182,27 @@ int ocq_tune_selected(int kernel);
 ocq_status ocq_tune_select(int kernel, int variant);
 ocq_status ocq_tune_describe(int kernel, int variant, int32_t *params, int n);
 
+/*
+ * Whole-frame build (as ocq_build_model with OCQ_REGION_FRAME) that allocates
+ * no memory.  The paper has no counterpart; it serves callers that cannot
+ * allocate device memory at call time -- pipelines that reserve every buffer
+ * at start-up and must not block on the allocator, or hosts that give the
+ * library a fixed memory budget.
+ *   frames: device, N*H*W*3 bytes.  model: device, max(1, 8^depth/64) u64
+ *   words, written in the exported layout (path code c at bit c%64 of word
+ *   c/64) -- the row ocq_model_export writes for a whole-frame model.
+ * Scratch is one static 16 MiB device array inside the library, present on
+ * every GPU that loads it until the process exits; requests needing more
+ * (depth d and N with (bit_length(N) + 2) * max(1, 8^d/32) * 4 bytes above
+ * 16 MiB) return OCQ_EINVAL with a message.  It calls no cudaMalloc/cudaFree.
+ * The first call on a device resolves the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the array and clears what it needs: calls whose work may
+ * overlap on the GPU race and must be ordered by the caller.
+ */
+ocq_status ocq_build_frame_noalloc(const uint8_t *frames, int N, int H, int W, int depth, int T, uint64_t *model,
+                                   void *stream);
+
 /* Number of kernels this library has launched in this process (all devices).
  * Lets a caller count the device work a call sequence issued. */
 uint64_t ocq_kernel_launches(void);

@@ -19,6 +19,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "async_copy.cuh"
 #include "pixels.cuh"
@@ -1093,4 +1094,104 @@ ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t
   }
 }
 
+// ---- whole-frame build that allocates nothing ------------------------------------
+//
+// ocq_build_model allocates the model and its scratch with cudaMallocAsync.
+// Some callers cannot allocate device memory at call time: camera pipelines
+// that reserve all memory at start-up and must never block on the allocator,
+// or hosts that hand the library a fixed budget and forbid allocation on the
+// processing path.  For them ocq_build_frame_noalloc builds a whole-frame
+// model into a buffer the caller owns, using as scratch one statically sized
+// device array of this file (kNoAllocScratchBytes on every GPU that loads the
+// library, held until the process exits).  All calls share the array, so calls
+// whose work overlaps on the GPU (different streams, or devices racing on the
+// same setup) must be ordered by the caller; each call clears what it needs.
+
+static constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocScratchBytes / 4];
+
+static std::mutex g_noalloc_mu;
+static uint32_t *g_noalloc_ptr[256];  // device address of the array, per device ordinal
+
+// Device address of the scratch array on the current device.  The host-side
+// symbol g_noalloc_scratch is not a device address, so it is resolved once per
+// device (with that device current) and cached.
+static ocq_status noalloc_scratch(uint32_t **out) {
+  int dev = 0;
+  ocq_status rc = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc != OCQ_OK) return rc;
+  if (dev < 0 || dev >= 256) {
+    set_error("device ordinal %d out of range", dev);
+    return OCQ_ENOTSUP;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    rc = cuda_status(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(no-alloc scratch)");
+    if (rc != OCQ_OK) return rc;
+    g_noalloc_ptr[dev] = static_cast<uint32_t *>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return OCQ_OK;
+}
+
 }  // namespace ocq
+
+using namespace ocq;
+
+extern "C" ocq_status ocq_build_frame_noalloc(const uint8_t *frames, int N, int H, int W, int depth, int T,
+                                              uint64_t *model, void *stream) {
+  if (!frames || !model || H < 1 || W < 1 || depth < 1 || depth > 8 || N < 1 || N > 65535 || T < 1 || T > N ||
+      (int64_t)N * H * W >= ((int64_t)1 << 40)) {
+    set_error("ocq_build_frame_noalloc: need frames, model != NULL, H, W >= 1, 1 <= depth <= 8, "
+              "1 <= T <= N <= 65535 (N=%d, T=%d, depth=%d)", N, T, depth);
+    return OCQ_EINVAL;
+  }
+  const int64_t wpr = wpr32(depth);
+  const int P = bit_length((uint32_t)N);
+  const int64_t cap = (int64_t)(kNoAllocScratchBytes / 4);
+  // scratch rows: the merged row, P counter planes, at least one frame's leaf set
+  if ((int64_t)(P + 2) * wpr > cap) {
+    set_error("ocq_build_frame_noalloc: depth %d with N = %d needs %lld bytes of scratch; the maximum is %zu bytes",
+              depth, N, (long long)((int64_t)(P + 2) * wpr * 4), kNoAllocScratchBytes);
+    return OCQ_EINVAL;
+  }
+  uint32_t *scratch = nullptr;
+  ocq_status rc = noalloc_scratch(&scratch);
+  if (rc != OCQ_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t *row = scratch;                  // [wpr] merged row (internal order)
+  uint32_t *planes = scratch + wpr;         // [P][wpr]
+  uint32_t *occ = planes + (int64_t)P * wpr; // [nb][wpr]
+  int64_t nb64 = cap / wpr - P - 1;
+  const int nb = (int)(nb64 < N ? nb64 : N);
+  const int64_t hw = (int64_t)H * W;
+  for (int f0 = 0; f0 < N && rc == OCQ_OK; f0 += nb) {
+    const int nf = N - f0 < nb ? N - f0 : nb;
+    rc = cuda_status(cudaMemsetAsync(occ, 0, (size_t)nf * wpr * 4, st), "clear occupancy");
+    if (rc != OCQ_OK) break;
+    if (depth <= 6) {
+      switch (depth) {
+        case 1: launch_occ_frame<1>(frames, hw, f0, nf, occ, st); break;
+        case 2: launch_occ_frame<2>(frames, hw, f0, nf, occ, st); break;
+        case 3: launch_occ_frame<3>(frames, hw, f0, nf, occ, st); break;
+        case 4: launch_occ_frame<4>(frames, hw, f0, nf, occ, st); break;
+        case 5: launch_occ_frame<5>(frames, hw, f0, nf, occ, st); break;
+        default: launch_occ_frame<6>(frames, hw, f0, nf, occ, st); break;
+      }
+    } else {
+      occ_global_kernel<<<grid_cap(hw * nf, 256, 16), 256, 0, st>>>(frames, H, W, OCQ_REGION_FRAME, 0, depth, f0, nf, 1,
+                                                                     wpr, occ);
+      count_launch();
+    }
+    rc = cuda_status(cudaGetLastError(), "occupancy kernel");
+    if (rc != OCQ_OK) break;
+    planes_merge_kernel<<<grid_cap(wpr, 256, 8), 256, 0, st>>>(occ, nf, wpr, planes, P, f0 == 0, f0 + nf >= N,
+                                                                (uint32_t)T, row);
+    count_launch();
+    rc = cuda_status(cudaGetLastError(), "planes_merge_kernel");
+  }
+  if (rc == OCQ_OK) rc = launch_export(row, 1, depth, model, st);
+  return rc;
+}
+

@@ -64,6 +64,7 @@ SIGNATURES = {
     "ocq_detect_host": (_i32, [_vp, _i32, _vp, _i32, _i32, _i32, ocq_region, _i32, _i32, _vp, _vp,
                                ctypes.POINTER(_vp)]),
     "ocq_kernel_launches": (ctypes.c_uint64, []),
+    "ocq_build_frame_noalloc": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp]),
     "ocq_tune_count": (_i32, [_i32]),
     "ocq_tune_selected": (_i32, [_i32]),
     "ocq_tune_select": (_i32, [_i32, _i32]),
@@ -251,3 +252,9 @@ def ocq_tune_describe(kernel: int, variant: int):
     buf = (ctypes.c_int32 * 5)()
     _check(load().ocq_tune_describe(kernel, variant, buf, 5))
     return list(buf)
+
+
+def ocq_build_frame_noalloc(frames, N, H, W, depth, T, model, stream=None):
+    """Whole-frame model into the caller's device buffer ``model``
+    (max(1, 8^depth/64) u64 words, exported layout); allocates nothing."""
+    _check(load().ocq_build_frame_noalloc(_p(frames), N, H, W, depth, T, _p(model), _s(stream)))
