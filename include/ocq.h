@@ -170,7 +170,9 @@ ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int
  *                             one 2-D tensor copy per stage; 2 byte counters bumped
  *                             by shared-memory reductions; 3 saturating counters fed by
  *                             direct loads, frames per stage = frames prefetched;
- *                             4 as 2 with a dedicated copy warp}
+ *                             4 as 2 with a dedicated copy warp; 5 as 4 with one 2-D
+ *                             tensor copy per stage; 6 as 4 setting kept bits as
+ *                             counts reach T; 7 as 5 and 6 together}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5

@@ -826,14 +826,33 @@ static ocq_status launch_pixel_direct(const uint8_t *frames, int N, ocq_model *m
 // one copy warp.  The copy warp refills stage s as soon as every counting
 // warp has signalled (mbarrier "empty[s]") that it is done with it; counting
 // warps wait only on "full[s]".  No CTA-wide barrier in the steady state.
-template <int D, int NT, int FPS, int S>
+// TENSOR: a stage is one 2-D tensor copy (FPS frame rows x NT*3 bytes)
+// instead of FPS row copies.  KEPT: the counters are bumped with an atomic
+// add that returns the old count, and the leaf's bit is set in the thread's
+// "kept" row (registers) the moment its count reaches T; the end of a tile
+// then only writes the kept row out and zeroes the touched counters (no
+// threshold pass).
+template <int D, int NT, int FPS, int S, bool KEPT>
+struct WsBuildCfg {
+  static constexpr int NC = 1 << (3 * D);
+  static constexpr int CW = (NC + 3) / 4;  // u8 counter words per pixel
+  static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  static constexpr int ROW = NT * 3;
+  static constexpr int STAGE = ROW * FPS;
+  static constexpr size_t STATE = (size_t)CW * NT * 4;
+  static constexpr size_t SMEM = STATE + (size_t)S * STAGE + (size_t)S * 16;
+  static_assert(ROW % 128 == 0 && STATE % 128 == 0, "stages stay 128-byte aligned");
+};
+
+template <int D, int NT, int FPS, int S, bool TENSOR, bool KEPT>
 __global__ void __launch_bounds__(NT + 32) build_pixel_ws_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
                                                                  int64_t ntiles, uint32_t T,
-                                                                 uint32_t *__restrict__ model) {
-  using C = RedBuildCfg<D, NT, FPS, S>;
-  extern __shared__ __align__(128) uint8_t smem[];
+                                                                 uint32_t *__restrict__ model,
+                                                                 const __grid_constant__ CUtensorMap tmap) {
+  using C = WsBuildCfg<D, NT, FPS, S, KEPT>;
+  extern __shared__ __align__(1024) uint8_t smem[];
   uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // [CW][NT]
-  uint8_t *stages = smem + ((C::STATE + (128 - (smem_addr(smem) + C::STATE) % 128) % 128));
+  uint8_t *stages = smem + C::STATE;
   uint64_t *full = reinterpret_cast<uint64_t *>(stages + (size_t)S * C::STAGE);
   uint64_t *empty = full + S;
   const int t = threadIdx.x;
@@ -856,7 +875,7 @@ __global__ void __launch_bounds__(NT + 32) build_pixel_ws_kernel(const uint8_t *
   if (t >= NT) {  // ---- copy warp ----
     if (t != NT) return;
     int s = 0;
-    uint32_t round = 0;  // fills of stage s so far / S ... tracked per ring turn
+    uint32_t round = 0;
     bool ok = true;
     for (int64_t i = 0; i < my_tiles && ok; ++i) {
       const int64_t tile = blockIdx.x + i * gridDim.x;
@@ -870,12 +889,18 @@ __global__ void __launch_bounds__(NT + 32) build_pixel_ws_kernel(const uint8_t *
           }
         }
         const int f0 = g * FPS;
-        const int nf = N - f0 < FPS ? N - f0 : FPS;
         const uint32_t bar = smem_addr(&full[s]);
-        mbar_expect_tx(bar, (uint32_t)(nf * C::ROW));
-        for (int j = 0; j < nf; ++j)
-          bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)j * C::ROW), base + (int64_t)(f0 + j) * hw * 3,
-                   C::ROW, bar);
+        if constexpr (TENSOR) {
+          // rows past frame N-1 are filled with zeros and still count as bytes
+          mbar_expect_tx(bar, (uint32_t)C::STAGE);
+          tensor2d_g2s(smem_addr(stages + (size_t)s * C::STAGE), &tmap, (int)(tile * (C::ROW / 4)), f0, bar);
+        } else {
+          const int nf = N - f0 < FPS ? N - f0 : FPS;
+          mbar_expect_tx(bar, (uint32_t)(nf * C::ROW));
+          for (int j = 0; j < nf; ++j)
+            bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)j * C::ROW),
+                     base + (int64_t)(f0 + j) * hw * 3, C::ROW, bar);
+        }
         if (++s == S) s = 0, ++round;
       }
     }
@@ -893,6 +918,9 @@ __global__ void __launch_bounds__(NT + 32) build_pixel_ws_kernel(const uint8_t *
   uint32_t round = 0;
   for (int64_t i = 0; i < my_tiles; ++i) {
     uint32_t words = 0;  // model words (32 leaves each) this pixel touched
+    uint32_t kept[C::WPR];
+#pragma unroll
+    for (int w = 0; w < C::WPR; ++w) kept[w] = 0;
     for (int g = 0; g < G; ++g) {
       if (!mbar_wait_bounded(smem_addr(&full[s]), round & 1, kWaitLimitNs)) {
         atomicExch(&g_build_timeout, 1u);
@@ -906,7 +934,17 @@ __global__ void __launch_bounds__(NT + 32) build_pixel_ws_kernel(const uint8_t *
           const uint8_t *px = stage + j * C::ROW;
           const uint32_t y = (uint32_t)px[0] | ((uint32_t)px[1] << 8) | ((uint32_t)px[2] << 16);
           const uint32_t q = planar_code<D>(y);
-          red_add_shared(&cnt[(q >> 2) * NT + t], 1u << ((q & 3u) * 8));
+          const uint32_t sh = (q & 3u) * 8;
+          if constexpr (KEPT) {
+            const uint32_t old = atomicAdd(&cnt[(q >> 2) * NT + t], 1u << sh);
+            if (((old >> sh) & 0xFFu) + 1u == T) {  // once per kept leaf and tile
+#pragma unroll
+              for (int w = 0; w < C::WPR; ++w)
+                if ((int)(q >> 5) == w) kept[w] |= 1u << (q & 31);
+            }
+          } else {
+            red_add_shared(&cnt[(q >> 2) * NT + t], 1u << sh);
+          }
           words |= 1u << (q >> 5);
         }
       }
@@ -915,51 +953,73 @@ __global__ void __launch_bounds__(NT + 32) build_pixel_ws_kernel(const uint8_t *
       if (++s == S) s = 0, ++round;
     }
     uint32_t *dst = model + ((blockIdx.x + i * gridDim.x) * NT + t) * C::WPR;
-    if constexpr (C::WPR % 4 == 0) {
+    if constexpr (KEPT) {
+      if constexpr (C::WPR % 4 == 0) {
 #pragma unroll
-      for (int w = 0; w < C::WPR; w += 4) *reinterpret_cast<uint4 *>(dst + w) = make_uint4(0, 0, 0, 0);
+        for (int w = 0; w < C::WPR; w += 4)
+          *reinterpret_cast<uint4 *>(dst + w) = make_uint4(kept[w], kept[w + 1], kept[w + 2], kept[w + 3]);
+      } else {
+#pragma unroll
+        for (int w = 0; w < C::WPR; ++w) dst[w] = kept[w];
+      }
+      for (; words; words &= words - 1) {  // zero the counters this tile used
+        const int w = __ffs(words) - 1;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (w * 8 + c < C::CW) cnt[(w * 8 + c) * NT + t] = 0;
+      }
     } else {
+      if constexpr (C::WPR % 4 == 0) {
 #pragma unroll
-      for (int w = 0; w < C::WPR; ++w) dst[w] = 0;
-    }
-    for (; words; words &= words - 1) {
-      const int w = __ffs(words) - 1;
-      uint32_t o = 0;
+        for (int w = 0; w < C::WPR; w += 4) *reinterpret_cast<uint4 *>(dst + w) = make_uint4(0, 0, 0, 0);
+      } else {
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if (w * 8 + c < C::CW) {
-          uint32_t *cp = &cnt[(w * 8 + c) * NT + t];
-          const uint32_t v = *cp;
-          if (v) {
-            const uint32_t ge = __vcmpgeu4(v, T * 0x01010101u);
-            o |= (((ge >> 7) & 1u) | ((ge >> 14) & 2u) | ((ge >> 21) & 4u) | ((ge >> 28) & 8u)) << (4 * c);
-            *cp = 0;
+        for (int w = 0; w < C::WPR; ++w) dst[w] = 0;
+      }
+      for (; words; words &= words - 1) {
+        const int w = __ffs(words) - 1;
+        uint32_t o = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (w * 8 + c < C::CW) {
+            uint32_t *cp = &cnt[(w * 8 + c) * NT + t];
+            const uint32_t v = *cp;
+            if (v) {
+              const uint32_t ge = __vcmpgeu4(v, T * 0x01010101u);
+              o |= (((ge >> 7) & 1u) | ((ge >> 14) & 2u) | ((ge >> 21) & 4u) | ((ge >> 28) & 8u)) << (4 * c);
+              *cp = 0;
+            }
           }
         }
+        dst[w] = o;
       }
-      dst[w] = o;
     }
   }
 }
 
-template <int D, int NT, int FPS, int S>
+template <int D, int NT, int FPS, int S, bool TENSOR, bool KEPT>
 static ocq_status launch_pixel_ws(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
-  using C = RedBuildCfg<D, NT, FPS, S>;
+  using C = WsBuildCfg<D, NT, FPS, S, KEPT>;
   if (N > 255) return launch_pixel_counters<D, true>(frames, N, m, st, 0);
   const int64_t hw = (int64_t)m->H * m->W;
-  const size_t smem = C::SMEM + (size_t)S * 8;  // + the empty barriers
-  const bool fits = smem <= 227 * 1024;
+  constexpr bool fits = C::SMEM <= 227 * 1024 && (!TENSOR || (NT * 3 / 4 <= 256 && FPS <= 256));
   const int64_t ntiles = fits ? hw / NT : 0;
+  CUtensorMap map;
+  memset(&map, 0, sizeof map);
+  if (TENSOR && ntiles > 0 && !encode_frames_map(&map, frames, N, hw, NT, FPS)) {
+    set_error("cuTensorMapEncodeTiled failed for the training frames");
+    return OCQ_ECUDA;
+  }
   if (ntiles > 0) {
-    auto kern = build_pixel_ws_kernel<D, NT, FPS, S>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = build_pixel_ws_kernel<D, NT, FPS, S, TENSOR, KEPT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess) return cuda_status(e, "build_pixel_ws_kernel smem");
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT + 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT + 32, C::SMEM);
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)sm_count() * per_sm;
     if (grid > ntiles) grid = ntiles;
-    kern<<<(unsigned)grid, NT + 32, smem, st>>>(frames, N, hw, ntiles, (uint32_t)m->T, m->bits);
+    kern<<<(unsigned)grid, NT + 32, C::SMEM, st>>>(frames, N, hw, ntiles, (uint32_t)m->T, m->bits, map);
     count_launch();
     ocq_status rc = cuda_status(cudaGetLastError(), "build_pixel_ws_kernel");
     if (rc != OCQ_OK) return rc;
@@ -1024,16 +1084,20 @@ struct BuildVariant {
   }
 // kind (4th field): 0 row copies, 1 2-D tensor copies, 2 byte counters bumped
 // by shared reductions, 3 direct loads (frames per stage = prefetched frames)
-#define OCQ_WV(NT, F, S)                                                                              \
+#define OCQ_WV(NT, F, S, KIND, TS, KP)                                                                \
   {                                                                                                  \
-    NT, F, S, 4, {                                                                                   \
-      {launch_pixel_ws<1, NT, F, S>, launch_pixel_ws<2, NT, F, S>, launch_pixel_ws<3, NT, F, S>},    \
-          {launch_pixel_ws<1, NT, F, S>, launch_pixel_ws<2, NT, F, S>, launch_pixel_ws<3, NT, F, S>} \
+    NT, F, S, KIND, {                                                                                \
+      {launch_pixel_ws<1, NT, F, S, TS, KP>, launch_pixel_ws<2, NT, F, S, TS, KP>,                   \
+       launch_pixel_ws<3, NT, F, S, TS, KP>},                                                        \
+          {launch_pixel_ws<1, NT, F, S, TS, KP>, launch_pixel_ws<2, NT, F, S, TS, KP>,               \
+           launch_pixel_ws<3, NT, F, S, TS, KP>}                                                     \
     }                                                                                                \
   }
-static const BuildVariant kBuildVariants[] = {OCQ_WV(128, 8, 3),  OCQ_WV(128, 4, 5),  OCQ_WV(128, 16, 2),
-                                              OCQ_WV(256, 4, 4),  OCQ_RV(128, 8, 3),  OCQ_RV(128, 16, 2),
-                                              OCQ_BV(128, 16, 2, false), OCQ_BV(128, 32, 2, true), OCQ_DV(64, 32)};
+// kind 4: copy warp + row copies; 5: copy warp + one tensor copy per stage;
+// 6: as 4 with kept bits set as counts reach T; 7: as 5 with kept bits
+static const BuildVariant kBuildVariants[] = {
+    OCQ_WV(128, 8, 3, 5, true, false),  OCQ_WV(128, 8, 3, 4, false, false), OCQ_WV(128, 4, 5, 5, true, false),
+    OCQ_WV(128, 8, 3, 7, true, true),   OCQ_RV(128, 8, 3),                   OCQ_BV(128, 16, 2, false)};
 #undef OCQ_WV
 #undef OCQ_DV
 #undef OCQ_BV
