@@ -178,18 +178,27 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("classify.cu", "build.cu", "pixels.cuh", "ocq_internal.cuh", "async_copy.cuh")
+KERNEL_SOURCES = {
+    "classify": ("classify.cu", "pixels.cuh", "ocq_internal.cuh", "async_copy.cuh"),
+    "build": ("build.cu", "pixels.cuh", "ocq_internal.cuh", "async_copy.cuh"),
+}
 
 
-def kernel_source_hash():
-    """Hash of the sources of the measured kernels (ties a committed ncu figure
+def kernel_source_hash(which: str = "classify"):
+    """Hash of the sources of a measured kernel (ties a committed ncu figure
     to the code it was taken on)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1412_1945_gb300", "csrc")
-    for name in KERNEL_SOURCES:
+    for name in KERNEL_SOURCES[which]:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def classify_kernel_name(O) -> str:
+    """Name of the per-pixel classify kernel the library currently selects."""
+    params = O.ocq_tune_describe(O.OCQ_TUNE_CLASSIFY_PIXEL, O.ocq_tune_selected(O.OCQ_TUNE_CLASSIFY_PIXEL))
+    return "classify_pixel_ws_kernel" if params[4] else "classify_pixel_tiled_kernel"
 
 
 def profiled_traffic(kernel: str, workload: str):
@@ -199,7 +208,7 @@ def profiled_traffic(kernel: str, workload: str):
     p = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(p):
         return None
-    want = kernel_source_hash()
+    want = kernel_source_hash("classify" if kernel.startswith("classify") else "build")
     for line in open(p):
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
         if len(cells) >= 4 and cells[0] == kernel and cells[1] == workload and cells[2] == want:
@@ -326,6 +335,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (classify: tiled per-pixel kernel, one launch)
     model_bytes = ocq.ocq.ocq_model_footprint(H, W, wl.region, wl.block, wl.depth)
+    kname = classify_kernel_name(ocq.ocq)
     cls_bytes = F * hw * 4 + model_bytes
     peak, peak_kind = measured_peaks()
     achieved = cls_bytes / (cls_ms / 1e3) / 1e9
@@ -336,10 +346,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(max_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": config_dict(wl, world),
-        "roofline": {"bound": "hbm", "kernel": "classify_pixel_tiled_kernel", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": profiled_traffic("classify_pixel_tiled_kernel", wl.name),
-                     "source_hash": kernel_source_hash(),
+                     "traffic": profiled_traffic(kname, wl.name),
+                     "source_hash": kernel_source_hash("classify"),
                      "algorithmic_bytes_per_launch": cls_bytes, "peak_source": peak_kind},
         "build": {"ms": round(build_ms, 4), "mpixel_s": round(N * hw / (build_ms / 1e3) / 1e6, 1),
                   "gbs": round(build_bytes / (build_ms / 1e3) / 1e9, 1),
