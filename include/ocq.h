@@ -159,6 +159,48 @@ ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int
                            int depth, int T, uint8_t *mask, void *stream, ocq_model **out_model);
 
 /*
+ * Batched form (no counterpart in the paper, which handles one video): many
+ * camera streams, each with its own frame size, region kind and depth, are
+ * built (S1-S3) and classified (S4) by ONE persistent kernel launch that is
+ * captured once in a CUDA graph and replayed.  Results are identical to
+ * ocq_build_model + ocq_classify per stream.
+ *   train: device, N*H*W*3; test: device, F*H*W*3; mask: device, F*H*W.
+ * Domain per stream: 1 <= T <= N <= 255; depth <= 5 for block and pixel
+ * regions (<= 8 for whole-frame); the buffers stay owned by the caller and
+ * must stay valid while the batch exists (their addresses are baked in).
+ */
+typedef struct {
+  const uint8_t *train;
+  int N, H, W;
+  ocq_region region;
+  int depth, T;
+  const uint8_t *test;
+  int F;
+  uint8_t *mask;
+} ocq_stream_desc;
+
+typedef struct ocq_batch ocq_batch;
+
+/* Plans the work list, allocates the models (one arena) and scratch.  The
+ * first ocq_batch_run captures the graph. */
+ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream, ocq_batch **out);
+/* Builds every stream's model and classifies every test frame (graph replay). */
+ocq_status ocq_batch_run(ocq_batch *batch, void *stream);
+/* Synchronises `stream`; OCQ_ETIMEOUT if an item gave up waiting for its model. */
+ocq_status ocq_batch_status(ocq_batch *batch, void *stream);
+/* Model of stream i: a view owned by the batch (never pass it to ocq_model_free). */
+ocq_status ocq_batch_model(const ocq_batch *batch, int i, const ocq_model **out);
+/* Tile shape of classification items for a region kind: pixels per item
+ * (multiple of 32) and frames per item; re-plans the work list. */
+ocq_status ocq_batch_set_tiles(ocq_batch *batch, int region_kind, int pixels, int frames);
+ocq_status ocq_batch_get_tiles(const ocq_batch *batch, int region_kind, int *pixels, int *frames, int64_t *items);
+/* Autotuner: times candidate tile shapes per region kind on this batch's own
+ * inputs (`reps` runs each, on `stream`) and keeps the fastest; results are
+ * cached per (region kind, depths, sizes) signature for the process. */
+ocq_status ocq_batch_autotune(ocq_batch *batch, int reps, void *stream);
+void ocq_batch_destroy(ocq_batch *batch);
+
+/*
  * Tuning interface (no counterpart in the paper; it selects between kernel
  * variants that compute identical results).  `kernel` names a tunable kernel:
  *   OCQ_TUNE_CLASSIFY_PIXEL  per-pixel classify, depth <= 3; params =

@@ -129,15 +129,23 @@ __global__ void planes_merge_kernel(const uint32_t *__restrict__ occ, int nb, in
 }
 
 // ---- block regions, depth <= 5 -----------------------------------------------
+// One CTA per block region.  Per training frame the block's leaves are marked
+// in a shared bitset; the first thread to set a bit in an empty word appends
+// the word to a list, so only listed words are folded into the bit-sliced
+// counters and cleared (a block has at most b*b leaves per frame, far fewer
+// than 8^d/32 words at depth 4-5).
 template <int D>
 __global__ void __launch_bounds__(256) build_block_kernel(const uint8_t *__restrict__ frames, int N, int H, int W,
                                                           int b, int bw, int P, uint32_t T,
                                                           uint32_t *__restrict__ model) {
   constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
   extern __shared__ uint32_t sm[];
-  uint32_t *seen = sm;         // [WPR]
-  uint32_t *planes = sm + WPR; // [P][WPR]
+  uint32_t *seen = sm;                   // [WPR]
+  uint32_t *planes = sm + WPR;           // [P][WPR]
+  uint32_t *list = planes + P * WPR;     // [WPR] words set in the current frame
+  __shared__ uint32_t nlist;
   for (int i = threadIdx.x; i < WPR * (P + 1); i += blockDim.x) sm[i] = 0;
+  if (threadIdx.x == 0) nlist = 0;
   const int64_t r = blockIdx.x;
   const int y0 = (int)(r / bw) * b, x0 = (int)(r % bw) * b;
   const int h = min(b, H - y0), w = min(b, W - x0);
@@ -151,20 +159,25 @@ __global__ void __launch_bounds__(256) build_block_kernel(const uint8_t *__restr
       const uint8_t *px = fr + ((int64_t)y * W + x) * 3;
       const uint32_t q = planar_code_rt(__ldg(px), __ldg(px + 1), __ldg(px + 2), D);
       const uint32_t m = 1u << (q & 31);
-      if (!(seen[q >> 5] & m)) atomicOr(&seen[q >> 5], m);
-    }
-    __syncthreads();
-    for (int wd = threadIdx.x; wd < WPR; wd += blockDim.x) {
-      uint32_t x = seen[wd];
-      if (x) {
-        for (int k = 0; k < P && x; ++k) {
-          const uint32_t t = planes[k * WPR + wd] & x;
-          planes[k * WPR + wd] ^= x;
-          x = t;
-        }
-        seen[wd] = 0;
+      if (!(seen[q >> 5] & m)) {
+        const uint32_t old = atomicOr(&seen[q >> 5], m);
+        if (old == 0) list[atomicAdd(&nlist, 1u)] = q >> 5;
       }
     }
+    __syncthreads();
+    const uint32_t n = nlist;
+    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
+      const uint32_t wd = list[k];
+      uint32_t x = seen[wd];
+      for (int j = 0; j < P && x; ++j) {
+        const uint32_t t = planes[j * WPR + wd] & x;
+        planes[j * WPR + wd] ^= x;
+        x = t;
+      }
+      seen[wd] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) nlist = 0;
     __syncthreads();
   }
   for (int wd = threadIdx.x; wd < WPR; wd += blockDim.x) {
@@ -694,11 +707,12 @@ template <int D>
 static ocq_status launch_block(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
   constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
   const int P = bit_length((uint32_t)N);
-  const size_t smem = (size_t)WPR * (P + 1) * 4;
+  const size_t smem = (size_t)WPR * (P + 2) * 4;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(build_block_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int bw = (m->W + m->block - 1) / m->block;
-  build_block_kernel<D><<<(unsigned)m->R, 256, smem, st>>>(frames, N, m->H, m->W, m->block, bw, P, (uint32_t)m->T,
+  const int threads = m->block * m->block >= 256 ? 256 : (m->block * m->block <= 32 ? 32 : ((m->block * m->block + 31) / 32) * 32);
+  build_block_kernel<D><<<(unsigned)m->R, threads, smem, st>>>(frames, N, m->H, m->W, m->block, bw, P, (uint32_t)m->T,
                                                             m->bits);
   count_launch();
   return cuda_status(cudaGetLastError(), "build_block_kernel");

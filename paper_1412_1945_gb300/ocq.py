@@ -44,6 +44,12 @@ class ocq_model_info(ctypes.Structure):
                 ("words_per_region", ctypes.c_int64)]
 
 
+class ocq_stream_desc(ctypes.Structure):
+    _fields_ = [("train", ctypes.c_void_p), ("N", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("region", ocq_region), ("depth", ctypes.c_int), ("T", ctypes.c_int), ("test", ctypes.c_void_p),
+                ("F", ctypes.c_int), ("mask", ctypes.c_void_p)]
+
+
 # name -> (restype, argtypes)
 _vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
 SIGNATURES = {
@@ -65,6 +71,14 @@ SIGNATURES = {
                                ctypes.POINTER(_vp)]),
     "ocq_kernel_launches": (ctypes.c_uint64, []),
     "ocq_build_frame_noalloc": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp]),
+    "ocq_batch_create": (_i32, [ctypes.POINTER(ocq_stream_desc), _i32, _vp, ctypes.POINTER(_vp)]),
+    "ocq_batch_run": (_i32, [_vp, _vp]),
+    "ocq_batch_status": (_i32, [_vp, _vp]),
+    "ocq_batch_model": (_i32, [_vp, _i32, ctypes.POINTER(_vp)]),
+    "ocq_batch_set_tiles": (_i32, [_vp, _i32, _i32, _i32]),
+    "ocq_batch_get_tiles": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "ocq_batch_autotune": (_i32, [_vp, _i32, _vp]),
+    "ocq_batch_destroy": (None, [_vp]),
     "ocq_tune_count": (_i32, [_i32]),
     "ocq_tune_selected": (_i32, [_i32]),
     "ocq_tune_select": (_i32, [_i32, _i32]),
@@ -258,3 +272,74 @@ def ocq_build_frame_noalloc(frames, N, H, W, depth, T, model, stream=None):
     """Whole-frame model into the caller's device buffer ``model``
     (max(1, 8^depth/64) u64 words, exported layout); allocates nothing."""
     _check(load().ocq_build_frame_noalloc(_p(frames), N, H, W, depth, T, _p(model), _s(stream)))
+
+
+class Batch:
+    """Owns an ``ocq_batch*`` (many streams, one persistent graph-replayed launch)."""
+
+    def __init__(self, handle: int, keep):
+        self.handle = handle
+        self._keep = keep  # descriptors' buffers must outlive the batch
+
+    def model(self, i: int) -> Model:
+        """View of stream i's model (owned by the batch; not freed by the view)."""
+        out = ctypes.c_void_p()
+        _check(load().ocq_batch_model(self.handle, i, ctypes.byref(out)))
+        return _View(out.value)
+
+    def destroy(self):
+        if self.handle:
+            load().ocq_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class _View(Model):
+    def free(self):
+        self.handle = None
+
+
+def ocq_batch_create(descs, stream=None) -> Batch:
+    """``descs``: list of dicts with train, N, H, W, kind, block, depth, T, test, F, mask."""
+    arr = (ocq_stream_desc * len(descs))()
+    for i, d in enumerate(descs):
+        arr[i] = ocq_stream_desc(_p(d["train"]), d["N"], d["H"], d["W"], _region(d["kind"], d.get("block", 0)),
+                                 d["depth"], d["T"], _p(d.get("test")), d.get("F", 0), _p(d.get("mask")))
+    out = ctypes.c_void_p()
+    _check(load().ocq_batch_create(arr, len(descs), _s(stream), ctypes.byref(out)))
+    return Batch(out.value, descs)
+
+
+def ocq_batch_run(batch, stream=None):
+    _check(load().ocq_batch_run(batch.handle, _s(stream)))
+
+
+def ocq_batch_status(batch, stream=None):
+    _check(load().ocq_batch_status(batch.handle, _s(stream)))
+
+
+def ocq_batch_model(batch, i) -> Model:
+    return batch.model(i)
+
+
+def ocq_batch_set_tiles(batch, kind, pixels, frames):
+    _check(load().ocq_batch_set_tiles(batch.handle, kind, pixels, frames))
+
+
+def ocq_batch_get_tiles(batch, kind):
+    px, fr, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    _check(load().ocq_batch_get_tiles(batch.handle, kind, ctypes.byref(px), ctypes.byref(fr), ctypes.byref(n)))
+    return px.value, fr.value, n.value
+
+
+def ocq_batch_autotune(batch, reps=2, stream=None):
+    _check(load().ocq_batch_autotune(batch.handle, reps, _s(stream)))
+
+
+def ocq_batch_destroy(batch):
+    batch.destroy()

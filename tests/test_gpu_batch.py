@@ -1,0 +1,134 @@
+"""Batched form: every stream's model and masks from the one persistent,
+graph-replayed launch equal the plain per-stream path (bit-exact), which the
+other tests tie to the oracle; a few streams are also checked against the
+oracle directly."""
+import numpy as np
+import pytest
+
+import ocq_synth
+import oracle
+from ocq_synth import configs
+
+pytestmark = pytest.mark.gpu
+FRAME, BLOCK, PIXEL = 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def ocq(cuda_ready):
+    return cuda_ready
+
+
+def _streams_host(specs, torch):
+    out = []
+    for i, (kind, scene, H, W, N, F, region, block, d, T) in enumerate(specs):
+        sc = ocq_synth.make_scene(scene, H, W, N, F, 1000 + i)
+        frames = ocq_synth.fill_host(sc, 0, N + F)
+        out.append(dict(train=torch.from_numpy(frames[:N].copy()).cuda(),
+                        test=torch.from_numpy(frames[N:].copy()).cuda(),
+                        mask=torch.full((F, H, W), 7, dtype=torch.uint8, device="cuda"),
+                        N=N, H=H, W=W, kind=region, block=block, depth=d, T=T, F=F,
+                        host_train=frames[:N], host_test=frames[N:]))
+    return out
+
+
+SMALL_MIX = [
+    (0, "clusters", 120, 160, 8, 8, FRAME, 0, 4, 4),
+    (0, "sway", 37, 53, 12, 9, FRAME, 0, 6, 5),
+    (0, "sway", 20, 30, 5, 4, FRAME, 0, 8, 2),
+    (0, "clusters", 64, 96, 9, 6, BLOCK, 8, 5, 3),
+    (0, "sway", 50, 70, 10, 7, BLOCK, 16, 3, 4),
+    (0, "sway", 33, 47, 7, 5, BLOCK, 5, 4, 7),
+    (0, "bimodal", 48, 64, 20, 11, PIXEL, 0, 3, 7),
+    (0, "bimodal", 29, 37, 15, 6, PIXEL, 0, 2, 5),
+    (0, "clusters", 40, 56, 12, 5, PIXEL, 0, 4, 4),
+    (0, "sway", 24, 40, 9, 5, PIXEL, 0, 5, 3),
+    (0, "bimodal", 16, 1024, 6, 4, PIXEL, 0, 1, 2),
+    (0, "clusters", 31, 33, 11, 3, FRAME, 0, 1, 11),
+]
+
+
+def _plain(ocq, s):
+    m = ocq.build_model(s["train"], s["depth"], s["T"], s["kind"], s["block"])
+    words = ocq.export_model(m).cpu().numpy()
+    mask = ocq.classify(m, s["test"]).cpu().numpy()
+    m.free()
+    return words, mask
+
+
+def test_batch_small_mix_matches_plain_and_oracle(ocq):
+    import torch
+
+    S = _streams_host(SMALL_MIX, torch)
+    b = ocq.ocq.ocq_batch_create(S)
+    try:
+        for rep in range(2):  # first run captures the graph, second replays it
+            for s in S:
+                s["mask"].fill_(7)
+            ocq.ocq.ocq_batch_run(b)
+            ocq.ocq.ocq_batch_status(b)
+            for i, s in enumerate(S):
+                words = ocq.export_model(b.model(i)).cpu().numpy()
+                pw, pm = _plain(ocq, s)
+                assert (words == pw).all(), (rep, i)
+                assert (s["mask"].cpu().numpy() == pm).all(), (rep, i)
+        for i in (0, 4, 6, 9):
+            s = S[i]
+            ow, om = oracle.run(s["host_train"], s["depth"], s["T"], s["kind"], s["block"], s["host_test"])
+            assert (ocq.export_model(b.model(i)).cpu().numpy().view(np.uint64) == ow).all(), i
+            assert (s["mask"].cpu().numpy() == om).all(), i
+    finally:
+        b.destroy()
+
+
+def test_batch_tiles_and_autotune_keep_results(ocq):
+    import torch
+
+    S = _streams_host(SMALL_MIX[:8], torch)
+    b = ocq.ocq.ocq_batch_create(S)
+    try:
+        ocq.ocq.ocq_batch_run(b)
+        ref = [s["mask"].clone() for s in S]
+        for kind, px, fr in ((FRAME, 512, 3), (BLOCK, 96, 1), (PIXEL, 4096, 64)):
+            ocq.ocq.ocq_batch_set_tiles(b, kind, px, fr)
+        for s in S:
+            s["mask"].fill_(9)
+        ocq.ocq.ocq_batch_run(b)
+        ocq.ocq.ocq_batch_status(b)
+        assert all((s["mask"] == r).all().item() for s, r in zip(S, ref))
+        ocq.ocq.ocq_batch_autotune(b, 1)
+        for s in S:
+            s["mask"].fill_(9)
+        ocq.ocq.ocq_batch_run(b)
+        ocq.ocq.ocq_batch_status(b)
+        assert all((s["mask"] == r).all().item() for s, r in zip(S, ref))
+    finally:
+        b.destroy()
+
+
+def test_batch_64_stream_preset_matches_plain(ocq):
+    """The 64-stream preset (resolutions up to 1920x1080, depth 3-5, 1x1 /
+    8x8 / whole-frame regions), frames generated on the device."""
+    import torch
+
+    descs = []
+    for wl in configs.batched_streams():
+        sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, wl.F, wl.seed, wl.stream)
+        tr = torch.empty((wl.N, wl.H, wl.W, 3), dtype=torch.uint8, device="cuda")
+        te = torch.empty((wl.F, wl.H, wl.W, 3), dtype=torch.uint8, device="cuda")
+        ocq_synth.fill_device(sc, 0, wl.N, tr)
+        ocq_synth.fill_device(sc, wl.N, wl.F, te)
+        descs.append(dict(train=tr, test=te, mask=torch.empty((wl.F, wl.H, wl.W), dtype=torch.uint8, device="cuda"),
+                          N=wl.N, H=wl.H, W=wl.W, kind=wl.region, block=wl.block, depth=wl.depth, T=wl.T, F=wl.F))
+    b = ocq.ocq.ocq_batch_create(descs)
+    try:
+        ocq.ocq.ocq_batch_run(b)
+        ocq.ocq.ocq_batch_status(b)
+        for i, s in enumerate(descs):
+            m = ocq.build_model(s["train"], s["depth"], s["T"], s["kind"], s["block"])
+            pmask = ocq.classify(m, s["test"])
+            same_model = (ocq.export_model(b.model(i)) == ocq.export_model(m)).all().item()
+            same_mask = (s["mask"] == pmask).all().item()
+            m.free()
+            assert same_model and same_mask, i
+    finally:
+        b.destroy()
