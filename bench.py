@@ -41,6 +41,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=None, help="override F (test frames)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-stream batched-vs-plain measurement")
+    ap.add_argument("--batched-reps", type=int, default=3)
     return ap.parse_args(argv)
 
 
@@ -360,6 +362,9 @@ def run_ours(args):
         "clocks": clocks,
     }
 
+    if not args.no_batched:
+        result["batched"] = batched_measure(ocq, dev, args.batched_reps)
+
     # end to end through the C ABI with host buffers (pinned), copies timed
     if not args.no_e2e:
         result["e2e"] = e2e_measure(ocq, wl, train, test, mask, stream, args, dist, dev, world)
@@ -372,6 +377,66 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(result), flush=True)
     dist.close()
+
+
+def batched_measure(ocq, dev, reps):
+    """The 64-stream preset (uneven resolutions, depths and regions): plain
+    per-stream ocq_build_model + ocq_classify calls on one stream, against the
+    batched form (one persistent, graph-replayed launch after the autotuner)."""
+    import torch
+
+    import ocq_synth
+    from ocq_synth import configs
+
+    O = ocq.ocq
+    descs = []
+    px = 0
+    for wl in configs.batched_streams():
+        sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, wl.F, wl.seed, wl.stream)
+        tr = torch.empty((wl.N, wl.H, wl.W, 3), dtype=torch.uint8, device=dev)
+        te = torch.empty((wl.F, wl.H, wl.W, 3), dtype=torch.uint8, device=dev)
+        ocq_synth.fill_device(sc, 0, wl.N, tr)
+        ocq_synth.fill_device(sc, wl.N, wl.F, te)
+        descs.append(dict(train=tr, test=te, mask=torch.empty((wl.F, wl.H, wl.W), dtype=torch.uint8, device=dev),
+                          N=wl.N, H=wl.H, W=wl.W, kind=wl.region, block=wl.block, depth=wl.depth, T=wl.T, F=wl.F))
+        px += (wl.N + wl.F) * wl.H * wl.W
+    stream = torch.cuda.current_stream()
+
+    def plain():
+        for s in descs:
+            m = O.ocq_build_model(s["train"], s["N"], s["H"], s["W"], s["kind"], s["block"], s["depth"], s["T"],
+                                  stream)
+            O.ocq_classify(m, s["test"], s["F"], s["mask"], stream)
+            m.free()
+
+    def timed(fn, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    plain_ms = timed(plain, reps)
+    b = O.ocq_batch_create(descs, stream)
+    t0 = time.perf_counter()
+    O.ocq_batch_autotune(b, 1, stream)
+    tune_s = time.perf_counter() - t0
+    batched_ms = timed(lambda: O.ocq_batch_run(b, stream), reps)
+    O.ocq_batch_status(b, stream)
+    tiles = {k: O.ocq_batch_get_work(b, i)[0] for i, k in enumerate(("frame", "block", "pixel"))}
+    n_items = O.ocq_batch_get_work(b, 0)[1]
+    b.destroy()
+    del descs
+    torch.cuda.empty_cache()
+    return {"streams": 64, "pixels_per_run": px, "plain_ms": round(plain_ms, 3), "batched_ms": round(batched_ms, 3),
+            "plain_mpixel_s": round(px / (plain_ms / 1e3) / 1e6, 1),
+            "batched_mpixel_s": round(px / (batched_ms / 1e3) / 1e6, 1),
+            "ratio": round(plain_ms / batched_ms, 3), "autotune_s": round(tune_s, 2),
+            "work_units_per_item": tiles, "items": n_items, "launches_per_run": 1}
 
 
 def e2e_measure(ocq, wl, train, test, mask, stream, args, dist, dev, world):

@@ -162,8 +162,9 @@ ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int
  * Batched form (no counterpart in the paper, which handles one video): many
  * camera streams, each with its own frame size, region kind and depth, are
  * built (S1-S3) and classified (S4) by ONE persistent kernel launch that is
- * captured once in a CUDA graph and replayed.  Results are identical to
- * ocq_build_model + ocq_classify per stream.
+ * captured once in a CUDA graph and replayed.  Its work items are the CTAs of
+ * the per-stream kernels (the same code), taken in list order by persistent
+ * CTAs, so results are identical to ocq_build_model + ocq_classify per stream.
  *   train: device, N*H*W*3; test: device, F*H*W*3; mask: device, F*H*W.
  * Domain per stream: 1 <= T <= N <= 255; depth <= 5 for block and pixel
  * regions (<= 8 for whole-frame); the buffers stay owned by the caller and
@@ -190,13 +191,14 @@ ocq_status ocq_batch_run(ocq_batch *batch, void *stream);
 ocq_status ocq_batch_status(ocq_batch *batch, void *stream);
 /* Model of stream i: a view owned by the batch (never pass it to ocq_model_free). */
 ocq_status ocq_batch_model(const ocq_batch *batch, int i, const ocq_model **out);
-/* Tile shape of classification items for a region kind: pixels per item
- * (multiple of 32) and frames per item; re-plans the work list. */
-ocq_status ocq_batch_set_tiles(ocq_batch *batch, int region_kind, int pixels, int frames);
-ocq_status ocq_batch_get_tiles(const ocq_batch *batch, int region_kind, int *pixels, int *frames, int64_t *items);
-/* Autotuner: times candidate tile shapes per region kind on this batch's own
+/* Classification work per item for a region kind, in 1024-pixel frame tiles
+ * (units >= 1); re-plans the work list.  get_work also returns the number of
+ * items in the list. */
+ocq_status ocq_batch_set_work(ocq_batch *batch, int region_kind, int units);
+ocq_status ocq_batch_get_work(const ocq_batch *batch, int region_kind, int *units, int64_t *items);
+/* Autotuner: times candidate work sizes per region kind on this batch's own
  * inputs (`reps` runs each, on `stream`) and keeps the fastest; results are
- * cached per (region kind, depths, sizes) signature for the process. */
+ * cached per (region kind, depths, sizes, frames) signature for the process. */
 ocq_status ocq_batch_autotune(ocq_batch *batch, int reps, void *stream);
 void ocq_batch_destroy(ocq_batch *batch);
 

@@ -2,20 +2,18 @@
 // built (S1-S3, Sec. 3, Alg. 1-2) and classified (S4, Alg. 3) in ONE
 // persistent kernel launch, replayed from a CUDA graph.
 //
-// The host turns the streams into a work list of items; persistent CTAs take
-// items in list order from an atomic counter.  Item kinds:
-//   OCC      whole-frame stream: leaf bitset of one frame's pixel chunk
-//   MERGE    whole-frame stream: bit-sliced count of the frames' bitsets -> model words
-//   BLOCK    block-region stream: one block's model row (per-frame bitset, listed words,
-//            bit-sliced counters in shared memory)
-//   PIXEL    pixel-region stream: 128 pixel locations' rows (byte counters in shared memory)
-//   CLASSIFY any stream: a tile of pixels x a run of test frames
-// Dependencies are per stream: MERGE waits for the stream's OCC items, CLASSIFY
-// for the stream's build items.  Every item a CTA waits on precedes it in the
-// list, so it was taken by a running CTA and completes; each wait is still
-// bounded (1 s) and records a timeout instead of spinning forever.
-// Tile shapes of CLASSIFY items (pixels x frames) are chosen per region kind
-// by the autotuner (ocq_batch_autotune), which times candidate work lists.
+// The work list holds the CTAs of the plain per-stream kernels as "virtual
+// CTAs" (vb of vg): each item runs the same device body the plain kernel runs
+// (build_bodies.cuh, classify_bodies.cuh), so every stream's result is the
+// plain path's result bit for bit, and each item is as efficient as a CTA of
+// the plain kernel.  Persistent CTAs (160 threads: four compute warps and a
+// copy warp for the bodies that stream frames) take items in list order from
+// an atomic counter.  Per stream, a merge waits for the stream's occupancy
+// items and classification for its build items; every waited-on item precedes
+// the waiter in the list, so it was taken by a running CTA, and each wait is
+// bounded (1 s) and records a timeout instead of spinning forever.  The
+// classification work per item (in 1024-pixel frame tiles) is chosen per
+// region kind by the autotuner (ocq_batch_autotune).
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -23,12 +21,26 @@
 #include <string>
 #include <vector>
 
-#include "async_copy.cuh"
-#include "pixels.cuh"
+#include "build_bodies.cuh"
+#include "classify_bodies.cuh"
 
 namespace ocq {
 
-enum : int32_t { IT_OCC = 0, IT_MERGE = 1, IT_BLOCK = 2, IT_PIXEL = 3, IT_CLASSIFY = 4 };
+// Operations a work item runs: each is the body of one of the plain kernels,
+// run as virtual CTA vb of vg.
+enum : int32_t {
+  OP_OCC_FRAME = 0,    // occ_frame_body           (whole frame, depth <= 6)
+  OP_OCC_GLOBAL,       // occ_global_body          (whole frame, depth >= 7)
+  OP_MERGE,            // planes_merge_body        (whole frame)
+  OP_BUILD_BLOCK,      // build_block_body         (blocks, depth <= 5)
+  OP_BUILD_PIXEL_WS,   // build_pixel_ws_body      (pixels, depth <= 3, aligned)
+  OP_BUILD_PIXEL_CNT,  // build_pixel_counters_body (pixels, depth <= 3, remainder / unaligned)
+  OP_BUILD_PIXEL_CHK,  // build_pixel_chunked_body (pixels, depth 4-5)
+  OP_CLS_FRAME,        // classify_frame_body      (whole frame, depth <= 6)
+  OP_CLS_PIXEL_WS,     // classify_pixel_ws_body   (pixels, depth <= 3, aligned)
+  OP_CLS_BLOCK_WS,     // classify_block_ws_body   (blocks, b % 8 == 0, W % 16 == 0)
+  OP_CLS_GENERIC       // classify_generic_body    (everything else, and remainders)
+};
 
 struct BStream {
   const uint8_t *train, *test;
@@ -36,23 +48,27 @@ struct BStream {
   uint32_t *model;  // R * wpr words, internal (planar) order
   uint32_t *occ;    // whole-frame streams: N * wpr words of scratch
   int64_t hw, R, wpr;
+  int64_t ptiles;      // per-pixel 1024-pixel classify tiles (hw / 1024)
+  int64_t btiles;      // pixel-build 128-pixel tiles (hw / 128)
+  int64_t blk_tiles;   // block classify tiles
   int32_t N, F, H, W, kind, block, bw, depth, T, P;
-  int32_t n_build;  // items that complete the model (MERGE, BLOCK or PIXEL)
-  int32_t n_occ;    // OCC items (whole-frame streams)
-};
-
-struct BItem {
-  int32_t type, stream;
-  int64_t a;     // first pixel / block / word
-  int32_t c;     // pixels / words in the item
-  int32_t f0;    // first frame
-  int32_t nf;    // frames
+  int32_t wt, ntx;     // block classify tile width and tiles per strip
+  int32_t n_build;     // items that complete the model
+  int32_t n_occ;       // occupancy items (whole frame)
+  int32_t occ_nbx;     // pixel chunks per frame in occupancy items
   int32_t pad;
 };
 
-static constexpr int kBatchThreads = 128;
+struct BItem {
+  int32_t op, stream;
+  int64_t vb, vg;
+  int64_t aux;  // first pixel of a remainder range (CNT / GENERIC)
+};
 
-// Counter block: [0] next item, [1] timeout flag, [2..2+S) OCC done, [2+S..2+2S) build done.
+static constexpr int kBatchThreads = 160;
+static constexpr int64_t kOccChunk = 16384;
+
+// Counter block: [0] next item, [1] timeout flag, [2..2+S) occupancy done, [2+S..2+2S) build done.
 __device__ __forceinline__ bool wait_count(const uint32_t *ctr, uint32_t want, uint32_t *err) {
   const volatile uint32_t *p = ctr;
   if (*p >= want) return true;
@@ -68,213 +84,93 @@ __device__ __forceinline__ bool wait_count(const uint32_t *ctr, uint32_t want, u
   return true;
 }
 
-__device__ __forceinline__ uint32_t planar_q(const uint8_t *px, int d) {
-  return planar_code_rt(px[0], px[1], px[2], d);
+__device__ __forceinline__ void mbar_inval(uint32_t bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// ---- items --------------------------------------------------------------------
-
-__device__ void item_occ(const BStream &S, const BItem &it, uint32_t *sm) {
-  const uint8_t *fr = S.train + ((int64_t)it.f0 * S.hw) * 3;
-  uint32_t *dst = S.occ + (int64_t)it.f0 * S.wpr;
-  if (S.wpr <= 8192) {
-    for (int64_t i = threadIdx.x; i < S.wpr; i += blockDim.x) sm[i] = 0;
-    __syncthreads();
-    for (int64_t p = it.a + threadIdx.x; p < it.a + it.c; p += blockDim.x) {
-      const uint32_t q = planar_q(fr + p * 3, S.depth);
-      const uint32_t m = 1u << (q & 31);
-      if (!(sm[q >> 5] & m)) atomicOr(&sm[q >> 5], m);
-    }
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < S.wpr; i += blockDim.x)
-      if (sm[i]) atomicOr(&dst[i], sm[i]);
-  } else {
-    for (int64_t p = it.a + threadIdx.x; p < it.a + it.c; p += blockDim.x) {
-      const uint32_t q = planar_q(fr + p * 3, S.depth);
-      const uint32_t m = 1u << (q & 31);
-      if (!(*(volatile uint32_t *)&dst[q >> 5] & m)) atomicOr(&dst[q >> 5], m);
-    }
-  }
-}
-
-__device__ void item_merge(const BStream &S, const BItem &it) {
-  for (int64_t w = it.a + threadIdx.x; w < it.a + it.c; w += blockDim.x) {
-    uint32_t pl[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) pl[k] = 0;
-    for (int f = 0; f < S.N; ++f) {
-      uint32_t x = *(volatile const uint32_t *)&S.occ[(int64_t)f * S.wpr + w];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        if (k < S.P) {
-          const uint32_t t = pl[k] & x;
-          pl[k] ^= x;
-          x = t;
-        }
+template <int D>
+__device__ __forceinline__ void run_item_d(const BStream &S, const BItem &it, uint32_t *err, uint8_t *smem) {
+  const uint32_t T = (uint32_t)S.T;
+  switch (it.op) {
+    case OP_OCC_FRAME:
+      if constexpr (D <= 6) occ_frame_body<D>(S.train, S.hw, 0, kOccChunk, S.occ, it.vb % S.occ_nbx, it.vb / S.occ_nbx);
+      break;
+    case OP_BUILD_BLOCK:
+      if constexpr (D <= 5) build_block_body<D>(S.train, S.N, S.H, S.W, S.block, S.bw, S.P, T, S.model, S.R, it.vb, it.vg);
+      break;
+    case OP_BUILD_PIXEL_WS:
+      if constexpr (D <= 3) {
+        build_pixel_ws_body<D, 128, 8, 3, false, false>(S.train, S.N, S.hw, S.btiles, T, S.model, nullptr, it.vb, it.vg,
+                                                        err);
+        __syncthreads();
+        using C = WsBuildCfg<D, 128, 8, 3, false>;
+        if (threadIdx.x < 6) mbar_inval(smem_addr(smem + C::STATE + 3 * C::STAGE + threadIdx.x * 8));
       }
-    }
-    uint32_t gt = 0, eq = 0xFFFFFFFFu;
-#pragma unroll
-    for (int k = 15; k >= 0; --k) {
-      if (k < S.P) {
-        const uint32_t c = pl[k];
-        if (((uint32_t)S.T >> k) & 1u) {
-          eq &= c;
-        } else {
-          gt |= eq & c;
-          eq &= ~c;
-        }
+      break;
+    case OP_BUILD_PIXEL_CNT:
+      if constexpr (D <= 3) build_pixel_counters_body<D, false>(S.train, S.N, S.hw, it.aux, T, S.model, it.vb);
+      break;
+    case OP_BUILD_PIXEL_CHK:
+      if constexpr (D >= 4 && D <= 5) build_pixel_chunked_body<D>(S.train, S.N, S.hw, T, S.model, nullptr, it.vb);
+      break;
+    case OP_CLS_FRAME:
+      if constexpr (D <= 6) classify_frame_body<D>(S.test, (int64_t)S.F * S.hw, S.model, S.mask, it.vb, it.vg);
+      break;
+    case OP_CLS_PIXEL_WS:
+      if constexpr (D <= 3) {
+        classify_pixel_ws_body<D, 4, 8, 4, 4>(S.test, S.F, S.hw, S.ptiles, S.model, S.mask, it.vb, it.vg, err);
+        __syncthreads();
+        const size_t off = classify_pixel_ws_bars<D, 4, 8, 4, 4>();
+        if (threadIdx.x < 8) mbar_inval(smem_addr(smem + off + threadIdx.x * 8));
       }
-    }
-    S.model[w] = gt | eq;
+      break;
+    case OP_CLS_BLOCK_WS:
+      if constexpr (D <= 5) {
+        classify_block_ws_body<D, 4, 4>(S.test, S.F, S.H, S.W, S.block, S.wt, S.ntx, S.blk_tiles, S.model, S.mask,
+                                        it.vb, it.vg, err);
+        __syncthreads();
+        constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+        const size_t off = classify_block_ws_rows_bytes(S.block, S.wt, WPR) + (size_t)4 * 4 * 1024 * 3;
+        if (threadIdx.x < 8) mbar_inval(smem_addr(smem + off + threadIdx.x * 8));
+      }
+      break;
+    default:
+      break;
   }
 }
 
-__device__ void item_block(const BStream &S, const BItem &it, uint32_t *sm, uint32_t *nlist) {
-  const int64_t wpr = S.wpr;
-  uint32_t *seen = sm, *planes = sm + wpr, *list = planes + (int64_t)S.P * wpr;
-  for (int64_t i = threadIdx.x; i < wpr * (S.P + 1); i += blockDim.x) sm[i] = 0;
-  if (threadIdx.x == 0) *nlist = 0;
-  const int64_t r = it.a;
-  const int b = S.block;
-  const int y0 = (int)(r / S.bw) * b, x0 = (int)(r % S.bw) * b;
-  const int h = min(b, S.H - y0), w = min(b, S.W - x0);
-  const int npx = h * w;
-  __syncthreads();
-  for (int f = 0; f < S.N; ++f) {
-    const uint8_t *fr = S.train + (int64_t)f * S.hw * 3;
-    for (int i = threadIdx.x; i < npx; i += blockDim.x) {
-      const int y = y0 + i / w, x = x0 + i % w;
-      const uint32_t q = planar_q(fr + ((int64_t)y * S.W + x) * 3, S.depth);
-      const uint32_t m = 1u << (q & 31);
-      if (!(seen[q >> 5] & m)) {
-        if (atomicOr(&seen[q >> 5], m) == 0) list[atomicAdd(nlist, 1u)] = q >> 5;
-      }
-    }
-    __syncthreads();
-    const uint32_t n = *nlist;
-    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
-      const uint32_t wd = list[k];
-      uint32_t x = seen[wd];
-      for (int j = 0; j < S.P && x; ++j) {
-        const uint32_t t = planes[j * wpr + wd] & x;
-        planes[j * wpr + wd] ^= x;
-        x = t;
-      }
-      seen[wd] = 0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *nlist = 0;
-    __syncthreads();
+__device__ void run_item(const BStream &S, const BItem &it, uint32_t *err, uint8_t *smem) {
+  switch (it.op) {
+    case OP_OCC_GLOBAL:
+      occ_global_body(S.train, S.H, S.W, OCQ_REGION_FRAME, 0, S.depth, 0, S.N, 1, S.wpr, S.occ, it.vb, it.vg);
+      return;
+    case OP_MERGE:
+      planes_merge_body(S.occ, S.N, S.wpr, nullptr, S.P, 1, 1, (uint32_t)S.T, S.model, it.vb, it.vg);
+      return;
+    case OP_CLS_GENERIC:
+      classify_generic_body(S.test, S.F, S.H, S.W, S.kind, S.block, S.depth, S.wpr, S.model, S.mask, it.aux, S.hw,
+                            it.vb, it.vg);
+      return;
+    default:
+      break;
   }
-  for (int64_t wd = threadIdx.x; wd < wpr; wd += blockDim.x) {
-    uint32_t gt = 0, eq = 0xFFFFFFFFu;
-    for (int k = S.P - 1; k >= 0; --k) {
-      const uint32_t c = planes[k * wpr + wd];
-      if (((uint32_t)S.T >> k) & 1u) {
-        eq &= c;
-      } else {
-        gt |= eq & c;
-        eq &= ~c;
-      }
-    }
-    S.model[r * wpr + wd] = gt | eq;
+  switch (S.depth) {
+    case 1: run_item_d<1>(S, it, err, smem); break;
+    case 2: run_item_d<2>(S, it, err, smem); break;
+    case 3: run_item_d<3>(S, it, err, smem); break;
+    case 4: run_item_d<4>(S, it, err, smem); break;
+    case 5: run_item_d<5>(S, it, err, smem); break;
+    case 6: run_item_d<6>(S, it, err, smem); break;
+    default: break;
   }
 }
 
-// Per-pixel rows, 128 pixel locations per item, one per thread.  Byte
-// counters (N <= 255, checked by the plan) for 512-leaf chunks in a private
-// column cnt[k*128 + t]; depth <= 3 is one chunk, deeper rows count only the
-// chunks the pixel's training colours touch.
-__device__ void item_pixel(const BStream &S, const BItem &it, uint32_t *cnt) {
-  const int t = threadIdx.x;
-  const int64_t p = it.a + t;
-  if (t >= it.c) return;
-  const int d = S.depth;
-  const uint32_t ncodes = 1u << (3 * d);
-  const uint32_t chunk = ncodes < 512 ? ncodes : 512u;
-  const int cwords = (int)((chunk + 3) / 4);
-  const int nchunks = (int)(ncodes / chunk);
-  const uint8_t *px = S.train + p * 3;
-  const int64_t fstride = S.hw * 3;
-  uint64_t touched = 0;
-  if (nchunks > 1) {
-    for (int f = 0; f < S.N; ++f) touched |= 1ull << (planar_q(px + f * fstride, d) >> 9);
-  } else {
-    touched = 1;
-  }
-  uint32_t *row = S.model + p * S.wpr;
-  for (int c = 0; c < nchunks; ++c) {
-    uint32_t *dst = row + (int64_t)c * (chunk >= 32 ? chunk / 32 : 1);
-    const int ow = chunk >= 32 ? (int)(chunk / 32) : 1;
-    if (!((touched >> c) & 1ull)) {
-      for (int w = 0; w < ow; ++w) dst[w] = 0;
-      continue;
-    }
-    for (int k = 0; k < cwords; ++k) cnt[k * kBatchThreads + t] = 0;
-    for (int f = 0; f < S.N; ++f) {
-      const uint32_t q = planar_q(px + f * fstride, d);
-      if ((int)(q / chunk) != c) continue;
-      const uint32_t l = q % chunk;
-      cnt[(l >> 2) * kBatchThreads + t] += 1u << ((l & 3u) * 8);
-    }
-    for (int w = 0; w < ow; ++w) {
-      uint32_t o = 0;
-      for (int k = 0; k < 8 && w * 8 + k < cwords; ++k) {
-        const uint32_t ge = __vcmpgeu4(cnt[(w * 8 + k) * kBatchThreads + t], (uint32_t)S.T * 0x01010101u);
-        o |= (((ge >> 7) & 1u) | ((ge >> 14) & 2u) | ((ge >> 21) & 4u) | ((ge >> 28) & 8u)) << (4 * k);
-      }
-      if (chunk < 32) o &= (1u << chunk) - 1u;
-      dst[w] = o;
-    }
-  }
-}
-
-// A tile of pixels x a run of test frames.  Whole-frame rows and per-pixel
-// rows of depth <= 3 are staged in shared memory (word-major for pixel rows,
-// so a warp's lookups fall in distinct banks); other rows are read from
-// global memory.
-__device__ void item_classify(const BStream &S, const BItem &it, uint32_t *sm) {
-  const int d = S.depth;
-  const int64_t pa = it.a, pc = it.c;
-  const bool frame_row = S.kind == OCQ_REGION_FRAME && S.wpr <= 8192;
-  const bool pixel_rows = S.kind == OCQ_REGION_PIXEL && d <= 3;
-  if (frame_row) {
-    for (int64_t i = threadIdx.x; i < S.wpr; i += blockDim.x) sm[i] = *(volatile const uint32_t *)&S.model[i];
-  } else if (pixel_rows) {
-    for (int64_t i = threadIdx.x; i < pc * S.wpr; i += blockDim.x) {
-      const int64_t pl = i / S.wpr, w = i % S.wpr;
-      sm[w * pc + pl] = *(volatile const uint32_t *)&S.model[(pa + pl) * S.wpr + w];
-    }
-  }
-  __syncthreads();
-  for (int f = it.f0; f < it.f0 + it.nf; ++f) {
-    const uint8_t *fr = S.test + (int64_t)f * S.hw * 3;
-    uint8_t *mk = S.mask + (int64_t)f * S.hw;
-    for (int64_t i = threadIdx.x; i < pc; i += blockDim.x) {
-      const int64_t p = pa + i;
-      const uint32_t q = planar_q(fr + p * 3, d);
-      uint32_t word;
-      if (frame_row) {
-        word = sm[q >> 5];
-      } else if (pixel_rows) {
-        word = sm[(q >> 5) * pc + i];
-      } else {
-        const int y = (int)(p / S.W), x = (int)(p % S.W);
-        word = __ldcg(S.model + region_of(y, x, S.W, S.kind, S.block, S.bw) * S.wpr + (q >> 5));
-      }
-      mk[p] = (uint8_t)(((word >> (q & 31)) & 1u) ^ 1u);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BStream *__restrict__ streams,
+__global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BStream *__restrict__ streams,
                                                               const BItem *__restrict__ items, int n_items, int S,
                                                               uint32_t *ctr) {
-  extern __shared__ uint32_t sm[];
+  extern __shared__ __align__(128) uint8_t dsmem[];
   __shared__ int cur;
   __shared__ int ok;
-  __shared__ uint32_t nlist;
   uint32_t *err = ctr + 1;
   uint32_t *occ_done = ctr + 2;
   uint32_t *build_done = ctr + 2 + S;
@@ -287,27 +183,41 @@ __global__ void __launch_bounds__(kBatchThreads) batch_kernel(const BStream *__r
     const BStream &st = streams[it.stream];
     if (threadIdx.x == 0) {
       ok = 1;
-      if (it.type == IT_MERGE) ok = wait_count(&occ_done[it.stream], (uint32_t)st.n_occ, err);
-      if (it.type == IT_CLASSIFY) ok = wait_count(&build_done[it.stream], (uint32_t)st.n_build, err);
+      if (it.op == OP_MERGE) ok = wait_count(&occ_done[it.stream], (uint32_t)st.n_occ, err);
+      if (it.op >= OP_CLS_FRAME) ok = wait_count(&build_done[it.stream], (uint32_t)st.n_build, err);
       __threadfence();
     }
     __syncthreads();
-    if (ok) {
-      switch (it.type) {
-        case IT_OCC: item_occ(st, it, sm); break;
-        case IT_MERGE: item_merge(st, it); break;
-        case IT_BLOCK: item_block(st, it, sm, &nlist); break;
-        case IT_PIXEL: item_pixel(st, it, sm); break;
-        default: item_classify(st, it, sm); break;
-      }
-    }
+    if (ok) run_item(st, it, err, dsmem);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0 && ok) {
-      if (it.type == IT_OCC) atomicAdd(&occ_done[it.stream], 1u);
-      if (it.type == IT_MERGE || it.type == IT_BLOCK || it.type == IT_PIXEL) atomicAdd(&build_done[it.stream], 1u);
+      if (it.op == OP_OCC_FRAME || it.op == OP_OCC_GLOBAL) atomicAdd(&occ_done[it.stream], 1u);
+      else if (it.op < OP_CLS_FRAME) atomicAdd(&build_done[it.stream], 1u);
     }
   }
+}
+
+// Shared memory one item of stream S needs (bytes).
+static size_t item_smem(const BStream &h) {
+  const int d = h.depth;
+  size_t need = 0;
+  if (h.kind == OCQ_REGION_FRAME) {
+    if (d <= 6) need = std::max<size_t>(need, (size_t)h.wpr * 4 * (d <= 4 ? 32 : 1));  // occ row / replicated row
+  } else if (h.kind == OCQ_REGION_BLOCK) {
+    need = std::max<size_t>(need, (size_t)h.wpr * (h.P + 2) * 4);
+    if (h.wt > 0) need = std::max<size_t>(need, classify_block_ws_rows_bytes(h.block, h.wt, (int)h.wpr) +
+                                                  (size_t)4 * 4 * 1024 * 3 + 8 * 8);
+  } else {
+    if (d <= 3) {
+      need = std::max<size_t>(need, (size_t)h.wpr * 4 * 1024 + (size_t)4 * 4 * 1024 * 3 + 8 * 8);  // classify ws
+      need = std::max<size_t>(need, (size_t)((1 << (3 * d)) / 4 > 0 ? (1 << (3 * d)) / 4 : 1) * 128 * 4 +
+                                        (size_t)3 * 8 * 128 * 3 + 6 * 8);                          // build ws
+    } else {
+      need = std::max<size_t>(need, (size_t)256 * 64 * 4);  // chunked build
+    }
+  }
+  return need;
 }
 
 }  // namespace ocq
@@ -321,8 +231,7 @@ struct ocq_batch {
   std::vector<BStream> hs;
   std::vector<ocq_model *> models;  // views (bits point into the arena)
   std::vector<BItem> items;
-  int tile_px[3] = {2048, 2048, 1024};  // CLASSIFY pixels per item, per region kind
-  int tile_frames[3] = {16, 16, 32};    // CLASSIFY frames per item, per region kind
+  int units[3] = {64, 64, 64};  // classification work per item, per region kind, in 1024-pixel frame tiles
   BStream *d_streams = nullptr;
   BItem *d_items = nullptr;
   size_t items_cap = 0;
@@ -337,32 +246,40 @@ struct ocq_batch {
   int device = 0;
 };
 
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Work list: the virtual CTAs of every stream's plain kernels.  Whole-frame
+// occupancy first, then the merges, then block and pixel builds (larger
+// streams first), then classification in the order the models become ready.
 static ocq_status plan_items(ocq_batch *b) {
   b->items.clear();
   const int S = (int)b->hs.size();
   std::vector<BStream> &hs = b->hs;
-  auto push = [&](int32_t type, int s, int64_t a, int32_t c, int32_t f0, int32_t nf) {
+  auto push = [&](int32_t op, int s, int64_t vb, int64_t vg, int64_t aux) {
     BItem it;
-    it.type = type, it.stream = s, it.a = a, it.c = c, it.f0 = f0, it.nf = nf, it.pad = 0;
+    it.op = op, it.stream = s, it.vb = vb, it.vg = vg, it.aux = aux;
     b->items.push_back(it);
   };
-  // 1. whole-frame occupancy, then their merges (so those models are ready early)
-  const int64_t occ_chunk = 16384;
   for (int s = 0; s < S; ++s) {
     BStream &st = hs[s];
     st.n_occ = 0, st.n_build = 0;
     if (st.kind != OCQ_REGION_FRAME) continue;
-    for (int f = 0; f < st.N; ++f)
-      for (int64_t a = 0; a < st.hw; a += occ_chunk, ++st.n_occ)
-        push(IT_OCC, s, a, (int32_t)std::min<int64_t>(occ_chunk, st.hw - a), f, 1);
+    if (st.depth <= 6) {
+      st.occ_nbx = (int32_t)cdiv(st.hw, kOccChunk);
+      for (int64_t v = 0; v < (int64_t)st.occ_nbx * st.N; ++v, ++st.n_occ) push(OP_OCC_FRAME, s, v, 0, 0);
+    } else {
+      const int64_t vg = std::max<int64_t>(1, std::min<int64_t>(4096, cdiv(st.hw * st.N, (int64_t)kBatchThreads * 256)));
+      for (int64_t v = 0; v < vg; ++v, ++st.n_occ) push(OP_OCC_GLOBAL, s, v, vg, 0);
+    }
   }
   for (int s = 0; s < S; ++s) {
     BStream &st = hs[s];
     if (st.kind != OCQ_REGION_FRAME) continue;
-    for (int64_t a = 0; a < st.wpr; a += 1024, ++st.n_build)
-      push(IT_MERGE, s, a, (int32_t)std::min<int64_t>(1024, st.wpr - a), 0, 0);
+    const int64_t vg = std::max<int64_t>(1, std::min<int64_t>(64, cdiv(st.wpr, kBatchThreads)));
+    for (int64_t v = 0; v < vg; ++v, ++st.n_build) push(OP_MERGE, s, v, vg, 0);
   }
-  // 2. block and pixel builds, larger streams first
   std::vector<int> order(S);
   for (int s = 0; s < S; ++s) order[s] = s;
   std::stable_sort(order.begin(), order.end(),
@@ -370,13 +287,21 @@ static ocq_status plan_items(ocq_batch *b) {
   for (int s : order) {
     BStream &st = hs[s];
     if (st.kind == OCQ_REGION_BLOCK) {
-      for (int64_t r = 0; r < st.R; ++r, ++st.n_build) push(IT_BLOCK, s, r, 1, 0, 0);
+      const int64_t vg = cdiv(st.R, 8);
+      for (int64_t v = 0; v < vg; ++v, ++st.n_build) push(OP_BUILD_BLOCK, s, v, vg, 0);
     } else if (st.kind == OCQ_REGION_PIXEL) {
-      for (int64_t a = 0; a < st.hw; a += kBatchThreads, ++st.n_build)
-        push(IT_PIXEL, s, a, (int32_t)std::min<int64_t>(kBatchThreads, st.hw - a), 0, 0);
+      if (st.depth >= 4) {
+        for (int64_t v = 0; v < cdiv(st.hw, 64); ++v, ++st.n_build) push(OP_BUILD_PIXEL_CHK, s, v, 0, 0);
+      } else {
+        if (st.btiles > 0) {
+          const int64_t vg = cdiv(st.btiles, 8);
+          for (int64_t v = 0; v < vg; ++v, ++st.n_build) push(OP_BUILD_PIXEL_WS, s, v, vg, 0);
+        }
+        const int64_t p0 = st.btiles * 128;
+        for (int64_t v = 0; v < cdiv(st.hw - p0, 128); ++v, ++st.n_build) push(OP_BUILD_PIXEL_CNT, s, v, 0, p0);
+      }
     }
   }
-  // 3. classification: whole-frame streams first (ready first), then in build order
   std::vector<int> corder;
   for (int s = 0; s < S; ++s)
     if (hs[s].kind == OCQ_REGION_FRAME) corder.push_back(s);
@@ -384,14 +309,27 @@ static ocq_status plan_items(ocq_batch *b) {
     if (hs[s].kind != OCQ_REGION_FRAME) corder.push_back(s);
   for (int s : corder) {
     BStream &st = hs[s];
-    int tp = b->tile_px[st.kind], tf = b->tile_frames[st.kind];
-    if (st.kind == OCQ_REGION_PIXEL && st.depth <= 3) {
-      const int64_t cap = (int64_t)(b->smem / 4) / st.wpr;  // rows that fit the staging area
-      if (tp > cap) tp = (int)cap;
+    const int64_t per = (int64_t)b->units[st.kind];
+    auto generic = [&](int64_t p0) {
+      const int64_t n = (st.hw - p0) * st.F;
+      if (n <= 0) return;
+      const int64_t vg = std::max<int64_t>(1, std::min<int64_t>(cdiv(n, per * 1024), cdiv(n, kBatchThreads)));
+      for (int64_t v = 0; v < vg; ++v) push(OP_CLS_GENERIC, s, v, vg, p0);
+    };
+    if (st.F == 0) continue;
+    if (st.kind == OCQ_REGION_FRAME && st.depth <= 6) {
+      const int64_t vg = std::max<int64_t>(1, cdiv(st.hw * st.F, per * 1024));
+      for (int64_t v = 0; v < vg; ++v) push(OP_CLS_FRAME, s, v, vg, 0);
+    } else if (st.kind == OCQ_REGION_PIXEL && st.ptiles > 0) {
+      const int64_t vg = std::max<int64_t>(1, cdiv(st.ptiles * st.F, per));
+      for (int64_t v = 0; v < vg; ++v) push(OP_CLS_PIXEL_WS, s, v, vg, 0);
+      generic(st.ptiles * 1024);
+    } else if (st.kind == OCQ_REGION_BLOCK && st.blk_tiles > 0) {
+      const int64_t vg = std::max<int64_t>(1, cdiv(st.blk_tiles * st.F, per));
+      for (int64_t v = 0; v < vg; ++v) push(OP_CLS_BLOCK_WS, s, v, vg, 0);
+    } else {
+      generic(0);
     }
-    for (int64_t a = 0; a < st.hw; a += tp)
-      for (int f = 0; f < st.F; f += tf)
-        push(IT_CLASSIFY, s, a, (int32_t)std::min<int64_t>(tp, st.hw - a), f, std::min(tf, st.F - f));
   }
   return OCQ_OK;
 }
@@ -420,12 +358,14 @@ static ocq_status enqueue_run(ocq_batch *b, cudaStream_t st) {
   const int S = (int)b->hs.size();
   ocq_status rc = cuda_status(cudaMemsetAsync(b->d_ctr, 0, (size_t)(2 + 2 * S) * 4, st), "reset batch counters");
   if (rc != OCQ_OK) return rc;
-  for (int s = 0; s < S; ++s) {
-    if (b->hs[s].kind == OCQ_REGION_FRAME) {
-      rc = cuda_status(cudaMemsetAsync(b->hs[s].occ, 0, (size_t)b->hs[s].N * b->hs[s].wpr * 4, st), "clear occupancy");
-      if (rc != OCQ_OK) return rc;
-    }
+  for (int s = 0; s < S && rc == OCQ_OK; ++s) {
+    const BStream &h = b->hs[s];
+    if (h.kind == OCQ_REGION_FRAME)
+      rc = cuda_status(cudaMemsetAsync(h.occ, 0, (size_t)h.N * h.wpr * 4, st), "clear occupancy");
+    else if (h.kind == OCQ_REGION_PIXEL && h.depth >= 4)
+      rc = cuda_status(cudaMemsetAsync(h.model, 0, (size_t)h.R * h.wpr * 4, st), "clear model");
   }
+  if (rc != OCQ_OK) return rc;
   batch_kernel<<<b->grid, kBatchThreads, b->smem, st>>>(b->d_streams, b->d_items, (int)b->items.size(), S, b->d_ctr);
   count_launch();
   return cuda_status(cudaGetLastError(), "batch_kernel");
@@ -477,7 +417,7 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
   b->owner = st;
   b->desc.assign(streams, streams + n);
   size_t bytes = 0;
-  size_t smem = 4096 * 4;
+  size_t smem = 16 * 1024;
   std::vector<size_t> model_off(n), occ_off(n);
   for (int s = 0; s < n; ++s) {
     const ocq_stream_desc &d = streams[s];
@@ -505,17 +445,26 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     int P = 0;
     for (uint32_t v = (uint32_t)d.N; v; v >>= 1) ++P;
     h.P = P;
+    const bool al = aligned16(d.train) && (d.F == 0 || (aligned16(d.test) && aligned16(d.mask)));
+    if (h.kind == OCQ_REGION_PIXEL && d.depth <= 3 && al && h.hw % 16 == 0) {
+      h.ptiles = h.hw / 1024;
+      h.btiles = h.hw / 128;
+    }
+    if (h.kind == OCQ_REGION_BLOCK && d.depth <= 5 && al) {
+      h.wt = block_tile_width(h.block, d.depth, d.W);
+      if (h.wt > 0) {
+        h.ntx = (d.W + h.wt - 1) / h.wt;
+        h.blk_tiles = (int64_t)h.ntx * ((d.H + h.block - 1) / h.block);
+      }
+    }
     b->hs.push_back(h);
     model_off[s] = bytes;
     bytes += ((size_t)R * h.wpr * 4 + 255) & ~(size_t)255;
     occ_off[s] = bytes;
     if (h.kind == OCQ_REGION_FRAME) bytes += ((size_t)d.N * h.wpr * 4 + 255) & ~(size_t)255;
-    // shared memory each item kind needs
-    if (h.kind == OCQ_REGION_FRAME) smem = std::max(smem, (size_t)std::min<int64_t>(h.wpr, 8192) * 4);
-    if (h.kind == OCQ_REGION_BLOCK) smem = std::max(smem, (size_t)h.wpr * (P + 2) * 4);
-    if (h.kind == OCQ_REGION_PIXEL) smem = std::max(smem, (size_t)128 * kBatchThreads * 4);
+    smem = std::max(smem, item_smem(h));
   }
-  b->smem = std::max<size_t>(smem, 64 * 1024);
+  b->smem = (smem + 127) & ~(size_t)127;
   if (b->smem > 227 * 1024) {
     set_error("ocq_batch_create: the streams need %zu bytes of shared memory per CTA", b->smem);
     delete b;
@@ -550,7 +499,7 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
   }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, b->smem);
-  b->grid = sm_count() * std::max(1, per_sm);  // all CTAs resident: every waited-on item is being run
+  b->grid = sm_count() * std::max(1, per_sm);
   rc = plan_items(b);
   if (rc == OCQ_OK) rc = upload_plan(b, st);
   if (rc != OCQ_OK) {
@@ -573,82 +522,77 @@ ocq_status ocq_batch_run(ocq_batch *b, void *stream) {
   return cuda_status(cudaGraphLaunch(b->exec, (cudaStream_t)stream), "batch graph launch");
 }
 
-ocq_status ocq_batch_set_tiles(ocq_batch *b, int region_kind, int pixels, int frames) {
-  if (!b || region_kind < 0 || region_kind > 2 || pixels < 32 || pixels % 32 || frames < 1) {
-    set_error("ocq_batch_set_tiles: bad arguments");
+ocq_status ocq_batch_set_work(ocq_batch *b, int region_kind, int units) {
+  if (!b || region_kind < 0 || region_kind > 2 || units < 1) {
+    set_error("ocq_batch_set_work: bad arguments");
     return OCQ_EINVAL;
   }
-  b->tile_px[region_kind] = pixels;
-  b->tile_frames[region_kind] = frames;
+  b->units[region_kind] = units;
   ocq_status rc = plan_items(b);
   if (rc == OCQ_OK) rc = upload_plan(b, b->owner);
   free_graph(b);
   return rc;
 }
 
-ocq_status ocq_batch_get_tiles(const ocq_batch *b, int region_kind, int *pixels, int *frames, int64_t *items) {
+ocq_status ocq_batch_get_work(const ocq_batch *b, int region_kind, int *units, int64_t *items) {
   if (!b || region_kind < 0 || region_kind > 2) {
-    set_error("ocq_batch_get_tiles: bad arguments");
+    set_error("ocq_batch_get_work: bad arguments");
     return OCQ_EINVAL;
   }
-  if (pixels) *pixels = b->tile_px[region_kind];
-  if (frames) *frames = b->tile_frames[region_kind];
+  if (units) *units = b->units[region_kind];
   if (items) *items = (int64_t)b->items.size();
   return OCQ_OK;
 }
 
-// Times candidate CLASSIFY tile shapes per region kind (each candidate runs the
-// whole batch `reps` times on `stream`) and keeps the fastest.  Results are
-// cached per shape signature (kind, depth, resolution) so an equal batch
-// later skips the search.
+// Autotuner: for each region kind present, times candidate classification
+// work sizes per item (the whole batch `reps` times each, on `stream`) and
+// keeps the fastest.  Results are cached per signature (kind, depths, sizes)
+// so an equal batch later skips the search.
 ocq_status ocq_batch_autotune(ocq_batch *b, int reps, void *stream) {
   if (!b || reps < 1) {
     set_error("ocq_batch_autotune: bad arguments");
     return OCQ_EINVAL;
   }
-  static std::map<std::string, std::pair<int, int>> cache;
+  static std::map<std::string, int> cache;
   cudaStream_t st = (cudaStream_t)stream;
   std::string sig[3];
   bool present[3] = {false, false, false};
   for (const BStream &h : b->hs) {
     present[h.kind] = true;
-    sig[h.kind] += std::to_string(h.depth) + "x" + std::to_string(h.hw) + ",";
+    sig[h.kind] += std::to_string(h.depth) + "x" + std::to_string(h.hw) + "f" + std::to_string(h.F) + ",";
   }
-  const int cand_px[] = {512, 1024, 2048, 4096};
-  const int cand_f[] = {8, 16, 32, 64};
+  const int cand[] = {8, 16, 32, 64, 128, 256};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   ocq_status rc = OCQ_OK;
   for (int k = 0; k < 3 && rc == OCQ_OK; ++k) {
     if (!present[k]) continue;
-    auto hit = cache.find(std::to_string(k) + ":" + sig[k]);
+    const std::string key = std::to_string(k) + ":" + sig[k];
+    auto hit = cache.find(key);
     if (hit != cache.end()) {
-      b->tile_px[k] = hit->second.first, b->tile_frames[k] = hit->second.second;
+      b->units[k] = hit->second;
       continue;
     }
     float best = 1e30f;
-    int bp = b->tile_px[k], bf = b->tile_frames[k];
-    for (int px : cand_px) {
-      for (int fr : cand_f) {
-        b->tile_px[k] = px, b->tile_frames[k] = fr;
-        rc = plan_items(b);
-        if (rc == OCQ_OK) rc = upload_plan(b, st);
-        if (rc != OCQ_OK) break;
-        enqueue_run(b, st);  // warm-up
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < reps; ++r) rc = enqueue_run(b, st);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rc != OCQ_OK) break;
-        if (ms < best) best = ms, bp = px, bf = fr;
-      }
+    int bu = b->units[k];
+    for (int u : cand) {
+      b->units[k] = u;
+      rc = plan_items(b);
+      if (rc == OCQ_OK) rc = upload_plan(b, st);
       if (rc != OCQ_OK) break;
+      rc = enqueue_run(b, st);  // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && rc == OCQ_OK; ++r) rc = enqueue_run(b, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc != OCQ_OK) break;
+      if (ms < best) best = ms, bu = u;
     }
-    b->tile_px[k] = bp, b->tile_frames[k] = bf;
-    cache[std::to_string(k) + ":" + sig[k]] = {bp, bf};
+    b->units[k] = bu;
+    cache[key] = bu;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -21,8 +21,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "async_copy.cuh"
-#include "pixels.cuh"
+#include "build_bodies.cuh"
 
 namespace ocq {
 
@@ -35,223 +34,53 @@ static int bit_length(uint32_t v) {
   return n;
 }
 
-template <int MAXP>
-__device__ __forceinline__ void planes_add_reg(uint32_t (&pl)[MAXP], int P, uint32_t x) {
-#pragma unroll
-  for (int k = 0; k < MAXP; ++k) {
-    if (k < P) {
-      uint32_t t = pl[k] & x;
-      pl[k] ^= x;
-      x = t;
-    }
-  }
-}
+// ---- plain kernels: one grid, virtual CTA = real CTA ----------------------------------
 
-template <int MAXP>
-__device__ __forceinline__ uint32_t planes_ge_reg(const uint32_t (&pl)[MAXP], int P, uint32_t T) {
-  uint32_t gt = 0, eq = 0xFFFFFFFFu;
-#pragma unroll
-  for (int k = MAXP - 1; k >= 0; --k) {
-    if (k < P) {
-      const uint32_t c = pl[k];
-      if ((T >> k) & 1u) {
-        eq &= c;
-      } else {
-        gt |= eq & c;
-        eq &= ~c;
-      }
-    }
-  }
-  return gt | eq;
-}
-
-// ---- dense per-frame occupancy ----------------------------------------------
-
-// Whole-frame regions, depth <= 6: CTA (x, y) marks the leaves of pixel chunk x
-// of frame f0 + y in a shared bitset, then ORs it into occ[y].
 template <int D>
 __global__ void __launch_bounds__(256) occ_frame_kernel(const uint8_t *__restrict__ frames, int64_t hw, int f0,
                                                         int64_t chunk, uint32_t *__restrict__ occ) {
-  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
-  __shared__ uint32_t seen[WPR];
-  for (int i = threadIdx.x; i < WPR; i += blockDim.x) seen[i] = 0;
-  __syncthreads();
-  const uint8_t *fr = frames + (int64_t)(f0 + blockIdx.y) * hw * 3;
-  const int64_t p0 = (int64_t)blockIdx.x * chunk;
-  const int64_t p1 = p0 + chunk < hw ? p0 + chunk : hw;
-  cta_for_codes<D>(fr, p0, p1, [&](uint32_t q, int64_t) {
-    const uint32_t m = 1u << (q & 31);
-    if (!(seen[q >> 5] & m)) atomicOr(&seen[q >> 5], m);
-  });
-  __syncthreads();
-  uint32_t *dst = occ + (int64_t)blockIdx.y * WPR;
-  for (int i = threadIdx.x; i < WPR; i += blockDim.x)
-    if (seen[i]) atomicOr(&dst[i], seen[i]);
+  occ_frame_body<D>(frames, hw, f0, chunk, occ, blockIdx.x, blockIdx.y);
 }
 
-// Any region kind and depth: one thread per pixel, global atomics into
-// occ[(f - f0) * R + r][...].
 __global__ void occ_global_kernel(const uint8_t *__restrict__ frames, int H, int W, int kind, int block, int d,
                                   int f0, int nf, int64_t R, int64_t wpr, uint32_t *__restrict__ occ) {
-  const int64_t hw = (int64_t)H * W;
-  const int64_t npix = hw * nf;
-  const int bw = kind == OCQ_REGION_BLOCK ? (W + block - 1) / block : 1;
-  const uint8_t *base = frames + (int64_t)f0 * hw * 3;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t f = i / hw, p = i - f * hw;
-    const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
-    const uint8_t *px = base + i * 3;
-    const uint32_t q = planar_code_rt(__ldg(px), __ldg(px + 1), __ldg(px + 2), d);
-    uint32_t *word = occ + (f * R + region_of(y, x, W, kind, block, bw)) * wpr + (q >> 5);
-    const uint32_t m = 1u << (q & 31);
-    if (!(*(volatile uint32_t *)word & m)) atomicOr(word, m);
-  }
+  occ_global_body(frames, H, W, kind, block, d, f0, nf, R, wpr, occ, blockIdx.x, gridDim.x);
 }
 
-// Folds nb frames of occupancy words into bit-sliced counters; on the last
-// batch writes count >= T into the model.
 __global__ void planes_merge_kernel(const uint32_t *__restrict__ occ, int nb, int64_t nwords,
                                     uint32_t *__restrict__ planes, int P, int first, int last, uint32_t T,
                                     uint32_t *__restrict__ model) {
-  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwords; w += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t pl[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) pl[k] = (!first && k < P) ? planes[k * nwords + w] : 0u;
-    for (int f = 0; f < nb; ++f) planes_add_reg<16>(pl, P, __ldg(occ + f * nwords + w));
-    if (last) {
-      model[w] = planes_ge_reg<16>(pl, P, T);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 16; ++k)
-        if (k < P) planes[k * nwords + w] = pl[k];
-    }
-  }
+  planes_merge_body(occ, nb, nwords, planes, P, first, last, T, model, blockIdx.x, gridDim.x);
 }
 
-// ---- block regions, depth <= 5 -----------------------------------------------
-// One CTA per block region.  Per training frame the block's leaves are marked
-// in a shared bitset; the first thread to set a bit in an empty word appends
-// the word to a list, so only listed words are folded into the bit-sliced
-// counters and cleared (a block has at most b*b leaves per frame, far fewer
-// than 8^d/32 words at depth 4-5).
 template <int D>
 __global__ void __launch_bounds__(256) build_block_kernel(const uint8_t *__restrict__ frames, int N, int H, int W,
                                                           int b, int bw, int P, uint32_t T,
-                                                          uint32_t *__restrict__ model) {
-  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
-  extern __shared__ uint32_t sm[];
-  uint32_t *seen = sm;                   // [WPR]
-  uint32_t *planes = sm + WPR;           // [P][WPR]
-  uint32_t *list = planes + P * WPR;     // [WPR] words set in the current frame
-  __shared__ uint32_t nlist;
-  for (int i = threadIdx.x; i < WPR * (P + 1); i += blockDim.x) sm[i] = 0;
-  if (threadIdx.x == 0) nlist = 0;
-  const int64_t r = blockIdx.x;
-  const int y0 = (int)(r / bw) * b, x0 = (int)(r % bw) * b;
-  const int h = min(b, H - y0), w = min(b, W - x0);
-  const int npx = h * w;
-  const int64_t hw = (int64_t)H * W;
-  __syncthreads();
-  for (int f = 0; f < N; ++f) {
-    const uint8_t *fr = frames + (int64_t)f * hw * 3;
-    for (int i = threadIdx.x; i < npx; i += blockDim.x) {
-      const int y = y0 + i / w, x = x0 + i % w;
-      const uint8_t *px = fr + ((int64_t)y * W + x) * 3;
-      const uint32_t q = planar_code_rt(__ldg(px), __ldg(px + 1), __ldg(px + 2), D);
-      const uint32_t m = 1u << (q & 31);
-      if (!(seen[q >> 5] & m)) {
-        const uint32_t old = atomicOr(&seen[q >> 5], m);
-        if (old == 0) list[atomicAdd(&nlist, 1u)] = q >> 5;
-      }
-    }
-    __syncthreads();
-    const uint32_t n = nlist;
-    for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
-      const uint32_t wd = list[k];
-      uint32_t x = seen[wd];
-      for (int j = 0; j < P && x; ++j) {
-        const uint32_t t = planes[j * WPR + wd] & x;
-        planes[j * WPR + wd] ^= x;
-        x = t;
-      }
-      seen[wd] = 0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) nlist = 0;
-    __syncthreads();
-  }
-  for (int wd = threadIdx.x; wd < WPR; wd += blockDim.x) {
-    uint32_t gt = 0, eq = 0xFFFFFFFFu;
-    for (int k = P - 1; k >= 0; --k) {
-      const uint32_t c = planes[k * WPR + wd];
-      if ((T >> k) & 1u) {
-        eq &= c;
-      } else {
-        gt |= eq & c;
-        eq &= ~c;
-      }
-    }
-    model[r * WPR + wd] = gt | eq;
-  }
+                                                          uint32_t *__restrict__ model, int64_t R) {
+  build_block_body<D>(frames, N, H, W, b, bw, P, T, model, R, blockIdx.x, gridDim.x);
 }
 
-// ---- pixel regions, depth <= 3 -------------------------------------------------
-// Thread t of a 128-thread CTA owns pixel location p and a private column of
-// counter words cnt[k * 128 + t] (4 u8 or 2 u16 counters per word).
 template <int D, bool WIDE>
 __global__ void __launch_bounds__(128) build_pixel_counters_kernel(const uint8_t *__restrict__ frames, int N,
                                                                    int64_t hw, int64_t p_begin, uint32_t T,
                                                                    uint32_t *__restrict__ model) {
-  constexpr int NC = 1 << (3 * D);
-  constexpr int CPW = WIDE ? 2 : 4;
-  constexpr int BITS = 32 / CPW;
-  constexpr int NW = (NC + CPW - 1) / CPW;
-  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
-  extern __shared__ uint32_t cnt[];
-  const int t = threadIdx.x;
-  const int64_t p = p_begin + (int64_t)blockIdx.x * 128 + t;
-  if (p >= hw) return;  // columns are private: no CTA-wide synchronisation below
-#pragma unroll 8
-  for (int k = 0; k < NW; ++k) cnt[k * 128 + t] = 0;
-  const uint8_t *px = frames + p * 3;
-  const int64_t fstride = hw * 3;
-  int f = 0;
-  for (; f + 4 <= N; f += 4) {
-    uint32_t q[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const uint8_t *s = px + (int64_t)(f + u) * fstride;
-      q[u] = planar_code_rt(__ldg(s), __ldg(s + 1), __ldg(s + 2), D);
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) cnt[(q[u] / CPW) * 128 + t] += 1u << ((q[u] % CPW) * BITS);
-  }
-  for (; f < N; ++f) {
-    const uint8_t *s = px + (int64_t)f * fstride;
-    const uint32_t q = planar_code_rt(__ldg(s), __ldg(s + 1), __ldg(s + 2), D);
-    cnt[(q / CPW) * 128 + t] += 1u << ((q % CPW) * BITS);
-  }
-  uint32_t out[WPR];
-#pragma unroll
-  for (int w = 0; w < WPR; ++w) out[w] = 0;
-#pragma unroll
-  for (int k = 0; k < NW; ++k) {
-    const uint32_t v = cnt[k * 128 + t];
-    uint32_t bits;
-    if constexpr (WIDE) {
-      const uint32_t ge = __vcmpgeu2(v, T * 0x00010001u);
-      bits = ((ge >> 15) & 1u) | ((ge >> 30) & 2u);
-    } else {
-      const uint32_t ge = __vcmpgeu4(v, T * 0x01010101u);
-      bits = ((ge >> 7) & 1u) | ((ge >> 14) & 2u) | ((ge >> 21) & 4u) | ((ge >> 28) & 8u);
-    }
-    const int c0 = k * CPW;  // first leaf of this counter word
-    if (c0 < NC) out[c0 >> 5] |= bits << (c0 & 31);
-  }
-  if (NC < 32) out[0] &= (NC < 32 ? ((1u << NC) - 1u) : 0xFFFFFFFFu);
-  uint32_t *dst = model + p * WPR;
-#pragma unroll
-  for (int w = 0; w < WPR; ++w) dst[w] = out[w];
+  build_pixel_counters_body<D, WIDE>(frames, N, hw, p_begin, T, model, blockIdx.x);
+}
+
+template <int D>
+__global__ void __launch_bounds__(64) build_pixel_chunked_kernel(const uint8_t *__restrict__ frames, int N,
+                                                                 int64_t hw, uint32_t T, uint32_t *__restrict__ model,
+                                                                 uint32_t *__restrict__ touched_g) {
+  build_pixel_chunked_body<D>(frames, N, hw, T, model, touched_g, blockIdx.x);
+}
+
+template <int D, int NT, int FPS, int S, bool TENSOR, bool KEPT>
+__global__ void __launch_bounds__(NT + 32) build_pixel_ws_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
+                                                                 int64_t ntiles, uint32_t T,
+                                                                 uint32_t *__restrict__ model,
+                                                                 const __grid_constant__ CUtensorMap tmap) {
+  build_pixel_ws_body<D, NT, FPS, S, TENSOR, KEPT>(frames, N, hw, ntiles, T, model, &tmap, blockIdx.x, gridDim.x,
+                                                   &g_build_timeout);
 }
 
 // Same counting with the frames staged by bulk asynchronous copies.  A
@@ -409,10 +238,6 @@ struct RedBuildCfg {
   static constexpr size_t SMEM = STATE + 128 + (size_t)S * STAGE + (size_t)S * 8;
   static_assert(ROW % 128 == 0, "stages stay 128-byte aligned");
 };
-
-__device__ __forceinline__ void red_add_shared(uint32_t *p, uint32_t v) {
-  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
-}
 
 template <int D, int NT, int FPS, int S>
 __global__ void __launch_bounds__(NT) build_pixel_red_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
@@ -576,67 +401,6 @@ __global__ void __launch_bounds__(NT) build_pixel_direct_kernel(const uint8_t *_
   }
 }
 
-// ---- pixel regions, depth >= 4 --------------------------------------------------
-// Counts leaves chunk by chunk (512 leaves, u16 counters in a private column
-// of 256 words) for the chunks the pixel's training colours touch.  `touched`
-// is a per-pixel chunk bitmap in global scratch (depth >= 6) or a register.
-template <int D>
-__global__ void __launch_bounds__(64) build_pixel_chunked_kernel(const uint8_t *__restrict__ frames, int N,
-                                                                 int64_t hw, uint32_t T, uint32_t *__restrict__ model,
-                                                                 uint32_t *__restrict__ touched_g) {
-  constexpr int NCH = 1 << (3 * D - 9);
-  constexpr int WPR = 1 << (3 * D - 5);
-  constexpr int TW = NCH / 32 > 0 ? NCH / 32 : 1;  // touched words per pixel (global form)
-  extern __shared__ uint32_t cnt[];                 // [256][64]
-  const int t = threadIdx.x;
-  const int64_t p = (int64_t)blockIdx.x * 64 + t;
-  if (p >= hw) return;
-  const uint8_t *px = frames + p * 3;
-  const int64_t fstride = hw * 3;
-  uint64_t touched = 0;
-  uint32_t *tg = touched_g ? touched_g + p * TW : nullptr;
-  for (int f = 0; f < N; ++f) {
-    const uint8_t *s = px + (int64_t)f * fstride;
-    const uint32_t q = planar_code_rt(__ldg(s), __ldg(s + 1), __ldg(s + 2), D);
-    const uint32_t c = q >> 9;
-    if constexpr (NCH <= 64)
-      touched |= 1ull << c;
-    else
-      tg[c >> 5] |= 1u << (c & 31);
-  }
-  uint32_t *row = model + p * WPR;
-  int tw = 0;
-  uint32_t cur = 0;
-  while (true) {
-    int c;
-    if constexpr (NCH <= 64) {
-      if (!touched) break;
-      c = __ffsll((long long)touched) - 1;
-      touched &= touched - 1;
-    } else {
-      while (!cur && tw < TW) cur = tg[tw++];
-      if (!cur) break;
-      c = (tw - 1) * 32 + __ffs(cur) - 1;
-      cur &= cur - 1;
-    }
-    for (int k = 0; k < 256; ++k) cnt[k * 64 + t] = 0;
-    for (int f = 0; f < N; ++f) {
-      const uint8_t *s = px + (int64_t)f * fstride;
-      const uint32_t q = planar_code_rt(__ldg(s), __ldg(s + 1), __ldg(s + 2), D);
-      if ((int)(q >> 9) == c) cnt[((q & 511u) >> 1) * 64 + t] += 1u << ((q & 1u) * 16);
-    }
-    for (int w = 0; w < 16; ++w) {
-      uint32_t out = 0;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const uint32_t ge = __vcmpgeu2(cnt[(w * 16 + k) * 64 + t], T * 0x00010001u);
-        out |= (((ge >> 15) & 1u) | ((ge >> 30) & 2u)) << (2 * k);
-      }
-      row[c * 16 + w] = out;
-    }
-  }
-}
-
 // ---- host dispatch ----------------------------------------------------------------
 
 static unsigned grid_cap(int64_t work, int threads, int per_sm) {
@@ -649,8 +413,9 @@ static unsigned grid_cap(int64_t work, int threads, int per_sm) {
 template <int D>
 static void launch_occ_frame(const uint8_t *frames, int64_t hw, int f0, int nf, uint32_t *occ, cudaStream_t st) {
   const int64_t chunk = 256 * 16 * 4;  // pixels per CTA (multiple of 16)
+  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
   dim3 grid((unsigned)((hw + chunk - 1) / chunk), (unsigned)nf);
-  occ_frame_kernel<D><<<grid, 256, 0, st>>>(frames, hw, f0, chunk, occ);
+  occ_frame_kernel<D><<<grid, 256, WPR * 4, st>>>(frames, hw, f0, chunk, occ);
   count_launch();
 }
 
@@ -713,7 +478,7 @@ static ocq_status launch_block(const uint8_t *frames, int N, ocq_model *m, cudaS
   const int bw = (m->W + m->block - 1) / m->block;
   const int threads = m->block * m->block >= 256 ? 256 : (m->block * m->block <= 32 ? 32 : ((m->block * m->block + 31) / 32) * 32);
   build_block_kernel<D><<<(unsigned)m->R, threads, smem, st>>>(frames, N, m->H, m->W, m->block, bw, P, (uint32_t)m->T,
-                                                            m->bits);
+                                                                m->bits, m->R);
   count_launch();
   return cuda_status(cudaGetLastError(), "build_block_kernel");
 }
@@ -834,181 +599,6 @@ static ocq_status launch_pixel_direct(const uint8_t *frames, int N, ocq_model *m
   kern<<<(unsigned)((hw + NT - 1) / NT), NT, C::SMEM, st>>>(frames, N, hw, 0, (uint32_t)m->T, m->bits);
   count_launch();
   return cuda_status(cudaGetLastError(), "build_pixel_direct_kernel");
-}
-
-// Warp-specialised form of build_pixel_red_kernel: NT counting threads plus
-// one copy warp.  The copy warp refills stage s as soon as every counting
-// warp has signalled (mbarrier "empty[s]") that it is done with it; counting
-// warps wait only on "full[s]".  No CTA-wide barrier in the steady state.
-// TENSOR: a stage is one 2-D tensor copy (FPS frame rows x NT*3 bytes)
-// instead of FPS row copies.  KEPT: the counters are bumped with an atomic
-// add that returns the old count, and the leaf's bit is set in the thread's
-// "kept" row (registers) the moment its count reaches T; the end of a tile
-// then only writes the kept row out and zeroes the touched counters (no
-// threshold pass).
-template <int D, int NT, int FPS, int S, bool KEPT>
-struct WsBuildCfg {
-  static constexpr int NC = 1 << (3 * D);
-  static constexpr int CW = (NC + 3) / 4;  // u8 counter words per pixel
-  static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
-  static constexpr int ROW = NT * 3;
-  static constexpr int STAGE = ROW * FPS;
-  static constexpr size_t STATE = (size_t)CW * NT * 4;
-  static constexpr size_t SMEM = STATE + (size_t)S * STAGE + (size_t)S * 16;
-  static_assert(ROW % 128 == 0 && STATE % 128 == 0, "stages stay 128-byte aligned");
-};
-
-template <int D, int NT, int FPS, int S, bool TENSOR, bool KEPT>
-__global__ void __launch_bounds__(NT + 32) build_pixel_ws_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
-                                                                 int64_t ntiles, uint32_t T,
-                                                                 uint32_t *__restrict__ model,
-                                                                 const __grid_constant__ CUtensorMap tmap) {
-  using C = WsBuildCfg<D, NT, FPS, S, KEPT>;
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);  // [CW][NT]
-  uint8_t *stages = smem + C::STATE;
-  uint64_t *full = reinterpret_cast<uint64_t *>(stages + (size_t)S * C::STAGE);
-  uint64_t *empty = full + S;
-  const int t = threadIdx.x;
-  constexpr int NCW = NT / 32;  // counting warps
-  if (t == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(smem_addr(&full[s]), 1);
-      mbar_init(smem_addr(&empty[s]), NCW);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (t < NT) {
-#pragma unroll 8
-    for (int c = 0; c < C::CW; ++c) cnt[c * NT + t] = 0;
-  }
-  __syncthreads();
-  const int G = (N + FPS - 1) / FPS;  // stages per tile
-  const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-
-  if (t >= NT) {  // ---- copy warp ----
-    if (t != NT) return;
-    int s = 0;
-    uint32_t round = 0;
-    bool ok = true;
-    for (int64_t i = 0; i < my_tiles && ok; ++i) {
-      const int64_t tile = blockIdx.x + i * gridDim.x;
-      const uint8_t *base = frames + tile * NT * 3;
-      for (int g = 0; g < G; ++g) {
-        if (round > 0) {  // wait until the counting warps released this stage's previous fill
-          if (!mbar_wait_bounded(smem_addr(&empty[s]), (round - 1) & 1, kWaitLimitNs)) {
-            atomicExch(&g_build_timeout, 1u);
-            ok = false;
-            break;
-          }
-        }
-        const int f0 = g * FPS;
-        const uint32_t bar = smem_addr(&full[s]);
-        if constexpr (TENSOR) {
-          // rows past frame N-1 are filled with zeros and still count as bytes
-          mbar_expect_tx(bar, (uint32_t)C::STAGE);
-          tensor2d_g2s(smem_addr(stages + (size_t)s * C::STAGE), &tmap, (int)(tile * (C::ROW / 4)), f0, bar);
-        } else {
-          const int nf = N - f0 < FPS ? N - f0 : FPS;
-          mbar_expect_tx(bar, (uint32_t)(nf * C::ROW));
-          for (int j = 0; j < nf; ++j)
-            bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)j * C::ROW),
-                     base + (int64_t)(f0 + j) * hw * 3, C::ROW, bar);
-        }
-        if (++s == S) s = 0, ++round;
-      }
-    }
-    // let the last fills land before this CTA can retire
-    for (int k = 0; k < S; ++k) {
-      const uint32_t fills = round + (k < s ? 1u : 0u);
-      if (fills > 0) mbar_wait_bounded(smem_addr(&full[k]), (fills - 1) & 1, kWaitLimitNs);
-    }
-    return;
-  }
-
-  // ---- counting threads ----
-  const int lane = t & 31;
-  int s = 0;
-  uint32_t round = 0;
-  for (int64_t i = 0; i < my_tiles; ++i) {
-    uint32_t words = 0;  // model words (32 leaves each) this pixel touched
-    uint32_t kept[C::WPR];
-#pragma unroll
-    for (int w = 0; w < C::WPR; ++w) kept[w] = 0;
-    for (int g = 0; g < G; ++g) {
-      if (!mbar_wait_bounded(smem_addr(&full[s]), round & 1, kWaitLimitNs)) {
-        atomicExch(&g_build_timeout, 1u);
-        return;
-      }
-      const uint8_t *stage = stages + (size_t)s * C::STAGE + 3 * t;
-      const int nf = N - g * FPS < FPS ? N - g * FPS : FPS;
-#pragma unroll
-      for (int j = 0; j < FPS; ++j) {
-        if (j < nf) {
-          const uint8_t *px = stage + j * C::ROW;
-          const uint32_t y = (uint32_t)px[0] | ((uint32_t)px[1] << 8) | ((uint32_t)px[2] << 16);
-          const uint32_t q = planar_code<D>(y);
-          const uint32_t sh = (q & 3u) * 8;
-          if constexpr (KEPT) {
-            const uint32_t old = atomicAdd(&cnt[(q >> 2) * NT + t], 1u << sh);
-            if (((old >> sh) & 0xFFu) + 1u == T) {  // once per kept leaf and tile
-#pragma unroll
-              for (int w = 0; w < C::WPR; ++w)
-                if ((int)(q >> 5) == w) kept[w] |= 1u << (q & 31);
-            }
-          } else {
-            red_add_shared(&cnt[(q >> 2) * NT + t], 1u << sh);
-          }
-          words |= 1u << (q >> 5);
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
-      if (++s == S) s = 0, ++round;
-    }
-    uint32_t *dst = model + ((blockIdx.x + i * gridDim.x) * NT + t) * C::WPR;
-    if constexpr (KEPT) {
-      if constexpr (C::WPR % 4 == 0) {
-#pragma unroll
-        for (int w = 0; w < C::WPR; w += 4)
-          *reinterpret_cast<uint4 *>(dst + w) = make_uint4(kept[w], kept[w + 1], kept[w + 2], kept[w + 3]);
-      } else {
-#pragma unroll
-        for (int w = 0; w < C::WPR; ++w) dst[w] = kept[w];
-      }
-      for (; words; words &= words - 1) {  // zero the counters this tile used
-        const int w = __ffs(words) - 1;
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          if (w * 8 + c < C::CW) cnt[(w * 8 + c) * NT + t] = 0;
-      }
-    } else {
-      if constexpr (C::WPR % 4 == 0) {
-#pragma unroll
-        for (int w = 0; w < C::WPR; w += 4) *reinterpret_cast<uint4 *>(dst + w) = make_uint4(0, 0, 0, 0);
-      } else {
-#pragma unroll
-        for (int w = 0; w < C::WPR; ++w) dst[w] = 0;
-      }
-      for (; words; words &= words - 1) {
-        const int w = __ffs(words) - 1;
-        uint32_t o = 0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (w * 8 + c < C::CW) {
-            uint32_t *cp = &cnt[(w * 8 + c) * NT + t];
-            const uint32_t v = *cp;
-            if (v) {
-              const uint32_t ge = __vcmpgeu4(v, T * 0x01010101u);
-              o |= (((ge >> 7) & 1u) | ((ge >> 14) & 2u) | ((ge >> 21) & 4u) | ((ge >> 28) & 8u)) << (4 * c);
-              *cp = 0;
-            }
-          }
-        }
-        dst[w] = o;
-      }
-    }
-  }
 }
 
 template <int D, int NT, int FPS, int S, bool TENSOR, bool KEPT>

@@ -75,8 +75,8 @@ SIGNATURES = {
     "ocq_batch_run": (_i32, [_vp, _vp]),
     "ocq_batch_status": (_i32, [_vp, _vp]),
     "ocq_batch_model": (_i32, [_vp, _i32, ctypes.POINTER(_vp)]),
-    "ocq_batch_set_tiles": (_i32, [_vp, _i32, _i32, _i32]),
-    "ocq_batch_get_tiles": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "ocq_batch_set_work": (_i32, [_vp, _i32, _i32]),
+    "ocq_batch_get_work": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "ocq_batch_autotune": (_i32, [_vp, _i32, _vp]),
     "ocq_batch_destroy": (None, [_vp]),
     "ocq_tune_count": (_i32, [_i32]),
@@ -327,14 +327,14 @@ def ocq_batch_model(batch, i) -> Model:
     return batch.model(i)
 
 
-def ocq_batch_set_tiles(batch, kind, pixels, frames):
-    _check(load().ocq_batch_set_tiles(batch.handle, kind, pixels, frames))
+def ocq_batch_set_work(batch, kind, units):
+    _check(load().ocq_batch_set_work(batch.handle, kind, units))
 
 
-def ocq_batch_get_tiles(batch, kind):
-    px, fr, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
-    _check(load().ocq_batch_get_tiles(batch.handle, kind, ctypes.byref(px), ctypes.byref(fr), ctypes.byref(n)))
-    return px.value, fr.value, n.value
+def ocq_batch_get_work(batch, kind):
+    u, n = ctypes.c_int(), ctypes.c_int64()
+    _check(load().ocq_batch_get_work(batch.handle, kind, ctypes.byref(u), ctypes.byref(n)))
+    return u.value, n.value
 
 
 def ocq_batch_autotune(batch, reps=2, stream=None):

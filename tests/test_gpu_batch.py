@@ -88,8 +88,8 @@ def test_batch_tiles_and_autotune_keep_results(ocq):
     try:
         ocq.ocq.ocq_batch_run(b)
         ref = [s["mask"].clone() for s in S]
-        for kind, px, fr in ((FRAME, 512, 3), (BLOCK, 96, 1), (PIXEL, 4096, 64)):
-            ocq.ocq.ocq_batch_set_tiles(b, kind, px, fr)
+        for kind, units in ((FRAME, 3), (BLOCK, 1), (PIXEL, 500)):
+            ocq.ocq.ocq_batch_set_work(b, kind, units)
         for s in S:
             s["mask"].fill_(9)
         ocq.ocq.ocq_batch_run(b)

@@ -258,3 +258,18 @@ def test_every_tuning_variant(ocq, torch, H, W):
                         assert (mask == om).all(), (kernel, v, d, T)
                 finally:
                     O.ocq_tune_select(kernel, saved)
+
+
+@pytest.mark.parametrize("b", [8, 16, 32, 64])
+@pytest.mark.parametrize("d", [1, 3, 4, 5])
+def test_block_tiled_classify(ocq, torch, b, d):
+    """Block regions with b % 8 == 0 and W % 16 == 0 go through the strip-tiled
+    classify kernel; partial blocks at the right and bottom edges included."""
+    H, W = 3 * b + 5, 176 if b <= 16 else 2 * b + 48
+    sc = ocq_synth.make_scene("sway", H, W, 9, 13, seed=300 + b + d)
+    frames = ocq_synth.fill_host(sc, 0, 22)
+    train, test = frames[:9], frames[9:]
+    words, mask = gpu_model_and_mask(ocq, torch, train, test, d, 4, BLOCK, b)
+    ow, om = oracle.run(train, d, 4, BLOCK, b, test)
+    assert (words == ow).all()
+    assert (mask == om).all()
