@@ -43,6 +43,8 @@ def parse_args(argv=None):
     ap.add_argument("--frames", type=int, default=None, help="override F (test frames)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-stream batched-vs-plain measurement")
     ap.add_argument("--batched-reps", type=int, default=3)
+    ap.add_argument("--no-serving", action="store_true", help="skip the 256-camera serving simulation")
+    ap.add_argument("--serving-seconds", type=float, default=40.0, help="wall-time limit of the serving run")
     return ap.parse_args(argv)
 
 
@@ -364,6 +366,8 @@ def run_ours(args):
 
     if not args.no_batched:
         result["batched"] = batched_measure(ocq, dev, args.batched_reps)
+    if not args.no_serving:
+        result["serving"] = serving_measure(ocq, dev, args.serving_seconds)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     if not args.no_e2e:
@@ -437,6 +441,109 @@ def batched_measure(ocq, dev, reps):
             "batched_mpixel_s": round(px / (batched_ms / 1e3) / 1e6, 1),
             "ratio": round(plain_ms / batched_ms, 3), "autotune_s": round(tune_s, 2),
             "work_units_per_item": tiles, "items": n_items, "launches_per_run": 1}
+
+
+def serving_measure(ocq, dev, time_limit_s, budget_frac=0.5, n_cameras=256, frames_per_camera=90, pool=8,
+                    mask_slots=32):
+    """The 256-camera serving preset in real time.  Cameras join as a Poisson
+    process (25.6/s) and then send frames as a Poisson process at 30 fps.
+    Waiting cameras are admitted first-fit against an HBM budget as slots and
+    memory free up; a camera admitted late has its arrivals shifted by the
+    delay.  Each frame is submitted at its arrival time; latency = completion
+    time - scheduled arrival (host steady clock), so host lag counts against
+    it.  A camera's N training frames and a pool of ``pool`` test frames
+    (cycled) are rendered on the device when it is admitted, so the numbers
+    are GPU-side; p50/p99 are over all completed frames."""
+    import collections
+    import heapq
+
+    import torch
+
+    import ocq_synth
+    from ocq_synth import configs
+
+    O = ocq.ocq
+    streams = configs.serving_streams(n_cameras, frames_per_camera)
+    fps = [O.ocq_server_camera_footprint(s.wl.H, s.wl.W, s.wl.region, s.wl.block, s.wl.depth, s.wl.T,
+                                         s.wl.N, s.wl.N) for s in streams]
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(free * budget_frac)
+    srv = O.ocq_server_create(budget, n_cameras)
+    joins = collections.deque(sorted(range(len(streams)), key=lambda i: streams[i].join_s))
+    waiting, live, sched, heap = [], {}, {}, []
+    lat, rejected, delays, done_cams, px_done, peak_used = [], 0, [], 0, 0, 0
+    base = time.monotonic()
+    try:
+        while (joins or waiting or live) and time.monotonic() - base < time_limit_s:
+            progressed = False
+            now = time.monotonic() - base
+            while joins and streams[joins[0]].join_s <= now:
+                i = joins.popleft()
+                if fps[i] > budget:
+                    rejected += 1  # can never fit this budget
+                else:
+                    waiting.append(i)
+            used = O.ocq_server_usage(srv)[0]
+            for i in list(waiting):
+                if used + fps[i] > budget:
+                    continue
+                wl = streams[i].wl
+                sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, pool, wl.seed, wl.stream)
+                fr = torch.empty((wl.N + pool, wl.H, wl.W, 3), dtype=torch.uint8, device=dev)
+                ocq_synth.fill_device(sc, 0, wl.N + pool, fr)
+                masks = torch.empty((mask_slots, wl.H, wl.W), dtype=torch.uint8, device=dev)
+                torch.cuda.current_stream(dev).synchronize()  # the server's streams do not wait on torch's
+                cam = O.ocq_server_admit(srv, wl.H, wl.W, wl.region, wl.block, wl.depth, wl.T, wl.N, wl.N, fr[:wl.N])
+                if cam is None:
+                    continue
+                waiting.remove(i)
+                used += fps[i]
+                peak_used = max(peak_used, used)
+                now = time.monotonic() - base
+                shift = max(0.0, now - streams[i].join_s)
+                delays.append(shift)
+                live[i] = dict(cam=cam, frames=fr, masks=masks, completed=0)
+                for t, a in enumerate(streams[i].arrivals):
+                    heapq.heappush(heap, (a + shift, i, t))
+                progressed = True
+            now = time.monotonic() - base
+            while heap and heap[0][0] <= now:
+                a, i, t = heapq.heappop(heap)
+                st, wl = live[i], streams[i].wl
+                tag = i * 100000 + t
+                sched[tag] = a
+                O.ocq_server_submit(srv, st["cam"], st["frames"][wl.N + t % pool], st["masks"][t % mask_slots], tag)
+                progressed = True
+            for _cam, _frame, tag, _arr, done_s in O.ocq_server_poll(srv, 8192):
+                i = tag // 100000
+                lat.append(done_s - base - sched.pop(tag))
+                st = live[i]
+                st["completed"] += 1
+                px_done += streams[i].wl.H * streams[i].wl.W
+                if st["completed"] == frames_per_camera:
+                    O.ocq_server_release(srv, st["cam"])
+                    del live[i]
+                    done_cams += 1
+                progressed = True
+            if not progressed:
+                time.sleep(0.0002)
+        wall = time.monotonic() - base
+        O.ocq_server_sync(srv)
+    finally:
+        srv.destroy()
+    torch.cuda.empty_cache()
+    lat_ms = sorted(x * 1e3 for x in lat)
+
+    def pct(q):
+        return round(lat_ms[min(len(lat_ms) - 1, int(q * len(lat_ms)))], 3) if lat_ms else None
+
+    return {"preset": "serve256_poisson_30fps", "cameras": n_cameras, "cameras_done": done_cams,
+            "cameras_never_fit": rejected, "frames_done": len(lat_ms),
+            "frames_offered": n_cameras * frames_per_camera, "wall_s": round(wall, 2),
+            "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": round(lat_ms[-1], 3) if lat_ms else None,
+            "mpixel_s": round(px_done / wall / 1e6, 1), "hbm_budget_bytes": budget, "peak_reserved_bytes": peak_used,
+            "admission_delay_p99_s": round(sorted(delays)[int(0.99 * (len(delays) - 1))], 3) if delays else None,
+            "window_N": 30, "remerge_every_K": 30, "T": 10}
 
 
 def e2e_measure(ocq, wl, train, test, mask, stream, args, dist, dev, world):

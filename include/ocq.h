@@ -203,6 +203,63 @@ ocq_status ocq_batch_autotune(ocq_batch *batch, int reps, void *stream);
 void ocq_batch_destroy(ocq_batch *batch);
 
 /*
+ * Served form.  The paper names "octree updation" (Sec. 4) without giving a
+ * procedure; this library's reading is a sliding window: the N training
+ * frames build M_0; test frame t (t = 0, 1, ...) is classified against
+ * M_floor(t/K); after classification it enters a ring of the last N frames;
+ * when (t+1) % K == 0 the ring is merged again (Alg. 2) into the next model.
+ * M_k therefore equals ocq_build_model over global frames [kK, kK + N - 1].
+ * A camera's model and ring stay in HBM from admission to release.  Each
+ * camera's work is ordered on its own CUDA stream and cameras run
+ * concurrently: frames that arrive while others are on the GPU are enqueued
+ * at once and their work overlaps.  Admission reserves the camera's
+ * footprint (ocq_server_camera_footprint) against the server's HBM budget and
+ * returns OCQ_EBUSY when slots or budget are exhausted; release returns them.
+ * One thread submits for a given camera; different cameras may use
+ * different threads.  Frame and mask buffers are the caller's (device) and
+ * must stay valid until the frame's completion is polled.  The camera's work
+ * runs on a stream of its own that does not wait on the caller's streams: a
+ * training or test frame must already be complete on the device when it is
+ * passed in (synchronise the stream that produced it first).
+ */
+typedef struct {
+  int H, W;
+  ocq_region region;
+  int depth, T;
+  int N; /* training frames = window length */
+  int K; /* re-merge period in test frames */
+} ocq_camera_desc;
+
+typedef struct {
+  int32_t camera;
+  int32_t reserved;
+  int64_t frame;    /* test frame index t of the camera */
+  uint64_t tag;     /* caller's tag from ocq_server_submit */
+  double arrival_s; /* host steady clock, seconds, at submit */
+  double done_s;    /* host steady clock when the frame's mask (and any re-merge) was done */
+} ocq_completion;
+
+typedef struct ocq_server ocq_server;
+
+ocq_status ocq_server_create(size_t hbm_budget, int max_cameras, ocq_server **out);
+/* Device bytes a camera of this description reserves (0 if invalid). */
+size_t ocq_server_camera_footprint(const ocq_camera_desc *desc);
+/* train: device, N*H*W*3 (copied into the ring; M_0 is built from it). */
+ocq_status ocq_server_admit(ocq_server *server, const ocq_camera_desc *desc, const uint8_t *train, int *camera);
+/* frame: device, H*W*3; mask: device, H*W (1 = foreground).  Non-blocking. */
+ocq_status ocq_server_submit(ocq_server *server, int camera, const uint8_t *frame, uint8_t *mask, uint64_t tag);
+/* Up to max completed frames, oldest first; *n receives the count. */
+ocq_status ocq_server_poll(ocq_server *server, ocq_completion *out, int max, int *n);
+/* Waits for the camera's frames, frees its ring and model, returns its budget. */
+ocq_status ocq_server_release(ocq_server *server, int camera);
+/* The camera's current model (owned by the server; valid until the next re-merge or release). */
+ocq_status ocq_server_camera_model(const ocq_server *server, int camera, const ocq_model **out);
+ocq_status ocq_server_usage(ocq_server *server, size_t *used, size_t *budget, int64_t *completed);
+/* Waits for every live camera's enqueued work. */
+ocq_status ocq_server_sync(ocq_server *server);
+void ocq_server_destroy(ocq_server *server);
+
+/*
  * Tuning interface (no counterpart in the paper; it selects between kernel
  * variants that compute identical results).  `kernel` names a tunable kernel:
  *   OCQ_TUNE_CLASSIFY_PIXEL  per-pixel classify, depth <= 3; params =

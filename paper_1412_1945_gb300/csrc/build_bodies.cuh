@@ -1,7 +1,8 @@
 // Device bodies of the build kernels (S2-S3, Alg. 1-2), parameterised by a
 // virtual CTA index (vb of vg) so the same code runs as a plain grid and as an
 // item of the batched persistent kernel.  Scratch written earlier in the same
-// launch (per-frame leaf bitsets) is read through L2 (ld.global.cg).
+// launch (per-frame leaf bitsets) is read with ordinary coherent loads, after
+// the reader's acquire (counter wait + fence).
 #pragma once
 
 #include <cuda.h>
@@ -91,14 +92,14 @@ __device__ __forceinline__ void occ_global_body(const uint8_t *__restrict__ fram
 
 // Folds nb frames of occupancy words into bit-sliced counters; on the last
 // batch writes count >= T into the model.
-__device__ __forceinline__ void planes_merge_body(const uint32_t *__restrict__ occ, int nb, int64_t nwords,
+__device__ __forceinline__ void planes_merge_body(const uint32_t *occ, int nb, int64_t nwords,
                                                   uint32_t *__restrict__ planes, int P, int first, int last,
                                                   uint32_t T, uint32_t *__restrict__ model, int64_t vb, int64_t vg) {
   for (int64_t w = vb * blockDim.x + threadIdx.x; w < nwords; w += vg * blockDim.x) {
     uint32_t pl[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) pl[k] = (!first && k < P) ? planes[k * nwords + w] : 0u;
-    for (int f = 0; f < nb; ++f) planes_add_reg<16>(pl, P, __ldcg(occ + f * nwords + w));
+    for (int f = 0; f < nb; ++f) planes_add_reg<16>(pl, P, occ[f * nwords + w]);
     if (last) {
       model[w] = planes_ge_reg<16>(pl, P, T);
     } else {

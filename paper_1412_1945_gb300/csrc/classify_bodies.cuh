@@ -1,8 +1,9 @@
 // Device bodies of the classify kernels (S4, Alg. 3), parameterised by a
 // virtual CTA index vb of vg so that the same code runs as a plain grid
 // (vb = blockIdx.x, vg = gridDim.x) and as an item of the batched persistent
-// kernel.  Model words are read through L2 (ld.global.cg): in the batched
-// kernel a model may have been written earlier in the same launch.
+// kernel.  Model words are read with ordinary (coherent, not read-only-path)
+// loads: in the batched kernel a model is written earlier in the same launch,
+// and its readers start only after an acquire (counter wait + fence).
 #pragma once
 
 #include "async_copy.cuh"
@@ -12,7 +13,7 @@ namespace ocq {
 
 // ---- generic ---------------------------------------------------------------------
 __device__ __forceinline__ void classify_generic_body(const uint8_t *__restrict__ frames, int F, int H, int W, int kind, int block,
-                                        int d, int64_t wpr, const uint32_t *__restrict__ model,
+                                        int d, int64_t wpr, const uint32_t *model,
                                         uint8_t *__restrict__ mask, int64_t pb, int64_t pe,
                                                      int64_t vb, int64_t vg) {
   const int64_t hw = (int64_t)H * W;
@@ -26,7 +27,7 @@ __device__ __forceinline__ void classify_generic_body(const uint8_t *__restrict_
     const uint8_t *px = frames + g * 3;
     const uint32_t q = planar_code_rt(__ldg(px), __ldg(px + 1), __ldg(px + 2), d);
     const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
-    const uint32_t word = __ldcg(model + region_of(y, x, W, kind, block, bw) * wpr + (q >> 5));
+    const uint32_t word = *(model + region_of(y, x, W, kind, block, bw) * wpr + (q >> 5));
     mask[g] = (uint8_t)(((word >> (q & 31)) & 1u) ^ 1u);
   }
 }
@@ -42,12 +43,12 @@ __device__ __forceinline__ uint32_t pack_mask4(uint32_t f0, uint32_t f1, uint32_
 // ---- whole-frame regions ------------------------------------------------------------
 template <int D>
 __device__ __forceinline__ void classify_frame_body(const uint8_t *__restrict__ frames, int64_t npix,
-                                                    const uint32_t *__restrict__ model, uint8_t *__restrict__ mask,
+                                                    const uint32_t *model, uint8_t *__restrict__ mask,
                                                     int64_t vb, int64_t vg) {
   constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
   constexpr int REP = D <= 4 ? 32 : 1;
   extern __shared__ uint32_t row[];  // [WPR][REP]
-  for (int i = threadIdx.x; i < WPR * REP; i += blockDim.x) row[i] = __ldcg(model + i / REP);
+  for (int i = threadIdx.x; i < WPR * REP; i += blockDim.x) row[i] = model[i / REP];
   __syncthreads();
   const int rep = REP == 32 ? (threadIdx.x & 31) : 0;
   const bool vec = ((reinterpret_cast<uintptr_t>(frames) | reinterpret_cast<uintptr_t>(mask)) & 15) == 0;
@@ -156,7 +157,7 @@ __device__ __forceinline__ size_t classify_pixel_ws_bars() {
 
 template <int D, int NW, int PPT, int S, int FPS>
 __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict__ frames, int F, int64_t hw,
-                                                       int64_t ntiles, const uint32_t *__restrict__ model,
+                                                       int64_t ntiles, const uint32_t *model,
                                                        uint8_t *__restrict__ mask, int64_t vb, int64_t vg,
                                                        unsigned int *timeout_flag) {
   using C = TiledCfg<D, NW, PPT, S, FPS>;
@@ -225,12 +226,12 @@ __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict
     const int64_t p_tile = tile * C::TILE;
     named_sync(1, NW * 32);  // every warp is done with the previous tile's rows
     {
-      const uint32_t *src = model + (p_tile + (int64_t)tid * PPT) * C::WPR;  // read through L2 (may be fresh)
+      const uint32_t *src = model + (p_tile + (int64_t)tid * PPT) * C::WPR;
       if constexpr (C::WPR % 4 == 0) {
         const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
 #pragma unroll 4
         for (int i = 0; i < PPT * C::WPR / 4; ++i) {
-          const uint4 v = __ldcg(s4 + i);
+          const uint4 v = s4[i];
           const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
@@ -242,7 +243,7 @@ __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict
 #pragma unroll
         for (int idx = 0; idx < PPT * C::WPR; ++idx) {
           const int j = idx / C::WPR, w = idx % C::WPR;
-          msm[((warp * PPT + j) * C::WPR + w) * 32 + lane] = __ldcg(src + idx);
+          msm[((warp * PPT + j) * C::WPR + w) * 32 + lane] = src[idx];
         }
       }
     }
@@ -285,7 +286,7 @@ __host__ __device__ __forceinline__ size_t classify_block_ws_rows_bytes(int b, i
 template <int D, int S, int FPS>
 __device__ __forceinline__ void classify_block_ws_body(const uint8_t *__restrict__ frames, int F, int H, int W, int b,
                                                        int wt, int ntx, int64_t ntiles,
-                                                       const uint32_t *__restrict__ model,
+                                                       const uint32_t *model,
                                                        uint8_t *__restrict__ mask, int64_t vb, int64_t vg,
                                                        unsigned int *timeout_flag) {
   constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
@@ -365,7 +366,7 @@ __device__ __forceinline__ void classify_block_ws_body(const uint8_t *__restrict
     named_sync(1, 128);
     for (int i = tid; i < nblk * WPR; i += 128) {
       const int j = i / WPR, w = i % WPR;
-      rows[i] = __ldcg(model + ((int64_t)ty * bw + (x0 / b) + j) * WPR + w);
+      rows[i] = *(model + ((int64_t)ty * bw + (x0 / b) + j) * WPR + w);
     }
     named_sync(1, 128);
     const bool act = tid < bh * gpr;

@@ -1,0 +1,263 @@
+// Served form: camera streams join and leave while frames arrive; each
+// camera's model and its sliding window of the last N frames stay resident
+// in HBM.  The paper names "octree updation" (Sec. 4) without a procedure; the
+// window semantics here are:
+//   * the N training frames build M_0 (Sec. 3, Alg. 1-2);
+//   * test frame t (t = 0, 1, ...) is classified against M_floor(t/K) (Alg. 3);
+//   * after classification frame t enters a ring of the last N frames;
+//   * when (t+1) % K == 0 the ring is merged again: M_(t+1)/K = merge(ring).
+// So M_k is the merged model of global frames [kK, kK+N-1] (training frames
+// first).  All of a camera's work is ordered on its own CUDA stream; cameras
+// run concurrently, so work of frames that arrive while others are on the GPU
+// overlaps on the device.  Admission reserves a camera's footprint (ring,
+// model, the model being rebuilt, build scratch) against an HBM budget and
+// returns OCQ_EBUSY when it does not fit; released cameras return their
+// share.  Completion times are taken by a host function enqueued after each
+// frame's work.
+#include <chrono>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "ocq_internal.cuh"
+
+namespace ocq {
+
+static double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Camera;
+
+struct Pending {
+  struct ocq_server *srv;
+  int camera;
+  int64_t frame;
+  uint64_t tag;
+  double arrival;
+};
+
+struct Camera {
+  int id = -1;
+  ocq_camera_desc d;
+  size_t footprint = 0;
+  uint8_t *ring = nullptr;  // N frames (HWC RGB8), slot = frame % N
+  ocq_model *model = nullptr;
+  cudaStream_t stream = nullptr;
+  int64_t submitted = 0;    // test frames submitted so far
+  bool live = false;
+};
+
+}  // namespace ocq
+
+using namespace ocq;
+
+struct ocq_server {
+  size_t budget = 0, used = 0;
+  int max_cameras = 0;
+  std::mutex mu;
+  std::vector<Camera> cams;
+  std::deque<ocq_completion> done;
+  int64_t completed = 0;
+};
+
+static size_t camera_footprint(const ocq_camera_desc &d) {
+  const size_t hw = (size_t)d.H * d.W;
+  const size_t model = ocq_model_footprint(d.H, d.W, d.region, d.depth);
+  const size_t ring = (size_t)d.N * hw * 3;
+  size_t scratch = 0;
+  if (d.region.kind == OCQ_REGION_FRAME) scratch = (size_t)d.N * wpr32(d.depth) * 4;
+  if (d.region.kind == OCQ_REGION_PIXEL && d.depth >= 6) scratch = hw * ((size_t)1 << (3 * d.depth - 9)) / 8;
+  return 2 * model + ring + scratch;  // the model being rebuilt lives beside the current one
+}
+
+static void CUDART_CB on_frame_done(void *arg) {
+  Pending *p = static_cast<Pending *>(arg);
+  {
+    std::lock_guard<std::mutex> lock(p->srv->mu);
+    ocq_completion c;
+    c.camera = p->camera;
+    c.frame = p->frame;
+    c.tag = p->tag;
+    c.arrival_s = p->arrival;
+    c.done_s = now_s();
+    p->srv->done.push_back(c);
+    p->srv->completed++;
+  }
+  delete p;
+}
+
+extern "C" {
+
+ocq_status ocq_server_create(size_t hbm_budget, int max_cameras, ocq_server **out) {
+  if (!out || max_cameras < 1) {
+    set_error("ocq_server_create: need out and max_cameras >= 1");
+    return OCQ_EINVAL;
+  }
+  ocq_server *s = new (std::nothrow) ocq_server();
+  if (!s) return OCQ_ENOMEM;
+  s->budget = hbm_budget;
+  s->max_cameras = max_cameras;
+  s->cams.resize(max_cameras);
+  *out = s;
+  return OCQ_OK;
+}
+
+size_t ocq_server_camera_footprint(const ocq_camera_desc *d) {
+  if (!d || ocq_model_footprint(d->H, d->W, d->region, d->depth) == 0 || d->N < 1) return 0;
+  return camera_footprint(*d);
+}
+
+ocq_status ocq_server_admit(ocq_server *s, const ocq_camera_desc *d, const uint8_t *train, int *camera) {
+  if (!s || !d || !train || !camera || d->N < 1 || d->N > 65535 || d->T < 1 || d->T > d->N || d->K < 1 ||
+      ocq_model_footprint(d->H, d->W, d->region, d->depth) == 0) {
+    set_error("ocq_server_admit: bad camera description");
+    return OCQ_EINVAL;
+  }
+  const size_t fp = camera_footprint(*d);
+  int slot = -1;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (int i = 0; i < s->max_cameras; ++i)
+      if (!s->cams[i].live) {
+        slot = i;
+        break;
+      }
+    if (slot < 0 || s->used + fp > s->budget) {
+      set_error("ocq_server_admit: no room (slots or HBM budget) for %zu bytes", fp);
+      return OCQ_EBUSY;
+    }
+    s->used += fp;
+    s->cams[slot].live = true;
+  }
+  Camera &c = s->cams[slot];
+  c.id = slot;
+  c.d = *d;
+  c.footprint = fp;
+  c.submitted = 0;
+  ocq_status rc = cuda_status(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "camera stream");
+  const size_t ring = (size_t)d->N * d->H * d->W * 3;
+  if (rc == OCQ_OK) rc = cuda_status(cudaMallocAsync((void **)&c.ring, ring, c.stream), "camera ring");
+  if (rc == OCQ_OK) rc = cuda_status(cudaMemcpyAsync(c.ring, train, ring, cudaMemcpyDeviceToDevice, c.stream), "ring fill");
+  if (rc == OCQ_OK) rc = ocq_build_model(c.ring, d->N, d->H, d->W, d->region, d->depth, d->T, c.stream, &c.model);
+  if (rc != OCQ_OK) {
+    if (c.ring) cudaFreeAsync(c.ring, c.stream);
+    if (c.stream) cudaStreamSynchronize(c.stream), cudaStreamDestroy(c.stream);
+    c.ring = nullptr, c.stream = nullptr;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->used -= fp;
+    c.live = false;
+    return rc;
+  }
+  *camera = slot;
+  return OCQ_OK;
+}
+
+ocq_status ocq_server_submit(ocq_server *s, int camera, const uint8_t *frame, uint8_t *mask, uint64_t tag) {
+  if (!s || camera < 0 || camera >= s->max_cameras || !s->cams[camera].live || !frame || !mask) {
+    set_error("ocq_server_submit: bad camera or buffers");
+    return OCQ_EINVAL;
+  }
+  Camera &c = s->cams[camera];
+  const double arrival = now_s();
+  const int64_t t = c.submitted++;
+  const size_t fbytes = (size_t)c.d.H * c.d.W * 3;
+  ocq_status rc = ocq_classify(c.model, frame, 1, mask, c.stream);
+  if (rc == OCQ_OK)
+    rc = cuda_status(cudaMemcpyAsync(c.ring + (size_t)((c.d.N + t) % c.d.N) * fbytes, frame, fbytes,
+                                     cudaMemcpyDeviceToDevice, c.stream),
+                     "ring push");
+  if (rc == OCQ_OK && (t + 1) % c.d.K == 0) {
+    ocq_model *next = nullptr;
+    rc = ocq_build_model(c.ring, c.d.N, c.d.H, c.d.W, c.d.region, c.d.depth, c.d.T, c.stream, &next);
+    if (rc == OCQ_OK) {
+      ocq_model_free(c.model);  // stream-ordered: frames already enqueued keep the old model
+      c.model = next;
+    }
+  }
+  if (rc != OCQ_OK) return rc;
+  Pending *p = new (std::nothrow) Pending{s, camera, t, tag, arrival};
+  if (!p) return OCQ_ENOMEM;
+  rc = cuda_status(cudaLaunchHostFunc(c.stream, on_frame_done, p), "completion callback");
+  if (rc != OCQ_OK) delete p;
+  return rc;
+}
+
+ocq_status ocq_server_poll(ocq_server *s, ocq_completion *out, int max, int *n) {
+  if (!s || !n || max < 0 || (max > 0 && !out)) {
+    set_error("ocq_server_poll: bad arguments");
+    return OCQ_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  int k = 0;
+  while (k < max && !s->done.empty()) {
+    out[k++] = s->done.front();
+    s->done.pop_front();
+  }
+  *n = k;
+  return OCQ_OK;
+}
+
+ocq_status ocq_server_release(ocq_server *s, int camera) {
+  if (!s || camera < 0 || camera >= s->max_cameras || !s->cams[camera].live) {
+    set_error("ocq_server_release: bad camera");
+    return OCQ_EINVAL;
+  }
+  Camera &c = s->cams[camera];
+  ocq_model_free(c.model);
+  cudaFreeAsync(c.ring, c.stream);
+  cudaError_t e = cudaStreamSynchronize(c.stream);  // its frames finish; its memory is returned
+  cudaStreamDestroy(c.stream);
+  c.model = nullptr, c.ring = nullptr, c.stream = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->used -= c.footprint;
+    c.live = false;
+  }
+  return cuda_status(e, "camera release");
+}
+
+ocq_status ocq_server_camera_model(const ocq_server *s, int camera, const ocq_model **out) {
+  if (!s || !out || camera < 0 || camera >= s->max_cameras || !s->cams[camera].live) {
+    set_error("ocq_server_camera_model: bad camera");
+    return OCQ_EINVAL;
+  }
+  *out = s->cams[camera].model;
+  return OCQ_OK;
+}
+
+ocq_status ocq_server_usage(ocq_server *s, size_t *used, size_t *budget, int64_t *completed) {
+  if (!s) {
+    set_error("ocq_server_usage: NULL server");
+    return OCQ_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (used) *used = s->used;
+  if (budget) *budget = s->budget;
+  if (completed) *completed = s->completed;
+  return OCQ_OK;
+}
+
+ocq_status ocq_server_sync(ocq_server *s) {
+  if (!s) {
+    set_error("ocq_server_sync: NULL server");
+    return OCQ_EINVAL;
+  }
+  for (Camera &c : s->cams)
+    if (c.live) {
+      cudaError_t e = cudaStreamSynchronize(c.stream);
+      if (e != cudaSuccess) return cuda_status(e, "server sync");
+    }
+  return OCQ_OK;
+}
+
+void ocq_server_destroy(ocq_server *s) {
+  if (!s) return;
+  for (int i = 0; i < s->max_cameras; ++i)
+    if (s->cams[i].live) ocq_server_release(s, i);
+  delete s;
+}
+
+}  // extern "C"

@@ -50,6 +50,16 @@ class ocq_stream_desc(ctypes.Structure):
                 ("F", ctypes.c_int), ("mask", ctypes.c_void_p)]
 
 
+class ocq_camera_desc(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("region", ocq_region), ("depth", ctypes.c_int),
+                ("T", ctypes.c_int), ("N", ctypes.c_int), ("K", ctypes.c_int)]
+
+
+class ocq_completion(ctypes.Structure):
+    _fields_ = [("camera", ctypes.c_int32), ("reserved", ctypes.c_int32), ("frame", ctypes.c_int64),
+                ("tag", ctypes.c_uint64), ("arrival_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
 # name -> (restype, argtypes)
 _vp, _i32, _i64, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
 SIGNATURES = {
@@ -79,6 +89,16 @@ SIGNATURES = {
     "ocq_batch_get_work": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "ocq_batch_autotune": (_i32, [_vp, _i32, _vp]),
     "ocq_batch_destroy": (None, [_vp]),
+    "ocq_server_create": (_i32, [_sz, _i32, ctypes.POINTER(_vp)]),
+    "ocq_server_camera_footprint": (_sz, [ctypes.POINTER(ocq_camera_desc)]),
+    "ocq_server_admit": (_i32, [_vp, ctypes.POINTER(ocq_camera_desc), _vp, ctypes.POINTER(_i32)]),
+    "ocq_server_submit": (_i32, [_vp, _i32, _vp, _vp, ctypes.c_uint64]),
+    "ocq_server_poll": (_i32, [_vp, ctypes.POINTER(ocq_completion), _i32, ctypes.POINTER(_i32)]),
+    "ocq_server_release": (_i32, [_vp, _i32]),
+    "ocq_server_camera_model": (_i32, [_vp, _i32, ctypes.POINTER(_vp)]),
+    "ocq_server_usage": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_i64)]),
+    "ocq_server_sync": (_i32, [_vp]),
+    "ocq_server_destroy": (None, [_vp]),
     "ocq_tune_count": (_i32, [_i32]),
     "ocq_tune_selected": (_i32, [_i32]),
     "ocq_tune_select": (_i32, [_i32, _i32]),
@@ -343,3 +363,82 @@ def ocq_batch_autotune(batch, reps=2, stream=None):
 
 def ocq_batch_destroy(batch):
     batch.destroy()
+
+
+class Server:
+    """Owns an ``ocq_server*`` (served form)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def destroy(self):
+        if self.handle:
+            load().ocq_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def _camera(H, W, kind, block, depth, T, N, K):
+    return ocq_camera_desc(H, W, _region(kind, block), depth, T, N, K)
+
+
+def ocq_server_create(hbm_budget, max_cameras) -> Server:
+    out = ctypes.c_void_p()
+    _check(load().ocq_server_create(hbm_budget, max_cameras, ctypes.byref(out)))
+    return Server(out.value)
+
+
+def ocq_server_camera_footprint(H, W, kind, block, depth, T, N, K) -> int:
+    d = _camera(H, W, kind, block, depth, T, N, K)
+    return int(load().ocq_server_camera_footprint(ctypes.byref(d)))
+
+
+def ocq_server_admit(server, H, W, kind, block, depth, T, N, K, train):
+    """Returns the camera id, or None when the server answers OCQ_EBUSY."""
+    d = _camera(H, W, kind, block, depth, T, N, K)
+    cam = ctypes.c_int()
+    rc = load().ocq_server_admit(server.handle, ctypes.byref(d), _p(train), ctypes.byref(cam))
+    if rc == OCQ_EBUSY:
+        return None
+    _check(rc)
+    return cam.value
+
+
+def ocq_server_submit(server, camera, frame, mask, tag=0):
+    _check(load().ocq_server_submit(server.handle, camera, _p(frame), _p(mask), tag))
+
+
+def ocq_server_poll(server, max_n=4096):
+    buf = (ocq_completion * max_n)()
+    n = ctypes.c_int()
+    _check(load().ocq_server_poll(server.handle, buf, max_n, ctypes.byref(n)))
+    return [(c.camera, c.frame, c.tag, c.arrival_s, c.done_s) for c in buf[:n.value]]
+
+
+def ocq_server_release(server, camera):
+    _check(load().ocq_server_release(server.handle, camera))
+
+
+def ocq_server_camera_model(server, camera) -> Model:
+    out = ctypes.c_void_p()
+    _check(load().ocq_server_camera_model(server.handle, camera, ctypes.byref(out)))
+    return _View(out.value)
+
+
+def ocq_server_usage(server):
+    u, b, c = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int64()
+    _check(load().ocq_server_usage(server.handle, ctypes.byref(u), ctypes.byref(b), ctypes.byref(c)))
+    return u.value, b.value, c.value
+
+
+def ocq_server_sync(server):
+    _check(load().ocq_server_sync(server.handle))
+
+
+def ocq_server_destroy(server):
+    server.destroy()
