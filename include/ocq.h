@@ -274,12 +274,16 @@ void ocq_server_destroy(ocq_server *server);
  *                             4 as 2 with a dedicated copy warp; 5 as 4 with one 2-D
  *                             tensor copy per stage; 6 as 4 setting kept bits as
  *                             counts reach T; 7 as 5 and 6 together}
+ *   OCQ_TUNE_CLASSIFY_PIXEL_DEEP per-pixel classify, depth >= 4 (a warp walks
+ *                            all frames of its pixel locations); params =
+ *                            {pixel locations per lane (1 or 4), frames prefetched,
+ *                             CTAs of 4 warps resident per SM, 0, 0}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5
  * int32 parameters (n >= 5).
  */
-enum { OCQ_TUNE_CLASSIFY_PIXEL = 0, OCQ_TUNE_BUILD_PIXEL = 1 };
+enum { OCQ_TUNE_CLASSIFY_PIXEL = 0, OCQ_TUNE_BUILD_PIXEL = 1, OCQ_TUNE_CLASSIFY_PIXEL_DEEP = 2 };
 int ocq_tune_count(int kernel);
 int ocq_tune_selected(int kernel);
 ocq_status ocq_tune_select(int kernel, int variant);

@@ -251,12 +251,14 @@ ocq_status ocq_device_status(void *stream) {
 int ocq_tune_count(int kernel) {
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL) return classify_variant_count();
   if (kernel == OCQ_TUNE_BUILD_PIXEL) return build_variant_count();
+  if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) return deep_variant_count();
   return -1;
 }
 
 int ocq_tune_selected(int kernel) {
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL) return classify_variant_selected();
   if (kernel == OCQ_TUNE_BUILD_PIXEL) return build_variant_selected();
+  if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) return deep_variant_selected();
   return -1;
 }
 
@@ -265,6 +267,7 @@ ocq_status ocq_tune_select(int kernel, int variant) {
   bool ok = false;
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL) ok = classify_variant_select(variant);
   if (kernel == OCQ_TUNE_BUILD_PIXEL) ok = build_variant_select(variant);
+  if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) ok = deep_variant_select(variant);
   if (!ok) {
     set_error("ocq_tune_select: no variant %d of kernel %d", variant, kernel);
     return OCQ_EINVAL;
@@ -281,8 +284,10 @@ ocq_status ocq_tune_describe(int kernel, int variant, int32_t *params, int n) {
   params[0] = params[1] = params[2] = params[3] = params[4] = 0;
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL)
     classify_variant_describe(variant, &params[0], &params[1], &params[2], &params[3], &params[4]);
-  else
+  else if (kernel == OCQ_TUNE_BUILD_PIXEL)
     build_variant_describe(variant, &params[0], &params[1], &params[2], &params[3]);
+  else
+    deep_variant_describe(variant, &params[0], &params[1], &params[2]);
   return OCQ_OK;
 }
 

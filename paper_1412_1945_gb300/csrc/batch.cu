@@ -32,13 +32,15 @@ enum : int32_t {
   OP_OCC_FRAME = 0,    // occ_frame_body           (whole frame, depth <= 6)
   OP_OCC_GLOBAL,       // occ_global_body          (whole frame, depth >= 7)
   OP_MERGE,            // planes_merge_body        (whole frame)
-  OP_BUILD_BLOCK,      // build_block_body         (blocks, depth <= 5)
+  OP_BUILD_BLOCK,      // build_block_body         (blocks, depth <= 5, b > 16)
+  OP_BUILD_BLOCK_WARP, // build_block_warp_body    (blocks, depth <= 5, b <= 16): regions [vb, aux)
   OP_BUILD_PIXEL_WS,   // build_pixel_ws_body      (pixels, depth <= 3, aligned)
   OP_BUILD_PIXEL_CNT,  // build_pixel_counters_body (pixels, depth <= 3, remainder / unaligned)
-  OP_BUILD_PIXEL_CHK,  // build_pixel_chunked_body (pixels, depth 4-5)
+  OP_BUILD_PIXEL_MG,   // build_pixel_mg_body      (pixels, depth 4-5): 32-pixel tiles [vb, aux)
   OP_CLS_FRAME,        // classify_frame_body      (whole frame, depth <= 6)
   OP_CLS_PIXEL_WS,     // classify_pixel_ws_body   (pixels, depth <= 3, aligned)
   OP_CLS_BLOCK_WS,     // classify_block_ws_body   (blocks, b % 8 == 0, W % 16 == 0)
+  OP_CLS_PIXEL_TB,     // classify_pixel_tb_body   (pixels, depth 4-5, H*W % 4 == 0): 128-pixel tiles [vb, aux)
   OP_CLS_GENERIC       // classify_generic_body    (everything else, and remainders)
 };
 
@@ -56,7 +58,9 @@ struct BStream {
   int32_t n_build;     // items that complete the model
   int32_t n_occ;       // occupancy items (whole frame)
   int32_t occ_nbx;     // pixel chunks per frame in occupancy items
-  int32_t pad;
+  int32_t ppl;         // block build, one warp per region: pixels per lane (0: CTA per region)
+  int32_t km;          // pixel build, depth 4-5: candidate counters (0: count every distinct leaf)
+  int32_t tb;          // pixel classify, depth 4-5: 1 if the tiled body applies
 };
 
 struct BItem {
@@ -88,6 +92,75 @@ __device__ __forceinline__ void mbar_inval(uint32_t bar) {
   asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// The warp-granular bodies run as calls of their own (one call site each), so
+// that their unrolled register arrays do not share one frame with every other
+// inlined body.
+template <int D, int PPL>
+__device__ __forceinline__ void block_warp_item(const BStream &S, int64_t r0, int64_t r1, uint32_t *tab) {
+  build_block_warp_body<D, PPL>(S.train, S.N, S.H, S.W, S.block, S.bw, (uint32_t)S.T, S.model, r0, r1,
+                                kBatchThreads / 32, tab);
+}
+
+template <int D>
+__device__ __forceinline__ void block_warp_item_d(const BStream &S, int64_t r0, int64_t r1, uint8_t *smem) {
+  constexpr int TS = WarpTableCfg<D>::S;
+  uint32_t *tab = reinterpret_cast<uint32_t *>(smem) + (threadIdx.x >> 5) * TS;
+  for (int i = threadIdx.x & 31; i < TS; i += 32) tab[i] = 0u;
+  __syncwarp();
+  switch (S.ppl) {
+    case 1: block_warp_item<D, 1>(S, r0, r1, tab); break;
+    case 2: block_warp_item<D, 2>(S, r0, r1, tab); break;
+    case 4: block_warp_item<D, 4>(S, r0, r1, tab); break;
+    default: block_warp_item<D, 8>(S, r0, r1, tab); break;
+  }
+}
+
+__device__ __noinline__ void block_warp_dispatch(const BStream &S, int64_t r0, int64_t r1, uint8_t *smem) {
+  switch (S.depth) {
+    case 1: block_warp_item_d<1>(S, r0, r1, smem); break;
+    case 2: block_warp_item_d<2>(S, r0, r1, smem); break;
+    case 3: block_warp_item_d<3>(S, r0, r1, smem); break;
+    case 4: block_warp_item_d<4>(S, r0, r1, smem); break;
+    default: block_warp_item_d<5>(S, r0, r1, smem); break;
+  }
+}
+
+template <int D, int KM>
+__device__ __forceinline__ void pixel_mg_item(const BStream &S, int64_t t0, int64_t t1, uint8_t *smem) {
+  leaf_t<D> *codes = reinterpret_cast<leaf_t<D> *>(smem) + (size_t)(threadIdx.x >> 5) * S.N * 32;
+  for (int64_t t = t0; t < t1; t += kBatchThreads / 32) {
+    build_pixel_mg_body<D, KM>(S.train, S.N, S.hw, (uint32_t)S.T, S.model, t, codes);
+    __syncwarp();
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void pixel_mg_item_d(const BStream &S, int64_t t0, int64_t t1, uint8_t *smem) {
+  switch (S.km) {
+    case 1: pixel_mg_item<D, 1>(S, t0, t1, smem); break;
+    case 2: pixel_mg_item<D, 2>(S, t0, t1, smem); break;
+    case 4: pixel_mg_item<D, 4>(S, t0, t1, smem); break;
+    case 8: pixel_mg_item<D, 8>(S, t0, t1, smem); break;
+    default: pixel_mg_item<D, 0>(S, t0, t1, smem); break;
+  }
+}
+
+__device__ __noinline__ void pixel_mg_dispatch(const BStream &S, int64_t t0, int64_t t1, uint8_t *smem) {
+  if (S.depth == 4)
+    pixel_mg_item_d<4>(S, t0, t1, smem);
+  else
+    pixel_mg_item_d<5>(S, t0, t1, smem);
+}
+
+__device__ __noinline__ void pixel_tb_dispatch(const BStream &S, int64_t t0, int64_t t1) {
+  for (int64_t t = t0; t < t1; t += kBatchThreads / 32) {
+    if (S.depth == 4)
+      classify_pixel_tb_body<4, 8>(S.test, S.F, S.hw, S.model, S.mask, t);
+    else
+      classify_pixel_tb_body<5, 8>(S.test, S.F, S.hw, S.model, S.mask, t);
+  }
+}
+
 template <int D>
 __device__ __forceinline__ void run_item_d(const BStream &S, const BItem &it, uint32_t *err, uint8_t *smem) {
   const uint32_t T = (uint32_t)S.T;
@@ -109,9 +182,6 @@ __device__ __forceinline__ void run_item_d(const BStream &S, const BItem &it, ui
       break;
     case OP_BUILD_PIXEL_CNT:
       if constexpr (D <= 3) build_pixel_counters_body<D, false>(S.train, S.N, S.hw, it.aux, T, S.model, it.vb);
-      break;
-    case OP_BUILD_PIXEL_CHK:
-      if constexpr (D >= 4 && D <= 5) build_pixel_chunked_body<D>(S.train, S.N, S.hw, T, S.model, nullptr, it.vb);
       break;
     case OP_CLS_FRAME:
       if constexpr (D <= 6) classify_frame_body<D>(S.test, (int64_t)S.F * S.hw, S.model, S.mask, it.vb, it.vg);
@@ -146,6 +216,15 @@ __device__ void run_item(const BStream &S, const BItem &it, uint32_t *err, uint8
       return;
     case OP_MERGE:
       planes_merge_body(S.occ, S.N, S.wpr, nullptr, S.P, 1, 1, (uint32_t)S.T, S.model, it.vb, it.vg);
+      return;
+    case OP_BUILD_BLOCK_WARP:
+      block_warp_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux, smem);
+      return;
+    case OP_BUILD_PIXEL_MG:
+      pixel_mg_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux, smem);
+      return;
+    case OP_CLS_PIXEL_TB:
+      pixel_tb_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux);
       return;
     case OP_CLS_GENERIC:
       classify_generic_body(S.test, S.F, S.H, S.W, S.kind, S.block, S.depth, S.wpr, S.model, S.mask, it.aux, S.hw,
@@ -205,7 +284,10 @@ static size_t item_smem(const BStream &h) {
   if (h.kind == OCQ_REGION_FRAME) {
     if (d <= 6) need = std::max<size_t>(need, (size_t)h.wpr * 4 * (d <= 4 ? 32 : 1));  // occ row / replicated row
   } else if (h.kind == OCQ_REGION_BLOCK) {
-    need = std::max<size_t>(need, (size_t)h.wpr * (h.P + 2) * 4);
+    if (h.ppl > 0)
+      need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * std::min(1 << (3 * d), 1024) * 4);
+    else
+      need = std::max<size_t>(need, (size_t)h.wpr * (h.P + 2) * 4);
     if (h.wt > 0) need = std::max<size_t>(need, classify_block_ws_rows_bytes(h.block, h.wt, (int)h.wpr) +
                                                   (size_t)4 * 4 * 1024 * 3 + 8 * 8);
   } else {
@@ -214,7 +296,7 @@ static size_t item_smem(const BStream &h) {
       need = std::max<size_t>(need, (size_t)((1 << (3 * d)) / 4 > 0 ? (1 << (3 * d)) / 4 : 1) * 128 * 4 +
                                         (size_t)3 * 8 * 128 * 3 + 6 * 8);                          // build ws
     } else {
-      need = std::max<size_t>(need, (size_t)256 * 64 * 4);  // chunked build
+      need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * h.N * 32 * 2);  // candidate build: leaves
     }
   }
   return need;
@@ -286,12 +368,19 @@ static ocq_status plan_items(ocq_batch *b) {
                    [&](int x, int y) { return hs[x].hw * hs[x].N > hs[y].hw * hs[y].N; });
   for (int s : order) {
     BStream &st = hs[s];
-    if (st.kind == OCQ_REGION_BLOCK) {
+    if (st.kind == OCQ_REGION_BLOCK && st.ppl > 0) {
+      constexpr int64_t kRegionsPerItem = 40;
+      for (int64_t r = 0; r < st.R; r += kRegionsPerItem, ++st.n_build)
+        push(OP_BUILD_BLOCK_WARP, s, r, 0, std::min(st.R, r + kRegionsPerItem));
+    } else if (st.kind == OCQ_REGION_BLOCK) {
       const int64_t vg = cdiv(st.R, 8);
       for (int64_t v = 0; v < vg; ++v, ++st.n_build) push(OP_BUILD_BLOCK, s, v, vg, 0);
     } else if (st.kind == OCQ_REGION_PIXEL) {
       if (st.depth >= 4) {
-        for (int64_t v = 0; v < cdiv(st.hw, 64); ++v, ++st.n_build) push(OP_BUILD_PIXEL_CHK, s, v, 0, 0);
+        constexpr int64_t kTilesPerItem = 40;  // 32-pixel tiles, 8 per warp
+        const int64_t tiles = cdiv(st.hw, 32);
+        for (int64_t t = 0; t < tiles; t += kTilesPerItem, ++st.n_build)
+          push(OP_BUILD_PIXEL_MG, s, t, 0, std::min(tiles, t + kTilesPerItem));
       } else {
         if (st.btiles > 0) {
           const int64_t vg = cdiv(st.btiles, 8);
@@ -324,6 +413,11 @@ static ocq_status plan_items(ocq_batch *b) {
       const int64_t vg = std::max<int64_t>(1, cdiv(st.ptiles * st.F, per));
       for (int64_t v = 0; v < vg; ++v) push(OP_CLS_PIXEL_WS, s, v, vg, 0);
       generic(st.ptiles * 1024);
+    } else if (st.kind == OCQ_REGION_PIXEL && st.tb) {
+      const int64_t tiles = cdiv(st.hw, 128);
+      const int64_t nw = kBatchThreads / 32;
+      const int64_t k = std::max<int64_t>(1, per * 1024 / (128 * (int64_t)st.F) / nw) * nw;
+      for (int64_t t = 0; t < tiles; t += k) push(OP_CLS_PIXEL_TB, s, t, 0, std::min(tiles, t + k));
     } else if (st.kind == OCQ_REGION_BLOCK && st.blk_tiles > 0) {
       const int64_t vg = std::max<int64_t>(1, cdiv(st.blk_tiles * st.F, per));
       for (int64_t v = 0; v < vg; ++v) push(OP_CLS_BLOCK_WS, s, v, vg, 0);
@@ -362,8 +456,6 @@ static ocq_status enqueue_run(ocq_batch *b, cudaStream_t st) {
     const BStream &h = b->hs[s];
     if (h.kind == OCQ_REGION_FRAME)
       rc = cuda_status(cudaMemsetAsync(h.occ, 0, (size_t)h.N * h.wpr * 4, st), "clear occupancy");
-    else if (h.kind == OCQ_REGION_PIXEL && h.depth >= 4)
-      rc = cuda_status(cudaMemsetAsync(h.model, 0, (size_t)h.R * h.wpr * 4, st), "clear model");
   }
   if (rc != OCQ_OK) return rc;
   batch_kernel<<<b->grid, kBatchThreads, b->smem, st>>>(b->d_streams, b->d_items, (int)b->items.size(), S, b->d_ctr);
@@ -449,6 +541,16 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     if (h.kind == OCQ_REGION_PIXEL && d.depth <= 3 && al && h.hw % 16 == 0) {
       h.ptiles = h.hw / 1024;
       h.btiles = h.hw / 128;
+    }
+    if (h.kind == OCQ_REGION_PIXEL && d.depth >= 4) {
+      const int k = d.N / d.T;
+      h.km = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : 0;
+      h.tb = d.F > 0 && h.hw % 4 == 0 &&
+             ((reinterpret_cast<uintptr_t>(d.test) | reinterpret_cast<uintptr_t>(d.mask)) & 3) == 0;
+    }
+    if (h.kind == OCQ_REGION_BLOCK && block_warp_ok(d.N, d.H, d.W, h.block)) {
+      const int npx = h.block * h.block;
+      h.ppl = npx <= 32 ? 1 : npx <= 64 ? 2 : npx <= 128 ? 4 : 8;
     }
     if (h.kind == OCQ_REGION_BLOCK && d.depth <= 5 && al) {
       h.wt = block_tile_width(h.block, d.depth, d.W);

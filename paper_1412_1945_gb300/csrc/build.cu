@@ -60,6 +60,28 @@ __global__ void __launch_bounds__(256) build_block_kernel(const uint8_t *__restr
   build_block_body<D>(frames, N, H, W, b, bw, P, T, model, R, blockIdx.x, gridDim.x);
 }
 
+template <int D, int PPL>
+__global__ void __launch_bounds__(256) build_block_warp_kernel(const uint8_t *__restrict__ frames, int N, int H, int W,
+                                                               int b, int bw, uint32_t T,
+                                                               uint32_t *__restrict__ model, int64_t R) {
+  extern __shared__ uint32_t tabs[];
+  constexpr int S = WarpTableCfg<D>::S;
+  uint32_t *tab = tabs + (threadIdx.x >> 5) * S;
+  for (int i = threadIdx.x & 31; i < S; i += 32) tab[i] = 0u;
+  __syncwarp();
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  build_block_warp_body<D, PPL>(frames, N, H, W, b, bw, T, model, (int64_t)blockIdx.x * (blockDim.x >> 5) +
+                                (threadIdx.x >> 5), R, nw, tab);
+}
+
+template <int D, int KM>
+__global__ void __launch_bounds__(128) build_pixel_mg_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
+                                                             uint32_t T, uint32_t *__restrict__ model) {
+  extern __shared__ __align__(16) uint8_t mg_smem[];
+  leaf_t<D> *codes = reinterpret_cast<leaf_t<D> *>(mg_smem) + (size_t)(threadIdx.x >> 5) * N * 32;
+  build_pixel_mg_body<D, KM>(frames, N, hw, T, model, (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5), codes);
+}
+
 template <int D, bool WIDE>
 __global__ void __launch_bounds__(128) build_pixel_counters_kernel(const uint8_t *__restrict__ frames, int N,
                                                                    int64_t hw, int64_t p_begin, uint32_t T,
@@ -483,6 +505,68 @@ static ocq_status launch_block(const uint8_t *frames, int N, ocq_model *m, cudaS
   return cuda_status(cudaGetLastError(), "build_block_kernel");
 }
 
+template <int D, int KM>
+static ocq_status launch_pixel_mg_km(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  const size_t smem = (size_t)4 * N * 32 * sizeof(leaf_t<D>);
+  auto kern = build_pixel_mg_kernel<D, KM>;
+  if (smem > 48 * 1024) {
+    ocq_status rc = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                                "build_pixel_mg_kernel smem");
+    if (rc != OCQ_OK) return rc;
+  }
+  const int64_t hw = (int64_t)m->H * m->W;
+  kern<<<(unsigned)((hw + 127) / 128), 128, smem, st>>>(frames, N, hw, (uint32_t)m->T, m->bits);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "build_pixel_mg_kernel");
+}
+
+// Candidate counters: the smallest of 1, 2, 4, 8 that is >= floor(N / T);
+// beyond 8, every distinct leaf is counted (KM = 0).
+template <int D>
+static ocq_status launch_pixel_mg(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  const int k = N / m->T;
+  if (k <= 1) return launch_pixel_mg_km<D, 1>(frames, N, m, st);
+  if (k <= 2) return launch_pixel_mg_km<D, 2>(frames, N, m, st);
+  if (k <= 4) return launch_pixel_mg_km<D, 4>(frames, N, m, st);
+  if (k <= 8) return launch_pixel_mg_km<D, 8>(frames, N, m, st);
+  return launch_pixel_mg_km<D, 0>(frames, N, m, st);
+}
+
+// One warp per block region (b <= 16, N <= 255, frame offsets within 32 bits).
+bool block_warp_ok(int N, int H, int W, int b) {
+  return b <= 16 && N <= 255 && (int64_t)H * W * 3 <= (int64_t)UINT32_MAX;
+}
+
+template <int D, int PPL>
+static ocq_status launch_block_warp_ppl(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  constexpr int S = WarpTableCfg<D>::S;
+  constexpr size_t smem = (size_t)8 * S * 4;
+  auto kern = build_block_warp_kernel<D, PPL>;
+  static int cap = 0;
+  if (!cap) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem);
+    cap = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+  }
+  const int bw = (m->W + m->block - 1) / m->block;
+  const int64_t ctas = (m->R + 7) / 8;
+  kern<<<(unsigned)(ctas < cap ? ctas : cap), 256, smem, st>>>(frames, N, m->H, m->W, m->block, bw,
+                                                               (uint32_t)m->T, m->bits, m->R);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "build_block_warp_kernel");
+}
+
+template <int D>
+static ocq_status launch_block_warp(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  const int npx = m->block * m->block;
+  if (npx <= 32) return launch_block_warp_ppl<D, 1>(frames, N, m, st);
+  if (npx <= 64) return launch_block_warp_ppl<D, 2>(frames, N, m, st);
+  if (npx <= 128) return launch_block_warp_ppl<D, 4>(frames, N, m, st);
+  return launch_block_warp_ppl<D, 8>(frames, N, m, st);
+}
+
 template <int D, bool WIDE>
 static ocq_status launch_pixel_counters(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st,
                                         int64_t p_begin = 0) {
@@ -737,6 +821,15 @@ bool build_take_timeout() {
 ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
   const int d = m->depth;
   if (m->kind == OCQ_REGION_FRAME || (m->kind == OCQ_REGION_BLOCK && d >= 6)) return build_dense(frames, N, m, st);
+  if (m->kind == OCQ_REGION_BLOCK && block_warp_ok(N, m->H, m->W, m->block)) {
+    switch (d) {
+      case 1: return launch_block_warp<1>(frames, N, m, st);
+      case 2: return launch_block_warp<2>(frames, N, m, st);
+      case 3: return launch_block_warp<3>(frames, N, m, st);
+      case 4: return launch_block_warp<4>(frames, N, m, st);
+      default: return launch_block_warp<5>(frames, N, m, st);
+    }
+  }
   if (m->kind == OCQ_REGION_BLOCK) {
     switch (d) {
       case 1: return launch_block<1>(frames, N, m, st);
@@ -750,6 +843,15 @@ ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t
   const bool staged_ok = m->T <= 255 && ((reinterpret_cast<uintptr_t>(frames) & 15) == 0) &&
                          ((int64_t)m->H * m->W) % 16 == 0;
   if (staged_ok && d <= 3) return launch_build_pixel_staged(frames, N, m, st);
+  if (d >= 4 && N <= 255) {
+    switch (d) {
+      case 4: return launch_pixel_mg<4>(frames, N, m, st);
+      case 5: return launch_pixel_mg<5>(frames, N, m, st);
+      case 6: return launch_pixel_mg<6>(frames, N, m, st);
+      case 7: return launch_pixel_mg<7>(frames, N, m, st);
+      default: return launch_pixel_mg<8>(frames, N, m, st);
+    }
+  }
   switch (d) {
     case 1: return wide ? launch_pixel_counters<1, true>(frames, N, m, st) : launch_pixel_counters<1, false>(frames, N, m, st);
     case 2: return wide ? launch_pixel_counters<2, true>(frames, N, m, st) : launch_pixel_counters<2, false>(frames, N, m, st);

@@ -7,6 +7,8 @@
 
 #include <cuda.h>
 
+#include <type_traits>
+
 #include "async_copy.cuh"
 #include "pixels.cuh"
 
@@ -224,6 +226,176 @@ __device__ __forceinline__ void build_block_body(const uint8_t *__restrict__ fra
   }
 }
 
+// ---- block regions, one warp per region ----------------------------------------
+// A b x b block (b <= 16, so at most 8 pixels per lane) holds at most b*b
+// distinct leaves per frame and usually a few dozen over all N frames, far
+// fewer than the 8^d leaves of its row.  So each warp counts its region's
+// leaves in a small table in shared memory instead of a dense counter row:
+// entry = (leaf + 1) << 16 | last frame << 8 | frames counted (N <= 255).
+// Per frame and pixel slot, __match_any_sync groups lanes holding the same
+// leaf and only the lowest such lane touches the entry, so a leaf is counted
+// once per frame (the "last frame" field makes later slots of the same frame
+// skip it).  With 8^d <= WarpTableCfg::S the table is indexed by the leaf
+// itself; above it, by a multiplicative hash with linear probing.  A region
+// with more than 3/4 S distinct leaves falls back to passes over S-leaf
+// chunks of the code space, each indexed directly.  The model row is zeroed
+// with vector stores and the kept leaves (count >= T) are ORed in.
+template <int D>
+struct WarpTableCfg {
+  static constexpr int NC = 1 << (3 * D);
+  static constexpr int S = NC < 1024 ? NC : 1024;  // entries per warp
+  static constexpr bool DIRECT = NC <= S;
+  static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  static constexpr int LOGS = 3 * D < 10 ? 3 * D : 10;
+};
+
+template <int D>
+__device__ __forceinline__ bool warp_table_count(uint32_t *tab, uint32_t q, uint32_t f, int chunk) {
+  using C = WarpTableCfg<D>;
+  uint32_t h;
+  if (C::DIRECT || chunk >= 0)
+    h = q & (C::S - 1);
+  else
+    h = (q * 2654435761u) >> (32 - C::LOGS);
+  const uint32_t key = (q + 1) << 16;
+  for (int probe = 0; probe < C::S; ++probe) {
+    uint32_t e = tab[h];
+    if (e == 0u) {
+      e = atomicCAS(&tab[h], 0u, key | (f << 8) | 1u);
+      if (e == 0u) return true;  // inserted
+    }
+    if ((e & 0xFFFF0000u) == key) {
+      if (((e >> 8) & 255u) != f) tab[h] = key | (f << 8) | ((e & 255u) + 1u);
+      return false;
+    }
+    h = (h + 1) & (C::S - 1);
+  }
+  return false;  // unreachable: the table is never more than 3/4 + 1/32 full
+}
+
+// Zeroes the region's model row (WPR words) with the warp's lanes.
+template <int D>
+__device__ __forceinline__ void warp_zero_row(uint32_t *row) {
+  constexpr int WPR = WarpTableCfg<D>::WPR;
+  const int lane = threadIdx.x & 31;
+  if constexpr (WPR >= 4) {
+    uint4 *r4 = reinterpret_cast<uint4 *>(row);
+    for (int i = lane; i < WPR / 4; i += 32) r4[i] = make_uint4(0, 0, 0, 0);
+  } else {
+    if (lane < WPR) row[lane] = 0u;
+  }
+}
+
+// Emits kept leaves of the table into the (zeroed) row and clears the table.
+// chunk < 0: entries carry their leaf; chunk >= 0 (direct pass) likewise.
+template <int D>
+__device__ __forceinline__ void warp_emit(uint32_t *tab, uint32_t *row, uint32_t T) {
+  using C = WarpTableCfg<D>;
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  for (int s = lane; s < C::S; s += 32) {
+    const uint32_t e = tab[s];
+    if (e) {
+      tab[s] = 0u;
+      if ((e & 255u) >= T) {
+        const uint32_t q = (e >> 16) - 1u;
+        atomicOr(&row[q >> 5], 1u << (q & 31));
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// One pass over the region's N frames; chunk < 0 counts every leaf (hashed),
+// chunk >= 0 only leaves in [chunk * S, chunk * S + S).  Returns false if the
+// hashed pass saw more than 3/4 S distinct leaves.
+template <int D, int PPL, int PF>
+__device__ __forceinline__ bool warp_region_pass(const uint8_t *__restrict__ frames, int N, int64_t fstride,
+                                                 const uint32_t (&off)[PPL], int npx, uint32_t *tab, int chunk) {
+  using C = WarpTableCfg<D>;
+  const int lane = threadIdx.x & 31;
+  int inserted = 0;
+  for (int f0 = 0; f0 < N; f0 += PF) {
+    uint32_t yv[PF][PPL];
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+#pragma unroll
+      for (int k = 0; k < PPL; ++k)
+        if (f0 + j < N && lane + 32 * k < npx) {
+          const uint8_t *s = frames + (int64_t)(f0 + j) * fstride + off[k];
+          yv[j][k] = (uint32_t)__ldg(s) | ((uint32_t)__ldg(s + 1) << 8) | ((uint32_t)__ldg(s + 2) << 16);
+        }
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (f0 + j >= N) break;
+#pragma unroll
+      for (int k = 0; k < PPL; ++k) {
+        if (32 * k >= npx) break;
+        const bool valid = lane + 32 * k < npx;
+        const uint32_t q = valid ? planar_code<D>(yv[j][k]) : 0xFFFFFFFFu;
+        const bool mine = valid && (chunk < 0 || (int)(q >> C::LOGS) == chunk);
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, mine ? q : 0xFFFFFFFFu);
+        bool ins = false;
+        if (mine && lane == __ffs(peers) - 1) ins = warp_table_count<D>(tab, q, (uint32_t)(f0 + j), chunk);
+        inserted += __popc(__ballot_sync(0xFFFFFFFFu, ins));
+        __syncwarp();
+      }
+      if (chunk < 0 && !C::DIRECT && inserted > 3 * C::S / 4) return false;
+    }
+  }
+  return true;
+}
+
+// Warp w of the caller handles regions r = r_first, r_first + r_step, ... < r_end.
+// tab: this warp's S-entry table, zero on entry and on return.
+template <int D, int PPL>
+__device__ __forceinline__ void build_block_warp_body(const uint8_t *__restrict__ frames, int N, int H, int W, int b,
+                                                      int bw, uint32_t T, uint32_t *__restrict__ model,
+                                                      int64_t r_first, int64_t r_end, int64_t r_step,
+                                                      uint32_t *tab) {
+  using C = WarpTableCfg<D>;
+  constexpr int PF = PPL >= 8 ? 2 : 16 / PPL;
+  const int lane = threadIdx.x & 31;
+  const int64_t fstride = (int64_t)H * W * 3;
+  for (int64_t r = r_first; r < r_end; r += r_step) {
+    const int y0 = (int)(r / bw) * b, x0 = (int)(r % bw) * b;
+    const int h = min(b, H - y0), w = min(b, W - x0);
+    const int npx = h * w;
+    uint32_t off[PPL];
+#pragma unroll
+    for (int k = 0; k < PPL; ++k) {
+      const int i = lane + 32 * k;
+      off[k] = i < npx ? (uint32_t)(((int64_t)(y0 + i / w) * W + x0 + i % w) * 3) : 0u;
+    }
+    uint32_t *row = model + r * C::WPR;
+    warp_zero_row<D>(row);
+    if (warp_region_pass<D, PPL, PF>(frames, N, fstride, off, npx, tab, -1)) {
+      warp_emit<D>(tab, row, T);
+    } else {
+      for (int s = lane; s < C::S; s += 32) tab[s] = 0u;
+      for (int c = 0; c < C::NC / C::S; ++c) {
+        __syncwarp();
+        warp_region_pass<D, PPL, PF>(frames, N, fstride, off, npx, tab, c);
+        warp_emit<D>(tab, row, T);
+      }
+    }
+  }
+}
+
+// ---- block regions, N <= 64: frame masks --------------------------------------
+// The frames a leaf occurs in, as an N-bit mask: the region's count for a leaf
+// is the popcount of the OR, over the region's pixels, of each pixel's mask
+// for that leaf.  A lane walks its pixel through all N frames keeping the
+// masks of the pixel's first two distinct leaves in registers (a background
+// pixel rarely shows more); any further leaf ORs its frame bit straight into
+// the region's table.  The lane then ORs its two masks into the table, so the
+// shared table sees a few operations per pixel rather than one per pixel and
+// frame.  A group of WPG warps shares one region and one table (slots of 32
+// pixels are split among its warps).  Table: masks[S] (u64), then keys[S]
+// (leaf + 1, 0 = empty; absent when 8^d <= 512 and the leaf is the index), then
+// an insert counter and an overflow flag.  A region with more than 3/4 S
+// distinct leaves is rebuilt by the group's first warp with the per-warp
+// table path above.
 // ---- pixel regions, depth <= 3 -------------------------------------------------
 // Thread t of a 128-thread CTA owns pixel location p and a private column of
 // counter words cnt[k * 128 + t] (4 u8 or 2 u16 counters per word).
@@ -340,6 +512,109 @@ __device__ __forceinline__ void build_pixel_chunked_body(const uint8_t *__restri
         out |= (((ge >> 15) & 1u) | ((ge >> 30) & 2u)) << (2 * k);
       }
       row[c * 16 + w] = out;
+    }
+  }
+}
+
+// ---- pixel regions, any depth: frequent-leaf candidates ---------------------------
+// A pixel location sees one leaf per frame, so its N leaves can hold at most
+// k = floor(N / T) leaves that occur in T or more frames.  Pass 1 keeps a
+// Misra-Gries summary of KM >= k counters over the pixel's leaves (every leaf
+// seen more than N / (KM + 1) < T times keeps a non-zero counter, so every leaf
+// to be kept is among the KM candidates) and stores the leaves in shared
+// memory; pass 2 counts each candidate exactly.  KM = 0 (large k): pass 2
+// instead counts every distinct leaf at its first occurrence.  The warp then
+// writes its 32 pixels' rows, which are contiguous: zeros with vector stores,
+// then the kept words.  Lane = pixel; the frames are read once and the model
+// written once, whatever the depth.
+template <int D>
+using leaf_t = typename std::conditional<(D <= 5), uint16_t, uint32_t>::type;
+
+template <int D, int KM>
+__device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ frames, int N, int64_t hw, uint32_t T,
+                                                    uint32_t *__restrict__ model, int64_t tile, leaf_t<D> *codes) {
+  constexpr int64_t WPR = D == 1 ? 1 : (int64_t)1 << (3 * D - 5);
+  constexpr int PF = 8;
+  const int lane = threadIdx.x & 31;
+  const int64_t p0 = tile * 32, p = p0 + lane;
+  const bool valid = p < hw;
+  const uint8_t *px = frames + (valid ? p : 0) * 3;
+  const int64_t fstride = hw * 3;
+  uint32_t key[KM > 0 ? KM : 1], cnt[KM > 0 ? KM : 1];
+#pragma unroll
+  for (int i = 0; i < (KM > 0 ? KM : 1); ++i) key[i] = 0u, cnt[i] = 0u;
+  for (int f0 = 0; f0 < N; f0 += PF) {
+    uint32_t yv[PF];
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+      if (valid && f0 + j < N) {
+        const uint8_t *s = px + (int64_t)(f0 + j) * fstride;
+        yv[j] = (uint32_t)__ldg(s) | ((uint32_t)__ldg(s + 1) << 8) | ((uint32_t)__ldg(s + 2) << 16);
+      }
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (!valid || f0 + j >= N) break;
+      const uint32_t q = planar_code<D>(yv[j]);
+      codes[(f0 + j) * 32 + lane] = (leaf_t<D>)q;
+      if constexpr (KM > 0) {
+        bool hit = false;
+#pragma unroll
+        for (int i = 0; i < KM; ++i)
+          if (cnt[i] && key[i] == q) ++cnt[i], hit = true;
+        if (!hit) {
+          bool placed = false;
+#pragma unroll
+          for (int i = 0; i < KM; ++i)
+            if (!placed && !cnt[i]) key[i] = q, cnt[i] = 1u, placed = true;
+          if (!placed) {
+#pragma unroll
+            for (int i = 0; i < KM; ++i) --cnt[i];
+          }
+        }
+      }
+    }
+  }
+  uint32_t exact[KM > 0 ? KM : 1];
+  if constexpr (KM > 0) {
+#pragma unroll
+    for (int i = 0; i < KM; ++i) exact[i] = 0u;
+    if (valid)
+      for (int f = 0; f < N; ++f) {
+        const uint32_t q = codes[f * 32 + lane];
+#pragma unroll
+        for (int i = 0; i < KM; ++i) exact[i] += (cnt[i] && key[i] == q) ? 1u : 0u;
+      }
+  }
+  const int64_t np = hw - p0 < 32 ? hw - p0 : 32;
+  uint32_t *base = model + p0 * WPR;
+  if constexpr (WPR >= 4) {
+    uint4 *b4 = reinterpret_cast<uint4 *>(base);
+    for (int64_t i = lane; i < np * WPR / 4; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
+  } else {
+    for (int64_t i = lane; i < np * WPR; i += 32) base[i] = 0u;
+  }
+  __syncwarp();
+  if (!valid) return;
+  uint32_t *row = base + lane * WPR;
+  if constexpr (KM > 0) {
+#pragma unroll
+    for (int i = 0; i < KM; ++i) {
+      if (exact[i] < T) continue;
+      uint32_t v = 0u;
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (exact[j] >= T && (key[j] >> 5) == (key[i] >> 5)) v |= 1u << (key[j] & 31);
+      row[key[i] >> 5] = v;
+    }
+  } else {
+    for (int f = 0; f < N; ++f) {
+      const uint32_t q = codes[f * 32 + lane];
+      bool first = true;
+      for (int g = 0; g < f && first; ++g) first = codes[g * 32 + lane] != q;
+      if (!first) continue;
+      uint32_t c = 1u;
+      for (int g = f + 1; g < N; ++g) c += codes[g * 32 + lane] == q ? 1u : 0u;
+      if (c >= T) atomicOr(&row[q >> 5], 1u << (q & 31));
     }
   }
 }

@@ -7,6 +7,9 @@
 //                                lives in shared memory (replicated per lane
 //                                for depth <= 4 so lookups never conflict),
 //                                frames stream through 16-byte loads.
+//   classify_pixel_tb_kernel     pixel regions, depth >= 4: a warp walks all
+//                                frames of 32 or 128 pixel locations; their
+//                                model sectors stay in L1 between frames.
 //   classify_pixel_tiled_kernel  pixel regions, depth <= 3: temporal blocking.
 //                                A CTA keeps the rows of a tile of pixel
 //                                locations in shared memory (lane-interleaved:
@@ -45,6 +48,22 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1)
                              const uint32_t *__restrict__ model, uint8_t *__restrict__ mask) {
   classify_pixel_ws_body<D, NW, PPT, S, FPS>(frames, F, hw, ntiles, model, mask, blockIdx.x, gridDim.x,
                                              &g_classify_timeout);
+}
+
+// Pixel regions at any depth (used for depth >= 4): warps stride over
+// 128-pixel tiles and walk all frames of each.
+template <int D, int PXL, int PF>
+__global__ void __launch_bounds__(128) classify_pixel_tb_kernel(const uint8_t *__restrict__ frames, int F,
+                                                                int64_t hw, const uint32_t *__restrict__ model,
+                                                                uint8_t *__restrict__ mask) {
+  const int64_t tiles = (hw + 32 * PXL - 1) / (32 * PXL);
+  const int64_t nw = (int64_t)gridDim.x * 4;
+  for (int64_t t = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5); t < tiles; t += nw) {
+    if constexpr (PXL == 4)
+      classify_pixel_tb_body<D, PF>(frames, F, hw, model, mask, t);
+    else
+      classify_pixel_tb1_body<D, PF>(frames, F, hw, model, mask, t);
+  }
 }
 
 template <int D, int S, int FPS>
@@ -289,6 +308,55 @@ void classify_variant_describe(int v, int *nw, int *ppt, int *stages, int *fps, 
   *ws = kClassifyVariants[v].ws;
 }
 
+// Deep per-pixel classify variants: pixel locations per lane (4 or 1), frames
+// prefetched, CTAs of 4 warps resident per SM.  Fewer resident pixel locations
+// leave more L1 per location for its model lines.
+struct DeepVariant {
+  int pxl, pf, cps;
+  ocq_status (*fn[5])(const ocq_model *, const uint8_t *, int, uint8_t *, int, cudaStream_t);
+};
+
+template <int D, int PXL, int PF>
+static ocq_status launch_pixel_tb(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, int cps,
+                                  cudaStream_t st) {
+  const int64_t hw = (int64_t)m->H * m->W;
+  const int64_t ctas = (hw + 128 * PXL - 1) / (128 * PXL);
+  const int64_t cap = (int64_t)sm_count() * cps;
+  auto kern = classify_pixel_tb_kernel<D, PXL, PF>;
+  static bool carved = false;
+  if (!carved) {  // no shared memory: leave the whole unified array to L1
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    carved = true;
+  }
+  kern<<<(unsigned)(ctas < cap ? ctas : cap), 128, 0, st>>>(frames, F, hw, m->bits, mask);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "classify_pixel_tb_kernel");
+}
+
+#define OCQ_DV(PXL, PF, CPS)                                                                              \
+  DeepVariant {                                                                                          \
+    PXL, PF, CPS, {                                                                                      \
+      launch_pixel_tb<4, PXL, PF>, launch_pixel_tb<5, PXL, PF>, launch_pixel_tb<6, PXL, PF>,             \
+          launch_pixel_tb<7, PXL, PF>, launch_pixel_tb<8, PXL, PF>                                       \
+    }                                                                                                    \
+  }
+static const DeepVariant kDeepVariants[] = {OCQ_DV(4, 8, 2),   OCQ_DV(4, 8, 3),  OCQ_DV(4, 8, 4),
+                                            OCQ_DV(1, 16, 4),  OCQ_DV(1, 16, 8), OCQ_DV(1, 16, 12),
+                                            OCQ_DV(1, 16, 16), OCQ_DV(1, 8, 16)};
+#undef OCQ_DV
+static int g_deep_variant = 1;
+
+int deep_variant_count() { return (int)(sizeof kDeepVariants / sizeof kDeepVariants[0]); }
+int deep_variant_selected() { return g_deep_variant; }
+bool deep_variant_select(int v) {
+  if (v < 0 || v >= deep_variant_count()) return false;
+  g_deep_variant = v;
+  return true;
+}
+void deep_variant_describe(int v, int *pxl, int *pf, int *cps) {
+  *pxl = kDeepVariants[v].pxl, *pf = kDeepVariants[v].pf, *cps = kDeepVariants[v].cps;
+}
+
 template <int D>
 static ocq_status launch_block_ws(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, int wt,
                                   cudaStream_t st) {
@@ -328,6 +396,11 @@ ocq_status launch_classify(const ocq_model *m, const uint8_t *frames, int F, uin
   const bool aligned = ((reinterpret_cast<uintptr_t>(frames) | reinterpret_cast<uintptr_t>(mask)) & 15) == 0;
   if (m->kind == OCQ_REGION_PIXEL && d <= 3 && aligned && hw % 16 == 0)
     return kClassifyVariants[g_classify_variant].fn[d - 1](m, frames, F, mask, st);
+  const bool aligned4 = ((reinterpret_cast<uintptr_t>(frames) | reinterpret_cast<uintptr_t>(mask)) & 3) == 0;
+  if (m->kind == OCQ_REGION_PIXEL && d >= 4 && aligned4 && hw % 4 == 0) {
+    const DeepVariant &v = kDeepVariants[g_deep_variant];
+    return v.fn[d - 4](m, frames, F, mask, v.cps, st);
+  }
   if (m->kind == OCQ_REGION_BLOCK && d <= 5 && aligned) {
     const int wt = block_tile_width(m->block, d, m->W);
     if (wt > 0) {

@@ -81,6 +81,108 @@ __device__ __forceinline__ void classify_frame_body(const uint8_t *__restrict__ 
   }
 }
 
+// ---- pixel regions, any depth: temporal blocking through L1 ----------------------
+// A warp owns 128 consecutive pixel locations (4 per lane) and walks all F
+// frames for them, so the few model sectors each location's colours hit stay
+// in the SM's L1 between frames instead of being fetched once per frame: the
+// rows are 8^d/8 bytes (512 B at d = 4, 4 KB at d = 5), too large to stage
+// whole in shared memory.  Frames are read with streaming 4-byte loads and the
+// mask written with streaming 4-byte stores, so neither displaces the model
+// lines.  Needs H*W % 4 == 0 and 4-byte aligned frames and mask.
+__device__ __forceinline__ uint32_t ld_stream4(const void *p) {
+  uint32_t v;
+  asm volatile("ld.global.cs.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_stream4(void *p, uint32_t v) {
+  asm volatile("st.global.cs.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Packed pixel k (0..3) of 4 pixels held as 3 words.
+template <int K>
+__device__ __forceinline__ uint32_t quad_pixel(const uint32_t (&w)[3]) {
+  constexpr int o = 3 * K, i = o / 4, s = o % 4;
+  constexpr uint32_t sel = (uint32_t)(s | ((s + 1) << 4) | ((s + 2) << 8) | ((s + 2) << 12));
+  if constexpr (i + 1 < 3)
+    return __byte_perm(w[i], w[i + 1], sel);
+  else
+    return __byte_perm(w[i], 0u, sel);
+}
+
+template <int D, int PF>
+__device__ __forceinline__ void classify_pixel_tb_body(const uint8_t *__restrict__ frames, int F, int64_t hw,
+                                                       const uint32_t *model, uint8_t *__restrict__ mask,
+                                                       int64_t tile) {
+  constexpr int64_t WPR = D == 1 ? 1 : (int64_t)1 << (3 * D - 5);
+  const int lane = threadIdx.x & 31;
+  const int64_t pq = tile * 128 + 4 * lane;
+  if (pq >= hw) return;
+  const uint8_t *rows = reinterpret_cast<const uint8_t *>(model + pq * WPR);
+  const uint8_t *src = frames + pq * 3;
+  uint8_t *dst = mask + pq;
+  for (int f0 = 0; f0 < F; f0 += PF) {
+    uint32_t w[PF][3];
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+      if (f0 + j < F) {
+        const uint8_t *s = src + (int64_t)(f0 + j) * hw * 3;
+        w[j][0] = ld_stream4(s), w[j][1] = ld_stream4(s + 4), w[j][2] = ld_stream4(s + 8);
+      }
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (f0 + j >= F) break;
+      uint32_t m[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) m[i] = (w[j][i] >> (8 - D)) & byte_mask(D);
+      uint32_t bg[4];
+      static_for<0, 4>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const uint32_t q = planar_from_masked<D>(quad_pixel<k>(m));
+        bg[k] = (uint32_t)rows[k * WPR * 4 + (q >> 3)] >> (q & 7);
+      });
+      st_stream4(dst + (int64_t)(f0 + j) * hw, pack_mask4(bg[0], bg[1], bg[2], bg[3]));
+    }
+  }
+}
+
+// One pixel location per lane (a warp owns 32): a smaller model working set
+// per warp than the 4-per-lane form, so more warps fit their lines in L1.
+__device__ __forceinline__ uint32_t ld_stream1(const uint8_t *p) {
+  uint32_t v;
+  asm volatile("ld.global.cs.u8 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void st_stream1(uint8_t *p, uint32_t v) {
+  asm volatile("st.global.cs.u8 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int D, int PF>
+__device__ __forceinline__ void classify_pixel_tb1_body(const uint8_t *__restrict__ frames, int F, int64_t hw,
+                                                        const uint32_t *model, uint8_t *__restrict__ mask,
+                                                        int64_t tile) {
+  constexpr int64_t WPR = D == 1 ? 1 : (int64_t)1 << (3 * D - 5);
+  const int64_t p = tile * 32 + (threadIdx.x & 31);
+  if (p >= hw) return;
+  const uint8_t *row = reinterpret_cast<const uint8_t *>(model + p * WPR);
+  const uint8_t *src = frames + p * 3;
+  uint8_t *dst = mask + p;
+  for (int f0 = 0; f0 < F; f0 += PF) {
+    uint32_t y[PF];
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+      if (f0 + j < F) {
+        const uint8_t *s = src + (int64_t)(f0 + j) * hw * 3;
+        y[j] = ld_stream1(s) | (ld_stream1(s + 1) << 8) | (ld_stream1(s + 2) << 16);
+      }
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (f0 + j >= F) break;
+      const uint32_t q = planar_code<D>(y[j]);
+      st_stream1(dst + (int64_t)(f0 + j) * hw, ((~(uint32_t)row[q >> 3]) >> (q & 7)) & 1u);
+    }
+  }
+}
+
 // ---- pixel regions: temporal blocking with bulk async copies --------------------------
 
 template <int D, int NW, int PPT, int S, int FPS>

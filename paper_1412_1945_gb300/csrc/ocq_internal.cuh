@@ -152,6 +152,8 @@ ocq_status launch_export(const uint32_t *bits, int64_t R, int depth, uint64_t *d
 ocq_status launch_import(const uint64_t *src, int64_t R, int depth, uint32_t *bits, cudaStream_t st);
 bool classify_take_timeout();
 bool build_take_timeout();
+// Block regions that the one-warp-per-region build handles (b <= 16, N <= 255).
+bool block_warp_ok(int N, int H, int W, int b);
 
 // Kernel variants the tuner can choose between (per-pixel tiled classify,
 // staged per-pixel build).
@@ -159,6 +161,10 @@ int classify_variant_count();
 int classify_variant_selected();
 bool classify_variant_select(int v);
 void classify_variant_describe(int v, int *nw, int *ppt, int *stages, int *fps, int *ws);
+int deep_variant_count();
+int deep_variant_selected();
+bool deep_variant_select(int v);
+void deep_variant_describe(int v, int *pxl, int *pf, int *cps);
 int build_variant_count();
 int build_variant_selected();
 bool build_variant_select(int v);

@@ -105,7 +105,7 @@ SIGNATURES = {
     "ocq_tune_describe": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_int32), _i32]),
 }
 
-OCQ_TUNE_CLASSIFY_PIXEL, OCQ_TUNE_BUILD_PIXEL = 0, 1
+OCQ_TUNE_CLASSIFY_PIXEL, OCQ_TUNE_BUILD_PIXEL, OCQ_TUNE_CLASSIFY_PIXEL_DEEP = 0, 1, 2
 
 
 def load(path: str | None = None):

@@ -273,3 +273,81 @@ def test_block_tiled_classify(ocq, torch, b, d):
     ow, om = oracle.run(train, d, 4, BLOCK, b, test)
     assert (words == ow).all()
     assert (mask == om).all()
+
+
+@pytest.mark.parametrize("b", [2, 5, 8, 11, 16, 17])
+@pytest.mark.parametrize("d", [2, 3, 4, 5])
+def test_block_build_warp_tables(ocq, torch, b, d):
+    """Block regions with b <= 16 and N <= 255 are built one warp per region
+    with a leaf table in shared memory; b = 17 takes the CTA-per-region
+    kernel.  Scene content, then uniform noise (far more distinct leaves per
+    region than the table holds at depth 4-5, so the chunked fallback runs),
+    with ragged blocks at the right and bottom edges."""
+    H, W = 2 * b + 3, 3 * b + 7
+    sc = ocq_synth.make_scene("sway", H, W, 10, 6, seed=500 + 7 * b + d)
+    frames = ocq_synth.fill_host(sc, 0, 16)
+    g = np.random.default_rng(900 + b * 11 + d)
+    noise = g.integers(0, 256, size=(10, H, W, 3), dtype=np.uint8)
+    for train in (frames[:10], noise):
+        for T in (1, 3, 10):
+            words, mask = gpu_model_and_mask(ocq, torch, train, frames[10:], d, T, BLOCK, b)
+            ow, om = oracle.run(train, d, T, BLOCK, b, frames[10:])
+            assert (words == ow).all(), T
+            assert (mask == om).all(), T
+
+
+@pytest.mark.parametrize("N", [254, 255, 256])
+def test_block_build_frame_count_limits(ocq, torch, N):
+    """The warp tables keep the last frame and the count in 8 bits each:
+    N = 255 is their limit, N = 256 goes to the CTA-per-region kernel."""
+    g = np.random.default_rng(N)
+    palette = g.integers(0, 256, size=(5, 3), dtype=np.uint8)
+    train = palette[g.integers(0, 5, size=(N, 12, 20))]
+    test = palette[g.integers(0, 5, size=(2, 12, 20))]
+    for T in (1, N // 5, N // 2, N):
+        words, mask = gpu_model_and_mask(ocq, torch, train, test, 4, T, BLOCK, 8)
+        ow, om = oracle.run(train, 4, T, BLOCK, 8, test)
+        assert (words == ow).all() and (mask == om).all(), T
+
+
+@pytest.mark.parametrize("d", [4, 5, 6])
+@pytest.mark.parametrize("H,W", [(24, 40), (13, 37), (9, 132)])
+def test_pixel_deep_candidates_and_tiles(ocq, torch, d, H, W):
+    """Pixel regions at depth >= 4: the build keeps 1, 2, 4 or 8 frequent-leaf
+    candidates per location (or counts every distinct leaf when N / T > 8), and
+    the classify walks all frames of 128-location tiles (H*W % 4 == 0) or falls
+    back to per-pixel lookups; several warps' tiles plus a ragged one."""
+    if d == 6:
+        H, W = min(H, 6), min(W, 20)
+    N = 40
+    sc = ocq_synth.make_scene("bimodal", H, W, N, 9, seed=600 + d + H)
+    frames = ocq_synth.fill_host(sc, 0, N + 9)
+    g = np.random.default_rng(d * 100 + W)
+    train = frames[:N].copy()
+    train[::7] = g.integers(0, 256, size=train[::7].shape, dtype=np.uint8)  # a few noisy frames
+    test = frames[N:]
+    for T in (1, 4, 5, 10, 14, 21, 40):  # N // T = 40, 10, 8, 4, 2, 1, 1
+        words, mask = gpu_model_and_mask(ocq, torch, train, test, d, T, PIXEL, 0)
+        ow, om = oracle.run(train, d, T, PIXEL, 0, test)
+        assert (words == ow).all(), T
+        assert (mask == om).all(), T
+
+
+def test_pixel_deep_classify_variants(ocq, torch):
+    """Every residency choice of the deep per-pixel classify gives the oracle's masks."""
+    O = ocq.ocq
+    H, W = 40, 72
+    sc = ocq_synth.make_scene("bimodal", H, W, 12, 10, seed=8)
+    frames = ocq_synth.fill_host(sc, 0, 22)
+    train, test = frames[:12], frames[12:]
+    kernel = O.OCQ_TUNE_CLASSIFY_PIXEL_DEEP
+    saved = O.ocq_tune_selected(kernel)
+    try:
+        for d in (4, 5):
+            ow, om = oracle.run(train, d, 3, PIXEL, 0, test)
+            for v in range(O.ocq_tune_count(kernel)):
+                O.ocq_tune_select(kernel, v)
+                words, mask = gpu_model_and_mask(ocq, torch, train, test, d, 3, PIXEL, 0)
+                assert (words == ow).all() and (mask == om).all(), (d, v)
+    finally:
+        O.ocq_tune_select(kernel, saved)
