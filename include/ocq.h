@@ -161,10 +161,12 @@ ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int
 /*
  * Batched form (no counterpart in the paper, which handles one video): many
  * camera streams, each with its own frame size, region kind and depth, are
- * built (S1-S3) and classified (S4) by ONE persistent kernel launch that is
- * captured once in a CUDA graph and replayed.  Its work items are the CTAs of
- * the per-stream kernels (the same code), taken in list order by persistent
- * CTAs, so results are identical to ocq_build_model + ocq_classify per stream.
+ * built (S1-S3) and classified (S4) by one CUDA graph, captured once and
+ * replayed.  By default the graph holds ONE persistent kernel whose work items
+ * are the CTAs of the per-stream kernels (the same code), taken in list order
+ * by persistent CTAs; the other form (ocq_batch_set_mode) holds the streams'
+ * plain kernels as concurrent branches.  Either way results are identical to
+ * ocq_build_model + ocq_classify per stream.
  *   train: device, N*H*W*3; test: device, F*H*W*3; mask: device, F*H*W.
  * Domain per stream: 1 <= T <= N <= 255; depth <= 5 for block and pixel
  * regions (<= 8 for whole-frame); the buffers stay owned by the caller and
@@ -196,9 +198,20 @@ ocq_status ocq_batch_model(const ocq_batch *batch, int i, const ocq_model **out)
  * items in the list. */
 ocq_status ocq_batch_set_work(ocq_batch *batch, int region_kind, int units);
 ocq_status ocq_batch_get_work(const ocq_batch *batch, int region_kind, int *units, int64_t *items);
+/* Form of the batch's graph:
+ *   OCQ_BATCH_PERSISTENT  one persistent work-list kernel (the default);
+ *   OCQ_BATCH_GRAPH       one branch per camera stream running that stream's
+ *                         plain kernels (build, then classify); branches run
+ *                         concurrently.
+ * Both give results identical to the per-stream calls.  Changing the form
+ * drops the captured graph; the next run captures it again. */
+enum { OCQ_BATCH_PERSISTENT = 0, OCQ_BATCH_GRAPH = 1 };
+ocq_status ocq_batch_set_mode(ocq_batch *batch, int mode);
+int ocq_batch_get_mode(const ocq_batch *batch);
 /* Autotuner: times candidate work sizes per region kind on this batch's own
- * inputs (`reps` runs each, on `stream`) and keeps the fastest; results are
- * cached per (region kind, depths, sizes, frames) signature for the process. */
+ * inputs (`reps` runs each, on `stream`) and keeps the fastest (results are
+ * cached per (region kind, depths, sizes, frames) signature for the process),
+ * then times both forms and keeps the faster. */
 ocq_status ocq_batch_autotune(ocq_batch *batch, int reps, void *stream);
 void ocq_batch_destroy(ocq_batch *batch);
 

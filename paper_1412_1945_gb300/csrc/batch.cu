@@ -326,6 +326,10 @@ struct ocq_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int device = 0;
+  int mode = OCQ_BATCH_PERSISTENT;
+  std::vector<cudaStream_t> side;  // branch streams of the graph form
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
 };
 
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
@@ -469,6 +473,46 @@ static void free_graph(ocq_batch *b) {
   b->exec = nullptr, b->graph = nullptr;
 }
 
+// Graph form: one branch per camera stream (side streams forked from and
+// joined back to the capture stream), each running that stream's plain
+// kernels, build then classify.  Branches are independent, so the graph runs
+// the streams' kernels concurrently; the work is the plain path's, kernel by
+// kernel.
+static ocq_status enqueue_branches(ocq_batch *b, cudaStream_t cs) {
+  const int S = (int)b->hs.size();
+  const int NB = std::min(S, 64);
+  ocq_status rc = OCQ_OK;
+  if (!b->fork) rc = cuda_status(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "fork event");
+  while (rc == OCQ_OK && (int)b->side.size() < NB) {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t e2 = nullptr;
+    rc = cuda_status(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking), "branch stream");
+    if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming), "join event");
+    if (s2) b->side.push_back(s2);
+    if (e2) b->joins.push_back(e2);
+  }
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(b->fork, cs), "fork");
+  for (int i = 0; i < NB && rc == OCQ_OK; ++i) rc = cuda_status(cudaStreamWaitEvent(b->side[i], b->fork, 0), "fork wait");
+  // Larger streams first on each branch stream.
+  std::vector<int> order(S);
+  for (int s = 0; s < S; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return b->hs[x].hw * (b->hs[x].N + b->hs[x].F) > b->hs[y].hw * (b->hs[y].N + b->hs[y].F);
+  });
+  for (int k = 0; k < S && rc == OCQ_OK; ++k) {
+    const int s = order[k];
+    const ocq_stream_desc &d = b->desc[s];
+    cudaStream_t st = b->side[k % NB];
+    rc = launch_build(d.train, d.N, b->models[s], st);
+    if (rc == OCQ_OK && d.F > 0) rc = launch_classify(b->models[s], d.test, d.F, d.mask, st);
+  }
+  for (int i = 0; i < NB && rc == OCQ_OK; ++i) {
+    rc = cuda_status(cudaEventRecord(b->joins[i], b->side[i]), "join");
+    if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent(cs, b->joins[i], 0), "join wait");
+  }
+  return rc;
+}
+
 static ocq_status capture(ocq_batch *b) {
   free_graph(b);
   cudaStream_t cs = nullptr;
@@ -476,7 +520,7 @@ static ocq_status capture(ocq_batch *b) {
   if (rc != OCQ_OK) return rc;
   rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
   if (rc == OCQ_OK) {
-    ocq_status r2 = enqueue_run(b, cs);
+    ocq_status r2 = b->mode == OCQ_BATCH_GRAPH ? enqueue_branches(b, cs) : enqueue_run(b, cs);
     cudaGraph_t g = nullptr;
     rc = cuda_status(cudaStreamEndCapture(cs, &g), "end capture");
     if (rc == OCQ_OK) rc = r2;
@@ -696,11 +740,30 @@ ocq_status ocq_batch_autotune(ocq_batch *b, int reps, void *stream) {
     b->units[k] = bu;
     cache[key] = bu;
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (rc == OCQ_OK) rc = plan_items(b);
   if (rc == OCQ_OK) rc = upload_plan(b, st);
-  free_graph(b);
+  // Then the form: the persistent kernel with the chosen work sizes against
+  // the graph of per-stream branches, each captured and replayed.
+  float t[2] = {1e30f, 1e30f};
+  for (int mode = 0; mode < 2 && rc == OCQ_OK; ++mode) {
+    free_graph(b);
+    b->mode = mode;
+    rc = capture(b);
+    if (rc != OCQ_OK) break;
+    rc = cuda_status(cudaGraphLaunch(b->exec, st), "autotune warm-up");
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && rc == OCQ_OK; ++r) rc = cuda_status(cudaGraphLaunch(b->exec, st), "autotune run");
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&t[mode], e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == OCQ_OK) {
+    const int best = t[1] < t[0] ? OCQ_BATCH_GRAPH : OCQ_BATCH_PERSISTENT;
+    if (best != b->mode) free_graph(b);
+    b->mode = best;
+  }
   return rc;
 }
 
@@ -716,6 +779,9 @@ ocq_status ocq_batch_model(const ocq_batch *b, int i, const ocq_model **out) {
 void ocq_batch_destroy(ocq_batch *b) {
   if (!b) return;
   free_graph(b);
+  for (cudaStream_t s2 : b->side) cudaStreamDestroy(s2);
+  for (cudaEvent_t e2 : b->joins) cudaEventDestroy(e2);
+  if (b->fork) cudaEventDestroy(b->fork);
   for (ocq_model *m : b->models) delete m;  // views: the arena owns the bits
   if (b->arena) cudaFree(b->arena);
   if (b->d_streams) cudaFree(b->d_streams);
@@ -738,7 +804,24 @@ ocq_status ocq_batch_status(ocq_batch *b, void *stream) {
     set_error("a batched item gave up waiting for its stream's model");
     return OCQ_ETIMEOUT;
   }
+  const bool ct = classify_take_timeout(), bt = build_take_timeout();
+  if (ct || bt) {
+    set_error("a kernel of the graph form gave up waiting for a copy");
+    return OCQ_ETIMEOUT;
+  }
   return OCQ_OK;
 }
+
+ocq_status ocq_batch_set_mode(ocq_batch *b, int mode) {
+  if (!b || (mode != OCQ_BATCH_PERSISTENT && mode != OCQ_BATCH_GRAPH)) {
+    set_error("ocq_batch_set_mode: bad arguments");
+    return OCQ_EINVAL;
+  }
+  if (mode != b->mode) free_graph(b);
+  b->mode = mode;
+  return OCQ_OK;
+}
+
+int ocq_batch_get_mode(const ocq_batch *b) { return b ? b->mode : -1; }
 
 }  // extern "C"

@@ -88,6 +88,8 @@ SIGNATURES = {
     "ocq_batch_set_work": (_i32, [_vp, _i32, _i32]),
     "ocq_batch_get_work": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "ocq_batch_autotune": (_i32, [_vp, _i32, _vp]),
+    "ocq_batch_set_mode": (_i32, [_vp, _i32]),
+    "ocq_batch_get_mode": (_i32, [_vp]),
     "ocq_batch_destroy": (None, [_vp]),
     "ocq_server_create": (_i32, [_sz, _i32, ctypes.POINTER(_vp)]),
     "ocq_server_camera_footprint": (_sz, [ctypes.POINTER(ocq_camera_desc)]),
@@ -106,6 +108,7 @@ SIGNATURES = {
 }
 
 OCQ_TUNE_CLASSIFY_PIXEL, OCQ_TUNE_BUILD_PIXEL, OCQ_TUNE_CLASSIFY_PIXEL_DEEP = 0, 1, 2
+OCQ_BATCH_PERSISTENT, OCQ_BATCH_GRAPH = 0, 1
 
 
 def load(path: str | None = None):
@@ -355,6 +358,14 @@ def ocq_batch_get_work(batch, kind):
     u, n = ctypes.c_int(), ctypes.c_int64()
     _check(load().ocq_batch_get_work(batch.handle, kind, ctypes.byref(u), ctypes.byref(n)))
     return u.value, n.value
+
+
+def ocq_batch_set_mode(batch, mode):
+    _check(load().ocq_batch_set_mode(batch.handle, mode))
+
+
+def ocq_batch_get_mode(batch) -> int:
+    return int(load().ocq_batch_get_mode(batch.handle))
 
 
 def ocq_batch_autotune(batch, reps=2, stream=None):

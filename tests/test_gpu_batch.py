@@ -55,12 +55,17 @@ def _plain(ocq, s):
     return words, mask
 
 
-def test_batch_small_mix_matches_plain_and_oracle(ocq):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_small_mix_matches_plain_and_oracle(ocq, mode):
+    """Both forms: the persistent work-list kernel (0) and the graph of
+    per-stream branches (1)."""
     import torch
 
     S = _streams_host(SMALL_MIX, torch)
     b = ocq.ocq.ocq_batch_create(S)
     try:
+        ocq.ocq.ocq_batch_set_mode(b, mode)
+        assert ocq.ocq.ocq_batch_get_mode(b) == mode
         for rep in range(2):  # first run captures the graph, second replays it
             for s in S:
                 s["mask"].fill_(7)
@@ -96,11 +101,14 @@ def test_batch_tiles_and_autotune_keep_results(ocq):
         ocq.ocq.ocq_batch_status(b)
         assert all((s["mask"] == r).all().item() for s, r in zip(S, ref))
         ocq.ocq.ocq_batch_autotune(b, 1)
-        for s in S:
-            s["mask"].fill_(9)
-        ocq.ocq.ocq_batch_run(b)
-        ocq.ocq.ocq_batch_status(b)
-        assert all((s["mask"] == r).all().item() for s, r in zip(S, ref))
+        assert ocq.ocq.ocq_batch_get_mode(b) in (0, 1)
+        for mode in (ocq.ocq.ocq_batch_get_mode(b), 1 - ocq.ocq.ocq_batch_get_mode(b)):
+            ocq.ocq.ocq_batch_set_mode(b, mode)
+            for s in S:
+                s["mask"].fill_(9)
+            ocq.ocq.ocq_batch_run(b)
+            ocq.ocq.ocq_batch_status(b)
+            assert all((s["mask"] == r).all().item() for s, r in zip(S, ref)), mode
     finally:
         b.destroy()
 
@@ -123,6 +131,13 @@ def test_batch_64_stream_preset_matches_plain(ocq):
     try:
         ocq.ocq.ocq_batch_run(b)
         ocq.ocq.ocq_batch_status(b)
+        persistent = [s["mask"].clone() for s in descs]
+        ocq.ocq.ocq_batch_set_mode(b, 1)
+        for s in descs:
+            s["mask"].fill_(5)
+        ocq.ocq.ocq_batch_run(b)
+        ocq.ocq.ocq_batch_status(b)
+        assert all((s["mask"] == p).all().item() for s, p in zip(descs, persistent))
         for i, s in enumerate(descs):
             m = ocq.build_model(s["train"], s["depth"], s["T"], s["kind"], s["block"])
             pmask = ocq.classify(m, s["test"])
