@@ -45,6 +45,9 @@ def parse_args(argv=None):
     ap.add_argument("--batched-reps", type=int, default=3)
     ap.add_argument("--no-serving", action="store_true", help="skip the 256-camera serving simulation")
     ap.add_argument("--serving-seconds", type=float, default=40.0, help="wall-time limit of the serving run")
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None,
+                    help="run one small fixed case twice (warm-up, then the pass to capture) for ncu, print one "
+                         "line and exit; no measurement")
     return ap.parse_args(argv)
 
 
@@ -183,8 +186,8 @@ def measured_peaks():
 
 
 KERNEL_SOURCES = {
-    "classify": ("classify.cu", "pixels.cuh", "ocq_internal.cuh", "async_copy.cuh"),
-    "build": ("build.cu", "pixels.cuh", "ocq_internal.cuh", "async_copy.cuh"),
+    "classify": ("classify.cu", "classify_bodies.cuh", "pixels.cuh", "ocq_internal.cuh", "async_copy.cuh"),
+    "build": ("build.cu", "build_bodies.cuh", "pixels.cuh", "ocq_internal.cuh", "async_copy.cuh"),
 }
 
 
@@ -635,8 +638,47 @@ def run_reference(args):
     }), flush=True)
 
 
+# Small cases for profiler captures: (scene, H, W, N, F, [(region, block, depth)]).
+# Frames of one pass: N + F = 70 frames of 1080p = 435 MB, larger than L2.
+PROFILE_CASES = {
+    "pixel_deep_1080p": ("clusters", 1080, 1920, 30, 40, [(2, 0, 4), (2, 0, 5)]),
+    "block8_1080p": ("clusters", 1080, 1920, 30, 40, [(1, 8, 3), (1, 8, 5)]),
+    "block16_1080p": ("sway", 1080, 1920, 30, 40, [(1, 16, 5)]),
+}
+
+
+def profile_case(args):
+    """Runs PROFILE_CASES[args.profile_case]: for each (region, block, depth),
+    ocq_build_model (T = 10) then ocq_classify, twice."""
+    import torch
+
+    import ocq_synth
+    import paper_1412_1945_gb300 as ocq
+
+    scene, H, W, N, F, runs = PROFILE_CASES[args.profile_case]
+    O = ocq.ocq
+    st = torch.cuda.current_stream()
+    sc = ocq_synth.make_scene(scene, H, W, N, F, 11)
+    tr = torch.empty((N, H, W, 3), dtype=torch.uint8, device="cuda")
+    te = torch.empty((F, H, W, 3), dtype=torch.uint8, device="cuda")
+    ocq_synth.fill_device(sc, 0, N, tr)
+    ocq_synth.fill_device(sc, N, F, te)
+    mask = torch.empty((F, H, W), dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        for region, block, depth in runs:
+            m = O.ocq_build_model(tr, N, H, W, region, block, depth, 10, st)
+            O.ocq_classify(m, te, F, mask, st)
+            m.free()
+    torch.cuda.synchronize()
+    ocq.device_status()
+    print(json.dumps({"profile_case": args.profile_case, "runs": runs, "passes": 2}), flush=True)
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
