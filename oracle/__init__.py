@@ -63,6 +63,12 @@ def _load():
             lib.oracle_tree_stats.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp, vp]
             lib.oracle_leaf_codes.restype = i32
             lib.oracle_leaf_codes.argtypes = [vp, i64, i32, vp]
+            lib.oracle_run_groups.restype = i32
+            lib.oracle_run_groups.argtypes = [vp, i32, i32, vp, i32, i32, i32, i32, i32, i32, i32, vp, i64, vp, vp]
+            lib.oracle_redraw.restype = i32
+            lib.oracle_redraw.argtypes = [vp, i64, i32, vp]
+            lib.oracle_confusion.restype = i32
+            lib.oracle_confusion.argtypes = [vp, vp, i64, i64, vp]
             _lib = lib
     return _lib
 
@@ -116,9 +122,11 @@ def _gathered_size(H, W, kind, block, regs, F):
     return total * F
 
 
-def run(train, depth, T, kind, block=0, test=None, regions=None):
+def run(train, depth, T, kind, block=0, test=None, regions=None, group=1):
     """Build the merged model from ``train`` (uint8[N,H,W,3]) and classify
-    ``test`` with Check Color on the merged trees.
+    ``test`` with Check Color on the merged trees.  ``group`` > 1 builds one
+    tree per group of that many consecutive frames (Sec. 3) and T counts
+    groups.
 
     Returns ``(model, mask)``: ``model`` is uint64[n_regions, words_per_region]
     (rows follow ``regions`` when given); ``mask`` is uint8[F,H,W] (or, with
@@ -144,9 +152,9 @@ def run(train, depth, T, kind, block=0, test=None, regions=None):
             mask = np.zeros((F, H, W), dtype=np.uint8)
         else:
             mask = np.zeros(_gathered_size(H, W, kind, block, regs, F), dtype=np.uint8)
-    rc = lib.oracle_run(train.ctypes.data, N, _ptr(test), F, H, W, kind, block, depth, T,
-                        _ptr(regs), nreg, model.ctypes.data, _ptr(mask))
-    _check(rc, "oracle_run")
+    rc = lib.oracle_run_groups(train.ctypes.data, N, group, _ptr(test), F, H, W, kind, block, depth, T,
+                               _ptr(regs), nreg, model.ctypes.data, _ptr(mask))
+    _check(rc, "oracle_run_groups")
     return model, mask
 
 
@@ -196,3 +204,45 @@ def leaf_codes(rgb, depth):
     rc = lib.oracle_leaf_codes(rgb.ctypes.data, rgb.shape[0], depth, out.ctypes.data)
     _check(rc, "oracle_leaf_codes")
     return out
+
+
+def redraw(rgb, depth):
+    """Each colour of ``rgb`` (uint8[..., 3]) redrawn as its leaf in a tree
+    pruned at ``depth`` levels (Sec. 2, Fig. 2)."""
+    lib = _load()
+    a = np.ascontiguousarray(rgb, dtype=np.uint8)
+    out = np.empty_like(a)
+    rc = lib.oracle_redraw(a.ctypes.data, a.size // 3, depth, out.ctypes.data)
+    _check(rc, "oracle_redraw")
+    return out
+
+
+def confusion(mask, gt):
+    """Per frame {Tp, Fp, Tn, Fn} of a foreground mask (uint8[F, H, W], non-zero
+    = foreground) against ground truth of the same shape (Sec. 5)."""
+    lib = _load()
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    g = np.ascontiguousarray(gt, dtype=np.uint8)
+    if m.shape != g.shape or m.ndim < 2:
+        raise ValueError("mask and gt must have the same shape [F, ...]")
+    F = m.shape[0]
+    out = np.zeros((F, 4), dtype=np.uint64)
+    rc = lib.oracle_confusion(m.ctypes.data, g.ctypes.data, F, m[0].size, out.ctypes.data)
+    _check(rc, "oracle_confusion")
+    return out
+
+
+def f_scores(counts):
+    """The paper's F0 (Sec. 5): P0 = Tn / (Tn + Fn), R0 = Tn / (Tn + Fp),
+    F0 = 2 P0 R0 / (P0 + R0); also the foreground F1 = 2 Tp / (2 Tp + Fp + Fn).
+    ``counts`` = {Tp, Fp, Tn, Fn} (summed over frames when 2-D).  A ratio with
+    a zero denominator is taken as 1 (nothing to get wrong)."""
+    c = np.asarray(counts, dtype=np.float64)
+    if c.ndim == 2:
+        c = c.sum(axis=0)
+    tp, fp, tn, fn = c
+    p0 = tn / (tn + fn) if tn + fn else 1.0
+    r0 = tn / (tn + fp) if tn + fp else 1.0
+    f0 = 2 * p0 * r0 / (p0 + r0) if p0 + r0 else 0.0
+    f1 = 2 * tp / (2 * tp + fp + fn) if 2 * tp + fp + fn else 1.0
+    return {"P0": p0, "R0": r0, "F0": f0, "F1": f1}

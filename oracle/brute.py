@@ -57,6 +57,22 @@ def model_sets(train, d, T, kind, block=0):
     return [{c for c, k in cnt.items() if k >= T} for cnt in counts]
 
 
+def model_sets_groups(train, d, T, kind, block=0, group=1):
+    """Per region, the set of leaves present in at least T of the trees built
+    from groups of ``group`` consecutive training frames (Sec. 3): a group's
+    tree holds every leaf of any of its frames."""
+    N, H, W, _ = train.shape
+    counts = [Counter() for _ in range(n_regions(H, W, kind, block))]
+    for g0 in range(0, N, group):
+        union = [set() for _ in counts]
+        for f in range(g0, min(N, g0 + group)):
+            for r, s in enumerate(frame_leaf_sets(train[f], d, kind, block)):
+                union[r] |= s
+        for r, s in enumerate(union):
+            counts[r].update(s)
+    return [{c for c, k in cnt.items() if k >= T} for cnt in counts]
+
+
 def classify(msets, frames, d, kind, block=0):
     """uint8 mask list-of-lists: 1 = foreground (leaf not in the region's model)."""
     F, H, W, _ = frames.shape

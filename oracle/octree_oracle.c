@@ -225,20 +225,27 @@ static int check_args(int H, int W, int kind, int block, int depth) {
   return 0;
 }
 
-/* Builds the N per-frame trees of region r (Store Color over the region's
- * pixels of each training frame). */
-static int build_region_trees(const uint8_t *frames, int N, int H, int W, int kind, int block, int depth,
-                              int64_t r, octree_node **roots) {
+/* Number of trees when one tree holds `group` consecutive frames (Sec. 3:
+ * "a tree for each frame ... or a group of frames"); the last group holds
+ * the remaining frames. */
+static int tree_count(int N, int group) { return (N + group - 1) / group; }
+
+/* Builds the trees of region r: tree j holds the region's pixels of training
+ * frames [j*group, j*group + group) (Store Color over each pixel); group = 1
+ * gives one tree per frame. */
+static int build_region_trees(const uint8_t *frames, int N, int group, int H, int W, int kind, int block,
+                              int depth, int64_t r, octree_node **roots) {
   int y0, y1, x0, x1;
   region_rect(H, W, kind, block, r, &y0, &y1, &x0, &x1);
-  for (int f = 0; f < N; ++f) roots[f] = NULL;
+  for (int j = 0; j < tree_count(N, group); ++j) roots[j] = NULL;
   for (int f = 0; f < N; ++f) {
+    octree_node **root = &roots[f / group];
     for (int y = y0; y < y1; ++y)
       for (int x = x0; x < x1; ++x) {
         const uint8_t *p = frames + (((size_t)f * H + y) * W + x) * 3;
-        octree_node *nr = store_color(roots[f], p[0], p[1], p[2], depth);
+        octree_node *nr = store_color(*root, p[0], p[1], p[2], depth);
         if (!nr) return 1;
-        roots[f] = nr;
+        *root = nr;
       }
   }
   return 0;
@@ -274,13 +281,21 @@ static void classify_region(const octree_node *tree, const uint8_t *frames, int 
  *   listed region, each frame, its pixels in row-major order (may be NULL).
  * Returns 0 on success, 1 on bad arguments, 2 on allocation failure.
  */
-int oracle_run(const uint8_t *train, int N, const uint8_t *test, int F, int H, int W, int kind, int block,
-               int depth, int T, const int64_t *regions, int64_t nreg, uint64_t *model_out, uint8_t *mask_out) {
-  if (check_args(H, W, kind, block, depth) || N < 1 || T < 1 || T > N || F < 0 || !train) return 1;
+/*
+ * As oracle_run, with one tree per group of `group` consecutive training
+ * frames (Sec. 3); T counts groups, 1 <= T <= ceil(N / group).
+ */
+int oracle_run_groups(const uint8_t *train, int N, int group, const uint8_t *test, int F, int H, int W, int kind,
+                      int block, int depth, int T, const int64_t *regions, int64_t nreg, uint64_t *model_out,
+                      uint8_t *mask_out) {
+  if (check_args(H, W, kind, block, depth) || N < 1 || group < 1 || T < 1 || T > tree_count(N, group) || F < 0 ||
+      !train)
+    return 1;
+  const int G = tree_count(N, group);
   const int64_t R = oracle_region_count(H, W, kind, block);
   const int64_t nr = regions ? nreg : R;
   const int64_t wpr = words_per_region(depth);
-  octree_node **roots = (octree_node **)malloc(sizeof(octree_node *) * (size_t)N);
+  octree_node **roots = (octree_node **)malloc(sizeof(octree_node *) * (size_t)G);
   if (!roots) return 2;
   size_t cursor = 0;
   int rc = 0;
@@ -290,11 +305,11 @@ int oracle_run(const uint8_t *train, int N, const uint8_t *test, int F, int H, i
       rc = 1;
       break;
     }
-    if (build_region_trees(train, N, H, W, kind, block, depth, r, roots)) rc = 2;
+    if (build_region_trees(train, N, group, H, W, kind, block, depth, r, roots)) rc = 2;
     int oom = 0;
-    octree_node *merged = rc ? NULL : merge_trees(roots, N, T, 0, depth, &oom);
+    octree_node *merged = rc ? NULL : merge_trees(roots, G, T, 0, depth, &oom);
     if (oom) rc = 2;
-    for (int f = 0; f < N; ++f) free_tree(roots[f]);
+    for (int j = 0; j < G; ++j) free_tree(roots[j]);
     if (rc == 0 && model_out) {
       uint64_t *row = model_out + (size_t)k * (size_t)wpr;
       memset(row, 0, sizeof(uint64_t) * (size_t)wpr);
@@ -306,6 +321,12 @@ int oracle_run(const uint8_t *train, int N, const uint8_t *test, int F, int H, i
   }
   free(roots);
   return rc;
+}
+
+/* One tree per training frame (Sec. 3, the hot path's case). */
+int oracle_run(const uint8_t *train, int N, const uint8_t *test, int F, int H, int W, int kind, int block,
+               int depth, int T, const int64_t *regions, int64_t nreg, uint64_t *model_out, uint8_t *mask_out) {
+  return oracle_run_groups(train, N, 1, test, F, H, W, kind, block, depth, T, regions, nreg, model_out, mask_out);
 }
 
 /* Build only: oracle_run without test frames. */
@@ -352,7 +373,7 @@ int oracle_tree_stats(const uint8_t *frame, int H, int W, int kind, int block, i
   const int64_t R = oracle_region_count(H, W, kind, block);
   for (int64_t r = 0; r < R; ++r) {
     octree_node *root = NULL;
-    if (build_region_trees(frame, 1, H, W, kind, block, depth, r, &root)) {
+    if (build_region_trees(frame, 1, 1, H, W, kind, block, depth, r, &root)) {
       free_tree(root);
       return 2;
     }
@@ -399,3 +420,47 @@ int oracle_leaf_codes(const uint8_t *rgb, int64_t n, int depth, uint32_t *codes_
 }
 
 int64_t oracle_words_per_region(int depth) { return (depth < 1 || depth > 8) ? -1 : words_per_region(depth); }
+
+/*
+ * Redraw (Sec. 2, Fig. 2): each colour is stored in a tree pruned at `depth`
+ * levels, and the newly exposed leaf gives the colour back with the depth
+ * original bits of each channel and zeros below.  The leaf's bits are read off
+ * its path: level l's child index carries bit 7 - l of red, green and blue.
+ */
+int oracle_redraw(const uint8_t *rgb, int64_t n, int depth, uint8_t *out) {
+  if (depth < 1 || depth > 8 || n < 0 || (n > 0 && (!rgb || !out))) return 1;
+  for (int64_t k = 0; k < n; ++k) {
+    const uint8_t r = rgb[3 * k], g = rgb[3 * k + 1], b = rgb[3 * k + 2];
+    uint8_t lr = 0, lg = 0, lb = 0;
+    for (int i = 7; i >= 8 - depth; --i) {
+      const int index = child_index(r, g, b, i);
+      lr |= (uint8_t)(((index >> 2) & 1) << i);
+      lg |= (uint8_t)(((index >> 1) & 1) << i);
+      lb |= (uint8_t)((index & 1) << i);
+    }
+    out[3 * k] = lr, out[3 * k + 1] = lg, out[3 * k + 2] = lb;
+  }
+  return 0;
+}
+
+/*
+ * Confusion counts of a foreground mask against ground truth, per frame
+ * (Sec. 5: true/false positives and negatives; foreground = positive, a
+ * non-zero byte is foreground in both).  counts_out: F rows of
+ * {Tp, Fp, Tn, Fn}.
+ */
+int oracle_confusion(const uint8_t *mask, const uint8_t *gt, int64_t F, int64_t npix, uint64_t *counts_out) {
+  if (F < 0 || npix < 0 || !counts_out || (F > 0 && npix > 0 && (!mask || !gt))) return 1;
+  for (int64_t f = 0; f < F; ++f) {
+    uint64_t tp = 0, fp = 0, tn = 0, fn = 0;
+    for (int64_t p = 0; p < npix; ++p) {
+      const int predicted = mask[f * npix + p] != 0, actual = gt[f * npix + p] != 0;
+      if (predicted && actual) ++tp;
+      else if (predicted && !actual) ++fp;
+      else if (!predicted && !actual) ++tn;
+      else ++fn;
+    }
+    counts_out[4 * f] = tp, counts_out[4 * f + 1] = fp, counts_out[4 * f + 2] = tn, counts_out[4 * f + 3] = fn;
+  }
+  return 0;
+}
