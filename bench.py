@@ -44,6 +44,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-stream batched-vs-plain measurement")
     ap.add_argument("--batched-reps", type=int, default=3)
     ap.add_argument("--no-serving", action="store_true", help="skip the 256-camera serving simulation")
+    ap.add_argument("--no-next", action="store_true",
+                    help="skip the redraw / F0 evaluation / group-of-frames measurements")
     ap.add_argument("--serving-seconds", type=float, default=40.0, help="wall-time limit of the serving run")
     ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None,
                     help="run one small fixed case twice (warm-up, then the pass to capture) for ncu, print one "
@@ -367,6 +369,8 @@ def run_ours(args):
         "clocks": clocks,
     }
 
+    if not args.no_next:
+        result["next"] = next_measure(ocq, wl, sc, train, test, mask, stream, dev, peak)
     if not args.no_batched:
         result["batched"] = batched_measure(ocq, dev, args.batched_reps)
     if not args.no_serving:
@@ -384,6 +388,71 @@ def run_ours(args):
     if rank == 0:
         print(json.dumps(result), flush=True)
     dist.close()
+
+
+def next_measure(ocq, wl, sc, train, test, mask, stream, dev, peak, reps=5):
+    """The paths beyond the four steps, on the same 1080p workload:
+    * F0 (Sec. 5) of the step's masks against the generator's ground truth, and
+      the confusion-count kernel's throughput (mask + truth bytes);
+    * redraw (Sec. 2, Fig. 2) of 200 test frames at the model's depth (RGB in
+      and out);
+    * the build with one tree per group of 5 frames (Sec. 3)."""
+    import torch
+
+    import ocq_synth
+
+    H, W, N, F = wl.H, wl.W, wl.N, wl.F
+    hw = H * W
+    gt = torch.empty((F, H, W), dtype=torch.uint8, device=dev)
+    chunk = 100
+    tmp = torch.empty((chunk, H, W, 3), dtype=torch.uint8, device=dev)
+    for f0 in range(0, F, chunk):
+        n = min(chunk, F - f0)
+        ocq_synth.fill_device(sc, N + f0, n, tmp[:n], gt[f0:f0 + n])
+    del tmp
+    counts = torch.empty((F, 4), dtype=torch.int64, device=dev)
+
+    def timed(fn):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    conf_ms = timed(lambda: ocq.ocq.ocq_confusion(mask, gt, F, hw, counts, stream))
+    tot = counts.sum(dim=0).cpu().tolist()
+    sc_ = ocq.f_scores(tot)
+    conf_bytes = 2 * F * hw
+    nr = min(200, F)
+    out = torch.empty((nr, H, W, 3), dtype=torch.uint8, device=dev)
+    red_ms = timed(lambda: ocq.ocq.ocq_redraw(test, nr * hw, wl.depth, out, stream))
+    red_bytes = 6 * nr * hw
+    del out
+
+    def grouped():
+        m = ocq.ocq.ocq_build_model_groups(train, N, H, W, wl.region, wl.block, wl.depth, 2, 5, stream)
+        m.free()
+    grp_ms = timed(grouped)
+    del gt, counts
+    torch.cuda.empty_cache()
+    return {
+        "f0": {"value": round(sc_["F0"], 6), "P0": round(sc_["P0"], 6), "R0": round(sc_["R0"], 6),
+               "F1_foreground": round(sc_["F1"], 6), "Tp_Fp_Tn_Fn": [int(v) for v in tot],
+               "frames": F, "truth": "generator's object masks"},
+        "confusion_kernel": {"ms": round(conf_ms, 4), "gbs": round(conf_bytes / (conf_ms / 1e3) / 1e9, 1),
+                             "hbm_frac": round(conf_bytes / (conf_ms / 1e3) / 1e9 / peak, 4),
+                             "algorithmic_bytes": conf_bytes},
+        "redraw": {"frames": nr, "depth": wl.depth, "ms": round(red_ms, 4),
+                   "mpixel_s": round(nr * hw / (red_ms / 1e3) / 1e6, 1),
+                   "gbs": round(red_bytes / (red_ms / 1e3) / 1e9, 1),
+                   "hbm_frac": round(red_bytes / (red_ms / 1e3) / 1e9 / peak, 4), "algorithmic_bytes": red_bytes},
+        "group_of_frames_build": {"group": 5, "T": 2, "trees": -(-N // 5), "ms": round(grp_ms, 4),
+                                  "mpixel_s": round(N * hw / (grp_ms / 1e3) / 1e6, 1)},
+    }
 
 
 def batched_measure(ocq, dev, reps):

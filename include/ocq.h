@@ -159,6 +159,40 @@ ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int
                            int depth, int T, uint8_t *mask, void *stream, ocq_model **out_model);
 
 /*
+ * One tree per group of `group` consecutive training frames instead of one per
+ * frame (Sec. 3: "a tree for each frame ... or a group of frames"; the last
+ * group holds the remaining frames).  A group's tree holds every leaf of any
+ * of its frames; T counts trees: 1 <= T <= ceil(N / group).  group = 1 is
+ * ocq_build_model.  Same buffers, ownership and errors as ocq_build_model.
+ */
+ocq_status ocq_build_model_groups(const uint8_t *frames, int N, int H, int W, ocq_region region, int depth, int T,
+                                  int group, void *stream, ocq_model **out);
+
+/*
+ * Redraw (Sec. 2, Fig. 2): each pixel's colour becomes the colour of its leaf
+ * in a tree pruned at `depth` levels, i.e. the depth most significant bits of
+ * each channel followed by zeros.  rgb, out: device, npix*3 bytes (HWC RGB8);
+ * out may equal rgb (in place).  Asynchronous on `stream`.
+ */
+ocq_status ocq_redraw(const uint8_t *rgb, int64_t npix, int depth, uint8_t *out, void *stream);
+
+/*
+ * Evaluation against ground truth (Sec. 5).  mask, gt: device, F*npix bytes
+ * (frame-major; a non-zero byte is foreground in both).  counts: device,
+ * F*4 u64 written as {Tp, Fp, Tn, Fn} per frame (foreground = positive).
+ * Asynchronous on `stream`.
+ */
+ocq_status ocq_confusion(const uint8_t *mask, const uint8_t *gt, int F, int64_t npix, uint64_t *counts,
+                         void *stream);
+/*
+ * Host: from counts {Tp, Fp, Tn, Fn} (one frame or their sum), the paper's
+ * scores out[0] = P0 = Tn/(Tn+Fn), out[1] = R0 = Tn/(Tn+Fp),
+ * out[2] = F0 = 2 P0 R0/(P0+R0), and out[3] = foreground F1 = 2Tp/(2Tp+Fp+Fn);
+ * a ratio with a zero denominator is 1.
+ */
+ocq_status ocq_f_scores(const uint64_t *counts, double *out);
+
+/*
  * Batched form (no counterpart in the paper, which handles one video): many
  * camera streams, each with its own frame size, region kind and depth, are
  * built (S1-S3) and classified (S4) by one CUDA graph, captured once and

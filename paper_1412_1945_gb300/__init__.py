@@ -92,3 +92,36 @@ def occupancy(frames, depth: int, kind="frame", block: int = 0, stream=None):
 def device_status(stream=None):
     """Synchronise and raise OcqError(OCQ_ETIMEOUT) if a bounded device wait gave up."""
     ocq.ocq_device_status(stream)
+
+
+def build_model_groups(frames, depth: int, T: int, group: int, kind="pixel", block: int = 0, stream=None) -> Model:
+    """S1-S3 with one tree per group of ``group`` consecutive frames; T counts trees."""
+    _frames(frames)
+    N, H, W, _ = frames.shape
+    return ocq.ocq_build_model_groups(frames, N, H, W, _kind(kind), block, depth, T, group, stream)
+
+
+def redraw(rgb, depth: int, out=None, stream=None):
+    """Each colour of ``rgb`` (CUDA uint8, last dim 3) as its leaf colour at ``depth``."""
+    import torch
+
+    if out is None:
+        out = torch.empty_like(rgb)
+    ocq.ocq_redraw(rgb, rgb.numel() // 3, depth, out, stream)
+    return out
+
+
+def confusion(mask, gt, stream=None):
+    """Per frame {Tp, Fp, Tn, Fn} of ``mask`` against ``gt`` (CUDA uint8 [F, ...]) as int64 [F, 4]."""
+    import torch
+
+    F = mask.shape[0]
+    counts = torch.empty((F, 4), dtype=torch.int64, device=mask.device)
+    ocq.ocq_confusion(mask, gt, F, mask[0].numel() if F else 0, counts, stream)
+    return counts
+
+
+def f_scores(counts):
+    """P0, R0, F0 (the paper's Sec. 5 scores) and foreground F1 from counts {Tp, Fp, Tn, Fn}."""
+    p0, r0, f0, f1 = ocq.ocq_f_scores(counts)
+    return {"P0": p0, "R0": r0, "F0": f0, "F1": f1}

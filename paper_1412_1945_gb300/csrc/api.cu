@@ -172,6 +172,34 @@ ocq_status ocq_build_model(const uint8_t *frames, int N, int H, int W, ocq_regio
   return OCQ_OK;
 }
 
+ocq_status ocq_build_model_groups(const uint8_t *frames, int N, int H, int W, ocq_region region, int depth, int T,
+                                  int group, void *stream, ocq_model **out) {
+  g_err[0] = 0;
+  if (!out) {
+    set_error("ocq_build_model_groups: out is NULL");
+    return OCQ_EINVAL;
+  }
+  *out = nullptr;
+  ocq_status rc = check_geometry(H, W, region, depth);
+  if (rc != OCQ_OK) return rc;
+  const int G = group >= 1 ? (N + group - 1) / group : 0;
+  if (!frames || N < 1 || N > 65535 || group < 1 || T < 1 || T > G || (int64_t)N * H * W >= kMaxPixels) {
+    set_error("ocq_build_model_groups: need frames != NULL, 1 <= N <= 65535, group >= 1 and "
+              "1 <= T <= ceil(N / group) (N=%d, group=%d, T=%d)", N, group, T);
+    return OCQ_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  ocq_model *m = new_model(H, W, region, depth, T, N, st, &rc);
+  if (!m) return rc;
+  rc = launch_build_groups(frames, N, group, m, st);
+  if (rc != OCQ_OK) {
+    ocq_model_free(m);
+    return rc;
+  }
+  *out = m;
+  return OCQ_OK;
+}
+
 ocq_status ocq_classify(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, void *stream) {
   g_err[0] = 0;
   if (!m || F < 0 || (F > 0 && (!frames || !mask)) || (int64_t)F * m->H * m->W >= kMaxPixels) {

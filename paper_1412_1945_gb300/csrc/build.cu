@@ -38,13 +38,13 @@ static int bit_length(uint32_t v) {
 
 template <int D>
 __global__ void __launch_bounds__(256) occ_frame_kernel(const uint8_t *__restrict__ frames, int64_t hw, int f0,
-                                                        int64_t chunk, uint32_t *__restrict__ occ) {
-  occ_frame_body<D>(frames, hw, f0, chunk, occ, blockIdx.x, blockIdx.y);
+                                                        int64_t chunk, uint32_t *__restrict__ occ, int group) {
+  occ_frame_body<D>(frames, hw, f0, chunk, occ, blockIdx.x, blockIdx.y, group);
 }
 
 __global__ void occ_global_kernel(const uint8_t *__restrict__ frames, int H, int W, int kind, int block, int d,
-                                  int f0, int nf, int64_t R, int64_t wpr, uint32_t *__restrict__ occ) {
-  occ_global_body(frames, H, W, kind, block, d, f0, nf, R, wpr, occ, blockIdx.x, gridDim.x);
+                                  int f0, int nf, int64_t R, int64_t wpr, uint32_t *__restrict__ occ, int group) {
+  occ_global_body(frames, H, W, kind, block, d, f0, nf, R, wpr, occ, blockIdx.x, gridDim.x, group);
 }
 
 __global__ void planes_merge_kernel(const uint32_t *__restrict__ occ, int nb, int64_t nwords,
@@ -433,23 +433,28 @@ static unsigned grid_cap(int64_t work, int threads, int per_sm) {
 }
 
 template <int D>
-static void launch_occ_frame(const uint8_t *frames, int64_t hw, int f0, int nf, uint32_t *occ, cudaStream_t st) {
+static void launch_occ_frame(const uint8_t *frames, int64_t hw, int f0, int nf, uint32_t *occ, int group,
+                             cudaStream_t st) {
   const int64_t chunk = 256 * 16 * 4;  // pixels per CTA (multiple of 16)
   constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
   dim3 grid((unsigned)((hw + chunk - 1) / chunk), (unsigned)nf);
-  occ_frame_kernel<D><<<grid, 256, WPR * 4, st>>>(frames, hw, f0, chunk, occ);
+  occ_frame_kernel<D><<<grid, 256, WPR * 4, st>>>(frames, hw, f0, chunk, occ, group);
   count_launch();
 }
 
-static ocq_status build_dense(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
-  const int P = bit_length((uint32_t)N);
+// Dense path: per-tree leaf bitsets in scratch, folded into bit-sliced
+// counters.  One tree per group of `group` consecutive frames (Sec. 3; the
+// last group holds the rest); T counts trees.  Scratch is batched by trees.
+static ocq_status build_dense(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st, int group = 1) {
+  const int G = (N + group - 1) / group;
+  const int P = bit_length((uint32_t)G);
   const int64_t nwords = m->R * m->wpr;
   const int64_t hw = (int64_t)m->H * m->W;
   const int64_t budget = (int64_t)512 << 20;
-  int nb = N;
-  if ((int64_t)N * nwords * 4 > budget) nb = (int)(budget / (nwords * 4) > 0 ? budget / (nwords * 4) : 1);
-  if (nb > N) nb = N;
-  const bool multi = nb < N;
+  int nb = G;
+  if ((int64_t)G * nwords * 4 > budget) nb = (int)(budget / (nwords * 4) > 0 ? budget / (nwords * 4) : 1);
+  if (nb > G) nb = G;
+  const bool multi = nb < G;
   uint32_t *occ = nullptr, *planes = nullptr;
   ocq_status rc = cuda_status(cudaMallocAsync((void **)&occ, (size_t)nb * nwords * 4, st), "build scratch");
   if (rc != OCQ_OK) return rc;
@@ -460,28 +465,31 @@ static ocq_status build_dense(const uint8_t *frames, int N, ocq_model *m, cudaSt
       return rc;
     }
   }
-  for (int f0 = 0; f0 < N && rc == OCQ_OK; f0 += nb) {
-    const int nf = N - f0 < nb ? N - f0 : nb;
-    rc = cuda_status(cudaMemsetAsync(occ, 0, (size_t)nf * nwords * 4, st), "clear occupancy");
+  for (int s0 = 0; s0 < G && rc == OCQ_OK; s0 += nb) {
+    const int ns = G - s0 < nb ? G - s0 : nb;
+    const int f0 = s0 * group;
+    const int f1 = (s0 + ns) * group < N ? (s0 + ns) * group : N;
+    const int nf = f1 - f0;
+    rc = cuda_status(cudaMemsetAsync(occ, 0, (size_t)ns * nwords * 4, st), "clear occupancy");
     if (rc != OCQ_OK) break;
     if (m->kind == OCQ_REGION_FRAME && m->depth <= 6) {
       switch (m->depth) {
-        case 1: launch_occ_frame<1>(frames, hw, f0, nf, occ, st); break;
-        case 2: launch_occ_frame<2>(frames, hw, f0, nf, occ, st); break;
-        case 3: launch_occ_frame<3>(frames, hw, f0, nf, occ, st); break;
-        case 4: launch_occ_frame<4>(frames, hw, f0, nf, occ, st); break;
-        case 5: launch_occ_frame<5>(frames, hw, f0, nf, occ, st); break;
-        default: launch_occ_frame<6>(frames, hw, f0, nf, occ, st); break;
+        case 1: launch_occ_frame<1>(frames, hw, f0, nf, occ, group, st); break;
+        case 2: launch_occ_frame<2>(frames, hw, f0, nf, occ, group, st); break;
+        case 3: launch_occ_frame<3>(frames, hw, f0, nf, occ, group, st); break;
+        case 4: launch_occ_frame<4>(frames, hw, f0, nf, occ, group, st); break;
+        case 5: launch_occ_frame<5>(frames, hw, f0, nf, occ, group, st); break;
+        default: launch_occ_frame<6>(frames, hw, f0, nf, occ, group, st); break;
       }
     } else {
       occ_global_kernel<<<grid_cap(hw * nf, 256, 16), 256, 0, st>>>(frames, m->H, m->W, m->kind, m->block, m->depth,
-                                                                     f0, nf, m->R, m->wpr, occ);
+                                                                     f0, nf, m->R, m->wpr, occ, group);
       count_launch();
     }
     rc = cuda_status(cudaGetLastError(), "occupancy kernel");
     if (rc != OCQ_OK) break;
-    planes_merge_kernel<<<grid_cap(nwords, 256, 8), 256, 0, st>>>(occ, nf, nwords, planes, P, f0 == 0,
-                                                                   f0 + nf >= N, (uint32_t)m->T, m->bits);
+    planes_merge_kernel<<<grid_cap(nwords, 256, 8), 256, 0, st>>>(occ, ns, nwords, planes, P, s0 == 0,
+                                                                   s0 + ns >= G, (uint32_t)m->T, m->bits);
     count_launch();
     rc = cuda_status(cudaGetLastError(), "planes_merge_kernel");
   }
@@ -818,6 +826,11 @@ bool build_take_timeout() {
   return flag != 0;
 }
 
+ocq_status launch_build_groups(const uint8_t *frames, int N, int group, ocq_model *m, cudaStream_t st) {
+  if (group == 1) return launch_build(frames, N, m, st);
+  return build_dense(frames, N, m, st, group);
+}
+
 ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
   const int d = m->depth;
   if (m->kind == OCQ_REGION_FRAME || (m->kind == OCQ_REGION_BLOCK && d >= 6)) return build_dense(frames, N, m, st);
@@ -942,16 +955,16 @@ extern "C" ocq_status ocq_build_frame_noalloc(const uint8_t *frames, int N, int 
     if (rc != OCQ_OK) break;
     if (depth <= 6) {
       switch (depth) {
-        case 1: launch_occ_frame<1>(frames, hw, f0, nf, occ, st); break;
-        case 2: launch_occ_frame<2>(frames, hw, f0, nf, occ, st); break;
-        case 3: launch_occ_frame<3>(frames, hw, f0, nf, occ, st); break;
-        case 4: launch_occ_frame<4>(frames, hw, f0, nf, occ, st); break;
-        case 5: launch_occ_frame<5>(frames, hw, f0, nf, occ, st); break;
-        default: launch_occ_frame<6>(frames, hw, f0, nf, occ, st); break;
+        case 1: launch_occ_frame<1>(frames, hw, f0, nf, occ, 1, st); break;
+        case 2: launch_occ_frame<2>(frames, hw, f0, nf, occ, 1, st); break;
+        case 3: launch_occ_frame<3>(frames, hw, f0, nf, occ, 1, st); break;
+        case 4: launch_occ_frame<4>(frames, hw, f0, nf, occ, 1, st); break;
+        case 5: launch_occ_frame<5>(frames, hw, f0, nf, occ, 1, st); break;
+        default: launch_occ_frame<6>(frames, hw, f0, nf, occ, 1, st); break;
       }
     } else {
       occ_global_kernel<<<grid_cap(hw * nf, 256, 16), 256, 0, st>>>(frames, H, W, OCQ_REGION_FRAME, 0, depth, f0, nf, 1,
-                                                                     wpr, occ);
+                                                                     wpr, occ, 1);
       count_launch();
     }
     rc = cuda_status(cudaGetLastError(), "occupancy kernel");

@@ -51,10 +51,11 @@ __device__ __forceinline__ uint32_t planes_ge_reg(const uint32_t (&pl)[MAXP], in
 // ---- dense per-frame occupancy ----------------------------------------------
 
 // Whole-frame regions, depth <= 6: CTA (x, y) marks the leaves of pixel chunk x
-// of frame f0 + y in a shared bitset, then ORs it into occ[y].
+// of frame f0 + y in a shared bitset, then ORs it into occ[y / group] (frames
+// of one group share a tree, Sec. 3; group = 1: one tree per frame).
 template <int D>
 __device__ __forceinline__ void occ_frame_body(const uint8_t *__restrict__ frames, int64_t hw, int f0, int64_t chunk,
-                                               uint32_t *__restrict__ occ, int64_t bx, int64_t by) {
+                                               uint32_t *__restrict__ occ, int64_t bx, int64_t by, int group = 1) {
   constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
   extern __shared__ uint32_t seen[];  // [WPR]
   for (int i = threadIdx.x; i < WPR; i += blockDim.x) seen[i] = 0;
@@ -67,16 +68,16 @@ __device__ __forceinline__ void occ_frame_body(const uint8_t *__restrict__ frame
     if (!(seen[q >> 5] & m)) atomicOr(&seen[q >> 5], m);
   });
   __syncthreads();
-  uint32_t *dst = occ + by * WPR;
+  uint32_t *dst = occ + (by / group) * WPR;
   for (int i = threadIdx.x; i < WPR; i += blockDim.x)
     if (seen[i]) atomicOr(&dst[i], seen[i]);
 }
 
 // Any region kind and depth: one thread per pixel, global atomics into
-// occ[(f - f0) * R + r][...].
+// occ[((f - f0) / group) * R + r][...].
 __device__ __forceinline__ void occ_global_body(const uint8_t *__restrict__ frames, int H, int W, int kind, int block,
                                                 int d, int f0, int nf, int64_t R, int64_t wpr,
-                                                uint32_t *__restrict__ occ, int64_t vb, int64_t vg) {
+                                                uint32_t *__restrict__ occ, int64_t vb, int64_t vg, int group = 1) {
   const int64_t hw = (int64_t)H * W;
   const int64_t npix = hw * nf;
   const int bw = kind == OCQ_REGION_BLOCK ? (W + block - 1) / block : 1;
@@ -86,7 +87,7 @@ __device__ __forceinline__ void occ_global_body(const uint8_t *__restrict__ fram
     const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
     const uint8_t *px = base + i * 3;
     const uint32_t q = planar_code_rt(__ldg(px), __ldg(px + 1), __ldg(px + 2), d);
-    uint32_t *word = occ + (f * R + region_of(y, x, W, kind, block, bw)) * wpr + (q >> 5);
+    uint32_t *word = occ + ((f / group) * R + region_of(y, x, W, kind, block, bw)) * wpr + (q >> 5);
     const uint32_t m = 1u << (q & 31);
     if (!(*(volatile uint32_t *)word & m)) atomicOr(word, m);
   }

@@ -145,6 +145,7 @@ __device__ __forceinline__ uint32_t group_pixel(const uint32_t (&w)[12]) {
 // ---- kernel launchers (build.cu, classify.cu, transform.cu) -------------------
 ocq_status launch_path_code(const uint8_t *rgb, int64_t npix, int depth, uint32_t *codes, cudaStream_t st);
 ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st);
+ocq_status launch_build_groups(const uint8_t *frames, int N, int group, ocq_model *m, cudaStream_t st);
 ocq_status launch_classify(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st);
 ocq_status launch_occupancy(const uint8_t *frames, int n, int H, int W, int kind, int block, int depth,
                             uint64_t *occ, cudaStream_t st);

@@ -89,6 +89,11 @@ SIGNATURES = {
     "ocq_batch_get_work": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "ocq_batch_autotune": (_i32, [_vp, _i32, _vp]),
     "ocq_batch_set_mode": (_i32, [_vp, _i32]),
+    "ocq_build_model_groups": (_i32, [_vp, _i32, _i32, _i32, ocq_region, _i32, _i32, _i32, _vp,
+                                      ctypes.POINTER(_vp)]),
+    "ocq_redraw": (_i32, [_vp, _i64, _i32, _vp, _vp]),
+    "ocq_confusion": (_i32, [_vp, _vp, _i32, _i64, _vp, _vp]),
+    "ocq_f_scores": (_i32, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_double)]),
     "ocq_batch_get_mode": (_i32, [_vp]),
     "ocq_batch_destroy": (None, [_vp]),
     "ocq_server_create": (_i32, [_sz, _i32, ctypes.POINTER(_vp)]),
@@ -221,6 +226,29 @@ def ocq_build_model(frames, N, H, W, kind, block, depth, T, stream=None) -> Mode
 
 def ocq_classify(model, frames, F, mask, stream=None):
     _check(load().ocq_classify(_h(model), _p(frames), F, _p(mask), _s(stream)))
+
+
+def ocq_build_model_groups(frames, N, H, W, kind, block, depth, T, group, stream=None) -> Model:
+    out = ctypes.c_void_p()
+    _check(load().ocq_build_model_groups(_p(frames), N, H, W, _region(kind, block), depth, T, group, _s(stream),
+                                         ctypes.byref(out)))
+    return Model(out.value)
+
+
+def ocq_redraw(rgb, npix, depth, out, stream=None):
+    _check(load().ocq_redraw(_p(rgb), npix, depth, _p(out), _s(stream)))
+
+
+def ocq_confusion(mask, gt, F, npix, counts, stream=None):
+    _check(load().ocq_confusion(_p(mask), _p(gt), F, npix, _p(counts), _s(stream)))
+
+
+def ocq_f_scores(counts):
+    """counts: 4 integers {Tp, Fp, Tn, Fn}; returns (P0, R0, F0, F1)."""
+    c = (ctypes.c_uint64 * 4)(*[int(v) for v in counts])
+    out = (ctypes.c_double * 4)()
+    _check(load().ocq_f_scores(c, out))
+    return tuple(out)
 
 
 def ocq_model_get_info(model) -> ocq_model_info:
