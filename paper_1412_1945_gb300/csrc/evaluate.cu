@@ -6,9 +6,10 @@
 //                     16-byte vectors: 6 bytes of HBM traffic per pixel.
 //   confusion_kernel  per frame, true/false positives and negatives of a
 //                     foreground mask against ground truth (non-zero byte =
-//                     foreground in both); 16-byte vectors of both inputs,
+//                     foreground in both); spans of 32 KB of each input per
+//                     CTA item, 8 16-byte vectors of both in flight per thread,
 //                     per-byte flags counted with popc, one 64-bit atomic per
-//                     counter and CTA.  2 bytes of HBM traffic per pixel.
+//                     counter and item.  2 bytes of HBM traffic per pixel.
 #include <cstdint>
 
 #include "ocq_internal.cuh"
@@ -39,34 +40,47 @@ __global__ void redraw_kernel(const uint8_t *__restrict__ in, int64_t nbytes, ui
   for (int64_t i = tail + t0; i < nbytes; i += stride) out[i] = in[i] & (uint8_t)keep;
 }
 
-// grid.y strides over frames; each CTA adds its counts to counts[f][0..3].
-__global__ void __launch_bounds__(256) confusion_kernel(const uint8_t *__restrict__ mask,
+// Work item = (frame f, span j): 256 threads x VPT 16-byte vectors of frame f
+// (or, without vectors, 256 x VPT x 16 bytes one at a time).  CTAs stride over
+// items; each item's counts are reduced in the CTA and added to counts[f].
+constexpr int kConfVpt = 8;
+
+__global__ void __launch_bounds__(256, 2) confusion_kernel(const uint8_t *__restrict__ mask,
                                                         const uint8_t *__restrict__ gt, int F, int64_t npix,
                                                         unsigned long long *__restrict__ counts, int vec) {
   __shared__ unsigned long long part[3][8];
-  for (int f = blockIdx.y; f < F; f += gridDim.y) {
+  constexpr int64_t kSpan = 256 * kConfVpt * 16;  // pixels per item
+  const int64_t spans = (npix + kSpan - 1) / kSpan;
+  const int64_t items = spans * F;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int f = (int)(it / spans);
+    const int64_t p0 = (it - (int64_t)f * spans) * kSpan;
+    const int64_t p1 = p0 + kSpan < npix ? p0 + kSpan : npix;
     const uint8_t *m = mask + (int64_t)f * npix;
     const uint8_t *g = gt + (int64_t)f * npix;
     uint32_t tp = 0, pm = 0, pg = 0;  // both, predicted foreground, actual foreground
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t tail = 0;
-    if (vec) {
-      const int64_t nv = npix >> 4;
-      for (int64_t i = t0; i < nv; i += stride) {
-        const uint4 a = ld_stream16(m + (i << 4)), b = ld_stream16(g + (i << 4));
-        const uint32_t am[4] = {a.x, a.y, a.z, a.w}, bg[4] = {b.x, b.y, b.z, b.w};
+    if (vec && p1 - p0 == kSpan) {
+      uint4 a[kConfVpt], b[kConfVpt];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const uint32_t x = nonzero_bytes(am[k]), y = nonzero_bytes(bg[k]);
+      for (int k = 0; k < kConfVpt; ++k) {
+        const int64_t o = p0 + ((int64_t)k * 256 + threadIdx.x) * 16;
+        a[k] = __ldcs(reinterpret_cast<const uint4 *>(m + o));
+        b[k] = __ldcs(reinterpret_cast<const uint4 *>(g + o));
+      }
+#pragma unroll
+      for (int k = 0; k < kConfVpt; ++k) {
+        const uint32_t am[4] = {a[k].x, a[k].y, a[k].z, a[k].w}, bg[4] = {b[k].x, b[k].y, b[k].z, b[k].w};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const uint32_t x = nonzero_bytes(am[w]), y = nonzero_bytes(bg[w]);
           tp += __popc(x & y), pm += __popc(x), pg += __popc(y);
         }
       }
-      tail = nv << 4;
-    }
-    for (int64_t i = tail + t0; i < npix; i += stride) {
-      const uint32_t x = m[i] != 0, y = g[i] != 0;
-      tp += x & y, pm += x, pg += y;
+    } else {
+      for (int64_t i = p0 + threadIdx.x; i < p1; i += 256) {
+        const uint32_t x = m[i] != 0, y = g[i] != 0;
+        tp += x & y, pm += x, pg += y;
+      }
     }
     unsigned long long v[3] = {tp, pm, pg};
 #pragma unroll
@@ -77,12 +91,12 @@ __global__ void __launch_bounds__(256) confusion_kernel(const uint8_t *__restric
       for (int k = 0; k < 3; ++k) part[k][warp] = v[k];
     __syncthreads();
     if (threadIdx.x == 0) {
-      unsigned long long s[3] = {0, 0, 0};
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-        for (int k = 0; k < 3; ++k) s[k] += part[k][w];
-      atomicAdd(&counts[4 * f + 0], s[0]);          // Tp
-      atomicAdd(&counts[4 * f + 1], s[1] - s[0]);   // Fp = predicted - Tp
-      atomicAdd(&counts[4 * f + 3], s[2] - s[0]);   // Fn = actual - Tp
+      unsigned long long s3[3] = {0, 0, 0};
+      for (int w = 0; w < 8; ++w)
+        for (int k = 0; k < 3; ++k) s3[k] += part[k][w];
+      atomicAdd(&counts[4 * f + 0], s3[0]);          // Tp
+      atomicAdd(&counts[4 * f + 1], s3[1] - s3[0]);  // Fp = predicted - Tp
+      atomicAdd(&counts[4 * f + 3], s3[2] - s3[0]);  // Fn = actual - Tp
     }
     __syncthreads();
   }
@@ -130,14 +144,10 @@ ocq_status ocq_confusion(const uint8_t *mask, const uint8_t *gt, int F, int64_t 
   if (rc != OCQ_OK || npix == 0) return rc;
   const int vec = ((reinterpret_cast<uintptr_t>(mask) | reinterpret_cast<uintptr_t>(gt)) & 15) == 0 &&
                   npix % 16 == 0;
-  const int64_t per_frame = (npix / (vec ? 16 : 1) + 255) / 256;
-  const int64_t target = (int64_t)sm_count() * 8;
-  int64_t gx = per_frame < target ? per_frame : target;
-  if (gx < 1) gx = 1;
-  int64_t gy = (target + gx - 1) / gx;
-  if (gy > F) gy = F;
-  if (gy > 65535) gy = 65535;
-  dim3 grid((unsigned)gx, (unsigned)gy);
+  const int64_t span = 256 * kConfVpt * 16;
+  const int64_t items = (npix + span - 1) / span * F;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  const unsigned grid = (unsigned)(items < cap ? items : cap);
   confusion_kernel<<<grid, 256, 0, st>>>(mask, gt, F, npix, reinterpret_cast<unsigned long long *>(counts), vec);
   count_launch();
   rc = cuda_status(cudaGetLastError(), "confusion_kernel");
