@@ -15,6 +15,15 @@ static std::atomic<uint64_t> g_launches{0};
 
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
+// Stream-ordered allocation from the memory pool the calling thread has
+// selected (a server's own pool, see PoolScope), else the device's default.
+static thread_local cudaMemPool_t t_pool = nullptr;
+cudaError_t malloc_async(void **p, size_t bytes, cudaStream_t st) {
+  return t_pool ? cudaMallocFromPoolAsync(p, bytes, t_pool, st) : cudaMallocAsync(p, bytes, st);
+}
+PoolScope::PoolScope(cudaMemPool_t pool) : prev_(t_pool) { t_pool = pool; }
+PoolScope::~PoolScope() { t_pool = prev_; }
+
 void set_error(const char *fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -81,7 +90,7 @@ static ocq_model *new_model(int H, int W, ocq_region region, int depth, int T, i
   m->stream = st;
   cudaGetDevice(&m->device);
   void *p = nullptr;
-  *rc = cuda_status(cudaMallocAsync(&p, m->bytes, st), "allocating the model");
+  *rc = cuda_status(malloc_async(&p, m->bytes, st), "allocating the model");
   if (*rc != OCQ_OK) {
     delete m;
     return nullptr;

@@ -456,10 +456,10 @@ static ocq_status build_dense(const uint8_t *frames, int N, ocq_model *m, cudaSt
   if (nb > G) nb = G;
   const bool multi = nb < G;
   uint32_t *occ = nullptr, *planes = nullptr;
-  ocq_status rc = cuda_status(cudaMallocAsync((void **)&occ, (size_t)nb * nwords * 4, st), "build scratch");
+  ocq_status rc = cuda_status(malloc_async((void **)&occ, (size_t)nb * nwords * 4, st), "build scratch");
   if (rc != OCQ_OK) return rc;
   if (multi) {
-    rc = cuda_status(cudaMallocAsync((void **)&planes, (size_t)P * nwords * 4, st), "build counters");
+    rc = cuda_status(malloc_async((void **)&planes, (size_t)P * nwords * 4, st), "build counters");
     if (rc != OCQ_OK) {
       cudaFreeAsync(occ, st);
       return rc;
@@ -663,7 +663,7 @@ static ocq_status launch_pixel_chunked(const uint8_t *frames, int N, ocq_model *
   uint32_t *touched = nullptr;
   if (NCH > 64) {
     const size_t tb = (size_t)hw * (NCH / 32) * 4;
-    rc = cuda_status(cudaMallocAsync((void **)&touched, tb, st), "chunk bitmap");
+    rc = cuda_status(malloc_async((void **)&touched, tb, st), "chunk bitmap");
     if (rc != OCQ_OK) return rc;
     rc = cuda_status(cudaMemsetAsync(touched, 0, tb, st), "clear chunk bitmap");
   }

@@ -29,7 +29,7 @@ extern "C" ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t
   cudaStream_t s0 = (cudaStream_t)stream;
   const size_t hw = (size_t)H * (size_t)W;
   uint8_t *train_d = nullptr;
-  ocq_status rc = cuda_status(cudaMallocAsync((void **)&train_d, (size_t)N * hw * 3, s0), "training frames");
+  ocq_status rc = cuda_status(malloc_async((void **)&train_d, (size_t)N * hw * 3, s0), "training frames");
   if (rc != OCQ_OK) return rc;
   rc = cuda_status(cudaMemcpyAsync(train_d, train, (size_t)N * hw * 3, cudaMemcpyHostToDevice, s0), "copy in");
   ocq_model *m = nullptr;
@@ -46,8 +46,8 @@ extern "C" ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t
   if (rc == OCQ_OK) rc = cuda_status(cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking), "stream");
   const int nb = std::min(3, std::max(1, nchunks));
   for (int b = 0; b < nb && rc == OCQ_OK; ++b) {
-    rc = cuda_status(cudaMallocAsync((void **)&c.in[b], (size_t)per * hw * 3, s0), "chunk buffer");
-    if (rc == OCQ_OK) rc = cuda_status(cudaMallocAsync((void **)&c.out[b], (size_t)per * hw, s0), "chunk buffer");
+    rc = cuda_status(malloc_async((void **)&c.in[b], (size_t)per * hw * 3, s0), "chunk buffer");
+    if (rc == OCQ_OK) rc = cuda_status(malloc_async((void **)&c.out[b], (size_t)per * hw, s0), "chunk buffer");
     if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.ev_in[b], cudaEventDisableTiming), "event");
     if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.ev_cls[b], cudaEventDisableTiming), "event");
     if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.ev_out[b], cudaEventDisableTiming), "event");

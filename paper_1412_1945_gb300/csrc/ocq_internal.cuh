@@ -32,6 +32,18 @@ namespace ocq {
 void set_error(const char *fmt, ...);
 ocq_status cuda_status(cudaError_t e, const char *what);
 int sm_count();
+// cudaMallocAsync from the pool the calling thread selected with PoolScope
+// (else the device's default pool).
+cudaError_t malloc_async(void **p, size_t bytes, cudaStream_t st);
+struct PoolScope {
+  explicit PoolScope(cudaMemPool_t pool);
+  ~PoolScope();
+  PoolScope(const PoolScope &) = delete;
+  PoolScope &operator=(const PoolScope &) = delete;
+
+ private:
+  cudaMemPool_t prev_;
+};
 void count_launch(int n = 1);
 int64_t region_count(int H, int W, int kind, int block);
 

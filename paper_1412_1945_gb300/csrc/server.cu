@@ -15,6 +15,7 @@
 // share.  Completion times are taken by a host function enqueued after each
 // frame's work.
 #include <chrono>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <new>
@@ -56,6 +57,7 @@ using namespace ocq;
 
 struct ocq_server {
   size_t budget = 0, used = 0;
+  cudaMemPool_t pool = nullptr;  // the cameras' rings, models and scratch
   int max_cameras = 0;
   std::mutex mu;
   std::vector<Camera> cams;
@@ -101,6 +103,27 @@ ocq_status ocq_server_create(size_t hbm_budget, int max_cameras, ocq_server **ou
   s->budget = hbm_budget;
   s->max_cameras = max_cameras;
   s->cams.resize(max_cameras);
+  // A pool of its own that keeps up to the budget mapped after frees, so a
+  // camera's release and the next admission do not unmap and map gigabytes
+  // (the default pool returns freed memory at every synchronisation, which
+  // blocks the calling thread for every camera it serves).
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPoolProps props;
+  memset(&props, 0, sizeof props);
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  ocq_status rc = cuda_status(cudaMemPoolCreate(&s->pool, &props), "server memory pool");
+  if (rc == OCQ_OK) {
+    uint64_t keep = hbm_budget;
+    rc = cuda_status(cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep), "pool threshold");
+  }
+  if (rc != OCQ_OK) {
+    if (s->pool) cudaMemPoolDestroy(s->pool);
+    delete s;
+    return rc;
+  }
   *out = s;
   return OCQ_OK;
 }
@@ -132,6 +155,7 @@ ocq_status ocq_server_admit(ocq_server *s, const ocq_camera_desc *d, const uint8
     s->used += fp;
     s->cams[slot].live = true;
   }
+  PoolScope scope(s->pool);
   Camera &c = s->cams[slot];
   c.id = slot;
   c.d = *d;
@@ -139,7 +163,7 @@ ocq_status ocq_server_admit(ocq_server *s, const ocq_camera_desc *d, const uint8
   c.submitted = 0;
   ocq_status rc = cuda_status(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "camera stream");
   const size_t ring = (size_t)d->N * d->H * d->W * 3;
-  if (rc == OCQ_OK) rc = cuda_status(cudaMallocAsync((void **)&c.ring, ring, c.stream), "camera ring");
+  if (rc == OCQ_OK) rc = cuda_status(malloc_async((void **)&c.ring, ring, c.stream), "camera ring");
   if (rc == OCQ_OK) rc = cuda_status(cudaMemcpyAsync(c.ring, train, ring, cudaMemcpyDeviceToDevice, c.stream), "ring fill");
   if (rc == OCQ_OK) rc = ocq_build_model(c.ring, d->N, d->H, d->W, d->region, d->depth, d->T, c.stream, &c.model);
   if (rc != OCQ_OK) {
@@ -160,6 +184,7 @@ ocq_status ocq_server_submit(ocq_server *s, int camera, const uint8_t *frame, ui
     set_error("ocq_server_submit: bad camera or buffers");
     return OCQ_EINVAL;
   }
+  PoolScope scope(s->pool);
   Camera &c = s->cams[camera];
   const double arrival = now_s();
   const int64_t t = c.submitted++;
@@ -257,6 +282,7 @@ void ocq_server_destroy(ocq_server *s) {
   if (!s) return;
   for (int i = 0; i < s->max_cameras; ++i)
     if (s->cams[i].live) ocq_server_release(s, i);
+  if (s->pool) cudaMemPoolDestroy(s->pool);  // every camera's memory was freed and its stream synchronised
   delete s;
 }
 

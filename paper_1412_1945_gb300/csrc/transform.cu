@@ -117,7 +117,7 @@ ocq_status launch_occupancy(const uint8_t *frames, int n, int H, int W, int kind
   const int64_t rows = (int64_t)n * R;
   const size_t bytes = (size_t)rows * (size_t)wpr32(depth) * sizeof(uint32_t);
   uint32_t *tmp = nullptr;
-  ocq_status rc = cuda_status(cudaMallocAsync((void **)&tmp, bytes, st), "occupancy scratch");
+  ocq_status rc = cuda_status(malloc_async((void **)&tmp, bytes, st), "occupancy scratch");
   if (rc != OCQ_OK) return rc;
   rc = cuda_status(cudaMemsetAsync(tmp, 0, bytes, st), "occupancy scratch clear");
   if (rc == OCQ_OK) {
