@@ -118,3 +118,76 @@ def test_serving_admission_by_footprint(cuda_ready):
         assert O.ocq_server_usage(srv)[0] == 0
     finally:
         srv.destroy()
+
+
+def _first(streams, W, region, depth=None):
+    for i, s in enumerate(streams):
+        if s.wl.W == W and s.wl.region == region and (depth is None or s.wl.depth == depth):
+            return i
+    raise LookupError((W, region, depth))
+
+
+def test_serving_preset_cameras_full_size_sampled(cuda_ready):
+    """Cameras of the 256-camera preset at full size (3840x2160 per-pixel
+    d = 5, 1920x1080 8x8 blocks d = 5, 320x240 whole frame), two windows each
+    (N = K = 30, T = 10), frames rendered on the device; the masks at sampled
+    pixel locations / blocks (whole frame: every pixel) equal the oracle's
+    under the window semantics, on the same frames rendered by the host
+    generator."""
+    import torch
+
+    from ocq_synth import configs
+
+    ocq = cuda_ready
+    O = ocq.ocq
+    streams = configs.serving_streams()
+    picks = [_first(streams, 3840, PIXEL, 5), _first(streams, 1920, BLOCK, 5), _first(streams, 320, FRAME)]
+    srv = O.ocq_server_create(1 << 36, 8)
+    rng = np.random.default_rng(77)
+    try:
+        for i in picks:
+            wl = streams[i].wl
+            H, W, N, K, T, d = wl.H, wl.W, wl.N, wl.N, wl.T, wl.depth
+            F = 2 * K
+            sc = ocq_synth.make_scene(wl.scene_kind, H, W, N, F, wl.seed, wl.stream)
+            dev = torch.empty((N + F, H, W, 3), dtype=torch.uint8, device="cuda")
+            ocq_synth.fill_device(sc, 0, N + F, dev)
+            masks = torch.full((F, H, W), 7, dtype=torch.uint8, device="cuda")
+            torch.cuda.synchronize()
+            cam = O.ocq_server_admit(srv, H, W, wl.region, wl.block, d, T, N, K, dev[:N])
+            assert cam is not None
+            for t in range(F):
+                O.ocq_server_submit(srv, cam, dev[N + t], masks[t], tag=t)
+            O.ocq_server_sync(srv)
+            assert len(O.ocq_server_poll(srv, 1000)) == F
+            O.ocq_server_release(srv, cam)
+            if wl.region == PIXEL:
+                idx = np.sort(rng.choice(H * W, size=300, replace=False))
+                frames = ocq_synth.fill_pixels_host(sc, 0, N + F, idx).reshape(N + F, len(idx), 1, 3)
+                got = masks.reshape(F, H * W)[:, torch.from_numpy(idx).cuda()].cpu().numpy().reshape(F, len(idx), 1)
+            elif wl.region == BLOCK:
+                b = wl.block
+                bw = -(-W // b)
+                blocks = np.sort(rng.choice(bw * (-(-H // b)), size=40, replace=False))
+                cols = []
+                for r in blocks:
+                    y0, x0 = (r // bw) * b, (r % bw) * b
+                    cols.append(np.array([(y0 + yy) * W + x0 + xx for yy in range(b) for xx in range(b)]))
+                idx = np.concatenate(cols)
+                # the sampled blocks side by side: one b-row frame of len(blocks) blocks
+                frames = ocq_synth.fill_pixels_host(sc, 0, N + F, idx).reshape(N + F, len(blocks), b, b, 3)
+                frames = frames.transpose(0, 2, 1, 3, 4).reshape(N + F, b, len(blocks) * b, 3)
+                flat = masks.reshape(F, H * W)[:, torch.from_numpy(idx).cuda()].cpu().numpy()
+                got = flat.reshape(F, len(blocks), b, b).transpose(0, 2, 1, 3).reshape(F, b, len(blocks) * b)
+            else:
+                frames = ocq_synth.fill_host(sc, 0, N + F)
+                got = masks.cpu().numpy()
+            kind, block = wl.region, wl.block
+            for k in range(2):  # window k: M_k from frames [kK, kK + N), then test frames kK .. kK + K - 1
+                model = oracle.build_model(frames[k * K:k * K + N], d, T, kind, block)
+                expect = oracle.classify(model, frames[N + k * K:N + k * K + K], d, kind, block)
+                assert (got[k * K:k * K + K] == expect).all(), (i, k)
+            del dev, masks
+            torch.cuda.empty_cache()
+    finally:
+        srv.destroy()
