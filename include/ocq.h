@@ -288,6 +288,9 @@ typedef struct {
 
 typedef struct ocq_server ocq_server;
 
+/* hbm_budget: device bytes the server may hold; they are reserved (mapped in a
+ * memory pool of the server's own) at creation, so admission and serving never
+ * wait on the allocator.  OCQ_ENOMEM if the device cannot provide them. */
 ocq_status ocq_server_create(size_t hbm_budget, int max_cameras, ocq_server **out);
 /* Device bytes a camera of this description reserves (0 if invalid). */
 size_t ocq_server_camera_footprint(const ocq_camera_desc *desc);

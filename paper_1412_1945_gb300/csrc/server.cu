@@ -7,13 +7,16 @@
 //   * after classification frame t enters a ring of the last N frames;
 //   * when (t+1) % K == 0 the ring is merged again: M_(t+1)/K = merge(ring).
 // So M_k is the merged model of global frames [kK, kK+N-1] (training frames
-// first).  All of a camera's work is ordered on its own CUDA stream; cameras
-// run concurrently, so work of frames that arrive while others are on the GPU
-// overlaps on the device.  Admission reserves a camera's footprint (ring,
-// model, the model being rebuilt, build scratch) against an HBM budget and
-// returns OCQ_EBUSY when it does not fit; released cameras return their
-// share.  Completion times are taken by a host function enqueued after each
-// frame's work.
+// first).  A camera's per-frame work (classify, ring copy) is ordered on its
+// own high-priority CUDA stream and its builds on a low-priority one, joined
+// by events: a re-merge starts once the window's last frame is in the ring,
+// and the camera's next frame waits for it.  Cameras run concurrently, so work
+// of frames that arrive while others are on the GPU overlaps on the device,
+// and one camera's long re-merge yields the SMs to other cameras' frames.
+// Admission reserves a camera's footprint (ring, model, the model being
+// rebuilt, build scratch) against an HBM budget and returns OCQ_EBUSY when it
+// does not fit; released cameras return their share.  A frame's completion
+// time is taken by a host function enqueued right after its mask.
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -46,8 +49,10 @@ struct Camera {
   size_t footprint = 0;
   uint8_t *ring = nullptr;  // N frames (HWC RGB8), slot = frame % N
   ocq_model *model = nullptr;
-  cudaStream_t stream = nullptr;
-  int64_t submitted = 0;    // test frames submitted so far
+  cudaStream_t stream = nullptr;  // high priority: classify, ring copies, completions
+  cudaStream_t merge = nullptr;   // low priority: builds (M_0 and re-merges)
+  cudaEvent_t ring_ready = nullptr, merged = nullptr;
+  int64_t submitted = 0;          // test frames submitted so far
   bool live = false;
 };
 
@@ -119,6 +124,20 @@ ocq_status ocq_server_create(size_t hbm_budget, int max_cameras, ocq_server **ou
     uint64_t keep = hbm_budget;
     rc = cuda_status(cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep), "pool threshold");
   }
+  // Map the whole budget now: growing the pool later maps memory on the
+  // thread that admits or submits, in the middle of serving.
+  if (rc == OCQ_OK && hbm_budget > 0) {
+    cudaStream_t st = nullptr;
+    void *p = nullptr;
+    rc = cuda_status(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "reserve stream");
+    if (rc == OCQ_OK) rc = cuda_status(cudaMallocFromPoolAsync(&p, hbm_budget, s->pool, st), "reserving the budget");
+    if (p) cudaFreeAsync(p, st);
+    if (st) {
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (rc == OCQ_OK) rc = cuda_status(e, "reserving the budget");
+      cudaStreamDestroy(st);
+    }
+  }
   if (rc != OCQ_OK) {
     if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
@@ -161,15 +180,25 @@ ocq_status ocq_server_admit(ocq_server *s, const ocq_camera_desc *d, const uint8
   c.d = *d;
   c.footprint = fp;
   c.submitted = 0;
-  ocq_status rc = cuda_status(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "camera stream");
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);  // lo = least urgent, hi = most urgent
+  ocq_status rc = cuda_status(cudaStreamCreateWithPriority(&c.stream, cudaStreamNonBlocking, hi), "camera stream");
+  if (rc == OCQ_OK) rc = cuda_status(cudaStreamCreateWithPriority(&c.merge, cudaStreamNonBlocking, lo), "merge stream");
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.ring_ready, cudaEventDisableTiming), "event");
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.merged, cudaEventDisableTiming), "event");
   const size_t ring = (size_t)d->N * d->H * d->W * 3;
-  if (rc == OCQ_OK) rc = cuda_status(malloc_async((void **)&c.ring, ring, c.stream), "camera ring");
-  if (rc == OCQ_OK) rc = cuda_status(cudaMemcpyAsync(c.ring, train, ring, cudaMemcpyDeviceToDevice, c.stream), "ring fill");
-  if (rc == OCQ_OK) rc = ocq_build_model(c.ring, d->N, d->H, d->W, d->region, d->depth, d->T, c.stream, &c.model);
+  if (rc == OCQ_OK) rc = cuda_status(malloc_async((void **)&c.ring, ring, c.merge), "camera ring");
+  if (rc == OCQ_OK) rc = cuda_status(cudaMemcpyAsync(c.ring, train, ring, cudaMemcpyDeviceToDevice, c.merge), "ring fill");
+  if (rc == OCQ_OK) rc = ocq_build_model(c.ring, d->N, d->H, d->W, d->region, d->depth, d->T, c.merge, &c.model);
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(c.merged, c.merge), "merged");
+  if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent(c.stream, c.merged, 0), "wait for M_0");
   if (rc != OCQ_OK) {
-    if (c.ring) cudaFreeAsync(c.ring, c.stream);
+    if (c.ring) cudaFreeAsync(c.ring, c.merge);
+    if (c.merge) cudaStreamSynchronize(c.merge), cudaStreamDestroy(c.merge);
     if (c.stream) cudaStreamSynchronize(c.stream), cudaStreamDestroy(c.stream);
-    c.ring = nullptr, c.stream = nullptr;
+    if (c.ring_ready) cudaEventDestroy(c.ring_ready);
+    if (c.merged) cudaEventDestroy(c.merged);
+    c.ring = nullptr, c.stream = nullptr, c.merge = nullptr, c.ring_ready = nullptr, c.merged = nullptr;
     std::lock_guard<std::mutex> lock(s->mu);
     s->used -= fp;
     c.live = false;
@@ -190,23 +219,35 @@ ocq_status ocq_server_submit(ocq_server *s, int camera, const uint8_t *frame, ui
   const int64_t t = c.submitted++;
   const size_t fbytes = (size_t)c.d.H * c.d.W * 3;
   ocq_status rc = ocq_classify(c.model, frame, 1, mask, c.stream);
-  if (rc == OCQ_OK)
-    rc = cuda_status(cudaMemcpyAsync(c.ring + (size_t)((c.d.N + t) % c.d.N) * fbytes, frame, fbytes,
-                                     cudaMemcpyDeviceToDevice, c.stream),
-                     "ring push");
-  if (rc == OCQ_OK && (t + 1) % c.d.K == 0) {
-    ocq_model *next = nullptr;
-    rc = ocq_build_model(c.ring, c.d.N, c.d.H, c.d.W, c.d.region, c.d.depth, c.d.T, c.stream, &next);
-    if (rc == OCQ_OK) {
-      ocq_model_free(c.model);  // stream-ordered: frames already enqueued keep the old model
-      c.model = next;
-    }
-  }
   if (rc != OCQ_OK) return rc;
   Pending *p = new (std::nothrow) Pending{s, camera, t, tag, arrival};
   if (!p) return OCQ_ENOMEM;
   rc = cuda_status(cudaLaunchHostFunc(c.stream, on_frame_done, p), "completion callback");
-  if (rc != OCQ_OK) delete p;
+  if (rc != OCQ_OK) {
+    delete p;
+    return rc;
+  }
+  rc = cuda_status(cudaMemcpyAsync(c.ring + (size_t)((c.d.N + t) % c.d.N) * fbytes, frame, fbytes,
+                                   cudaMemcpyDeviceToDevice, c.stream),
+                   "ring push");
+  if (rc == OCQ_OK && (t + 1) % c.d.K == 0) {
+    // Re-merge on the low-priority stream once the ring holds frame t; the
+    // camera's later frames wait for the new model.  The old model is freed
+    // on the camera stream after the last frame that reads it.
+    rc = cuda_status(cudaEventRecord(c.ring_ready, c.stream), "ring ready");
+    if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent(c.merge, c.ring_ready, 0), "merge wait");
+    ocq_model *next = nullptr;
+    if (rc == OCQ_OK) rc = ocq_build_model(c.ring, c.d.N, c.d.H, c.d.W, c.d.region, c.d.depth, c.d.T, c.merge, &next);
+    if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(c.merged, c.merge), "merged");
+    if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent(c.stream, c.merged, 0), "wait for the new model");
+    if (rc == OCQ_OK) {
+      c.model->stream = c.stream;  // freed in camera-stream order, after the frames that used it
+      ocq_model_free(c.model);
+      c.model = next;
+    } else if (next) {
+      ocq_model_free(next);
+    }
+  }
   return rc;
 }
 
@@ -231,11 +272,20 @@ ocq_status ocq_server_release(ocq_server *s, int camera) {
     return OCQ_EINVAL;
   }
   Camera &c = s->cams[camera];
+  // Builds and frames both finish before the memory goes back to the pool.
+  cudaStreamWaitEvent(c.stream, c.merged, 0);
+  c.model->stream = c.stream;
   ocq_model_free(c.model);
   cudaFreeAsync(c.ring, c.stream);
-  cudaError_t e = cudaStreamSynchronize(c.stream);  // its frames finish; its memory is returned
+  cudaError_t e = cudaStreamSynchronize(c.stream);
+  cudaError_t e2 = cudaStreamSynchronize(c.merge);
+  if (e == cudaSuccess) e = e2;
   cudaStreamDestroy(c.stream);
-  c.model = nullptr, c.ring = nullptr, c.stream = nullptr;
+  cudaStreamDestroy(c.merge);
+  cudaEventDestroy(c.ring_ready);
+  cudaEventDestroy(c.merged);
+  c.model = nullptr, c.ring = nullptr, c.stream = nullptr, c.merge = nullptr;
+  c.ring_ready = nullptr, c.merged = nullptr;
   {
     std::lock_guard<std::mutex> lock(s->mu);
     s->used -= c.footprint;
@@ -273,6 +323,7 @@ ocq_status ocq_server_sync(ocq_server *s) {
   for (Camera &c : s->cams)
     if (c.live) {
       cudaError_t e = cudaStreamSynchronize(c.stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c.merge);
       if (e != cudaSuccess) return cuda_status(e, "server sync");
     }
   return OCQ_OK;

@@ -142,7 +142,7 @@ def test_serving_preset_cameras_full_size_sampled(cuda_ready):
     O = ocq.ocq
     streams = configs.serving_streams()
     picks = [_first(streams, 3840, PIXEL, 5), _first(streams, 1920, BLOCK, 5), _first(streams, 320, FRAME)]
-    srv = O.ocq_server_create(1 << 36, 8)
+    srv = O.ocq_server_create(72 << 30, 8)
     rng = np.random.default_rng(77)
     try:
         for i in picks:
