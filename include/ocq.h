@@ -328,12 +328,16 @@ void ocq_server_destroy(ocq_server *server);
  *                            all frames of its pixel locations); params =
  *                            {pixel locations per lane (1 or 4), frames prefetched,
  *                             CTAs of 4 warps resident per SM, 0, 0}
+ *   OCQ_TUNE_CLASSIFY_BLOCK_DEEP block classify, depth >= 4 with b % 4 == 0; params =
+ *                            {form: 0 the strip's rows staged in shared memory
+ *                             (b % 8 == 0, W % 16 == 0, depth <= 5), 1 L1-cached
+ *                             lookups by warps walking all frames, 0, 0, 0}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5
  * int32 parameters (n >= 5).
  */
-enum { OCQ_TUNE_CLASSIFY_PIXEL = 0, OCQ_TUNE_BUILD_PIXEL = 1, OCQ_TUNE_CLASSIFY_PIXEL_DEEP = 2 };
+enum { OCQ_TUNE_CLASSIFY_PIXEL = 0, OCQ_TUNE_BUILD_PIXEL = 1, OCQ_TUNE_CLASSIFY_PIXEL_DEEP = 2, OCQ_TUNE_CLASSIFY_BLOCK_DEEP = 3 };
 int ocq_tune_count(int kernel);
 int ocq_tune_selected(int kernel);
 ocq_status ocq_tune_select(int kernel, int variant);

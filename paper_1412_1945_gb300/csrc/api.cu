@@ -289,6 +289,7 @@ int ocq_tune_count(int kernel) {
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL) return classify_variant_count();
   if (kernel == OCQ_TUNE_BUILD_PIXEL) return build_variant_count();
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) return deep_variant_count();
+  if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) return block_form_count();
   return -1;
 }
 
@@ -296,6 +297,7 @@ int ocq_tune_selected(int kernel) {
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL) return classify_variant_selected();
   if (kernel == OCQ_TUNE_BUILD_PIXEL) return build_variant_selected();
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) return deep_variant_selected();
+  if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) return block_form_selected();
   return -1;
 }
 
@@ -305,6 +307,7 @@ ocq_status ocq_tune_select(int kernel, int variant) {
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL) ok = classify_variant_select(variant);
   if (kernel == OCQ_TUNE_BUILD_PIXEL) ok = build_variant_select(variant);
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) ok = deep_variant_select(variant);
+  if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) ok = block_form_select(variant);
   if (!ok) {
     set_error("ocq_tune_select: no variant %d of kernel %d", variant, kernel);
     return OCQ_EINVAL;
@@ -323,8 +326,10 @@ ocq_status ocq_tune_describe(int kernel, int variant, int32_t *params, int n) {
     classify_variant_describe(variant, &params[0], &params[1], &params[2], &params[3], &params[4]);
   else if (kernel == OCQ_TUNE_BUILD_PIXEL)
     build_variant_describe(variant, &params[0], &params[1], &params[2], &params[3]);
-  else
+  else if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP)
     deep_variant_describe(variant, &params[0], &params[1], &params[2]);
+  else
+    params[0] = variant;
   return OCQ_OK;
 }
 

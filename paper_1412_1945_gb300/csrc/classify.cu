@@ -7,6 +7,8 @@
 //                                lives in shared memory (replicated per lane
 //                                for depth <= 4 so lookups never conflict),
 //                                frames stream through 16-byte loads.
+//   classify_block_tb_kernel<D>  b x b blocks (b % 4 == 0), depth >= 4: as the
+//                                per-pixel form, 8-warp CTAs over whole blocks.
 //   classify_pixel_tb_kernel     pixel regions, depth >= 4: a warp walks all
 //                                frames of 32 or 128 pixel locations; their
 //                                model sectors stay in L1 between frames.
@@ -64,6 +66,16 @@ __global__ void __launch_bounds__(128) classify_pixel_tb_kernel(const uint8_t *_
     else
       classify_pixel_tb1_body<D, PF>(frames, F, hw, model, mask, t);
   }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) classify_block_tb_kernel(const uint8_t *__restrict__ frames, int F, int H,
+                                                                int W, int b, int bw, int nseg, int64_t tiles,
+                                                                const uint32_t *__restrict__ model,
+                                                                uint8_t *__restrict__ mask) {
+  const int64_t nw = (int64_t)gridDim.x * 8;
+  for (int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); t < tiles; t += nw)
+    classify_block_tb_body<D, 8>(frames, F, H, W, b, bw, nseg, model, mask, t);
 }
 
 template <int D, int S, int FPS>
@@ -357,6 +369,38 @@ void deep_variant_describe(int v, int *pxl, int *pf, int *cps) {
   *pxl = kDeepVariants[v].pxl, *pf = kDeepVariants[v].pf, *cps = kDeepVariants[v].cps;
 }
 
+// Block classify form for depth >= 4 (see classify_block_tb_body): 0 = rows
+// staged in shared memory (classify_block_ws_kernel), 1 = L1 (tb).
+static int g_block_deep_form = 1;
+static int g_block_tb_cps = 4;  // CTAs of 8 warps per SM
+
+int block_form_count() { return 2; }
+int block_form_selected() { return g_block_deep_form; }
+bool block_form_select(int v) {
+  if (v < 0 || v > 1) return false;
+  g_block_deep_form = v;
+  return true;
+}
+
+template <int D>
+static ocq_status launch_block_tb(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st) {
+  const int bw = (m->W + m->block - 1) / m->block;
+  const int bh = (m->H + m->block - 1) / m->block;
+  const int nseg = (m->W + 127) / 128;
+  const int64_t tiles = (int64_t)bh * nseg * m->block;
+  const int64_t ctas = (tiles + 7) / 8;
+  const int64_t cap = (int64_t)sm_count() * g_block_tb_cps;
+  static bool carved = false;
+  if (!carved) {
+    cudaFuncSetAttribute(classify_block_tb_kernel<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    carved = true;
+  }
+  classify_block_tb_kernel<D><<<(unsigned)(ctas < cap ? ctas : cap), 256, 0, st>>>(
+      frames, F, m->H, m->W, m->block, bw, nseg, tiles, m->bits, mask);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "classify_block_tb_kernel");
+}
+
 template <int D>
 static ocq_status launch_block_ws(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, int wt,
                                   cudaStream_t st) {
@@ -400,6 +444,16 @@ ocq_status launch_classify(const ocq_model *m, const uint8_t *frames, int F, uin
   if (m->kind == OCQ_REGION_PIXEL && d >= 4 && aligned4 && hw % 4 == 0) {
     const DeepVariant &v = kDeepVariants[g_deep_variant];
     return v.fn[d - 4](m, frames, F, mask, v.cps, st);
+  }
+  if (m->kind == OCQ_REGION_BLOCK && d >= 4 && m->block % 4 == 0 && m->W % 4 == 0 && aligned4 &&
+      (g_block_deep_form == 1 || d > 5 || block_tile_width(m->block, d, m->W) <= 0 || !aligned)) {
+    switch (d) {
+      case 4: return launch_block_tb<4>(m, frames, F, mask, st);
+      case 5: return launch_block_tb<5>(m, frames, F, mask, st);
+      case 6: return launch_block_tb<6>(m, frames, F, mask, st);
+      case 7: return launch_block_tb<7>(m, frames, F, mask, st);
+      default: return launch_block_tb<8>(m, frames, F, mask, st);
+    }
   }
   if (m->kind == OCQ_REGION_BLOCK && d <= 5 && aligned) {
     const int wt = block_tile_width(m->block, d, m->W);

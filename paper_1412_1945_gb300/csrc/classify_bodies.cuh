@@ -145,6 +145,54 @@ __device__ __forceinline__ void classify_pixel_tb_body(const uint8_t *__restrict
   }
 }
 
+// Block regions (b % 4 == 0, W % 4 == 0), any depth: as the per-pixel form,
+// a warp walks all F frames of 128 consecutive pixels of one pixel row (4 per
+// lane, all 4 in one block), their lookups hitting L1.  Tile t covers pixel row
+// k = t % b of block row br and 128-pixel segment sg, t / b = br * nseg + sg,
+// so the b warps of consecutive tiles cover whole blocks: a CTA of 8 warps
+// reads each block row's model sectors once per SM when b <= 8.
+template <int D, int PF>
+__device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict__ frames, int F, int H, int W,
+                                                       int b, int bw, int nseg, const uint32_t *model,
+                                                       uint8_t *__restrict__ mask, int64_t t) {
+  constexpr int64_t WPR = D == 1 ? 1 : (int64_t)1 << (3 * D - 5);
+  const int lane = threadIdx.x & 31;
+  const int k = (int)(t % b);
+  const int64_t q = t / b;
+  const int br = (int)(q / nseg), sg = (int)(q % nseg);
+  const int y = br * b + k;
+  const int x = sg * 128 + 4 * lane;
+  if (y >= H || x >= W) return;
+  const int64_t hw = (int64_t)H * W;
+  const int64_t pq = (int64_t)y * W + x;
+  const uint8_t *row = reinterpret_cast<const uint8_t *>(model + ((int64_t)br * bw + x / b) * WPR);
+  const uint8_t *src = frames + pq * 3;
+  uint8_t *dst = mask + pq;
+  for (int f0 = 0; f0 < F; f0 += PF) {
+    uint32_t w[PF][3];
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+      if (f0 + j < F) {
+        const uint8_t *s = src + (int64_t)(f0 + j) * hw * 3;
+        w[j][0] = ld_stream4(s), w[j][1] = ld_stream4(s + 4), w[j][2] = ld_stream4(s + 8);
+      }
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (f0 + j >= F) break;
+      uint32_t m[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) m[i] = (w[j][i] >> (8 - D)) & byte_mask(D);
+      uint32_t bg[4];
+      static_for<0, 4>([&](auto kc) {
+        constexpr int kk = decltype(kc)::value;
+        const uint32_t c = planar_from_masked<D>(quad_pixel<kk>(m));
+        bg[kk] = (uint32_t)row[c >> 3] >> (c & 7);
+      });
+      st_stream4(dst + (int64_t)(f0 + j) * hw, pack_mask4(bg[0], bg[1], bg[2], bg[3]));
+    }
+  }
+}
+
 // One pixel location per lane (a warp owns 32): a smaller model working set
 // per warp than the 4-per-lane form, so more warps fit their lines in L1.
 __device__ __forceinline__ uint32_t ld_stream1(const uint8_t *p) {

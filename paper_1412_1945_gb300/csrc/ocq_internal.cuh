@@ -178,6 +178,9 @@ int deep_variant_count();
 int deep_variant_selected();
 bool deep_variant_select(int v);
 void deep_variant_describe(int v, int *pxl, int *pf, int *cps);
+int block_form_count();
+int block_form_selected();
+bool block_form_select(int v);
 int build_variant_count();
 int build_variant_selected();
 bool build_variant_select(int v);

@@ -112,7 +112,7 @@ SIGNATURES = {
     "ocq_tune_describe": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_int32), _i32]),
 }
 
-OCQ_TUNE_CLASSIFY_PIXEL, OCQ_TUNE_BUILD_PIXEL, OCQ_TUNE_CLASSIFY_PIXEL_DEEP = 0, 1, 2
+OCQ_TUNE_CLASSIFY_PIXEL, OCQ_TUNE_BUILD_PIXEL, OCQ_TUNE_CLASSIFY_PIXEL_DEEP, OCQ_TUNE_CLASSIFY_BLOCK_DEEP = 0, 1, 2, 3
 OCQ_BATCH_PERSISTENT, OCQ_BATCH_GRAPH = 0, 1
 
 

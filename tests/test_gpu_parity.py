@@ -351,3 +351,31 @@ def test_pixel_deep_classify_variants(ocq, torch):
                 assert (words == ow).all() and (mask == om).all(), (d, v)
     finally:
         O.ocq_tune_select(kernel, saved)
+
+
+@pytest.mark.parametrize("b", [4, 8, 12, 16])
+@pytest.mark.parametrize("d", [4, 5, 6])
+def test_block_deep_classify_forms(ocq, torch, b, d):
+    """Block regions at depth >= 4: both classify forms (rows staged in shared
+    memory where it applies, and L1-cached lookups by warps walking all frames)
+    give the oracle's masks; partial blocks at the right and bottom edges, a
+    width that is not a multiple of 128, and one that is not a multiple of 4
+    (generic kernel)."""
+    O = ocq.ocq
+    kernel = O.OCQ_TUNE_CLASSIFY_BLOCK_DEEP
+    saved = O.ocq_tune_selected(kernel)
+    try:
+        for H, W in ((2 * b + 3, 4 * 36), (b + 1, 139)):
+            if d == 6:
+                H, W = min(H, 2 * b), min(W, 3 * b + (W % 4))
+            sc = ocq_synth.make_scene("sway", H, W, 9, 7, seed=40 * b + d + W)
+            frames = ocq_synth.fill_host(sc, 0, 16)
+            train, test = frames[:9], frames[9:]
+            ow, om = oracle.run(train, d, 3, BLOCK, b, test)
+            for form in range(O.ocq_tune_count(kernel)):
+                O.ocq_tune_select(kernel, form)
+                words, mask = gpu_model_and_mask(ocq, torch, train, test, d, 3, BLOCK, b)
+                assert (words == ow).all(), (H, W, form)
+                assert (mask == om).all(), (H, W, form)
+    finally:
+        O.ocq_tune_select(kernel, saved)
