@@ -328,10 +328,11 @@ void ocq_server_destroy(ocq_server *server);
  *                            all frames of its pixel locations); params =
  *                            {pixel locations per lane (1 or 4), frames prefetched,
  *                             CTAs of 4 warps resident per SM, 0, 0}
- *   OCQ_TUNE_CLASSIFY_BLOCK_DEEP block classify, depth >= 4 with b % 4 == 0; params =
+ *   OCQ_TUNE_CLASSIFY_BLOCK_DEEP block classify with b % 4 == 0; params =
  *                            {form: 0 the strip's rows staged in shared memory
  *                             (b % 8 == 0, W % 16 == 0, depth <= 5), 1 L1-cached
- *                             lookups by warps walking all frames, 0, 0, 0}
+ *                             lookups by warps walking all frames at depth >= 4,
+ *                             2 the same at depth >= 3, 0, 0, 0}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5

@@ -369,15 +369,16 @@ void deep_variant_describe(int v, int *pxl, int *pf, int *cps) {
   *pxl = kDeepVariants[v].pxl, *pf = kDeepVariants[v].pf, *cps = kDeepVariants[v].cps;
 }
 
-// Block classify form for depth >= 4 (see classify_block_tb_body): 0 = rows
-// staged in shared memory (classify_block_ws_kernel), 1 = L1 (tb).
-static int g_block_deep_form = 1;
+// Block classify form (see classify_block_tb_body): 0 = rows staged in shared
+// memory (classify_block_ws_kernel), 1 = L1 (tb) for depth >= 4, 2 = L1 for
+// depth >= 3 as well.
+static int g_block_deep_form = 2;
 static int g_block_tb_cps = 4;  // CTAs of 8 warps per SM
 
-int block_form_count() { return 2; }
+int block_form_count() { return 3; }
 int block_form_selected() { return g_block_deep_form; }
 bool block_form_select(int v) {
-  if (v < 0 || v > 1) return false;
+  if (v < 0 || v > 2) return false;
   g_block_deep_form = v;
   return true;
 }
@@ -445,9 +446,11 @@ ocq_status launch_classify(const ocq_model *m, const uint8_t *frames, int F, uin
     const DeepVariant &v = kDeepVariants[g_deep_variant];
     return v.fn[d - 4](m, frames, F, mask, v.cps, st);
   }
-  if (m->kind == OCQ_REGION_BLOCK && d >= 4 && m->block % 4 == 0 && m->W % 4 == 0 && aligned4 &&
-      (g_block_deep_form == 1 || d > 5 || block_tile_width(m->block, d, m->W) <= 0 || !aligned)) {
+  const bool ws_ok = m->kind == OCQ_REGION_BLOCK && d <= 5 && aligned && block_tile_width(m->block, d, m->W) > 0;
+  if (m->kind == OCQ_REGION_BLOCK && d >= 3 && m->block % 4 == 0 && m->W % 4 == 0 && aligned4 &&
+      (!ws_ok || (d >= 4 && g_block_deep_form >= 1) || g_block_deep_form == 2)) {
     switch (d) {
+      case 3: return launch_block_tb<3>(m, frames, F, mask, st);
       case 4: return launch_block_tb<4>(m, frames, F, mask, st);
       case 5: return launch_block_tb<5>(m, frames, F, mask, st);
       case 6: return launch_block_tb<6>(m, frames, F, mask, st);

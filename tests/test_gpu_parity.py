@@ -354,7 +354,7 @@ def test_pixel_deep_classify_variants(ocq, torch):
 
 
 @pytest.mark.parametrize("b", [4, 8, 12, 16])
-@pytest.mark.parametrize("d", [4, 5, 6])
+@pytest.mark.parametrize("d", [3, 4, 5, 6])
 def test_block_deep_classify_forms(ocq, torch, b, d):
     """Block regions at depth >= 4: both classify forms (rows staged in shared
     memory where it applies, and L1-cached lookups by warps walking all frames)
