@@ -41,6 +41,7 @@ enum : int32_t {
   OP_CLS_PIXEL_WS,     // classify_pixel_ws_body   (pixels, depth <= 3, aligned)
   OP_CLS_BLOCK_WS,     // classify_block_ws_body   (blocks, b % 8 == 0, W % 16 == 0)
   OP_CLS_PIXEL_TB,     // classify_pixel_tb_body   (pixels, depth 4-5, H*W % 4 == 0): 128-pixel tiles [vb, aux)
+  OP_CLS_BLOCK_TB,     // classify_block_tb_body   (blocks, depth 3-5, b % 4 == 0, W % 4 == 0): tiles [vb, aux)
   OP_CLS_GENERIC       // classify_generic_body    (everything else, and remainders)
 };
 
@@ -60,7 +61,9 @@ struct BStream {
   int32_t occ_nbx;     // pixel chunks per frame in occupancy items
   int32_t ppl;         // block build, one warp per region: pixels per lane (0: CTA per region)
   int32_t km;          // pixel build, depth 4-5: candidate counters (0: count every distinct leaf)
-  int32_t tb;          // pixel classify, depth 4-5: 1 if the tiled body applies
+  int32_t tb;          // pixel classify depth 4-5 / block classify depth 3-5: 1 if the L1 body applies
+  int32_t nseg;        // block classify (L1 body): 128-pixel segments per pixel row
+  int32_t pad2;
 };
 
 struct BItem {
@@ -152,6 +155,16 @@ __device__ __noinline__ void pixel_mg_dispatch(const BStream &S, int64_t t0, int
     pixel_mg_item_d<5>(S, t0, t1, smem);
 }
 
+__device__ __noinline__ void block_tb_dispatch(const BStream &S, int64_t t0, int64_t t1) {
+  for (int64_t t = t0; t < t1; t += kBatchThreads / 32) {
+    switch (S.depth) {
+      case 3: classify_block_tb_body<3, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
+      case 4: classify_block_tb_body<4, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
+      default: classify_block_tb_body<5, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
+    }
+  }
+}
+
 __device__ __noinline__ void pixel_tb_dispatch(const BStream &S, int64_t t0, int64_t t1) {
   for (int64_t t = t0; t < t1; t += kBatchThreads / 32) {
     if (S.depth == 4)
@@ -225,6 +238,9 @@ __device__ void run_item(const BStream &S, const BItem &it, uint32_t *err, uint8
       return;
     case OP_CLS_PIXEL_TB:
       pixel_tb_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux);
+      return;
+    case OP_CLS_BLOCK_TB:
+      block_tb_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux);
       return;
     case OP_CLS_GENERIC:
       classify_generic_body(S.test, S.F, S.H, S.W, S.kind, S.block, S.depth, S.wpr, S.model, S.mask, it.aux, S.hw,
@@ -422,6 +438,11 @@ static ocq_status plan_items(ocq_batch *b) {
       const int64_t nw = kBatchThreads / 32;
       const int64_t k = std::max<int64_t>(1, per * 1024 / (128 * (int64_t)st.F) / nw) * nw;
       for (int64_t t = 0; t < tiles; t += k) push(OP_CLS_PIXEL_TB, s, t, 0, std::min(tiles, t + k));
+    } else if (st.kind == OCQ_REGION_BLOCK && st.tb) {
+      const int64_t tiles = cdiv(st.H, st.block) * (int64_t)st.nseg * st.block;
+      const int64_t nw = kBatchThreads / 32;
+      const int64_t k = std::max<int64_t>(1, per * 1024 / (128 * (int64_t)st.F) / nw) * nw;
+      for (int64_t t = 0; t < tiles; t += k) push(OP_CLS_BLOCK_TB, s, t, 0, std::min(tiles, t + k));
     } else if (st.kind == OCQ_REGION_BLOCK && st.blk_tiles > 0) {
       const int64_t vg = std::max<int64_t>(1, cdiv(st.blk_tiles * st.F, per));
       for (int64_t v = 0; v < vg; ++v) push(OP_CLS_BLOCK_WS, s, v, vg, 0);
@@ -591,6 +612,11 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
       h.km = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : 0;
       h.tb = d.F > 0 && h.hw % 4 == 0 &&
              ((reinterpret_cast<uintptr_t>(d.test) | reinterpret_cast<uintptr_t>(d.mask)) & 3) == 0;
+    }
+    if (h.kind == OCQ_REGION_BLOCK && d.depth >= 3 && h.block % 4 == 0 && d.W % 4 == 0 && d.F > 0 &&
+        ((reinterpret_cast<uintptr_t>(d.test) | reinterpret_cast<uintptr_t>(d.mask)) & 3) == 0) {
+      h.tb = 1;
+      h.nseg = (d.W + 127) / 128;
     }
     if (h.kind == OCQ_REGION_BLOCK && block_warp_ok(d.N, d.H, d.W, h.block)) {
       const int npx = h.block * h.block;
