@@ -233,14 +233,18 @@ __device__ __forceinline__ void build_block_body(const uint8_t *__restrict__ fra
 // fewer than the 8^d leaves of its row.  So each warp counts its region's
 // leaves in a small table in shared memory instead of a dense counter row:
 // entry = (leaf + 1) << 16 | last frame << 8 | frames counted (N <= 255).
-// Per frame and pixel slot, __match_any_sync groups lanes holding the same
-// leaf and only the lowest such lane touches the entry, so a leaf is counted
-// once per frame (the "last frame" field makes later slots of the same frame
-// skip it).  With 8^d <= WarpTableCfg::S the table is indexed by the leaf
-// itself; above it, by a multiplicative hash with linear probing.  A region
-// with more than 3/4 S distinct leaves falls back to passes over S-leaf
-// chunks of the code space, each indexed directly.  The model row is zeroed
-// with vector stores and the kept leaves (count >= T) are ORed in.
+// Every lane updates the entry of its own pixel's leaf: in frame f the entry
+// is either still (leaf, earlier frame, c) or already (leaf, f, c + 1), and a
+// lane that reads the first writes the second, so lanes holding the same leaf
+// in the same frame write the same value and the leaf is counted once per
+// frame whatever order they run in.  Only a new leaf claiming an empty slot of
+// the hashed table needs an atomic (two leaves may hash to one slot).  One
+// __syncwarp per frame makes frame f's updates visible before frame f + 1.
+// With 8^d <= WarpTableCfg::S the table is indexed by the leaf itself; above
+// it, by a multiplicative hash with linear probing.  A region with more than
+// 3/4 S distinct leaves falls back to passes over S-leaf chunks of the code
+// space, each indexed directly.  The model row is zeroed with vector stores and
+// the kept leaves (count >= T) are ORed in.
 template <int D>
 struct WarpTableCfg {
   static constexpr int NC = 1 << (3 * D);
@@ -250,28 +254,38 @@ struct WarpTableCfg {
   static constexpr int LOGS = 3 * D < 10 ? 3 * D : 10;
 };
 
-template <int D>
-__device__ __forceinline__ bool warp_table_count(uint32_t *tab, uint32_t q, uint32_t f, int chunk) {
+// Counts leaf q in frame f; returns 1 if it took an empty slot of the hashed
+// table.  INDEXED: the slot is q mod S (direct table, or a chunk pass).
+template <int D, bool INDEXED>
+__device__ __forceinline__ uint32_t warp_table_count(uint32_t *tab, uint32_t q, uint32_t f) {
   using C = WarpTableCfg<D>;
-  uint32_t h;
-  if (C::DIRECT || chunk >= 0)
-    h = q & (C::S - 1);
-  else
-    h = (q * 2654435761u) >> (32 - C::LOGS);
-  const uint32_t key = (q + 1) << 16;
-  for (int probe = 0; probe < C::S; ++probe) {
-    uint32_t e = tab[h];
-    if (e == 0u) {
-      e = atomicCAS(&tab[h], 0u, key | (f << 8) | 1u);
-      if (e == 0u) return true;  // inserted
+  const uint32_t stamp = ((q + 1) << 16) | (f << 8);
+  if constexpr (INDEXED) {
+    volatile uint32_t *slot = &tab[q & (C::S - 1)];
+    const uint32_t e = *slot;
+    if (e == 0u)
+      *slot = stamp | 1u;
+    else if (((e >> 8) & 255u) != f)
+      *slot = stamp | ((e & 255u) + 1u);
+    return 0u;
+  } else {
+    const uint32_t key = (q + 1) << 16;
+    uint32_t h = (q * 2654435761u) >> (32 - C::LOGS);
+    for (int probe = 0; probe < C::S; ++probe) {
+      volatile uint32_t *slot = &tab[h];
+      uint32_t e = *slot;
+      if (e == 0u) {
+        e = atomicCAS(&tab[h], 0u, stamp | 1u);
+        if (e == 0u) return 1u;  // inserted
+      }
+      if ((e & 0xFFFF0000u) == key) {
+        if (((e >> 8) & 255u) != f) *slot = stamp | ((e & 255u) + 1u);
+        return 0u;
+      }
+      h = (h + 1) & (C::S - 1);
     }
-    if ((e & 0xFFFF0000u) == key) {
-      if (((e >> 8) & 255u) != f) tab[h] = key | (f << 8) | ((e & 255u) + 1u);
-      return false;
-    }
-    h = (h + 1) & (C::S - 1);
+    return 0u;  // unreachable: the table is never more than 3/4 + 1/4 full
   }
-  return false;  // unreachable: the table is never more than 3/4 + 1/32 full
 }
 
 // Zeroes the region's model row (WPR words) with the warp's lanes.
@@ -288,7 +302,6 @@ __device__ __forceinline__ void warp_zero_row(uint32_t *row) {
 }
 
 // Emits kept leaves of the table into the (zeroed) row and clears the table.
-// chunk < 0: entries carry their leaf; chunk >= 0 (direct pass) likewise.
 template <int D>
 __device__ __forceinline__ void warp_emit(uint32_t *tab, uint32_t *row, uint32_t T) {
   using C = WarpTableCfg<D>;
@@ -307,23 +320,25 @@ __device__ __forceinline__ void warp_emit(uint32_t *tab, uint32_t *row, uint32_t
   __syncwarp();
 }
 
-// One pass over the region's N frames; chunk < 0 counts every leaf (hashed),
-// chunk >= 0 only leaves in [chunk * S, chunk * S + S).  Returns false if the
-// hashed pass saw more than 3/4 S distinct leaves.
-template <int D, int PPL, int PF>
+// One pass over the region's N frames.  CHUNKED: only leaves in
+// [chunk * S, chunk * S + S), indexed directly; otherwise every leaf.  Returns
+// false if the hashed pass saw more than 3/4 S distinct leaves.
+template <int D, int PPL, int PF, bool CHUNKED>
 __device__ __forceinline__ bool warp_region_pass(const uint8_t *__restrict__ frames, int N, int64_t fstride,
                                                  const uint32_t (&off)[PPL], int npx, uint32_t *tab, int chunk) {
   using C = WarpTableCfg<D>;
+  constexpr bool INDEXED = C::DIRECT || CHUNKED;
   const int lane = threadIdx.x & 31;
-  int inserted = 0;
+  uint32_t inserted = 0;
   for (int f0 = 0; f0 < N; f0 += PF) {
     uint32_t yv[PF][PPL];
+    const uint8_t *fb = frames + (int64_t)f0 * fstride;
 #pragma unroll
     for (int j = 0; j < PF; ++j)
 #pragma unroll
       for (int k = 0; k < PPL; ++k)
         if (f0 + j < N && lane + 32 * k < npx) {
-          const uint8_t *s = frames + (int64_t)(f0 + j) * fstride + off[k];
+          const uint8_t *s = fb + (int64_t)j * fstride + off[k];
           yv[j][k] = (uint32_t)__ldg(s) | ((uint32_t)__ldg(s + 1) << 8) | ((uint32_t)__ldg(s + 2) << 16);
         }
 #pragma unroll
@@ -331,17 +346,15 @@ __device__ __forceinline__ bool warp_region_pass(const uint8_t *__restrict__ fra
       if (f0 + j >= N) break;
 #pragma unroll
       for (int k = 0; k < PPL; ++k) {
-        if (32 * k >= npx) break;
-        const bool valid = lane + 32 * k < npx;
-        const uint32_t q = valid ? planar_code<D>(yv[j][k]) : 0xFFFFFFFFu;
-        const bool mine = valid && (chunk < 0 || (int)(q >> C::LOGS) == chunk);
-        const unsigned peers = __match_any_sync(0xFFFFFFFFu, mine ? q : 0xFFFFFFFFu);
-        bool ins = false;
-        if (mine && lane == __ffs(peers) - 1) ins = warp_table_count<D>(tab, q, (uint32_t)(f0 + j), chunk);
-        inserted += __popc(__ballot_sync(0xFFFFFFFFu, ins));
-        __syncwarp();
+        if (lane + 32 * k < npx) {
+          const uint32_t q = planar_code<D>(yv[j][k]);
+          if (!CHUNKED || (int)(q >> C::LOGS) == chunk)
+            inserted += warp_table_count<D, INDEXED>(tab, q, (uint32_t)(f0 + j));
+        }
       }
-      if (chunk < 0 && !C::DIRECT && inserted > 3 * C::S / 4) return false;
+      __syncwarp();
+      if constexpr (!INDEXED)
+        if (__reduce_add_sync(0xFFFFFFFFu, inserted) > (uint32_t)(3 * C::S / 4)) return false;
     }
   }
   return true;
@@ -370,33 +383,19 @@ __device__ __forceinline__ void build_block_warp_body(const uint8_t *__restrict_
     }
     uint32_t *row = model + r * C::WPR;
     warp_zero_row<D>(row);
-    if (warp_region_pass<D, PPL, PF>(frames, N, fstride, off, npx, tab, -1)) {
+    if (warp_region_pass<D, PPL, PF, false>(frames, N, fstride, off, npx, tab, -1)) {
       warp_emit<D>(tab, row, T);
     } else {
       for (int s = lane; s < C::S; s += 32) tab[s] = 0u;
       for (int c = 0; c < C::NC / C::S; ++c) {
         __syncwarp();
-        warp_region_pass<D, PPL, PF>(frames, N, fstride, off, npx, tab, c);
+        warp_region_pass<D, PPL, PF, true>(frames, N, fstride, off, npx, tab, c);
         warp_emit<D>(tab, row, T);
       }
     }
   }
 }
 
-// ---- block regions, N <= 64: frame masks --------------------------------------
-// The frames a leaf occurs in, as an N-bit mask: the region's count for a leaf
-// is the popcount of the OR, over the region's pixels, of each pixel's mask
-// for that leaf.  A lane walks its pixel through all N frames keeping the
-// masks of the pixel's first two distinct leaves in registers (a background
-// pixel rarely shows more); any further leaf ORs its frame bit straight into
-// the region's table.  The lane then ORs its two masks into the table, so the
-// shared table sees a few operations per pixel rather than one per pixel and
-// frame.  A group of WPG warps shares one region and one table (slots of 32
-// pixels are split among its warps).  Table: masks[S] (u64), then keys[S]
-// (leaf + 1, 0 = empty; absent when 8^d <= 512 and the leaf is the index), then
-// an insert counter and an overflow flag.  A region with more than 3/4 S
-// distinct leaves is rebuilt by the group's first warp with the per-warp
-// table path above.
 // ---- pixel regions, depth <= 3 -------------------------------------------------
 // Thread t of a 128-thread CTA owns pixel location p and a private column of
 // counter words cnt[k * 128 + t] (4 u8 or 2 u16 counters per word).
