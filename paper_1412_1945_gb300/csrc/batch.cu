@@ -34,15 +34,11 @@ enum : int32_t {
   OP_MERGE,            // planes_merge_body        (whole frame)
   OP_BUILD_BLOCK,      // build_block_body         (blocks, depth <= 5, b > 16)
   OP_BUILD_BLOCK_WARP, // build_block_warp_body    (blocks, depth <= 5, b <= 16): regions [vb, aux)
-  OP_BUILD_PIXEL_WS,   // build_pixel_ws_body      (pixels, depth <= 3, aligned)
-  OP_BUILD_PIXEL_CNT,  // build_pixel_counters_body (pixels, depth <= 3, remainder / unaligned)
-  OP_BUILD_PIXEL_MG,   // build_pixel_mg_body      (pixels, depth 4-5): 32-pixel tiles [vb, aux)
+  OP_BUILD_PIXEL_MG,   // build_pixel_mg_body      (pixels): 32-pixel tiles [vb, aux)
   OP_CLS_FRAME,        // classify_frame_body      (whole frame, depth <= 6)
-  OP_CLS_PIXEL_WS,     // classify_pixel_ws_body   (pixels, depth <= 3, aligned)
-  OP_CLS_BLOCK_WS,     // classify_block_ws_body   (blocks, b % 8 == 0, W % 16 == 0)
-  OP_CLS_PIXEL_TB,     // classify_pixel_tb_body   (pixels, depth 4-5, H*W % 4 == 0): 128-pixel tiles [vb, aux)
-  OP_CLS_BLOCK_TB,     // classify_block_tb_body   (blocks, depth 3-5, b % 4 == 0, W % 4 == 0): tiles [vb, aux)
-  OP_CLS_GENERIC       // classify_generic_body    (everything else, and remainders)
+  OP_CLS_PIXEL_TB,     // classify_pixel_tb_body   (pixels, H*W % 4 == 0): 128-pixel tiles [vb, aux)
+  OP_CLS_BLOCK_TB,     // classify_block_tb_body   (blocks, b % 4 == 0, W % 4 == 0): tiles [vb, aux)
+  OP_CLS_GENERIC       // classify_generic_body    (everything else)
 };
 
 struct BStream {
@@ -51,19 +47,15 @@ struct BStream {
   uint32_t *model;  // R * wpr words, internal (planar) order
   uint32_t *occ;    // whole-frame streams: N * wpr words of scratch
   int64_t hw, R, wpr;
-  int64_t ptiles;      // per-pixel 1024-pixel classify tiles (hw / 1024)
-  int64_t btiles;      // pixel-build 128-pixel tiles (hw / 128)
-  int64_t blk_tiles;   // block classify tiles
   int32_t N, F, H, W, kind, block, bw, depth, T, P;
-  int32_t wt, ntx;     // block classify tile width and tiles per strip
   int32_t n_build;     // items that complete the model
   int32_t n_occ;       // occupancy items (whole frame)
   int32_t occ_nbx;     // pixel chunks per frame in occupancy items
   int32_t ppl;         // block build, one warp per region: pixels per lane (0: CTA per region)
-  int32_t km;          // pixel build, depth 4-5: candidate counters (0: count every distinct leaf)
-  int32_t tb;          // pixel classify depth 4-5 / block classify depth 3-5: 1 if the L1 body applies
+  int32_t km;          // pixel build: candidate counters (0: count every distinct leaf)
+  int32_t tb;          // pixel / block classify: 1 if the L1 body applies
   int32_t nseg;        // block classify (L1 body): 128-pixel segments per pixel row
-  int32_t pad2;
+  int32_t pad;
 };
 
 struct BItem {
@@ -72,7 +64,7 @@ struct BItem {
   int64_t aux;  // first pixel of a remainder range (CNT / GENERIC)
 };
 
-static constexpr int kBatchThreads = 160;
+static constexpr int kBatchThreads = 256;
 static constexpr int64_t kOccChunk = 16384;
 
 // Counter block: [0] next item, [1] timeout flag, [2..2+S) occupancy done, [2+S..2+2S) build done.
@@ -89,10 +81,6 @@ __device__ __forceinline__ bool wait_count(const uint32_t *ctr, uint32_t want, u
     }
   }
   return true;
-}
-
-__device__ __forceinline__ void mbar_inval(uint32_t bar) {
-  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 // The warp-granular bodies run as calls of their own (one call site each), so
@@ -149,15 +137,20 @@ __device__ __forceinline__ void pixel_mg_item_d(const BStream &S, int64_t t0, in
 }
 
 __device__ __noinline__ void pixel_mg_dispatch(const BStream &S, int64_t t0, int64_t t1, uint8_t *smem) {
-  if (S.depth == 4)
-    pixel_mg_item_d<4>(S, t0, t1, smem);
-  else
-    pixel_mg_item_d<5>(S, t0, t1, smem);
+  switch (S.depth) {
+    case 1: pixel_mg_item_d<1>(S, t0, t1, smem); break;
+    case 2: pixel_mg_item_d<2>(S, t0, t1, smem); break;
+    case 3: pixel_mg_item_d<3>(S, t0, t1, smem); break;
+    case 4: pixel_mg_item_d<4>(S, t0, t1, smem); break;
+    default: pixel_mg_item_d<5>(S, t0, t1, smem); break;
+  }
 }
 
 __device__ __noinline__ void block_tb_dispatch(const BStream &S, int64_t t0, int64_t t1) {
   for (int64_t t = t0; t < t1; t += kBatchThreads / 32) {
     switch (S.depth) {
+      case 1: classify_block_tb_body<1, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
+      case 2: classify_block_tb_body<2, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
       case 3: classify_block_tb_body<3, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
       case 4: classify_block_tb_body<4, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
       default: classify_block_tb_body<5, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
@@ -167,15 +160,18 @@ __device__ __noinline__ void block_tb_dispatch(const BStream &S, int64_t t0, int
 
 __device__ __noinline__ void pixel_tb_dispatch(const BStream &S, int64_t t0, int64_t t1) {
   for (int64_t t = t0; t < t1; t += kBatchThreads / 32) {
-    if (S.depth == 4)
-      classify_pixel_tb_body<4, 8>(S.test, S.F, S.hw, S.model, S.mask, t);
-    else
-      classify_pixel_tb_body<5, 8>(S.test, S.F, S.hw, S.model, S.mask, t);
+    switch (S.depth) {
+      case 1: classify_pixel_tb_body<1, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+      case 2: classify_pixel_tb_body<2, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+      case 3: classify_pixel_tb_body<3, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+      case 4: classify_pixel_tb_body<4, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+      default: classify_pixel_tb_body<5, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+    }
   }
 }
 
 template <int D>
-__device__ __forceinline__ void run_item_d(const BStream &S, const BItem &it, uint32_t *err, uint8_t *smem) {
+__device__ __forceinline__ void run_item_d(const BStream &S, const BItem &it, uint8_t *smem) {
   const uint32_t T = (uint32_t)S.T;
   switch (it.op) {
     case OP_OCC_FRAME:
@@ -184,45 +180,15 @@ __device__ __forceinline__ void run_item_d(const BStream &S, const BItem &it, ui
     case OP_BUILD_BLOCK:
       if constexpr (D <= 5) build_block_body<D>(S.train, S.N, S.H, S.W, S.block, S.bw, S.P, T, S.model, S.R, it.vb, it.vg);
       break;
-    case OP_BUILD_PIXEL_WS:
-      if constexpr (D <= 3) {
-        build_pixel_ws_body<D, 128, 8, 3, false, false>(S.train, S.N, S.hw, S.btiles, T, S.model, nullptr, it.vb, it.vg,
-                                                        err);
-        __syncthreads();
-        using C = WsBuildCfg<D, 128, 8, 3, false>;
-        if (threadIdx.x < 6) mbar_inval(smem_addr(smem + C::STATE + 3 * C::STAGE + threadIdx.x * 8));
-      }
-      break;
-    case OP_BUILD_PIXEL_CNT:
-      if constexpr (D <= 3) build_pixel_counters_body<D, false>(S.train, S.N, S.hw, it.aux, T, S.model, it.vb);
-      break;
     case OP_CLS_FRAME:
       if constexpr (D <= 6) classify_frame_body<D>(S.test, (int64_t)S.F * S.hw, S.model, S.mask, it.vb, it.vg);
-      break;
-    case OP_CLS_PIXEL_WS:
-      if constexpr (D <= 3) {
-        classify_pixel_ws_body<D, 4, 8, 4, 4>(S.test, S.F, S.hw, S.ptiles, S.model, S.mask, it.vb, it.vg, err);
-        __syncthreads();
-        const size_t off = classify_pixel_ws_bars<D, 4, 8, 4, 4>();
-        if (threadIdx.x < 8) mbar_inval(smem_addr(smem + off + threadIdx.x * 8));
-      }
-      break;
-    case OP_CLS_BLOCK_WS:
-      if constexpr (D <= 5) {
-        classify_block_ws_body<D, 4, 4>(S.test, S.F, S.H, S.W, S.block, S.wt, S.ntx, S.blk_tiles, S.model, S.mask,
-                                        it.vb, it.vg, err);
-        __syncthreads();
-        constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
-        const size_t off = classify_block_ws_rows_bytes(S.block, S.wt, WPR) + (size_t)4 * 4 * 1024 * 3;
-        if (threadIdx.x < 8) mbar_inval(smem_addr(smem + off + threadIdx.x * 8));
-      }
       break;
     default:
       break;
   }
 }
 
-__device__ void run_item(const BStream &S, const BItem &it, uint32_t *err, uint8_t *smem) {
+__device__ void run_item(const BStream &S, const BItem &it, uint8_t *smem) {
   switch (it.op) {
     case OP_OCC_GLOBAL:
       occ_global_body(S.train, S.H, S.W, OCQ_REGION_FRAME, 0, S.depth, 0, S.N, 1, S.wpr, S.occ, it.vb, it.vg);
@@ -250,17 +216,17 @@ __device__ void run_item(const BStream &S, const BItem &it, uint32_t *err, uint8
       break;
   }
   switch (S.depth) {
-    case 1: run_item_d<1>(S, it, err, smem); break;
-    case 2: run_item_d<2>(S, it, err, smem); break;
-    case 3: run_item_d<3>(S, it, err, smem); break;
-    case 4: run_item_d<4>(S, it, err, smem); break;
-    case 5: run_item_d<5>(S, it, err, smem); break;
-    case 6: run_item_d<6>(S, it, err, smem); break;
+    case 1: run_item_d<1>(S, it, smem); break;
+    case 2: run_item_d<2>(S, it, smem); break;
+    case 3: run_item_d<3>(S, it, smem); break;
+    case 4: run_item_d<4>(S, it, smem); break;
+    case 5: run_item_d<5>(S, it, smem); break;
+    case 6: run_item_d<6>(S, it, smem); break;
     default: break;
   }
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BStream *__restrict__ streams,
+__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BStream *__restrict__ streams,
                                                               const BItem *__restrict__ items, int n_items, int S,
                                                               uint32_t *ctr) {
   extern __shared__ __align__(128) uint8_t dsmem[];
@@ -283,7 +249,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BStream *
       __threadfence();
     }
     __syncthreads();
-    if (ok) run_item(st, it, err, dsmem);
+    if (ok) run_item(st, it, dsmem);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0 && ok) {
@@ -304,16 +270,8 @@ static size_t item_smem(const BStream &h) {
       need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * std::min(1 << (3 * d), 1024) * 4);
     else
       need = std::max<size_t>(need, (size_t)h.wpr * (h.P + 2) * 4);
-    if (h.wt > 0) need = std::max<size_t>(need, classify_block_ws_rows_bytes(h.block, h.wt, (int)h.wpr) +
-                                                  (size_t)4 * 4 * 1024 * 3 + 8 * 8);
   } else {
-    if (d <= 3) {
-      need = std::max<size_t>(need, (size_t)h.wpr * 4 * 1024 + (size_t)4 * 4 * 1024 * 3 + 8 * 8);  // classify ws
-      need = std::max<size_t>(need, (size_t)((1 << (3 * d)) / 4 > 0 ? (1 << (3 * d)) / 4 : 1) * 128 * 4 +
-                                        (size_t)3 * 8 * 128 * 3 + 6 * 8);                          // build ws
-    } else {
-      need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * h.N * 32 * 2);  // candidate build: leaves
-    }
+    need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * h.N * 32 * 2);  // candidate build: leaves
   }
   return need;
 }
@@ -347,8 +305,6 @@ struct ocq_batch {
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
 };
-
-static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -396,19 +352,10 @@ static ocq_status plan_items(ocq_batch *b) {
       const int64_t vg = cdiv(st.R, 8);
       for (int64_t v = 0; v < vg; ++v, ++st.n_build) push(OP_BUILD_BLOCK, s, v, vg, 0);
     } else if (st.kind == OCQ_REGION_PIXEL) {
-      if (st.depth >= 4) {
-        constexpr int64_t kTilesPerItem = 40;  // 32-pixel tiles, 8 per warp
-        const int64_t tiles = cdiv(st.hw, 32);
-        for (int64_t t = 0; t < tiles; t += kTilesPerItem, ++st.n_build)
-          push(OP_BUILD_PIXEL_MG, s, t, 0, std::min(tiles, t + kTilesPerItem));
-      } else {
-        if (st.btiles > 0) {
-          const int64_t vg = cdiv(st.btiles, 8);
-          for (int64_t v = 0; v < vg; ++v, ++st.n_build) push(OP_BUILD_PIXEL_WS, s, v, vg, 0);
-        }
-        const int64_t p0 = st.btiles * 128;
-        for (int64_t v = 0; v < cdiv(st.hw - p0, 128); ++v, ++st.n_build) push(OP_BUILD_PIXEL_CNT, s, v, 0, p0);
-      }
+      constexpr int64_t kTilesPerItem = 64;  // 32-pixel tiles, 8 per warp
+      const int64_t tiles = cdiv(st.hw, 32);
+      for (int64_t t = 0; t < tiles; t += kTilesPerItem, ++st.n_build)
+        push(OP_BUILD_PIXEL_MG, s, t, 0, std::min(tiles, t + kTilesPerItem));
     }
   }
   std::vector<int> corder;
@@ -429,10 +376,6 @@ static ocq_status plan_items(ocq_batch *b) {
     if (st.kind == OCQ_REGION_FRAME && st.depth <= 6) {
       const int64_t vg = std::max<int64_t>(1, cdiv(st.hw * st.F, per * 1024));
       for (int64_t v = 0; v < vg; ++v) push(OP_CLS_FRAME, s, v, vg, 0);
-    } else if (st.kind == OCQ_REGION_PIXEL && st.ptiles > 0) {
-      const int64_t vg = std::max<int64_t>(1, cdiv(st.ptiles * st.F, per));
-      for (int64_t v = 0; v < vg; ++v) push(OP_CLS_PIXEL_WS, s, v, vg, 0);
-      generic(st.ptiles * 1024);
     } else if (st.kind == OCQ_REGION_PIXEL && st.tb) {
       const int64_t tiles = cdiv(st.hw, 128);
       const int64_t nw = kBatchThreads / 32;
@@ -443,9 +386,6 @@ static ocq_status plan_items(ocq_batch *b) {
       const int64_t nw = kBatchThreads / 32;
       const int64_t k = std::max<int64_t>(1, per * 1024 / (128 * (int64_t)st.F) / nw) * nw;
       for (int64_t t = 0; t < tiles; t += k) push(OP_CLS_BLOCK_TB, s, t, 0, std::min(tiles, t + k));
-    } else if (st.kind == OCQ_REGION_BLOCK && st.blk_tiles > 0) {
-      const int64_t vg = std::max<int64_t>(1, cdiv(st.blk_tiles * st.F, per));
-      for (int64_t v = 0; v < vg; ++v) push(OP_CLS_BLOCK_WS, s, v, vg, 0);
     } else {
       generic(0);
     }
@@ -602,18 +542,13 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     int P = 0;
     for (uint32_t v = (uint32_t)d.N; v; v >>= 1) ++P;
     h.P = P;
-    const bool al = aligned16(d.train) && (d.F == 0 || (aligned16(d.test) && aligned16(d.mask)));
-    if (h.kind == OCQ_REGION_PIXEL && d.depth <= 3 && al && h.hw % 16 == 0) {
-      h.ptiles = h.hw / 1024;
-      h.btiles = h.hw / 128;
-    }
-    if (h.kind == OCQ_REGION_PIXEL && d.depth >= 4) {
+    if (h.kind == OCQ_REGION_PIXEL) {
       const int k = d.N / d.T;
       h.km = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : 0;
       h.tb = d.F > 0 && h.hw % 4 == 0 &&
              ((reinterpret_cast<uintptr_t>(d.test) | reinterpret_cast<uintptr_t>(d.mask)) & 3) == 0;
     }
-    if (h.kind == OCQ_REGION_BLOCK && d.depth >= 3 && h.block % 4 == 0 && d.W % 4 == 0 && d.F > 0 &&
+    if (h.kind == OCQ_REGION_BLOCK && h.block % 4 == 0 && d.W % 4 == 0 && d.F > 0 &&
         ((reinterpret_cast<uintptr_t>(d.test) | reinterpret_cast<uintptr_t>(d.mask)) & 3) == 0) {
       h.tb = 1;
       h.nseg = (d.W + 127) / 128;
@@ -621,13 +556,6 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     if (h.kind == OCQ_REGION_BLOCK && block_warp_ok(d.N, d.H, d.W, h.block)) {
       const int npx = h.block * h.block;
       h.ppl = npx <= 32 ? 1 : npx <= 64 ? 2 : npx <= 128 ? 4 : 8;
-    }
-    if (h.kind == OCQ_REGION_BLOCK && d.depth <= 5 && al) {
-      h.wt = block_tile_width(h.block, d.depth, d.W);
-      if (h.wt > 0) {
-        h.ntx = (d.W + h.wt - 1) / h.wt;
-        h.blk_tiles = (int64_t)h.ntx * ((d.H + h.block - 1) / h.block);
-      }
     }
     b->hs.push_back(h);
     model_off[s] = bytes;
