@@ -323,7 +323,9 @@ void ocq_server_destroy(ocq_server *server);
  *                             direct loads, frames per stage = frames prefetched;
  *                             4 as 2 with a dedicated copy warp; 5 as 4 with one 2-D
  *                             tensor copy per stage; 6 as 4 setting kept bits as
- *                             counts reach T; 7 as 5 and 6 together}
+ *                             counts reach T; 7 as 5 and 6 together; 8 frequent-leaf
+ *                             candidates per pixel counted in registers, no shared
+ *                             counters (N <= 255, else as variant 0)}
  *   OCQ_TUNE_CLASSIFY_PIXEL_DEEP per-pixel classify, depth >= 4 (a warp walks
  *                            all frames of its pixel locations); params =
  *                            {pixel locations per lane (1 or 4), frames prefetched,

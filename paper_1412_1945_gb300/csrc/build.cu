@@ -791,9 +791,26 @@ struct BuildVariant {
   }
 // kind 4: copy warp + row copies; 5: copy warp + one tensor copy per stage;
 // 6: as 4 with kept bits set as counts reach T; 7: as 5 with kept bits
+// kind 8: frequent-leaf candidates per pixel (build_pixel_mg_kernel: no shared
+// counters, frames read once with direct loads); beyond 255 frames it falls
+// back to the first variant.
+template <int D>
+static ocq_status launch_pixel_candidates(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  if (N > 255) return launch_pixel_ws<D, 128, 8, 3, true, false>(frames, N, m, st);
+  return launch_pixel_mg<D>(frames, N, m, st);
+}
+#define OCQ_MV                                                                                            \
+  {                                                                                                       \
+    128, 8, 0, 8, {                                                                                       \
+      {launch_pixel_candidates<1>, launch_pixel_candidates<2>, launch_pixel_candidates<3>},               \
+          {launch_pixel_candidates<1>, launch_pixel_candidates<2>, launch_pixel_candidates<3>}            \
+    }                                                                                                     \
+  }
 static const BuildVariant kBuildVariants[] = {
     OCQ_WV(128, 8, 3, 5, true, false),  OCQ_WV(128, 8, 3, 4, false, false), OCQ_WV(128, 4, 5, 5, true, false),
-    OCQ_WV(128, 8, 3, 7, true, true),   OCQ_RV(128, 8, 3),                   OCQ_BV(128, 16, 2, false)};
+    OCQ_WV(128, 8, 3, 7, true, true),   OCQ_RV(128, 8, 3),                   OCQ_BV(128, 16, 2, false),
+    OCQ_MV};
+#undef OCQ_MV
 #undef OCQ_WV
 #undef OCQ_DV
 #undef OCQ_BV

@@ -379,3 +379,26 @@ def test_block_deep_classify_forms(ocq, torch, b, d):
                 assert (mask == om).all(), (H, W, form)
     finally:
         O.ocq_tune_select(kernel, saved)
+
+
+@pytest.mark.parametrize("H,W,N,F", [(37, 53, 6, 5), (1080, 1920, 10, 70)])
+def test_detect_from_host_memory(ocq, torch, H, W, N, F):
+    """ocq_detect_host (copies in, build, chunked classify with copies in and
+    out overlapped) gives the device path's masks;
+    the 1080p case spans three chunks, the last one short."""
+    sc = ocq_synth.make_scene("bimodal", H, W, N, F, seed=H + F)
+    train = torch.empty((N, H, W, 3), dtype=torch.uint8, device="cuda")
+    test = torch.empty((F, H, W, 3), dtype=torch.uint8, device="cuda")
+    ocq_synth.fill_device(sc, 0, N, train)
+    ocq_synth.fill_device(sc, N, F, test)
+    h_train = train.cpu().pin_memory()
+    h_test = test.cpu().pin_memory()
+    h_mask = torch.full((F, H, W), 9, dtype=torch.uint8).pin_memory()
+    ocq.ocq.ocq_detect_host(h_train, N, h_test, F, H, W, PIXEL, 0, 3, 3, h_mask)
+    m = ocq.build_model(train, 3, 3, "pixel")
+    dev_mask = ocq.classify(m, test).cpu()
+    m.free()
+    assert torch.equal(h_mask, dev_mask)
+    if H * W < 10000:
+        _, om = oracle.run(h_train.numpy(), 3, 3, PIXEL, 0, h_test.numpy())
+        assert (h_mask.numpy() == om).all()
