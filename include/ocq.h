@@ -347,6 +347,23 @@ ocq_status ocq_tune_select(int kernel, int variant);
 ocq_status ocq_tune_describe(int kernel, int variant, int32_t *params, int n);
 
 /*
+ * Test hooks (no counterpart in the paper).  They make failures happen on the
+ * host side so that the error paths can be tested without faulting a GPU.
+ *   ocq_debug_fail_allocations: the next `count` device allocations the library
+ *     makes fail as if the device were out of memory (the call returns
+ *     OCQ_ENOMEM after releasing what it had allocated); 0 clears.
+ *   ocq_debug_async_bytes_in_use: bytes currently allocated from the current
+ *     device's default stream-ordered pool (to check for leaks).
+ *   ocq_batch_debug_hold_builds: leaves stream `stream`'s build items out of
+ *     the persistent work list (-1 restores them); its classify items then wait
+ *     for a model that never comes, give up after the bounded wait (1 s) and
+ *     ocq_batch_status reports OCQ_ETIMEOUT; the GPU context stays usable.
+ */
+void ocq_debug_fail_allocations(int count);
+ocq_status ocq_debug_async_bytes_in_use(size_t *bytes);
+ocq_status ocq_batch_debug_hold_builds(ocq_batch *batch, int stream);
+
+/*
  * Whole-frame build (as ocq_build_model with OCQ_REGION_FRAME) that allocates
  * no memory.  The paper has no counterpart; it serves callers that cannot
  * allocate device memory at call time -- pipelines that reserve every buffer

@@ -18,7 +18,11 @@ void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_r
 // Stream-ordered allocation from the memory pool the calling thread has
 // selected (a server's own pool, see PoolScope), else the device's default.
 static thread_local cudaMemPool_t t_pool = nullptr;
+static std::atomic<int> g_fail_allocs{0};  // test hook: allocations still to refuse
 cudaError_t malloc_async(void **p, size_t bytes, cudaStream_t st) {
+  int n = g_fail_allocs.load();
+  while (n > 0)
+    if (g_fail_allocs.compare_exchange_weak(n, n - 1)) return cudaErrorMemoryAllocation;
   return t_pool ? cudaMallocFromPoolAsync(p, bytes, t_pool, st) : cudaMallocAsync(p, bytes, st);
 }
 PoolScope::PoolScope(cudaMemPool_t pool) : prev_(t_pool) { t_pool = pool; }
@@ -313,6 +317,20 @@ ocq_status ocq_tune_select(int kernel, int variant) {
     return OCQ_EINVAL;
   }
   return OCQ_OK;
+}
+
+void ocq_debug_fail_allocations(int count) { g_fail_allocs.store(count > 0 ? count : 0); }
+
+ocq_status ocq_debug_async_bytes_in_use(size_t *bytes) {
+  if (!bytes) return OCQ_EINVAL;
+  int dev = 0;
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, dev);
+  uint64_t used = 0;
+  if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+  *bytes = (size_t)used;
+  return cuda_status(e, "default pool usage");
 }
 
 ocq_status ocq_tune_describe(int kernel, int variant, int32_t *params, int n) {

@@ -301,6 +301,7 @@ struct ocq_batch {
   cudaGraphExec_t exec = nullptr;
   int device = 0;
   int mode = OCQ_BATCH_PERSISTENT;
+  int hold = -1;  // test hook: stream whose build items are left out of the work list
   std::vector<cudaStream_t> side;  // branch streams of the graph form
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
@@ -316,6 +317,7 @@ static ocq_status plan_items(ocq_batch *b) {
   const int S = (int)b->hs.size();
   std::vector<BStream> &hs = b->hs;
   auto push = [&](int32_t op, int s, int64_t vb, int64_t vg, int64_t aux) {
+    if (s == b->hold && op < OP_CLS_FRAME) return;  // counted, never run: its classify items time out
     BItem it;
     it.op = op, it.stream = s, it.vb = vb, it.vg = vg, it.aux = aux;
     b->items.push_back(it);
@@ -777,5 +779,17 @@ ocq_status ocq_batch_set_mode(ocq_batch *b, int mode) {
 }
 
 int ocq_batch_get_mode(const ocq_batch *b) { return b ? b->mode : -1; }
+
+ocq_status ocq_batch_debug_hold_builds(ocq_batch *b, int stream) {
+  if (!b || stream < -1 || stream >= (int)b->hs.size()) {
+    set_error("ocq_batch_debug_hold_builds: bad arguments");
+    return OCQ_EINVAL;
+  }
+  b->hold = stream;
+  ocq_status rc = plan_items(b);
+  if (rc == OCQ_OK) rc = upload_plan(b, b->owner);
+  free_graph(b);
+  return rc;
+}
 
 }  // extern "C"

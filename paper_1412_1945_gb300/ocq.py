@@ -89,6 +89,9 @@ SIGNATURES = {
     "ocq_batch_get_work": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "ocq_batch_autotune": (_i32, [_vp, _i32, _vp]),
     "ocq_batch_set_mode": (_i32, [_vp, _i32]),
+    "ocq_debug_fail_allocations": (None, [_i32]),
+    "ocq_debug_async_bytes_in_use": (_i32, [ctypes.POINTER(ctypes.c_size_t)]),
+    "ocq_batch_debug_hold_builds": (_i32, [_vp, _i32]),
     "ocq_build_model_groups": (_i32, [_vp, _i32, _i32, _i32, ocq_region, _i32, _i32, _i32, _vp,
                                       ctypes.POINTER(_vp)]),
     "ocq_redraw": (_i32, [_vp, _i64, _i32, _vp, _vp]),
@@ -386,6 +389,20 @@ def ocq_batch_get_work(batch, kind):
     u, n = ctypes.c_int(), ctypes.c_int64()
     _check(load().ocq_batch_get_work(batch.handle, kind, ctypes.byref(u), ctypes.byref(n)))
     return u.value, n.value
+
+
+def ocq_debug_fail_allocations(count):
+    load().ocq_debug_fail_allocations(count)
+
+
+def ocq_debug_async_bytes_in_use() -> int:
+    n = ctypes.c_size_t()
+    _check(load().ocq_debug_async_bytes_in_use(ctypes.byref(n)))
+    return n.value
+
+
+def ocq_batch_debug_hold_builds(batch, stream):
+    _check(load().ocq_batch_debug_hold_builds(batch.handle, stream))
 
 
 def ocq_batch_set_mode(batch, mode):
