@@ -49,7 +49,7 @@ typedef enum {
   OCQ_ECUDA = 3,    /* a CUDA call failed (message in ocq_last_error) */
   OCQ_ETIMEOUT = 4, /* a bounded device-side wait gave up */
   OCQ_EBUSY = 5,    /* no capacity right now (serving admission); retry later */
-  OCQ_ENOTSUP = 6   /* valid request this build does not handle */
+  OCQ_ENOTSUP = 6   /* valid request the library does not handle */
 } ocq_status;
 
 /* Region geometry (Sec. 3 "subdivide a video into multiple regions"; Sec. 4).
@@ -160,8 +160,7 @@ ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int
 
 /*
  * One tree per group of `group` consecutive training frames instead of one per
- * frame (Sec. 3: "a tree for each frame ... or a group of frames"; the last
- * group holds the remaining frames).  A group's tree holds every leaf of any
+ * frame (Sec. 3 allows either; the last group holds the remaining frames).  A group's tree holds every leaf of any
  * of its frames; T counts trees: 1 <= T <= ceil(N / group).  group = 1 is
  * ocq_build_model.  Same buffers, ownership and errors as ocq_build_model.
  */

@@ -225,9 +225,9 @@ static int check_args(int H, int W, int kind, int block, int depth) {
   return 0;
 }
 
-/* Number of trees when one tree holds `group` consecutive frames (Sec. 3:
- * "a tree for each frame ... or a group of frames"); the last group holds
- * the remaining frames. */
+/* Number of trees when one tree holds `group` consecutive frames (Sec. 3
+ * allows one tree per frame or per group of frames); the last group holds the
+ * remaining frames. */
 static int tree_count(int N, int group) { return (N + group - 1) / group; }
 
 /* Builds the trees of region r: tree j holds the region's pixels of training

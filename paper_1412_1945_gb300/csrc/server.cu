@@ -1,7 +1,7 @@
 // Served form: camera streams join and leave while frames arrive; each
 // camera's model and its sliding window of the last N frames stay resident
-// in HBM.  The paper names "octree updation" (Sec. 4) without a procedure; the
-// window semantics here are:
+// in HBM.  The title of the paper's Sec. 4 mentions updating the octree but
+// gives no procedure; the window semantics here are:
 //   * the N training frames build M_0 (Sec. 3, Alg. 1-2);
 //   * test frame t (t = 0, 1, ...) is classified against M_floor(t/K) (Alg. 3);
 //   * after classification frame t enters a ring of the last N frames;
