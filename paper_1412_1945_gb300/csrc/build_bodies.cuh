@@ -360,6 +360,63 @@ __device__ __forceinline__ bool warp_region_pass(const uint8_t *__restrict__ fra
   return true;
 }
 
+// The same pass for a full 8 x 8 block whose rows start on 4-byte boundaries
+// (W % 4 == 0, 4-byte aligned frames): per frame the block is 8 rows of 24
+// bytes = 48 words, word m = row * 6 + u; lane l loads words l and 32 + l
+// (l < 16), and each of the lane's two pixels (i = lane, lane + 32; row i / 8,
+// column i % 8, bytes 24 * row + 3 * column .. + 2) is assembled from the two
+// words holding it with shuffles and a funnel shift.  Two 4-byte loads per lane
+// and frame instead of six byte loads.
+template <int D, int PF, bool CHUNKED>
+__device__ __forceinline__ bool warp_region_pass_b8(const uint8_t *__restrict__ frames, int N, int64_t fstride,
+                                                    const uint8_t *blk, int W, uint32_t *tab, int chunk) {
+  using C = WarpTableCfg<D>;
+  constexpr bool INDEXED = C::DIRECT || CHUNKED;
+  const int lane = threadIdx.x & 31;
+  const int64_t row = (int64_t)W * 3;
+  const uint32_t *wa = reinterpret_cast<const uint32_t *>(blk + (lane / 6) * row + 4 * (lane % 6));
+  const int m2 = 32 + (lane & 15);
+  const uint32_t *wb = reinterpret_cast<const uint32_t *>(blk + (m2 / 6) * row + 4 * (m2 % 6));
+  int src[2][2], sh[2], hi[2][2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int i = lane + 32 * k;
+    const int o = (i >> 3) * 24 + 3 * (i & 7);
+    const int w0 = o >> 2;
+    sh[k] = 8 * (o & 3);
+    src[k][0] = w0 & 31, hi[k][0] = w0 >> 5;
+    src[k][1] = (w0 + 1) & 31, hi[k][1] = (w0 + 1) >> 5;
+  }
+  uint32_t inserted = 0;
+  const int64_t fwords = fstride / 4;
+  for (int f0 = 0; f0 < N; f0 += PF) {
+    uint32_t a[PF], bw[PF];
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+      if (f0 + j < N) {
+        a[j] = __ldg(wa + (int64_t)(f0 + j) * fwords);
+        bw[j] = lane < 16 ? __ldg(wb + (int64_t)(f0 + j) * fwords) : 0u;
+      }
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (f0 + j >= N) break;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const uint32_t l0 = __shfl_sync(0xFFFFFFFFu, a[j], src[k][0]), h0 = __shfl_sync(0xFFFFFFFFu, bw[j], src[k][0]);
+        const uint32_t l1 = __shfl_sync(0xFFFFFFFFu, a[j], src[k][1]), h1 = __shfl_sync(0xFFFFFFFFu, bw[j], src[k][1]);
+        const uint32_t lo = hi[k][0] ? h0 : l0, up = hi[k][1] ? h1 : l1;
+        const uint32_t q = planar_code<D>(__funnelshift_r(lo, up, sh[k]));
+        if (!CHUNKED || (int)(q >> C::LOGS) == chunk)
+          inserted += warp_table_count<D, INDEXED>(tab, q, (uint32_t)(f0 + j));
+      }
+      __syncwarp();
+      if constexpr (!INDEXED)
+        if (__reduce_add_sync(0xFFFFFFFFu, inserted) > (uint32_t)(3 * C::S / 4)) return false;
+    }
+  }
+  return true;
+}
+
 // Warp w of the caller handles regions r = r_first, r_first + r_step, ... < r_end.
 // tab: this warp's S-entry table, zero on entry and on return.
 template <int D, int PPL>
@@ -383,7 +440,19 @@ __device__ __forceinline__ void build_block_warp_body(const uint8_t *__restrict_
     }
     uint32_t *row = model + r * C::WPR;
     warp_zero_row<D>(row);
-    if (warp_region_pass<D, PPL, PF, false>(frames, N, fstride, off, npx, tab, -1)) {
+    // Full 8 x 8 blocks with 4-byte aligned rows take the word-load pass at
+    // depth <= 3 (at depth 4-5 its extra registers cost more occupancy than
+    // the loads save: measured 0.226 / 0.252 ms vs 0.211 / 0.243 ms).
+    bool fits;
+    if constexpr (PPL == 2 && C::DIRECT) {
+      const bool b8 = b == 8 && npx == 64 && (W & 3) == 0 && (reinterpret_cast<uintptr_t>(frames) & 3) == 0;
+      const uint8_t *blk = frames + ((int64_t)y0 * W + x0) * 3;
+      fits = b8 ? warp_region_pass_b8<D, PF, false>(frames, N, fstride, blk, W, tab, -1)
+                : warp_region_pass<D, PPL, PF, false>(frames, N, fstride, off, npx, tab, -1);
+    } else {
+      fits = warp_region_pass<D, PPL, PF, false>(frames, N, fstride, off, npx, tab, -1);
+    }
+    if (fits) {
       warp_emit<D>(tab, row, T);
     } else {
       for (int s = lane; s < C::S; s += 32) tab[s] = 0u;

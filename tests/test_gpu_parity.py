@@ -283,17 +283,17 @@ def test_block_build_warp_tables(ocq, torch, b, d):
     kernel.  Scene content, then uniform noise (far more distinct leaves per
     region than the table holds at depth 4-5, so the chunked fallback runs),
     with ragged blocks at the right and bottom edges."""
-    H, W = 2 * b + 3, 3 * b + 7
-    sc = ocq_synth.make_scene("sway", H, W, 10, 6, seed=500 + 7 * b + d)
-    frames = ocq_synth.fill_host(sc, 0, 16)
-    g = np.random.default_rng(900 + b * 11 + d)
-    noise = g.integers(0, 256, size=(10, H, W, 3), dtype=np.uint8)
-    for train in (frames[:10], noise):
-        for T in (1, 3, 10):
-            words, mask = gpu_model_and_mask(ocq, torch, train, frames[10:], d, T, BLOCK, b)
-            ow, om = oracle.run(train, d, T, BLOCK, b, frames[10:])
-            assert (words == ow).all(), T
-            assert (mask == om).all(), T
+    for H, W in ((2 * b + 3, 3 * b + 7), (2 * b + 3, 4 * b + 4)):  # W % 4 == 0: word loads for full 8x8 blocks
+        sc = ocq_synth.make_scene("sway", H, W, 10, 6, seed=500 + 7 * b + d + W)
+        frames = ocq_synth.fill_host(sc, 0, 16)
+        g = np.random.default_rng(900 + b * 11 + d + W)
+        noise = g.integers(0, 256, size=(10, H, W, 3), dtype=np.uint8)
+        for train in (frames[:10], noise):
+            for T in (1, 3, 10):
+                words, mask = gpu_model_and_mask(ocq, torch, train, frames[10:], d, T, BLOCK, b)
+                ow, om = oracle.run(train, d, T, BLOCK, b, frames[10:])
+                assert (words == ow).all(), (W, T)
+                assert (mask == om).all(), (W, T)
 
 
 @pytest.mark.parametrize("N", [254, 255, 256])
