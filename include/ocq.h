@@ -301,6 +301,20 @@ ocq_status ocq_server_submit(ocq_server *server, int camera, const uint8_t *fram
 ocq_status ocq_server_poll(ocq_server *server, ocq_completion *out, int max, int *n);
 /* Waits for the camera's frames, frees its ring and model, returns its budget. */
 ocq_status ocq_server_release(ocq_server *server, int camera);
+/* Checkpoint of a camera's serving state, enqueued after its submitted work:
+ * the current model in the exported layout (model_words: device, `words` >=
+ * regions * words_per_region u64), the window ring oldest frame first
+ * (ring_out: device, N*H*W*3 bytes) and the number of test frames submitted.
+ * `stream` waits for the copies; read the buffers after it.  No counterpart
+ * in the paper. */
+ocq_status ocq_server_snapshot(ocq_server *server, int camera, uint64_t *model_words, size_t words,
+                               uint8_t *ring_out, int64_t *submitted, void *stream);
+/* Admits a camera from a snapshot (same description, model words, ring and
+ * count): its next frame is test frame `submitted` and its re-merges happen
+ * exactly as if it had not stopped.  Reserves the footprint like admit
+ * (OCQ_EBUSY when it does not fit); the inputs must be complete on the device. */
+ocq_status ocq_server_resume(ocq_server *server, const ocq_camera_desc *desc, const uint64_t *model_words,
+                             const uint8_t *ring, int64_t submitted, int *camera);
 /* The camera's current model (owned by the server; valid until the next re-merge or release). */
 ocq_status ocq_server_camera_model(const ocq_server *server, int camera, const ocq_model **out);
 ocq_status ocq_server_usage(ocq_server *server, size_t *used, size_t *budget, int64_t *completed);

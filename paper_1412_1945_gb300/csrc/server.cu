@@ -294,6 +294,101 @@ ocq_status ocq_server_release(ocq_server *s, int camera) {
   return cuda_status(e, "camera release");
 }
 
+ocq_status ocq_server_snapshot(ocq_server *s, int camera, uint64_t *model_words, size_t words, uint8_t *ring_out,
+                               int64_t *submitted, void *stream) {
+  if (!s || camera < 0 || camera >= s->max_cameras || !s->cams[camera].live || !model_words || !ring_out ||
+      !submitted) {
+    set_error("ocq_server_snapshot: bad camera or buffers");
+    return OCQ_EINVAL;
+  }
+  Camera &c = s->cams[camera];
+  const int64_t t = c.submitted;
+  const size_t fbytes = (size_t)c.d.H * c.d.W * 3;
+  // After t test frames the ring holds global frames t .. t + N - 1 (training
+  // frames are 0 .. N - 1), frame g in slot g mod N: copy them oldest first.
+  ocq_status rc = cuda_status(cudaStreamWaitEvent(c.stream, c.merged, 0), "snapshot wait");
+  if (rc == OCQ_OK) rc = ocq_model_export(c.model, model_words, words, c.stream);
+  for (int i = 0; i < c.d.N && rc == OCQ_OK; ++i)
+    rc = cuda_status(cudaMemcpyAsync(ring_out + (size_t)i * fbytes, c.ring + (size_t)((t + i) % c.d.N) * fbytes,
+                                     fbytes, cudaMemcpyDeviceToDevice, c.stream),
+                     "snapshot ring");
+  cudaEvent_t done = nullptr;
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&done, cudaEventDisableTiming), "event");
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(done, c.stream), "snapshot done");
+  if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent((cudaStream_t)stream, done, 0), "snapshot join");
+  if (done) cudaEventDestroy(done);
+  if (rc == OCQ_OK) *submitted = t;
+  return rc;
+}
+
+ocq_status ocq_server_resume(ocq_server *s, const ocq_camera_desc *d, const uint64_t *model_words,
+                             const uint8_t *ring, int64_t submitted, int *camera) {
+  if (!s || !d || !model_words || !ring || !camera || submitted < 0 || d->N < 1 || d->N > 65535 || d->T < 1 ||
+      d->T > d->N || d->K < 1 || ocq_model_footprint(d->H, d->W, d->region, d->depth) == 0) {
+    set_error("ocq_server_resume: bad camera description or snapshot");
+    return OCQ_EINVAL;
+  }
+  const size_t fp = camera_footprint(*d);
+  int slot = -1;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (int i = 0; i < s->max_cameras; ++i)
+      if (!s->cams[i].live) {
+        slot = i;
+        break;
+      }
+    if (slot < 0 || s->used + fp > s->budget) {
+      set_error("ocq_server_resume: no room (slots or HBM budget) for %zu bytes", fp);
+      return OCQ_EBUSY;
+    }
+    s->used += fp;
+    s->cams[slot].live = true;
+  }
+  PoolScope scope(s->pool);
+  Camera &c = s->cams[slot];
+  c.id = slot;
+  c.d = *d;
+  c.footprint = fp;
+  c.submitted = submitted;
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  ocq_status rc = cuda_status(cudaStreamCreateWithPriority(&c.stream, cudaStreamNonBlocking, hi), "camera stream");
+  if (rc == OCQ_OK) rc = cuda_status(cudaStreamCreateWithPriority(&c.merge, cudaStreamNonBlocking, lo), "merge stream");
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.ring_ready, cudaEventDisableTiming), "event");
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.merged, cudaEventDisableTiming), "event");
+  const size_t fbytes = (size_t)d->H * d->W * 3;
+  if (rc == OCQ_OK) rc = cuda_status(malloc_async((void **)&c.ring, (size_t)d->N * fbytes, c.merge), "camera ring");
+  for (int i = 0; i < d->N && rc == OCQ_OK; ++i)  // snapshot frame i is global frame submitted + i
+    rc = cuda_status(cudaMemcpyAsync(c.ring + (size_t)((submitted + i) % d->N) * fbytes, ring + (size_t)i * fbytes,
+                                     fbytes, cudaMemcpyDeviceToDevice, c.merge),
+                     "ring restore");
+  if (rc == OCQ_OK) {
+    ocq_model_info info;
+    memset(&info, 0, sizeof info);
+    info.H = d->H, info.W = d->W, info.region_kind = d->region.kind, info.block = d->region.block;
+    info.depth = d->depth, info.T = d->T, info.N = d->N;
+    rc = ocq_model_import(model_words, &info, c.merge, &c.model);
+  }
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(c.merged, c.merge), "merged");
+  if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent(c.stream, c.merged, 0), "wait for the model");
+  if (rc != OCQ_OK) {
+    if (c.model) ocq_model_free(c.model);
+    if (c.ring) cudaFreeAsync(c.ring, c.merge);
+    if (c.merge) cudaStreamSynchronize(c.merge), cudaStreamDestroy(c.merge);
+    if (c.stream) cudaStreamSynchronize(c.stream), cudaStreamDestroy(c.stream);
+    if (c.ring_ready) cudaEventDestroy(c.ring_ready);
+    if (c.merged) cudaEventDestroy(c.merged);
+    c.model = nullptr, c.ring = nullptr, c.stream = nullptr, c.merge = nullptr, c.ring_ready = nullptr;
+    c.merged = nullptr;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->used -= fp;
+    c.live = false;
+    return rc;
+  }
+  *camera = slot;
+  return OCQ_OK;
+}
+
 ocq_status ocq_server_camera_model(const ocq_server *s, int camera, const ocq_model **out) {
   if (!s || !out || camera < 0 || camera >= s->max_cameras || !s->cams[camera].live) {
     set_error("ocq_server_camera_model: bad camera");

@@ -90,6 +90,8 @@ SIGNATURES = {
     "ocq_batch_autotune": (_i32, [_vp, _i32, _vp]),
     "ocq_batch_set_mode": (_i32, [_vp, _i32]),
     "ocq_debug_fail_allocations": (None, [_i32]),
+    "ocq_server_snapshot": (_i32, [_vp, _i32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_i64), _vp]),
+    "ocq_server_resume": (_i32, [_vp, ctypes.POINTER(ocq_camera_desc), _vp, _vp, _i64, ctypes.POINTER(_i32)]),
     "ocq_debug_async_bytes_in_use": (_i32, [ctypes.POINTER(ctypes.c_size_t)]),
     "ocq_batch_debug_hold_builds": (_i32, [_vp, _i32]),
     "ocq_build_model_groups": (_i32, [_vp, _i32, _i32, _i32, ocq_region, _i32, _i32, _i32, _vp,
@@ -474,6 +476,27 @@ def ocq_server_poll(server, max_n=4096):
     n = ctypes.c_int()
     _check(load().ocq_server_poll(server.handle, buf, max_n, ctypes.byref(n)))
     return [(c.camera, c.frame, c.tag, c.arrival_s, c.done_s) for c in buf[:n.value]]
+
+
+def ocq_server_snapshot(server, camera, model_words, ring_out, stream=None) -> int:
+    """Enqueues the camera's checkpoint into ``model_words`` (int64/uint64 CUDA
+    tensor) and ``ring_out`` (N*H*W*3 bytes); returns the frames submitted."""
+    n = ctypes.c_int64()
+    _check(load().ocq_server_snapshot(server.handle, camera, _p(model_words), model_words.numel(), _p(ring_out),
+                                      ctypes.byref(n), _s(stream)))
+    return n.value
+
+
+def ocq_server_resume(server, H, W, kind, block, depth, T, N, K, model_words, ring, submitted):
+    """Returns the camera id, or None when the server answers OCQ_EBUSY."""
+    d = _camera(H, W, kind, block, depth, T, N, K)
+    cam = ctypes.c_int()
+    rc = load().ocq_server_resume(server.handle, ctypes.byref(d), _p(model_words), _p(ring), submitted,
+                                  ctypes.byref(cam))
+    if rc == OCQ_EBUSY:
+        return None
+    _check(rc)
+    return cam.value
 
 
 def ocq_server_release(server, camera):

@@ -191,3 +191,47 @@ def test_serving_preset_cameras_full_size_sampled(cuda_ready):
             torch.cuda.empty_cache()
     finally:
         srv.destroy()
+
+
+def test_serving_snapshot_and_resume(cuda_ready):
+    """A camera checkpointed after 13 test frames (mid-window; re-merges after
+    frames 3, 7, 11) and resumed in a fresh server gives, for frames 13-21,
+    the masks of the window semantics, as if it had never stopped."""
+    import torch
+
+    ocq = cuda_ready
+    O = ocq.ocq
+    H, W, kind, block, d, T, N, K, F, cut = 30, 44, BLOCK, 5, 4, 3, 6, 4, 22, 13
+    sc = ocq_synth.make_scene("sway", H, W, N, F, 123)
+    host = ocq_synth.fill_host(sc, 0, N + F)
+    dev = torch.from_numpy(host).cuda()
+    masks = torch.full((F, H, W), 9, dtype=torch.uint8, device="cuda")
+    wpr = max(1, 8 ** d // 64)
+    regions = -(-H // block) * -(-W // block)
+    words = torch.zeros((regions, wpr), dtype=torch.int64, device="cuda")
+    ring = torch.zeros((N, H, W, 3), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    srv = O.ocq_server_create(1 << 28, 2)
+    try:
+        cam = O.ocq_server_admit(srv, H, W, kind, block, d, T, N, K, dev[:N])
+        for t in range(cut):
+            O.ocq_server_submit(srv, cam, dev[N + t], masks[t], tag=t)
+        assert O.ocq_server_snapshot(srv, cam, words, ring) == cut
+        torch.cuda.synchronize()
+        O.ocq_server_release(srv, cam)
+    finally:
+        srv.destroy()
+    srv = O.ocq_server_create(1 << 28, 2)
+    try:
+        cam = O.ocq_server_resume(srv, H, W, kind, block, d, T, N, K, words, ring, cut)
+        assert cam is not None
+        for t in range(cut, F):
+            O.ocq_server_submit(srv, cam, dev[N + t], masks[t], tag=t)
+        O.ocq_server_sync(srv)
+        O.ocq_server_release(srv, cam)
+    finally:
+        srv.destroy()
+    expect = _window_oracle(host, ("sway", H, W, kind, block, d, T, N, K, F))
+    got = masks.cpu().numpy()
+    for t in range(F):
+        assert (got[t] == expect[t]).all(), t
