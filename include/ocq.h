@@ -241,6 +241,12 @@ ocq_status ocq_batch_get_work(const ocq_batch *batch, int region_kind, int *unit
 enum { OCQ_BATCH_PERSISTENT = 0, OCQ_BATCH_GRAPH = 1 };
 ocq_status ocq_batch_set_mode(ocq_batch *batch, int mode);
 int ocq_batch_get_mode(const ocq_batch *batch);
+/* Persistent form: whether per-pixel streams of depth <= 3 classify from rows
+ * staged in shared memory (on) or through L1 (off, the default).  Staging
+ * speeds those streams up but raises every CTA's shared memory; the autotuner
+ * times both.  Results are identical either way. */
+ocq_status ocq_batch_set_staging(ocq_batch *batch, int on);
+int ocq_batch_get_staging(const ocq_batch *batch);
 /* Autotuner: times candidate work sizes per region kind on this batch's own
  * inputs (`reps` runs each, on `stream`) and keeps the fastest (results are
  * cached per (region kind, depths, sizes, frames) signature for the process),

@@ -55,7 +55,7 @@ struct BStream {
   int32_t km;          // pixel build: candidate counters (0: count every distinct leaf)
   int32_t tb;          // pixel / block classify: 1 if the L1 body applies
   int32_t nseg;        // block classify (L1 body): 128-pixel segments per pixel row
-  int32_t pad;
+  int32_t stage;       // pixel classify, depth <= 3: rows staged in shared memory (else L1)
 };
 
 struct BItem {
@@ -158,14 +158,25 @@ __device__ __noinline__ void block_tb_dispatch(const BStream &S, int64_t t0, int
   }
 }
 
-__device__ __noinline__ void pixel_tb_dispatch(const BStream &S, int64_t t0, int64_t t1) {
+// Depth <= 3 with staging on: the warp's rows staged in shared memory (128 x 16
+// words at most); otherwise L1 lookups.
+__device__ __noinline__ void pixel_tb_dispatch(const BStream &S, int64_t t0, int64_t t1, uint8_t *smem) {
+  uint32_t *rows = reinterpret_cast<uint32_t *>(smem) + (threadIdx.x >> 5) * 128 * 16;
   for (int64_t t = t0; t < t1; t += kBatchThreads / 32) {
-    switch (S.depth) {
-      case 1: classify_pixel_tb_body<1, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
-      case 2: classify_pixel_tb_body<2, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
-      case 3: classify_pixel_tb_body<3, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
-      case 4: classify_pixel_tb_body<4, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
-      default: classify_pixel_tb_body<5, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+    if (S.stage) {
+      switch (S.depth) {
+        case 1: classify_pixel_tbs_body<1, 8>(S.test, S.F, S.hw, S.model, S.mask, t, rows); break;
+        case 2: classify_pixel_tbs_body<2, 8>(S.test, S.F, S.hw, S.model, S.mask, t, rows); break;
+        default: classify_pixel_tbs_body<3, 8>(S.test, S.F, S.hw, S.model, S.mask, t, rows); break;
+      }
+    } else {
+      switch (S.depth) {
+        case 1: classify_pixel_tb_body<1, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+        case 2: classify_pixel_tb_body<2, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+        case 3: classify_pixel_tb_body<3, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+        case 4: classify_pixel_tb_body<4, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+        default: classify_pixel_tb_body<5, 8>(S.test, S.F, S.hw, S.model, S.mask, t); break;
+      }
     }
   }
 }
@@ -203,7 +214,7 @@ __device__ void run_item(const BStream &S, const BItem &it, uint8_t *smem) {
       pixel_mg_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux, smem);
       return;
     case OP_CLS_PIXEL_TB:
-      pixel_tb_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux);
+      pixel_tb_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux, smem);
       return;
     case OP_CLS_BLOCK_TB:
       block_tb_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux);
@@ -272,6 +283,8 @@ static size_t item_smem(const BStream &h) {
       need = std::max<size_t>(need, (size_t)h.wpr * (h.P + 2) * 4);
   } else {
     need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * h.N * 32 * 2);  // candidate build: leaves
+    if (h.stage)
+      need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * 128 * 16 * 4);  // staged rows, 16-word stride
   }
   return need;
 }
@@ -301,6 +314,7 @@ struct ocq_batch {
   cudaGraphExec_t exec = nullptr;
   int device = 0;
   int mode = OCQ_BATCH_PERSISTENT;
+  bool stage = false;  // depth <= 3 per-pixel classify rows staged in shared memory
   int hold = -1;  // test hook: stream whose build items are left out of the work list
   std::vector<cudaStream_t> side;  // branch streams of the graph form
   std::vector<cudaEvent_t> joins;
@@ -308,6 +322,30 @@ struct ocq_batch {
 };
 
 static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Shared memory per CTA for the current streams and staging choice, the
+// kernel's attribute and the persistent grid (CTAs resident at once).
+static ocq_status size_kernel(ocq_batch *b) {
+  size_t smem = 16 * 1024;
+  for (BStream &h : b->hs) {
+    h.stage = b->stage && h.kind == OCQ_REGION_PIXEL && h.depth <= 3 && h.tb;
+    smem = std::max(smem, item_smem(h));
+  }
+  smem = (smem + 127) & ~(size_t)127;
+  if (smem > 227 * 1024) {
+    set_error("ocq_batch: the streams need %zu bytes of shared memory per CTA", smem);
+    return OCQ_ENOTSUP;
+  }
+  b->smem = smem;
+  ocq_status rc = cuda_status(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)b->smem),
+                              "batch_kernel smem");
+  if (rc != OCQ_OK) return rc;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, b->smem);
+  b->grid = sm_count() * std::max(1, per_sm);
+  return OCQ_OK;
+}
 
 // Work list: the virtual CTAs of every stream's plain kernels.  Whole-frame
 // occupancy first, then the merges, then block and pixel builds (larger
@@ -594,15 +632,8 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     m->device = b->device;
     b->models.push_back(m);
   }
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
-  if (e != cudaSuccess) {
-    ocq_batch_destroy(b);
-    return cuda_status(e, "batch_kernel smem");
-  }
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel, kBatchThreads, b->smem);
-  b->grid = sm_count() * std::max(1, per_sm);
-  rc = plan_items(b);
+  rc = size_kernel(b);
+  if (rc == OCQ_OK) rc = plan_items(b);
   if (rc == OCQ_OK) rc = upload_plan(b, st);
   if (rc != OCQ_OK) {
     ocq_batch_destroy(b);
@@ -698,6 +729,31 @@ ocq_status ocq_batch_autotune(ocq_batch *b, int reps, void *stream) {
   }
   if (rc == OCQ_OK) rc = plan_items(b);
   if (rc == OCQ_OK) rc = upload_plan(b, st);
+  // Staging of depth <= 3 per-pixel rows in shared memory: it speeds those
+  // streams up but raises every CTA's shared memory (less L1 for the others),
+  // so it is timed both ways on this batch.
+  bool stageable = false;
+  for (const BStream &h : b->hs) stageable |= h.kind == OCQ_REGION_PIXEL && h.depth <= 3 && h.tb;
+  if (stageable && rc == OCQ_OK) {
+    float ts[2] = {1e30f, 1e30f};
+    for (int stg = 0; stg < 2 && rc == OCQ_OK; ++stg) {
+      b->stage = stg == 1;
+      rc = size_kernel(b);
+      if (rc == OCQ_OK) rc = plan_items(b);
+      if (rc == OCQ_OK) rc = upload_plan(b, st);
+      if (rc != OCQ_OK) break;
+      rc = enqueue_run(b, st);  // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && rc == OCQ_OK; ++r) rc = enqueue_run(b, st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ts[stg], e0, e1);
+    }
+    b->stage = ts[1] < ts[0];
+    if (rc == OCQ_OK) rc = size_kernel(b);
+    if (rc == OCQ_OK) rc = plan_items(b);
+    if (rc == OCQ_OK) rc = upload_plan(b, st);
+  }
   // Then the form: the persistent kernel with the chosen work sizes against
   // the graph of per-stream branches, each captured and replayed.
   float t[2] = {1e30f, 1e30f};
@@ -779,6 +835,21 @@ ocq_status ocq_batch_set_mode(ocq_batch *b, int mode) {
 }
 
 int ocq_batch_get_mode(const ocq_batch *b) { return b ? b->mode : -1; }
+
+ocq_status ocq_batch_set_staging(ocq_batch *b, int on) {
+  if (!b) {
+    set_error("ocq_batch_set_staging: NULL batch");
+    return OCQ_EINVAL;
+  }
+  b->stage = on != 0;
+  ocq_status rc = size_kernel(b);
+  if (rc == OCQ_OK) rc = plan_items(b);
+  if (rc == OCQ_OK) rc = upload_plan(b, b->owner);
+  free_graph(b);
+  return rc;
+}
+
+int ocq_batch_get_staging(const ocq_batch *b) { return b ? (int)b->stage : -1; }
 
 ocq_status ocq_batch_debug_hold_builds(ocq_batch *b, int stream) {
   if (!b || stream < -1 || stream >= (int)b->hs.size()) {

@@ -193,6 +193,56 @@ __device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict
   }
 }
 
+// Pixel regions, depth <= 3: as classify_pixel_tb_body, with the warp's 128
+// rows (WPR <= 16 words each) staged in shared memory first, interleaved so
+// that word w of the lane's k-th pixel sits at [(w * 4 + k) * 32 + lane]: every
+// lookup of a warp instruction hits 32 different banks.  rows: this warp's
+// 128 * WPR words.
+template <int D, int PF>
+__device__ __forceinline__ void classify_pixel_tbs_body(const uint8_t *__restrict__ frames, int F, int64_t hw,
+                                                        const uint32_t *model, uint8_t *__restrict__ mask,
+                                                        int64_t tile, uint32_t *rows) {
+  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  static_assert(D <= 3, "rows of at most 16 words");
+  const int lane = threadIdx.x & 31;
+  const int64_t p0 = tile * 128;
+  const int64_t np = hw - p0 < 128 ? hw - p0 : 128;
+  __syncwarp();
+  for (int e = lane; e < np * WPR; e += 32) {  // coalesced: element e = pixel e / WPR, word e % WPR
+    const int pl = e / WPR, w = e % WPR;
+    rows[(w * 4 + (pl & 3)) * 32 + (pl >> 2)] = model[p0 * WPR + e];
+  }
+  __syncwarp();
+  const int64_t pq = p0 + 4 * lane;
+  if (pq >= hw) return;
+  const uint8_t *src = frames + pq * 3;
+  uint8_t *dst = mask + pq;
+  for (int f0 = 0; f0 < F; f0 += PF) {
+    uint32_t w[PF][3];
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+      if (f0 + j < F) {
+        const uint8_t *sp = src + (int64_t)(f0 + j) * hw * 3;
+        w[j][0] = ld_stream4(sp), w[j][1] = ld_stream4(sp + 4), w[j][2] = ld_stream4(sp + 8);
+      }
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (f0 + j >= F) break;
+      uint32_t m[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) m[i] = (w[j][i] >> (8 - D)) & byte_mask(D);
+      uint32_t bg[4];
+      static_for<0, 4>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const uint32_t q = planar_from_masked<D>(quad_pixel<k>(m));
+        const uint32_t v = rows[((q >> 5) * 4 + k) * 32 + lane];
+        bg[k] = __funnelshift_r(v, v, q);
+      });
+      st_stream4(dst + (int64_t)(f0 + j) * hw, pack_mask4(bg[0], bg[1], bg[2], bg[3]));
+    }
+  }
+}
+
 // One pixel location per lane (a warp owns 32): a smaller model working set
 // per warp than the 4-per-lane form, so more warps fit their lines in L1.
 __device__ __forceinline__ uint32_t ld_stream1(const uint8_t *p) {

@@ -89,6 +89,8 @@ SIGNATURES = {
     "ocq_batch_get_work": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "ocq_batch_autotune": (_i32, [_vp, _i32, _vp]),
     "ocq_batch_set_mode": (_i32, [_vp, _i32]),
+    "ocq_batch_set_staging": (_i32, [_vp, _i32]),
+    "ocq_batch_get_staging": (_i32, [_vp]),
     "ocq_debug_fail_allocations": (None, [_i32]),
     "ocq_server_snapshot": (_i32, [_vp, _i32, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(_i64), _vp]),
     "ocq_server_resume": (_i32, [_vp, ctypes.POINTER(ocq_camera_desc), _vp, _vp, _i64, ctypes.POINTER(_i32)]),
@@ -405,6 +407,14 @@ def ocq_debug_async_bytes_in_use() -> int:
 
 def ocq_batch_debug_hold_builds(batch, stream):
     _check(load().ocq_batch_debug_hold_builds(batch.handle, stream))
+
+
+def ocq_batch_set_staging(batch, on):
+    _check(load().ocq_batch_set_staging(batch.handle, 1 if on else 0))
+
+
+def ocq_batch_get_staging(batch) -> int:
+    return int(load().ocq_batch_get_staging(batch.handle))
 
 
 def ocq_batch_set_mode(batch, mode):

@@ -55,17 +55,19 @@ def _plain(ocq, s):
     return words, mask
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_batch_small_mix_matches_plain_and_oracle(ocq, mode):
-    """Both forms: the persistent work-list kernel (0) and the graph of
-    per-stream branches (1)."""
+@pytest.mark.parametrize("mode,staging", [(0, 0), (0, 1), (1, 0)])
+def test_batch_small_mix_matches_plain_and_oracle(ocq, mode, staging):
+    """Both forms: the persistent work-list kernel (0; per-pixel depth <= 3
+    rows through L1 or staged in shared memory) and the graph of per-stream
+    branches (1)."""
     import torch
 
     S = _streams_host(SMALL_MIX, torch)
     b = ocq.ocq.ocq_batch_create(S)
     try:
         ocq.ocq.ocq_batch_set_mode(b, mode)
-        assert ocq.ocq.ocq_batch_get_mode(b) == mode
+        ocq.ocq.ocq_batch_set_staging(b, staging)
+        assert ocq.ocq.ocq_batch_get_mode(b) == mode and ocq.ocq.ocq_batch_get_staging(b) == staging
         for rep in range(2):  # first run captures the graph, second replays it
             for s in S:
                 s["mask"].fill_(7)
