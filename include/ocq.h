@@ -151,7 +151,9 @@ ocq_status ocq_device_status(void *stream);
  * overlapped on three streams, and writes the F*H*W mask bytes to `mask`.
  * train: host, N*H*W*3 bytes; test: host, F*H*W*3; mask: host, F*H*W.
  * Page-locked host buffers give full copy bandwidth; pageable ones work too.
- * Synchronous: returns after every mask byte is in host memory.  If
+ * Synchronous: returns after every mask byte is in host memory.  Its device
+ * staging buffers come from a pool of its own that stays mapped between calls
+ * (about 1 GB for 1080p frames).  If
  * out_model is not NULL it receives the model (caller frees), else the model
  * is freed.
  */

@@ -3,6 +3,8 @@
 // (copy in / classify / copy masks out overlap on three streams), and copies
 // the masks back.  All compute runs in the library's kernels.
 #include <algorithm>
+#include <cstring>
+#include <mutex>
 
 #include "ocq_internal.cuh"
 
@@ -18,6 +20,29 @@ struct Chunks {
 
 using namespace ocq;
 
+// Staging buffers (training frames, chunk ring) come from a pool of this
+// pipeline that keeps freed memory mapped, so repeated calls do not map and
+// unmap a gigabyte each time; one pool per device, created on first use.
+static cudaMemPool_t pipeline_pool(int dev) {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  if (dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
+
 extern "C" ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t *test, int F, int H, int W,
                                       ocq_region region, int depth, int T, uint8_t *mask, void *stream,
                                       ocq_model **out_model) {
@@ -27,6 +52,9 @@ extern "C" ocq_status ocq_detect_host(const uint8_t *train, int N, const uint8_t
     return OCQ_EINVAL;
   }
   cudaStream_t s0 = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  PoolScope scope(pipeline_pool(dev));
   const size_t hw = (size_t)H * (size_t)W;
   uint8_t *train_d = nullptr;
   ocq_status rc = cuda_status(malloc_async((void **)&train_d, (size_t)N * hw * 3, s0), "training frames");
