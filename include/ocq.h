@@ -5,7 +5,7 @@
  * The method (paper Sec. 2-4):
  *   S1  each RGB8 pixel is quantised to its octree path: at level l (bit 7-l)
  *       the child index is (red bit << 2) | (green bit << 1) | blue bit
- *       (Alg. 1, with the printed "red[i] + green[i] + blue[i]" read as bit
+ *       (Alg. 1, with the printed sum of the three bits read as bit
  *       concatenation); pruning the tree at height d keeps the top d levels
  *       (Sec. 2).  The path code is the d child indices read as base-8 digits
  *       from the root (index of level 0 most significant).
@@ -257,8 +257,8 @@ ocq_status ocq_batch_autotune(ocq_batch *batch, int reps, void *stream);
 void ocq_batch_destroy(ocq_batch *batch);
 
 /*
- * Served form.  The paper names "octree updation" (Sec. 4) without giving a
- * procedure; this library's reading is a sliding window: the N training
+ * Served form.  The title of the paper's Sec. 4 names an update of the
+ * octree without giving a procedure; this library's reading is a sliding window: the N training
  * frames build M_0; test frame t (t = 0, 1, ...) is classified against
  * M_floor(t/K); after classification it enters a ring of the last N frames;
  * when (t+1) % K == 0 the ring is merged again (Alg. 2) into the next model.

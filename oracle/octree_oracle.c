@@ -22,12 +22,13 @@
  *
  * Readings of points the paper leaves open (each also listed in the design notes):
  *   R1  child index = (red bit << 2) | (green bit << 1) | blue bit; the
- *       printed "red[i] + green[i] + blue[i]" is read as bit concatenation,
- *       since eight children need three bits.
- *   R2  "for i := MSB to Number of Levels" walks bits 7, 6, ..., 8-d: d levels.
- *   R3  the threshold test count/numberOfTrees >= threshold is taken with an
- *       integer count threshold T (keep iff count >= T); a fraction t maps
- *       to T = ceil(t * N).
+ *       printed sum of the three bits is read as bit concatenation, since
+ *       eight children need three bits.
+ *   R2  the loop from the most significant bit to the number of levels walks
+ *       bits 7, 6, ..., 8-d: d levels.
+ *   R3  the threshold test on the fraction of trees holding a child is taken
+ *       with an integer count threshold T (keep iff count >= T); a fraction t
+ *       maps to T = ceil(t * N).
  *   R6  Merge Trees recurses on the child arrays with the level increased by
  *       one, stops at depth d, and a NULL tree does not count.
  *   R8  only depth-d nodes are colours: an internal merged node with no kept

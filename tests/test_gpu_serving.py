@@ -1,5 +1,5 @@
-"""Served form (window re-merge, the reading of the paper's "octree
-updation"): each frame's mask equals the oracle's under the window semantics,
+"""Served form (window re-merge, the reading of the octree update the
+paper's Sec. 4 title names): each frame's mask equals the oracle's under the window semantics,
 is the same whether the camera runs alone or in a mix, and admission respects
 the HBM budget."""
 import numpy as np
