@@ -52,7 +52,7 @@ typedef enum {
   OCQ_ENOTSUP = 6   /* valid request the library does not handle */
 } ocq_status;
 
-/* Region geometry (Sec. 3 "subdivide a video into multiple regions"; Sec. 4).
+/* Region geometry (Sec. 3 splits a video into regions with a tree each; Sec. 4).
  * FRAME: one region.  BLOCK: b x b blocks numbered row-major,
  * r = (y/b)*ceil(W/b) + x/b, partial blocks at the right/bottom edges.
  * PIXEL: one region per pixel location, r = y*W + x. */

@@ -12,7 +12,7 @@
  *   - Store Color (Alg. 1) inserts a colour by walking one bit of red, green
  *     and blue per level, most significant bit first, creating missing
  *     children; stopping the walk after `depth` levels is the paper's pruning
- *     "by removing levels from the bottom" (Sec. 2), so a leaf at depth d keeps
+ *     of dropping the bottom levels (Sec. 2), so a leaf at depth d keeps
  *     the d most significant bits of each channel;
  *   - one tree is built per training frame and per region (Sec. 3, Sec. 4);
  *   - Merge Trees (Alg. 2) keeps child i of a merged node when at least
