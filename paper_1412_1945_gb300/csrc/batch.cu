@@ -87,7 +87,7 @@ __device__ __forceinline__ bool wait_count(const uint32_t *ctr, uint32_t want, u
 // that their unrolled register arrays do not share one frame with every other
 // inlined body.
 template <int D, int PPL>
-__device__ __forceinline__ void block_warp_item(const BStream &S, int64_t r0, int64_t r1, uint32_t *tab) {
+__device__ __noinline__ void block_warp_item(const BStream &S, int64_t r0, int64_t r1, uint32_t *tab) {
   build_block_warp_body<D, PPL>(S.train, S.N, S.H, S.W, S.block, S.bw, (uint32_t)S.T, S.model, r0, r1,
                                 kBatchThreads / 32, tab);
 }
