@@ -39,6 +39,13 @@
  *       single pixels (kind 2) are numbered y*W + x.
  *   R12 the mask is u8 with 1 = foreground, 0 = background.
  *
+ * Pins (tests/test_oracle_pins.py, tests/test_oracle_next.py): every function
+ * here is checked against closed forms, invariants, hand-derived cases or the
+ * set-based restatement.  Parity unpinned (conventions the paper does not fix,
+ * so nothing it prints can confirm them): the bit order R1 inside exported
+ * path codes (classification does not depend on it), the fraction-to-T
+ * rounding R3, and the serving window semantics built on these functions.
+ *
  * A leaf's identity ("path code") is the sequence of child indices from the
  * root: code = sum over levels l of index_l * 8^(d-1-l).  The merged model of a
  * region is exported as a bitset of 8^d bits in u64 words, leaf c at bit c%64
