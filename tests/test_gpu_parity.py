@@ -402,3 +402,33 @@ def test_detect_from_host_memory(ocq, torch, H, W, N, F):
     if H * W < 10000:
         _, om = oracle.run(h_train.numpy(), 3, 3, PIXEL, 0, h_test.numpy())
         assert (h_mask.numpy() == om).all()
+
+
+def test_degenerate_inputs(ocq, torch):
+    """No test frames (nothing written), a single pixel, a single training
+    frame with T = 1, and a batch stream with no test frames."""
+    O = ocq.ocq
+    one = to_dev(np.array([[[[10, 20, 30]]]], np.uint8), torch)
+    m = ocq.build_model(one, 8, 1, "pixel")
+    empty = torch.empty((0, 1, 1, 3), dtype=torch.uint8, device="cuda")
+    mask = torch.full((0, 1, 1), 7, dtype=torch.uint8, device="cuda")
+    O.ocq_classify(m, empty, 0, mask)
+    got = ocq.classify(m, to_dev(np.array([[[[10, 20, 30]]], [[[10, 20, 31]]]], np.uint8), torch)).cpu().numpy()
+    m.free()
+    assert got.ravel().tolist() == [0, 1]
+    g = np.random.default_rng(2)
+    train = g.integers(0, 256, size=(1, 9, 13, 3), dtype=np.uint8)
+    for kind, block in ((FRAME, 0), (BLOCK, 4), (PIXEL, 0)):
+        words, mask = gpu_model_and_mask(ocq, torch, train, train, 5, 1, kind, block)
+        ow, om = oracle.run(train, 5, 1, kind, block, train)
+        assert (words == ow).all() and not mask.any()
+    tr = to_dev(train, torch)
+    desc = [dict(train=tr, test=None, mask=None, N=1, H=9, W=13, kind=BLOCK, block=4, depth=3, T=1, F=0)]
+    b = O.ocq_batch_create(desc)
+    try:
+        O.ocq_batch_run(b)
+        O.ocq_batch_status(b)
+        assert (ocq.export_model(b.model(0)).cpu().numpy().view(np.uint64) ==
+                oracle.build_model(train, 3, 1, BLOCK, 4)).all()
+    finally:
+        b.destroy()
