@@ -74,12 +74,13 @@ __global__ void __launch_bounds__(256) build_block_warp_kernel(const uint8_t *__
                                 (threadIdx.x >> 5), R, nw, tab);
 }
 
-template <int D, int KM>
+template <int D, int KM, bool GRP>
 __global__ void __launch_bounds__(128) build_pixel_mg_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
-                                                             uint32_t T, uint32_t *__restrict__ model) {
+                                                             uint32_t T, uint32_t *__restrict__ model, int group) {
   extern __shared__ __align__(16) uint8_t mg_smem[];
   leaf_t<D> *codes = reinterpret_cast<leaf_t<D> *>(mg_smem) + (size_t)(threadIdx.x >> 5) * N * 32;
-  build_pixel_mg_body<D, KM>(frames, N, hw, T, model, (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5), codes);
+  build_pixel_mg_body<D, KM, GRP>(frames, N, hw, T, model, (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5), codes,
+                                  group);
 }
 
 template <int D, bool WIDE>
@@ -513,31 +514,38 @@ static ocq_status launch_block(const uint8_t *frames, int N, ocq_model *m, cudaS
   return cuda_status(cudaGetLastError(), "build_block_kernel");
 }
 
-template <int D, int KM>
-static ocq_status launch_pixel_mg_km(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+template <int D, int KM, bool GRP>
+static ocq_status launch_pixel_mg_km(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st, int group) {
   const size_t smem = (size_t)4 * N * 32 * sizeof(leaf_t<D>);
-  auto kern = build_pixel_mg_kernel<D, KM>;
+  auto kern = build_pixel_mg_kernel<D, KM, GRP>;
   if (smem > 48 * 1024) {
     ocq_status rc = cuda_status(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                                 "build_pixel_mg_kernel smem");
     if (rc != OCQ_OK) return rc;
   }
   const int64_t hw = (int64_t)m->H * m->W;
-  kern<<<(unsigned)((hw + 127) / 128), 128, smem, st>>>(frames, N, hw, (uint32_t)m->T, m->bits);
+  kern<<<(unsigned)((hw + 127) / 128), 128, smem, st>>>(frames, N, hw, (uint32_t)m->T, m->bits, group);
   count_launch();
   return cuda_status(cudaGetLastError(), "build_pixel_mg_kernel");
 }
 
 // Candidate counters: the smallest of 1, 2, 4, 8 that is >= floor(N / T);
-// beyond 8, every distinct leaf is counted (KM = 0).
-template <int D>
-static ocq_status launch_pixel_mg(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+// beyond 8, every distinct leaf is counted (KM = 0).  group > 1: one tree per
+// group of frames (T counts groups; the same bound holds).
+template <int D, bool GRP>
+static ocq_status launch_pixel_mg_g(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st, int group) {
   const int k = N / m->T;
-  if (k <= 1) return launch_pixel_mg_km<D, 1>(frames, N, m, st);
-  if (k <= 2) return launch_pixel_mg_km<D, 2>(frames, N, m, st);
-  if (k <= 4) return launch_pixel_mg_km<D, 4>(frames, N, m, st);
-  if (k <= 8) return launch_pixel_mg_km<D, 8>(frames, N, m, st);
-  return launch_pixel_mg_km<D, 0>(frames, N, m, st);
+  if (k <= 1) return launch_pixel_mg_km<D, 1, GRP>(frames, N, m, st, group);
+  if (k <= 2) return launch_pixel_mg_km<D, 2, GRP>(frames, N, m, st, group);
+  if (k <= 4) return launch_pixel_mg_km<D, 4, GRP>(frames, N, m, st, group);
+  if (k <= 8) return launch_pixel_mg_km<D, 8, GRP>(frames, N, m, st, group);
+  return launch_pixel_mg_km<D, 0, GRP>(frames, N, m, st, group);
+}
+
+template <int D>
+static ocq_status launch_pixel_mg(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st, int group = 1) {
+  return group > 1 ? launch_pixel_mg_g<D, true>(frames, N, m, st, group)
+                   : launch_pixel_mg_g<D, false>(frames, N, m, st, 1);
 }
 
 // One warp per block region (b <= 16, N <= 255, frame offsets within 32 bits).
@@ -845,6 +853,18 @@ bool build_take_timeout() {
 
 ocq_status launch_build_groups(const uint8_t *frames, int N, int group, ocq_model *m, cudaStream_t st) {
   if (group == 1) return launch_build(frames, N, m, st);
+  if (m->kind == OCQ_REGION_PIXEL && N <= 255) {  // per pixel location: candidates over group-distinct leaves
+    switch (m->depth) {
+      case 1: return launch_pixel_mg<1>(frames, N, m, st, group);
+      case 2: return launch_pixel_mg<2>(frames, N, m, st, group);
+      case 3: return launch_pixel_mg<3>(frames, N, m, st, group);
+      case 4: return launch_pixel_mg<4>(frames, N, m, st, group);
+      case 5: return launch_pixel_mg<5>(frames, N, m, st, group);
+      case 6: return launch_pixel_mg<6>(frames, N, m, st, group);
+      case 7: return launch_pixel_mg<7>(frames, N, m, st, group);
+      default: return launch_pixel_mg<8>(frames, N, m, st, group);
+    }
+  }
   return build_dense(frames, N, m, st, group);
 }
 

@@ -592,16 +592,22 @@ __device__ __forceinline__ void build_pixel_chunked_body(const uint8_t *__restri
 // seen more than N / (KM + 1) < T times keeps a non-zero counter, so every leaf
 // to be kept is among the KM candidates) and stores the leaves in shared
 // memory; pass 2 counts each candidate exactly.  KM = 0 (large k): pass 2
-// instead counts every distinct leaf at its first occurrence.  The warp then
+// instead counts every distinct leaf at its first occurrence.  With one tree
+// per group of frames the same bound holds for the stream of leaves taken once
+// per group, which is what the summary then sees.  The warp then
 // writes its 32 pixels' rows, which are contiguous: zeros with vector stores,
 // then the kept words.  Lane = pixel; the frames are read once and the model
 // written once, whatever the depth.
 template <int D>
 using leaf_t = typename std::conditional<(D <= 5), uint16_t, uint32_t>::type;
 
-template <int D, int KM>
+template <int D, int KM, bool GRP = false>
 __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ frames, int N, int64_t hw, uint32_t T,
-                                                    uint32_t *__restrict__ model, int64_t tile, leaf_t<D> *codes) {
+                                                    uint32_t *__restrict__ model, int64_t tile, leaf_t<D> *codes,
+                                                    int group = 1) {
+  // GRP: one tree per group of `group` consecutive frames (Sec. 3): a leaf
+  // enters the summary once per group that holds it, and the exact pass counts
+  // the groups holding each candidate (T counts groups).
   constexpr int64_t WPR = D == 1 ? 1 : (int64_t)1 << (3 * D - 5);
   constexpr int PF = 8;
   const int lane = threadIdx.x & 31;
@@ -623,21 +629,27 @@ __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ 
 #pragma unroll
     for (int j = 0; j < PF; ++j) {
       if (!valid || f0 + j >= N) break;
+      const int f = f0 + j;
       const uint32_t q = planar_code<D>(yv[j]);
-      codes[(f0 + j) * 32 + lane] = (leaf_t<D>)q;
+      codes[f * 32 + lane] = (leaf_t<D>)q;
       if constexpr (KM > 0) {
-        bool hit = false;
-#pragma unroll
-        for (int i = 0; i < KM; ++i)
-          if (cnt[i] && key[i] == q) ++cnt[i], hit = true;
-        if (!hit) {
-          bool placed = false;
+        bool seen = false;
+        if constexpr (GRP)
+          for (int e = f - f % group; e < f && !seen; ++e) seen = codes[e * 32 + lane] == q;
+        if (!seen) {
+          bool hit = false;
 #pragma unroll
           for (int i = 0; i < KM; ++i)
-            if (!placed && !cnt[i]) key[i] = q, cnt[i] = 1u, placed = true;
-          if (!placed) {
+            if (cnt[i] && key[i] == q) ++cnt[i], hit = true;
+          if (!hit) {
+            bool placed = false;
 #pragma unroll
-            for (int i = 0; i < KM; ++i) --cnt[i];
+            for (int i = 0; i < KM; ++i)
+              if (!placed && !cnt[i]) key[i] = q, cnt[i] = 1u, placed = true;
+            if (!placed) {
+#pragma unroll
+              for (int i = 0; i < KM; ++i) --cnt[i];
+            }
           }
         }
       }
@@ -645,13 +657,16 @@ __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ 
   }
   uint32_t exact[KM > 0 ? KM : 1];
   if constexpr (KM > 0) {
+    int last[KM];
 #pragma unroll
-    for (int i = 0; i < KM; ++i) exact[i] = 0u;
+    for (int i = 0; i < KM; ++i) exact[i] = 0u, last[i] = -1;
     if (valid)
       for (int f = 0; f < N; ++f) {
         const uint32_t q = codes[f * 32 + lane];
+        const int g = GRP ? f / group : f;
 #pragma unroll
-        for (int i = 0; i < KM; ++i) exact[i] += (cnt[i] && key[i] == q) ? 1u : 0u;
+        for (int i = 0; i < KM; ++i)
+          if (cnt[i] && key[i] == q && last[i] != g) ++exact[i], last[i] = g;
       }
   }
   const int64_t np = hw - p0 < 32 ? hw - p0 : 32;
@@ -681,12 +696,18 @@ __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ 
       bool first = true;
       for (int g = 0; g < f && first; ++g) first = codes[g * 32 + lane] != q;
       if (!first) continue;
-      uint32_t c = 1u;
-      for (int g = f + 1; g < N; ++g) c += codes[g * 32 + lane] == q ? 1u : 0u;
+      uint32_t c = 0u;
+      int last = -1;
+      for (int g = f; g < N; ++g)
+        if (codes[g * 32 + lane] == q) {
+          const int grp = GRP ? g / group : g;
+          if (grp != last) ++c, last = grp;
+        }
       if (c >= T) atomicOr(&row[q >> 5], 1u << (q & 31));
     }
   }
 }
+
 
 // Warp-specialised form of build_pixel_red_kernel: NT counting threads plus
 // one copy warp.  The copy warp refills stage s as soon as every counting

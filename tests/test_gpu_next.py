@@ -78,7 +78,7 @@ def test_confusion_of_classified_scene(ocq, torch):
 
 
 CASES = [(FRAME, 0, d) for d in (1, 3, 5, 7)] + [(BLOCK, b, d) for b, d in ((4, 2), (5, 4), (8, 5))] + \
-        [(PIXEL, 0, d) for d in (2, 3, 5)]
+        [(PIXEL, 0, d) for d in (2, 3, 5, 7)]
 
 
 @pytest.mark.parametrize("kind,block,d", CASES)
