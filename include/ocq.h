@@ -90,7 +90,10 @@ const char *ocq_version(void);
 /* Number of regions of an H x W frame for `region`, or -1 if invalid. */
 int64_t ocq_region_count(int H, int W, ocq_region region);
 
-/* Device bytes an ocq_model of this geometry occupies (0 if invalid). */
+/* Device bytes an ocq_model of this geometry occupies at most (0 if invalid):
+ * its leaf bitsets, plus for per-pixel regions of depth 4-5 a kept-leaf index
+ * of 16 B per location (built with the model when no location can keep more
+ * than 8 leaves, floor(N / T) <= 8; the classify then compares with it). */
 size_t ocq_model_footprint(int H, int W, ocq_region region, int depth);
 
 /*
@@ -356,12 +359,27 @@ void ocq_server_destroy(ocq_server *server);
  *                             (b % 8 == 0, W % 16 == 0, depth <= 5), 1 L1-cached
  *                             lookups by warps walking all frames at depth >= 4,
  *                             2 the same at depth >= 3, 0, 0, 0}
+ *   OCQ_TUNE_CLASSIFY_PIXEL_LIST per-pixel classify at depth 4-5 for models built
+ *                            by the candidate build, which also keeps each location's
+ *                            kept leaves as a list (16 B per location); variant 0
+ *                            looks up the row, 1 compares with the list (one warp
+ *                            per 128 locations walking all frames), 2 and up compare
+ *                            with the list in the warp-specialised bulk-copy form
+ *                            (frames and mask 16-byte aligned, H*W % 16 == 0; else
+ *                            variant 1 runs); params = {warps, locations per thread,
+ *                            stages, frames per stage, 0} (zeros for 0 and 1)
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5
  * int32 parameters (n >= 5).
  */
-enum { OCQ_TUNE_CLASSIFY_PIXEL = 0, OCQ_TUNE_BUILD_PIXEL = 1, OCQ_TUNE_CLASSIFY_PIXEL_DEEP = 2, OCQ_TUNE_CLASSIFY_BLOCK_DEEP = 3 };
+enum {
+  OCQ_TUNE_CLASSIFY_PIXEL = 0,
+  OCQ_TUNE_BUILD_PIXEL = 1,
+  OCQ_TUNE_CLASSIFY_PIXEL_DEEP = 2,
+  OCQ_TUNE_CLASSIFY_BLOCK_DEEP = 3,
+  OCQ_TUNE_CLASSIFY_PIXEL_LIST = 4
+};
 int ocq_tune_count(int kernel);
 int ocq_tune_selected(int kernel);
 ocq_status ocq_tune_select(int kernel, int variant);

@@ -132,7 +132,9 @@ int64_t ocq_region_count(int H, int W, ocq_region region) { return region_count(
 
 size_t ocq_model_footprint(int H, int W, ocq_region region, int depth) {
   if (check_geometry(H, W, region, depth) != OCQ_OK) return 0;
-  return (size_t)region_count(H, W, region.kind, region.block) * (size_t)wpr32(depth) * sizeof(uint32_t);
+  const size_t bits = (size_t)region_count(H, W, region.kind, region.block) * (size_t)wpr32(depth) * sizeof(uint32_t);
+  const bool indexed = region.kind == OCQ_REGION_PIXEL && (depth == 4 || depth == 5);
+  return bits + (indexed ? (size_t)H * W * 8 * sizeof(uint16_t) : 0);
 }
 
 ocq_status ocq_path_code(const uint8_t *rgb, int64_t npix, int depth, uint32_t *codes, void *stream) {
@@ -271,6 +273,7 @@ ocq_status ocq_model_import(const uint64_t *src, const ocq_model_info *info, voi
 void ocq_model_free(ocq_model *m) {
   if (!m) return;
   if (m->bits) cudaFreeAsync(m->bits, m->stream);
+  if (m->kept) cudaFreeAsync(m->kept, m->stream);
   delete m;
 }
 
@@ -294,6 +297,7 @@ int ocq_tune_count(int kernel) {
   if (kernel == OCQ_TUNE_BUILD_PIXEL) return build_variant_count();
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) return deep_variant_count();
   if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) return block_form_count();
+  if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_LIST) return list_form_count();
   return -1;
 }
 
@@ -302,6 +306,7 @@ int ocq_tune_selected(int kernel) {
   if (kernel == OCQ_TUNE_BUILD_PIXEL) return build_variant_selected();
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) return deep_variant_selected();
   if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) return block_form_selected();
+  if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_LIST) return list_form_selected();
   return -1;
 }
 
@@ -312,6 +317,7 @@ ocq_status ocq_tune_select(int kernel, int variant) {
   if (kernel == OCQ_TUNE_BUILD_PIXEL) ok = build_variant_select(variant);
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) ok = deep_variant_select(variant);
   if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) ok = block_form_select(variant);
+  if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_LIST) ok = list_form_select(variant);
   if (!ok) {
     set_error("ocq_tune_select: no variant %d of kernel %d", variant, kernel);
     return OCQ_EINVAL;
@@ -346,6 +352,8 @@ ocq_status ocq_tune_describe(int kernel, int variant, int32_t *params, int n) {
     build_variant_describe(variant, &params[0], &params[1], &params[2], &params[3]);
   else if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP)
     deep_variant_describe(variant, &params[0], &params[1], &params[2]);
+  else if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_LIST)
+    list_form_describe(variant, &params[0], &params[1], &params[2], &params[3]);
   else
     params[0] = variant;
   return OCQ_OK;

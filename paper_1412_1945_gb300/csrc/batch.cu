@@ -555,7 +555,7 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
   b->desc.assign(streams, streams + n);
   size_t bytes = 0;
   size_t smem = 16 * 1024;
-  std::vector<size_t> model_off(n), occ_off(n);
+  std::vector<size_t> model_off(n), occ_off(n), kept_off(n);
   for (int s = 0; s < n; ++s) {
     const ocq_stream_desc &d = streams[s];
     const int64_t R = region_count(d.H, d.W, d.region.kind, d.region.block);
@@ -602,6 +602,10 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     bytes += ((size_t)R * h.wpr * 4 + 255) & ~(size_t)255;
     occ_off[s] = bytes;
     if (h.kind == OCQ_REGION_FRAME) bytes += ((size_t)d.N * h.wpr * 4 + 255) & ~(size_t)255;
+    // the kept-leaf index a per-pixel build of depth 4-5 writes (graph form):
+    // allocated here so that no allocation is captured into the graph
+    kept_off[s] = bytes;
+    if (h.kind == OCQ_REGION_PIXEL && (h.depth == 4 || h.depth == 5)) bytes += (size_t)R * 16;
     smem = std::max(smem, item_smem(h));
   }
   b->smem = (smem + 127) & ~(size_t)127;
@@ -630,6 +634,8 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     m->H = h.H, m->W = h.W, m->kind = h.kind, m->block = h.block, m->depth = h.depth, m->T = h.T, m->N = h.N;
     m->R = h.R, m->wpr = h.wpr, m->bits = h.model, m->bytes = (size_t)h.R * h.wpr * 4, m->stream = st;
     m->device = b->device;
+    if (h.kind == OCQ_REGION_PIXEL && (h.depth == 4 || h.depth == 5))
+      m->kept = reinterpret_cast<uint16_t *>(b->arena + kept_off[s]);
     b->models.push_back(m);
   }
   rc = size_kernel(b);

@@ -76,11 +76,12 @@ __global__ void __launch_bounds__(256) build_block_warp_kernel(const uint8_t *__
 
 template <int D, int KM, bool GRP>
 __global__ void __launch_bounds__(128) build_pixel_mg_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
-                                                             uint32_t T, uint32_t *__restrict__ model, int group) {
+                                                             uint32_t T, uint32_t *__restrict__ model, int group,
+                                                             uint16_t *__restrict__ kept) {
   extern __shared__ __align__(16) uint8_t mg_smem[];
   leaf_t<D> *codes = reinterpret_cast<leaf_t<D> *>(mg_smem) + (size_t)(threadIdx.x >> 5) * N * 32;
   build_pixel_mg_body<D, KM, GRP>(frames, N, hw, T, model, (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5), codes,
-                                  group);
+                                  group, kept);
 }
 
 template <int D, bool WIDE>
@@ -524,7 +525,14 @@ static ocq_status launch_pixel_mg_km(const uint8_t *frames, int N, ocq_model *m,
     if (rc != OCQ_OK) return rc;
   }
   const int64_t hw = (int64_t)m->H * m->W;
-  kern<<<(unsigned)((hw + 127) / 128), 128, smem, st>>>(frames, N, hw, (uint32_t)m->T, m->bits, group);
+  if (D >= 4 && D <= 5 && KM > 0 && !m->kept) {  // the kept-leaf index for the classify (16 B per location)
+    ocq_status rc = cuda_status(malloc_async((void **)&m->kept, (size_t)hw * 8 * sizeof(uint16_t), st),
+                                "kept-leaf index");
+    if (rc != OCQ_OK) return rc;
+  }
+  m->kept_len = D >= 4 && D <= 5 && KM > 0 ? (KM < 2 ? 2 : KM) : 0;
+  kern<<<(unsigned)((hw + 127) / 128), 128, smem, st>>>(frames, N, hw, (uint32_t)m->T, m->bits, group,
+                                                         m->kept_len ? m->kept : nullptr);
   count_launch();
   return cuda_status(cudaGetLastError(), "build_pixel_mg_kernel");
 }
@@ -853,6 +861,7 @@ bool build_take_timeout() {
 
 ocq_status launch_build_groups(const uint8_t *frames, int N, int group, ocq_model *m, cudaStream_t st) {
   if (group == 1) return launch_build(frames, N, m, st);
+  m->kept_len = 0;  // until a candidate build writes the kept-leaf index
   if (m->kind == OCQ_REGION_PIXEL && N <= 255) {  // per pixel location: candidates over group-distinct leaves
     switch (m->depth) {
       case 1: return launch_pixel_mg<1>(frames, N, m, st, group);
@@ -870,6 +879,7 @@ ocq_status launch_build_groups(const uint8_t *frames, int N, int group, ocq_mode
 
 ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
   const int d = m->depth;
+  m->kept_len = 0;  // until a candidate build writes the kept-leaf index
   if (m->kind == OCQ_REGION_FRAME || (m->kind == OCQ_REGION_BLOCK && d >= 6)) return build_dense(frames, N, m, st);
   if (m->kind == OCQ_REGION_BLOCK && block_warp_ok(N, m->H, m->W, m->block)) {
     switch (d) {

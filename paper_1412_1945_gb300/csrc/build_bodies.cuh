@@ -597,14 +597,16 @@ __device__ __forceinline__ void build_pixel_chunked_body(const uint8_t *__restri
 // per group, which is what the summary then sees.  The warp then
 // writes its 32 pixels' rows, which are contiguous: zeros with vector stores,
 // then the kept words.  Lane = pixel; the frames are read once and the model
-// written once, whatever the depth.
+// written once, whatever the depth.  With candidates (KM > 0) at depth <= 5,
+// `kept` (if not null) also receives each location's kept leaves as 8 u16
+// codes padded with kKeptNone: the kept-leaf index of the classify.
 template <int D>
 using leaf_t = typename std::conditional<(D <= 5), uint16_t, uint32_t>::type;
 
 template <int D, int KM, bool GRP = false>
 __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ frames, int N, int64_t hw, uint32_t T,
                                                     uint32_t *__restrict__ model, int64_t tile, leaf_t<D> *codes,
-                                                    int group = 1) {
+                                                    int group = 1, uint16_t *kept = nullptr) {
   // GRP: one tree per group of `group` consecutive frames (Sec. 3): a leaf
   // enters the summary once per group that holds it, and the exact pass counts
   // the groups holding each candidate (T counts groups).
@@ -681,6 +683,8 @@ __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ 
   if (!valid) return;
   uint32_t *row = base + lane * WPR;
   if constexpr (KM > 0) {
+    uint32_t list[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    int n = 0;
 #pragma unroll
     for (int i = 0; i < KM; ++i) {
       if (exact[i] < T) continue;
@@ -689,7 +693,15 @@ __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ 
       for (int j = 0; j < KM; ++j)
         if (exact[j] >= T && (key[j] >> 5) == (key[i] >> 5)) v |= 1u << (key[j] & 31);
       row[key[i] >> 5] = v;
+      if constexpr (D <= 5) {  // at most KM <= 8 kept leaves: the whole list
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (n >> 1 == e) list[e] = (n & 1) ? (list[e] & 0xFFFFu) | (key[i] << 16) : 0xFFFF0000u | key[i];
+        ++n;
+      }
     }
+    if constexpr (D <= 5)
+      if (kept) reinterpret_cast<uint4 *>(kept)[p] = make_uint4(list[0], list[1], list[2], list[3]);
   } else {
     for (int f = 0; f < N; ++f) {
       const uint32_t q = codes[f * 32 + lane];

@@ -9,6 +9,10 @@
 //                                frames stream through 16-byte loads.
 //   classify_block_tb_kernel<D>  b x b blocks (b % 4 == 0), depth >= 4: as the
 //                                per-pixel form, 8-warp CTAs over whole blocks.
+//   classify_pixel_list_kernel   pixel regions, depth 4-5, models with a kept-leaf
+//                                index: leaves compared in registers, no row gathers.
+//   classify_pixel_wsl_kernel    the same lists in the warp-specialised bulk-copy
+//                                form of classify_pixel_ws_kernel.
 //   classify_pixel_tb_kernel     pixel regions, depth >= 4: a warp walks all
 //                                frames of 32 or 128 pixel locations; their
 //                                model sectors stay in L1 between frames.
@@ -76,6 +80,17 @@ __global__ void __launch_bounds__(256) classify_block_tb_kernel(const uint8_t *_
   const int64_t nw = (int64_t)gridDim.x * 8;
   for (int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); t < tiles; t += nw)
     classify_block_tb_body<D, 8>(frames, F, H, W, b, bw, nseg, model, mask, t);
+}
+
+// Pixel regions, depth 4-5, models with a kept-leaf index.
+template <int D, int KL>
+__global__ void __launch_bounds__(128) classify_pixel_list_kernel(const uint8_t *__restrict__ frames, int F,
+                                                                  int64_t hw, const uint16_t *__restrict__ kept,
+                                                                  uint8_t *__restrict__ mask) {
+  const int64_t tiles = (hw + 127) / 128;
+  const int64_t nw = (int64_t)gridDim.x * 4;
+  for (int64_t t = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5); t < tiles; t += nw)
+    classify_pixel_list_body<D, 8, KL>(frames, F, hw, kept, mask, t);
 }
 
 template <int D, int S, int FPS>
@@ -197,6 +212,17 @@ __global__ void __launch_bounds__(NW * 32, 1)
     u += nfr;
     __syncthreads();  // all reads of this tile's rows are done before the next reload
   }
+}
+
+// Pixel regions, depth 4-5, models with a kept-leaf index: the warp-specialised
+// form with each location's kept leaves held in registers.
+template <int D, int NW, int PPT, int S, int FPS, int KL>
+__global__ void __launch_bounds__(NW * 32 + 32, 1)
+    classify_pixel_wsl_kernel(const uint8_t *__restrict__ frames, int F, int64_t hw, int64_t ntiles,
+                              const uint32_t *__restrict__ model, const uint16_t *__restrict__ kept,
+                              uint8_t *__restrict__ mask) {
+  classify_pixel_ws_body<D, NW, PPT, S, FPS, KL>(frames, F, hw, ntiles, model, mask, blockIdx.x, gridDim.x,
+                                                 &g_classify_timeout, kept);
 }
 
 // ---- host dispatch -----------------------------------------------------------------------
@@ -383,6 +409,81 @@ bool block_form_select(int v) {
   return true;
 }
 
+template <int D, int NW, int PPT, int S, int FPS, int KL>
+static ocq_status launch_list_ws_kl(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask,
+                                    cudaStream_t st) {
+  using C = TiledCfg<D, NW, PPT, S, FPS>;
+  const int64_t hw = (int64_t)m->H * m->W;
+  const size_t smem = (size_t)S * C::STAGE + (size_t)S * 16;
+  const int64_t ntiles = hw / C::TILE;
+  ocq_status rc = OCQ_OK;
+  if (ntiles > 0) {
+    auto kern = classify_pixel_wsl_kernel<D, NW, PPT, S, FPS, KL>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e, "classify_pixel_wsl_kernel smem");
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::THREADS + 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sm_count() * per_sm;
+    const int64_t U = ntiles * F;
+    if (grid > U) grid = U;
+    kern<<<(unsigned)grid, C::THREADS + 32, smem, st>>>(frames, F, hw, ntiles, m->bits, m->kept, mask);
+    count_launch();
+    rc = cuda_status(cudaGetLastError(), "classify_pixel_wsl_kernel");
+  }
+  if (rc == OCQ_OK) rc = launch_generic(m, frames, F, mask, ntiles * C::TILE, hw, st);
+  return rc;
+}
+
+template <int D, int NW, int PPT, int S, int FPS>
+static ocq_status launch_list_ws(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st) {
+  if (m->kept_len <= 2) return launch_list_ws_kl<D, NW, PPT, S, FPS, 2>(m, frames, F, mask, st);
+  if (m->kept_len <= 4) return launch_list_ws_kl<D, NW, PPT, S, FPS, 4>(m, frames, F, mask, st);
+  return launch_list_ws_kl<D, NW, PPT, S, FPS, 8>(m, frames, F, mask, st);
+}
+
+// Deep per-pixel classify forms for models with a kept-leaf index: 0 = from
+// the rows (classify_pixel_tb_kernel), 1 = lists, one warp per 128 locations
+// walking all frames (classify_pixel_list_kernel), 2-3 = lists, warp-
+// specialised with bulk copies (classify_pixel_wsl_kernel; NW, PPT, S, FPS).
+struct ListForm {
+  int nw, ppt, stages, fps;
+  ClassifyFn fn[2];  // depth 4, 5
+};
+#define OCQ_LF(NW, PPT, S, FPS) \
+  { NW, PPT, S, FPS, {launch_list_ws<4, NW, PPT, S, FPS>, launch_list_ws<5, NW, PPT, S, FPS>} }
+static const ListForm kListForms[] = {{0, 0, 0, 0, {nullptr, nullptr}}, {0, 0, 0, 0, {nullptr, nullptr}},
+                                      OCQ_LF(4, 16, 3, 2), OCQ_LF(8, 8, 4, 2)};
+#undef OCQ_LF
+static int g_use_kept = 2;
+int list_form_count() { return (int)(sizeof kListForms / sizeof kListForms[0]); }
+int list_form_selected() { return g_use_kept; }
+bool list_form_select(int v) {
+  if (v < 0 || v >= list_form_count()) return false;
+  g_use_kept = v;
+  return true;
+}
+void list_form_describe(int v, int *nw, int *ppt, int *stages, int *fps) {
+  *nw = kListForms[v].nw, *ppt = kListForms[v].ppt, *stages = kListForms[v].stages, *fps = kListForms[v].fps;
+}
+
+template <int D>
+static ocq_status launch_pixel_list(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask,
+                                   cudaStream_t st) {
+  const int64_t hw = (int64_t)m->H * m->W;
+  const int64_t ctas = (hw + 511) / 512;
+  const int64_t cap = (int64_t)sm_count() * 8;
+  const unsigned grid = (unsigned)(ctas < cap ? ctas : cap);
+  if (m->kept_len <= 2)
+    classify_pixel_list_kernel<D, 2><<<grid, 128, 0, st>>>(frames, F, hw, m->kept, mask);
+  else if (m->kept_len <= 4)
+    classify_pixel_list_kernel<D, 4><<<grid, 128, 0, st>>>(frames, F, hw, m->kept, mask);
+  else
+    classify_pixel_list_kernel<D, 8><<<grid, 128, 0, st>>>(frames, F, hw, m->kept, mask);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "classify_pixel_list_kernel");
+}
+
 template <int D>
 static ocq_status launch_block_tb(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, cudaStream_t st) {
   const int bw = (m->W + m->block - 1) / m->block;
@@ -442,6 +543,11 @@ ocq_status launch_classify(const ocq_model *m, const uint8_t *frames, int F, uin
   if (m->kind == OCQ_REGION_PIXEL && d <= 3 && aligned && hw % 16 == 0)
     return kClassifyVariants[g_classify_variant].fn[d - 1](m, frames, F, mask, st);
   const bool aligned4 = ((reinterpret_cast<uintptr_t>(frames) | reinterpret_cast<uintptr_t>(mask)) & 3) == 0;
+  const bool indexed = m->kind == OCQ_REGION_PIXEL && (d == 4 || d == 5) && m->kept && m->kept_len > 0;
+  if (indexed && g_use_kept >= 2 && aligned && hw % 16 == 0)
+    return kListForms[g_use_kept].fn[d - 4](m, frames, F, mask, st);
+  if (indexed && g_use_kept && aligned4 && hw % 4 == 0)
+    return d == 4 ? launch_pixel_list<4>(m, frames, F, mask, st) : launch_pixel_list<5>(m, frames, F, mask, st);
   if (m->kind == OCQ_REGION_PIXEL && d >= 4 && aligned4 && hw % 4 == 0) {
     const DeepVariant &v = kDeepVariants[g_deep_variant];
     return v.fn[d - 4](m, frames, F, mask, v.cps, st);

@@ -193,6 +193,72 @@ __device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict
   }
 }
 
+// Kept-leaf lists: a location's entry of the index is 8 u16 planar codes
+// (16 B), of which only the first KL (2, 4 or 8: the build's candidate count)
+// can be kept leaves; the rest are kKeptNone.  They are unpacked into one
+// register per code, in the form a pixel's leaf takes before its planar code
+// is formed: r_d | g_d << 8 | b_d << 16 | b_d << 24 (what group_pixel and
+// quad_pixel return from masked words).  A lookup is then KL integer compares
+// of that word; an unused entry becomes 0xFFFFFFFF, which no pixel gives.
+template <int D, int KL>
+__device__ __forceinline__ void list_unpack(const uint4 v, uint32_t (&l)[KL]) {
+  constexpr uint32_t M = (1u << D) - 1u;
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+  for (int e = 0; e < KL; ++e) {
+    const uint32_t c = (w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu;
+    l[e] = c == kKeptNone ? 0xFFFFFFFFu : (c & M) | (((c >> D) & M) << 8) | (((c >> (2 * D)) & M) * 0x01010000u);
+  }
+}
+
+template <int KL>
+__device__ __forceinline__ bool list_holds(const uint32_t (&l)[KL], uint32_t t) {
+  bool hit = false;
+#pragma unroll
+  for (int e = 0; e < KL; ++e) hit |= l[e] == t;
+  return hit;
+}
+
+// Pixel regions, depth 4-5, model with a kept-leaf index (from the candidate
+// build): as classify_pixel_tb_body, but a lookup compares the pixel's leaf
+// with its location's kept leaves held in registers instead of gathering a
+// byte of a 512 B / 4 KB row.
+template <int D, int PF, int KL>
+__device__ __forceinline__ void classify_pixel_list_body(const uint8_t *__restrict__ frames, int F, int64_t hw,
+                                                         const uint16_t *kept, uint8_t *__restrict__ mask,
+                                                         int64_t tile) {
+  const int lane = threadIdx.x & 31;
+  const int64_t pq = tile * 128 + 4 * lane;
+  if (pq >= hw) return;
+  uint32_t lst[4][KL];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) list_unpack<D, KL>(__ldg(reinterpret_cast<const uint4 *>(kept) + pq + k), lst[k]);
+  const uint8_t *src = frames + pq * 3;
+  uint8_t *dst = mask + pq;
+  for (int f0 = 0; f0 < F; f0 += PF) {
+    uint32_t w[PF][3];
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+      if (f0 + j < F) {
+        const uint8_t *sp = src + (int64_t)(f0 + j) * hw * 3;
+        w[j][0] = ld_stream4(sp), w[j][1] = ld_stream4(sp + 4), w[j][2] = ld_stream4(sp + 8);
+      }
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (f0 + j >= F) break;
+      uint32_t m[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) m[i] = (w[j][i] >> (8 - D)) & byte_mask(D);
+      uint32_t bg[4];
+      static_for<0, 4>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        bg[k] = list_holds<KL>(lst[k], quad_pixel<k>(m)) ? 1u : 0u;
+      });
+      st_stream4(dst + (int64_t)(f0 + j) * hw, pack_mask4(bg[0], bg[1], bg[2], bg[3]));
+    }
+  }
+}
+
 // Pixel regions, depth <= 3: as classify_pixel_tb_body, with the warp's 128
 // rows (WPR <= 16 words each) staged in shared memory first, interleaved so
 // that word w of the lane's k-th pixel sits at [(w * 4 + k) * 32 + lane]: every
@@ -296,15 +362,11 @@ struct TiledCfg {
   static_assert(PPT == 8 || PPT == 16, "8 or 16 pixels per thread");
 };
 
-// Classifies one frame of the tile from shared memory: thread (warp, lane)
-// handles pixels (warp*32 + lane)*PPT + j of the tile.
-template <int D, int NW, int PPT, int S, int FPS>
-__device__ __forceinline__ void classify_tile_frame(const uint8_t *__restrict__ src, const uint32_t *__restrict__ mrow,
-                                                    uint8_t *__restrict__ dst) {
-  using C = TiledCfg<D, NW, PPT, S, FPS>;
+// Loads this thread's PPT pixels of one frame's tile from shared memory
+// (thread tid holds pixels tid*PPT ..) and keeps the top D bits of each byte.
+template <int D, int PPT>
+__device__ __forceinline__ void tile_frame_words(const uint8_t *__restrict__ src, uint32_t (&w)[12]) {
   const int tid = threadIdx.x;
-  uint32_t fbit[PPT];
-  uint32_t w[12];
   if constexpr (PPT == 16) {
     const uint4 *s4 = reinterpret_cast<const uint4 *>(src + tid * 48);
     const uint4 a = s4[0], b = s4[1], c = s4[2];
@@ -320,14 +382,12 @@ __device__ __forceinline__ void classify_tile_frame(const uint8_t *__restrict__ 
 #pragma unroll
     for (int e = 0; e < 6; ++e) w[e] = (w[e] >> (8 - D)) & byte_mask(D);
   }
-  // mrow points at word 0 of pixel j=0 for this lane; pixel j's word q>>5 is at
-  // mrow[(j*WPR + (q>>5))*32]
-  static_for<0, PPT>([&](auto jc) {
-    constexpr int j = decltype(jc)::value;
-    const uint32_t q = planar_from_masked<D>(group_pixel<j>(w));
-    const uint32_t v = mrow[(j * C::WPR + (q >> 5)) * 32];
-    fbit[j] = __funnelshift_r(v, v, q);
-  });
+}
+
+// Writes this thread's PPT mask bytes (bit 0 of fbit[j] = leaf kept).
+template <int PPT>
+__device__ __forceinline__ void store_tile_mask(uint8_t *__restrict__ dst, const uint32_t (&fbit)[PPT]) {
+  const int tid = threadIdx.x;
   if constexpr (PPT == 16) {
     uint4 o;
     o.x = pack_mask4(fbit[0], fbit[1], fbit[2], fbit[3]);
@@ -342,6 +402,41 @@ __device__ __forceinline__ void classify_tile_frame(const uint8_t *__restrict__ 
   }
 }
 
+// Classifies one frame of the tile from shared memory: thread (warp, lane)
+// handles pixels (warp*32 + lane)*PPT + j of the tile.
+template <int D, int NW, int PPT, int S, int FPS>
+__device__ __forceinline__ void classify_tile_frame(const uint8_t *__restrict__ src, const uint32_t *__restrict__ mrow,
+                                                    uint8_t *__restrict__ dst) {
+  using C = TiledCfg<D, NW, PPT, S, FPS>;
+  uint32_t fbit[PPT];
+  uint32_t w[12];
+  tile_frame_words<D, PPT>(src, w);
+  // mrow points at word 0 of pixel j=0 for this lane; pixel j's word q>>5 is at
+  // mrow[(j*WPR + (q>>5))*32]
+  static_for<0, PPT>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    const uint32_t q = planar_from_masked<D>(group_pixel<j>(w));
+    const uint32_t v = mrow[(j * C::WPR + (q >> 5)) * 32];
+    fbit[j] = __funnelshift_r(v, v, q);
+  });
+  store_tile_mask<PPT>(dst, fbit);
+}
+
+// As classify_tile_frame for depth 4-5 models with a kept-leaf index: pixel
+// j's (at most KL) kept leaves sit in lst[j].
+template <int D, int PPT, int KL>
+__device__ __forceinline__ void classify_tile_frame_list(const uint8_t *__restrict__ src, const uint32_t (&lst)[PPT][KL],
+                                                         uint8_t *__restrict__ dst) {
+  uint32_t fbit[PPT];
+  uint32_t w[12];
+  tile_frame_words<D, PPT>(src, w);
+  static_for<0, PPT>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    fbit[j] = list_holds<KL>(lst[j], group_pixel<j>(w)) ? 1u : 0u;
+  });
+  store_tile_mask<PPT>(dst, fbit);
+}
+
 // Warp-specialised form: NW classifying warps plus one copy warp.  The copy
 // warp streams every group of the CTA's work range, refilling a stage as soon
 // as all classifying warps have released it (mbarrier "empty"); classifying
@@ -349,21 +444,22 @@ __device__ __forceinline__ void classify_tile_frame(const uint8_t *__restrict__ 
 // barrier 1, the copy warp is not part of it) reload the tile's rows.  A
 // timed-out wait raises a shared abort flag; the warps then run to the end
 // without waiting, so no barrier is left short of arrivals.
-template <int D, int NW, int PPT, int S, int FPS>
-__device__ __forceinline__ size_t classify_pixel_ws_bars() {
-  using C = TiledCfg<D, NW, PPT, S, FPS>;
-  return (size_t)C::MODEL_WORDS * 4 + (size_t)S * C::STAGE;
-}
-
-template <int D, int NW, int PPT, int S, int FPS>
+//
+// KL > 0 (depth 4-5, models with a kept-leaf index of KL codes per location):
+// no rows in shared memory; each classifying thread holds the kept-leaf lists
+// of its PPT locations in registers (read from `kept` at a tile change) and
+// compares.
+template <int D, int NW, int PPT, int S, int FPS, int KL = 0>
 __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict__ frames, int F, int64_t hw,
                                                        int64_t ntiles, const uint32_t *model,
                                                        uint8_t *__restrict__ mask, int64_t vb, int64_t vg,
-                                                       unsigned int *timeout_flag) {
+                                                       unsigned int *timeout_flag, const uint16_t *kept = nullptr) {
   using C = TiledCfg<D, NW, PPT, S, FPS>;
+  constexpr bool LIST = KL > 0;
+  constexpr size_t MODEL_BYTES = LIST ? 0 : (size_t)C::MODEL_WORDS * 4;
   extern __shared__ __align__(128) uint8_t smem[];
   uint32_t *msm = reinterpret_cast<uint32_t *>(smem);
-  uint8_t *stages = smem + (size_t)C::MODEL_WORDS * 4;
+  uint8_t *stages = smem + MODEL_BYTES;
   uint64_t *full = reinterpret_cast<uint64_t *>(stages + (size_t)S * C::STAGE);
   uint64_t *empty = full + S;
   __shared__ volatile int abort_flag;
@@ -417,6 +513,7 @@ __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict
   // ---- classifying warps ----
   const int lane = tid & 31, warp = tid >> 5;
   const uint32_t *mrow = msm + warp * PPT * C::WPR * 32 + lane;
+  uint32_t lst[LIST ? PPT : 1][LIST ? KL : 1];
   int s = 0;
   uint32_t round = 0;
   for (int64_t u = u_begin; u < u_end;) {
@@ -424,30 +521,36 @@ __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict
     const int fa = (int)(u - tile * F);
     const int nfr = (int)((u_end - u) < (int64_t)(F - fa) ? (u_end - u) : (int64_t)(F - fa));
     const int64_t p_tile = tile * C::TILE;
-    named_sync(1, NW * 32);  // every warp is done with the previous tile's rows
-    {
-      const uint32_t *src = model + (p_tile + (int64_t)tid * PPT) * C::WPR;
-      if constexpr (C::WPR % 4 == 0) {
-        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
-#pragma unroll 4
-        for (int i = 0; i < PPT * C::WPR / 4; ++i) {
-          const uint4 v = s4[i];
-          const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+    if constexpr (LIST) {
+      const uint4 *k4 = reinterpret_cast<const uint4 *>(kept) + p_tile + (int64_t)tid * PPT;
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int idx = i * 4 + e, j = idx / C::WPR, w = idx % C::WPR;
-            msm[((warp * PPT + j) * C::WPR + w) * 32 + lane] = vv[e];
+      for (int j = 0; j < PPT; ++j) list_unpack<D, KL>(__ldg(k4 + j), lst[j]);
+    } else {
+      named_sync(1, NW * 32);  // every warp is done with the previous tile's rows
+      {
+        const uint32_t *src = model + (p_tile + (int64_t)tid * PPT) * C::WPR;
+        if constexpr (C::WPR % 4 == 0) {
+          const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+#pragma unroll 4
+          for (int i = 0; i < PPT * C::WPR / 4; ++i) {
+            const uint4 v = s4[i];
+            const uint32_t vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int idx = i * 4 + e, j = idx / C::WPR, w = idx % C::WPR;
+              msm[((warp * PPT + j) * C::WPR + w) * 32 + lane] = vv[e];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int idx = 0; idx < PPT * C::WPR; ++idx) {
+            const int j = idx / C::WPR, w = idx % C::WPR;
+            msm[((warp * PPT + j) * C::WPR + w) * 32 + lane] = src[idx];
           }
         }
-      } else {
-#pragma unroll
-        for (int idx = 0; idx < PPT * C::WPR; ++idx) {
-          const int j = idx / C::WPR, w = idx % C::WPR;
-          msm[((warp * PPT + j) * C::WPR + w) * 32 + lane] = src[idx];
-        }
       }
+      named_sync(1, NW * 32);
     }
-    named_sync(1, NW * 32);
     for (int g = 0; g * FPS < nfr; ++g) {
       const int f0 = fa + g * FPS;
       const int nf = (nfr - g * FPS) < FPS ? (nfr - g * FPS) : FPS;
@@ -456,9 +559,14 @@ __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict
           const uint8_t *stage = stages + (size_t)s * C::STAGE;
 #pragma unroll
           for (int i = 0; i < FPS; ++i)
-            if (i < nf)
-              classify_tile_frame<D, NW, PPT, S, FPS>(stage + (size_t)i * C::FRAME_BYTES, mrow,
-                                                      mask + (int64_t)(f0 + i) * hw + p_tile);
+            if (i < nf) {
+              if constexpr (LIST)
+                classify_tile_frame_list<D, PPT, KL>(stage + (size_t)i * C::FRAME_BYTES, lst,
+                                                     mask + (int64_t)(f0 + i) * hw + p_tile);
+              else
+                classify_tile_frame<D, NW, PPT, S, FPS>(stage + (size_t)i * C::FRAME_BYTES, mrow,
+                                                        mask + (int64_t)(f0 + i) * hw + p_tile);
+            }
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
         } else {

@@ -24,7 +24,16 @@ struct ocq_model {
   size_t bytes;
   cudaStream_t stream; // stream the model was created on (stream-ordered free)
   int device;
+  // Pixel regions, depth 4-5, built by the candidate build with k = floor(N/T)
+  // <= 8 (no location keeps more than 8 leaves): per pixel location its kept
+  // leaves as 8 u16 planar codes, kKeptNone padding.  A derived index for the
+  // classify; the bitset stays the model.  Valid while kept_len > 0 (a batch
+  // lends every such model a buffer, written only by a candidate build).
+  uint16_t *kept;
+  int kept_len;  // entries of a list that can hold a kept leaf: 2, 4 or 8; 0 = no valid index
 };
+
+constexpr uint16_t kKeptNone = 0xFFFFu;  // no planar code of depth <= 5 equals it
 
 namespace ocq {
 
@@ -178,6 +187,10 @@ int deep_variant_count();
 int deep_variant_selected();
 bool deep_variant_select(int v);
 void deep_variant_describe(int v, int *pxl, int *pf, int *cps);
+int list_form_count();
+int list_form_selected();
+bool list_form_select(int v);
+void list_form_describe(int v, int *nw, int *ppt, int *stages, int *fps);
 int block_form_count();
 int block_form_selected();
 bool block_form_select(int v);

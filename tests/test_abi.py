@@ -60,6 +60,9 @@ def test_host_side_helpers(lib):
     # model bytes: regions x max(1, 8^d / 32) u32 words
     assert ocq.ocq_model_footprint(1080, 1920, ocq.OCQ_REGION_PIXEL, 0, 3) == 1920 * 1080 * 64
     assert ocq.ocq_model_footprint(240, 320, ocq.OCQ_REGION_BLOCK, 16, 5) == 300 * 4096
+    # per-pixel depth 4-5: plus the kept-leaf index, 8 u16 codes per location
+    assert ocq.ocq_model_footprint(1080, 1920, ocq.OCQ_REGION_PIXEL, 0, 4) == 1920 * 1080 * (512 + 16)
+    assert ocq.ocq_model_footprint(1080, 1920, ocq.OCQ_REGION_PIXEL, 0, 6) == 1920 * 1080 * 32768
     assert ocq.ocq_model_footprint(120, 160, ocq.OCQ_REGION_FRAME, 0, 1) == 4
     assert ocq.ocq_model_footprint(120, 160, ocq.OCQ_REGION_FRAME, 0, 9) == 0
 

@@ -334,23 +334,31 @@ def test_pixel_deep_candidates_and_tiles(ocq, torch, d, H, W):
 
 
 def test_pixel_deep_classify_variants(ocq, torch):
-    """Every residency choice of the deep per-pixel classify gives the oracle's masks."""
+    """Every form of the deep per-pixel classify (kept-leaf lists in each
+    launch form, or the rows with each residency choice) gives the oracle's
+    masks, with few and with many (> 8, the rows decide) kept leaves per
+    location; 2880 locations leave a ragged tail after whole tiles."""
     O = ocq.ocq
     H, W = 40, 72
     sc = ocq_synth.make_scene("bimodal", H, W, 12, 10, seed=8)
     frames = ocq_synth.fill_host(sc, 0, 22)
-    train, test = frames[:12], frames[12:]
-    kernel = O.OCQ_TUNE_CLASSIFY_PIXEL_DEEP
-    saved = O.ocq_tune_selected(kernel)
+    train, test = frames[:12].copy(), frames[12:]
+    train[::2, ::3] = np.random.default_rng(8).integers(0, 256, size=train[::2, ::3].shape, dtype=np.uint8)
+    deep, lst = O.OCQ_TUNE_CLASSIFY_PIXEL_DEEP, O.OCQ_TUNE_CLASSIFY_PIXEL_LIST
+    saved = O.ocq_tune_selected(deep), O.ocq_tune_selected(lst)
     try:
         for d in (4, 5):
-            ow, om = oracle.run(train, d, 3, PIXEL, 0, test)
-            for v in range(O.ocq_tune_count(kernel)):
-                O.ocq_tune_select(kernel, v)
-                words, mask = gpu_model_and_mask(ocq, torch, train, test, d, 3, PIXEL, 0)
-                assert (words == ow).all() and (mask == om).all(), (d, v)
+            for T in (1, 2, 3, 6, 12):  # lists of 8, 4, 2 codes; T = 1: no list (k = 12 > 8)
+                ow, om = oracle.run(train, d, T, PIXEL, 0, test)
+                for form in range(O.ocq_tune_count(lst)):
+                    O.ocq_tune_select(lst, form)
+                    for v in range(O.ocq_tune_count(deep)) if form == 0 else (saved[0],):
+                        O.ocq_tune_select(deep, v)
+                        words, mask = gpu_model_and_mask(ocq, torch, train, test, d, T, PIXEL, 0)
+                        assert (words == ow).all() and (mask == om).all(), (d, T, form, v)
     finally:
-        O.ocq_tune_select(kernel, saved)
+        O.ocq_tune_select(deep, saved[0])
+        O.ocq_tune_select(lst, saved[1])
 
 
 @pytest.mark.parametrize("b", [4, 8, 12, 16])
