@@ -56,6 +56,8 @@ struct BStream {
   int32_t tb;          // pixel / block classify: 1 if the L1 body applies
   int32_t nseg;        // block classify (L1 body): 128-pixel segments per pixel row
   int32_t stage;       // pixel classify, depth <= 3: rows staged in shared memory (else L1)
+  int32_t kl;          // pixel regions, depth 4-5, candidates: kept-leaf list length (0: no index)
+  uint16_t *kept;      // kept-leaf index (kl > 0): written by the build, read by the classify
 };
 
 struct BItem {
@@ -120,7 +122,7 @@ template <int D, int KM>
 __device__ __forceinline__ void pixel_mg_item(const BStream &S, int64_t t0, int64_t t1, uint8_t *smem) {
   leaf_t<D> *codes = reinterpret_cast<leaf_t<D> *>(smem) + (size_t)(threadIdx.x >> 5) * S.N * 32;
   for (int64_t t = t0; t < t1; t += kBatchThreads / 32) {
-    build_pixel_mg_body<D, KM>(S.train, S.N, S.hw, (uint32_t)S.T, S.model, t, codes);
+    build_pixel_mg_body<D, KM>(S.train, S.N, S.hw, (uint32_t)S.T, S.model, t, codes, 1, S.kl ? S.kept : nullptr);
     __syncwarp();
   }
 }
@@ -181,6 +183,25 @@ __device__ __noinline__ void pixel_tb_dispatch(const BStream &S, int64_t t0, int
   }
 }
 
+// Depth 4-5 with a kept-leaf index: the location's kept leaves in registers.
+template <int D>
+__device__ __forceinline__ void pixel_list_item(const BStream &S, int64_t t) {
+  switch (S.kl) {
+    case 2: classify_pixel_list_body<D, 4, 2>(S.test, S.F, S.hw, S.kept, S.mask, t); break;
+    case 4: classify_pixel_list_body<D, 4, 4>(S.test, S.F, S.hw, S.kept, S.mask, t); break;
+    default: classify_pixel_list_body<D, 4, 8>(S.test, S.F, S.hw, S.kept, S.mask, t); break;
+  }
+}
+
+__device__ __noinline__ void pixel_list_dispatch(const BStream &S, int64_t t0, int64_t t1) {
+  for (int64_t t = t0; t < t1; t += kBatchThreads / 32) {
+    if (S.depth == 4)
+      pixel_list_item<4>(S, t);
+    else
+      pixel_list_item<5>(S, t);
+  }
+}
+
 template <int D>
 __device__ __forceinline__ void run_item_d(const BStream &S, const BItem &it, uint8_t *smem) {
   const uint32_t T = (uint32_t)S.T;
@@ -214,7 +235,10 @@ __device__ void run_item(const BStream &S, const BItem &it, uint8_t *smem) {
       pixel_mg_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux, smem);
       return;
     case OP_CLS_PIXEL_TB:
-      pixel_tb_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux, smem);
+      if (S.kl)
+        pixel_list_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux);
+      else
+        pixel_tb_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux, smem);
       return;
     case OP_CLS_BLOCK_TB:
       block_tb_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux);
@@ -585,6 +609,7 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     if (h.kind == OCQ_REGION_PIXEL) {
       const int k = d.N / d.T;
       h.km = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : 0;
+      h.kl = (d.depth == 4 || d.depth == 5) && h.km > 0 ? (h.km < 2 ? 2 : h.km) : 0;
       h.tb = d.F > 0 && h.hw % 4 == 0 &&
              ((reinterpret_cast<uintptr_t>(d.test) | reinterpret_cast<uintptr_t>(d.mask)) & 3) == 0;
     }
@@ -634,8 +659,10 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     m->H = h.H, m->W = h.W, m->kind = h.kind, m->block = h.block, m->depth = h.depth, m->T = h.T, m->N = h.N;
     m->R = h.R, m->wpr = h.wpr, m->bits = h.model, m->bytes = (size_t)h.R * h.wpr * 4, m->stream = st;
     m->device = b->device;
-    if (h.kind == OCQ_REGION_PIXEL && (h.depth == 4 || h.depth == 5))
-      m->kept = reinterpret_cast<uint16_t *>(b->arena + kept_off[s]);
+    if (h.kind == OCQ_REGION_PIXEL && (h.depth == 4 || h.depth == 5)) {
+      h.kept = reinterpret_cast<uint16_t *>(b->arena + kept_off[s]);
+      m->kept = h.kept, m->kept_len = h.kl;
+    }
     b->models.push_back(m);
   }
   rc = size_kernel(b);
