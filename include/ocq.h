@@ -367,7 +367,15 @@ void ocq_server_destroy(ocq_server *server);
  *                            with the list in the warp-specialised bulk-copy form
  *                            (frames and mask 16-byte aligned, H*W % 16 == 0; else
  *                            variant 1 runs); params = {warps, locations per thread,
- *                            stages, frames per stage, 0} (zeros for 0 and 1)
+ *                            stages, frames per stage, 0} (zeros for 0 and 1); a list
+ *                            model (below) has no rows, so variant 0 acts as 1 there
+ *   OCQ_TUNE_PIXEL_MODEL_FORM  what ocq_build_model / ocq_build_model_groups build for
+ *                            per-pixel regions of depth 4-5 with N <= 255 and
+ *                            floor(N / T) <= 8 (no location can keep more than 8
+ *                            leaves): 1 (default) a list model, the kept leaves of
+ *                            each location as a 16 B list and no leaf bitset (export
+ *                            expands it into the bitset layout); 0 the bitset rows
+ *                            plus that list; params = {variant, 0, ...}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5
@@ -378,7 +386,8 @@ enum {
   OCQ_TUNE_BUILD_PIXEL = 1,
   OCQ_TUNE_CLASSIFY_PIXEL_DEEP = 2,
   OCQ_TUNE_CLASSIFY_BLOCK_DEEP = 3,
-  OCQ_TUNE_CLASSIFY_PIXEL_LIST = 4
+  OCQ_TUNE_CLASSIFY_PIXEL_LIST = 4,
+  OCQ_TUNE_PIXEL_MODEL_FORM = 5
 };
 int ocq_tune_count(int kernel);
 int ocq_tune_selected(int kernel);

@@ -78,8 +78,9 @@ static ocq_status check_geometry(int H, int W, ocq_region region, int depth) {
   return OCQ_OK;
 }
 
+// rows = false: a list model (kept-leaf index only), allocated by its build.
 static ocq_model *new_model(int H, int W, ocq_region region, int depth, int T, int N, cudaStream_t st,
-                            ocq_status *rc) {
+                            ocq_status *rc, bool rows = true) {
   ocq_model *m = new (std::nothrow) ocq_model();
   if (!m) {
     set_error("host allocation failed");
@@ -90,9 +91,10 @@ static ocq_model *new_model(int H, int W, ocq_region region, int depth, int T, i
   m->depth = depth, m->T = T, m->N = N;
   m->R = region_count(H, W, region.kind, region.block);
   m->wpr = wpr32(depth);
-  m->bytes = (size_t)m->R * (size_t)m->wpr * sizeof(uint32_t);
+  m->bytes = rows ? (size_t)m->R * (size_t)m->wpr * sizeof(uint32_t) : 0;
   m->stream = st;
   cudaGetDevice(&m->device);
+  if (!rows) return m;
   void *p = nullptr;
   *rc = cuda_status(malloc_async(&p, m->bytes, st), "allocating the model");
   if (*rc != OCQ_OK) {
@@ -176,7 +178,7 @@ ocq_status ocq_build_model(const uint8_t *frames, int N, int H, int W, ocq_regio
     return OCQ_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  ocq_model *m = new_model(H, W, region, depth, T, N, st, &rc);
+  ocq_model *m = new_model(H, W, region, depth, T, N, st, &rc, !list_model_applies(region.kind, depth, N, T));
   if (!m) return rc;
   rc = launch_build(frames, N, m, st);
   if (rc != OCQ_OK) {
@@ -204,7 +206,7 @@ ocq_status ocq_build_model_groups(const uint8_t *frames, int N, int H, int W, oc
     return OCQ_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  ocq_model *m = new_model(H, W, region, depth, T, N, st, &rc);
+  ocq_model *m = new_model(H, W, region, depth, T, N, st, &rc, !list_model_applies(region.kind, depth, N, T));
   if (!m) return rc;
   rc = launch_build_groups(frames, N, group, m, st);
   if (rc != OCQ_OK) {
@@ -245,6 +247,7 @@ ocq_status ocq_model_export(const ocq_model *m, uint64_t *dst, size_t words, voi
     set_error("ocq_model_export: NULL argument or destination too small");
     return OCQ_EINVAL;
   }
+  if (!m->bits) return launch_export_list(m->kept, m->R, m->depth, dst, (cudaStream_t)stream);
   return launch_export(m->bits, m->R, m->depth, dst, (cudaStream_t)stream);
 }
 
@@ -298,6 +301,7 @@ int ocq_tune_count(int kernel) {
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) return deep_variant_count();
   if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) return block_form_count();
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_LIST) return list_form_count();
+  if (kernel == OCQ_TUNE_PIXEL_MODEL_FORM) return 2;
   return -1;
 }
 
@@ -307,6 +311,7 @@ int ocq_tune_selected(int kernel) {
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) return deep_variant_selected();
   if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) return block_form_selected();
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_LIST) return list_form_selected();
+  if (kernel == OCQ_TUNE_PIXEL_MODEL_FORM) return list_model_form();
   return -1;
 }
 
@@ -318,6 +323,7 @@ ocq_status ocq_tune_select(int kernel, int variant) {
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_DEEP) ok = deep_variant_select(variant);
   if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) ok = block_form_select(variant);
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_LIST) ok = list_form_select(variant);
+  if (kernel == OCQ_TUNE_PIXEL_MODEL_FORM) ok = list_model_select(variant);
   if (!ok) {
     set_error("ocq_tune_select: no variant %d of kernel %d", variant, kernel);
     return OCQ_EINVAL;

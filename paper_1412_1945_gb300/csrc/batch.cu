@@ -580,6 +580,7 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
   size_t bytes = 0;
   size_t smem = 16 * 1024;
   std::vector<size_t> model_off(n), occ_off(n), kept_off(n);
+  std::vector<char> list_only(n, 0);
   for (int s = 0; s < n; ++s) {
     const ocq_stream_desc &d = streams[s];
     const int64_t R = region_count(d.H, d.W, d.region.kind, d.region.block);
@@ -610,6 +611,8 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
       const int k = d.N / d.T;
       h.km = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : 0;
       h.kl = (d.depth == 4 || d.depth == 5) && h.km > 0 ? (h.km < 2 ? 2 : h.km) : 0;
+      // a list model (no rows) where every classify item can read the index
+      list_only[s] = h.kl > 0 && h.tb && list_model_applies(h.kind, d.depth, d.N, d.T);
       h.tb = d.F > 0 && h.hw % 4 == 0 &&
              ((reinterpret_cast<uintptr_t>(d.test) | reinterpret_cast<uintptr_t>(d.mask)) & 3) == 0;
     }
@@ -624,13 +627,13 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     }
     b->hs.push_back(h);
     model_off[s] = bytes;
-    bytes += ((size_t)R * h.wpr * 4 + 255) & ~(size_t)255;
+    if (!list_only[s]) bytes += ((size_t)R * h.wpr * 4 + 255) & ~(size_t)255;
     occ_off[s] = bytes;
     if (h.kind == OCQ_REGION_FRAME) bytes += ((size_t)d.N * h.wpr * 4 + 255) & ~(size_t)255;
-    // the kept-leaf index a per-pixel build of depth 4-5 writes (graph form):
+    // the kept-leaf index a per-pixel candidate build of depth 4-5 writes:
     // allocated here so that no allocation is captured into the graph
     kept_off[s] = bytes;
-    if (h.kind == OCQ_REGION_PIXEL && (h.depth == 4 || h.depth == 5)) bytes += (size_t)R * 16;
+    if (h.kl > 0) bytes += ((size_t)R * 16 + 255) & ~(size_t)255;
     smem = std::max(smem, item_smem(h));
   }
   b->smem = (smem + 127) & ~(size_t)127;
@@ -649,7 +652,7 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
   }
   for (int s = 0; s < n; ++s) {
     BStream &h = b->hs[s];
-    h.model = reinterpret_cast<uint32_t *>(b->arena + model_off[s]);
+    h.model = list_only[s] ? nullptr : reinterpret_cast<uint32_t *>(b->arena + model_off[s]);
     h.occ = h.kind == OCQ_REGION_FRAME ? reinterpret_cast<uint32_t *>(b->arena + occ_off[s]) : nullptr;
     ocq_model *m = new (std::nothrow) ocq_model();
     if (!m) {
@@ -657,9 +660,9 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
       return OCQ_ENOMEM;
     }
     m->H = h.H, m->W = h.W, m->kind = h.kind, m->block = h.block, m->depth = h.depth, m->T = h.T, m->N = h.N;
-    m->R = h.R, m->wpr = h.wpr, m->bits = h.model, m->bytes = (size_t)h.R * h.wpr * 4, m->stream = st;
+    m->R = h.R, m->wpr = h.wpr, m->bits = h.model, m->bytes = h.model ? (size_t)h.R * h.wpr * 4 : 0, m->stream = st;
     m->device = b->device;
-    if (h.kind == OCQ_REGION_PIXEL && (h.depth == 4 || h.depth == 5)) {
+    if (h.kl > 0) {
       h.kept = reinterpret_cast<uint16_t *>(b->arena + kept_off[s]);
       m->kept = h.kept, m->kept_len = h.kl;
     }

@@ -525,14 +525,19 @@ static ocq_status launch_pixel_mg_km(const uint8_t *frames, int N, ocq_model *m,
     if (rc != OCQ_OK) return rc;
   }
   const int64_t hw = (int64_t)m->H * m->W;
-  if (D >= 4 && D <= 5 && KM > 0 && !m->kept) {  // the kept-leaf index for the classify (16 B per location)
+  constexpr bool kIndex = D >= 4 && D <= 5 && KM > 0;  // at most 8 kept leaves per location
+  if (!kIndex && !m->bits) {
+    set_error("internal: a list model needs the candidate build at depth 4-5 with floor(N/T) <= 8");
+    return OCQ_EINVAL;
+  }
+  if (kIndex && !m->kept) {  // the kept-leaf index (16 B per location)
     ocq_status rc = cuda_status(malloc_async((void **)&m->kept, (size_t)hw * 8 * sizeof(uint16_t), st),
                                 "kept-leaf index");
     if (rc != OCQ_OK) return rc;
   }
-  m->kept_len = D >= 4 && D <= 5 && KM > 0 ? (KM < 2 ? 2 : KM) : 0;
+  m->kept_len = kIndex ? (KM < 2 ? 2 : KM) : 0;
   kern<<<(unsigned)((hw + 127) / 128), 128, smem, st>>>(frames, N, hw, (uint32_t)m->T, m->bits, group,
-                                                         m->kept_len ? m->kept : nullptr);
+                                                         kIndex ? m->kept : nullptr);
   count_launch();
   return cuda_status(cudaGetLastError(), "build_pixel_mg_kernel");
 }
@@ -857,6 +862,17 @@ bool build_take_timeout() {
   if (cudaMemcpyFromSymbol(&flag, g_build_timeout, sizeof flag) != cudaSuccess) return false;
   if (flag) cudaMemcpyToSymbol(g_build_timeout, &zero, sizeof zero);
   return flag != 0;
+}
+
+static int g_list_models = 1;
+bool list_model_applies(int kind, int depth, int N, int T) {
+  return g_list_models && kind == OCQ_REGION_PIXEL && (depth == 4 || depth == 5) && N <= 255 && T >= 1 && N / T <= 8;
+}
+int list_model_form() { return g_list_models; }
+bool list_model_select(int v) {
+  if (v < 0 || v > 1) return false;
+  g_list_models = v;
+  return true;
 }
 
 ocq_status launch_build_groups(const uint8_t *frames, int N, int group, ocq_model *m, cudaStream_t st) {

@@ -599,7 +599,8 @@ __device__ __forceinline__ void build_pixel_chunked_body(const uint8_t *__restri
 // then the kept words.  Lane = pixel; the frames are read once and the model
 // written once, whatever the depth.  With candidates (KM > 0) at depth <= 5,
 // `kept` (if not null) also receives each location's kept leaves as 8 u16
-// codes padded with kKeptNone: the kept-leaf index of the classify.
+// codes padded with kKeptNone: the kept-leaf index of the classify; model =
+// null (a list model) then writes no rows at all.
 template <int D>
 using leaf_t = typename std::conditional<(D <= 5), uint16_t, uint32_t>::type;
 
@@ -672,27 +673,31 @@ __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ 
       }
   }
   const int64_t np = hw - p0 < 32 ? hw - p0 : 32;
-  uint32_t *base = model + p0 * WPR;
-  if constexpr (WPR >= 4) {
-    uint4 *b4 = reinterpret_cast<uint4 *>(base);
-    for (int64_t i = lane; i < np * WPR / 4; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
-  } else {
-    for (int64_t i = lane; i < np * WPR; i += 32) base[i] = 0u;
+  uint32_t *base = model ? model + p0 * WPR : nullptr;  // null: a list model, no rows
+  if (base) {
+    if constexpr (WPR >= 4) {
+      uint4 *b4 = reinterpret_cast<uint4 *>(base);
+      for (int64_t i = lane; i < np * WPR / 4; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
+    } else {
+      for (int64_t i = lane; i < np * WPR; i += 32) base[i] = 0u;
+    }
   }
   __syncwarp();
   if (!valid) return;
-  uint32_t *row = base + lane * WPR;
+  uint32_t *row = base ? base + lane * WPR : nullptr;
   if constexpr (KM > 0) {
     uint32_t list[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
     int n = 0;
 #pragma unroll
     for (int i = 0; i < KM; ++i) {
       if (exact[i] < T) continue;
-      uint32_t v = 0u;
+      if (row) {
+        uint32_t v = 0u;
 #pragma unroll
-      for (int j = 0; j < KM; ++j)
-        if (exact[j] >= T && (key[j] >> 5) == (key[i] >> 5)) v |= 1u << (key[j] & 31);
-      row[key[i] >> 5] = v;
+        for (int j = 0; j < KM; ++j)
+          if (exact[j] >= T && (key[j] >> 5) == (key[i] >> 5)) v |= 1u << (key[j] & 31);
+        row[key[i] >> 5] = v;
+      }
       if constexpr (D <= 5) {  // at most KM <= 8 kept leaves: the whole list
 #pragma unroll
         for (int e = 0; e < 4; ++e)

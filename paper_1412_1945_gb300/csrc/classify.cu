@@ -225,6 +225,28 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1)
                                                  &g_classify_timeout, kept);
 }
 
+// Pixel regions, depth 4-5, kept-leaf index, any alignment: one pixel-frame per
+// thread step over locations [pb, pe); the planar code is compared with the
+// location's 8 list entries.
+__global__ void __launch_bounds__(256) classify_list_generic_kernel(const uint8_t *__restrict__ frames, int F,
+                                                                    int64_t hw, int d,
+                                                                    const uint16_t *__restrict__ kept,
+                                                                    uint8_t *__restrict__ mask, int64_t pb,
+                                                                    int64_t pe) {
+  const int64_t np = pe - pb, n = np * F;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = i / np, p = pb + i % np;
+    const uint8_t *px = frames + (f * hw + p) * 3;
+    const uint32_t q = planar_code_rt(px[0], px[1], px[2], d);
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(kept) + p);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    bool hit = false;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) hit |= ((w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu) == q;
+    mask[f * hw + p] = hit ? 0 : 1;
+  }
+}
+
 // ---- host dispatch -----------------------------------------------------------------------
 
 static unsigned grid_cap(int64_t work, int threads, int per_sm) {
@@ -409,6 +431,15 @@ bool block_form_select(int v) {
   return true;
 }
 
+static ocq_status launch_list_generic(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask, int64_t pb,
+                                      int64_t pe, cudaStream_t st) {
+  if (pe <= pb) return OCQ_OK;
+  classify_list_generic_kernel<<<grid_cap((pe - pb) * F, 256, 16), 256, 0, st>>>(
+      frames, F, (int64_t)m->H * m->W, m->depth, m->kept, mask, pb, pe);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "classify_list_generic_kernel");
+}
+
 template <int D, int NW, int PPT, int S, int FPS, int KL>
 static ocq_status launch_list_ws_kl(const ocq_model *m, const uint8_t *frames, int F, uint8_t *mask,
                                     cudaStream_t st) {
@@ -431,7 +462,7 @@ static ocq_status launch_list_ws_kl(const ocq_model *m, const uint8_t *frames, i
     count_launch();
     rc = cuda_status(cudaGetLastError(), "classify_pixel_wsl_kernel");
   }
-  if (rc == OCQ_OK) rc = launch_generic(m, frames, F, mask, ntiles * C::TILE, hw, st);
+  if (rc == OCQ_OK) rc = launch_list_generic(m, frames, F, mask, ntiles * C::TILE, hw, st);
   return rc;
 }
 
@@ -544,10 +575,13 @@ ocq_status launch_classify(const ocq_model *m, const uint8_t *frames, int F, uin
     return kClassifyVariants[g_classify_variant].fn[d - 1](m, frames, F, mask, st);
   const bool aligned4 = ((reinterpret_cast<uintptr_t>(frames) | reinterpret_cast<uintptr_t>(mask)) & 3) == 0;
   const bool indexed = m->kind == OCQ_REGION_PIXEL && (d == 4 || d == 5) && m->kept && m->kept_len > 0;
-  if (indexed && g_use_kept >= 2 && aligned && hw % 16 == 0)
-    return kListForms[g_use_kept].fn[d - 4](m, frames, F, mask, st);
-  if (indexed && g_use_kept && aligned4 && hw % 4 == 0)
+  // a list model (no rows) always takes an index form; form 0 then acts as 1
+  const int form = indexed && !m->bits && g_use_kept == 0 ? 1 : g_use_kept;
+  if (indexed && form >= 2 && aligned && hw % 16 == 0)
+    return kListForms[form].fn[d - 4](m, frames, F, mask, st);
+  if (indexed && form && aligned4 && hw % 4 == 0)
     return d == 4 ? launch_pixel_list<4>(m, frames, F, mask, st) : launch_pixel_list<5>(m, frames, F, mask, st);
+  if (indexed && !m->bits) return launch_list_generic(m, frames, F, mask, 0, hw, st);
   if (m->kind == OCQ_REGION_PIXEL && d >= 4 && aligned4 && hw % 4 == 0) {
     const DeepVariant &v = kDeepVariants[g_deep_variant];
     return v.fn[d - 4](m, frames, F, mask, v.cps, st);

@@ -20,15 +20,16 @@ struct ocq_model {
   int H, W, kind, block, depth, T, N;
   int64_t R;           // regions
   int64_t wpr;         // u32 words per region (internal layout)
-  uint32_t *bits;      // device, R * wpr words
+  uint32_t *bits;      // device, R * wpr words; nullptr for a list model (kept-leaf index only)
   size_t bytes;
   cudaStream_t stream; // stream the model was created on (stream-ordered free)
   int device;
   // Pixel regions, depth 4-5, built by the candidate build with k = floor(N/T)
   // <= 8 (no location keeps more than 8 leaves): per pixel location its kept
-  // leaves as 8 u16 planar codes, kKeptNone padding.  A derived index for the
-  // classify; the bitset stays the model.  Valid while kept_len > 0 (a batch
-  // lends every such model a buffer, written only by a candidate build).
+  // leaves as 8 u16 planar codes, kKeptNone padding.  Beside the rows it is a
+  // derived index for the classify; without rows (bits == nullptr, a "list
+  // model") it is the model itself, and export expands it into the bitset
+  // layout.  Valid while kept_len > 0.
   uint16_t *kept;
   int kept_len;  // entries of a list that can hold a kept leaf: 2, 4 or 8; 0 = no valid index
 };
@@ -190,6 +191,13 @@ void deep_variant_describe(int v, int *pxl, int *pf, int *cps);
 int list_form_count();
 int list_form_selected();
 bool list_form_select(int v);
+// List models: per-pixel regions of depth 4-5 whose candidate build keeps at
+// most 8 leaves per location (N <= 255, floor(N / T) <= 8) are built as the
+// kept-leaf index alone, unless switched off (form 0).
+bool list_model_applies(int kind, int depth, int N, int T);
+int list_model_form();
+bool list_model_select(int v);
+ocq_status launch_export_list(const uint16_t *kept, int64_t R, int depth, uint64_t *dst, cudaStream_t st);
 void list_form_describe(int v, int *nw, int *ppt, int *stages, int *fps);
 int block_form_count();
 int block_form_selected();

@@ -89,6 +89,40 @@ ocq_status launch_export(const uint32_t *bits, int64_t R, int depth, uint64_t *d
   return cuda_status(cudaGetLastError(), "export_kernel");
 }
 
+// List models: a warp per location row.  Lane e < 8 turns list entry e into
+// its path code (or an out-of-range value for kKeptNone) and the warp shares
+// the 8 codes; then lane l writes the row's output words l, l + 32, .. : word
+// k holds the bits of the codes in 64k .. 64k+63.  Stores are coalesced and
+// each location's list is read once.
+__global__ void export_list_kernel(const uint16_t *__restrict__ kept, int64_t R, int d, int64_t wpr_out,
+                                   uint64_t *__restrict__ dst) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R; r += warps) {
+    uint32_t mine = 0xFFFFFFFFu;
+    if (lane < 8) {
+      const uint32_t q = __ldg(kept + r * 8 + lane);
+      if (q != kKeptNone) mine = planar_to_path(q, d);
+    }
+    uint32_t c[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) c[e] = __shfl_sync(0xFFFFFFFFu, mine, e);
+    for (int64_t k = lane; k < wpr_out; k += 32) {
+      uint64_t out = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        if (c[e] != 0xFFFFFFFFu && (int64_t)(c[e] >> 6) == k) out |= 1ull << (c[e] & 63);
+      dst[r * wpr_out + k] = out;
+    }
+  }
+}
+
+ocq_status launch_export_list(const uint16_t *kept, int64_t R, int depth, uint64_t *dst, cudaStream_t st) {
+  export_list_kernel<<<grid_for(R * 32, 256, 8), 256, 0, st>>>(kept, R, depth, wpr64(depth), dst);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "export_list_kernel");
+}
+
 ocq_status launch_import(const uint64_t *src, int64_t R, int depth, uint32_t *bits, cudaStream_t st) {
   const int64_t total = R * wpr32(depth);
   import_kernel<<<grid_for(total, 256, 8), 256, 0, st>>>(src, R, depth, wpr64(depth), wpr32(depth), bits);

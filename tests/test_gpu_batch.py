@@ -42,6 +42,8 @@ SMALL_MIX = [
     (0, "bimodal", 29, 37, 15, 6, PIXEL, 0, 2, 5),
     (0, "clusters", 40, 56, 12, 5, PIXEL, 0, 4, 4),
     (0, "sway", 24, 40, 9, 5, PIXEL, 0, 5, 3),
+    (0, "clusters", 13, 23, 10, 4, PIXEL, 0, 4, 5),  # H*W % 4 != 0: rows kept beside the index
+    (0, "bimodal", 12, 20, 30, 3, PIXEL, 0, 5, 2),  # floor(N/T) = 15 > 8: rows, no index
     (0, "bimodal", 16, 1024, 6, 4, PIXEL, 0, 1, 2),
     (0, "clusters", 31, 33, 11, 3, FRAME, 0, 1, 11),
 ]

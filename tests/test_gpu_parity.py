@@ -344,21 +344,50 @@ def test_pixel_deep_classify_variants(ocq, torch):
     frames = ocq_synth.fill_host(sc, 0, 22)
     train, test = frames[:12].copy(), frames[12:]
     train[::2, ::3] = np.random.default_rng(8).integers(0, 256, size=train[::2, ::3].shape, dtype=np.uint8)
-    deep, lst = O.OCQ_TUNE_CLASSIFY_PIXEL_DEEP, O.OCQ_TUNE_CLASSIFY_PIXEL_LIST
-    saved = O.ocq_tune_selected(deep), O.ocq_tune_selected(lst)
+    deep, lst, mf = O.OCQ_TUNE_CLASSIFY_PIXEL_DEEP, O.OCQ_TUNE_CLASSIFY_PIXEL_LIST, O.OCQ_TUNE_PIXEL_MODEL_FORM
+    saved = O.ocq_tune_selected(deep), O.ocq_tune_selected(lst), O.ocq_tune_selected(mf)
     try:
         for d in (4, 5):
             for T in (1, 2, 3, 6, 12):  # lists of 8, 4, 2 codes; T = 1: no list (k = 12 > 8)
                 ow, om = oracle.run(train, d, T, PIXEL, 0, test)
-                for form in range(O.ocq_tune_count(lst)):
-                    O.ocq_tune_select(lst, form)
-                    for v in range(O.ocq_tune_count(deep)) if form == 0 else (saved[0],):
-                        O.ocq_tune_select(deep, v)
-                        words, mask = gpu_model_and_mask(ocq, torch, train, test, d, T, PIXEL, 0)
-                        assert (words == ow).all() and (mask == om).all(), (d, T, form, v)
+                for model_form in (1, 0):  # list model (exported from the lists), rows + lists
+                    O.ocq_tune_select(mf, model_form)
+                    for form in range(O.ocq_tune_count(lst)):
+                        O.ocq_tune_select(lst, form)
+                        for v in range(O.ocq_tune_count(deep)) if form == 0 else (saved[0],):
+                            O.ocq_tune_select(deep, v)
+                            words, mask = gpu_model_and_mask(ocq, torch, train, test, d, T, PIXEL, 0)
+                            assert (words == ow).all() and (mask == om).all(), (d, T, model_form, form, v)
     finally:
         O.ocq_tune_select(deep, saved[0])
         O.ocq_tune_select(lst, saved[1])
+        O.ocq_tune_select(mf, saved[2])
+
+
+def test_list_model_any_alignment(ocq, torch):
+    """List models classify through every launch shape: H*W % 16 != 0 (tail),
+    H*W % 4 != 0 (the one-pixel form), and frames at an odd offset; model
+    export equals the oracle's bitsets."""
+    H_W = ((33, 48), (13, 23), (40, 72))
+    for H, W in H_W:
+        sc = ocq_synth.make_scene("clusters", H, W, 10, 7, seed=H)
+        frames = ocq_synth.fill_host(sc, 0, 17)
+        train, test = frames[:10], frames[10:]
+        for d, T in ((4, 3), (5, 2)):
+            ow, om = oracle.run(train, d, T, PIXEL, 0, test)
+            m = ocq.build_model(torch.from_numpy(train).cuda(), d, T, "pixel")
+            words = ocq.export_model(m).cpu().numpy().view(np.uint64)
+            assert (words == ow).all(), (H, W, d)
+            buf = torch.from_numpy(np.concatenate([np.zeros(1, np.uint8), test.reshape(-1)])).cuda()
+            for off in (0, 1):
+                te = buf[off:off + test.size] if off else buf[1:].clone()
+                mask = torch.empty(test.shape[:3], dtype=torch.uint8, device="cuda")
+                mbuf = torch.empty(mask.numel() + 1, dtype=torch.uint8, device="cuda")
+                out = mbuf[off:off + mask.numel()]
+                ocq.ocq.ocq_classify(m, te, test.shape[0], out, torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                assert (out.cpu().numpy().reshape(om.shape) == om).all(), (H, W, d, off)
+            m.free()
 
 
 @pytest.mark.parametrize("b", [4, 8, 12, 16])
