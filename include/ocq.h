@@ -135,7 +135,12 @@ ocq_status ocq_model_get_info(const ocq_model *model, ocq_model_info *info);
 ocq_status ocq_model_export(const ocq_model *model, uint64_t *dst, size_t words, void *stream);
 
 /* Creates a model from an exported bitset `src` (device) and its header
- * (H, W, region_kind, block, depth are required; T and N are recorded). */
+ * (H, W, region_kind, block, depth are required; T and N are recorded).  When
+ * the header describes a model ocq_build_model would build as a list model
+ * (per-pixel, depth 4-5, 1 <= T <= N <= 255, floor(N/T) <= 8), the bitset is
+ * read into lists: the call then waits for `stream` and returns OCQ_EINVAL if
+ * a pixel location holds more than floor(N/T) leaves (more than N frames can
+ * give leaves kept in T of them). */
 ocq_status ocq_model_import(const uint64_t *src, const ocq_model_info *info, void *stream, ocq_model **out);
 
 /* Frees a model (stream-ordered on the stream it was created on); NULL is ignored. */
@@ -302,7 +307,11 @@ typedef struct ocq_server ocq_server;
  * memory pool of the server's own) at creation, so admission and serving never
  * wait on the allocator.  OCQ_ENOMEM if the device cannot provide them. */
 ocq_status ocq_server_create(size_t hbm_budget, int max_cameras, ocq_server **out);
-/* Device bytes a camera of this description reserves (0 if invalid). */
+/* Device bytes a camera of this description reserves (0 if invalid): two
+ * models (the current one and the one being merged) in the form ocq_build_model
+ * gives the description at admission (for per-pixel regions of depth 4-5 with
+ * floor(N/T) <= 8 a list model, 16 B per location; see
+ * OCQ_TUNE_PIXEL_MODEL_FORM), the ring of N frames and build scratch. */
 size_t ocq_server_camera_footprint(const ocq_camera_desc *desc);
 /* train: device, N*H*W*3 (copied into the ring; M_0 is built from it). */
 ocq_status ocq_server_admit(ocq_server *server, const ocq_camera_desc *desc, const uint8_t *train, int *camera);

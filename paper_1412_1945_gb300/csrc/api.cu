@@ -105,6 +105,15 @@ static ocq_model *new_model(int H, int W, ocq_region region, int depth, int T, i
   return m;
 }
 
+size_t model_bytes(int H, int W, ocq_region region, int depth, int N, int T) {
+  const size_t rows = (size_t)region_count(H, W, region.kind, region.block) * (size_t)wpr32(depth) * sizeof(uint32_t);
+  const size_t index = (size_t)H * W * 8 * sizeof(uint16_t);
+  if (list_model_applies(region.kind, depth, N, T)) return index;
+  const bool indexed = region.kind == OCQ_REGION_PIXEL && (depth == 4 || depth == 5) && N <= 255 && T >= 1 &&
+                       N / T <= 8;
+  return rows + (indexed ? index : 0);
+}
+
 }  // namespace ocq
 
 using namespace ocq;
@@ -262,9 +271,27 @@ ocq_status ocq_model_import(const uint64_t *src, const ocq_model_info *info, voi
   ocq_status rc = check_geometry(info->H, info->W, region, info->depth);
   if (rc != OCQ_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  ocq_model *m = new_model(info->H, info->W, region, info->depth, info->T, info->N, st, &rc);
+  const bool list = list_model_applies(region.kind, info->depth, info->N, info->T);
+  ocq_model *m = new_model(info->H, info->W, region, info->depth, info->T, info->N, st, &rc, !list);
   if (!m) return rc;
-  rc = launch_import(src, m->R, m->depth, m->bits, st);
+  if (list) {  // the form ocq_build_model gives this description: the kept leaves as lists
+    unsigned int *flag = nullptr, overflow = 0;
+    rc = cuda_status(malloc_async((void **)&m->kept, (size_t)m->R * 8 * sizeof(uint16_t), st), "kept-leaf index");
+    if (rc == OCQ_OK) rc = cuda_status(malloc_async((void **)&flag, sizeof *flag, st), "import flag");
+    if (rc == OCQ_OK) rc = cuda_status(cudaMemsetAsync(flag, 0, sizeof *flag, st), "import flag");
+    if (rc == OCQ_OK) rc = launch_import_list(src, m->R, m->depth, info->N / info->T, m->kept, flag, st);
+    if (rc == OCQ_OK) rc = cuda_status(cudaMemcpyAsync(&overflow, flag, sizeof overflow, cudaMemcpyDeviceToHost, st),
+                                       "import flag");
+    if (flag) cudaFreeAsync(flag, st);
+    if (rc == OCQ_OK) rc = cuda_status(cudaStreamSynchronize(st), "import");
+    if (rc == OCQ_OK && overflow) {
+      set_error("ocq_model_import: a pixel location holds more than floor(N/T) = %d leaves", info->N / info->T);
+      rc = OCQ_EINVAL;
+    }
+    m->kept_len = list_length(info->N, info->T);
+  } else {
+    rc = launch_import(src, m->R, m->depth, m->bits, st);
+  }
   if (rc != OCQ_OK) {
     ocq_model_free(m);
     return rc;

@@ -198,6 +198,16 @@ bool list_model_applies(int kind, int depth, int N, int T);
 int list_model_form();
 bool list_model_select(int v);
 ocq_status launch_export_list(const uint16_t *kept, int64_t R, int depth, uint64_t *dst, cudaStream_t st);
+ocq_status launch_import_list(const uint64_t *src, int64_t R, int depth, int limit, uint16_t *kept,
+                              unsigned int *overflow, cudaStream_t st);
+// Entries of a list that can hold a kept leaf when floor(N/T) <= 8: 2, 4 or 8.
+inline int list_length(int N, int T) {
+  const int k = N / T;
+  return k <= 2 ? 2 : k <= 4 ? 4 : 8;
+}
+// Device bytes of a model built from N frames with threshold T (list model,
+// rows with or without the index): what ocq_build_model allocates.
+size_t model_bytes(int H, int W, ocq_region region, int depth, int N, int T);
 void list_form_describe(int v, int *nw, int *ppt, int *stages, int *fps);
 int block_form_count();
 int block_form_selected();

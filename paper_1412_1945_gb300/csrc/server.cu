@@ -72,7 +72,7 @@ struct ocq_server {
 
 static size_t camera_footprint(const ocq_camera_desc &d) {
   const size_t hw = (size_t)d.H * d.W;
-  const size_t model = ocq_model_footprint(d.H, d.W, d.region, d.depth);
+  const size_t model = model_bytes(d.H, d.W, d.region, d.depth, d.N, d.T);
   const size_t ring = (size_t)d.N * hw * 3;
   size_t scratch = 0;
   if (d.region.kind == OCQ_REGION_FRAME) scratch = (size_t)d.N * wpr32(d.depth) * 4;

@@ -123,6 +123,52 @@ ocq_status launch_export_list(const uint16_t *kept, int64_t R, int depth, uint64
   return cuda_status(cudaGetLastError(), "export_list_kernel");
 }
 
+// Import into a list model: a warp per location row.  Lane l scans the row's
+// words l, l + 32, ..; the set bits (path codes) become planar codes, placed by
+// a warp prefix sum over the lanes' counts; the rest of the 8 entries are
+// kKeptNone.  A row with more than `limit` (<= 8) bits cannot be a list of
+// this model: it sets *overflow and its list is left padded.
+__global__ void import_list_kernel(const uint64_t *__restrict__ src, int64_t R, int d, int64_t wpr_in, int limit,
+                                   uint16_t *__restrict__ kept, unsigned int *overflow) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R; r += warps) {
+    const uint64_t *row = src + r * wpr_in;
+    int n = 0;
+    for (int64_t k = lane; k < wpr_in; k += 32) n += __popcll(__ldg(row + k));
+    int before = n;  // inclusive prefix sum of the counts over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xFFFFFFFFu, before, o);
+      if (lane >= o) before += v;
+    }
+    const int total = __shfl_sync(0xFFFFFFFFu, before, 31);
+    uint16_t *list = kept + r * 8;
+    if (total > limit) {
+      if (lane == 0) atomicExch(overflow, 1u);
+      if (lane < 8) list[lane] = kKeptNone;
+      continue;
+    }
+    int at = before - n;  // this lane's first entry
+    for (int64_t k = lane; k < wpr_in && at < before; k += 32) {
+      uint64_t w = __ldg(row + k);
+      while (w) {
+        const int b = __ffsll((long long)w) - 1;
+        w &= w - 1;
+        list[at++] = (uint16_t)path_to_planar((uint32_t)(k * 64 + b), d);
+      }
+    }
+    if (lane >= total && lane < 8) list[lane] = kKeptNone;
+  }
+}
+
+ocq_status launch_import_list(const uint64_t *src, int64_t R, int depth, int limit, uint16_t *kept,
+                              unsigned int *overflow, cudaStream_t st) {
+  import_list_kernel<<<grid_for(R * 32, 256, 8), 256, 0, st>>>(src, R, depth, wpr64(depth), limit, kept, overflow);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "import_list_kernel");
+}
+
 ocq_status launch_import(const uint64_t *src, int64_t R, int depth, uint32_t *bits, cudaStream_t st) {
   const int64_t total = R * wpr32(depth);
   import_kernel<<<grid_for(total, 256, 8), 256, 0, st>>>(src, R, depth, wpr64(depth), wpr32(depth), bits);

@@ -153,6 +153,31 @@ def test_export_import_roundtrip(ocq, torch):
             m.free(), m2.free(), m3.free()
 
 
+def test_list_model_import(ocq, torch):
+    """A header that makes a list model (per pixel, d = 4-5, floor(N/T) <= 8)
+    reads the bitset into lists: export round-trips, an oracle-made model
+    classifies as the oracle does, and a location with more than floor(N/T)
+    leaves is refused with OCQ_EINVAL; other headers keep the rows."""
+    H, W, N = 14, 22, 12
+    sc = ocq_synth.make_scene("clusters", H, W, N, 5, seed=5)
+    frames = ocq_synth.fill_host(sc, 0, N + 5)
+    train, test = frames[:N], frames[N:]
+    t = to_dev(test, torch)
+    for d, T in ((4, 3), (5, 2), (5, 1)):  # k = 4, 6, 12 (the last: rows)
+        ow, om = oracle.run(train, d, T, PIXEL, 0, test)
+        m = ocq.import_model(to_dev(ow.view(np.int64), torch), H, W, PIXEL, 0, d, T=T, N=N)
+        assert (ocq.export_model(m).cpu().numpy().view(np.uint64) == ow).all(), (d, T)
+        assert (ocq.classify(m, t).cpu().numpy() == om).all(), (d, T)
+        m.free()
+        if N // T <= 8:
+            bad = ow.copy()
+            bad[7, :] = 0
+            bad[7, 0] = (1 << (N // T + 1)) - 1  # floor(N/T) + 1 leaves at location 7
+            with pytest.raises(ocq.ocq.OcqError) as e:
+                ocq.import_model(to_dev(bad.view(np.int64), torch), H, W, PIXEL, 0, d, T=T, N=N)
+            assert e.value.status == 1
+
+
 # ---- the preset workloads -----------------------------------------------------------
 
 def _workload_frames(wl, n_test=None):

@@ -193,21 +193,24 @@ def test_serving_preset_cameras_full_size_sampled(cuda_ready):
         srv.destroy()
 
 
-def test_serving_snapshot_and_resume(cuda_ready):
+@pytest.mark.parametrize("kind,block,d", [(BLOCK, 5, 4), (PIXEL, 0, 5)])
+def test_serving_snapshot_and_resume(cuda_ready, kind, block, d):
     """A camera checkpointed after 13 test frames (mid-window; re-merges after
     frames 3, 7, 11) and resumed in a fresh server gives, for frames 13-21,
-    the masks of the window semantics, as if it had never stopped."""
+    the masks of the window semantics, as if it had never stopped.  The
+    per-pixel d = 5 camera (N = 6, T = 3) keeps list models: the snapshot
+    expands one, the resume reads it back into lists."""
     import torch
 
     ocq = cuda_ready
     O = ocq.ocq
-    H, W, kind, block, d, T, N, K, F, cut = 30, 44, BLOCK, 5, 4, 3, 6, 4, 22, 13
+    H, W, T, N, K, F, cut = 30, 44, 3, 6, 4, 22, 13
     sc = ocq_synth.make_scene("sway", H, W, N, F, 123)
     host = ocq_synth.fill_host(sc, 0, N + F)
     dev = torch.from_numpy(host).cuda()
     masks = torch.full((F, H, W), 9, dtype=torch.uint8, device="cuda")
     wpr = max(1, 8 ** d // 64)
-    regions = -(-H // block) * -(-W // block)
+    regions = -(-H // block) * -(-W // block) if kind == BLOCK else H * W
     words = torch.zeros((regions, wpr), dtype=torch.int64, device="cuda")
     ring = torch.zeros((N, H, W, 3), dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
