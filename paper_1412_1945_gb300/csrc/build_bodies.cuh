@@ -821,7 +821,8 @@ __device__ __forceinline__ void build_pixel_ws_body(const uint8_t *__restrict__ 
   int s = 0;
   uint32_t round = 0;
   for (int64_t i = 0; i < my_tiles; ++i) {
-    uint32_t words = 0;  // model words (32 leaves each) this pixel touched
+    uint32_t words = 0;     // KEPT: model words (32 leaves each) this pixel touched
+    uint64_t touched = 0;   // else: groups of 8 leaves (two counter words) this pixel touched
     uint32_t kept[C::WPR];
 #pragma unroll
     for (int w = 0; w < C::WPR; ++w) kept[w] = 0;
@@ -846,10 +847,11 @@ __device__ __forceinline__ void build_pixel_ws_body(const uint8_t *__restrict__ 
               for (int w = 0; w < C::WPR; ++w)
                 if ((int)(q >> 5) == w) kept[w] |= 1u << (q & 31);
             }
+            words |= 1u << (q >> 5);
           } else {
             red_add_shared(&cnt[(q >> 2) * NT + t], 1u << sh);
+            touched |= 1ull << (q >> 3);
           }
-          words |= 1u << (q >> 5);
         }
       }
       __syncwarp();
@@ -880,23 +882,27 @@ __device__ __forceinline__ void build_pixel_ws_body(const uint8_t *__restrict__ 
 #pragma unroll
         for (int w = 0; w < C::WPR; ++w) dst[w] = 0;
       }
-      for (; words; words &= words - 1) {
-        const int w = __ffs(words) - 1;
-        uint32_t o = 0;
+      // threshold only the counter words of the 8-leaf groups that occurred,
+      // in increasing order, so each model word is assembled then stored once
+      int cur = -1;
+      uint32_t o = 0;
+      for (; touched; touched &= touched - 1) {
+        const int g = __ffsll((long long)touched) - 1;
+        if ((g >> 2) != cur) {
+          if (cur >= 0) dst[cur] = o;
+          cur = g >> 2, o = 0;
+        }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (w * 8 + c < C::CW) {
-            uint32_t *cp = &cnt[(w * 8 + c) * NT + t];
-            const uint32_t v = *cp;
-            if (v) {
-              const uint32_t ge = __vcmpgeu4(v, T * 0x01010101u);
-              o |= (((ge >> 7) & 1u) | ((ge >> 14) & 2u) | ((ge >> 21) & 4u) | ((ge >> 28) & 8u)) << (4 * c);
-              *cp = 0;
-            }
+        for (int c = 0; c < 2; ++c) {
+          if (2 * g + c < C::CW) {
+            uint32_t *cp = &cnt[(2 * g + c) * NT + t];
+            const uint32_t ge = __vcmpgeu4(*cp, T * 0x01010101u);
+            o |= (((ge >> 7) & 1u) | ((ge >> 14) & 2u) | ((ge >> 21) & 4u) | ((ge >> 28) & 8u)) << ((g & 3) * 8 + 4 * c);
+            *cp = 0;
           }
         }
-        dst[w] = o;
       }
+      if (cur >= 0) dst[cur] = o;
     }
   }
 }
