@@ -67,6 +67,28 @@ def test_host_side_helpers(lib):
     assert ocq.ocq_model_footprint(120, 160, ocq.OCQ_REGION_FRAME, 0, 9) == 0
 
 
+def test_camera_footprint_follows_the_model_form(lib):
+    """A camera reserves two models of the form ocq_build_model gives its
+    description, plus its ring: per-pixel d = 5 with floor(N/T) <= 8 is a
+    list model (16 B per location), with floor(N/T) > 8 rows (4 KB per
+    location), and with list models switched off rows plus the lists."""
+    from paper_1412_1945_gb300 import ocq
+
+    H, W, N, K = 1080, 1920, 30, 30
+    hw, ring = H * W, N * H * W * 3
+    pix = ocq.OCQ_REGION_PIXEL
+    assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 5, 10, N, K) == 2 * hw * 16 + ring
+    assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 5, 3, N, K) == 2 * hw * 4096 + ring
+    assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 3, 10, N, K) == 2 * hw * 64 + ring
+    mf = ocq.OCQ_TUNE_PIXEL_MODEL_FORM
+    saved = ocq.ocq_tune_selected(mf)
+    try:
+        ocq.ocq_tune_select(mf, 0)
+        assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 5, 10, N, K) == 2 * hw * (4096 + 16) + ring
+    finally:
+        ocq.ocq_tune_select(mf, saved)
+
+
 @pytest.mark.parametrize("N,H,W,kind,block,depth,T", [
     (0, 8, 8, 0, 0, 3, 1),      # N < 1
     (4, 8, 8, 0, 0, 3, 5),      # T > N

@@ -153,6 +153,30 @@ def test_export_import_roundtrip(ocq, torch):
             m.free(), m2.free(), m3.free()
 
 
+def test_list_model_full_lists(ocq, torch):
+    """Lists at capacity: 16 frames cycling through 8 colours, T = 2, so every
+    location keeps exactly floor(N/T) = 8 leaves (all 8 entries used); a
+    ninth colour and the kept ones classify as the oracle says, in every
+    classify form."""
+    cols = np.array([[0, 0, 0], [255, 0, 0], [0, 255, 0], [0, 0, 255], [255, 255, 0], [255, 0, 255],
+                     [0, 255, 255], [255, 255, 255], [128, 64, 32]], dtype=np.uint8)
+    H, W = 16, 36
+    train = np.broadcast_to(cols[np.arange(16) % 8][:, None, None, :], (16, H, W, 3)).copy()
+    test = np.broadcast_to(cols[np.arange(9)][:, None, None, :], (9, H, W, 3)).copy()
+    lst = ocq.ocq.OCQ_TUNE_CLASSIFY_PIXEL_LIST
+    saved = ocq.ocq.ocq_tune_selected(lst)
+    try:
+        for d in (4, 5):
+            ow, om = oracle.run(train, d, 2, PIXEL, 0, test)
+            assert om[:8].sum() == 0 and om[8].all()
+            for form in range(ocq.ocq.ocq_tune_count(lst)):
+                ocq.ocq.ocq_tune_select(lst, form)
+                words, mask = gpu_model_and_mask(ocq, torch, train, test, d, 2, PIXEL, 0)
+                assert (words == ow).all() and (mask == om).all(), (d, form)
+    finally:
+        ocq.ocq.ocq_tune_select(lst, saved)
+
+
 def test_list_model_import(ocq, torch):
     """A header that makes a list model (per pixel, d = 4-5, floor(N/T) <= 8)
     reads the bitset into lists: export round-trips, an oracle-made model

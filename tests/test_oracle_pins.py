@@ -245,6 +245,25 @@ def test_monotone_in_T(kind, block):
         prev = m
 
 
+def test_pixel_location_keeps_at_most_N_over_T_leaves():
+    """Per pixel location each frame's tree holds exactly one leaf, so a leaf
+    in T or more trees uses up T of the N frames: at most floor(N/T) leaves
+    survive the merge (the bound that makes 8-entry kept-leaf lists exact when
+    floor(N/T) <= 8), and the bound is reached when the frames cycle through
+    floor(N/T) colours."""
+    train, _ = _random_video(23, 12, 5, 7, ncol=4)
+    for d in (4, 5):
+        for T in (1, 2, 3, 4, 6, 12):
+            m = oracle.build_model(train, d, T, PIXEL, 0)
+            per_loc = np.array([bin(int(w)).count("1") for w in m.reshape(-1)]).reshape(m.shape).sum(axis=1)
+            assert per_loc.max() <= 12 // T, (d, T)
+    # k = floor(12 / 3) = 4 colours, each in exactly 3 of the 12 frames
+    cols = np.array([[0, 0, 0], [255, 0, 0], [0, 255, 0], [0, 0, 255]], dtype=np.uint8)
+    cyc = np.broadcast_to(cols[np.arange(12) % 4][:, None, None, :], (12, 2, 3, 3)).copy()
+    m = oracle.build_model(cyc, 4, 3, PIXEL, 0)
+    assert all(sum(bin(int(w)).count("1") for w in row) == 4 for row in m)
+
+
 @pytest.mark.parametrize("kind,block", [(FRAME, 0), (BLOCK, 4), (PIXEL, 0)])
 def test_permutation_invariance(kind, block):
     train, g = _random_video(13, 7, 6, 8)
