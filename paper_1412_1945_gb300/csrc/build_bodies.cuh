@@ -618,9 +618,12 @@ __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ 
   const bool valid = p < hw;
   const uint8_t *px = frames + (valid ? p : 0) * 3;
   const int64_t fstride = hw * 3;
+  // a counter at zero holds the key kNoKey, which no leaf code equals, so a
+  // key match alone tells a live candidate
+  constexpr uint32_t kNoKey = 0xFFFFFFFFu;
   uint32_t key[KM > 0 ? KM : 1], cnt[KM > 0 ? KM : 1];
 #pragma unroll
-  for (int i = 0; i < (KM > 0 ? KM : 1); ++i) key[i] = 0u, cnt[i] = 0u;
+  for (int i = 0; i < (KM > 0 ? KM : 1); ++i) key[i] = kNoKey, cnt[i] = 0u;
   for (int f0 = 0; f0 < N; f0 += PF) {
     uint32_t yv[PF];
 #pragma unroll
@@ -643,15 +646,16 @@ __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ 
           bool hit = false;
 #pragma unroll
           for (int i = 0; i < KM; ++i)
-            if (cnt[i] && key[i] == q) ++cnt[i], hit = true;
+            if (key[i] == q) ++cnt[i], hit = true;
           if (!hit) {
             bool placed = false;
 #pragma unroll
             for (int i = 0; i < KM; ++i)
               if (!placed && !cnt[i]) key[i] = q, cnt[i] = 1u, placed = true;
-            if (!placed) {
+            if (!placed) {  // every counter is >= 1 here
 #pragma unroll
-              for (int i = 0; i < KM; ++i) --cnt[i];
+              for (int i = 0; i < KM; ++i)
+                if (--cnt[i] == 0u) key[i] = kNoKey;
             }
           }
         }
@@ -666,10 +670,16 @@ __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ 
     if (valid)
       for (int f = 0; f < N; ++f) {
         const uint32_t q = codes[f * 32 + lane];
-        const int g = GRP ? f / group : f;
+        if constexpr (GRP) {  // count each group once
+          const int g = f / group;
 #pragma unroll
-        for (int i = 0; i < KM; ++i)
-          if (cnt[i] && key[i] == q && last[i] != g) ++exact[i], last[i] = g;
+          for (int i = 0; i < KM; ++i)
+            if (key[i] == q && last[i] != g) ++exact[i], last[i] = g;
+        } else {  // one leaf per frame: a frame matches a key at most once
+#pragma unroll
+          for (int i = 0; i < KM; ++i)
+            if (key[i] == q) ++exact[i];
+        }
       }
   }
   const int64_t np = hw - p0 < 32 ? hw - p0 : 32;
