@@ -434,9 +434,13 @@ ocq_status ocq_batch_debug_hold_builds(ocq_batch *batch, int stream);
  * (depth d and N with (bit_length(N) + 2) * max(1, 8^d/32) * 4 bytes above
  * 16 MiB) return OCQ_EINVAL with a message.  It calls no cudaMalloc/cudaFree.
  * The first call on a device resolves the array's device address (with that
- * device current); make that first call before any stream capture.  Every
- * call shares the array and clears what it needs: calls whose work may
- * overlap on the GPU race and must be ordered by the caller.
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not call the entry point on a device
+ * after its primary context was reset (cudaDeviceReset), since the kept
+ * address is then stale.  All calls on one device share that device's array
+ * and each clears what it needs: calls on the same device whose work may
+ * overlap (different streams or host threads) race and must be ordered by
+ * the caller; calls on different devices use separate arrays.
  */
 ocq_status ocq_build_frame_noalloc(const uint8_t *frames, int N, int H, int W, int depth, int T, uint64_t *model,
                                    void *stream);

@@ -28,6 +28,8 @@ cudaError_t malloc_async(void **p, size_t bytes, cudaStream_t st) {
 PoolScope::PoolScope(cudaMemPool_t pool) : prev_(t_pool) { t_pool = pool; }
 PoolScope::~PoolScope() { t_pool = prev_; }
 
+void clear_error() { g_err[0] = 0; }
+
 void set_error(const char *fmt, ...) {
   va_list ap;
   va_start(ap, fmt);

@@ -949,9 +949,10 @@ ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t
 // processing path.  For them ocq_build_frame_noalloc builds a whole-frame
 // model into a buffer the caller owns, using as scratch one statically sized
 // device array of this file (kNoAllocScratchBytes on every GPU that loads the
-// library, held until the process exits).  All calls share the array, so calls
-// whose work overlaps on the GPU (different streams, or devices racing on the
-// same setup) must be ordered by the caller; each call clears what it needs.
+// library, held until the process exits).  All calls on one device share that
+// device's array, so calls on the same device whose work may overlap
+// (different streams or host threads) must be ordered by the caller; calls on
+// different devices use separate arrays.  Each call clears what it needs.
 
 static constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocScratchBytes / 4];
@@ -961,7 +962,9 @@ static uint32_t *g_noalloc_ptr[256];  // device address of the array, per device
 
 // Device address of the scratch array on the current device.  The host-side
 // symbol g_noalloc_scratch is not a device address, so it is resolved once per
-// device (with that device current) and cached.
+// device (with that device current) and cached for the life of the process;
+// a reset of the device's primary context (cudaDeviceReset) invalidates the
+// cached address, so the entry point is not to be used after one.
 static ocq_status noalloc_scratch(uint32_t **out) {
   int dev = 0;
   ocq_status rc = cuda_status(cudaGetDevice(&dev), "cudaGetDevice");
@@ -987,6 +990,7 @@ using namespace ocq;
 
 extern "C" ocq_status ocq_build_frame_noalloc(const uint8_t *frames, int N, int H, int W, int depth, int T,
                                               uint64_t *model, void *stream) {
+  clear_error();
   if (!frames || !model || H < 1 || W < 1 || depth < 1 || depth > 8 || N < 1 || N > 65535 || T < 1 || T > N ||
       (int64_t)N * H * W >= ((int64_t)1 << 40)) {
     set_error("ocq_build_frame_noalloc: need frames, model != NULL, H, W >= 1, 1 <= depth <= 8, "

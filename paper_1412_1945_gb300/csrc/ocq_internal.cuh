@@ -40,6 +40,7 @@ namespace ocq {
 
 // ---- host-side helpers (api.cu) --------------------------------------------
 void set_error(const char *fmt, ...);
+void clear_error();  // empties the calling thread's last-error text
 ocq_status cuda_status(cudaError_t e, const char *what);
 int sm_count();
 // cudaMallocAsync from the pool the calling thread selected with PoolScope

@@ -329,7 +329,22 @@ def ocq_tune_describe(kernel: int, variant: int):
 
 def ocq_build_frame_noalloc(frames, N, H, W, depth, T, model, stream=None):
     """Whole-frame model into the caller's device buffer ``model``
-    (max(1, 8^depth/64) u64 words, exported layout); allocates nothing."""
+    (max(1, 8^depth/64) u64 words, exported layout); allocates nothing.
+
+    The C entry point takes no buffer lengths, so tensors are checked here
+    (CUDA, contiguous, large enough) before the call; raw integer addresses
+    are passed through unchecked."""
+    if not isinstance(frames, int) and frames is not None:
+        if not (frames.is_cuda and frames.is_contiguous() and frames.element_size() == 1):
+            raise ValueError("frames must be a contiguous CUDA tensor of bytes (uint8)")
+        if frames.numel() < N * H * W * 3:
+            raise ValueError(f"frames holds {frames.numel()} bytes; N*H*W*3 = {N * H * W * 3} are read")
+    if not isinstance(model, int) and model is not None:
+        words = max(1, 8 ** depth // 64) if 1 <= depth <= 8 else 1
+        if not (model.is_cuda and model.is_contiguous() and model.element_size() == 8):
+            raise ValueError("model must be a contiguous CUDA tensor of 8-byte words (int64/uint64)")
+        if model.numel() < words:
+            raise ValueError(f"model holds {model.numel()} words; depth {depth} writes {words}")
     _check(load().ocq_build_frame_noalloc(_p(frames), N, H, W, depth, T, _p(model), _s(stream)))
 
 

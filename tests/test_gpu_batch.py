@@ -1,7 +1,7 @@
 """Batched form: every stream's model and masks from the one persistent,
-graph-replayed launch equal the plain per-stream path (bit-exact), which the
-other tests tie to the oracle; a few streams are also checked against the
-oracle directly."""
+graph-replayed launch equal the plain per-stream path and the oracle
+(bit-exact): every stream of the small mix in full, every stream of the
+64-stream preset at sampled regions."""
 import numpy as np
 import pytest
 
@@ -80,7 +80,7 @@ def test_batch_small_mix_matches_plain_and_oracle(ocq, mode, staging):
                 pw, pm = _plain(ocq, s)
                 assert (words == pw).all(), (rep, i)
                 assert (s["mask"].cpu().numpy() == pm).all(), (rep, i)
-        for i in (0, 4, 6, 9):
+        for i in range(len(S)):
             s = S[i]
             ow, om = oracle.run(s["host_train"], s["depth"], s["T"], s["kind"], s["block"], s["host_test"])
             assert (ocq.export_model(b.model(i)).cpu().numpy().view(np.uint64) == ow).all(), i
@@ -117,9 +117,45 @@ def test_batch_tiles_and_autotune_keep_results(ocq):
         b.destroy()
 
 
+def _sampled_oracle_check(ocq, s, model, mask, rng):
+    """Stream ``s`` against the oracle at sampled regions: regions are
+    independent (Sec. 3), so a block (or a set of pixel locations) cropped out
+    of every frame is its own video.  Whole-frame streams: the model in full
+    and the masks of three test frames."""
+    import torch
+
+    H, W, F, d, T, kind, b = s["H"], s["W"], s["F"], s["depth"], s["T"], s["kind"], s["block"]
+    words = ocq.export_model(model)
+    if kind == FRAME:
+        ow, om = oracle.run(s["train"].cpu().numpy(), d, T, FRAME, 0, s["test"][[0, F // 2, F - 1]].cpu().numpy())
+        assert (words.cpu().numpy().view(np.uint64) == ow).all()
+        assert (mask[[0, F // 2, F - 1]].cpu().numpy() == om).all()
+    elif kind == BLOCK:
+        bh, bw = (H + b - 1) // b, (W + b - 1) // b
+        picks = {0, bh * bw - 1, bw - 1, (bh - 1) * bw} | set(rng.integers(0, bh * bw, size=12).tolist())
+        for r in sorted(picks):
+            y0, x0 = (r // bw) * b, (r % bw) * b
+            tr = s["train"][:, y0:y0 + b, x0:x0 + b].contiguous().cpu().numpy()
+            te = s["test"][:, y0:y0 + b, x0:x0 + b].contiguous().cpu().numpy()
+            ow, om = oracle.run(tr, d, T, BLOCK, b, te)
+            assert (words[r].cpu().numpy().view(np.uint64) == ow[0]).all(), r
+            assert (mask[:, y0:y0 + b, x0:x0 + b].cpu().numpy() == om).all(), r
+    else:
+        hw = H * W
+        picks = {0, 1, 127, 128, hw // 2, hw - 1} | set(rng.integers(0, hw, size=200).tolist())
+        idx = np.array(sorted(picks), np.int64)
+        ys, xs = torch.from_numpy(idx // W).cuda(), torch.from_numpy(idx % W).cuda()
+        ow, om = oracle.run(s["train"][:, ys, xs].cpu().numpy()[:, None], d, T, PIXEL, 0,
+                            s["test"][:, ys, xs].cpu().numpy()[:, None])
+        assert (words[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint64) == ow).all()
+        assert (mask[:, ys, xs].cpu().numpy() == om[:, 0]).all()
+
+
 def test_batch_64_stream_preset_matches_plain(ocq):
     """The 64-stream preset (resolutions up to 1920x1080, depth 3-5, 1x1 /
-    8x8 / whole-frame regions), frames generated on the device."""
+    8x8 / whole-frame regions), frames generated on the device: both forms
+    equal the plain path, and every stream equals the oracle at sampled
+    regions."""
     import torch
 
     descs = []
@@ -149,5 +185,8 @@ def test_batch_64_stream_preset_matches_plain(ocq):
             same_mask = (s["mask"] == pmask).all().item()
             m.free()
             assert same_model and same_mask, i
+        rng = np.random.default_rng(64)
+        for i, s in enumerate(descs):
+            _sampled_oracle_check(ocq, s, b.model(i), s["mask"], rng)
     finally:
         b.destroy()
