@@ -52,9 +52,11 @@ def test_noalloc_rejects_oversized_requests(cuda_ready):
     ocq = cuda_ready
     frames = torch.zeros((1, 2, 2, 3), dtype=torch.uint8, device="cuda")
     out = torch.zeros(1 << 18, dtype=torch.int64, device="cuda")
-    # depth 8 needs 2 MiB per scratch row; N = 65535 needs 16 planes + 2 rows
+    # depth 8 needs 2 MiB per scratch row; N = 65535 needs 16 planes + 2 rows.
+    # The library refuses the size before it reads any frame, so the raw
+    # address goes past the binding's buffer checks to the C entry point.
     with pytest.raises(ocq.OcqError) as e:
-        ocq.ocq.ocq_build_frame_noalloc(frames, 65535, 2, 2, 8, 1, out)
+        ocq.ocq.ocq_build_frame_noalloc(frames.data_ptr(), 65535, 2, 2, 8, 1, out)
     assert e.value.status == ocq.ocq.OCQ_EINVAL and "maximum" in str(e.value)
 
 
