@@ -385,6 +385,12 @@ void ocq_server_destroy(ocq_server *server);
  *                            each location as a 16 B list and no leaf bitset (export
  *                            expands it into the bitset layout); 0 the bitset rows
  *                            plus that list; params = {variant, 0, ...}
+ *   OCQ_TUNE_BUILD_BLOCK     block build with b <= 16 and N <= 255: 1 (default)
+ *                            warps over 16 x 16 pixel tiles (four 8 x 8 or one
+ *                            16 x 16 region, 8 pixels per lane) where b is 8 or 16,
+ *                            depth is 2-5, W % 8 == 0 and the frames are 8-byte
+ *                            aligned, else one warp per region; 0 one warp per
+ *                            region always; params = {variant, 0, ...}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5
@@ -396,7 +402,8 @@ enum {
   OCQ_TUNE_CLASSIFY_PIXEL_DEEP = 2,
   OCQ_TUNE_CLASSIFY_BLOCK_DEEP = 3,
   OCQ_TUNE_CLASSIFY_PIXEL_LIST = 4,
-  OCQ_TUNE_PIXEL_MODEL_FORM = 5
+  OCQ_TUNE_PIXEL_MODEL_FORM = 5,
+  OCQ_TUNE_BUILD_BLOCK = 6
 };
 int ocq_tune_count(int kernel);
 int ocq_tune_selected(int kernel);

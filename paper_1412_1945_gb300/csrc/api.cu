@@ -331,6 +331,7 @@ int ocq_tune_count(int kernel) {
   if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) return block_form_count();
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_LIST) return list_form_count();
   if (kernel == OCQ_TUNE_PIXEL_MODEL_FORM) return 2;
+  if (kernel == OCQ_TUNE_BUILD_BLOCK) return block_build_form_count();
   return -1;
 }
 
@@ -341,6 +342,7 @@ int ocq_tune_selected(int kernel) {
   if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) return block_form_selected();
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_LIST) return list_form_selected();
   if (kernel == OCQ_TUNE_PIXEL_MODEL_FORM) return list_model_form();
+  if (kernel == OCQ_TUNE_BUILD_BLOCK) return block_build_form_selected();
   return -1;
 }
 
@@ -353,6 +355,7 @@ ocq_status ocq_tune_select(int kernel, int variant) {
   if (kernel == OCQ_TUNE_CLASSIFY_BLOCK_DEEP) ok = block_form_select(variant);
   if (kernel == OCQ_TUNE_CLASSIFY_PIXEL_LIST) ok = list_form_select(variant);
   if (kernel == OCQ_TUNE_PIXEL_MODEL_FORM) ok = list_model_select(variant);
+  if (kernel == OCQ_TUNE_BUILD_BLOCK) ok = block_build_form_select(variant);
   if (!ok) {
     set_error("ocq_tune_select: no variant %d of kernel %d", variant, kernel);
     return OCQ_EINVAL;

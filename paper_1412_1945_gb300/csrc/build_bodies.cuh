@@ -465,6 +465,293 @@ __device__ __forceinline__ void build_block_warp_body(const uint8_t *__restrict_
   }
 }
 
+// ---- block regions of 8 x 8 or 16 x 16 pixels, warp tiles ------------------------
+// A warp covers a tile of 16 x 16 pixels: four 8 x 8 block regions or one
+// 16 x 16 region.  Lane l owns the 8 consecutive pixels of tile row l / 2 in
+// its left (l even) or right half, read per frame as three 8-byte loads and
+// split into pixels with byte permutes, so all of a lane's pixels lie in one
+// region.  The loads of the next frames are in flight while the current ones
+// are counted (two register buffers of PF frames).  The table holds, per leaf
+// of the region, the last frame that counted it and the number of frames that
+// did (the per-frame tree of Alg. 1 holds a leaf once, however many pixels
+// reach it; Alg. 2 counts trees):
+//   * direct tables (depth <= 3, and depth 4 with one region per tile): a u16
+//     entry (frame + 1) << 8 | count per leaf, at a bijective XOR-shuffle of the
+//     leaf code (so leaves that differ only in their blue bits do not share a
+//     bank) and with each region's table skewed by 8 banks.  A lane rewrites
+//     its leaf's entry only while the frame field is older than the current
+//     frame, so lanes holding the same leaf in the same frame store the same
+//     value and the leaf is counted once per frame with no atomic;
+//   * hashed tables (otherwise): u32 entries (leaf + 1) << 16 | (frame + 1) << 8
+//     | count in buckets of 4 (one 16-byte load finds a leaf among them), 4
+//     (depth 4) or 8 (depth 5) slots per pixel of the region, linear probing
+//     over buckets; only a leaf claiming an empty slot uses atomicCAS.  A region
+//     whose table passes 3/4 full stops counting and is recounted by the
+//     chunked passes of the one-warp-per-region build, so no result depends on
+//     the table's size.
+// A lane reads the entries of all its pixels of a frame before it writes any:
+// the new value is a function of the old one and the frame, so a lane holding
+// the same leaf twice writes the same value twice.  One __syncwarp per frame
+// orders frame f's updates before frame f + 1's.
+template <int D, int B>
+struct BlockTileCfg {
+  static constexpr int RPT = (16 / B) * (16 / B);  // regions per tile
+  static constexpr int NPX = B * B;                // pixels per region
+  static constexpr int NC = 1 << (3 * D);
+  static constexpr bool DIRECT = D <= 3 || (D == 4 && B == 16);
+  static constexpr int S = DIRECT ? NC : (D == 4 ? 4 : 8) * NPX;  // entries per region table
+  static constexpr int SS = DIRECT ? S + 16 : S + 8;               // entries between regions (8-bank skew)
+  static constexpr int NB = S / 4;                                  // hashed: buckets per region
+  static constexpr int LOGNB = NB >= 512 ? 9 : NB >= 128 ? 7 : NB >= 64 ? 6 : 5;
+  static constexpr int LIM = 3 * S / 4;
+  static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  static constexpr int TABLE_BYTES = (RPT * SS * (DIRECT ? 2 : 4) + 15) & ~15;
+  static constexpr int WARP_SMEM = TABLE_BYTES + 16;  // + RPT insert counters
+  // 256-thread CTAs resident per SM the kernel is compiled for (registers)
+  static constexpr int MINB = D == 5 && B == 16 ? 2 : 3;
+  static constexpr int PF = DIRECT ? 4 : 2;  // frames per register buffer
+};
+
+// Planar code of a masked pixel word (bytes r_d, g_d, b_d; byte 3 ignored)
+// with one byte dot product at every depth <= 5.
+template <int D>
+__device__ __forceinline__ uint32_t planar_dp(uint32_t t) {
+  if constexpr (D <= 3)
+    return __dp4a(t, 1u | ((1u << D) << 8) | ((1u << (2 * D)) << 16), 0u);
+  else
+    return __dp4a(t, 1u | ((1u << D) << 8), (t >> (16 - 2 * D)) & (0xFFu << (2 * D)));
+}
+
+// 16-byte shared-memory load that is not cached or merged with other accesses.
+__device__ __forceinline__ uint4 lds128_volatile(const void *p) {
+  uint4 v;
+  asm volatile("ld.volatile.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(smem_addr(p))
+               : "memory");
+  return v;
+}
+
+// Slot of leaf q in a direct table: a bijection of [0, 2^15) (each bit XORed
+// with higher bits only).
+__device__ __forceinline__ uint32_t tile_slot(uint32_t q) { return q ^ (q >> 5) ^ (q >> 10); }
+
+// Packed pixel k (0..7) of 24 bytes held as 6 words.
+template <int K>
+__device__ __forceinline__ uint32_t oct_pixel(const uint32_t (&w)[6]) {
+  constexpr int o = 3 * K, i = o / 4, s = o % 4;
+  constexpr uint32_t sel = (uint32_t)(s | ((s + 1) << 4) | ((s + 2) << 8) | ((s + 2) << 12));
+  if constexpr (i + 1 < 6)
+    return __byte_perm(w[i], w[i + 1], sel);
+  else
+    return __byte_perm(w[i], 0u, sel);
+}
+
+// Hashed table: counts leaf q (key = (q + 1) << 16) of frame f (fh = (f + 1) << 8)
+// given the home bucket's entries `bk` read earlier in the frame.
+template <int D, int B>
+__device__ __forceinline__ void tile_hash_count(uint32_t *tab, uint32_t *ins, uint32_t hb, uint4 bk, uint32_t key,
+                                                uint32_t fh) {
+  using C = BlockTileCfg<D, B>;
+  volatile uint32_t *vt = tab;
+  const uint32_t e4[4] = {bk.x, bk.y, bk.z, bk.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if ((e4[j] & 0xFFFF0000u) == key) {  // the common case: the leaf is in its home bucket
+      if ((e4[j] & 0xFF00u) < fh) vt[4 * hb + j] = key | fh | ((e4[j] + 1u) & 0xFFu);
+      return;
+    }
+  for (int probe = 0; probe < C::NB; ++probe) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t s = 4 * hb + j;
+      uint32_t e = vt[s];
+      if (e == 0u) {
+        e = atomicCAS(&tab[s], 0u, key | fh | 1u);
+        if (e == 0u) {
+          atomicAdd(ins, 1u);
+          return;
+        }
+      }
+      if ((e & 0xFFFF0000u) == key) {
+        if ((e & 0xFF00u) < fh) vt[s] = key | fh | ((e + 1u) & 0xFFu);
+        return;
+      }
+    }
+    hb = (hb + 1u) & (C::NB - 1);
+  }
+  atomicAdd(ins, (uint32_t)C::S);  // no free slot: recount the region
+}
+
+// Warp w of the caller handles tiles t = t_first, t_first + t_step, ... < t_end
+// (row-major over ceil(H/16) x ceil(W/16) tiles).  Needs b in {8, 16},
+// W % 8 == 0, 8-byte aligned frames, N <= 255, H*W*3 < 2^32.
+// wsm: this warp's WARP_SMEM bytes (16-byte aligned), zero on entry and on return.
+template <int D, int B, int PF>
+__device__ __forceinline__ void build_block_tile_body(const uint8_t *__restrict__ frames, int N, int H, int W, int bw,
+                                                      uint32_t T, uint32_t *__restrict__ model, int64_t t_first,
+                                                      int64_t t_end, int64_t t_step, uint8_t *wsm) {
+  using C = BlockTileCfg<D, B>;
+  const int lane = threadIdx.x & 31;
+  const int trow = lane >> 1, half = lane & 1;
+  const int tiles_x = (W + 15) >> 4;
+  const int64_t fstride = (int64_t)H * W * 3;
+  const int ri = B == 8 ? (((trow >> 3) << 1) | half) : 0;  // the lane's region within the tile
+  uint32_t *ins = reinterpret_cast<uint32_t *>(wsm + C::TABLE_BYTES);
+  uint16_t *t16 = reinterpret_cast<uint16_t *>(wsm) + ri * C::SS;
+  uint32_t *t32 = reinterpret_cast<uint32_t *>(wsm) + ri * C::SS;
+  for (int64_t t = t_first; t < t_end; t += t_step) {
+    const int ty = (int)(t / tiles_x), tx = (int)(t - (int64_t)ty * tiles_x);
+    const int y = ty * 16 + trow, x = tx * 16 + half * 8;
+    const bool active = y < H && x < W;
+    const uint8_t *src = frames + ((int64_t)y * W + x) * 3;
+    bool skip = !active;
+    auto load = [&](uint32_t (&v)[PF][6], int f0) {
+#pragma unroll
+      for (int j = 0; j < PF; ++j)
+        if (active && f0 + j < N) {
+          const uint2 *s = reinterpret_cast<const uint2 *>(src + (int64_t)(f0 + j) * fstride);
+          const uint2 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2);
+          v[j][0] = a.x, v[j][1] = a.y, v[j][2] = b.x, v[j][3] = b.y, v[j][4] = c.x, v[j][5] = c.y;
+        }
+    };
+    auto count = [&](const uint32_t (&v)[PF][6], int f0) {
+#pragma unroll
+      for (int j = 0; j < PF; ++j) {
+        if (f0 + j >= N) break;
+        if (!skip) {
+          const uint32_t f = (uint32_t)(f0 + j);
+          uint32_t m[6];
+#pragma unroll
+          for (int i = 0; i < 6; ++i) m[i] = (v[j][i] >> (8 - D)) & byte_mask(D);
+          uint32_t q[8];
+          static_for<0, 8>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            q[k] = planar_dp<D>(oct_pixel<k>(m));
+          });
+          if constexpr (C::DIRECT) {
+            volatile uint16_t *vt = t16;
+            const uint32_t fh = (f + 1u) << 8;
+            uint32_t e[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) e[k] = vt[tile_slot(q[k])];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (e[k] < fh) vt[tile_slot(q[k])] = (uint16_t)(fh | ((e[k] + 1u) & 0xFFu));
+          } else {
+            const uint32_t fh = (f + 1u) << 8;
+#pragma unroll
+            for (int g = 0; g < 8; g += 4) {
+              uint32_t hb[4];
+              uint4 bk[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                hb[k] = (q[g + k] * 2654435761u) >> (32 - C::LOGNB);
+                bk[k] = lds128_volatile(t32 + 4 * hb[k]);
+              }
+#pragma unroll
+              for (int k = 0; k < 4; ++k) tile_hash_count<D, B>(t32, ins + ri, hb[k], bk[k], (q[g + k] + 1u) << 16, fh);
+            }
+          }
+        }
+        __syncwarp();
+        if constexpr (!C::DIRECT) skip = skip || *(volatile uint32_t *)(ins + ri) > (uint32_t)C::LIM;
+      }
+    };
+    {
+      uint32_t va[PF][6], vb[PF][6];
+      load(va, 0);
+      for (int f0 = 0; f0 < N; f0 += 2 * PF) {
+        load(vb, f0 + PF);
+        count(va, f0);
+        if (f0 + PF >= N) break;
+        load(va, f0 + 2 * PF);
+        count(vb, f0 + PF);
+      }
+    }
+    __syncwarp();
+    // Emit the tile's regions (a region is absent when its top-left pixel lies
+    // outside the frame).
+    auto ry0 = [&](int r) { return ty * 16 + (B == 8 ? (r >> 1) * 8 : 0); };
+    auto rx0 = [&](int r) { return tx * 16 + (B == 8 ? (r & 1) * 8 : 0); };
+    auto region_row = [&](int r) -> uint32_t * {
+      const int y0 = ry0(r), x0 = rx0(r);
+      if (y0 >= H || x0 >= W) return nullptr;
+      return model + ((int64_t)(y0 / B) * bw + x0 / B) * C::WPR;
+    };
+    if constexpr (C::DIRECT) {
+      // Word wd of region r's row: leaves 32 wd .. 32 wd + 31.
+      constexpr int EPW = C::NC < 32 ? C::NC : 32;
+      for (int g = lane; g < C::RPT * C::WPR; g += 32) {
+        const int r = g / C::WPR, wd = g - r * C::WPR;
+        const uint16_t *tr = reinterpret_cast<const uint16_t *>(wsm) + r * C::SS;
+        uint32_t bits = 0;
+#pragma unroll 8
+        for (int i = 0; i < EPW; ++i) bits |= (uint32_t)((tr[tile_slot((uint32_t)(32 * wd + i))] & 0xFFu) >= T) << i;
+        uint32_t *row = region_row(r);
+        if (row) row[wd] = bits;
+      }
+      __syncwarp();
+      uint4 *z = reinterpret_cast<uint4 *>(wsm);
+      for (int i = lane; i < C::TABLE_BYTES / 16; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+      __syncwarp();
+    } else {
+      uint32_t ovf = 0;  // regions to recount
+#pragma unroll
+      for (int r = 0; r < C::RPT; ++r) {
+        uint32_t *row = region_row(r);
+        const bool over = *(volatile uint32_t *)(ins + r) > (uint32_t)C::LIM;
+        if (row && over) ovf |= 1u << r;
+        if (row) {
+          uint4 *r4 = reinterpret_cast<uint4 *>(row);
+          for (int i = lane; i < C::WPR / 4; i += 32) r4[i] = make_uint4(0, 0, 0, 0);
+        }
+      }
+      __syncwarp();
+      for (int r = 0; r < C::RPT; ++r) {
+        uint32_t *row = region_row(r);
+        uint32_t *tab = reinterpret_cast<uint32_t *>(wsm) + r * C::SS;
+        const bool emit = row && !((ovf >> r) & 1u);
+        for (int i = lane; i < C::S; i += 32) {
+          const uint32_t e = tab[i];
+          if (e) {
+            tab[i] = 0u;
+            if (emit && (e & 0xFFu) >= T) {
+              const uint32_t q = (e >> 16) - 1u;
+              atomicOr(&row[q >> 5], 1u << (q & 31));
+            }
+          }
+        }
+      }
+      __syncwarp();
+      // Recount regions whose table overflowed: chunked direct passes over
+      // 1024-leaf slices of the code space (table = the first 4 KB of wsm).
+      uint32_t *tab = reinterpret_cast<uint32_t *>(wsm);
+      while (ovf) {
+        const int r = __ffs(ovf) - 1;
+        ovf &= ovf - 1;
+        uint32_t *row = region_row(r);
+        const int y0 = ry0(r), x0 = rx0(r);
+        const int h = min(B, H - y0), w = min(B, W - x0), npx = h * w;
+        constexpr int PPL = C::NPX / 32;
+        uint32_t off[PPL];
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+          const int i = lane + 32 * k;
+          off[k] = i < npx ? (uint32_t)(((int64_t)(y0 + i / w) * W + x0 + i % w) * 3) : 0u;
+        }
+        for (int c = 0; c < WarpTableCfg<D>::NC / WarpTableCfg<D>::S; ++c) {
+          __syncwarp();
+          warp_region_pass<D, PPL, 4, true>(frames, N, fstride, off, npx, tab, c);
+          warp_emit<D>(tab, row, T);
+        }
+      }
+      if (lane < C::RPT) ins[lane] = 0u;
+      __syncwarp();
+    }
+  }
+}
+
 // ---- pixel regions, depth <= 3 -------------------------------------------------
 // Thread t of a 128-thread CTA owns pixel location p and a private column of
 // counter words cnt[k * 128 + t] (4 u8 or 2 u16 counters per word).

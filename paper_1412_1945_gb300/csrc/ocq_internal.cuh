@@ -178,6 +178,12 @@ bool classify_take_timeout();
 bool build_take_timeout();
 // Block regions that the one-warp-per-region build handles (b <= 16, N <= 255).
 bool block_warp_ok(int N, int H, int W, int b);
+// Block regions that the 16 x 16 warp-tile build handles (b in {8, 16}, ...),
+// and its selection (1: used where it applies; 0: one warp per region).
+bool block_tile_ok(int N, int H, int W, int b, int depth, const void *frames);
+int block_build_form_count();
+int block_build_form_selected();
+bool block_build_form_select(int v);
 
 // Kernel variants the tuner can choose between (per-pixel tiled classify,
 // staged per-pixel build).

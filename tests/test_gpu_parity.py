@@ -345,18 +345,50 @@ def test_block_build_warp_tables(ocq, torch, b, d):
                 assert (mask == om).all(), (W, T)
 
 
+@pytest.mark.parametrize("b", [8, 16])
+@pytest.mark.parametrize("d", [2, 3, 4, 5])
+def test_block_build_tiles(ocq, torch, b, d):
+    """8 x 8 and 16 x 16 blocks with W % 8 == 0 are built by warps over 16 x 16
+    pixel tiles (direct leaf tables at depth <= 3 and at depth 4 with 16 x 16
+    blocks, hashed tables otherwise).  Widths with a half tile at the right
+    edge, heights with ragged blocks at the bottom; scene content, then uniform
+    noise (more distinct leaves per region than a hashed table takes, so the
+    region is recounted by the chunked passes), and both build forms."""
+    O = ocq.ocq
+    kern = O.OCQ_TUNE_BUILD_BLOCK
+    saved = O.ocq_tune_selected(kern)
+    try:
+        for H, W in ((2 * b + 3, 40), (3 * b + 5, 64), (17, 8)):
+            sc = ocq_synth.make_scene("sway", H, W, 12, 5, seed=700 + 13 * b + d + W)
+            frames = ocq_synth.fill_host(sc, 0, 17)
+            g = np.random.default_rng(910 + b * 7 + d + W)
+            noise = g.integers(0, 256, size=(12, H, W, 3), dtype=np.uint8)
+            for train in (frames[:12], noise):
+                for T in (1, 4, 12):
+                    ow, om = oracle.run(train, d, T, BLOCK, b, frames[12:])
+                    for form in (1, 0):
+                        O.ocq_tune_select(kern, form)
+                        words, mask = gpu_model_and_mask(ocq, torch, train, frames[12:], d, T, BLOCK, b)
+                        assert (words == ow).all(), (H, W, T, form)
+                        assert (mask == om).all(), (H, W, T, form)
+    finally:
+        O.ocq_tune_select(kern, saved)
+
+
 @pytest.mark.parametrize("N", [254, 255, 256])
 def test_block_build_frame_count_limits(ocq, torch, N):
     """The warp tables keep the last frame and the count in 8 bits each:
     N = 255 is their limit, N = 256 goes to the CTA-per-region kernel."""
     g = np.random.default_rng(N)
     palette = g.integers(0, 256, size=(5, 3), dtype=np.uint8)
-    train = palette[g.integers(0, 5, size=(N, 12, 20))]
-    test = palette[g.integers(0, 5, size=(2, 12, 20))]
-    for T in (1, N // 5, N // 2, N):
-        words, mask = gpu_model_and_mask(ocq, torch, train, test, 4, T, BLOCK, 8)
-        ow, om = oracle.run(train, 4, T, BLOCK, 8, test)
-        assert (words == ow).all() and (mask == om).all(), T
+    for W in (20, 24):  # one warp per region; 16 x 16 warp tiles (W % 8 == 0)
+        train = palette[g.integers(0, 5, size=(N, 12, W))]
+        test = palette[g.integers(0, 5, size=(2, 12, W))]
+        for d in (3, 4, 5):
+            for T in (1, N // 5, N // 2, N):
+                words, mask = gpu_model_and_mask(ocq, torch, train, test, d, T, BLOCK, 8)
+                ow, om = oracle.run(train, d, T, BLOCK, 8, test)
+                assert (words == ow).all() and (mask == om).all(), (W, d, T)
 
 
 @pytest.mark.parametrize("d", [4, 5, 6])
