@@ -47,6 +47,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-next", action="store_true",
                     help="skip the redraw / F0 evaluation / group-of-frames measurements")
     ap.add_argument("--serving-seconds", type=float, default=40.0, help="wall-time limit of the serving run")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the per-config section (tiny whole-frame and 16x16-block presets)")
+    ap.add_argument("--config", choices=("tiny", "blocks"), default=None,
+                    help="print the line of one smaller preset instead of the 1080p per-pixel workload")
     ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None,
                     help="run one small fixed case twice (warm-up, then the pass to capture) for ncu, print one "
                          "line and exit; no measurement")
@@ -288,6 +292,171 @@ def oracle_throughput_all_cores(wl, budget_s: float, workers: int):
     return px / wall / 1e6, sum(r[2] for r in res), wall
 
 
+def oracle_regions_throughput(wl, budget_s: float, seed: int = 7, frames=None):
+    """The oracle as it stands (single thread) on whole regions of a
+    whole-frame or block preset: each timed call runs Alg. 1-3 on one region
+    cropped out of every training and test frame (regions are independent,
+    Sec. 3), until about ``budget_s`` of oracle time.  Mpixel/s of
+    (N + F) x region pixels; the frames are rendered outside the timed region."""
+    import numpy as np
+
+    import ocq_synth
+    import oracle
+
+    oracle.build()
+    if frames is None:
+        sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, wl.F, wl.seed, wl.stream)
+        frames = ocq_synth.fill_host(sc, 0, wl.N + wl.F)
+    rng = np.random.default_rng(seed)
+    b = wl.block if wl.region == 1 else max(wl.H, wl.W)
+    bh, bw = -(-wl.H // b), -(-wl.W // b)
+    done_px, spent, regions = 0, 0.0, 0
+    while spent < budget_s:
+        r = int(rng.integers(0, bh * bw))
+        y0, x0 = (r // bw) * b, (r % bw) * b
+        crop = np.ascontiguousarray(frames[:, y0:y0 + b, x0:x0 + b])
+        t0 = time.perf_counter()
+        oracle.run(crop[:wl.N], wl.depth, wl.T, wl.region, wl.block, crop[wl.N:])
+        spent += time.perf_counter() - t0
+        done_px += crop.shape[0] * crop.shape[1] * crop.shape[2]
+        regions += 1
+    return done_px / spent / 1e6, regions, spent
+
+
+def _oracle_regions_worker(job):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    from ocq_synth import configs
+
+    name, seed, budget_s = job
+    v, regions, spent = oracle_regions_throughput(configs.PRESETS[name], budget_s, seed=seed)
+    return v * spent * 1e6, spent, regions
+
+
+def oracle_regions_all_cores(wl, budget_s: float, workers: int):
+    """The same in ``workers`` spawned processes at once (region parallel)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_regions_worker, [(wl.name, 2000 + w, budget_s) for w in range(workers)]))
+    return sum(r[0] for r in res) / max(r[1] for r in res) / 1e6, sum(r[2] for r in res), max(r[1] for r in res)
+
+
+def preset_measure(ocq, wl, dev, peak, steps=20, warmup=3, flush_mb=256):
+    """One smaller preset (whole frame or blocks) through ocq_build_model +
+    ocq_classify, inputs resident in HBM.  Its frames fit in the 129 MB L2, so
+    a 256 MB buffer is written before every step (outside the events) and each
+    step starts with a cold L2.  Per-kernel times are CUDA events around the
+    two calls, averaged over ``steps``."""
+    import torch
+
+    import ocq_synth
+
+    O = ocq.ocq
+    H, W, N, F = wl.H, wl.W, wl.N, wl.F
+    hw = H * W
+    sc = ocq_synth.make_scene(wl.scene_kind, H, W, N, F, wl.seed, wl.stream)
+    train = torch.empty((N, H, W, 3), dtype=torch.uint8, device=dev)
+    test = torch.empty((F, H, W, 3), dtype=torch.uint8, device=dev)
+    mask = torch.empty((F, H, W), dtype=torch.uint8, device=dev)
+    ocq_synth.fill_device(sc, 0, N, train)
+    ocq_synth.fill_device(sc, N, F, test)
+    flush = torch.empty(flush_mb << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        m = O.ocq_build_model(train, N, H, W, wl.region, wl.block, wl.depth, wl.T, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        O.ocq_classify(m, test, F, mask, stream)
+        if ev is not None:
+            ev[2].record(stream)
+        m.free()
+
+    for _ in range(warmup):
+        step()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    l0 = O.ocq_kernel_launches()
+    for k in range(steps):
+        flush.fill_(k & 255)
+        step(evs[k])
+    torch.cuda.synchronize()
+    launches = (O.ocq_kernel_launches() - l0) / steps
+    ocq.device_status()
+    build_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    cls_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    model_bytes = O.ocq_model_footprint(H, W, wl.region, wl.block, wl.depth)
+    bb, cb = N * hw * 3 + model_bytes, F * hw * 4 + model_bytes
+    del train, test, mask, flush
+    torch.cuda.empty_cache()
+    return {"H": H, "W": W, "train_frames": N, "test_frames": F,
+            "region": ("frame", "block", "pixel")[wl.region], "block": wl.block, "depth": wl.depth, "T": wl.T,
+            "step_ms": round(build_ms + cls_ms, 4),
+            "step_mpixel_s": round((N + F) * hw / ((build_ms + cls_ms) / 1e3) / 1e6, 1),
+            "build": {"ms": round(build_ms, 4), "mpixel_s": round(N * hw / (build_ms / 1e3) / 1e6, 1),
+                      "algorithmic_bytes": bb, "hbm_frac": round(bb / (build_ms / 1e3) / 1e9 / peak, 4)},
+            "classify": {"ms": round(cls_ms, 4), "mpixel_s": round(F * hw / (cls_ms / 1e3) / 1e6, 1),
+                         "algorithmic_bytes": cb, "hbm_frac": round(cb / (cls_ms / 1e3) / 1e9 / peak, 4)},
+            "launches_per_step": launches,
+            "l2": f"frames of one step = {(N + F) * hw * 3 / 1e6:.1f} MB (fit in L2); a {flush_mb} MB buffer is "
+                  "written before each step, outside the timed events"}
+
+
+def presets_section(ocq, dev, peak, cpu_seconds, with_cpu=True):
+    """The tiny whole-frame and the 16x16-block presets: GPU figures, plus the
+    oracle on one core and on every host core (region parallel)."""
+    from ocq_synth import configs
+
+    out = {}
+    for wl in (configs.TINY_FRAME, configs.BLOCKS_320x240):
+        r = preset_measure(ocq, wl, dev, peak)
+        if with_cpu:
+            v, regions, spent = oracle_regions_throughput(wl, cpu_seconds)
+            r["cpu_baseline"] = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{regions} regions x all {wl.N}+{wl.F} frames ({spent:.1f} s)"}
+            workers = os.cpu_count() or 1
+            v, regions, spent = oracle_regions_all_cores(wl, cpu_seconds, workers)
+            r["cpu_baseline_all_cores"] = {"value": round(v, 4), "unit": UNIT, "cores": workers, "kind": "oracle",
+                                           "sample": f"{regions} regions x all {wl.N}+{wl.F} frames, {workers} "
+                                                     f"processes at once ({spent:.1f} s)"}
+        out[wl.name] = r
+    return out
+
+
+def run_preset_line(args):
+    """``--config tiny|blocks``: the JSON line of one smaller preset."""
+    import torch
+
+    from ocq_synth import configs
+
+    import paper_1412_1945_gb300 as ocq
+
+    ocq.load()
+    wl = configs.TINY_FRAME if args.config == "tiny" else configs.BLOCKS_320x240
+    dev = torch.device("cuda", 0)
+    peak, peak_kind = measured_peaks()
+    r = preset_measure(ocq, wl, dev, peak, steps=args.steps, warmup=max(3, args.warmup))
+    dom = "classify" if r["classify"]["ms"] >= r["build"]["ms"] else "build"
+    line = {"metric": METRIC, "value": r["step_mpixel_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": r["step_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": wl.name, "H": wl.H, "W": wl.W, "train_frames": wl.N, "test_frames": wl.F,
+                       "region": r["region"], "block": wl.block, "depth": wl.depth, "T": wl.T,
+                       "parallelism": "replicas1", "l2": r["l2"]},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(r[dom]["algorithmic_bytes"] /
+                                                                          (r[dom]["ms"] / 1e3) / 1e9, 1),
+                         "peak": peak, "unit": "GB/s", "frac": r[dom]["hbm_frac"], "traffic": None,
+                         "peak_source": peak_kind},
+            "build": r["build"], "classify": r["classify"], "gpu_launches": int(r["launches_per_step"] * args.steps)}
+    if not args.no_cpu_baseline:
+        v, regions, spent = oracle_regions_throughput(wl, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{regions} regions x all {wl.N}+{wl.F} frames ({spent:.1f} s)"}
+    print(json.dumps(line), flush=True)
+
+
 # ---- our arm ---------------------------------------------------------------------
 
 def workload_for(args, stream_id):
@@ -408,6 +577,9 @@ def run_ours(args):
         result["batched"] = batched_measure(ocq, dev, args.batched_reps)
     if not args.no_serving:
         result["serving"] = serving_measure(ocq, dev, args.serving_seconds)
+    if not args.no_configs and world == 1:
+        result["configs"] = presets_section(ocq, dev, peak, min(5.0, args.cpu_seconds),
+                                            with_cpu=not args.no_cpu_baseline)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, locs, spent = oracle_throughput(wl, args.cpu_seconds)
@@ -803,6 +975,9 @@ def main(argv=None):
     args = parse_args(argv)
     if args.profile_case:
         profile_case(args)
+        return
+    if args.config and args.impl != "reference":
+        run_preset_line(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -307,24 +307,43 @@ typedef struct ocq_server ocq_server;
  * memory pool of the server's own) at creation, so admission and serving never
  * wait on the allocator.  OCQ_ENOMEM if the device cannot provide them. */
 ocq_status ocq_server_create(size_t hbm_budget, int max_cameras, ocq_server **out);
-/* Device bytes a camera of this description reserves (0 if invalid): two
- * models (the current one and the one being merged) in the form ocq_build_model
- * gives the description at admission (for per-pixel regions of depth 4-5 with
- * floor(N/T) <= 8 a list model, 16 B per location; see
- * OCQ_TUNE_PIXEL_MODEL_FORM), the ring of N frames and build scratch. */
+/* Device bytes a camera of this description reserves (0 if invalid): the model
+ * in the form ocq_build_model gives the description at admission (for
+ * per-pixel regions of depth 4-5 with floor(N/T) <= 8 a list model, 16 B per
+ * location; see OCQ_TUNE_PIXEL_MODEL_FORM), build scratch, and the window:
+ *   - whole frame, when a leaf bitset (max(1, 8^d/32) u32 words) is no larger
+ *     than a frame: N leaf bitsets, the entering frame's bitset and 8^d u16
+ *     counts (frames holding each leaf); a re-merge thresholds the counts in
+ *     place;
+ *   - pixel regions, and blocks with b <= 16, at depth <= 5 and N <= 255: N
+ *     planes of per-pixel u16 leaf codes (2 bytes per pixel and frame); a
+ *     re-merge counts the codes into the model in place;
+ *   - otherwise the N frames themselves and a second model (the one being
+ *     rebuilt from them by ocq_build_model).
+ * The window keeps what the update of the model needs of the last N frames
+ * (the paper's Sec. 4 names the update but gives no procedure). */
 size_t ocq_server_camera_footprint(const ocq_camera_desc *desc);
-/* train: device, N*H*W*3 (copied into the ring; M_0 is built from it). */
+/* Bytes of a camera's window image (what ocq_server_snapshot writes to
+ * ring_out, oldest frame first): N * (leaf-bitset bytes, 2*H*W, or 3*H*W)
+ * in the form ocq_server_camera_footprint describes; never more than N*H*W*3.
+ * 0 if the description is invalid. */
+size_t ocq_server_window_bytes(const ocq_camera_desc *desc);
+/* train: device, N*H*W*3 (the window is filled from it and M_0 built from
+ * it; read on the device after the call returns, so keep it until the
+ * camera's first mask is done). */
 ocq_status ocq_server_admit(ocq_server *server, const ocq_camera_desc *desc, const uint8_t *train, int *camera);
 /* frame: device, H*W*3; mask: device, H*W (1 = foreground).  Non-blocking. */
 ocq_status ocq_server_submit(ocq_server *server, int camera, const uint8_t *frame, uint8_t *mask, uint64_t tag);
 /* Up to max completed frames, oldest first; *n receives the count. */
 ocq_status ocq_server_poll(ocq_server *server, ocq_completion *out, int max, int *n);
-/* Waits for the camera's frames, frees its ring and model, returns its budget. */
+/* Waits for the camera's frames, frees its window and model, returns its budget. */
 ocq_status ocq_server_release(ocq_server *server, int camera);
 /* Checkpoint of a camera's serving state, enqueued after its submitted work:
  * the current model in the exported layout (model_words: device, `words` >=
- * regions * words_per_region u64), the window ring oldest frame first
- * (ring_out: device, N*H*W*3 bytes) and the number of test frames submitted.
+ * regions * words_per_region u64), the window image oldest frame first
+ * (ring_out: device, at least ocq_server_window_bytes(desc) bytes; N*H*W*3
+ * always suffices; layout internal to this library) and the number of test
+ * frames submitted.
  * `stream` waits for the copies; read the buffers after it.  No counterpart
  * in the paper. */
 ocq_status ocq_server_snapshot(ocq_server *server, int camera, uint64_t *model_words, size_t words,

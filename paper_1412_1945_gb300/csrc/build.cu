@@ -458,6 +458,25 @@ static void launch_occ_frame(const uint8_t *frames, int64_t hw, int f0, int nf, 
   count_launch();
 }
 
+ocq_status launch_frame_occupancy(const uint8_t *frames, int n, int H, int W, int depth, uint32_t *occ,
+                                  cudaStream_t st) {
+  const int64_t hw = (int64_t)H * W;
+  if (n <= 0 || hw <= 0) return OCQ_OK;
+  switch (depth) {
+    case 1: launch_occ_frame<1>(frames, hw, 0, n, occ, 1, st); break;
+    case 2: launch_occ_frame<2>(frames, hw, 0, n, occ, 1, st); break;
+    case 3: launch_occ_frame<3>(frames, hw, 0, n, occ, 1, st); break;
+    case 4: launch_occ_frame<4>(frames, hw, 0, n, occ, 1, st); break;
+    case 5: launch_occ_frame<5>(frames, hw, 0, n, occ, 1, st); break;
+    case 6: launch_occ_frame<6>(frames, hw, 0, n, occ, 1, st); break;
+    default:
+      occ_global_kernel<<<grid_cap(hw * n, 256, 16), 256, 0, st>>>(frames, H, W, OCQ_REGION_FRAME, 0, depth, 0, n, 1,
+                                                                   wpr32(depth), occ, 1);
+      count_launch();
+  }
+  return cuda_status(cudaGetLastError(), "frame occupancy");
+}
+
 // Dense path: per-tree leaf bitsets in scratch, folded into bit-sliced
 // counters.  One tree per group of `group` consecutive frames (Sec. 3; the
 // last group holds the rest); T counts trees.  Scratch is batched by trees.

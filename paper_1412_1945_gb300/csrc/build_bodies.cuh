@@ -323,23 +323,29 @@ __device__ __forceinline__ void warp_emit(uint32_t *tab, uint32_t *row, uint32_t
 // One pass over the region's N frames.  CHUNKED: only leaves in
 // [chunk * S, chunk * S + S), indexed directly; otherwise every leaf.  Returns
 // false if the hashed pass saw more than 3/4 S distinct leaves.
-template <int D, int PPL, int PF, bool CHUNKED>
-__device__ __forceinline__ bool warp_region_pass(const uint8_t *__restrict__ frames, int N, int64_t fstride,
+// SRC = uint16_t: `frames` holds planar leaf codes (a serving window's
+// per-frame occupancy), fstride and off count codes instead of bytes.
+template <int D, int PPL, int PF, bool CHUNKED, typename SRC = uint8_t>
+__device__ __forceinline__ bool warp_region_pass(const SRC *__restrict__ frames, int N, int64_t fstride,
                                                  const uint32_t (&off)[PPL], int npx, uint32_t *tab, int chunk) {
+  constexpr bool CODES = std::is_same<SRC, uint16_t>::value;
   using C = WarpTableCfg<D>;
   constexpr bool INDEXED = C::DIRECT || CHUNKED;
   const int lane = threadIdx.x & 31;
   uint32_t inserted = 0;
   for (int f0 = 0; f0 < N; f0 += PF) {
     uint32_t yv[PF][PPL];
-    const uint8_t *fb = frames + (int64_t)f0 * fstride;
+    const SRC *fb = frames + (int64_t)f0 * fstride;
 #pragma unroll
     for (int j = 0; j < PF; ++j)
 #pragma unroll
       for (int k = 0; k < PPL; ++k)
         if (f0 + j < N && lane + 32 * k < npx) {
-          const uint8_t *s = fb + (int64_t)j * fstride + off[k];
-          yv[j][k] = (uint32_t)__ldg(s) | ((uint32_t)__ldg(s + 1) << 8) | ((uint32_t)__ldg(s + 2) << 16);
+          const SRC *s = fb + (int64_t)j * fstride + off[k];
+          if constexpr (CODES)
+            yv[j][k] = __ldg(s);
+          else
+            yv[j][k] = (uint32_t)__ldg(s) | ((uint32_t)__ldg(s + 1) << 8) | ((uint32_t)__ldg(s + 2) << 16);
         }
 #pragma unroll
     for (int j = 0; j < PF; ++j) {
@@ -347,7 +353,7 @@ __device__ __forceinline__ bool warp_region_pass(const uint8_t *__restrict__ fra
 #pragma unroll
       for (int k = 0; k < PPL; ++k) {
         if (lane + 32 * k < npx) {
-          const uint32_t q = planar_code<D>(yv[j][k]);
+          const uint32_t q = (CODES ? yv[j][k] : planar_code<D>(yv[j][k]));
           if (!CHUNKED || (int)(q >> C::LOGS) == chunk)
             inserted += warp_table_count<D, INDEXED>(tab, q, (uint32_t)(f0 + j));
         }
@@ -891,13 +897,15 @@ __device__ __forceinline__ void build_pixel_chunked_body(const uint8_t *__restri
 template <int D>
 using leaf_t = typename std::conditional<(D <= 5), uint16_t, uint32_t>::type;
 
-template <int D, int KM, bool GRP = false>
+template <int D, int KM, bool GRP = false, bool CODES = false>
 __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ frames, int N, int64_t hw, uint32_t T,
                                                     uint32_t *__restrict__ model, int64_t tile, leaf_t<D> *codes,
                                                     int group = 1, uint16_t *kept = nullptr) {
   // GRP: one tree per group of `group` consecutive frames (Sec. 3): a leaf
   // enters the summary once per group that holds it, and the exact pass counts
   // the groups holding each candidate (T counts groups).
+  // CODES: `frames` holds planar leaf codes, u16 [N][hw] (depth <= 5), the
+  // per-frame occupancy a serving window keeps, instead of RGB bytes.
   constexpr int64_t WPR = D == 1 ? 1 : (int64_t)1 << (3 * D - 5);
   constexpr int PF = 8;
   const int lane = threadIdx.x & 31;
@@ -916,14 +924,18 @@ __device__ __forceinline__ void build_pixel_mg_body(const uint8_t *__restrict__ 
 #pragma unroll
     for (int j = 0; j < PF; ++j)
       if (valid && f0 + j < N) {
-        const uint8_t *s = px + (int64_t)(f0 + j) * fstride;
-        yv[j] = (uint32_t)__ldg(s) | ((uint32_t)__ldg(s + 1) << 8) | ((uint32_t)__ldg(s + 2) << 16);
+        if constexpr (CODES) {
+          yv[j] = __ldg(reinterpret_cast<const uint16_t *>(frames) + (int64_t)(f0 + j) * hw + p);
+        } else {
+          const uint8_t *s = px + (int64_t)(f0 + j) * fstride;
+          yv[j] = (uint32_t)__ldg(s) | ((uint32_t)__ldg(s + 1) << 8) | ((uint32_t)__ldg(s + 2) << 16);
+        }
       }
 #pragma unroll
     for (int j = 0; j < PF; ++j) {
       if (!valid || f0 + j >= N) break;
       const int f = f0 + j;
-      const uint32_t q = planar_code<D>(yv[j]);
+      const uint32_t q = CODES ? yv[j] : planar_code<D>(yv[j]);
       codes[f * 32 + lane] = (leaf_t<D>)q;
       if constexpr (KM > 0) {
         bool seen = false;

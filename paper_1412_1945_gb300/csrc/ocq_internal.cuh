@@ -174,6 +174,21 @@ ocq_status launch_occupancy(const uint8_t *frames, int n, int H, int W, int kind
                             uint64_t *occ, cudaStream_t st);
 ocq_status launch_export(const uint32_t *bits, int64_t R, int depth, uint64_t *dst, cudaStream_t st);
 ocq_status launch_import(const uint64_t *src, int64_t R, int depth, uint32_t *bits, cudaStream_t st);
+// Serving windows (window.cu): per-frame occupancy kept in place of frames.
+// Leaf bitsets of n whole frames (internal order) ORed into occ[f * wpr32(d)]
+// (occ zero beforehand).
+ocq_status launch_frame_occupancy(const uint8_t *frames, int n, int H, int W, int depth, uint32_t *occ,
+                                  cudaStream_t st);
+// Pixel and block regions with depth <= 5, N <= 255 (blocks: b <= 16) keep a
+// ring of per-pixel u16 leaf codes.
+bool window_codes_apply(int kind, int block, int depth, int N, int H, int W);
+ocq_status launch_window_codes(const uint8_t *frames, int64_t npix, int depth, uint16_t *codes, cudaStream_t st);
+ocq_status launch_window_count_update(uint32_t *slot, uint32_t *fresh, uint16_t *counts, int depth,
+                                      cudaStream_t st);
+ocq_status launch_window_counts_init(const uint32_t *ring, int N, int depth, uint16_t *counts, cudaStream_t st);
+ocq_status launch_window_threshold(const uint16_t *counts, int depth, uint32_t T, uint32_t *bits, cudaStream_t st);
+// Re-merge of a pixel or block model in place from N code planes.
+ocq_status launch_remerge_codes(const uint16_t *ring, int N, ocq_model *m, cudaStream_t st);
 bool classify_take_timeout();
 bool build_take_timeout();
 // Block regions that the one-warp-per-region build handles (b <= 16, N <= 255).

@@ -13,10 +13,19 @@
 // and the camera's next frame waits for it.  Cameras run concurrently, so work
 // of frames that arrive while others are on the GPU overlaps on the device,
 // and one camera's long re-merge yields the SMs to other cameras' frames.
-// Admission reserves a camera's footprint (ring, model, the model being
-// rebuilt, build scratch) against an HBM budget and returns OCQ_EBUSY when it
-// does not fit; released cameras return their share.  A frame's completion
-// time is taken by a host function enqueued right after its mask.
+// The window keeps what the merge needs of those frames, not the frames
+// (window.cu): whole-frame cameras a ring of N leaf bitsets plus resident
+// per-leaf counts, updated as each frame enters (re-merge = a threshold pass);
+// pixel and block cameras of depth <= 5 a ring of per-pixel u16 leaf codes
+// (re-merge = counting the codes, no frame is read again).  Both re-merge the
+// model in place on the camera stream, after the frames that read the old one.
+// Cameras outside those forms (deeper, N > 255, blocks wider than 16, or a
+// whole-frame bitset larger than a frame) keep the N frames and rebuild with
+// ocq_build_model on a low-priority stream.
+// Admission reserves a camera's footprint (window, model, build scratch; the
+// frame ring also a second model) against an HBM budget and returns OCQ_EBUSY
+// when it does not fit; released cameras return their share.  A frame's
+// completion time is taken by a host function enqueued right after its mask.
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -43,11 +52,31 @@ struct Pending {
   double arrival;
 };
 
+enum WindowForm { WIN_FRAMES = 0, WIN_BITS = 1, WIN_CODES = 2 };
+
+static int window_form(const ocq_camera_desc &d) {
+  if (d.region.kind == OCQ_REGION_FRAME)
+    return (size_t)wpr32(d.depth) * 4 <= (size_t)d.H * d.W * 3 ? WIN_BITS : WIN_FRAMES;
+  return window_codes_apply(d.region.kind, d.region.block, d.depth, d.N, d.H, d.W) ? WIN_CODES : WIN_FRAMES;
+}
+
+// Bytes of one window slot (one frame's entry) of each form.
+static size_t window_slot_bytes(const ocq_camera_desc &d, int form) {
+  const size_t hw = (size_t)d.H * d.W;
+  return form == WIN_BITS ? (size_t)wpr32(d.depth) * 4 : form == WIN_CODES ? hw * 2 : hw * 3;
+}
+
 struct Camera {
   int id = -1;
   ocq_camera_desc d;
   size_t footprint = 0;
-  uint8_t *ring = nullptr;  // N frames (HWC RGB8), slot = frame % N
+  int win = WIN_FRAMES;
+  // slot = frame % N: WIN_FRAMES N frames (HWC RGB8); WIN_BITS N leaf bitsets
+  // (wpr32(depth) u32 words, internal order); WIN_CODES N planes of H*W u16
+  // leaf codes
+  uint8_t *ring = nullptr;
+  uint32_t *fresh = nullptr;   // WIN_BITS: the entering frame's bitset
+  uint16_t *counts = nullptr;  // WIN_BITS: per leaf, window frames holding it
   ocq_model *model = nullptr;
   cudaStream_t stream = nullptr;  // high priority: classify, ring copies, completions
   cudaStream_t merge = nullptr;   // low priority: builds (M_0 and re-merges)
@@ -73,11 +102,46 @@ struct ocq_server {
 static size_t camera_footprint(const ocq_camera_desc &d) {
   const size_t hw = (size_t)d.H * d.W;
   const size_t model = model_bytes(d.H, d.W, d.region, d.depth, d.N, d.T);
-  const size_t ring = (size_t)d.N * hw * 3;
-  size_t scratch = 0;
+  const int form = window_form(d);
+  const size_t ring = (size_t)d.N * window_slot_bytes(d, form);
+  size_t scratch = 0;  // what a build of the model allocates beside it
   if (d.region.kind == OCQ_REGION_FRAME) scratch = (size_t)d.N * wpr32(d.depth) * 4;
   if (d.region.kind == OCQ_REGION_PIXEL && d.depth >= 6) scratch = hw * ((size_t)1 << (3 * d.depth - 9)) / 8;
+  if (form == WIN_BITS)  // the entering frame's bitset and the u16 counts; re-merged in place
+    return model + ring + (size_t)wpr32(d.depth) * 4 + ((size_t)1 << (3 * d.depth)) * 2 + scratch;
+  if (form == WIN_CODES) return model + ring + scratch;
   return 2 * model + ring + scratch;  // the model being rebuilt lives beside the current one
+}
+
+// Allocates the camera's window on its build stream and fills it from the N
+// frames `src` (frame i = global frame i into slot i).
+static ocq_status window_fill(Camera &c, const uint8_t *src) {
+  const ocq_camera_desc &d = c.d;
+  const size_t slot = window_slot_bytes(d, c.win);
+  ocq_status rc = cuda_status(malloc_async((void **)&c.ring, (size_t)d.N * slot, c.merge), "camera window");
+  if (rc != OCQ_OK) return rc;
+  if (c.win == WIN_FRAMES)
+    return cuda_status(cudaMemcpyAsync(c.ring, src, (size_t)d.N * slot, cudaMemcpyDeviceToDevice, c.merge),
+                       "ring fill");
+  if (c.win == WIN_CODES)
+    return launch_window_codes(src, (int64_t)d.N * d.H * d.W, d.depth, reinterpret_cast<uint16_t *>(c.ring), c.merge);
+  rc = cuda_status(malloc_async((void **)&c.fresh, slot, c.merge), "window bitset");
+  if (rc == OCQ_OK)
+    rc = cuda_status(malloc_async((void **)&c.counts, ((size_t)1 << (3 * d.depth)) * 2, c.merge), "window counts");
+  if (rc == OCQ_OK) rc = cuda_status(cudaMemsetAsync(c.ring, 0, (size_t)d.N * slot, c.merge), "clear window");
+  if (rc == OCQ_OK) rc = cuda_status(cudaMemsetAsync(c.fresh, 0, slot, c.merge), "clear window");
+  if (rc == OCQ_OK)
+    rc = launch_frame_occupancy(src, d.N, d.H, d.W, d.depth, reinterpret_cast<uint32_t *>(c.ring), c.merge);
+  if (rc == OCQ_OK)
+    rc = launch_window_counts_init(reinterpret_cast<uint32_t *>(c.ring), d.N, d.depth, c.counts, c.merge);
+  return rc;
+}
+
+static void window_free(Camera &c, cudaStream_t st) {
+  if (c.ring) cudaFreeAsync(c.ring, st);
+  if (c.fresh) cudaFreeAsync(c.fresh, st);
+  if (c.counts) cudaFreeAsync(c.counts, st);
+  c.ring = nullptr, c.fresh = nullptr, c.counts = nullptr;
 }
 
 static void CUDART_CB on_frame_done(void *arg) {
@@ -152,6 +216,11 @@ size_t ocq_server_camera_footprint(const ocq_camera_desc *d) {
   return camera_footprint(*d);
 }
 
+size_t ocq_server_window_bytes(const ocq_camera_desc *d) {
+  if (!d || ocq_model_footprint(d->H, d->W, d->region, d->depth) == 0 || d->N < 1) return 0;
+  return (size_t)d->N * window_slot_bytes(*d, window_form(*d));
+}
+
 ocq_status ocq_server_admit(ocq_server *s, const ocq_camera_desc *d, const uint8_t *train, int *camera) {
   if (!s || !d || !train || !camera || d->N < 1 || d->N > 65535 || d->T < 1 || d->T > d->N || d->K < 1 ||
       ocq_model_footprint(d->H, d->W, d->region, d->depth) == 0) {
@@ -180,20 +249,21 @@ ocq_status ocq_server_admit(ocq_server *s, const ocq_camera_desc *d, const uint8
   c.d = *d;
   c.footprint = fp;
   c.submitted = 0;
+  c.win = window_form(*d);
   int lo = 0, hi = 0;
   cudaDeviceGetStreamPriorityRange(&lo, &hi);  // lo = least urgent, hi = most urgent
   ocq_status rc = cuda_status(cudaStreamCreateWithPriority(&c.stream, cudaStreamNonBlocking, hi), "camera stream");
   if (rc == OCQ_OK) rc = cuda_status(cudaStreamCreateWithPriority(&c.merge, cudaStreamNonBlocking, lo), "merge stream");
   if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.ring_ready, cudaEventDisableTiming), "event");
   if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.merged, cudaEventDisableTiming), "event");
-  const size_t ring = (size_t)d->N * d->H * d->W * 3;
-  if (rc == OCQ_OK) rc = cuda_status(malloc_async((void **)&c.ring, ring, c.merge), "camera ring");
-  if (rc == OCQ_OK) rc = cuda_status(cudaMemcpyAsync(c.ring, train, ring, cudaMemcpyDeviceToDevice, c.merge), "ring fill");
-  if (rc == OCQ_OK) rc = ocq_build_model(c.ring, d->N, d->H, d->W, d->region, d->depth, d->T, c.merge, &c.model);
+  if (rc == OCQ_OK) rc = window_fill(c, train);
+  if (rc == OCQ_OK) rc = ocq_build_model(train, d->N, d->H, d->W, d->region, d->depth, d->T, c.merge, &c.model);
   if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(c.merged, c.merge), "merged");
   if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent(c.stream, c.merged, 0), "wait for M_0");
   if (rc != OCQ_OK) {
-    if (c.ring) cudaFreeAsync(c.ring, c.merge);
+    if (c.model) ocq_model_free(c.model);
+    c.model = nullptr;
+    window_free(c, c.merge);
     if (c.merge) cudaStreamSynchronize(c.merge), cudaStreamDestroy(c.merge);
     if (c.stream) cudaStreamSynchronize(c.stream), cudaStreamDestroy(c.stream);
     if (c.ring_ready) cudaEventDestroy(c.ring_ready);
@@ -227,8 +297,24 @@ ocq_status ocq_server_submit(ocq_server *s, int camera, const uint8_t *frame, ui
     delete p;
     return rc;
   }
-  rc = cuda_status(cudaMemcpyAsync(c.ring + (size_t)((c.d.N + t) % c.d.N) * fbytes, frame, fbytes,
-                                   cudaMemcpyDeviceToDevice, c.stream),
+  const int64_t slot = (c.d.N + t) % c.d.N;
+  if (c.win == WIN_BITS) {
+    // the frame's leaf bitset enters the window; every K frames the counts
+    // are thresholded into the model (in place: later frames read it)
+    uint32_t *ring = reinterpret_cast<uint32_t *>(c.ring) + slot * wpr32(c.d.depth);
+    rc = launch_frame_occupancy(frame, 1, c.d.H, c.d.W, c.d.depth, c.fresh, c.stream);
+    if (rc == OCQ_OK) rc = launch_window_count_update(ring, c.fresh, c.counts, c.d.depth, c.stream);
+    if (rc == OCQ_OK && (t + 1) % c.d.K == 0)
+      rc = launch_window_threshold(c.counts, c.d.depth, (uint32_t)c.d.T, c.model->bits, c.stream);
+    return rc;
+  }
+  if (c.win == WIN_CODES) {
+    uint16_t *ring = reinterpret_cast<uint16_t *>(c.ring);
+    rc = launch_window_codes(frame, (int64_t)c.d.H * c.d.W, c.d.depth, ring + slot * c.d.H * c.d.W, c.stream);
+    if (rc == OCQ_OK && (t + 1) % c.d.K == 0) rc = launch_remerge_codes(ring, c.d.N, c.model, c.stream);
+    return rc;
+  }
+  rc = cuda_status(cudaMemcpyAsync(c.ring + (size_t)slot * fbytes, frame, fbytes, cudaMemcpyDeviceToDevice, c.stream),
                    "ring push");
   if (rc == OCQ_OK && (t + 1) % c.d.K == 0) {
     // Re-merge on the low-priority stream once the ring holds frame t; the
@@ -276,7 +362,7 @@ ocq_status ocq_server_release(ocq_server *s, int camera) {
   cudaStreamWaitEvent(c.stream, c.merged, 0);
   c.model->stream = c.stream;
   ocq_model_free(c.model);
-  cudaFreeAsync(c.ring, c.stream);
+  window_free(c, c.stream);
   cudaError_t e = cudaStreamSynchronize(c.stream);
   cudaError_t e2 = cudaStreamSynchronize(c.merge);
   if (e == cudaSuccess) e = e2;
@@ -303,9 +389,10 @@ ocq_status ocq_server_snapshot(ocq_server *s, int camera, uint64_t *model_words,
   }
   Camera &c = s->cams[camera];
   const int64_t t = c.submitted;
-  const size_t fbytes = (size_t)c.d.H * c.d.W * 3;
-  // After t test frames the ring holds global frames t .. t + N - 1 (training
-  // frames are 0 .. N - 1), frame g in slot g mod N: copy them oldest first.
+  const size_t fbytes = window_slot_bytes(c.d, c.win);
+  // After t test frames the window holds global frames t .. t + N - 1
+  // (training frames are 0 .. N - 1), frame g in slot g mod N: copy the slots
+  // oldest first.
   ocq_status rc = cuda_status(cudaStreamWaitEvent(c.stream, c.merged, 0), "snapshot wait");
   if (rc == OCQ_OK) rc = ocq_model_export(c.model, model_words, words, c.stream);
   for (int i = 0; i < c.d.N && rc == OCQ_OK; ++i)
@@ -350,18 +437,27 @@ ocq_status ocq_server_resume(ocq_server *s, const ocq_camera_desc *d, const uint
   c.d = *d;
   c.footprint = fp;
   c.submitted = submitted;
+  c.win = window_form(*d);
   int lo = 0, hi = 0;
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
   ocq_status rc = cuda_status(cudaStreamCreateWithPriority(&c.stream, cudaStreamNonBlocking, hi), "camera stream");
   if (rc == OCQ_OK) rc = cuda_status(cudaStreamCreateWithPriority(&c.merge, cudaStreamNonBlocking, lo), "merge stream");
   if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.ring_ready, cudaEventDisableTiming), "event");
   if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&c.merged, cudaEventDisableTiming), "event");
-  const size_t fbytes = (size_t)d->H * d->W * 3;
-  if (rc == OCQ_OK) rc = cuda_status(malloc_async((void **)&c.ring, (size_t)d->N * fbytes, c.merge), "camera ring");
-  for (int i = 0; i < d->N && rc == OCQ_OK; ++i)  // snapshot frame i is global frame submitted + i
+  const size_t fbytes = window_slot_bytes(*d, c.win);
+  if (rc == OCQ_OK) rc = cuda_status(malloc_async((void **)&c.ring, (size_t)d->N * fbytes, c.merge), "camera window");
+  for (int i = 0; i < d->N && rc == OCQ_OK; ++i)  // snapshot slot i is global frame submitted + i
     rc = cuda_status(cudaMemcpyAsync(c.ring + (size_t)((submitted + i) % d->N) * fbytes, ring + (size_t)i * fbytes,
                                      fbytes, cudaMemcpyDeviceToDevice, c.merge),
-                     "ring restore");
+                     "window restore");
+  if (rc == OCQ_OK && c.win == WIN_BITS) {  // the counts follow from the bitsets
+    rc = cuda_status(malloc_async((void **)&c.fresh, fbytes, c.merge), "window bitset");
+    if (rc == OCQ_OK)
+      rc = cuda_status(malloc_async((void **)&c.counts, ((size_t)1 << (3 * d->depth)) * 2, c.merge), "window counts");
+    if (rc == OCQ_OK) rc = cuda_status(cudaMemsetAsync(c.fresh, 0, fbytes, c.merge), "clear window");
+    if (rc == OCQ_OK)
+      rc = launch_window_counts_init(reinterpret_cast<uint32_t *>(c.ring), d->N, d->depth, c.counts, c.merge);
+  }
   if (rc == OCQ_OK) {
     ocq_model_info info;
     memset(&info, 0, sizeof info);
@@ -373,7 +469,7 @@ ocq_status ocq_server_resume(ocq_server *s, const ocq_camera_desc *d, const uint
   if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent(c.stream, c.merged, 0), "wait for the model");
   if (rc != OCQ_OK) {
     if (c.model) ocq_model_free(c.model);
-    if (c.ring) cudaFreeAsync(c.ring, c.merge);
+    window_free(c, c.merge);
     if (c.merge) cudaStreamSynchronize(c.merge), cudaStreamDestroy(c.merge);
     if (c.stream) cudaStreamSynchronize(c.stream), cudaStreamDestroy(c.stream);
     if (c.ring_ready) cudaEventDestroy(c.ring_ready);

@@ -105,6 +105,7 @@ SIGNATURES = {
     "ocq_batch_destroy": (None, [_vp]),
     "ocq_server_create": (_i32, [_sz, _i32, ctypes.POINTER(_vp)]),
     "ocq_server_camera_footprint": (_sz, [ctypes.POINTER(ocq_camera_desc)]),
+    "ocq_server_window_bytes": (_sz, [ctypes.POINTER(ocq_camera_desc)]),
     "ocq_server_admit": (_i32, [_vp, ctypes.POINTER(ocq_camera_desc), _vp, ctypes.POINTER(_i32)]),
     "ocq_server_submit": (_i32, [_vp, _i32, _vp, _vp, ctypes.c_uint64]),
     "ocq_server_poll": (_i32, [_vp, ctypes.POINTER(ocq_completion), _i32, ctypes.POINTER(_i32)]),
@@ -482,6 +483,11 @@ def ocq_server_camera_footprint(H, W, kind, block, depth, T, N, K) -> int:
     return int(load().ocq_server_camera_footprint(ctypes.byref(d)))
 
 
+def ocq_server_window_bytes(H, W, kind, block, depth, T, N, K) -> int:
+    d = _camera(H, W, kind, block, depth, T, N, K)
+    return int(load().ocq_server_window_bytes(ctypes.byref(d)))
+
+
 def ocq_server_admit(server, H, W, kind, block, depth, T, N, K, train):
     """Returns the camera id, or None when the server answers OCQ_EBUSY."""
     d = _camera(H, W, kind, block, depth, T, N, K)
@@ -506,7 +512,9 @@ def ocq_server_poll(server, max_n=4096):
 
 def ocq_server_snapshot(server, camera, model_words, ring_out, stream=None) -> int:
     """Enqueues the camera's checkpoint into ``model_words`` (int64/uint64 CUDA
-    tensor) and ``ring_out`` (N*H*W*3 bytes); returns the frames submitted."""
+    tensor) and ``ring_out`` (the window image: at least
+    ocq_server_window_bytes bytes; N*H*W*3 always suffices); returns the
+    frames submitted."""
     n = ctypes.c_int64()
     _check(load().ocq_server_snapshot(server.handle, camera, _p(model_words), model_words.numel(), _p(ring_out),
                                       ctypes.byref(n), _s(stream)))

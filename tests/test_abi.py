@@ -68,23 +68,36 @@ def test_host_side_helpers(lib):
 
 
 def test_camera_footprint_follows_the_model_form(lib):
-    """A camera reserves two models of the form ocq_build_model gives its
-    description, plus its ring: per-pixel d = 5 with floor(N/T) <= 8 is a
+    """A camera reserves the model in the form ocq_build_model gives its
+    description and its window: per-pixel d = 5 with floor(N/T) <= 8 is a
     list model (16 B per location), with floor(N/T) > 8 rows (4 KB per
-    location), and with list models switched off rows plus the lists."""
+    location), and with list models switched off rows plus the lists; pixel
+    cameras of depth <= 5 keep 2-byte leaf codes per pixel and frame and merge
+    in place (one model), depth 6 keeps the frames and a second model; a
+    whole-frame camera keeps N leaf bitsets and per-leaf u16 counts."""
     from paper_1412_1945_gb300 import ocq
 
     H, W, N, K = 1080, 1920, 30, 30
-    hw, ring = H * W, N * H * W * 3
+    hw, codes, frames = H * W, N * H * W * 2, N * H * W * 3
     pix = ocq.OCQ_REGION_PIXEL
-    assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 5, 10, N, K) == 2 * hw * 16 + ring
-    assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 5, 3, N, K) == 2 * hw * 4096 + ring
-    assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 3, 10, N, K) == 2 * hw * 64 + ring
+    assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 5, 10, N, K) == hw * 16 + codes
+    assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 5, 3, N, K) == hw * 4096 + codes
+    assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 3, 10, N, K) == hw * 64 + codes
+    assert ocq.ocq_server_window_bytes(H, W, pix, 0, 3, 10, N, K) == codes
+    # depth 6: two models of 8^6 bits per location, the frames, and the build's
+    # chunk scratch (8^(d-3)/8 bytes per location)
+    assert ocq.ocq_server_camera_footprint(64, 64, pix, 0, 6, 10, N, K) == 2 * (64 * 64 * 8 ** 6 // 8) + \
+        N * 64 * 64 * 3 + 64 * 64 * 8 ** 3 // 8
+    fr = ocq.OCQ_REGION_FRAME
+    wb = 8 ** 4 // 8
+    assert ocq.ocq_server_camera_footprint(H, W, fr, 0, 4, 10, N, K) == wb + N * wb + wb + 2 * 8 ** 4 + N * wb
+    assert ocq.ocq_server_window_bytes(H, W, fr, 0, 4, 10, N, K) == N * wb
+    assert ocq.ocq_server_window_bytes(8, 8, fr, 0, 6, 10, N, K) == N * 8 * 8 * 3  # bitset larger than a frame
     mf = ocq.OCQ_TUNE_PIXEL_MODEL_FORM
     saved = ocq.ocq_tune_selected(mf)
     try:
         ocq.ocq_tune_select(mf, 0)
-        assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 5, 10, N, K) == 2 * hw * (4096 + 16) + ring
+        assert ocq.ocq_server_camera_footprint(H, W, pix, 0, 5, 10, N, K) == hw * (4096 + 16) + codes
     finally:
         ocq.ocq_tune_select(mf, saved)
 

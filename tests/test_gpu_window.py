@@ -1,0 +1,87 @@
+"""Serving windows: the three forms a camera's window takes (leaf bitsets with
+resident counts, per-pixel leaf codes, or the frames themselves) each give the
+masks of the window semantics (test frame t against the merge of global frames
+[kK, kK + N - 1], k = floor(t / K); Alg. 2 and 3 on the oracle), and each
+reserves what its form needs."""
+import numpy as np
+import pytest
+
+import ocq_synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+FRAME, BLOCK, PIXEL = 0, 1, 2
+
+# (scene, H, W, region, block, depth, T, N, K, test frames, form)
+#   form 1: leaf bitsets + counts, 2: per-pixel codes, 0: frames
+CAMERAS = [
+    ("clusters", 36, 52, FRAME, 0, 5, 3, 7, 3, 12, 1),
+    ("sway", 96, 128, FRAME, 0, 6, 2, 5, 4, 9, 1),
+    ("clusters", 6, 10, FRAME, 0, 6, 2, 4, 3, 7, 0),     # a bitset (32 KB) larger than a frame
+    ("sway", 33, 40, BLOCK, 8, 5, 3, 9, 4, 10, 2),
+    ("sway", 40, 40, BLOCK, 16, 3, 4, 6, 5, 11, 2),
+    ("sway", 34, 38, BLOCK, 17, 3, 2, 5, 2, 7, 0),       # blocks wider than 16
+    ("bimodal", 22, 30, PIXEL, 0, 3, 2, 6, 4, 10, 2),
+    ("clusters", 17, 23, PIXEL, 0, 4, 3, 9, 2, 8, 2),
+    ("bimodal", 16, 20, PIXEL, 0, 5, 1, 12, 5, 11, 2),   # floor(N/T) > 8: rows, every distinct leaf counted
+    ("sway", 12, 16, PIXEL, 0, 6, 2, 5, 3, 7, 0),        # depth 6: frames
+]
+
+
+def _window_oracle(frames, cam):
+    scene, H, W, region, block, d, T, N, K, F, form = cam
+    out, models = [], {}
+    for t in range(F):
+        k = t // K
+        if k not in models:
+            models[k] = oracle.build_model(frames[k * K:k * K + N], d, T, region, block)
+        out.append(oracle.classify(models[k], frames[N + t:N + t + 1], d, region, block)[0])
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("i", range(len(CAMERAS)))
+def test_window_forms_follow_the_window_semantics(cuda_ready, i):
+    import torch
+
+    O = cuda_ready.ocq
+    cam = CAMERAS[i]
+    scene, H, W, region, block, d, T, N, K, F, form = cam
+    hw = H * W
+    slot = {1: max(1, 8 ** d // 32) * 4, 2: 2 * hw, 0: 3 * hw}[form]
+    assert O.ocq_server_window_bytes(H, W, region, block, d, T, N, K) == N * slot
+    sc = ocq_synth.make_scene(scene, H, W, N, F, 7100 + i)
+    host = ocq_synth.fill_host(sc, 0, N + F)
+    dev = torch.from_numpy(host).cuda()
+    masks = torch.full((F, H, W), 9, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    srv = O.ocq_server_create(1 << 28, 2)
+    try:
+        c = O.ocq_server_admit(srv, H, W, region, block, d, T, N, K, dev[:N].contiguous())
+        assert c is not None
+        for t in range(F):
+            O.ocq_server_submit(srv, c, dev[N + t], masks[t], tag=t)
+        O.ocq_server_sync(srv)
+        model = cuda_ready.export_model(O.ocq_server_camera_model(srv, c)).cpu().numpy().view(np.uint64)
+        O.ocq_server_release(srv, c)
+    finally:
+        srv.destroy()
+    assert (masks.cpu().numpy() == _window_oracle(host, cam)).all()
+    # after F test frames the model is M_floor(F/K), merged from frames [kK, kK + N)
+    k = F // K
+    assert (model == oracle.build_model(host[k * K:k * K + N], d, T, region, block)).all()
+
+
+def test_window_footprints_shrink(cuda_ready):
+    """A 4K whole-frame camera keeps kilobytes instead of its frames; 4K
+    per-pixel cameras keep 2 bytes per pixel and frame instead of 3, and one
+    model instead of two."""
+    O = cuda_ready.ocq
+    H, W, N, K, T = 2160, 3840, 30, 30, 10
+    frame = O.ocq_server_camera_footprint(H, W, FRAME, 0, 4, T, N, K)
+    assert frame < 1 << 20
+    for d in (3, 5):
+        model = O.ocq_model_footprint(H, W, PIXEL, 0, d)
+        fp = O.ocq_server_camera_footprint(H, W, PIXEL, 0, d, T, N, K)
+        if d == 5:
+            model = H * W * 16  # a list model (floor(N/T) = 3 <= 8)
+        assert fp == model + N * H * W * 2
