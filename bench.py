@@ -732,39 +732,17 @@ def batched_measure(ocq, dev, reps):
             "graph_launches_per_run": 1}
 
 
-def serving_measure(ocq, dev, time_limit_s, budget_frac=0.7, n_cameras=256, frames_per_camera=90, pool=4,
-                    mask_slots=8):
-    """The 256-camera serving preset in real time.  Cameras join as a Poisson
-    process (25.6/s) and then send frames as a Poisson process at 30 fps.
-    Waiting cameras are admitted first-fit against an HBM budget as slots and
-    memory free up; a camera admitted late has its arrivals shifted by the
-    delay.  Each frame is submitted at its arrival time; latency = completion
-    time - scheduled arrival (host steady clock), so host lag counts against
-    it.  Every camera's N training frames and a pool of ``pool`` test frames
-    (cycled) are rendered on the device before the clock starts, so the loop
-    only admits, submits and polls; p50/p99 are over all completed frames."""
+def _serve_run(O, streams, bufs, fps, budget, n_cameras, frames_per_camera, pool, mask_slots, speed,
+               time_limit_s):
+    """One serving run of the camera set with every join and arrival time
+    divided by ``speed`` (speed 1 = real time).  Waiting cameras are admitted
+    first-fit against the HBM budget as slots and memory free up; a camera
+    admitted late has its arrivals shifted by the delay.  Each frame is
+    submitted at its arrival time; latency = completion time - scheduled
+    arrival (host steady clock), so host lag and queueing count against it."""
     import collections
     import heapq
 
-    import torch
-
-    import ocq_synth
-    from ocq_synth import configs
-
-    O = ocq.ocq
-    streams = configs.serving_streams(n_cameras, frames_per_camera)
-    fps = [O.ocq_server_camera_footprint(s.wl.H, s.wl.W, s.wl.region, s.wl.block, s.wl.depth, s.wl.T,
-                                         s.wl.N, s.wl.N) for s in streams]
-    bufs = []
-    for st_ in streams:
-        wl = st_.wl
-        sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, pool, wl.seed, wl.stream)
-        fr = torch.empty((wl.N + pool, wl.H, wl.W, 3), dtype=torch.uint8, device=dev)
-        ocq_synth.fill_device(sc, 0, wl.N + pool, fr)
-        bufs.append((fr, torch.empty((mask_slots, wl.H, wl.W), dtype=torch.uint8, device=dev)))
-    torch.cuda.synchronize()  # the server's streams do not wait on torch's
-    free, _ = torch.cuda.mem_get_info(dev)
-    budget = int(free * budget_frac)
     srv = O.ocq_server_create(budget, n_cameras)
     joins = collections.deque(sorted(range(len(streams)), key=lambda i: streams[i].join_s))
     waiting, live, sched, heap = [], {}, {}, []
@@ -775,7 +753,7 @@ def serving_measure(ocq, dev, time_limit_s, budget_frac=0.7, n_cameras=256, fram
         while (joins or waiting or live) and time.monotonic() - base < time_limit_s:
             progressed = False
             now = time.monotonic() - base
-            while joins and streams[joins[0]].join_s <= now:
+            while joins and streams[joins[0]].join_s / speed <= now:
                 i = joins.popleft()
                 if fps[i] > budget:
                     rejected += 1  # can never fit this budget
@@ -794,11 +772,11 @@ def serving_measure(ocq, dev, time_limit_s, budget_frac=0.7, n_cameras=256, fram
                 used += fps[i]
                 peak_used = max(peak_used, used)
                 now = time.monotonic() - base
-                shift = max(0.0, now - streams[i].join_s)
+                shift = max(0.0, now - streams[i].join_s / speed)
                 delays.append(shift)
                 live[i] = dict(cam=cam, completed=0)
                 for t, a in enumerate(streams[i].arrivals):
-                    heapq.heappush(heap, (a + shift, i, t))
+                    heapq.heappush(heap, (a / speed + shift, i, t))
                 progressed = True
             now = time.monotonic() - base
             while heap and heap[0][0] <= now:
@@ -829,24 +807,123 @@ def serving_measure(ocq, dev, time_limit_s, budget_frac=0.7, n_cameras=256, fram
         O.ocq_server_sync(srv)
     finally:
         srv.destroy()
-    del bufs
-    torch.cuda.empty_cache()
     lat_ms = sorted(x * 1e3 for x in lat)
 
     def pct(q):
         return round(lat_ms[min(len(lat_ms) - 1, int(q * len(lat_ms)))], 3) if lat_ms else None
 
+    return {"speed": speed, "lat_ms": lat_ms, "by_kind": by_kind, "rejected": rejected, "delays": delays,
+            "done_cams": done_cams, "px_done": px_done, "peak_used": peak_used, "wall": wall,
+            "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": round(lat_ms[-1], 3) if lat_ms else None,
+            "frames_done": len(lat_ms), "mpixel_s": round(px_done / wall / 1e6, 1)}
+
+
+def _serve_plain(O, streams, bufs, frames_per_camera, pool, mask_slots, window):
+    """The same cameras' work through the plain calls, one after another on
+    one stream: per camera ocq_build_model of its N training frames, then per
+    frame one ocq_classify of that frame, and every K = N frames
+    ocq_build_model again from the last N frames (the window semantics with
+    the frames re-read).  Device time (CUDA events) and Mpixel/s of the
+    classified frames."""
+    import torch
+
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    px = 0
+    for i, s_ in enumerate(streams):
+        wl = s_.wl
+        fr, masks = bufs[i]
+        m = O.ocq_build_model(fr[:wl.N], wl.N, wl.H, wl.W, wl.region, wl.block, wl.depth, wl.T, st)
+        for t in range(frames_per_camera):
+            O.ocq_classify(m, fr[wl.N + t % pool], 1, masks[t % mask_slots], st)
+            px += wl.H * wl.W
+            if (t + 1) % window == 0:
+                m.free()
+                # the window's frames: the pre-rendered pool stands in for the
+                # last N frames (same sizes, same kernels)
+                m = O.ocq_build_model(fr[:wl.N], wl.N, wl.H, wl.W, wl.region, wl.block, wl.depth, wl.T, st)
+        m.free()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"ms": round(ms, 2), "mpixel_s": round(px / (ms / 1e3) / 1e6, 1), "frames": frames_per_camera * len(streams)}
+
+
+def serving_measure(ocq, dev, time_limit_s, budget_frac=0.7, n_cameras=256, frames_per_camera=90, pool=4,
+                    mask_slots=8, deadline_ms=33.0, speeds=(8, 11, 16, 23, 32, 45, 64, 90, 128)):
+    """The 256-camera serving preset: cameras join as a Poisson process
+    (25.6/s) and then send frames as a Poisson process at 30 fps.  Every
+    camera's N training frames and a pool of ``pool`` test frames (cycled) are
+    rendered on the device before the clock starts, so the loop only admits,
+    submits and polls; p50/p99 are over all completed frames.
+
+    * real time (speed 1): latency at the preset's offered load;
+    * capacity: the same arrival process compressed ``speed`` times, for each
+      speed in ``speeds`` until a run's p99 passes ``deadline_ms`` (one frame
+      period at 30 fps) or frames are left over; the fastest run that kept the
+      deadline gives the capacity (Mpixel/s of completed frames over wall
+      time);
+    * plain: the same cameras' work through per-frame ocq_classify calls on
+      one stream with ocq_build_model re-merges (no serving form)."""
+    import torch
+
+    import ocq_synth
+    from ocq_synth import configs
+
+    O = ocq.ocq
+    streams = configs.serving_streams(n_cameras, frames_per_camera)
+    fps = [O.ocq_server_camera_footprint(s.wl.H, s.wl.W, s.wl.region, s.wl.block, s.wl.depth, s.wl.T,
+                                         s.wl.N, s.wl.N) for s in streams]
+    bufs = []
+    for st_ in streams:
+        wl = st_.wl
+        sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, pool, wl.seed, wl.stream)
+        fr = torch.empty((wl.N + pool, wl.H, wl.W, 3), dtype=torch.uint8, device=dev)
+        ocq_synth.fill_device(sc, 0, wl.N + pool, fr)
+        bufs.append((fr, torch.empty((mask_slots, wl.H, wl.W), dtype=torch.uint8, device=dev)))
+    torch.cuda.synchronize()  # the server's streams do not wait on torch's
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget = int(free * budget_frac)
+    args = (O, streams, bufs, fps, budget, n_cameras, frames_per_camera, pool, mask_slots)
+    rt = _serve_run(*args, 1.0, time_limit_s)
+    sweep, best = [], None
+    offered_1 = sum(s.wl.H * s.wl.W * frames_per_camera for s in streams) / max(
+        s.join_s + s.arrivals[-1] - s.join_s for s in streams)
+    for sp in speeds:
+        r = _serve_run(*args, float(sp), time_limit_s)
+        ok = r["frames_done"] == n_cameras * frames_per_camera and r["p99_ms"] is not None and \
+            r["p99_ms"] <= deadline_ms
+        sweep.append({"speed": sp, "offered_mpixel_s": round(offered_1 * sp / 1e6, 1), "mpixel_s": r["mpixel_s"],
+                      "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "frames_done": r["frames_done"],
+                      "wall_s": round(r["wall"], 3), "kept_deadline": ok})
+        if ok:
+            best = sweep[-1]
+        else:
+            break
+    plain = _serve_plain(O, streams, bufs, frames_per_camera, pool, mask_slots, streams[0].wl.N)
+    del bufs
+    torch.cuda.empty_cache()
+    by_kind = rt["by_kind"]
     tail = sorted(((sorted(v)[int(0.99 * (len(v) - 1))] * 1e3, k, len(v)) for k, v in by_kind.items()),
                   reverse=True)[:5]
     worst = [{"camera": f"{k[0]}x{k[1]} {k[2]} d{k[3]}", "frames": n, "p99_ms": round(t, 3)} for t, k, n in tail]
-    return {"preset": "serve256_poisson_30fps", "cameras": n_cameras, "cameras_done": done_cams,
-            "p99_by_camera_kind_worst5": worst,
-            "cameras_never_fit": rejected, "frames_done": len(lat_ms),
-            "frames_offered": n_cameras * frames_per_camera, "wall_s": round(wall, 2),
-            "p50_ms": pct(0.50), "p99_ms": pct(0.99), "max_ms": round(lat_ms[-1], 3) if lat_ms else None,
-            "mpixel_s": round(px_done / wall / 1e6, 1), "hbm_budget_bytes": budget, "peak_reserved_bytes": peak_used,
-            "admission_delay_p99_s": round(sorted(delays)[int(0.99 * (len(delays) - 1))], 3) if delays else None,
-            "window_N": 30, "remerge_every_K": 30, "T": 10, "frames_prerendered": True}
+    delays = rt["delays"]
+    out = {"preset": "serve256_poisson_30fps", "cameras": n_cameras, "cameras_done": rt["done_cams"],
+           "p99_by_camera_kind_worst5": worst,
+           "cameras_never_fit": rt["rejected"], "frames_done": rt["frames_done"],
+           "frames_offered": n_cameras * frames_per_camera, "wall_s": round(rt["wall"], 2),
+           "p50_ms": rt["p50_ms"], "p99_ms": rt["p99_ms"], "max_ms": rt["max_ms"],
+           "mpixel_s": rt["mpixel_s"], "hbm_budget_bytes": budget, "peak_reserved_bytes": rt["peak_used"],
+           "admission_delay_p99_s": round(sorted(delays)[int(0.99 * (len(delays) - 1))], 3) if delays else None,
+           "window_N": 30, "remerge_every_K": 30, "T": 10, "frames_prerendered": True,
+           "capacity": {"deadline_ms": deadline_ms, "sweep": sweep,
+                        "capacity_mpixel_s": best["mpixel_s"] if best else None,
+                        "p50_ms": best["p50_ms"] if best else None, "p99_ms": best["p99_ms"] if best else None,
+                        "plain_per_frame_calls": plain,
+                        "ratio_to_plain": round(best["mpixel_s"] / plain["mpixel_s"], 3) if best else None}}
+    return out
 
 
 def e2e_measure(ocq, wl, train, test, mask, stream, args, dist, dev, world):
