@@ -112,6 +112,22 @@ ocq_status ocq_occupancy(const uint8_t *frames, int n, int H, int W, ocq_region 
                          uint64_t *occ, void *stream);
 
 /*
+ * S3 alone (Alg. 2) over leaf sets given as bitsets: the merged model of N
+ * per-frame trees whose regions were each split into `parts` pieces (for
+ * example row bands of whole frames held by different GPUs).  A frame's tree
+ * of a region holds a leaf iff the tree of some piece does (Alg. 1 inserts
+ * every pixel of the region into that one tree), so the pieces' bitsets are
+ * ORed, and a leaf is kept when at least T of the N frames hold it.
+ * occ: device, parts * N * regions * words_per_region u64 in the exported
+ * layout, piece-major, each piece as ocq_occupancy writes it (row f*regions +
+ * r).  H, W: the whole frame's size (regions count as for ocq_build_model).
+ * The model has leaf bitset rows (no kept-leaf lists).  Scratch is
+ * stream-ordered device memory.  Errors as ocq_build_model.
+ */
+ocq_status ocq_merge_occupancy(const uint64_t *occ, int parts, int N, int H, int W, ocq_region region, int depth,
+                               int T, void *stream, ocq_model **out);
+
+/*
  * S1-S3 (Sec. 3, Alg. 1 + Alg. 2): build the merged model of N training
  * frames.  frames: device, N*H*W*3 bytes.  On success *out owns a new
  * device-resident model, ready for use on `stream` once the enqueued work has

@@ -200,6 +200,43 @@ ocq_status ocq_build_model(const uint8_t *frames, int N, int H, int W, ocq_regio
   return OCQ_OK;
 }
 
+ocq_status ocq_merge_occupancy(const uint64_t *occ, int parts, int N, int H, int W, ocq_region region, int depth,
+                               int T, void *stream, ocq_model **out) {
+  g_err[0] = 0;
+  if (!out) {
+    set_error("ocq_merge_occupancy: out is NULL");
+    return OCQ_EINVAL;
+  }
+  *out = nullptr;
+  ocq_status rc = check_geometry(H, W, region, depth);
+  if (rc != OCQ_OK) return rc;
+  if (!occ || parts < 1 || N < 1 || N > 65535 || T < 1 || T > N) {
+    set_error("ocq_merge_occupancy: need occ != NULL, parts >= 1 and 1 <= T <= N <= 65535 (parts=%d, N=%d, T=%d)",
+              parts, N, T);
+    return OCQ_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  ocq_model *m = new_model(H, W, region, depth, T, N, st, &rc, true);
+  if (!m) return rc;
+  const int64_t rows = (int64_t)N * m->R;
+  const int64_t w64 = rows * wpr64(depth), w32 = rows * m->wpr;
+  uint64_t *un = nullptr;
+  uint32_t *planar = nullptr;
+  if (parts > 1) rc = cuda_status(malloc_async((void **)&un, (size_t)w64 * 8, st), "merge scratch");
+  if (rc == OCQ_OK) rc = cuda_status(malloc_async((void **)&planar, (size_t)w32 * 4, st), "merge scratch");
+  if (rc == OCQ_OK && parts > 1) rc = launch_or_parts(occ, parts, w64, un, st);
+  if (rc == OCQ_OK) rc = launch_import(parts > 1 ? un : occ, rows, depth, planar, st);
+  if (rc == OCQ_OK) rc = launch_merge_counts(planar, N, m->R * m->wpr, (uint32_t)T, m->bits, st);
+  if (un) cudaFreeAsync(un, st);
+  if (planar) cudaFreeAsync(planar, st);
+  if (rc != OCQ_OK) {
+    ocq_model_free(m);
+    return rc;
+  }
+  *out = m;
+  return OCQ_OK;
+}
+
 ocq_status ocq_build_model_groups(const uint8_t *frames, int N, int H, int W, ocq_region region, int depth, int T,
                                   int group, void *stream, ocq_model **out) {
   g_err[0] = 0;

@@ -458,6 +458,14 @@ static void launch_occ_frame(const uint8_t *frames, int64_t hw, int f0, int nf, 
   count_launch();
 }
 
+ocq_status launch_merge_counts(const uint32_t *occ, int N, int64_t nwords, uint32_t T, uint32_t *model,
+                               cudaStream_t st) {
+  const int P = bit_length((uint32_t)N);
+  planes_merge_kernel<<<grid_cap(nwords, 256, 8), 256, 0, st>>>(occ, N, nwords, nullptr, P, 1, 1, T, model);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "planes_merge_kernel");
+}
+
 ocq_status launch_frame_occupancy(const uint8_t *frames, int n, int H, int W, int depth, uint32_t *occ,
                                   cudaStream_t st) {
   const int64_t hw = (int64_t)H * W;

@@ -174,6 +174,12 @@ ocq_status launch_occupancy(const uint8_t *frames, int n, int H, int W, int kind
                             uint64_t *occ, cudaStream_t st);
 ocq_status launch_export(const uint32_t *bits, int64_t R, int depth, uint64_t *dst, cudaStream_t st);
 ocq_status launch_import(const uint64_t *src, int64_t R, int depth, uint32_t *bits, cudaStream_t st);
+// out[w] = OR of occ[p * words + w] over p < parts (exported layout).
+ocq_status launch_or_parts(const uint64_t *occ, int parts, int64_t words, uint64_t *out, cudaStream_t st);
+// model[w] = (number of the N rows of occ holding bit) >= T, word-wise over
+// nwords internal words (occ: N * nwords, N <= 65535).
+ocq_status launch_merge_counts(const uint32_t *occ, int N, int64_t nwords, uint32_t T, uint32_t *model,
+                               cudaStream_t st);
 // Serving windows (window.cu): per-frame occupancy kept in place of frames.
 // Leaf bitsets of n whole frames (internal order) ORed into occ[f * wpr32(d)]
 // (occ zero beforehand).

@@ -169,6 +169,24 @@ ocq_status launch_import_list(const uint64_t *src, int64_t R, int depth, int lim
   return cuda_status(cudaGetLastError(), "import_list_kernel");
 }
 
+// Union of `parts` leaf-set bitsets per row (exported layout): the tree of a
+// region whose pixels were split into parts holds a leaf iff some part's tree
+// does (Alg. 1 inserts every pixel of the region into one tree).
+__global__ void or_parts_kernel(const uint64_t *__restrict__ occ, int parts, int64_t words,
+                                uint64_t *__restrict__ out) {
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t v = 0;
+    for (int p = 0; p < parts; ++p) v |= occ[(int64_t)p * words + w];
+    out[w] = v;
+  }
+}
+
+ocq_status launch_or_parts(const uint64_t *occ, int parts, int64_t words, uint64_t *out, cudaStream_t st) {
+  or_parts_kernel<<<grid_for(words, 256, 8), 256, 0, st>>>(occ, parts, words, out);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "or_parts_kernel");
+}
+
 ocq_status launch_import(const uint64_t *src, int64_t R, int depth, uint32_t *bits, cudaStream_t st) {
   const int64_t total = R * wpr32(depth);
   import_kernel<<<grid_for(total, 256, 8), 256, 0, st>>>(src, R, depth, wpr64(depth), wpr32(depth), bits);

@@ -80,6 +80,7 @@ SIGNATURES = {
     "ocq_detect_host": (_i32, [_vp, _i32, _vp, _i32, _i32, _i32, ocq_region, _i32, _i32, _vp, _vp,
                                ctypes.POINTER(_vp)]),
     "ocq_kernel_launches": (ctypes.c_uint64, []),
+    "ocq_merge_occupancy": (_i32, [_vp, _i32, _i32, _i32, _i32, ocq_region, _i32, _i32, _vp, ctypes.POINTER(_vp)]),
     "ocq_build_frame_noalloc": (_i32, [_vp, _i32, _i32, _i32, _i32, _i32, _vp, _vp]),
     "ocq_batch_create": (_i32, [ctypes.POINTER(ocq_stream_desc), _i32, _vp, ctypes.POINTER(_vp)]),
     "ocq_batch_run": (_i32, [_vp, _vp]),
@@ -230,6 +231,13 @@ def ocq_build_model(frames, N, H, W, kind, block, depth, T, stream=None) -> Mode
     out = ctypes.c_void_p()
     _check(load().ocq_build_model(_p(frames), N, H, W, _region(kind, block), depth, T, _s(stream),
                                   ctypes.byref(out)))
+    return Model(out.value)
+
+
+def ocq_merge_occupancy(occ, parts, N, H, W, kind, block, depth, T, stream=None) -> Model:
+    out = ctypes.c_void_p()
+    _check(load().ocq_merge_occupancy(_p(occ), parts, N, H, W, _region(kind, block), depth, T, _s(stream),
+                                      ctypes.byref(out)))
     return Model(out.value)
 
 
