@@ -151,11 +151,11 @@ __device__ __noinline__ void pixel_mg_dispatch(const BStream &S, int64_t t0, int
 __device__ __noinline__ void block_tb_dispatch(const BStream &S, int64_t t0, int64_t t1) {
   for (int64_t t = t0; t < t1; t += kBatchThreads / 32) {
     switch (S.depth) {
-      case 1: classify_block_tb_body<1, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
-      case 2: classify_block_tb_body<2, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
-      case 3: classify_block_tb_body<3, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
-      case 4: classify_block_tb_body<4, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
-      default: classify_block_tb_body<5, 8>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
+      case 1: classify_block_tb_body<1, 4>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
+      case 2: classify_block_tb_body<2, 4>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
+      case 3: classify_block_tb_body<3, 4>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
+      case 4: classify_block_tb_body<4, 4>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
+      default: classify_block_tb_body<5, 4>(S.test, S.F, S.H, S.W, S.block, S.bw, S.nseg, S.model, S.mask, t); break;
     }
   }
 }

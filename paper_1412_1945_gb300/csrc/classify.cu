@@ -24,6 +24,7 @@
 //                                ring of stages filled by bulk asynchronous
 //                                copies (cp.async.bulk + mbarrier), so each
 //                                row is read from HBM about once per launch.
+#include <algorithm>
 #include <cstdint>
 
 #include "classify_bodies.cuh"
@@ -72,14 +73,21 @@ __global__ void __launch_bounds__(128) classify_pixel_tb_kernel(const uint8_t *_
   }
 }
 
+// Item u = chunk * tiles + tile: frames [chunk * fchunk, chunk * fchunk +
+// fchunk) of tile `tile` (one chunk of all F frames unless the frame is too
+// small to give every warp of the grid a tile).
 template <int D>
 __global__ void __launch_bounds__(256) classify_block_tb_kernel(const uint8_t *__restrict__ frames, int F, int H,
                                                                 int W, int b, int bw, int nseg, int64_t tiles,
+                                                                int fchunk, int64_t items,
                                                                 const uint32_t *__restrict__ model,
                                                                 uint8_t *__restrict__ mask) {
   const int64_t nw = (int64_t)gridDim.x * 8;
-  for (int64_t t = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); t < tiles; t += nw)
-    classify_block_tb_body<D, 8>(frames, F, H, W, b, bw, nseg, model, mask, t);
+  for (int64_t u = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); u < items; u += nw) {
+    const int64_t c = u / tiles;
+    const int f0 = (int)(c * fchunk);
+    classify_block_tb_body<D, 4>(frames, F, H, W, b, bw, nseg, model, mask, u - c * tiles, f0, f0 + fchunk);
+  }
 }
 
 // Pixel regions, depth 4-5, models with a kept-leaf index.
@@ -521,15 +529,24 @@ static ocq_status launch_block_tb(const ocq_model *m, const uint8_t *frames, int
   const int bh = (m->H + m->block - 1) / m->block;
   const int nseg = (m->W + 127) / 128;
   const int64_t tiles = (int64_t)bh * nseg * m->block;
-  const int64_t ctas = (tiles + 7) / 8;
   const int64_t cap = (int64_t)sm_count() * g_block_tb_cps;
+  // Split the frames when the tiles alone cannot give each warp of the grid
+  // two items (a frame of a few hundred thousand pixels), in chunks of at
+  // least 16 frames.
+  int chunks = 1;
+  if (tiles < 2 * cap * 8) chunks = (int)std::min<int64_t>((2 * cap * 8 + tiles - 1) / tiles, (F + 15) / 16);
+  if (chunks < 1) chunks = 1;
+  const int fchunk = (F + chunks - 1) / chunks;
+  chunks = (F + fchunk - 1) / fchunk;
+  const int64_t items = tiles * chunks;
+  const int64_t ctas = (items + 7) / 8;
   static bool carved = false;
   if (!carved) {
     cudaFuncSetAttribute(classify_block_tb_kernel<D>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     carved = true;
   }
   classify_block_tb_kernel<D><<<(unsigned)(ctas < cap ? ctas : cap), 256, 0, st>>>(
-      frames, F, m->H, m->W, m->block, bw, nseg, tiles, m->bits, mask);
+      frames, F, m->H, m->W, m->block, bw, nseg, tiles, fchunk, items, m->bits, mask);
   count_launch();
   return cuda_status(cudaGetLastError(), "classify_block_tb_kernel");
 }

@@ -151,11 +151,17 @@ __device__ __forceinline__ void classify_pixel_tb_body(const uint8_t *__restrict
 // k = t % b of block row br and 128-pixel segment sg, t / b = br * nseg + sg,
 // so the b warps of consecutive tiles cover whole blocks: a CTA of 8 warps
 // reads each block row's model sectors once per SM when b <= 8.
+//
+// Frames [fb, fe) only (fe < 0: all F), so a launch can split the frames of a
+// small frame over more warps.  The loads of the next PF frames are in flight
+// while the current PF are looked up (two register buffers).
 template <int D, int PF>
 __device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict__ frames, int F, int H, int W,
                                                        int b, int bw, int nseg, const uint32_t *model,
-                                                       uint8_t *__restrict__ mask, int64_t t) {
+                                                       uint8_t *__restrict__ mask, int64_t t, int fb = 0,
+                                                       int fe = -1) {
   constexpr int64_t WPR = D == 1 ? 1 : (int64_t)1 << (3 * D - 5);
+  if (fe < 0 || fe > F) fe = F;
   const int lane = threadIdx.x & 31;
   const int k = (int)(t % b);
   const int64_t q = t / b;
@@ -168,17 +174,18 @@ __device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict
   const uint8_t *row = reinterpret_cast<const uint8_t *>(model + ((int64_t)br * bw + x / b) * WPR);
   const uint8_t *src = frames + pq * 3;
   uint8_t *dst = mask + pq;
-  for (int f0 = 0; f0 < F; f0 += PF) {
-    uint32_t w[PF][3];
+  auto load = [&](uint32_t (&w)[PF][3], int f0) {
 #pragma unroll
     for (int j = 0; j < PF; ++j)
-      if (f0 + j < F) {
+      if (f0 + j < fe) {
         const uint8_t *s = src + (int64_t)(f0 + j) * hw * 3;
         w[j][0] = ld_stream4(s), w[j][1] = ld_stream4(s + 4), w[j][2] = ld_stream4(s + 8);
       }
+  };
+  auto work = [&](const uint32_t (&w)[PF][3], int f0) {
 #pragma unroll
     for (int j = 0; j < PF; ++j) {
-      if (f0 + j >= F) break;
+      if (f0 + j >= fe) break;
       uint32_t m[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) m[i] = (w[j][i] >> (8 - D)) & byte_mask(D);
@@ -190,6 +197,15 @@ __device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict
       });
       st_stream4(dst + (int64_t)(f0 + j) * hw, pack_mask4(bg[0], bg[1], bg[2], bg[3]));
     }
+  };
+  uint32_t wa[PF][3], wb[PF][3];
+  load(wa, fb);
+  for (int f0 = fb; f0 < fe; f0 += 2 * PF) {
+    load(wb, f0 + PF);
+    work(wa, f0);
+    if (f0 + PF >= fe) break;
+    load(wa, f0 + 2 * PF);
+    work(wb, f0 + PF);
   }
 }
 
