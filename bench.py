@@ -712,7 +712,7 @@ def batched_measure(ocq, dev, reps):
     tune_s = time.perf_counter() - t0
     chosen = O.ocq_batch_get_mode(b)
     form_ms = {}
-    for mode in (1 - chosen, chosen):  # the autotuner's choice last, so it is what the batch keeps
+    for mode in [m for m in (0, 1, 2) if m != chosen] + [chosen]:  # the autotuner's choice last: the batch keeps it
         O.ocq_batch_set_mode(b, mode)
         form_ms[mode] = timed(lambda: O.ocq_batch_run(b, stream), reps)
         O.ocq_batch_status(b, stream)
@@ -722,7 +722,7 @@ def batched_measure(ocq, dev, reps):
     b.destroy()
     del descs
     torch.cuda.empty_cache()
-    names = {0: "persistent_kernel", 1: "graph_of_stream_branches"}
+    names = {0: "persistent_kernel", 1: "graph_of_stream_branches", 2: "grouped_launches_per_body"}
     return {"streams": 64, "pixels_per_run": px, "plain_ms": round(plain_ms, 3), "batched_ms": round(batched_ms, 3),
             "plain_mpixel_s": round(px / (plain_ms / 1e3) / 1e6, 1),
             "batched_mpixel_s": round(px / (batched_ms / 1e3) / 1e6, 1),

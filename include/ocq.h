@@ -262,9 +262,17 @@ ocq_status ocq_batch_get_work(const ocq_batch *batch, int region_kind, int *unit
  *   OCQ_BATCH_GRAPH       one branch per camera stream running that stream's
  *                         plain kernels (build, then classify); branches run
  *                         concurrently.
- * Both give results identical to the per-stream calls.  Changing the form
+ *   OCQ_BATCH_GROUPED     one launch per kernel body (and depth, block size,
+ *                         counter or list length) over all the streams that
+ *                         use it, each launch with that body's own CTA shape,
+ *                         shared memory and residency; the launches of one
+ *                         class of streams (whole frame, blocks, pixels at
+ *                         depth <= 3, pixels at depth 4-5) run in order on
+ *                         one branch, the classes' branches concurrently;
+ *                         streams outside those bodies run their plain kernels.
+ * All give results identical to the per-stream calls.  Changing the form
  * drops the captured graph; the next run captures it again. */
-enum { OCQ_BATCH_PERSISTENT = 0, OCQ_BATCH_GRAPH = 1 };
+enum { OCQ_BATCH_PERSISTENT = 0, OCQ_BATCH_GRAPH = 1, OCQ_BATCH_GROUPED = 2 };
 ocq_status ocq_batch_set_mode(ocq_batch *batch, int mode);
 int ocq_batch_get_mode(const ocq_batch *batch);
 /* Persistent form: whether per-pixel streams of depth <= 3 classify from rows
@@ -276,7 +284,7 @@ int ocq_batch_get_staging(const ocq_batch *batch);
 /* Autotuner: times candidate work sizes per region kind on this batch's own
  * inputs (`reps` runs each, on `stream`) and keeps the fastest (results are
  * cached per (region kind, depths, sizes, frames) signature for the process),
- * then times both forms and keeps the faster. */
+ * then times the three forms and keeps the fastest. */
 ocq_status ocq_batch_autotune(ocq_batch *batch, int reps, void *stream);
 void ocq_batch_destroy(ocq_batch *batch);
 

@@ -23,6 +23,7 @@
 
 #include "build_bodies.cuh"
 #include "classify_bodies.cuh"
+#include "grouped.cuh"
 
 namespace ocq {
 
@@ -343,6 +344,12 @@ struct ocq_batch {
   std::vector<cudaStream_t> side;  // branch streams of the graph form
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
+  // grouped form: launches per kernel body over the streams they cover, and
+  // the streams left to their plain kernels
+  std::vector<GLaunch> glaunch;
+  std::vector<int> gfallback;
+  GSeg *d_gsegs = nullptr;
+  bool gplanned = false;
 };
 
 static int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -538,14 +545,102 @@ static ocq_status enqueue_branches(ocq_batch *b, cudaStream_t cs) {
   return rc;
 }
 
+// Grouped form: one launch per kernel body and template over all streams it
+// covers (grouped.cu), chained per class of streams (whole frame, blocks,
+// pixels at depth <= 3, pixels at depth 4-5) on one branch each; streams
+// outside those bodies run their plain kernels on branches of their own.
+static ocq_status plan_grouped(ocq_batch *b) {
+  if (b->gplanned) return OCQ_OK;
+  std::vector<GStreamIn> in;
+  for (size_t s = 0; s < b->hs.size(); ++s) {
+    const BStream &h = b->hs[s];
+    GStreamIn x;
+    x.train = h.train, x.test = h.test, x.mask = h.mask, x.model = h.model, x.occ = h.occ, x.kept = h.kept;
+    x.N = h.N, x.F = h.F, x.H = h.H, x.W = h.W, x.kind = h.kind, x.block = h.block, x.depth = h.depth, x.T = h.T;
+    x.km = h.km, x.kl = h.kl;
+    in.push_back(x);
+  }
+  ocq_status rc = grouped_plan(in, b->glaunch, b->gfallback);
+  if (rc != OCQ_OK) return rc;
+  size_t nseg = 0;
+  for (const GLaunch &L : b->glaunch) nseg += L.segs.size();
+  if (nseg > 0) {
+    rc = cuda_status(cudaMalloc((void **)&b->d_gsegs, nseg * sizeof(GSeg)), "grouped segments");
+    if (rc != OCQ_OK) return rc;
+    size_t at = 0;
+    for (GLaunch &L : b->glaunch) {
+      L.dev = b->d_gsegs + at;
+      rc = cuda_status(cudaMemcpy(L.dev, L.segs.data(), L.segs.size() * sizeof(GSeg), cudaMemcpyHostToDevice),
+                       "upload grouped segments");
+      if (rc != OCQ_OK) return rc;
+      at += L.segs.size();
+    }
+  }
+  b->gplanned = true;
+  return OCQ_OK;
+}
+
+static ocq_status ensure_side_streams(ocq_batch *b, int n) {
+  ocq_status rc = OCQ_OK;
+  if (!b->fork) rc = cuda_status(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), "fork event");
+  while (rc == OCQ_OK && (int)b->side.size() < n) {
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t e2 = nullptr;
+    rc = cuda_status(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking), "branch stream");
+    if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming), "join event");
+    if (s2) b->side.push_back(s2);
+    if (e2) b->joins.push_back(e2);
+  }
+  return rc;
+}
+
+static ocq_status enqueue_grouped(ocq_batch *b, cudaStream_t cs) {
+  ocq_status rc = plan_grouped(b);
+  if (rc != OCQ_OK) return rc;
+  const int nfb = std::min<int>((int)b->gfallback.size(), 8);
+  const int NB = GB_COUNT + nfb;
+  rc = ensure_side_streams(b, NB);
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(b->fork, cs), "fork");
+  for (int i = 0; i < NB && rc == OCQ_OK; ++i) rc = cuda_status(cudaStreamWaitEvent(b->side[i], b->fork, 0), "fork wait");
+  // whole-frame occupancy is ORed into zeroed scratch
+  for (size_t s = 0; s < b->hs.size() && rc == OCQ_OK; ++s) {
+    const BStream &h = b->hs[s];
+    if (h.kind != OCQ_REGION_FRAME || !h.occ) continue;
+    if (std::find(b->gfallback.begin(), b->gfallback.end(), (int)s) != b->gfallback.end()) continue;
+    rc = cuda_status(cudaMemsetAsync(h.occ, 0, (size_t)h.N * h.wpr * 4, b->side[GB_FRAME]), "clear occupancy");
+  }
+  for (const GLaunch &L : b->glaunch) {
+    if (rc != OCQ_OK) break;
+    rc = grouped_launch(L, b->side[L.branch]);
+  }
+  for (size_t k = 0; k < b->gfallback.size() && rc == OCQ_OK; ++k) {
+    const int s = b->gfallback[k];
+    const ocq_stream_desc &d = b->desc[s];
+    cudaStream_t st = b->side[GB_COUNT + (int)(k % (size_t)nfb)];
+    rc = launch_build(d.train, d.N, b->models[s], st);
+    if (rc == OCQ_OK && d.F > 0) rc = launch_classify(b->models[s], d.test, d.F, d.mask, st);
+  }
+  for (int i = 0; i < NB && rc == OCQ_OK; ++i) {
+    rc = cuda_status(cudaEventRecord(b->joins[i], b->side[i]), "join");
+    if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent(cs, b->joins[i], 0), "join wait");
+  }
+  return rc;
+}
+
 static ocq_status capture(ocq_batch *b) {
   free_graph(b);
+  if (b->mode == OCQ_BATCH_GROUPED) {  // plan (device tables, kernel attributes) before capturing
+    ocq_status rp = plan_grouped(b);
+    if (rp != OCQ_OK) return rp;
+  }
   cudaStream_t cs = nullptr;
   ocq_status rc = cuda_status(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
   if (rc != OCQ_OK) return rc;
   rc = cuda_status(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
   if (rc == OCQ_OK) {
-    ocq_status r2 = b->mode == OCQ_BATCH_GRAPH ? enqueue_branches(b, cs) : enqueue_run(b, cs);
+    ocq_status r2 = b->mode == OCQ_BATCH_GRAPH     ? enqueue_branches(b, cs)
+                    : b->mode == OCQ_BATCH_GROUPED ? enqueue_grouped(b, cs)
+                                                   : enqueue_run(b, cs);
     cudaGraph_t g = nullptr;
     rc = cuda_status(cudaStreamEndCapture(cs, &g), "end capture");
     if (rc == OCQ_OK) rc = r2;
@@ -792,8 +887,8 @@ ocq_status ocq_batch_autotune(ocq_batch *b, int reps, void *stream) {
   }
   // Then the form: the persistent kernel with the chosen work sizes against
   // the graph of per-stream branches, each captured and replayed.
-  float t[2] = {1e30f, 1e30f};
-  for (int mode = 0; mode < 2 && rc == OCQ_OK; ++mode) {
+  float t[3] = {1e30f, 1e30f, 1e30f};
+  for (int mode = 0; mode < 3 && rc == OCQ_OK; ++mode) {
     free_graph(b);
     b->mode = mode;
     rc = capture(b);
@@ -808,7 +903,9 @@ ocq_status ocq_batch_autotune(ocq_batch *b, int reps, void *stream) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc == OCQ_OK) {
-    const int best = t[1] < t[0] ? OCQ_BATCH_GRAPH : OCQ_BATCH_PERSISTENT;
+    int best = OCQ_BATCH_PERSISTENT;
+    for (int mode = 1; mode < 3; ++mode)
+      if (t[mode] < t[best]) best = mode;
     if (best != b->mode) free_graph(b);
     b->mode = best;
   }
@@ -835,6 +932,7 @@ void ocq_batch_destroy(ocq_batch *b) {
   if (b->d_streams) cudaFree(b->d_streams);
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_ctr) cudaFree(b->d_ctr);
+  if (b->d_gsegs) cudaFree(b->d_gsegs);
   delete b;
 }
 
@@ -852,8 +950,8 @@ ocq_status ocq_batch_status(ocq_batch *b, void *stream) {
     set_error("a batched item gave up waiting for its stream's model");
     return OCQ_ETIMEOUT;
   }
-  const bool ct = classify_take_timeout(), bt = build_take_timeout();
-  if (ct || bt) {
+  const bool ct = classify_take_timeout(), bt = build_take_timeout(), gt = grouped_take_timeout();
+  if (ct || bt || gt) {
     set_error("a kernel of the graph form gave up waiting for a copy");
     return OCQ_ETIMEOUT;
   }
@@ -861,7 +959,7 @@ ocq_status ocq_batch_status(ocq_batch *b, void *stream) {
 }
 
 ocq_status ocq_batch_set_mode(ocq_batch *b, int mode) {
-  if (!b || (mode != OCQ_BATCH_PERSISTENT && mode != OCQ_BATCH_GRAPH)) {
+  if (!b || (mode != OCQ_BATCH_PERSISTENT && mode != OCQ_BATCH_GRAPH && mode != OCQ_BATCH_GROUPED)) {
     set_error("ocq_batch_set_mode: bad arguments");
     return OCQ_EINVAL;
   }

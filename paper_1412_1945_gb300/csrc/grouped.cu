@@ -1,0 +1,399 @@
+// Grouped launches of the batched form: one launch per kernel body and
+// template (depth, block size, counter or list length) over every camera
+// stream that uses it.  Each stream owns a contiguous range of the launch's
+// CTAs (its virtual grid: CTA vb of vg, found by a binary search on the CTA
+// index), and each CTA runs the body the plain per-stream kernel runs, with
+// that kernel's CTA shape, shared memory and residency, so a stream's result
+// is the plain path's bit for bit.  The launches of one class of streams form
+// a chain (builds, then classification) in one branch of the batch's graph;
+// the classes' branches run concurrently.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "build_bodies.cuh"
+#include "classify_bodies.cuh"
+#include "grouped.cuh"
+
+namespace ocq {
+
+// Set when a bounded wait of a grouped body gives up; read and cleared by
+// grouped_take_timeout().
+__device__ unsigned int g_grouped_timeout;
+
+__device__ __forceinline__ const GSeg &seg_of(const GSeg *__restrict__ g, int n, int64_t &vb) {
+  int lo = 0, hi = n - 1;  // the last segment whose first CTA is <= blockIdx.x
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (g[mid].cta0 <= (int64_t)blockIdx.x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  vb = (int64_t)blockIdx.x - g[lo].cta0;
+  return g[lo];
+}
+
+// ---- whole frame -------------------------------------------------------------------
+
+template <int D>
+__global__ void __launch_bounds__(256) g_occ_frame(const GSeg *__restrict__ g, int n) {
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  occ_frame_body<D>(s.in, s.hw, 0, kGroupOccChunk, s.occ, vb % s.aux, vb / s.aux);
+}
+
+__global__ void __launch_bounds__(256) g_merge(const GSeg *__restrict__ g, int n) {
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  planes_merge_body(s.occ, s.N, s.units, nullptr, s.P, 1, 1, (uint32_t)s.T, s.model, vb, s.vg);
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) g_cls_frame(const GSeg *__restrict__ g, int n) {
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  classify_frame_body<D>(s.in, (int64_t)s.F * s.hw, s.model, s.mask, vb, s.vg);
+}
+
+// ---- blocks ----------------------------------------------------------------------
+
+template <int D, int B>
+__global__ void __launch_bounds__(256, BlockTileCfg<D, B>::MINB) g_block_tile(const GSeg *__restrict__ g, int n) {
+  extern __shared__ __align__(16) uint8_t gt_smem[];
+  constexpr int WB = BlockTileCfg<D, B>::WARP_SMEM;
+  uint8_t *wsm = gt_smem + (threadIdx.x >> 5) * WB;
+  for (int i = threadIdx.x & 31; i < WB / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
+  __syncwarp();
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  build_block_tile_body<D, B, BlockTileCfg<D, B>::PF>(s.in, s.N, s.H, s.W, s.bw, (uint32_t)s.T, s.model,
+                                                      vb * 8 + (threadIdx.x >> 5), s.units, s.vg * 8, wsm);
+}
+
+template <int D, int PPL>
+__global__ void __launch_bounds__(256) g_block_warp(const GSeg *__restrict__ g, int n) {
+  extern __shared__ uint32_t gw_tabs[];
+  constexpr int S = WarpTableCfg<D>::S;
+  uint32_t *tab = gw_tabs + (threadIdx.x >> 5) * S;
+  for (int i = threadIdx.x & 31; i < S; i += 32) tab[i] = 0u;
+  __syncwarp();
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  build_block_warp_body<D, PPL>(s.in, s.N, s.H, s.W, s.block, s.bw, (uint32_t)s.T, s.model,
+                                vb * 8 + (threadIdx.x >> 5), s.units, s.vg * 8, tab);
+}
+
+// items u = chunk * tiles + tile over frames [chunk * fchunk, + fchunk)
+template <int D>
+__global__ void __launch_bounds__(256) g_block_tb(const GSeg *__restrict__ g, int n) {
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  const int64_t tiles = s.aux;
+  for (int64_t u = vb * 8 + (threadIdx.x >> 5); u < s.units; u += s.vg * 8) {
+    const int64_t c = u / tiles;
+    const int f0 = (int)(c * s.aux2);
+    classify_block_tb_body<D, 4>(s.in, s.F, s.H, s.W, s.block, s.bw, s.aux3, s.model, s.mask, u - c * tiles, f0,
+                                 f0 + s.aux2);
+  }
+}
+
+// ---- pixel locations ----------------------------------------------------------------
+
+template <int D, int NT, int FPS, int S>
+__global__ void __launch_bounds__(NT + 32) g_pixel_ws_build(const GSeg *__restrict__ g, int n) {
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  build_pixel_ws_body<D, NT, FPS, S, false, false>(s.in, s.N, s.hw, s.units, (uint32_t)s.T, s.model, nullptr, vb,
+                                                   s.vg, &g_grouped_timeout);
+}
+
+template <int D, int NW, int PPT, int S, int FPS>
+__global__ void __launch_bounds__(NW * 32 + 32, 1) g_pixel_ws_cls(const GSeg *__restrict__ g, int n) {
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  classify_pixel_ws_body<D, NW, PPT, S, FPS>(s.in, s.F, s.hw, s.units, s.model, s.mask, vb, s.vg,
+                                             &g_grouped_timeout);
+}
+
+template <int D, int KM>
+__global__ void __launch_bounds__(128) g_pixel_mg(const GSeg *__restrict__ g, int n) {
+  extern __shared__ __align__(16) uint8_t gm_smem[];
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  leaf_t<D> *codes = reinterpret_cast<leaf_t<D> *>(gm_smem) + (size_t)(threadIdx.x >> 5) * s.N * 32;
+  const int64_t tile = vb * 4 + (threadIdx.x >> 5);
+  if (tile * 32 >= s.hw) return;  // whole warps only
+  build_pixel_mg_body<D, KM>(s.in, s.N, s.hw, (uint32_t)s.T, s.model, tile, codes, 1, s.kept);
+}
+
+template <int D, int KL>
+__global__ void __launch_bounds__(128) g_pixel_list(const GSeg *__restrict__ g, int n) {
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  for (int64_t t = vb * 4 + (threadIdx.x >> 5); t < s.units; t += s.vg * 4)
+    classify_pixel_list_body<D, 8, KL>(s.in, s.F, s.hw, s.kept, s.mask, t);
+}
+
+// ---- host side ----------------------------------------------------------------------
+
+using GKern = void (*)(const GSeg *, int);
+
+struct KInfo {
+  GKern fn = nullptr;
+  int threads = 256;
+  size_t smem = 0;  // fixed part; GK_PIX_MG adds its per-stream codes
+};
+
+template <int D>
+static KInfo kinfo_d(int kind, int b) {
+  KInfo k;
+  constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  switch (kind) {
+    case GK_OCC:
+      if constexpr (D <= 6) k.fn = g_occ_frame<D>, k.smem = (size_t)WPR * 4;
+      break;
+    case GK_CLS_FRAME:
+      if constexpr (D <= 6) k.fn = g_cls_frame<D>, k.smem = (size_t)WPR * (D <= 4 ? 32 : 1) * 4;
+      break;
+    case GK_BLOCK_TILE:
+      if constexpr (D >= 2 && D <= 5) {
+        if (b == 16) k.fn = g_block_tile<D, 16>, k.smem = (size_t)8 * BlockTileCfg<D, 16>::WARP_SMEM;
+        if constexpr (D <= 3)
+          if (b == 8) k.fn = g_block_tile<D, 8>, k.smem = (size_t)8 * BlockTileCfg<D, 8>::WARP_SMEM;
+      }
+      break;
+    case GK_BLOCK_WARP:
+      if constexpr (D <= 5) {
+        k.smem = (size_t)8 * WarpTableCfg<D>::S * 4;
+        k.fn = b == 1 ? g_block_warp<D, 1> : b == 2 ? g_block_warp<D, 2> : b == 4 ? g_block_warp<D, 4> : g_block_warp<D, 8>;
+      }
+      break;
+    case GK_BLOCK_TB:
+      if constexpr (D <= 5) k.fn = g_block_tb<D>;
+      break;
+    case GK_PIX_WS_BUILD:
+      if constexpr (D <= 3) k.fn = g_pixel_ws_build<D, 128, 8, 3>, k.threads = 160,
+                            k.smem = WsBuildCfg<D, 128, 8, 3, false>::SMEM;
+      break;
+    case GK_PIX_WS_CLS:
+      if constexpr (D <= 3) k.fn = g_pixel_ws_cls<D, 4, 8, 4, 4>, k.threads = 160,
+                            k.smem = TiledCfg<D, 4, 8, 4, 4>::SMEM + 4 * 8;
+      break;
+    case GK_PIX_MG:
+      if constexpr (D == 4 || D == 5) {
+        k.threads = 128;
+        k.fn = b == 1 ? g_pixel_mg<D, 1> : b == 2 ? g_pixel_mg<D, 2> : b == 4 ? g_pixel_mg<D, 4> : g_pixel_mg<D, 8>;
+      }
+      break;
+    case GK_PIX_LIST:
+      if constexpr (D == 4 || D == 5) {
+        k.threads = 128;
+        k.fn = b == 2 ? g_pixel_list<D, 2> : b == 4 ? g_pixel_list<D, 4> : g_pixel_list<D, 8>;
+      }
+      break;
+    default:
+      break;
+  }
+  return k;
+}
+
+static KInfo kinfo(int kind, int a, int b) {
+  if (kind == GK_MERGE) {
+    KInfo k;
+    k.fn = g_merge;
+    return k;
+  }
+  switch (a) {
+    case 1: return kinfo_d<1>(kind, b);
+    case 2: return kinfo_d<2>(kind, b);
+    case 3: return kinfo_d<3>(kind, b);
+    case 4: return kinfo_d<4>(kind, b);
+    case 5: return kinfo_d<5>(kind, b);
+    case 6: return kinfo_d<6>(kind, b);
+    default: return KInfo();
+  }
+}
+
+// CTAs of the kernel resident on the whole GPU (at least one per SM).
+static int64_t resident(const KInfo &k, size_t smem) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute((const void *)k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)k.fn, k.threads, smem);
+  return (int64_t)sm_count() * (per > 0 ? per : 1);
+}
+
+static int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &out, std::vector<int> &fallback) {
+  out.clear();
+  fallback.clear();
+  // launch key -> index in `out`, created in the order the phases run
+  std::vector<GLaunch> L;
+  auto launch = [&](int kind, int a, int b, int branch) -> GLaunch & {
+    for (GLaunch &x : L)
+      if (x.kind == kind && x.a == a && x.b == b) return x;
+    GLaunch x;
+    x.kind = kind, x.a = a, x.b = b, x.branch = branch;
+    L.push_back(x);
+    return L.back();
+  };
+  auto base = [](const GStreamIn &x, const uint8_t *src) {
+    GSeg s;
+    memset(&s, 0, sizeof s);
+    s.in = src, s.mask = x.mask, s.model = x.model, s.occ = x.occ, s.kept = x.kept;
+    s.hw = (int64_t)x.H * x.W;
+    s.N = x.N, s.F = x.F, s.H = x.H, s.W = x.W, s.block = x.block, s.T = x.T;
+    s.bw = x.block > 0 ? (x.W + x.block - 1) / x.block : 1;
+    int P = 0;
+    for (uint32_t v = (uint32_t)x.N; v; v >>= 1) ++P;
+    s.P = P;
+    return s;
+  };
+  const int64_t sms = sm_count();
+  for (int i = 0; i < (int)in.size(); ++i) {
+    const GStreamIn &x = in[i];
+    const int64_t hw = (int64_t)x.H * x.W;
+    const int d = x.depth;
+    const uintptr_t tm = reinterpret_cast<uintptr_t>(x.test) | reinterpret_cast<uintptr_t>(x.mask);
+    if (x.kind == OCQ_REGION_FRAME) {
+      if (d > 6 || x.N > 255) {
+        fallback.push_back(i);
+        continue;
+      }
+      GSeg o = base(x, x.train);
+      o.aux = cdiv64(hw, kGroupOccChunk), o.vg = o.aux * x.N;
+      launch(GK_OCC, d, 0, GB_FRAME).segs.push_back(o);
+      GSeg m = base(x, x.train);
+      m.units = wpr32(d), m.vg = std::max<int64_t>(1, std::min<int64_t>(64, cdiv64(m.units, 256)));
+      launch(GK_MERGE, 0, 0, GB_FRAME).segs.push_back(m);
+      if (x.F > 0) {
+        GSeg c = base(x, x.test);
+        c.units = (int64_t)x.F * hw;
+        launch(GK_CLS_FRAME, d, 0, GB_FRAME).segs.push_back(c);
+      }
+    } else if (x.kind == OCQ_REGION_BLOCK) {
+      const bool cls_ok = x.F == 0 || (x.block % 4 == 0 && x.W % 4 == 0 && (tm & 3) == 0);
+      const bool tile = block_tile_ok(x.N, x.H, x.W, x.block, d, x.train);
+      const bool warp = !tile && d <= 5 && block_warp_ok(x.N, x.H, x.W, x.block);
+      if (!cls_ok || (!tile && !warp)) {
+        fallback.push_back(i);
+        continue;
+      }
+      GSeg bld = base(x, x.train);
+      if (tile) {
+        bld.units = cdiv64(x.H, 16) * cdiv64(x.W, 16);
+        launch(GK_BLOCK_TILE, d, x.block, GB_BLOCK).segs.push_back(bld);
+      } else {
+        const int npx = x.block * x.block;
+        const int ppl = npx <= 32 ? 1 : npx <= 64 ? 2 : npx <= 128 ? 4 : 8;
+        bld.units = region_count(x.H, x.W, OCQ_REGION_BLOCK, x.block);
+        launch(GK_BLOCK_WARP, d, ppl, GB_BLOCK).segs.push_back(bld);
+      }
+      if (x.F > 0) {
+        GSeg c = base(x, x.test);
+        const int bh = (x.H + x.block - 1) / x.block;
+        c.aux3 = (x.W + 127) / 128;
+        const int64_t tiles = (int64_t)bh * c.aux3 * x.block;
+        const int64_t cap = sms * 4 * 8;
+        int chunks = 1;
+        if (tiles < 2 * cap) chunks = (int)std::min<int64_t>(cdiv64(2 * cap, tiles), (x.F + 15) / 16);
+        if (chunks < 1) chunks = 1;
+        const int fchunk = (x.F + chunks - 1) / chunks;
+        chunks = (x.F + fchunk - 1) / fchunk;
+        c.aux = tiles, c.aux2 = fchunk, c.units = tiles * chunks;
+        launch(GK_BLOCK_TB, d, 0, GB_BLOCK).segs.push_back(c);
+      }
+    } else {
+      const uintptr_t all = tm | reinterpret_cast<uintptr_t>(x.train);
+      if (d <= 3 && x.N <= 255 && x.T <= 255 && hw % 1024 == 0 && (all & 15) == 0 && x.model) {
+        GSeg bld = base(x, x.train);
+        bld.units = hw / 128;
+        launch(GK_PIX_WS_BUILD, d, 0, GB_PIXEL).segs.push_back(bld);
+        if (x.F > 0) {
+          GSeg c = base(x, x.test);
+          c.units = hw / 1024;
+          launch(GK_PIX_WS_CLS, d, 0, GB_PIXEL).segs.push_back(c);
+        }
+      } else if ((d == 4 || d == 5) && x.N <= 255 && x.km > 0 && x.kl > 0 && x.kept &&
+                 (x.F == 0 || (hw % 4 == 0 && (tm & 3) == 0))) {
+        GSeg bld = base(x, x.train);
+        bld.vg = cdiv64(hw, 128);
+        launch(GK_PIX_MG, d, x.km, GB_PIXEL_DEEP).segs.push_back(bld);
+        if (x.F > 0) {
+          GSeg c = base(x, x.test);
+          c.units = cdiv64(hw, 128);
+          launch(GK_PIX_LIST, d, x.kl, GB_PIXEL_DEEP).segs.push_back(c);
+        }
+      } else {
+        fallback.push_back(i);
+        continue;
+      }
+    }
+  }
+  // Phase order inside each branch follows the GroupKind order (builds before
+  // classification); launches of one kind keep ascending template arguments.
+  std::stable_sort(L.begin(), L.end(), [](const GLaunch &p, const GLaunch &q) {
+    if (p.branch != q.branch) return p.branch < q.branch;
+    if (p.kind != q.kind) return p.kind < q.kind;
+    return p.a != q.a ? p.a < q.a : p.b < q.b;
+  });
+  for (GLaunch &x : L) {
+    KInfo k = kinfo(x.kind, x.a, x.b);
+    if (!k.fn) {
+      set_error("internal: no grouped kernel for kind %d (%d, %d)", x.kind, x.a, x.b);
+      return OCQ_EINVAL;
+    }
+    x.threads = k.threads;
+    x.smem = k.smem;
+    if (x.kind == GK_PIX_MG)
+      for (const GSeg &s : x.segs) x.smem = std::max(x.smem, (size_t)4 * s.N * 32 * 2);
+    if (x.smem > 227 * 1024) {
+      set_error("internal: grouped kernel needs %zu bytes of shared memory", x.smem);
+      return OCQ_ENOTSUP;
+    }
+    const int64_t cap = resident(k, x.smem);
+    int64_t cta = 0;
+    for (GSeg &s : x.segs) {
+      switch (x.kind) {
+        case GK_CLS_FRAME: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 16 * 256), cap)); break;
+        case GK_BLOCK_TILE:
+        case GK_BLOCK_WARP:
+        case GK_BLOCK_TB: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 8), cap)); break;
+        case GK_PIX_WS_BUILD: s.vg = std::max<int64_t>(1, std::min<int64_t>(s.units, cap)); break;
+        case GK_PIX_WS_CLS: s.vg = std::max<int64_t>(1, std::min<int64_t>(s.units * s.F, cap)); break;
+        case GK_PIX_LIST: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 4), cap)); break;
+        default: break;  // GK_OCC, GK_MERGE, GK_PIX_MG: set above
+      }
+      s.cta0 = cta;
+      cta += s.vg;
+    }
+    x.grid = cta;
+  }
+  out.swap(L);
+  return OCQ_OK;
+}
+
+ocq_status grouped_launch(const GLaunch &L, cudaStream_t st) {
+  if (L.grid <= 0 || L.segs.empty()) return OCQ_OK;
+  if (L.grid > 0x7FFFFFFFLL) {
+    set_error("grouped launch of %lld CTAs", (long long)L.grid);
+    return OCQ_ENOTSUP;
+  }
+  KInfo k = kinfo(L.kind, L.a, L.b);
+  const GSeg *segs = L.dev;
+  int n = (int)L.segs.size();
+  void *args[] = {(void *)&segs, (void *)&n};
+  cudaError_t e = cudaLaunchKernel((const void *)k.fn, dim3((unsigned)L.grid), dim3((unsigned)L.threads), args, L.smem, st);
+  count_launch();
+  return cuda_status(e, "grouped kernel");
+}
+
+bool grouped_take_timeout() {
+  unsigned int flag = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&flag, g_grouped_timeout, sizeof flag) != cudaSuccess) return false;
+  if (flag) cudaMemcpyToSymbol(g_grouped_timeout, &zero, sizeof zero);
+  return flag != 0;
+}
+
+}  // namespace ocq

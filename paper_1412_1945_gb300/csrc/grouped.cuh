@@ -1,0 +1,72 @@
+// Grouped launches of the batched form (grouped.cu): shared by the batch
+// planner (batch.cu).
+#pragma once
+
+#include <vector>
+
+#include "ocq_internal.cuh"
+
+namespace ocq {
+
+constexpr int64_t kGroupOccChunk = 16384;  // pixels per whole-frame occupancy CTA
+
+// One stream's share of a grouped launch: CTAs [cta0, cta0 + vg) of the
+// launch run the body for this stream as virtual CTAs 0 .. vg - 1.
+struct GSeg {
+  const uint8_t *in;  // frames read: training frames (builds) or test frames
+  uint8_t *mask;
+  uint32_t *model;    // leaf bitset rows, internal order (null for a list model)
+  uint32_t *occ;      // whole frame: N per-frame leaf bitsets
+  uint16_t *kept;     // kept-leaf lists
+  int64_t hw, cta0, vg;
+  int64_t units;      // tiles, items or words the body walks
+  int64_t aux;        // occupancy: CTAs per frame; block classify: tiles
+  int32_t N, F, H, W, block, bw, T, P;
+  int32_t aux2, aux3;  // block classify: frames per chunk, 128-pixel segments per row
+};
+
+// Kernel kinds (one launch per kind and template arguments a, b).
+enum GroupKind : int {
+  GK_OCC = 0,      // whole-frame occupancy, a = depth
+  GK_MERGE,        // whole-frame merge (any depth)
+  GK_CLS_FRAME,    // whole-frame classify, a = depth
+  GK_BLOCK_TILE,   // block build over 16 x 16 warp tiles, a = depth, b = block size
+  GK_BLOCK_WARP,   // block build, one warp per region, a = depth, b = pixels per lane
+  GK_BLOCK_TB,     // block classify, warps walking frames, a = depth
+  GK_PIX_WS_BUILD, // per-pixel build, depth <= 3, counters + copy warp, a = depth
+  GK_PIX_WS_CLS,   // per-pixel classify, depth <= 3, rows staged + copy warp, a = depth
+  GK_PIX_MG,       // per-pixel candidate build, a = depth, b = candidate counters
+  GK_PIX_LIST      // per-pixel classify against kept-leaf lists, a = depth, b = list length
+};
+
+// Branches of the batch graph a grouped launch belongs to.
+enum GroupBranch : int { GB_FRAME = 0, GB_BLOCK, GB_PIXEL, GB_PIXEL_DEEP, GB_COUNT };
+
+struct GLaunch {
+  int kind = 0, a = 0, b = 0, branch = 0;
+  std::vector<GSeg> segs;
+  GSeg *dev = nullptr;  // device copy of segs (owned by the batch's upload buffer)
+  int threads = 256;
+  size_t smem = 0;
+  int64_t grid = 0;
+};
+
+// What the planner needs to know of a camera stream.
+struct GStreamIn {
+  const uint8_t *train, *test;
+  uint8_t *mask;
+  uint32_t *model, *occ;
+  uint16_t *kept;
+  int N, F, H, W, kind, block, depth, T, km, kl;
+};
+
+// Plans grouped launches for the streams they cover, in dependency order per
+// branch; streams they do not cover are listed in `fallback` (run by their
+// plain kernels).  Sets each launch's CTA shape, shared memory and grid.
+ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &out, std::vector<int> &fallback);
+// Enqueues one planned launch (segments already on the device) on `st`.
+ocq_status grouped_launch(const GLaunch &L, cudaStream_t st);
+// True (and cleared) if a bounded wait of a grouped body gave up.
+bool grouped_take_timeout();
+
+}  // namespace ocq

@@ -123,7 +123,7 @@ SIGNATURES = {
 
 OCQ_TUNE_CLASSIFY_PIXEL, OCQ_TUNE_BUILD_PIXEL, OCQ_TUNE_CLASSIFY_PIXEL_DEEP, OCQ_TUNE_CLASSIFY_BLOCK_DEEP = 0, 1, 2, 3
 OCQ_TUNE_CLASSIFY_PIXEL_LIST, OCQ_TUNE_PIXEL_MODEL_FORM, OCQ_TUNE_BUILD_BLOCK = 4, 5, 6
-OCQ_BATCH_PERSISTENT, OCQ_BATCH_GRAPH = 0, 1
+OCQ_BATCH_PERSISTENT, OCQ_BATCH_GRAPH, OCQ_BATCH_GROUPED = 0, 1, 2
 
 
 def load(path: str | None = None):

@@ -57,11 +57,12 @@ def _plain(ocq, s):
     return words, mask
 
 
-@pytest.mark.parametrize("mode,staging", [(0, 0), (0, 1), (1, 0)])
+@pytest.mark.parametrize("mode,staging", [(0, 0), (0, 1), (1, 0), (2, 0)])
 def test_batch_small_mix_matches_plain_and_oracle(ocq, mode, staging):
-    """Both forms: the persistent work-list kernel (0; per-pixel depth <= 3
-    rows through L1 or staged in shared memory) and the graph of per-stream
-    branches (1)."""
+    """Every form: the persistent work-list kernel (0; per-pixel depth <= 3
+    rows through L1 or staged in shared memory), the graph of per-stream
+    branches (1) and the grouped launches per kernel body (2; the mix holds
+    streams those bodies cover and streams left to their plain kernels)."""
     import torch
 
     S = _streams_host(SMALL_MIX, torch)
@@ -172,12 +173,13 @@ def test_batch_64_stream_preset_matches_plain(ocq):
         ocq.ocq.ocq_batch_run(b)
         ocq.ocq.ocq_batch_status(b)
         persistent = [s["mask"].clone() for s in descs]
-        ocq.ocq.ocq_batch_set_mode(b, 1)
-        for s in descs:
-            s["mask"].fill_(5)
-        ocq.ocq.ocq_batch_run(b)
-        ocq.ocq.ocq_batch_status(b)
-        assert all((s["mask"] == p).all().item() for s, p in zip(descs, persistent))
+        for mode in (2, 1):  # grouped launches, then the graph of per-stream branches
+            ocq.ocq.ocq_batch_set_mode(b, mode)
+            for s in descs:
+                s["mask"].fill_(5)
+            ocq.ocq.ocq_batch_run(b)
+            ocq.ocq.ocq_batch_status(b)
+            assert all((s["mask"] == p).all().item() for s, p in zip(descs, persistent)), mode
         for i, s in enumerate(descs):
             m = ocq.build_model(s["train"], s["depth"], s["T"], s["kind"], s["block"])
             pmask = ocq.classify(m, s["test"])
