@@ -430,10 +430,12 @@ void ocq_server_destroy(ocq_server *server);
  *                            plus that list; params = {variant, 0, ...}
  *   OCQ_TUNE_BUILD_BLOCK     block build with b <= 16 and N <= 255: 1 (default)
  *                            warps over 16 x 16 pixel tiles (four 8 x 8 or one
- *                            16 x 16 region, 8 pixels per lane) where b is 8 or 16,
- *                            depth is 2-5, W % 8 == 0 and the frames are 8-byte
- *                            aligned, else one warp per region; 0 one warp per
- *                            region always; params = {variant, 0, ...}
+ *                            16 x 16 region, 8 pixels per lane; direct leaf tables
+ *                            at depth <= 3, two-level prefix tables deeper) where b
+ *                            is 16 (depth 2-5) or 8 (depth 2-4), W % 8 == 0 and
+ *                            the frames are 8-byte aligned, else one warp per
+ *                            region; 0 one warp per region always; params =
+ *                            {variant, 0, ...}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5

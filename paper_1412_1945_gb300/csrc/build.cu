@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) build_block_warp_kernel(const uint8_t *__
 }
 
 template <int D, int B, int PF>
-__global__ void __launch_bounds__(256, BlockTileCfg<D, B>::MINB) build_block_tile_kernel(const uint8_t *__restrict__ frames, int N, int H, int W,
+__global__ void __launch_bounds__(BlockTileCfg<D, B>::WPC * 32, BlockTileCfg<D, B>::MINB) build_block_tile_kernel(const uint8_t *__restrict__ frames, int N, int H, int W,
                                                                int bw, uint32_t T, uint32_t *__restrict__ model,
                                                                int64_t ntiles) {
   extern __shared__ __align__(16) uint8_t tile_smem[];
@@ -630,13 +630,13 @@ static ocq_status launch_block_warp_ppl(const uint8_t *frames, int N, ocq_model 
 
 // Warp tiles of 16 x 16 pixels for 8 x 8 and 16 x 16 blocks (depth 2-5,
 // N <= 255, W % 8 == 0, 8-byte aligned frames, frame offsets within 32 bits).
-// With 8 x 8 blocks at depth 4-5 (hashed tables for four regions per warp) the
-// one-warp-per-region build measured faster (0.23 / 0.29 ms against 0.36 /
-// 0.55 ms for 30 frames of 1080p), so the tiles take 8 x 8 blocks at depth
-// <= 3 and 16 x 16 blocks at every depth.
+// 8 x 8 blocks at depth 5 stay with one warp per region: four regions' prefix
+// pools leave 12 warps per SM and measured slower there (30 frames of 1080p:
+// 0.27 / 0.32 ms against 0.25 / 0.29 ms), while the tiles win everywhere else
+// (8 x 8 at depth 3 and 4: 1.5x and 1.3x; 16 x 16 at depth 4 and 5: 4x and 3x).
 static int g_block_form = 1;  // 1: warp tiles where they apply; 0: one warp per region
 bool block_tile_ok(int N, int H, int W, int b, int depth, const void *frames) {
-  return g_block_form == 1 && (b == 16 || (b == 8 && depth <= 3)) && depth >= 2 && depth <= 5 && N <= 255 &&
+  return g_block_form == 1 && (b == 16 || (b == 8 && depth <= 4)) && depth >= 2 && depth <= 5 && N <= 255 &&
          W % 8 == 0 && (reinterpret_cast<uintptr_t>(frames) & 7) == 0 && (int64_t)H * W * 3 <= (int64_t)UINT32_MAX;
 }
 int block_build_form_count() { return 2; }
@@ -650,7 +650,8 @@ bool block_build_form_select(int v) {
 template <int D, int B>
 static ocq_status launch_block_tile(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
   constexpr int PF = BlockTileCfg<D, B>::PF;
-  constexpr size_t smem = (size_t)8 * BlockTileCfg<D, B>::WARP_SMEM;
+  constexpr int WPC = BlockTileCfg<D, B>::WPC;
+  constexpr size_t smem = (size_t)WPC * BlockTileCfg<D, B>::WARP_SMEM;
   auto kern = build_block_tile_kernel<D, B, PF>;
   static int cap = 0;
   if (!cap) {
@@ -658,23 +659,21 @@ static ocq_status launch_block_tile(const uint8_t *frames, int N, ocq_model *m, 
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, WPC * 32, smem);
     cap = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
   }
   const int bw = (m->W + m->block - 1) / m->block;
   const int64_t ntiles = (int64_t)((m->H + 15) / 16) * ((m->W + 15) / 16);
-  const int64_t ctas = (ntiles + 7) / 8;
-  kern<<<(unsigned)(ctas < cap ? ctas : cap), 256, smem, st>>>(frames, N, m->H, m->W, bw, (uint32_t)m->T, m->bits,
-                                                               ntiles);
+  const int64_t ctas = (ntiles + WPC - 1) / WPC;
+  kern<<<(unsigned)(ctas < cap ? ctas : cap), WPC * 32, smem, st>>>(frames, N, m->H, m->W, bw, (uint32_t)m->T,
+                                                                    m->bits, ntiles);
   count_launch();
   return cuda_status(cudaGetLastError(), "build_block_tile_kernel");
 }
 
 template <int D>
 static ocq_status launch_block_tile_b(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
-  if constexpr (D <= 3)
-    if (m->block == 8) return launch_block_tile<D, 8>(frames, N, m, st);
-  return launch_block_tile<D, 16>(frames, N, m, st);
+  return m->block == 8 ? launch_block_tile<D, 8>(frames, N, m, st) : launch_block_tile<D, 16>(frames, N, m, st);
 }
 
 template <int D>

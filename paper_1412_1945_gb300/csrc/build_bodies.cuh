@@ -488,13 +488,18 @@ __device__ __forceinline__ void build_block_warp_body(const uint8_t *__restrict_
 //     its leaf's entry only while the frame field is older than the current
 //     frame, so lanes holding the same leaf in the same frame store the same
 //     value and the leaf is counted once per frame with no atomic;
-//   * hashed tables (otherwise): u32 entries (leaf + 1) << 16 | (frame + 1) << 8
-//     | count in buckets of 4 (one 16-byte load finds a leaf among them), 4
-//     (depth 4) or 8 (depth 5) slots per pixel of the region, linear probing
-//     over buckets; only a leaf claiming an empty slot uses atomicCAS.  A region
-//     whose table passes 3/4 full stops counting and is recounted by the
-//     chunked passes of the one-warp-per-region build, so no result depends on
-//     the table's size.
+//   * two-level tables (otherwise): a leaf of depth 4-5 is its depth-3 prefix
+//     (the path's first three levels, 512 values) and a suffix (the remaining
+//     levels, 8^(d-3) values).  Per region a directory maps each prefix the
+//     region's pixels reach to a sub-table of u16 entries as above, one per
+//     suffix, taken from a pool the warp's regions share on the prefix's first
+//     touch (atomicCAS on the directory entry, then atomicAdd on the pool
+//     count; a lane that finds the entry being claimed retries after the
+//     frame's warp barrier).  A region's pixels reach few prefixes (a few dozen
+//     at most on the synthetic scenes), so a lookup is two dependent shared
+//     loads and no probing.  A region whose claim finds the pool exhausted
+//     stops counting and is recounted by the chunked passes of the
+//     one-warp-per-region build, so no result depends on the pool's size.
 // A lane reads the entries of all its pixels of a frame before it writes any:
 // the new value is a function of the old one and the frame, so a lane holding
 // the same leaf twice writes the same value twice.  One __syncwarp per frame
@@ -505,17 +510,27 @@ struct BlockTileCfg {
   static constexpr int NPX = B * B;                // pixels per region
   static constexpr int NC = 1 << (3 * D);
   static constexpr bool DIRECT = D <= 3 || (D == 4 && B == 16);
-  static constexpr int S = DIRECT ? NC : (D == 4 ? 4 : 8) * NPX;  // entries per region table
-  static constexpr int SS = DIRECT ? S + 16 : S + 8;               // entries between regions (8-bank skew)
-  static constexpr int NB = S / 4;                                  // hashed: buckets per region
-  static constexpr int LOGNB = NB >= 512 ? 9 : NB >= 128 ? 7 : NB >= 64 ? 6 : 5;
-  static constexpr int LIM = 3 * S / 4;
+  // direct tables: entries per region and between regions (8-bank skew)
+  static constexpr int S = NC;
+  static constexpr int SS = S + 16;
+  // two-level tables: directory entries per region (depth-3 prefixes), entries
+  // per sub-table (suffixes), sub-tables in the warp's pool
+  static constexpr int NPRE = 512;
+  static constexpr int SUB = D > 3 ? 1 << (3 * (D - 3)) : 1;
+  static constexpr int NP = D == 4 ? 128 : (B == 8 ? 96 : 128);  // (8 x 8 at depth 5 is not dispatched here)
+  static constexpr int DIR_BYTES = RPT * NPRE * 2;
+  static constexpr int POOL_BYTES = NP * SUB * 2;
+  static constexpr int OWNER_BYTES = NP * 2;
   static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
-  static constexpr int TABLE_BYTES = (RPT * SS * (DIRECT ? 2 : 4) + 15) & ~15;
-  static constexpr int WARP_SMEM = TABLE_BYTES + 16;  // + RPT insert counters
-  // 256-thread CTAs resident per SM the kernel is compiled for (registers)
-  static constexpr int MINB = D == 5 && B == 16 ? 2 : 3;
+  static constexpr int TABLE_BYTES = DIRECT ? (RPT * SS * 2 + 15) & ~15
+                                            : (DIR_BYTES + POOL_BYTES + OWNER_BYTES + 16 + 15) & ~15;
+  static constexpr int WARP_SMEM = TABLE_BYTES + 16;  // + RPT per-region flags
+  static constexpr int WPC = DIRECT ? 8 : 4;  // warps per CTA
+  // CTAs resident per SM the kernel is compiled for (registers; two-level
+  // tables at depth 5 fit 3 CTAs in shared memory)
+  static constexpr int MINB = DIRECT ? 3 : (D == 4 ? 4 : 3);
   static constexpr int PF = DIRECT ? 4 : 2;  // frames per register buffer
+  static_assert(DIRECT || TABLE_BYTES >= 4096, "the recount passes use a 4 KB table");
 };
 
 // Planar code of a masked pixel word (bytes r_d, g_d, b_d; byte 3 ignored)
@@ -526,16 +541,6 @@ __device__ __forceinline__ uint32_t planar_dp(uint32_t t) {
     return __dp4a(t, 1u | ((1u << D) << 8) | ((1u << (2 * D)) << 16), 0u);
   else
     return __dp4a(t, 1u | ((1u << D) << 8), (t >> (16 - 2 * D)) & (0xFFu << (2 * D)));
-}
-
-// 16-byte shared-memory load that is not cached or merged with other accesses.
-__device__ __forceinline__ uint4 lds128_volatile(const void *p) {
-  uint4 v;
-  asm volatile("ld.volatile.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "r"(smem_addr(p))
-               : "memory");
-  return v;
 }
 
 // Slot of leaf q in a direct table: a bijection of [0, 2^15) (each bit XORed
@@ -553,40 +558,37 @@ __device__ __forceinline__ uint32_t oct_pixel(const uint32_t (&w)[6]) {
     return __byte_perm(w[i], 0u, sel);
 }
 
-// Hashed table: counts leaf q (key = (q + 1) << 16) of frame f (fh = (f + 1) << 8)
-// given the home bucket's entries `bk` read earlier in the frame.
+// Two-level tables: the sub-table (1-based) of prefix p in directory `dir`,
+// claiming one from the pool on the prefix's first touch; 0 when the entry is
+// being claimed by another lane (retry after the frame's warp barrier) or the
+// pool is exhausted (the region's flag is raised).
 template <int D, int B>
-__device__ __forceinline__ void tile_hash_count(uint32_t *tab, uint32_t *ins, uint32_t hb, uint4 bk, uint32_t key,
-                                                uint32_t fh) {
+__device__ __forceinline__ uint32_t tile_claim(uint16_t *dir, uint32_t p, int ri, uint32_t *pcount, uint16_t *owner,
+                                               uint32_t *flag) {
   using C = BlockTileCfg<D, B>;
-  volatile uint32_t *vt = tab;
-  const uint32_t e4[4] = {bk.x, bk.y, bk.z, bk.w};
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if ((e4[j] & 0xFFFF0000u) == key) {  // the common case: the leaf is in its home bucket
-      if ((e4[j] & 0xFF00u) < fh) vt[4 * hb + j] = key | fh | ((e4[j] + 1u) & 0xFFu);
-      return;
+  const unsigned short old = atomicCAS(reinterpret_cast<unsigned short *>(dir + p), (unsigned short)0,
+                                       (unsigned short)0xFFFF);
+  if (old == 0) {
+    const uint32_t j = atomicAdd(pcount, 1u);
+    if (j < (uint32_t)C::NP) {
+      owner[j] = (uint16_t)((ri << 9) | p);
+      *reinterpret_cast<volatile uint16_t *>(dir + p) = (uint16_t)(j + 1);
+      return j + 1;
     }
-  for (int probe = 0; probe < C::NB; ++probe) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t s = 4 * hb + j;
-      uint32_t e = vt[s];
-      if (e == 0u) {
-        e = atomicCAS(&tab[s], 0u, key | fh | 1u);
-        if (e == 0u) {
-          atomicAdd(ins, 1u);
-          return;
-        }
-      }
-      if ((e & 0xFFFF0000u) == key) {
-        if ((e & 0xFF00u) < fh) vt[s] = key | fh | ((e + 1u) & 0xFFu);
-        return;
-      }
-    }
-    hb = (hb + 1u) & (C::NB - 1);
+    atomicOr(flag, 1u);  // pool exhausted: recount the region
+    return 0;
   }
-  atomicAdd(ins, (uint32_t)C::S);  // no free slot: recount the region
+  return old == 0xFFFF ? 0u : (uint32_t)old;
+}
+
+// Planar code of depth D from a depth-3 prefix and its suffix.
+template <int D>
+__device__ __forceinline__ uint32_t tile_compose(uint32_t p, uint32_t s) {
+  constexpr int E = D - 3;
+  constexpr uint32_t M = (1u << E) - 1u;
+  const uint32_t r = ((p & 7u) << E) | (s & M), g = (((p >> 3) & 7u) << E) | ((s >> E) & M),
+                 b = ((p >> 6) << E) | (s >> (2 * E));
+  return r | (g << D) | (b << (2 * D));
 }
 
 // Warp w of the caller handles tiles t = t_first, t_first + t_step, ... < t_end
@@ -603,9 +605,12 @@ __device__ __forceinline__ void build_block_tile_body(const uint8_t *__restrict_
   const int tiles_x = (W + 15) >> 4;
   const int64_t fstride = (int64_t)H * W * 3;
   const int ri = B == 8 ? (((trow >> 3) << 1) | half) : 0;  // the lane's region within the tile
-  uint32_t *ins = reinterpret_cast<uint32_t *>(wsm + C::TABLE_BYTES);
-  uint16_t *t16 = reinterpret_cast<uint16_t *>(wsm) + ri * C::SS;
-  uint32_t *t32 = reinterpret_cast<uint32_t *>(wsm) + ri * C::SS;
+  uint32_t *flags = reinterpret_cast<uint32_t *>(wsm + C::TABLE_BYTES);  // per region: recount
+  uint16_t *t16 = reinterpret_cast<uint16_t *>(wsm) + ri * C::SS;           // direct
+  uint16_t *dir = reinterpret_cast<uint16_t *>(wsm) + ri * C::NPRE;         // two-level
+  uint16_t *pool = reinterpret_cast<uint16_t *>(wsm + C::DIR_BYTES);
+  uint16_t *owner = reinterpret_cast<uint16_t *>(wsm + C::DIR_BYTES + C::POOL_BYTES);
+  uint32_t *pcount = reinterpret_cast<uint32_t *>(wsm + C::DIR_BYTES + C::POOL_BYTES + C::OWNER_BYTES);
   for (int64_t t = t_first; t < t_end; t += t_step) {
     const int ty = (int)(t / tiles_x), tx = (int)(t - (int64_t)ty * tiles_x);
     const int y = ty * 16 + trow, x = tx * 16 + half * 8;
@@ -625,43 +630,77 @@ __device__ __forceinline__ void build_block_tile_body(const uint8_t *__restrict_
 #pragma unroll
       for (int j = 0; j < PF; ++j) {
         if (f0 + j >= N) break;
-        if (!skip) {
-          const uint32_t f = (uint32_t)(f0 + j);
-          uint32_t m[6];
+        const uint32_t fh = (uint32_t)(f0 + j + 1) << 8;
+        uint32_t m[6];
 #pragma unroll
-          for (int i = 0; i < 6; ++i) m[i] = (v[j][i] >> (8 - D)) & byte_mask(D);
-          uint32_t q[8];
-          static_for<0, 8>([&](auto kc) {
-            constexpr int k = decltype(kc)::value;
-            q[k] = planar_dp<D>(oct_pixel<k>(m));
-          });
-          if constexpr (C::DIRECT) {
+        for (int i = 0; i < 6; ++i) m[i] = (v[j][i] >> (8 - D)) & byte_mask(D);
+        if constexpr (C::DIRECT) {
+          if (!skip) {
+            uint32_t q[8];
+            static_for<0, 8>([&](auto kc) {
+              constexpr int k = decltype(kc)::value;
+              q[k] = planar_dp<D>(oct_pixel<k>(m));
+            });
             volatile uint16_t *vt = t16;
-            const uint32_t fh = (f + 1u) << 8;
             uint32_t e[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) e[k] = vt[tile_slot(q[k])];
 #pragma unroll
             for (int k = 0; k < 8; ++k)
               if (e[k] < fh) vt[tile_slot(q[k])] = (uint16_t)(fh | ((e[k] + 1u) & 0xFFu));
-          } else {
-            const uint32_t fh = (f + 1u) << 8;
-#pragma unroll
-            for (int g = 0; g < 8; g += 4) {
-              uint32_t hb[4];
-              uint4 bk[4];
-#pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                hb[k] = (q[g + k] * 2654435761u) >> (32 - C::LOGNB);
-                bk[k] = lds128_volatile(t32 + 4 * hb[k]);
-              }
-#pragma unroll
-              for (int k = 0; k < 4; ++k) tile_hash_count<D, B>(t32, ins + ri, hb[k], bk[k], (q[g + k] + 1u) << 16, fh);
-            }
           }
+          __syncwarp();
+        } else {
+          // prefix: the top 3 of the D bits per channel; suffix: the rest
+          constexpr int E = D - 3;
+          uint32_t pre[8], suf[8], sub[8];
+          uint32_t deferred = 0;
+          if (!skip) {
+            static_for<0, 8>([&](auto kc) {
+              constexpr int k = decltype(kc)::value;
+              const uint32_t px = oct_pixel<k>(m);
+              pre[k] = __dp4a((px >> E) & byte_mask(3), 1u | (8u << 8) | (64u << 16), 0u);
+              suf[k] = __dp4a(px & byte_mask(E), 1u | ((1u << E) << 8) | ((1u << (2 * E)) << 16), 0u);
+            });
+            volatile uint16_t *vd = dir;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sub[k] = vd[pre[k]];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (sub[k] == 0u || sub[k] == 0xFFFFu) {
+                sub[k] = tile_claim<D, B>(dir, pre[k], ri, pcount, owner, flags + ri);
+                if (!sub[k]) deferred |= 1u << k;
+              }
+            volatile uint16_t *vp = pool;
+            uint32_t e[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (!((deferred >> k) & 1u)) e[k] = vp[(sub[k] - 1u) * C::SUB + suf[k]];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (!((deferred >> k) & 1u) && e[k] < fh)
+                vp[(sub[k] - 1u) * C::SUB + suf[k]] = (uint16_t)(fh | ((e[k] + 1u) & 0xFFu));
+          }
+          __syncwarp();
+          // pixels whose prefix another lane was claiming: its directory entry
+          // is set now (or the pool ran out and the region is recounted)
+          if (__any_sync(0xFFFFFFFFu, deferred != 0u)) {
+            if (deferred && !*(volatile uint32_t *)(flags + ri)) {
+              volatile uint16_t *vd = dir;
+              volatile uint16_t *vp = pool;
+#pragma unroll
+              for (int k = 0; k < 8; ++k)
+                if ((deferred >> k) & 1u) {
+                  const uint32_t sb = vd[pre[k]];
+                  if (sb == 0u || sb == 0xFFFFu) continue;  // unreachable unless the region overflowed
+                  const uint32_t e = vp[(sb - 1u) * C::SUB + suf[k]];
+                  if (e < fh) vp[(sb - 1u) * C::SUB + suf[k]] = (uint16_t)(fh | ((e + 1u) & 0xFFu));
+                }
+            }
+            __syncwarp();
+          }
+          skip = skip || *(volatile uint32_t *)(flags + ri) != 0u;
         }
-        __syncwarp();
-        if constexpr (!C::DIRECT) skip = skip || *(volatile uint32_t *)(ins + ri) > (uint32_t)C::LIM;
       }
     };
     {
@@ -706,32 +745,34 @@ __device__ __forceinline__ void build_block_tile_body(const uint8_t *__restrict_
 #pragma unroll
       for (int r = 0; r < C::RPT; ++r) {
         uint32_t *row = region_row(r);
-        const bool over = *(volatile uint32_t *)(ins + r) > (uint32_t)C::LIM;
-        if (row && over) ovf |= 1u << r;
+        if (row && *(volatile uint32_t *)(flags + r)) ovf |= 1u << r;
         if (row) {
           uint4 *r4 = reinterpret_cast<uint4 *>(row);
           for (int i = lane; i < C::WPR / 4; i += 32) r4[i] = make_uint4(0, 0, 0, 0);
         }
       }
       __syncwarp();
-      for (int r = 0; r < C::RPT; ++r) {
-        uint32_t *row = region_row(r);
-        uint32_t *tab = reinterpret_cast<uint32_t *>(wsm) + r * C::SS;
-        const bool emit = row && !((ovf >> r) & 1u);
-        for (int i = lane; i < C::S; i += 32) {
-          const uint32_t e = tab[i];
-          if (e) {
-            tab[i] = 0u;
-            if (emit && (e & 0xFFu) >= T) {
-              const uint32_t q = (e >> 16) - 1u;
-              atomicOr(&row[q >> 5], 1u << (q & 31));
-            }
+      const uint32_t used = min(*(volatile uint32_t *)pcount, (uint32_t)C::NP);
+      for (uint32_t i = lane; i < used * C::SUB; i += 32) {
+        const uint32_t e = pool[i];
+        if (e) {
+          pool[i] = 0;
+          const uint32_t o = owner[i / C::SUB];
+          const int r = (int)(o >> 9);
+          uint32_t *row = region_row(r);
+          if (row && !((ovf >> r) & 1u) && (e & 0xFFu) >= T) {
+            const uint32_t q = tile_compose<D>(o & 511u, i % C::SUB);
+            atomicOr(&row[q >> 5], 1u << (q & 31));
           }
         }
       }
+      uint4 *z = reinterpret_cast<uint4 *>(wsm);  // the directories
+      for (int i = lane; i < C::DIR_BYTES / 16; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+      if (lane == 0) *pcount = 0u;
       __syncwarp();
-      // Recount regions whose table overflowed: chunked direct passes over
-      // 1024-leaf slices of the code space (table = the first 4 KB of wsm).
+      // Recount regions whose pool claim failed: chunked direct passes over
+      // 1024-leaf slices of the code space (table = the first 4 KB of wsm,
+      // zero after the clearing above).
       uint32_t *tab = reinterpret_cast<uint32_t *>(wsm);
       while (ovf) {
         const int r = __ffs(ovf) - 1;
@@ -752,7 +793,7 @@ __device__ __forceinline__ void build_block_tile_body(const uint8_t *__restrict_
           warp_emit<D>(tab, row, T);
         }
       }
-      if (lane < C::RPT) ins[lane] = 0u;
+      if (lane < C::RPT) flags[lane] = 0u;
       __syncwarp();
     }
   }

@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(256) g_cls_frame(const GSeg *__restrict__ g, i
 // ---- blocks ----------------------------------------------------------------------
 
 template <int D, int B>
-__global__ void __launch_bounds__(256, BlockTileCfg<D, B>::MINB) g_block_tile(const GSeg *__restrict__ g, int n) {
+__global__ void __launch_bounds__(BlockTileCfg<D, B>::WPC * 32, BlockTileCfg<D, B>::MINB)
+    g_block_tile(const GSeg *__restrict__ g, int n) {
   extern __shared__ __align__(16) uint8_t gt_smem[];
   constexpr int WB = BlockTileCfg<D, B>::WARP_SMEM;
   uint8_t *wsm = gt_smem + (threadIdx.x >> 5) * WB;
@@ -67,8 +68,9 @@ __global__ void __launch_bounds__(256, BlockTileCfg<D, B>::MINB) g_block_tile(co
   __syncwarp();
   int64_t vb;
   const GSeg &s = seg_of(g, n, vb);
+  constexpr int WPC = BlockTileCfg<D, B>::WPC;
   build_block_tile_body<D, B, BlockTileCfg<D, B>::PF>(s.in, s.N, s.H, s.W, s.bw, (uint32_t)s.T, s.model,
-                                                      vb * 8 + (threadIdx.x >> 5), s.units, s.vg * 8, wsm);
+                                                      vb * WPC + (threadIdx.x >> 5), s.units, s.vg * WPC, wsm);
 }
 
 template <int D, int PPL>
@@ -158,9 +160,12 @@ static KInfo kinfo_d(int kind, int b) {
       break;
     case GK_BLOCK_TILE:
       if constexpr (D >= 2 && D <= 5) {
-        if (b == 16) k.fn = g_block_tile<D, 16>, k.smem = (size_t)8 * BlockTileCfg<D, 16>::WARP_SMEM;
-        if constexpr (D <= 3)
-          if (b == 8) k.fn = g_block_tile<D, 8>, k.smem = (size_t)8 * BlockTileCfg<D, 8>::WARP_SMEM;
+        if (b == 16)
+          k.fn = g_block_tile<D, 16>, k.threads = BlockTileCfg<D, 16>::WPC * 32,
+          k.smem = (size_t)BlockTileCfg<D, 16>::WPC * BlockTileCfg<D, 16>::WARP_SMEM;
+        if (b == 8)
+          k.fn = g_block_tile<D, 8>, k.threads = BlockTileCfg<D, 8>::WPC * 32,
+          k.smem = (size_t)BlockTileCfg<D, 8>::WPC * BlockTileCfg<D, 8>::WARP_SMEM;
       }
       break;
     case GK_BLOCK_WARP:
@@ -357,7 +362,7 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
     for (GSeg &s : x.segs) {
       switch (x.kind) {
         case GK_CLS_FRAME: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 16 * 256), cap)); break;
-        case GK_BLOCK_TILE:
+        case GK_BLOCK_TILE: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, x.threads / 32), cap)); break;
         case GK_BLOCK_WARP:
         case GK_BLOCK_TB: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 8), cap)); break;
         case GK_PIX_WS_BUILD: s.vg = std::max<int64_t>(1, std::min<int64_t>(s.units, cap)); break;
