@@ -779,13 +779,21 @@ def _serve_run(O, streams, bufs, fps, budget, n_cameras, frames_per_camera, pool
                     heapq.heappush(heap, (a / speed + shift, i, t))
                 progressed = True
             now = time.monotonic() - base
+            # every frame that has arrived goes into one batched submit (one
+            # serving tick on the GPU for all cameras' frames)
+            b_cam, b_fr, b_mk, b_tag = [], [], [], []
             while heap and heap[0][0] <= now:
                 a, i, t = heapq.heappop(heap)
                 wl = streams[i].wl
                 fr, masks = bufs[i]
                 tag = i * 100000 + t
                 sched[tag] = a
-                O.ocq_server_submit(srv, live[i]["cam"], fr[wl.N + t % pool], masks[t % mask_slots], tag)
+                b_cam.append(live[i]["cam"])
+                b_fr.append(fr[wl.N + t % pool].data_ptr())
+                b_mk.append(masks[t % mask_slots].data_ptr())
+                b_tag.append(tag)
+            if b_cam:
+                O.ocq_server_submit_many(srv, b_cam, b_fr, b_mk, b_tag)
                 progressed = True
             for _cam, _frame, tag, _arr, done_s in O.ocq_server_poll(srv, 8192):
                 i = tag // 100000

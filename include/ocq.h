@@ -336,7 +336,7 @@ ocq_status ocq_server_create(size_t hbm_budget, int max_cameras, ocq_server **ou
  * per-pixel regions of depth 4-5 with floor(N/T) <= 8 a list model, 16 B per
  * location; see OCQ_TUNE_PIXEL_MODEL_FORM), build scratch, and the window:
  *   - whole frame, when a leaf bitset (max(1, 8^d/32) u32 words) is no larger
- *     than a frame: N leaf bitsets, the entering frame's bitset and 8^d u16
+ *     than a frame: N leaf bitsets, N bitsets of entering frames and 8^d u16
  *     counts (frames holding each leaf); a re-merge thresholds the counts in
  *     place;
  *   - pixel regions, and blocks with b <= 16, at depth <= 5 and N <= 255: N
@@ -356,8 +356,22 @@ size_t ocq_server_window_bytes(const ocq_camera_desc *desc);
  * it; read on the device after the call returns, so keep it until the
  * camera's first mask is done). */
 ocq_status ocq_server_admit(ocq_server *server, const ocq_camera_desc *desc, const uint8_t *train, int *camera);
-/* frame: device, H*W*3; mask: device, H*W (1 = foreground).  Non-blocking. */
+/* frame: device, H*W*3; mask: device, H*W (1 = foreground).  Non-blocking.
+ * The same as ocq_server_submit_many with one frame. */
 ocq_status ocq_server_submit(ocq_server *server, int camera, const uint8_t *frame, uint8_t *mask, uint64_t tag);
+/* Continuous batching: n frames (entry i: camera cameras[i], device frame
+ * frames[i] and mask masks[i], tag tags[i]; a camera's frames in arrival
+ * order) submitted at once.  Frames of cameras with a bitset or code window
+ * (ocq_server_camera_footprint) run in ticks on the server's high-priority
+ * stream: a tick holds, for every camera, its next frames up to its next
+ * re-merge (at most N), classifies all of them with one grouped launch per
+ * kernel body (every camera's frames together), records their completion when
+ * the masks are written, enters them into their windows and re-merges the
+ * cameras whose window period ends; the next tick follows.  Frames of the
+ * other cameras run one by one on their cameras' streams.  Every mask is the
+ * one the window semantics give, whatever the grouping.  Non-blocking. */
+ocq_status ocq_server_submit_many(ocq_server *server, int n, const int *cameras, const uint8_t *const *frames,
+                                  uint8_t *const *masks, const uint64_t *tags);
 /* Up to max completed frames, oldest first; *n receives the count. */
 ocq_status ocq_server_poll(ocq_server *server, ocq_completion *out, int max, int *n);
 /* Waits for the camera's frames, frees its window and model, returns its budget. */

@@ -137,6 +137,64 @@ __global__ void __launch_bounds__(128) g_pixel_list(const GSeg *__restrict__ g, 
     classify_pixel_list_body<D, 8, KL>(s.in, s.F, s.hw, s.kept, s.mask, t);
 }
 
+// ---- serving ticks ------------------------------------------------------------------
+
+// Per-pixel leaf codes of one frame into its window slot (segment: in = frame,
+// kept = the slot's codes, units = pixels).
+template <int D>
+__global__ void __launch_bounds__(256) g_codes(const GSeg *__restrict__ g, int n) {
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  const int64_t tid = vb * blockDim.x + threadIdx.x, nth = s.vg * blockDim.x;
+  const uint8_t *frames = s.in;
+  uint16_t *codes = s.kept;
+  const int64_t npix = s.units;
+  int64_t tail = 0;
+  if ((reinterpret_cast<uintptr_t>(frames) & 15) == 0 && (reinterpret_cast<uintptr_t>(codes) & 15) == 0) {
+    const int64_t ng = npix >> 4;
+    for (int64_t q = tid; q < ng; q += nth) {
+      uint32_t w[12];
+      load_group_masked<D, true>(frames + q * 48, w);
+      uint32_t c[8];
+      static_for<0, 8>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        c[k] = planar_from_masked<D>(group_pixel<2 * k>(w)) | (planar_from_masked<D>(group_pixel<2 * k + 1>(w)) << 16);
+      });
+      reinterpret_cast<uint4 *>(codes + q * 16)[0] = make_uint4(c[0], c[1], c[2], c[3]);
+      reinterpret_cast<uint4 *>(codes + q * 16)[1] = make_uint4(c[4], c[5], c[6], c[7]);
+    }
+    tail = ng << 4;
+  }
+  for (int64_t p = tail + tid; p < npix; p += nth) {
+    const uint8_t *px = frames + p * 3;
+    codes[p] = (uint16_t)planar_code_rt(px[0], px[1], px[2], D);
+  }
+}
+
+// A camera's F entering frames, in order: bitset j (occ + j * units words)
+// replaces ring slot (aux + j) mod N and each leaf's count follows; the
+// bitsets are cleared for the next tick (segment: model = ring, kept = counts,
+// units = words per bitset, aux2 = leaves per word).
+__global__ void __launch_bounds__(256) g_count(const GSeg *__restrict__ g, int n) {
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  uint16_t *counts = s.kept;
+  for (int64_t w = vb * blockDim.x + threadIdx.x; w < s.units; w += s.vg * blockDim.x)
+    for (int j = 0; j < s.F; ++j) {
+      uint32_t *slot = s.model + ((s.aux + j) % s.N) * s.units;
+      uint32_t *fresh = s.occ + (int64_t)j * s.units;
+      const uint32_t old = slot[w], nw = fresh[w];
+      uint32_t diff = old ^ nw;
+      while (diff) {
+        const int i = __ffs(diff) - 1;
+        diff &= diff - 1;
+        if (i < s.aux2) counts[w * 32 + i] += ((nw >> i) & 1u) ? (uint16_t)1 : (uint16_t)0xFFFFu;
+      }
+      slot[w] = nw;
+      fresh[w] = 0u;
+    }
+}
+
 // ---- host side ----------------------------------------------------------------------
 
 using GKern = void (*)(const GSeg *, int);
@@ -197,6 +255,9 @@ static KInfo kinfo_d(int kind, int b) {
         k.fn = b == 2 ? g_pixel_list<D, 2> : b == 4 ? g_pixel_list<D, 4> : g_pixel_list<D, 8>;
       }
       break;
+    case GK_CODES:
+      if constexpr (D <= 5) k.fn = g_codes<D>;
+      break;
     default:
       break;
   }
@@ -204,9 +265,9 @@ static KInfo kinfo_d(int kind, int b) {
 }
 
 static KInfo kinfo(int kind, int a, int b) {
-  if (kind == GK_MERGE) {
+  if (kind == GK_MERGE || kind == GK_COUNT) {
     KInfo k;
-    k.fn = g_merge;
+    k.fn = kind == GK_MERGE ? g_merge : g_count;
     return k;
   }
   switch (a) {
@@ -377,6 +438,120 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
   }
   out.swap(L);
   return OCQ_OK;
+}
+
+// Sets CTA shapes, shared memory and per-segment virtual grids of planned
+// launches (segments' units filled in).
+static ocq_status finish_plan(std::vector<GLaunch> &L) {
+  for (GLaunch &x : L) {
+    KInfo k = kinfo(x.kind, x.a, x.b);
+    if (!k.fn) {
+      set_error("internal: no grouped kernel for kind %d (%d, %d)", x.kind, x.a, x.b);
+      return OCQ_EINVAL;
+    }
+    x.threads = k.threads;
+    x.smem = k.smem;
+    const int64_t cap = resident(k, x.smem);
+    int64_t cta = 0;
+    for (GSeg &s : x.segs) {
+      switch (x.kind) {
+        case GK_CLS_FRAME:
+        case GK_CODES: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 16 * 256), cap)); break;
+        case GK_BLOCK_TB: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 8), cap)); break;
+        case GK_PIX_WS_CLS: s.vg = std::max<int64_t>(1, std::min<int64_t>(s.units * s.F, cap)); break;
+        case GK_PIX_LIST: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 4), cap)); break;
+        case GK_COUNT: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 256), 64)); break;
+        default: break;  // GK_OCC: set by the planner
+      }
+      s.cta0 = cta;
+      cta += s.vg;
+    }
+    x.grid = cta;
+  }
+  return OCQ_OK;
+}
+
+ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunch> &out, std::vector<int> &single) {
+  out.clear();
+  single.clear();
+  std::vector<GLaunch> L;
+  auto launch = [&](int kind, int a, int b) -> GLaunch & {
+    for (GLaunch &x : L)
+      if (x.kind == kind && x.a == a && x.b == b) return x;
+    GLaunch x;
+    x.kind = kind, x.a = a, x.b = b;
+    L.push_back(x);
+    return L.back();
+  };
+  for (int i = 0; i < (int)in.size(); ++i) {
+    const GFrameIn &f = in[i];
+    const ocq_model *m = f.model;
+    const int d = m->depth;
+    const int64_t hw = (int64_t)m->H * m->W;
+    const uintptr_t al = reinterpret_cast<uintptr_t>(f.frame) | reinterpret_cast<uintptr_t>(f.mask);
+    GSeg c;
+    memset(&c, 0, sizeof c);
+    c.in = f.frame, c.mask = f.mask, c.model = m->bits, c.kept = m->kept, c.hw = hw;
+    c.N = m->N, c.F = 1, c.H = m->H, c.W = m->W, c.block = m->block, c.T = m->T;
+    c.bw = m->block > 0 ? (m->W + m->block - 1) / m->block : 1;
+    bool grouped = false;
+    if (m->kind == OCQ_REGION_FRAME && d <= 6) {
+      c.units = hw;
+      launch(GK_CLS_FRAME, d, 0).segs.push_back(c);
+      grouped = true;
+    } else if (m->kind == OCQ_REGION_BLOCK && d <= 5 && m->block % 4 == 0 && m->W % 4 == 0 && (al & 3) == 0) {
+      c.aux3 = (m->W + 127) / 128;
+      c.aux = (int64_t)((m->H + m->block - 1) / m->block) * c.aux3 * m->block;  // tiles
+      c.aux2 = 1, c.units = c.aux;
+      launch(GK_BLOCK_TB, d, 0).segs.push_back(c);
+      grouped = true;
+    } else if (m->kind == OCQ_REGION_PIXEL && d <= 3 && m->bits && hw % 1024 == 0 && (al & 15) == 0) {
+      c.units = hw / 1024;
+      launch(GK_PIX_WS_CLS, d, 0).segs.push_back(c);
+      grouped = true;
+    } else if (m->kind == OCQ_REGION_PIXEL && (d == 4 || d == 5) && m->kept && m->kept_len > 0 && hw % 4 == 0 &&
+               (al & 3) == 0) {
+      c.units = (hw + 127) / 128;
+      launch(GK_PIX_LIST, d, m->kept_len).segs.push_back(c);
+      grouped = true;
+    }
+    if (!grouped) single.push_back(i);
+  }
+  // the window: codes, or bitsets then the counts (after every classify)
+  for (const GFrameIn &f : in) {
+    const ocq_model *m = f.model;
+    const int64_t hw = (int64_t)m->H * m->W;
+    GSeg w;
+    memset(&w, 0, sizeof w);
+    w.in = f.frame, w.hw = hw, w.N = f.N, w.F = 1;
+    if (f.win == 2) {
+      w.kept = reinterpret_cast<uint16_t *>(f.ring) + f.slot * hw;
+      w.units = hw;
+      launch(GK_CODES, m->depth, 0).segs.push_back(w);
+    } else {
+      const int64_t wpr = wpr32(m->depth);
+      w.occ = f.fresh + (int64_t)f.j * wpr;
+      w.aux = (hw + kGroupOccChunk - 1) / kGroupOccChunk, w.vg = w.aux;
+      launch(GK_OCC, m->depth, 0).segs.push_back(w);
+    }
+  }
+  for (const GFrameIn &f : in) {
+    if (f.win != 1 || f.j != 0) continue;
+    GSeg k;
+    memset(&k, 0, sizeof k);
+    k.model = reinterpret_cast<uint32_t *>(f.ring), k.occ = f.fresh, k.kept = f.counts;
+    k.units = wpr32(f.model->depth), k.aux = f.slot, k.N = f.N, k.F = f.m;
+    k.aux2 = f.model->depth == 1 ? 8 : 32;
+    launch(GK_COUNT, 0, 0).segs.push_back(k);
+  }
+  // classify launches first, then the window's (a camera's counts after its bitsets)
+  std::stable_sort(L.begin(), L.end(), [](const GLaunch &p, const GLaunch &q) {
+    auto rank = [](int k) { return k == GK_COUNT ? 3 : k == GK_OCC || k == GK_CODES ? 2 : 1; };
+    return rank(p.kind) < rank(q.kind);
+  });
+  ocq_status rc = finish_plan(L);
+  if (rc == OCQ_OK) out.swap(L);
+  return rc;
 }
 
 ocq_status grouped_launch(const GLaunch &L, cudaStream_t st) {

@@ -36,7 +36,9 @@ enum GroupKind : int {
   GK_PIX_WS_BUILD, // per-pixel build, depth <= 3, counters + copy warp, a = depth
   GK_PIX_WS_CLS,   // per-pixel classify, depth <= 3, rows staged + copy warp, a = depth
   GK_PIX_MG,       // per-pixel candidate build, a = depth, b = candidate counters
-  GK_PIX_LIST      // per-pixel classify against kept-leaf lists, a = depth, b = list length
+  GK_PIX_LIST,     // per-pixel classify against kept-leaf lists, a = depth, b = list length
+  GK_CODES,        // serving window: per-pixel u16 leaf codes of one frame, a = depth
+  GK_COUNT         // serving window: a camera's new leaf bitsets into its ring and counts
 };
 
 // Branches of the batch graph a grouped launch belongs to.
@@ -64,6 +66,25 @@ struct GStreamIn {
 // branch; streams they do not cover are listed in `fallback` (run by their
 // plain kernels).  Sets each launch's CTA shape, shared memory and grid.
 ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &out, std::vector<int> &fallback);
+// One frame of a served camera in a serving tick (continuous batching: the
+// frames that arrived since the last tick, of every camera, classified and
+// entered into their windows by a few grouped launches).
+struct GFrameIn {
+  const uint8_t *frame;
+  uint8_t *mask;
+  const ocq_model *model;
+  int win;            // 1: leaf bitsets + counts, 2: per-pixel codes
+  uint8_t *ring;      // the camera's window
+  uint32_t *fresh;    // bits: N bitsets of entering frames
+  uint16_t *counts;   // bits
+  int N;
+  int64_t slot;       // ring slot of this frame
+  int j;              // this frame's index among its camera's frames of the tick
+  int m;              // the camera's frames in the tick (first frame's record: j == 0)
+};
+// Plans a tick: grouped classify launches, then window launches.  Frames no
+// grouped classify body takes are listed in `single` (classified one by one).
+ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunch> &out, std::vector<int> &single);
 // Enqueues one planned launch (segments already on the device) on `st`.
 ocq_status grouped_launch(const GLaunch &L, cudaStream_t st);
 // True (and cleared) if a bounded wait of a grouped body gave up.

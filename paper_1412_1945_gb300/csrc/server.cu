@@ -33,6 +33,7 @@
 #include <new>
 #include <vector>
 
+#include "grouped.cuh"
 #include "ocq_internal.cuh"
 
 namespace ocq {
@@ -75,8 +76,9 @@ struct Camera {
   // (wpr32(depth) u32 words, internal order); WIN_CODES N planes of H*W u16
   // leaf codes
   uint8_t *ring = nullptr;
-  uint32_t *fresh = nullptr;   // WIN_BITS: the entering frame's bitset
+  uint32_t *fresh = nullptr;   // WIN_BITS: the entering frames' bitsets (N slots)
   uint16_t *counts = nullptr;  // WIN_BITS: per leaf, window frames holding it
+  bool m0_joined = false;      // the server's tick stream waits for M_0 once
   ocq_model *model = nullptr;
   cudaStream_t stream = nullptr;  // high priority: classify, ring copies, completions
   cudaStream_t merge = nullptr;   // low priority: builds (M_0 and re-merges)
@@ -97,7 +99,54 @@ struct ocq_server {
   std::vector<Camera> cams;
   std::deque<ocq_completion> done;
   int64_t completed = 0;
+  // Continuous batching: the frames of cameras with a bitset or code window
+  // run in ticks on one high-priority stream; a tick classifies every frame
+  // it holds (of every camera) and enters them into their windows with a few
+  // grouped launches.
+  cudaStream_t tick = nullptr;
+  cudaEvent_t tick_ev = nullptr;
+  GSeg *d_segs = nullptr;
+  size_t segs_cap = 0;
+  // frames of cameras whose M_0 is still being built: held on the host (a tick
+  // would otherwise wait for the build and hold back every other camera)
+  struct Held {
+    int camera;
+    const uint8_t *frame;
+    uint8_t *mask;
+    uint64_t tag;
+    double arrival;
+  };
+  std::vector<Held> held;
 };
+
+// Cameras whose frames run in ticks (windows the grouped tick kernels serve).
+static bool tick_camera(const Camera &c) {
+  return c.win == WIN_CODES || (c.win == WIN_BITS && c.d.depth <= 6);
+}
+
+struct TickDone {
+  ocq_server *srv;
+  std::vector<Pending> frames;
+};
+
+static void CUDART_CB on_tick_done(void *arg) {
+  TickDone *d = static_cast<TickDone *>(arg);
+  {
+    std::lock_guard<std::mutex> lock(d->srv->mu);
+    const double t = now_s();
+    for (const Pending &p : d->frames) {
+      ocq_completion c;
+      c.camera = p.camera;
+      c.frame = p.frame;
+      c.tag = p.tag;
+      c.arrival_s = p.arrival;
+      c.done_s = t;
+      d->srv->done.push_back(c);
+      d->srv->completed++;
+    }
+  }
+  delete d;
+}
 
 static size_t camera_footprint(const ocq_camera_desc &d) {
   const size_t hw = (size_t)d.H * d.W;
@@ -107,8 +156,8 @@ static size_t camera_footprint(const ocq_camera_desc &d) {
   size_t scratch = 0;  // what a build of the model allocates beside it
   if (d.region.kind == OCQ_REGION_FRAME) scratch = (size_t)d.N * wpr32(d.depth) * 4;
   if (d.region.kind == OCQ_REGION_PIXEL && d.depth >= 6) scratch = hw * ((size_t)1 << (3 * d.depth - 9)) / 8;
-  if (form == WIN_BITS)  // the entering frame's bitset and the u16 counts; re-merged in place
-    return model + ring + (size_t)wpr32(d.depth) * 4 + ((size_t)1 << (3 * d.depth)) * 2 + scratch;
+  if (form == WIN_BITS)  // N entering-frame bitsets and the u16 counts; re-merged in place
+    return model + 2 * ring + ((size_t)1 << (3 * d.depth)) * 2 + scratch;
   if (form == WIN_CODES) return model + ring + scratch;
   return 2 * model + ring + scratch;  // the model being rebuilt lives beside the current one
 }
@@ -125,11 +174,11 @@ static ocq_status window_fill(Camera &c, const uint8_t *src) {
                        "ring fill");
   if (c.win == WIN_CODES)
     return launch_window_codes(src, (int64_t)d.N * d.H * d.W, d.depth, reinterpret_cast<uint16_t *>(c.ring), c.merge);
-  rc = cuda_status(malloc_async((void **)&c.fresh, slot, c.merge), "window bitset");
+  rc = cuda_status(malloc_async((void **)&c.fresh, (size_t)d.N * slot, c.merge), "window bitsets");
   if (rc == OCQ_OK)
     rc = cuda_status(malloc_async((void **)&c.counts, ((size_t)1 << (3 * d.depth)) * 2, c.merge), "window counts");
   if (rc == OCQ_OK) rc = cuda_status(cudaMemsetAsync(c.ring, 0, (size_t)d.N * slot, c.merge), "clear window");
-  if (rc == OCQ_OK) rc = cuda_status(cudaMemsetAsync(c.fresh, 0, slot, c.merge), "clear window");
+  if (rc == OCQ_OK) rc = cuda_status(cudaMemsetAsync(c.fresh, 0, (size_t)d.N * slot, c.merge), "clear window");
   if (rc == OCQ_OK)
     rc = launch_frame_occupancy(src, d.N, d.H, d.W, d.depth, reinterpret_cast<uint32_t *>(c.ring), c.merge);
   if (rc == OCQ_OK)
@@ -202,7 +251,15 @@ ocq_status ocq_server_create(size_t hbm_budget, int max_cameras, ocq_server **ou
       cudaStreamDestroy(st);
     }
   }
+  if (rc == OCQ_OK) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    rc = cuda_status(cudaStreamCreateWithPriority(&s->tick, cudaStreamNonBlocking, hi), "tick stream");
+    if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&s->tick_ev, cudaEventDisableTiming), "tick event");
+  }
   if (rc != OCQ_OK) {
+    if (s->tick_ev) cudaEventDestroy(s->tick_ev);
+    if (s->tick) cudaStreamDestroy(s->tick);
     if (s->pool) cudaMemPoolDestroy(s->pool);
     delete s;
     return rc;
@@ -250,6 +307,7 @@ ocq_status ocq_server_admit(ocq_server *s, const ocq_camera_desc *d, const uint8
   c.footprint = fp;
   c.submitted = 0;
   c.win = window_form(*d);
+  c.m0_joined = false;
   int lo = 0, hi = 0;
   cudaDeviceGetStreamPriorityRange(&lo, &hi);  // lo = least urgent, hi = most urgent
   ocq_status rc = cuda_status(cudaStreamCreateWithPriority(&c.stream, cudaStreamNonBlocking, hi), "camera stream");
@@ -278,14 +336,12 @@ ocq_status ocq_server_admit(ocq_server *s, const ocq_camera_desc *d, const uint8
   return OCQ_OK;
 }
 
-ocq_status ocq_server_submit(ocq_server *s, int camera, const uint8_t *frame, uint8_t *mask, uint64_t tag) {
-  if (!s || camera < 0 || camera >= s->max_cameras || !s->cams[camera].live || !frame || !mask) {
-    set_error("ocq_server_submit: bad camera or buffers");
-    return OCQ_EINVAL;
-  }
-  PoolScope scope(s->pool);
+// The per-frame path (cameras that keep their frames): classify on the
+// camera's stream, completion callback, ring copy, and every K frames a
+// rebuild on the camera's low-priority stream.
+static ocq_status submit_frame_path(ocq_server *s, int camera, const uint8_t *frame, uint8_t *mask, uint64_t tag,
+                                    double arrival) {
   Camera &c = s->cams[camera];
-  const double arrival = now_s();
   const int64_t t = c.submitted++;
   const size_t fbytes = (size_t)c.d.H * c.d.W * 3;
   ocq_status rc = ocq_classify(c.model, frame, 1, mask, c.stream);
@@ -337,10 +393,201 @@ ocq_status ocq_server_submit(ocq_server *s, int camera, const uint8_t *frame, ui
   return rc;
 }
 
+// One tick: the frames `idx` (in submission order, at most N per camera and
+// none after a camera's re-merge frame) classified by grouped launches on the
+// tick stream, one completion callback when their masks are written, then
+// their window entries and the re-merges that fall at the tick's end.
+static ocq_status run_tick(ocq_server *s, const std::vector<int> &idx, const int *cameras,
+                           const uint8_t *const *frames, uint8_t *const *masks, const uint64_t *tags,
+                           const double *arrival) {
+  std::vector<GFrameIn> fin;
+  std::vector<int> first(s->max_cameras, -1), taken(s->max_cameras, 0);
+  TickDone *done = new (std::nothrow) TickDone();
+  if (!done) return OCQ_ENOMEM;
+  done->srv = s;
+  ocq_status rc = OCQ_OK;
+  for (int i : idx) {
+    Camera &c = s->cams[cameras[i]];
+    if (!c.m0_joined) {  // M_0 (admission or resume) is built on the camera's build stream
+      rc = cuda_status(cudaStreamWaitEvent(s->tick, c.merged, 0), "wait for M_0");
+      if (rc != OCQ_OK) break;
+      c.m0_joined = true;
+    }
+    const int64_t t = c.submitted + taken[c.id];
+    GFrameIn f;
+    f.frame = frames[i], f.mask = masks[i], f.model = c.model, f.win = c.win == WIN_BITS ? 1 : 2;
+    f.ring = c.ring, f.fresh = c.fresh, f.counts = c.counts, f.N = c.d.N;
+    f.slot = (c.d.N + t) % c.d.N, f.j = taken[c.id], f.m = 0;
+    if (first[c.id] < 0) first[c.id] = (int)fin.size();
+    taken[c.id]++;
+    fin.push_back(f);
+    done->frames.push_back(Pending{s, c.id, t, tags[i], arrival[i]});
+  }
+  for (GFrameIn &f : fin)
+    if (f.j == 0) f.m = taken[done->frames[&f - &fin[0]].camera];
+  std::vector<GLaunch> L;
+  std::vector<int> single;
+  if (rc == OCQ_OK) rc = grouped_plan_tick(fin, L, single);
+  size_t nseg = 0;
+  for (const GLaunch &x : L) nseg += x.segs.size();
+  if (rc == OCQ_OK && nseg > s->segs_cap) {  // stream-ordered: earlier ticks' kernels are done with it
+    if (s->d_segs) cudaFreeAsync(s->d_segs, s->tick);
+    s->d_segs = nullptr;
+    s->segs_cap = std::max(nseg, 2 * s->segs_cap);
+    rc = cuda_status(malloc_async((void **)&s->d_segs, s->segs_cap * sizeof(GSeg), s->tick), "tick segments");
+  }
+  std::vector<GSeg> host;
+  host.reserve(nseg);
+  for (GLaunch &x : L) host.insert(host.end(), x.segs.begin(), x.segs.end());
+  if (rc == OCQ_OK && nseg)
+    rc = cuda_status(cudaMemcpyAsync(s->d_segs, host.data(), nseg * sizeof(GSeg), cudaMemcpyHostToDevice, s->tick),
+                     "upload tick segments");
+  size_t at = 0;
+  for (GLaunch &x : L) x.dev = s->d_segs + at, at += x.segs.size();
+  for (size_t k = 0; k < single.size() && rc == OCQ_OK; ++k)
+    rc = ocq_classify(fin[single[k]].model, fin[single[k]].frame, 1, fin[single[k]].mask, s->tick);
+  size_t li = 0;
+  for (; li < L.size() && rc == OCQ_OK; ++li) {  // classification (window launches follow)
+    if (L[li].kind == GK_CODES || L[li].kind == GK_OCC || L[li].kind == GK_COUNT) break;
+    rc = grouped_launch(L[li], s->tick);
+  }
+  if (rc == OCQ_OK) {  // the masks are written: completion time
+    rc = cuda_status(cudaLaunchHostFunc(s->tick, on_tick_done, done), "tick completion");
+    if (rc == OCQ_OK) done = nullptr;
+  }
+  for (; li < L.size() && rc == OCQ_OK; ++li) rc = grouped_launch(L[li], s->tick);
+  // re-merges: a camera's last frame of the tick closes its window period
+  for (int cam = 0; cam < s->max_cameras && rc == OCQ_OK; ++cam) {
+    if (!taken[cam]) continue;
+    Camera &c = s->cams[cam];
+    c.submitted += taken[cam];
+    if (c.submitted % c.d.K != 0) continue;
+    if (c.win == WIN_BITS)
+      rc = launch_window_threshold(c.counts, c.d.depth, (uint32_t)c.d.T, c.model->bits, s->tick);
+    else
+      rc = launch_remerge_codes(reinterpret_cast<uint16_t *>(c.ring), c.d.N, c.model, s->tick);
+  }
+  delete done;
+  return rc;
+}
+
+// Runs the frames `pending` (indices into the arrays, submission order) of
+// cameras served in ticks as ticks, each holding for every camera its next
+// frames up to its next re-merge (and at most N).
+static ocq_status run_ticks(ocq_server *s, std::vector<int> pending, const int *cameras, const uint8_t *const *frames,
+                            uint8_t *const *masks, const uint64_t *tags, const double *arrival) {
+  std::vector<int> take, rest, count(s->max_cameras, 0);
+  std::vector<char> closed(s->max_cameras, 0);
+  ocq_status rc = OCQ_OK;
+  while (rc == OCQ_OK && !pending.empty()) {
+    take.clear(), rest.clear();
+    std::fill(count.begin(), count.end(), 0);
+    std::fill(closed.begin(), closed.end(), 0);
+    for (int i : pending) {
+      const Camera &c = s->cams[cameras[i]];
+      if (closed[c.id]) {
+        rest.push_back(i);
+        continue;
+      }
+      const int64_t t = c.submitted + count[c.id];
+      take.push_back(i);
+      if (++count[c.id] == c.d.N || (t + 1) % c.d.K == 0) closed[c.id] = 1;
+    }
+    rc = run_tick(s, take, cameras, frames, masks, tags, arrival);
+    pending.swap(rest);
+  }
+  return rc;
+}
+
+static bool m0_ready(Camera &c) { return c.m0_joined || cudaEventQuery(c.merged) == cudaSuccess; }
+
+// Moves held frames of cameras whose M_0 is ready (all of them with `wait`)
+// into ticks, after first appending `extra` frames; frames of a camera stay
+// in submission order (a camera with held frames holds its new ones too).
+static ocq_status flush(ocq_server *s, bool wait, int n = 0, const int *cameras = nullptr,
+                        const uint8_t *const *frames = nullptr, uint8_t *const *masks = nullptr,
+                        const uint64_t *tags = nullptr, double arrival = 0.0) {
+  for (int i = 0; i < n; ++i) s->held.push_back({cameras[i], frames[i], masks[i], tags[i], arrival});
+  if (s->held.empty()) return OCQ_OK;
+  std::vector<char> ready(s->max_cameras, 0), seen(s->max_cameras, 0);
+  std::vector<int> cam, idx;
+  std::vector<const uint8_t *> fr;
+  std::vector<uint8_t *> mk;
+  std::vector<uint64_t> tg;
+  std::vector<double> ar;
+  std::vector<ocq_server::Held> keep;
+  for (const ocq_server::Held &h : s->held) {
+    Camera &c = s->cams[h.camera];
+    if (!seen[h.camera]) {
+      seen[h.camera] = 1;
+      if (wait && !c.m0_joined) cudaEventSynchronize(c.merged);
+      ready[h.camera] = m0_ready(c);
+    }
+    if (!ready[h.camera]) {
+      keep.push_back(h);
+      continue;
+    }
+    idx.push_back((int)cam.size());
+    cam.push_back(h.camera), fr.push_back(h.frame), mk.push_back(h.mask), tg.push_back(h.tag), ar.push_back(h.arrival);
+  }
+  s->held.swap(keep);
+  if (idx.empty()) return OCQ_OK;
+  return run_ticks(s, idx, cam.data(), fr.data(), mk.data(), tg.data(), ar.data());
+}
+
+// Continuous batching: the frames of cameras served in ticks go into ticks
+// (held on the host while a camera's M_0 is being built); the other cameras'
+// frames take the per-frame path.
+static ocq_status submit_many(ocq_server *s, int n, const int *cameras, const uint8_t *const *frames,
+                              uint8_t *const *masks, const uint64_t *tags) {
+  for (int i = 0; i < n; ++i)
+    if (cameras[i] < 0 || cameras[i] >= s->max_cameras || !s->cams[cameras[i]].live || !frames[i] || !masks[i]) {
+      set_error("ocq_server_submit: bad camera or buffers (entry %d)", i);
+      return OCQ_EINVAL;
+    }
+  PoolScope scope(s->pool);
+  const double arrival = now_s();
+  std::vector<int> cam;
+  std::vector<const uint8_t *> fr;
+  std::vector<uint8_t *> mk;
+  std::vector<uint64_t> tg;
+  ocq_status rc = OCQ_OK;
+  for (int i = 0; i < n && rc == OCQ_OK; ++i) {
+    if (tick_camera(s->cams[cameras[i]]))
+      cam.push_back(cameras[i]), fr.push_back(frames[i]), mk.push_back(masks[i]), tg.push_back(tags[i]);
+    else
+      rc = submit_frame_path(s, cameras[i], frames[i], masks[i], tags[i], arrival);
+  }
+  if (rc == OCQ_OK) rc = flush(s, false, (int)cam.size(), cam.data(), fr.data(), mk.data(), tg.data(), arrival);
+  return rc;
+}
+
+ocq_status ocq_server_submit(ocq_server *s, int camera, const uint8_t *frame, uint8_t *mask, uint64_t tag) {
+  if (!s) {
+    set_error("ocq_server_submit: NULL server");
+    return OCQ_EINVAL;
+  }
+  return submit_many(s, 1, &camera, &frame, &mask, &tag);
+}
+
+ocq_status ocq_server_submit_many(ocq_server *s, int n, const int *cameras, const uint8_t *const *frames,
+                                  uint8_t *const *masks, const uint64_t *tags) {
+  if (!s || n < 0 || (n > 0 && (!cameras || !frames || !masks || !tags))) {
+    set_error("ocq_server_submit_many: bad arguments");
+    return OCQ_EINVAL;
+  }
+  return n ? submit_many(s, n, cameras, frames, masks, tags) : OCQ_OK;
+}
+
 ocq_status ocq_server_poll(ocq_server *s, ocq_completion *out, int max, int *n) {
   if (!s || !n || max < 0 || (max > 0 && !out)) {
     set_error("ocq_server_poll: bad arguments");
     return OCQ_EINVAL;
+  }
+  if (!s->held.empty()) {  // cameras whose M_0 is now built
+    PoolScope scope(s->pool);
+    ocq_status rc = flush(s, false);
+    if (rc != OCQ_OK) return rc;
   }
   std::lock_guard<std::mutex> lock(s->mu);
   int k = 0;
@@ -357,9 +604,17 @@ ocq_status ocq_server_release(ocq_server *s, int camera) {
     set_error("ocq_server_release: bad camera");
     return OCQ_EINVAL;
   }
+  if (!s->held.empty()) {  // the camera's held frames run first
+    PoolScope scope(s->pool);
+    flush(s, true);
+  }
   Camera &c = s->cams[camera];
   // Builds and frames both finish before the memory goes back to the pool.
   cudaStreamWaitEvent(c.stream, c.merged, 0);
+  if (tick_camera(c)) {  // its frames ran on the tick stream
+    cudaEventRecord(s->tick_ev, s->tick);
+    cudaStreamWaitEvent(c.stream, s->tick_ev, 0);
+  }
   c.model->stream = c.stream;
   ocq_model_free(c.model);
   window_free(c, c.stream);
@@ -387,6 +642,11 @@ ocq_status ocq_server_snapshot(ocq_server *s, int camera, uint64_t *model_words,
     set_error("ocq_server_snapshot: bad camera or buffers");
     return OCQ_EINVAL;
   }
+  if (!s->held.empty()) {  // the camera's held frames run first
+    PoolScope scope(s->pool);
+    ocq_status rf = flush(s, true);
+    if (rf != OCQ_OK) return rf;
+  }
   Camera &c = s->cams[camera];
   const int64_t t = c.submitted;
   const size_t fbytes = window_slot_bytes(c.d, c.win);
@@ -394,6 +654,10 @@ ocq_status ocq_server_snapshot(ocq_server *s, int camera, uint64_t *model_words,
   // (training frames are 0 .. N - 1), frame g in slot g mod N: copy the slots
   // oldest first.
   ocq_status rc = cuda_status(cudaStreamWaitEvent(c.stream, c.merged, 0), "snapshot wait");
+  if (rc == OCQ_OK && tick_camera(c)) {  // after the ticks that hold its frames
+    rc = cuda_status(cudaEventRecord(s->tick_ev, s->tick), "snapshot tick");
+    if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent(c.stream, s->tick_ev, 0), "snapshot wait");
+  }
   if (rc == OCQ_OK) rc = ocq_model_export(c.model, model_words, words, c.stream);
   for (int i = 0; i < c.d.N && rc == OCQ_OK; ++i)
     rc = cuda_status(cudaMemcpyAsync(ring_out + (size_t)i * fbytes, c.ring + (size_t)((t + i) % c.d.N) * fbytes,
@@ -403,6 +667,8 @@ ocq_status ocq_server_snapshot(ocq_server *s, int camera, uint64_t *model_words,
   if (rc == OCQ_OK) rc = cuda_status(cudaEventCreateWithFlags(&done, cudaEventDisableTiming), "event");
   if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(done, c.stream), "snapshot done");
   if (rc == OCQ_OK) rc = cuda_status(cudaStreamWaitEvent((cudaStream_t)stream, done, 0), "snapshot join");
+  // later ticks rewrite the window and the model: after the copies
+  if (rc == OCQ_OK && tick_camera(c)) rc = cuda_status(cudaStreamWaitEvent(s->tick, done, 0), "snapshot tick join");
   if (done) cudaEventDestroy(done);
   if (rc == OCQ_OK) *submitted = t;
   return rc;
@@ -438,6 +704,7 @@ ocq_status ocq_server_resume(ocq_server *s, const ocq_camera_desc *d, const uint
   c.footprint = fp;
   c.submitted = submitted;
   c.win = window_form(*d);
+  c.m0_joined = false;
   int lo = 0, hi = 0;
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
   ocq_status rc = cuda_status(cudaStreamCreateWithPriority(&c.stream, cudaStreamNonBlocking, hi), "camera stream");
@@ -451,10 +718,10 @@ ocq_status ocq_server_resume(ocq_server *s, const ocq_camera_desc *d, const uint
                                      fbytes, cudaMemcpyDeviceToDevice, c.merge),
                      "window restore");
   if (rc == OCQ_OK && c.win == WIN_BITS) {  // the counts follow from the bitsets
-    rc = cuda_status(malloc_async((void **)&c.fresh, fbytes, c.merge), "window bitset");
+    rc = cuda_status(malloc_async((void **)&c.fresh, (size_t)d->N * fbytes, c.merge), "window bitsets");
     if (rc == OCQ_OK)
       rc = cuda_status(malloc_async((void **)&c.counts, ((size_t)1 << (3 * d->depth)) * 2, c.merge), "window counts");
-    if (rc == OCQ_OK) rc = cuda_status(cudaMemsetAsync(c.fresh, 0, fbytes, c.merge), "clear window");
+    if (rc == OCQ_OK) rc = cuda_status(cudaMemsetAsync(c.fresh, 0, (size_t)d->N * fbytes, c.merge), "clear window");
     if (rc == OCQ_OK)
       rc = launch_window_counts_init(reinterpret_cast<uint32_t *>(c.ring), d->N, d->depth, c.counts, c.merge);
   }
@@ -511,19 +778,30 @@ ocq_status ocq_server_sync(ocq_server *s) {
     set_error("ocq_server_sync: NULL server");
     return OCQ_EINVAL;
   }
+  if (!s->held.empty()) {
+    PoolScope scope(s->pool);
+    ocq_status rc = flush(s, true);
+    if (rc != OCQ_OK) return rc;
+  }
   for (Camera &c : s->cams)
     if (c.live) {
       cudaError_t e = cudaStreamSynchronize(c.stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c.merge);
       if (e != cudaSuccess) return cuda_status(e, "server sync");
     }
-  return OCQ_OK;
+  return cuda_status(cudaStreamSynchronize(s->tick), "server sync");
 }
 
 void ocq_server_destroy(ocq_server *s) {
   if (!s) return;
   for (int i = 0; i < s->max_cameras; ++i)
     if (s->cams[i].live) ocq_server_release(s, i);
+  if (s->tick) {
+    if (s->d_segs) cudaFreeAsync(s->d_segs, s->tick);
+    cudaStreamSynchronize(s->tick);
+    cudaStreamDestroy(s->tick);
+  }
+  if (s->tick_ev) cudaEventDestroy(s->tick_ev);
   if (s->pool) cudaMemPoolDestroy(s->pool);  // every camera's memory was freed and its stream synchronised
   delete s;
 }

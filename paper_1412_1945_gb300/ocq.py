@@ -109,6 +109,8 @@ SIGNATURES = {
     "ocq_server_window_bytes": (_sz, [ctypes.POINTER(ocq_camera_desc)]),
     "ocq_server_admit": (_i32, [_vp, ctypes.POINTER(ocq_camera_desc), _vp, ctypes.POINTER(_i32)]),
     "ocq_server_submit": (_i32, [_vp, _i32, _vp, _vp, ctypes.c_uint64]),
+    "ocq_server_submit_many": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
     "ocq_server_poll": (_i32, [_vp, ctypes.POINTER(ocq_completion), _i32, ctypes.POINTER(_i32)]),
     "ocq_server_release": (_i32, [_vp, _i32]),
     "ocq_server_camera_model": (_i32, [_vp, _i32, ctypes.POINTER(_vp)]),
@@ -509,6 +511,21 @@ def ocq_server_admit(server, H, W, kind, block, depth, T, N, K, train):
 
 def ocq_server_submit(server, camera, frame, mask, tag=0):
     _check(load().ocq_server_submit(server.handle, camera, _p(frame), _p(mask), tag))
+
+
+def ocq_server_submit_many(server, cameras, frames, masks, tags):
+    """Submits len(cameras) frames at once (continuous batching); frames and
+    masks are CUDA tensors or raw device addresses."""
+    n = len(cameras)
+    if not (len(frames) == len(masks) == len(tags) == n):
+        raise ValueError("cameras, frames, masks and tags must have the same length")
+    if n == 0:
+        return
+    cam = (_i32 * n)(*cameras)
+    fr = (_vp * n)(*[_p(f) for f in frames])
+    mk = (_vp * n)(*[_p(m) for m in masks])
+    tg = (ctypes.c_uint64 * n)(*tags)
+    _check(load().ocq_server_submit_many(server.handle, n, cam, fr, mk, tg))
 
 
 def ocq_server_poll(server, max_n=4096):

@@ -90,7 +90,7 @@ def test_camera_footprint_follows_the_model_form(lib):
         N * 64 * 64 * 3 + 64 * 64 * 8 ** 3 // 8
     fr = ocq.OCQ_REGION_FRAME
     wb = 8 ** 4 // 8
-    assert ocq.ocq_server_camera_footprint(H, W, fr, 0, 4, 10, N, K) == wb + N * wb + wb + 2 * 8 ** 4 + N * wb
+    assert ocq.ocq_server_camera_footprint(H, W, fr, 0, 4, 10, N, K) == wb + N * wb + N * wb + 2 * 8 ** 4 + N * wb
     assert ocq.ocq_server_window_bytes(H, W, fr, 0, 4, 10, N, K) == N * wb
     assert ocq.ocq_server_window_bytes(8, 8, fr, 0, 6, 10, N, K) == N * 8 * 8 * 3  # bitset larger than a frame
     mf = ocq.OCQ_TUNE_PIXEL_MODEL_FORM

@@ -85,3 +85,47 @@ def test_window_footprints_shrink(cuda_ready):
         if d == 5:
             model = H * W * 16  # a list model (floor(N/T) = 3 <= 8)
         assert fp == model + N * H * W * 2
+
+
+@pytest.mark.parametrize("chunks", [1, 3, 7])
+def test_batched_submits_follow_the_window_semantics(cuda_ready, chunks):
+    """Every camera of the set in one server, their frames interleaved and
+    handed over in `chunks` batched submits (continuous batching: a tick holds
+    several frames of several cameras and splits at each camera's re-merge);
+    each camera's masks and final model follow the window semantics."""
+    import torch
+
+    O = cuda_ready.ocq
+    srv = O.ocq_server_create(1 << 30, len(CAMERAS))
+    hosts, devs, masks, ids = [], [], [], []
+    try:
+        for i, cam in enumerate(CAMERAS):
+            scene, H, W, region, block, d, T, N, K, F, form = cam
+            host = ocq_synth.fill_host(ocq_synth.make_scene(scene, H, W, N, F, 7300 + i), 0, N + F)
+            hosts.append(host)
+            devs.append(torch.from_numpy(host).cuda())
+            masks.append(torch.full((F, H, W), 9, dtype=torch.uint8, device="cuda"))
+        torch.cuda.synchronize()
+        for i, cam in enumerate(CAMERAS):
+            scene, H, W, region, block, d, T, N, K, F, form = cam
+            ids.append(O.ocq_server_admit(srv, H, W, region, block, d, T, N, K, devs[i][:N].contiguous()))
+            assert ids[-1] is not None
+        order = [(i, t) for t in range(max(c[9] for c in CAMERAS)) for i, c in enumerate(CAMERAS) if t < c[9]]
+        rng = np.random.default_rng(chunks)
+        cuts = sorted(rng.choice(np.arange(1, len(order)), size=chunks - 1, replace=False).tolist()) if chunks > 1 else []
+        for a, b in zip([0] + cuts, cuts + [len(order)]):
+            part = order[a:b]
+            O.ocq_server_submit_many(srv, [ids[i] for i, _ in part],
+                                     [devs[i][CAMERAS[i][7] + t] for i, t in part],
+                                     [masks[i][t] for i, t in part], [1000 * i + t for i, t in part])
+        O.ocq_server_sync(srv)
+        done = O.ocq_server_poll(srv, 100000)
+        assert len(done) == len(order)
+        for i, cam in enumerate(CAMERAS):
+            scene, H, W, region, block, d, T, N, K, F, form = cam
+            assert (masks[i].cpu().numpy() == _window_oracle(hosts[i], cam)).all(), i
+            model = cuda_ready.export_model(O.ocq_server_camera_model(srv, ids[i])).cpu().numpy().view(np.uint64)
+            k = F // K
+            assert (model == oracle.build_model(hosts[i][k * K:k * K + N], d, T, region, block)).all(), i
+    finally:
+        srv.destroy()
