@@ -517,9 +517,10 @@ struct BlockTileCfg {
   // per sub-table (suffixes), sub-tables in the warp's pool
   static constexpr int NPRE = 512;
   static constexpr int SUB = D > 3 ? 1 << (3 * (D - 3)) : 1;
+  static constexpr int SUBS = SUB + 2;  // entries between sub-tables (a one-bank skew)
   static constexpr int NP = D == 4 ? 128 : (B == 8 ? 96 : 128);  // (8 x 8 at depth 5 is not dispatched here)
   static constexpr int DIR_BYTES = RPT * NPRE * 2;
-  static constexpr int POOL_BYTES = NP * SUB * 2;
+  static constexpr int POOL_BYTES = (NP * SUBS * 2 + 15) & ~15;
   static constexpr int OWNER_BYTES = NP * 2;
   static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
   static constexpr int TABLE_BYTES = DIRECT ? (RPT * SS * 2 + 15) & ~15
@@ -675,11 +676,11 @@ __device__ __forceinline__ void build_block_tile_body(const uint8_t *__restrict_
             uint32_t e[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k)
-              if (!((deferred >> k) & 1u)) e[k] = vp[(sub[k] - 1u) * C::SUB + suf[k]];
+              if (!((deferred >> k) & 1u)) e[k] = vp[(sub[k] - 1u) * C::SUBS + suf[k]];
 #pragma unroll
             for (int k = 0; k < 8; ++k)
               if (!((deferred >> k) & 1u) && e[k] < fh)
-                vp[(sub[k] - 1u) * C::SUB + suf[k]] = (uint16_t)(fh | ((e[k] + 1u) & 0xFFu));
+                vp[(sub[k] - 1u) * C::SUBS + suf[k]] = (uint16_t)(fh | ((e[k] + 1u) & 0xFFu));
           }
           __syncwarp();
           // pixels whose prefix another lane was claiming: its directory entry
@@ -693,8 +694,8 @@ __device__ __forceinline__ void build_block_tile_body(const uint8_t *__restrict_
                 if ((deferred >> k) & 1u) {
                   const uint32_t sb = vd[pre[k]];
                   if (sb == 0u || sb == 0xFFFFu) continue;  // unreachable unless the region overflowed
-                  const uint32_t e = vp[(sb - 1u) * C::SUB + suf[k]];
-                  if (e < fh) vp[(sb - 1u) * C::SUB + suf[k]] = (uint16_t)(fh | ((e + 1u) & 0xFFu));
+                  const uint32_t e = vp[(sb - 1u) * C::SUBS + suf[k]];
+                  if (e < fh) vp[(sb - 1u) * C::SUBS + suf[k]] = (uint16_t)(fh | ((e + 1u) & 0xFFu));
                 }
             }
             __syncwarp();
@@ -754,14 +755,15 @@ __device__ __forceinline__ void build_block_tile_body(const uint8_t *__restrict_
       __syncwarp();
       const uint32_t used = min(*(volatile uint32_t *)pcount, (uint32_t)C::NP);
       for (uint32_t i = lane; i < used * C::SUB; i += 32) {
-        const uint32_t e = pool[i];
+        const uint32_t jt = i / C::SUB, sx = i - jt * C::SUB;
+        const uint32_t e = pool[jt * C::SUBS + sx];
         if (e) {
-          pool[i] = 0;
-          const uint32_t o = owner[i / C::SUB];
+          pool[jt * C::SUBS + sx] = 0;
+          const uint32_t o = owner[jt];
           const int r = (int)(o >> 9);
           uint32_t *row = region_row(r);
           if (row && !((ovf >> r) & 1u) && (e & 0xFFu) >= T) {
-            const uint32_t q = tile_compose<D>(o & 511u, i % C::SUB);
+            const uint32_t q = tile_compose<D>(o & 511u, sx);
             atomicOr(&row[q >> 5], 1u << (q & 31));
           }
         }
