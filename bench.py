@@ -51,6 +51,8 @@ def parse_args(argv=None):
                     help="skip the per-config section (tiny whole-frame and 16x16-block presets)")
     ap.add_argument("--config", choices=("tiny", "blocks"), default=None,
                     help="print the line of one smaller preset instead of the 1080p per-pixel workload")
+    ap.add_argument("--time-forms", action="store_true",
+                    help="with --profile-case: CUDA-event times of each build (both block-build forms) and classify")
     ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES), default=None,
                     help="run one small fixed case twice (warm-up, then the pass to capture) for ncu, print one "
                          "line and exit; no measurement")
@@ -1026,6 +1028,8 @@ PROFILE_CASES = {
     "pixel_deep_1080p": ("clusters", 1080, 1920, 30, 40, [(2, 0, 4), (2, 0, 5)]),
     "block8_1080p": ("clusters", 1080, 1920, 30, 40, [(1, 8, 3), (1, 8, 5)]),
     "block16_1080p": ("sway", 1080, 1920, 30, 40, [(1, 16, 5)]),
+    "block_mix_1080p": ("sway", 1080, 1920, 30, 40, [(1, 8, 3), (1, 8, 4), (1, 8, 5), (1, 16, 4), (1, 16, 5)]),
+    "block16_320x240": ("sway", 240, 320, 30, 300, [(1, 16, 5)]),
 }
 
 
@@ -1046,6 +1050,35 @@ def profile_case(args):
     ocq_synth.fill_device(sc, 0, N, tr)
     ocq_synth.fill_device(sc, N, F, te)
     mask = torch.empty((F, H, W), dtype=torch.uint8, device="cuda")
+    if args.time_forms:  # CUDA events, 10 runs each, after one warm-up run
+        def timed(fn, n=10):
+            fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            for _ in range(n):
+                fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            return round(e0.elapsed_time(e1) / n, 4)
+
+        kb = O.OCQ_TUNE_BUILD_BLOCK
+        saved = O.ocq_tune_selected(kb)
+        out = []
+        for region, block, depth in runs:
+            r = {"region": region, "block": block, "depth": depth}
+            for form in (0, 1):
+                O.ocq_tune_select(kb, form)
+                r[f"build_ms_form{form}"] = timed(
+                    lambda: O.ocq_build_model(tr, N, H, W, region, block, depth, 10, st).free())
+            O.ocq_tune_select(kb, saved)
+            m = O.ocq_build_model(tr, N, H, W, region, block, depth, 10, st)
+            r["classify_ms"] = timed(lambda: O.ocq_classify(m, te, F, mask, st))
+            m.free()
+            out.append(r)
+        ocq.device_status()
+        print(json.dumps({"profile_case": args.profile_case, "frames": [N, F], "times": out}), flush=True)
+        return
     for _ in range(2):
         for region, block, depth in runs:
             m = O.ocq_build_model(tr, N, H, W, region, block, depth, 10, st)
