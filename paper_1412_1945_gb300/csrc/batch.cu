@@ -598,17 +598,17 @@ static ocq_status enqueue_grouped(ocq_batch *b, cudaStream_t cs) {
   ocq_status rc = plan_grouped(b);
   if (rc != OCQ_OK) return rc;
   const int nfb = std::min<int>((int)b->gfallback.size(), 8);
-  const int NB = GB_COUNT + nfb;
+  const int NB = kGroupBranches + nfb;
   rc = ensure_side_streams(b, NB);
-  if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(b->fork, cs), "fork");
-  for (int i = 0; i < NB && rc == OCQ_OK; ++i) rc = cuda_status(cudaStreamWaitEvent(b->side[i], b->fork, 0), "fork wait");
-  // whole-frame occupancy is ORed into zeroed scratch
+  // whole-frame occupancy is ORed into zeroed scratch (before the branches fork)
   for (size_t s = 0; s < b->hs.size() && rc == OCQ_OK; ++s) {
     const BStream &h = b->hs[s];
     if (h.kind != OCQ_REGION_FRAME || !h.occ) continue;
     if (std::find(b->gfallback.begin(), b->gfallback.end(), (int)s) != b->gfallback.end()) continue;
-    rc = cuda_status(cudaMemsetAsync(h.occ, 0, (size_t)h.N * h.wpr * 4, b->side[GB_FRAME]), "clear occupancy");
+    rc = cuda_status(cudaMemsetAsync(h.occ, 0, (size_t)h.N * h.wpr * 4, cs), "clear occupancy");
   }
+  if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(b->fork, cs), "fork");
+  for (int i = 0; i < NB && rc == OCQ_OK; ++i) rc = cuda_status(cudaStreamWaitEvent(b->side[i], b->fork, 0), "fork wait");
   for (const GLaunch &L : b->glaunch) {
     if (rc != OCQ_OK) break;
     rc = grouped_launch(L, b->side[L.branch]);
@@ -616,7 +616,7 @@ static ocq_status enqueue_grouped(ocq_batch *b, cudaStream_t cs) {
   for (size_t k = 0; k < b->gfallback.size() && rc == OCQ_OK; ++k) {
     const int s = b->gfallback[k];
     const ocq_stream_desc &d = b->desc[s];
-    cudaStream_t st = b->side[GB_COUNT + (int)(k % (size_t)nfb)];
+    cudaStream_t st = b->side[kGroupBranches + (int)(k % (size_t)nfb)];
     rc = launch_build(d.train, d.N, b->models[s], st);
     if (rc == OCQ_OK && d.F > 0) rc = launch_classify(b->models[s], d.test, d.F, d.mask, st);
   }

@@ -296,9 +296,28 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
   fallback.clear();
   // launch key -> index in `out`, created in the order the phases run
   std::vector<GLaunch> L;
-  auto launch = [&](int kind, int a, int b, int branch) -> GLaunch & {
+  // each class's streams dealt to kGroupSplit branches, largest first
+  std::vector<int> share(in.size(), 0);
+  {
+    std::vector<int> order(in.size());
+    for (size_t i = 0; i < in.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return (int64_t)in[x].H * in[x].W * (in[x].N + in[x].F) > (int64_t)in[y].H * in[y].W * (in[y].N + in[y].F);
+    });
+    int dealt[GB_COUNT] = {0, 0, 0, 0};
+    for (int i : order) {
+      const GStreamIn &x = in[i];
+      const int cls = x.kind == OCQ_REGION_FRAME ? GB_FRAME
+                      : x.kind == OCQ_REGION_BLOCK ? GB_BLOCK
+                      : x.depth <= 3 ? GB_PIXEL : GB_PIXEL_DEEP;
+      share[i] = dealt[cls]++ % kGroupSplit;
+    }
+  }
+  int cur = 0;  // the stream being planned
+  auto launch = [&](int kind, int a, int b, int cls) -> GLaunch & {
+    const int branch = cls * kGroupSplit + share[cur];
     for (GLaunch &x : L)
-      if (x.kind == kind && x.a == a && x.b == b) return x;
+      if (x.kind == kind && x.a == a && x.b == b && x.branch == branch) return x;
     GLaunch x;
     x.kind = kind, x.a = a, x.b = b, x.branch = branch;
     L.push_back(x);
@@ -318,6 +337,7 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
   };
   const int64_t sms = sm_count();
   for (int i = 0; i < (int)in.size(); ++i) {
+    cur = i;
     const GStreamIn &x = in[i];
     const int64_t hw = (int64_t)x.H * x.W;
     const int d = x.depth;

@@ -41,8 +41,12 @@ enum GroupKind : int {
   GK_COUNT         // serving window: a camera's new leaf bitsets into its ring and counts
 };
 
-// Branches of the batch graph a grouped launch belongs to.
+// Classes of streams; each class's streams are dealt, largest first, to
+// kGroupSplit branches of the batch graph (so one half's classification runs
+// beside the other half's builds): branch = class * kGroupSplit + share.
 enum GroupBranch : int { GB_FRAME = 0, GB_BLOCK, GB_PIXEL, GB_PIXEL_DEEP, GB_COUNT };
+constexpr int kGroupSplit = 2;
+constexpr int kGroupBranches = GB_COUNT * kGroupSplit;
 
 struct GLaunch {
   int kind = 0, a = 0, b = 0, branch = 0;
