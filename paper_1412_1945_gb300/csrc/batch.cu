@@ -600,15 +600,16 @@ static ocq_status enqueue_grouped(ocq_batch *b, cudaStream_t cs) {
   const int nfb = std::min<int>((int)b->gfallback.size(), 8);
   const int NB = kGroupBranches + nfb;
   rc = ensure_side_streams(b, NB);
-  // whole-frame occupancy is ORed into zeroed scratch (before the branches fork)
-  for (size_t s = 0; s < b->hs.size() && rc == OCQ_OK; ++s) {
-    const BStream &h = b->hs[s];
-    if (h.kind != OCQ_REGION_FRAME || !h.occ) continue;
-    if (std::find(b->gfallback.begin(), b->gfallback.end(), (int)s) != b->gfallback.end()) continue;
-    rc = cuda_status(cudaMemsetAsync(h.occ, 0, (size_t)h.N * h.wpr * 4, cs), "clear occupancy");
-  }
   if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(b->fork, cs), "fork");
   for (int i = 0; i < NB && rc == OCQ_OK; ++i) rc = cuda_status(cudaStreamWaitEvent(b->side[i], b->fork, 0), "fork wait");
+  // whole-frame occupancy is ORed into zeroed scratch: cleared on the branch
+  // that builds the stream
+  for (const GLaunch &L : b->glaunch) {
+    if (L.kind != GK_OCC) continue;
+    for (const GSeg &g : L.segs)
+      if (rc == OCQ_OK)
+        rc = cuda_status(cudaMemsetAsync(g.occ, 0, (size_t)g.N * wpr32(L.a) * 4, b->side[L.branch]), "clear occupancy");
+  }
   for (const GLaunch &L : b->glaunch) {
     if (rc != OCQ_OK) break;
     rc = grouped_launch(L, b->side[L.branch]);

@@ -291,6 +291,7 @@ static int64_t resident(const KInfo &k, size_t smem) {
 
 static int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+
 ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &out, std::vector<int> &fallback) {
   out.clear();
   fallback.clear();
@@ -451,6 +452,8 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
         case GK_PIX_LIST: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 4), cap)); break;
         default: break;  // GK_OCC, GK_MERGE, GK_PIX_MG: set above
       }
+    }
+    for (GSeg &s : x.segs) {
       s.cta0 = cta;
       cta += s.vg;
     }
