@@ -1067,7 +1067,7 @@ def profile_case(args):
         out = []
         for region, block, depth in runs:
             r = {"region": region, "block": block, "depth": depth}
-            for form in (0, 1):
+            for form in range(O.ocq_tune_count(kb)):
                 O.ocq_tune_select(kb, form)
                 r[f"build_ms_form{form}"] = timed(
                     lambda: O.ocq_build_model(tr, N, H, W, region, block, depth, 10, st).free())

@@ -442,14 +442,24 @@ void ocq_server_destroy(ocq_server *server);
  *                            each location as a 16 B list and no leaf bitset (export
  *                            expands it into the bitset layout); 0 the bitset rows
  *                            plus that list; params = {variant, 0, ...}
- *   OCQ_TUNE_BUILD_BLOCK     block build with b <= 16 and N <= 255: 1 (default)
- *                            warps over 16 x 16 pixel tiles (four 8 x 8 or one
- *                            16 x 16 region, 8 pixels per lane; direct leaf tables
- *                            at depth <= 3, two-level prefix tables deeper) where b
- *                            is 16 (depth 2-5) or 8 (depth 2-4), W % 8 == 0 and
- *                            the frames are 8-byte aligned, else one warp per
- *                            region; 0 one warp per region always; params =
- *                            {variant, 0, ...}
+ *   OCQ_TUNE_BUILD_BLOCK     block build with b <= 16 and N <= 255.  Forms for b
+ *                            in {8, 16}, depth 2-5, W % 8 == 0 and 8-byte aligned
+ *                            frames: warps over 16 x 16 pixel tiles (four 8 x 8 or
+ *                            one 16 x 16 region, 8 pixels per lane; direct leaf
+ *                            tables at depth <= 3, two-level prefix tables
+ *                            deeper), or the N frames split over the 8 warps of a
+ *                            CTA (shared u8 counters per region, a leaf bitset per
+ *                            warp for the frame it counts); every other block
+ *                            build runs one warp per region.  1 (default) picks
+ *                            by shape and size: frames split for 16 x 16 at depth
+ *                            5, 8 x 8 at depth 4, 8 x 8 at depth 5 up to 16384
+ *                            regions and any frame of fewer than 1024 tiles;
+ *                            tiles for depth <= 3 and 16 x 16 at depth 4; one warp
+ *                            per region for 8 x 8 at depth 5 above 16384
+ *                            regions.  0 one warp per region always; 2 frames
+ *                            split wherever they apply; 3 tiles wherever they
+ *                            apply (8 x 8 at depth 5: one warp per region);
+ *                            params = {variant, 0, ...}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5

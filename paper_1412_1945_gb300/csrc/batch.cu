@@ -630,6 +630,7 @@ static ocq_status enqueue_grouped(ocq_batch *b, cudaStream_t cs) {
 
 static ocq_status capture(ocq_batch *b) {
   free_graph(b);
+  SharedGpuScope shared;  // the streams' builds run beside one another
   if (b->mode == OCQ_BATCH_GROUPED) {  // plan (device tables, kernel attributes) before capturing
     ocq_status rp = plan_grouped(b);
     if (rp != OCQ_OK) return rp;

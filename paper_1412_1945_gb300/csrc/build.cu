@@ -88,6 +88,17 @@ __global__ void __launch_bounds__(BlockTileCfg<D, B>::WPC * 32, BlockTileCfg<D, 
                                   (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), ntiles, nw, wsm);
 }
 
+template <int D, int B>
+__global__ void __launch_bounds__(256, BlockFsCfg<D, B>::MINB) build_block_fs_kernel(const uint8_t *__restrict__ frames, int N, int H, int W,
+                                                               int bw, uint32_t T, uint32_t *__restrict__ model,
+                                                               int64_t ngroups) {
+  extern __shared__ __align__(16) uint32_t fs_smem[];
+  for (int i = threadIdx.x; i < BlockFsCfg<D, B>::SMEM / 16; i += blockDim.x)
+    reinterpret_cast<uint4 *>(fs_smem)[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  build_block_fs_body<D, B>(frames, N, H, W, bw, T, model, ngroups, blockIdx.x, gridDim.x, fs_smem);
+}
+
 template <int D, int KM, bool GRP>
 __global__ void __launch_bounds__(128) build_pixel_mg_kernel(const uint8_t *__restrict__ frames, int N, int64_t hw,
                                                              uint32_t T, uint32_t *__restrict__ model, int group,
@@ -628,23 +639,83 @@ static ocq_status launch_block_warp_ppl(const uint8_t *frames, int N, ocq_model 
   return cuda_status(cudaGetLastError(), "build_block_warp_kernel");
 }
 
-// Warp tiles of 16 x 16 pixels for 8 x 8 and 16 x 16 blocks (depth 2-5,
-// N <= 255, W % 8 == 0, 8-byte aligned frames, frame offsets within 32 bits).
-// 8 x 8 blocks at depth 5 stay with one warp per region: four regions' prefix
-// pools leave 12 warps per SM and measured slower there (30 frames of 1080p:
-// 0.27 / 0.32 ms against 0.25 / 0.29 ms), while the tiles win everywhere else
-// (8 x 8 at depth 3 and 4: 1.5x and 1.3x; 16 x 16 at depth 4 and 5: 4x and 3x).
-static int g_block_form = 1;  // 1: warp tiles where they apply; 0: one warp per region
-bool block_tile_ok(int N, int H, int W, int b, int depth, const void *frames) {
-  return g_block_form == 1 && (b == 16 || (b == 8 && depth <= 4)) && depth >= 2 && depth <= 5 && N <= 255 &&
-         W % 8 == 0 && (reinterpret_cast<uintptr_t>(frames) & 7) == 0 && (int64_t)H * W * 3 <= (int64_t)UINT32_MAX;
+// Block builds for b in {8, 16} (depth 2-5, N <= 255, W % 8 == 0, 8-byte
+// aligned frames, frame offsets within 32 bits): warps over 16 x 16 pixel
+// tiles, or the frames split over the 8 warps of a CTA.  Form 1 (the default)
+// picks by shape and size, from CUDA-event times of 30-frame builds at
+// 320x240 .. 1920x1080 (cluster and sway scenes):
+//   * frames split: 16 x 16 at depth 5 (1080p 0.19 against 0.25 ms for the
+//     tiles), 8 x 8 at depth 4 (1080p 0.15 against 0.17 ms), 8 x 8 at depth 5
+//     up to 16384 regions (720p 0.13 against 0.145 ms one warp per region;
+//     at 1080p one warp per region is 0.22 against 0.27 ms on the cluster
+//     scene), and every frame of fewer than 1024 tiles (320x240: 1.2-2.5x),
+//     where the tiles leave most SMs idle;
+//   * warp tiles: depth <= 3, and 16 x 16 at depth 4 (1080p 0.12 against
+//     0.14 ms);
+//   * one warp per region: 8 x 8 at depth 5 above 16384 regions.
+// Where other streams' kernels share the GPU (the batched forms), form 1
+// takes the forms that do the least work per region instead: tiles, and one
+// warp per region for 8 x 8 at depth 5 (64-stream mix, 8 x 8 depth 4 class:
+// 0.32 against 0.36 ms in the graph of branches).
+// Forms 0, 2 and 3 force one warp per region, frames split and tiles.
+static int g_block_form = 1;
+static thread_local bool t_shared_gpu = false;
+SharedGpuScope::SharedGpuScope() : prev(t_shared_gpu) { t_shared_gpu = true; }
+SharedGpuScope::~SharedGpuScope() { t_shared_gpu = prev; }
+static bool block_shape_ok(int N, int H, int W, int b, int depth, const void *frames) {
+  return (b == 8 || b == 16) && depth >= 2 && depth <= 5 && N <= 255 && W % 8 == 0 &&
+         (reinterpret_cast<uintptr_t>(frames) & 7) == 0 && (int64_t)H * W * 3 <= (int64_t)UINT32_MAX;
 }
-int block_build_form_count() { return 2; }
+enum BlockBuildKind { BB_WARP = 0, BB_TILE, BB_FS };
+static BlockBuildKind block_build_kind(int N, int H, int W, int b, int depth, const void *frames) {
+  if (g_block_form == 0 || !block_shape_ok(N, H, W, b, depth, frames)) return BB_WARP;
+  if (g_block_form == 2) return BB_FS;
+  if (g_block_form == 3 || t_shared_gpu) return b == 8 && depth == 5 ? BB_WARP : BB_TILE;
+  const int64_t tiles = (int64_t)((H + 15) / 16) * ((W + 15) / 16);
+  const int64_t regions = (int64_t)((H + b - 1) / b) * ((W + b - 1) / b);
+  if (tiles < 1024 || (b == 16 && depth == 5) || (b == 8 && depth == 4)) return BB_FS;
+  if (b == 8 && depth == 5) return regions <= 16384 ? BB_FS : BB_WARP;
+  return BB_TILE;
+}
+bool block_tile_ok(int N, int H, int W, int b, int depth, const void *frames) {
+  return block_build_kind(N, H, W, b, depth, frames) == BB_TILE;
+}
+bool block_fs_ok(int N, int H, int W, int b, int depth, const void *frames) {
+  return block_build_kind(N, H, W, b, depth, frames) == BB_FS;
+}
+int block_build_form_count() { return 4; }
 int block_build_form_selected() { return g_block_form; }
 bool block_build_form_select(int v) {
-  if (v < 0 || v > 1) return false;
+  if (v < 0 || v > 3) return false;
   g_block_form = v;
   return true;
+}
+
+template <int D, int B>
+static ocq_status launch_block_fs(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  using C = BlockFsCfg<D, B>;
+  auto kern = build_block_fs_kernel<D, B>;
+  static int cap = 0;
+  if (!cap) {
+    if (C::SMEM > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, C::SMEM);
+    cap = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+  }
+  const int bw = (m->W + m->block - 1) / m->block;
+  const int64_t ngroups = C::TILE ? (int64_t)((m->H + 15) / 16) * ((m->W + 15) / 16)
+                                  : (int64_t)((m->H + 7) / 8) * (m->W / 8);
+  kern<<<(unsigned)(ngroups < cap ? ngroups : cap), 256, C::SMEM, st>>>(frames, N, m->H, m->W, bw, (uint32_t)m->T,
+                                                                        m->bits, ngroups);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "build_block_fs_kernel");
+}
+
+template <int D>
+static ocq_status launch_block_fs_b(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  return m->block == 8 ? launch_block_fs<D, 8>(frames, N, m, st) : launch_block_fs<D, 16>(frames, N, m, st);
 }
 
 template <int D, int B>
@@ -986,6 +1057,14 @@ ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t
   const int d = m->depth;
   m->kept_len = 0;  // until a candidate build writes the kept-leaf index
   if (m->kind == OCQ_REGION_FRAME || (m->kind == OCQ_REGION_BLOCK && d >= 6)) return build_dense(frames, N, m, st);
+  if (m->kind == OCQ_REGION_BLOCK && block_fs_ok(N, m->H, m->W, m->block, d, frames)) {
+    switch (d) {
+      case 2: return launch_block_fs_b<2>(frames, N, m, st);
+      case 3: return launch_block_fs_b<3>(frames, N, m, st);
+      case 4: return launch_block_fs_b<4>(frames, N, m, st);
+      default: return launch_block_fs_b<5>(frames, N, m, st);
+    }
+  }
   if (m->kind == OCQ_REGION_BLOCK && block_tile_ok(N, m->H, m->W, m->block, d, frames)) {
     switch (d) {
       case 2: return launch_block_tile_b<2>(frames, N, m, st);

@@ -801,6 +801,219 @@ __device__ __forceinline__ void build_block_tile_body(const uint8_t *__restrict_
   }
 }
 
+// ---- block regions, frames split over the warps of a CTA --------------------
+// Sec. 3 regions with the N training frames dealt to the 8 warps of a CTA, so
+// that a region's frames are counted in parallel (and a frame of few regions
+// still fills the GPU).  The CTA's shared memory holds, per region of its
+// group: u8 leaf counters (frame counts, N <= 255), the model row being built
+// (a leaf's bit is set when its count reaches T) and, at depth 5, one bit per
+// 16 counters marking the counters to clear; per warp and region: the leaf
+// bitset of the frame it is counting (the per-frame "stored once" of Alg. 1,
+// so that a frame adds at most one to a leaf's count, Alg. 2).
+// Groups: 16 x 16 pixel tiles (one 16 x 16 or four 8 x 8 regions; a warp takes
+// one frame of the tile, 8 pixels per lane as in the warp tiles) or, for 8 x 8
+// regions at depth 5, single regions (a warp takes one frame of the region,
+// 2 pixels per lane), which keeps the counters at 32 KB per CTA.
+template <int D, int B>
+struct BlockFsCfg {
+  static constexpr bool TILE = !(B == 8 && D == 5);
+  static constexpr int RPT = TILE ? (16 / B) * (16 / B) : 1;  // regions per group
+  static constexpr int NC = 1 << (3 * D);
+  static constexpr int CW = NC / 4;                 // counter words per region
+  static constexpr int BW = NC >= 32 ? NC / 32 : 1;  // model row words (leaf bitset)
+  static constexpr bool TOUCH = D >= 5;              // clear only the touched counters
+  static constexpr int TW = TOUCH ? NC / 512 : 0;    // touch words per region
+  static constexpr int WPC = 8;
+  static constexpr bool FILTER = false;
+  static constexpr int CNT_OFF = 0;
+  static constexpr int MB_OFF = RPT * CW;
+  static constexpr int TOUCH_OFF = MB_OFF + RPT * BW;
+  static constexpr int FB_OFF = TOUCH_OFF + RPT * TW;
+  static constexpr int WORDS = FB_OFF + WPC * RPT * BW;
+  static constexpr int SMEM = ((WORDS * 4) + 15) & ~15;
+  static constexpr int MINB = D >= 5 ? 3 : 4;
+  static constexpr int WPR = D == 1 ? 1 : 1 << (3 * D - 5);
+  static_assert(WPR == BW, "model rows are one bit per leaf");
+};
+
+// Counts one masked leaf code q of the warp's current frame: sets its bit in
+// the frame bitset fb; the first pixel of the frame with this leaf adds one to
+// its counter, marks the counter group touched and, when the count reaches T,
+// sets the leaf's bit in the model row image mb.  A plain read of fb first
+// keeps the lanes of a uniform patch from queueing on one atomic (a stale
+// read only costs the atomic, whose result decides).
+template <int D, int B>
+__device__ __forceinline__ void fs_count_leaf(uint32_t q, uint32_t *fb, uint32_t *cnt, uint32_t *mb,
+                                              uint32_t *touch, uint32_t T) {
+  const uint32_t bit = 1u << (q & 31u);
+  if (BlockFsCfg<D, B>::FILTER && (reinterpret_cast<volatile uint32_t *>(fb)[q >> 5] & bit)) return;
+  const uint32_t old = atomicOr(fb + (q >> 5), bit);
+  if (!(old & bit)) {
+    const uint32_t sh = (q & 3u) << 3;
+    const uint32_t c = (atomicAdd(cnt + (q >> 2), 1u << sh) >> sh) & 0xFFu;
+    if constexpr (BlockFsCfg<D, B>::TOUCH)
+      if (c == 0u) atomicOr(touch + (q >> 9), 1u << ((q >> 4) & 31u));
+    if (c + 1u == T) atomicOr(mb + (q >> 5), bit);
+  }
+}
+
+// CTA vb of vg handles groups vb, vb + vg, ... < ngroups (tiles row-major over
+// ceil(H/16) x ceil(W/16), or 8 x 8 regions row-major).  Needs b in {8, 16},
+// W % 8 == 0, 8-byte aligned frames, 1 <= T <= N <= 255, H*W*3 < 2^32, and
+// blockDim.x == 256.  sm: BlockFsCfg::SMEM bytes, zero on entry and on return.
+template <int D, int B>
+__device__ __forceinline__ void build_block_fs_body(const uint8_t *__restrict__ frames, int N, int H, int W, int bw,
+                                                    uint32_t T, uint32_t *__restrict__ model, int64_t ngroups,
+                                                    int64_t vb, int64_t vg, uint32_t *sm) {
+  using C = BlockFsCfg<D, B>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t fstride = (int64_t)H * W * 3;
+  uint32_t *cnt = sm + C::CNT_OFF, *mb = sm + C::MB_OFF, *touch = sm + C::TOUCH_OFF;
+  // lane geometry within a group
+  int ly, lx, ri;
+  if constexpr (C::TILE) {
+    ly = lane >> 1, lx = (lane & 1) * 8;
+    ri = B == 8 ? (((lane >> 4) << 1) | (lane & 1)) : 0;
+  } else {
+    ly = lane >> 2, lx = (lane & 3) * 2;
+    ri = 0;
+  }
+  uint32_t *fb = sm + C::FB_OFF + (warp * C::RPT + ri) * C::BW;
+  uint32_t *cr = cnt + ri * C::CW, *mr = mb + ri * C::BW, *tr = touch + ri * C::TW;
+  const int gx = C::TILE ? (W + 15) >> 4 : bw;
+  constexpr int GS = C::TILE ? 16 : 8;  // group side in pixels
+  constexpr int NW = C::TILE ? 6 : 2;   // words a lane loads per frame
+  // Where the lane's pixels of group g start (tile lanes read 24 bytes at an
+  // 8-byte boundary; region lanes read the two words holding bytes 6j .. 6j + 5
+  // of their row, j = lane & 3), and whether they lie in the frame.
+  struct Geo {
+    const uint8_t *src;
+    uint32_t sel;
+    bool active;
+  };
+  auto geo = [&](int64_t g) {
+    Geo o{frames, 0u, false};
+    if (g < ngroups) {
+      const int gy = (int)(g / gx), gxi = (int)(g - (int64_t)gy * gx);
+      const int y = gy * GS + ly, x = gxi * GS + lx;
+      o.active = y < H && x < W;
+      const int64_t pofs = ((int64_t)y * W + x) * 3;
+      o.src = frames + (C::TILE ? pofs : (pofs & ~(int64_t)3));
+      o.sel = C::TILE ? 0u : (uint32_t)(pofs & 3);
+    }
+    return o;
+  };
+  auto load = [&](uint32_t (&v)[NW], const Geo &o, int f) {
+    if (o.active && f < N) {
+      const uint8_t *s = o.src + (int64_t)f * fstride;
+      if constexpr (C::TILE) {
+        const uint2 a = __ldg(reinterpret_cast<const uint2 *>(s)), b2 = __ldg(reinterpret_cast<const uint2 *>(s) + 1),
+                    c2 = __ldg(reinterpret_cast<const uint2 *>(s) + 2);
+        v[0] = a.x, v[1] = a.y, v[2] = b2.x, v[3] = b2.y, v[4] = c2.x, v[5] = c2.y;
+      } else {
+        v[0] = __ldg(reinterpret_cast<const uint32_t *>(s));
+        v[1] = __ldg(reinterpret_cast<const uint32_t *>(s) + 1);
+      }
+    }
+  };
+  auto count = [&](const uint32_t (&v)[NW], const Geo &o) {
+    if (o.active) {
+      uint32_t m[6];
+#pragma unroll
+      for (int i = 0; i < NW; ++i) m[i] = (v[i] >> (8 - D)) & byte_mask(D);
+      if constexpr (C::TILE) {
+        uint32_t q[8];
+        static_for<0, 8>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          q[k] = planar_dp<D>(oct_pixel<k>(m));
+        });
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (k == 0 || q[k] != q[k - 1]) fs_count_leaf<D, B>(q[k], fb, cr, mr, tr, T);
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < 8; ++k) fb[q[k] >> 5] = 0u;
+      } else {
+        const uint32_t s0 = o.sel | ((o.sel + 1) << 4) | ((o.sel + 2) << 8), s1 = s0 + 0x333u;
+        const uint32_t q0 = planar_dp<D>(__byte_perm(m[0], m[1], s0));
+        const uint32_t q1 = planar_dp<D>(__byte_perm(m[0], m[1], s1));
+        fs_count_leaf<D, B>(q0, fb, cr, mr, tr, T);
+        if (q1 != q0) fs_count_leaf<D, B>(q1, fb, cr, mr, tr, T);
+        __syncwarp();
+        fb[q0 >> 5] = 0u;
+        fb[q1 >> 5] = 0u;
+      }
+    } else {
+      __syncwarp();
+    }
+    __syncwarp();
+  };
+  // Emits group g's model rows (a region is absent when its top-left pixel
+  // lies outside the frame) and clears its counters.
+  auto emit = [&](int64_t g) {
+    const int gy = (int)(g / gx), gxi = (int)(g - (int64_t)gy * gx);
+#pragma unroll
+    for (int r = 0; r < C::RPT; ++r) {
+      const int ry = gy * GS + (C::TILE && B == 8 ? (r >> 1) * 8 : 0);
+      const int rx = gxi * GS + (C::TILE && B == 8 ? (r & 1) * 8 : 0);
+      uint32_t *row = ry < H && rx < W ? model + ((int64_t)(ry / B) * bw + rx / B) * C::WPR : nullptr;
+      uint32_t *m2 = mb + r * C::BW;
+      if constexpr (C::BW >= 4) {
+        for (int i = threadIdx.x; i < C::BW / 4; i += blockDim.x) {
+          uint4 *s4 = reinterpret_cast<uint4 *>(m2) + i;
+          if (row) reinterpret_cast<uint4 *>(row)[i] = *s4;
+          *s4 = make_uint4(0, 0, 0, 0);
+        }
+      } else {
+        for (int i = threadIdx.x; i < C::BW; i += blockDim.x) {
+          if (row) row[i] = m2[i];
+          m2[i] = 0u;
+        }
+      }
+      uint32_t *c2 = cnt + r * C::CW;
+      if constexpr (C::TOUCH) {
+        // thread t clears the touched ones of counter groups 8t .. 8t + 7
+        uint32_t *t2 = touch + r * C::TW;
+        for (int t = threadIdx.x; t < C::CW / 32; t += blockDim.x) {
+          uint32_t tb = (t2[t >> 2] >> ((t & 3) << 3)) & 0xFFu;
+          while (tb) {
+            const int i = __ffs(tb) - 1;
+            tb &= tb - 1u;
+            reinterpret_cast<uint4 *>(c2)[8 * t + i] = make_uint4(0, 0, 0, 0);
+          }
+        }
+        __syncthreads();  // every thread has read the touch bits
+        for (int t = threadIdx.x; t < C::TW; t += blockDim.x) t2[t] = 0u;
+      } else {
+        for (int i = threadIdx.x; i < C::CW / 4; i += blockDim.x)
+          reinterpret_cast<uint4 *>(c2)[i] = make_uint4(0, 0, 0, 0);
+      }
+    }
+  };
+  // The warp's frames of a group are f = warp + 8 j; frame f + 8 is loaded
+  // while f is counted, and the first frame of the next group while the
+  // current group's rows are emitted.
+  int64_t g = vb;
+  Geo cur = geo(g);
+  uint32_t v[NW];
+  load(v, cur, warp);
+  for (; g < ngroups; g += vg) {
+    for (int f = warp; f < N; f += C::WPC) {
+      uint32_t nx[NW];
+      load(nx, cur, f + C::WPC);
+      count(v, cur);
+#pragma unroll
+      for (int i = 0; i < NW; ++i) v[i] = nx[i];
+    }
+    const Geo next = geo(g + vg);
+    load(v, next, warp);
+    __syncthreads();
+    emit(g);
+    __syncthreads();
+    cur = next;
+  }
+}
+
 // ---- pixel regions, depth <= 3 -------------------------------------------------
 // Thread t of a 128-thread CTA owns pixel location p and a private column of
 // counter words cnt[k * 128 + t] (4 u8 or 2 u16 counters per word).

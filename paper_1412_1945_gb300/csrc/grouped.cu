@@ -86,6 +86,17 @@ __global__ void __launch_bounds__(256) g_block_warp(const GSeg *__restrict__ g, 
                                 vb * 8 + (threadIdx.x >> 5), s.units, s.vg * 8, tab);
 }
 
+template <int D, int B>
+__global__ void __launch_bounds__(256, BlockFsCfg<D, B>::MINB) g_block_fs(const GSeg *__restrict__ g, int n) {
+  extern __shared__ __align__(16) uint32_t gf_smem[];
+  for (int i = threadIdx.x; i < BlockFsCfg<D, B>::SMEM / 16; i += blockDim.x)
+    reinterpret_cast<uint4 *>(gf_smem)[i] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  build_block_fs_body<D, B>(s.in, s.N, s.H, s.W, s.bw, (uint32_t)s.T, s.model, s.units, vb, s.vg, gf_smem);
+}
+
 // items u = chunk * tiles + tile over frames [chunk * fchunk, + fchunk)
 template <int D>
 __global__ void __launch_bounds__(256) g_block_tb(const GSeg *__restrict__ g, int n) {
@@ -226,6 +237,12 @@ static KInfo kinfo_d(int kind, int b) {
           k.smem = (size_t)BlockTileCfg<D, 8>::WPC * BlockTileCfg<D, 8>::WARP_SMEM;
       }
       break;
+    case GK_BLOCK_FS:
+      if constexpr (D >= 2 && D <= 5) {
+        if (b == 16) k.fn = g_block_fs<D, 16>, k.smem = BlockFsCfg<D, 16>::SMEM;
+        if (b == 8) k.fn = g_block_fs<D, 8>, k.smem = BlockFsCfg<D, 8>::SMEM;
+      }
+      break;
     case GK_BLOCK_WARP:
       if constexpr (D <= 5) {
         k.smem = (size_t)8 * WarpTableCfg<D>::S * 4;
@@ -361,14 +378,18 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
       }
     } else if (x.kind == OCQ_REGION_BLOCK) {
       const bool cls_ok = x.F == 0 || (x.block % 4 == 0 && x.W % 4 == 0 && (tm & 3) == 0);
-      const bool tile = block_tile_ok(x.N, x.H, x.W, x.block, d, x.train);
-      const bool warp = !tile && d <= 5 && block_warp_ok(x.N, x.H, x.W, x.block);
-      if (!cls_ok || (!tile && !warp)) {
+      const bool fs = block_fs_ok(x.N, x.H, x.W, x.block, d, x.train);
+      const bool tile = !fs && block_tile_ok(x.N, x.H, x.W, x.block, d, x.train);
+      const bool warp = !fs && !tile && d <= 5 && block_warp_ok(x.N, x.H, x.W, x.block);
+      if (!cls_ok || (!fs && !tile && !warp)) {
         fallback.push_back(i);
         continue;
       }
       GSeg bld = base(x, x.train);
-      if (tile) {
+      if (fs) {
+        bld.units = x.block == 8 && d == 5 ? cdiv64(x.H, 8) * (x.W / 8) : cdiv64(x.H, 16) * cdiv64(x.W, 16);
+        launch(GK_BLOCK_FS, d, x.block, GB_BLOCK).segs.push_back(bld);
+      } else if (tile) {
         bld.units = cdiv64(x.H, 16) * cdiv64(x.W, 16);
         launch(GK_BLOCK_TILE, d, x.block, GB_BLOCK).segs.push_back(bld);
       } else {
@@ -445,6 +466,7 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
       switch (x.kind) {
         case GK_CLS_FRAME: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 16 * 256), cap)); break;
         case GK_BLOCK_TILE: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, x.threads / 32), cap)); break;
+        case GK_BLOCK_FS: s.vg = std::max<int64_t>(1, std::min<int64_t>(s.units, cap)); break;
         case GK_BLOCK_WARP:
         case GK_BLOCK_TB: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 8), cap)); break;
         case GK_PIX_WS_BUILD: s.vg = std::max<int64_t>(1, std::min<int64_t>(s.units, cap)); break;

@@ -202,6 +202,17 @@ bool block_warp_ok(int N, int H, int W, int b);
 // Block regions that the 16 x 16 warp-tile build handles (b in {8, 16}, ...),
 // and its selection (1: used where it applies; 0: one warp per region).
 bool block_tile_ok(int N, int H, int W, int b, int depth, const void *frames);
+bool block_fs_ok(int N, int H, int W, int b, int depth, const void *frames);
+// While one is alive on this thread, the default block build form picks for
+// work per region rather than for filling the GPU (the batched forms, where
+// other streams' kernels run beside it).
+struct SharedGpuScope {
+  SharedGpuScope();
+  ~SharedGpuScope();
+  SharedGpuScope(const SharedGpuScope &) = delete;
+  SharedGpuScope &operator=(const SharedGpuScope &) = delete;
+  bool prev;
+};
 int block_build_form_count();
 int block_build_form_selected();
 bool block_build_form_select(int v);

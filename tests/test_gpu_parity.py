@@ -353,7 +353,9 @@ def test_block_build_tiles(ocq, torch, b, d):
     blocks, hashed tables otherwise).  Widths with a half tile at the right
     edge, heights with ragged blocks at the bottom; scene content, then uniform
     noise (more distinct leaves per region than a hashed table takes, so the
-    region is recounted by the chunked passes), and both build forms."""
+    region is recounted by the chunked passes), and every build form (one
+    warp per region, the default choice, frames split over a CTA's warps,
+    warp tiles)."""
     O = ocq.ocq
     kern = O.OCQ_TUNE_BUILD_BLOCK
     saved = O.ocq_tune_selected(kern)
@@ -366,7 +368,7 @@ def test_block_build_tiles(ocq, torch, b, d):
             for train in (frames[:12], noise):
                 for T in (1, 4, 12):
                     ow, om = oracle.run(train, d, T, BLOCK, b, frames[12:])
-                    for form in (1, 0):
+                    for form in range(O.ocq_tune_count(kern)):
                         O.ocq_tune_select(kern, form)
                         words, mask = gpu_model_and_mask(ocq, torch, train, frames[12:], d, T, BLOCK, b)
                         assert (words == ow).all(), (H, W, T, form)
@@ -377,18 +379,26 @@ def test_block_build_tiles(ocq, torch, b, d):
 
 @pytest.mark.parametrize("N", [254, 255, 256])
 def test_block_build_frame_count_limits(ocq, torch, N):
-    """The warp tables keep the last frame and the count in 8 bits each:
+    """The warp tables and the frame-split counters keep counts in 8 bits:
     N = 255 is their limit, N = 256 goes to the CTA-per-region kernel."""
+    O = ocq.ocq
+    kern = O.OCQ_TUNE_BUILD_BLOCK
+    saved = O.ocq_tune_selected(kern)
     g = np.random.default_rng(N)
     palette = g.integers(0, 256, size=(5, 3), dtype=np.uint8)
-    for W in (20, 24):  # one warp per region; 16 x 16 warp tiles (W % 8 == 0)
-        train = palette[g.integers(0, 5, size=(N, 12, W))]
-        test = palette[g.integers(0, 5, size=(2, 12, W))]
-        for d in (3, 4, 5):
-            for T in (1, N // 5, N // 2, N):
-                words, mask = gpu_model_and_mask(ocq, torch, train, test, d, T, BLOCK, 8)
-                ow, om = oracle.run(train, d, T, BLOCK, 8, test)
-                assert (words == ow).all() and (mask == om).all(), (W, d, T)
+    try:
+        for W in (20, 24):  # one warp per region; tiles or frames split (W % 8 == 0)
+            train = palette[g.integers(0, 5, size=(N, 12, W))]
+            test = palette[g.integers(0, 5, size=(2, 12, W))]
+            for d in (3, 4, 5):
+                for T in (1, N // 5, N // 2, N):
+                    ow, om = oracle.run(train, d, T, BLOCK, 8, test)
+                    for form in range(O.ocq_tune_count(kern)):
+                        O.ocq_tune_select(kern, form)
+                        words, mask = gpu_model_and_mask(ocq, torch, train, test, d, T, BLOCK, 8)
+                        assert (words == ow).all() and (mask == om).all(), (W, d, T, form)
+    finally:
+        O.ocq_tune_select(kern, saved)
 
 
 @pytest.mark.parametrize("d", [4, 5, 6])
