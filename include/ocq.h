@@ -372,7 +372,16 @@ ocq_status ocq_server_submit(ocq_server *server, int camera, const uint8_t *fram
  * one the window semantics give, whatever the grouping.  Non-blocking. */
 ocq_status ocq_server_submit_many(ocq_server *server, int n, const int *cameras, const uint8_t *const *frames,
                                   uint8_t *const *masks, const uint64_t *tags);
-/* Up to max completed frames, oldest first; *n receives the count. */
+/* Batching window of the ticks: frames of cameras served in ticks wait on the
+ * host until the oldest of them has waited `seconds` (checked at every submit
+ * and poll; release, snapshot and sync run them at once), so that a tick
+ * classifies several frames of a camera against one read of its model (a
+ * per-pixel model row is 16-64 B per pixel against a frame's 3 B).  0 (the
+ * default) runs them at the next submit.  seconds in [0, 1]; a caller that
+ * sets it polls at least that often.  No counterpart in the paper. */
+ocq_status ocq_server_set_batch_delay(ocq_server *server, double seconds);
+/* Up to max completed frames, oldest first; *n receives the count (runs the
+ * held frames whose batching window ended). */
 ocq_status ocq_server_poll(ocq_server *server, ocq_completion *out, int max, int *n);
 /* Waits for the camera's frames, frees its window and model, returns its budget. */
 ocq_status ocq_server_release(ocq_server *server, int camera);

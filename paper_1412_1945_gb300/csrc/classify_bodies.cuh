@@ -155,11 +155,15 @@ __device__ __forceinline__ void classify_pixel_tb_body(const uint8_t *__restrict
 // Frames [fb, fe) only (fe < 0: all F), so a launch can split the frames of a
 // small frame over more warps.  The loads of the next PF frames are in flight
 // while the current PF are looked up (two register buffers).
+// ftab/mtab (device tables, or null): frame f and its mask at ftab[f] and
+// mtab[f] instead of frames + f*H*W*3 and mask + f*H*W (frames gathered from
+// several buffers, as a serving tick's).
 template <int D, int PF>
 __device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict__ frames, int F, int H, int W,
                                                        int b, int bw, int nseg, const uint32_t *model,
                                                        uint8_t *__restrict__ mask, int64_t t, int fb = 0,
-                                                       int fe = -1) {
+                                                       int fe = -1, const uint8_t *const *ftab = nullptr,
+                                                       uint8_t *const *mtab = nullptr) {
   constexpr int64_t WPR = D == 1 ? 1 : (int64_t)1 << (3 * D - 5);
   if (fe < 0 || fe > F) fe = F;
   const int lane = threadIdx.x & 31;
@@ -174,11 +178,13 @@ __device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict
   const uint8_t *row = reinterpret_cast<const uint8_t *>(model + ((int64_t)br * bw + x / b) * WPR);
   const uint8_t *src = frames + pq * 3;
   uint8_t *dst = mask + pq;
+  auto fsrc = [&](int f) { return ftab ? ftab[f] + pq * 3 : src + (int64_t)f * hw * 3; };
+  auto fdst = [&](int f) { return mtab ? mtab[f] + pq : dst + (int64_t)f * hw; };
   auto load = [&](uint32_t (&w)[PF][3], int f0) {
 #pragma unroll
     for (int j = 0; j < PF; ++j)
       if (f0 + j < fe) {
-        const uint8_t *s = src + (int64_t)(f0 + j) * hw * 3;
+        const uint8_t *s = fsrc(f0 + j);
         w[j][0] = ld_stream4(s), w[j][1] = ld_stream4(s + 4), w[j][2] = ld_stream4(s + 8);
       }
   };
@@ -195,7 +201,7 @@ __device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict
         const uint32_t c = planar_from_masked<D>(quad_pixel<kk>(m));
         bg[kk] = (uint32_t)row[c >> 3] >> (c & 7);
       });
-      st_stream4(dst + (int64_t)(f0 + j) * hw, pack_mask4(bg[0], bg[1], bg[2], bg[3]));
+      st_stream4(fdst(f0 + j), pack_mask4(bg[0], bg[1], bg[2], bg[3]));
     }
   };
   uint32_t wa[PF][3], wb[PF][3];
@@ -239,10 +245,12 @@ __device__ __forceinline__ bool list_holds(const uint32_t (&l)[KL], uint32_t t) 
 // build): as classify_pixel_tb_body, but a lookup compares the pixel's leaf
 // with its location's kept leaves held in registers instead of gathering a
 // byte of a 512 B / 4 KB row.
+// ftab/mtab as in classify_block_tb_body.
 template <int D, int PF, int KL>
 __device__ __forceinline__ void classify_pixel_list_body(const uint8_t *__restrict__ frames, int F, int64_t hw,
                                                          const uint16_t *kept, uint8_t *__restrict__ mask,
-                                                         int64_t tile) {
+                                                         int64_t tile, const uint8_t *const *ftab = nullptr,
+                                                         uint8_t *const *mtab = nullptr) {
   const int lane = threadIdx.x & 31;
   const int64_t pq = tile * 128 + 4 * lane;
   if (pq >= hw) return;
@@ -256,7 +264,7 @@ __device__ __forceinline__ void classify_pixel_list_body(const uint8_t *__restri
 #pragma unroll
     for (int j = 0; j < PF; ++j)
       if (f0 + j < F) {
-        const uint8_t *sp = src + (int64_t)(f0 + j) * hw * 3;
+        const uint8_t *sp = ftab ? ftab[f0 + j] + pq * 3 : src + (int64_t)(f0 + j) * hw * 3;
         w[j][0] = ld_stream4(sp), w[j][1] = ld_stream4(sp + 4), w[j][2] = ld_stream4(sp + 8);
       }
 #pragma unroll
@@ -270,7 +278,7 @@ __device__ __forceinline__ void classify_pixel_list_body(const uint8_t *__restri
         constexpr int k = decltype(kc)::value;
         bg[k] = list_holds<KL>(lst[k], quad_pixel<k>(m)) ? 1u : 0u;
       });
-      st_stream4(dst + (int64_t)(f0 + j) * hw, pack_mask4(bg[0], bg[1], bg[2], bg[3]));
+      st_stream4(mtab ? mtab[f0 + j] + pq : dst + (int64_t)(f0 + j) * hw, pack_mask4(bg[0], bg[1], bg[2], bg[3]));
     }
   }
 }
@@ -465,11 +473,14 @@ __device__ __forceinline__ void classify_tile_frame_list(const uint8_t *__restri
 // no rows in shared memory; each classifying thread holds the kept-leaf lists
 // of its PPT locations in registers (read from `kept` at a tile change) and
 // compares.
+// ftab/mtab as in classify_block_tb_body.
 template <int D, int NW, int PPT, int S, int FPS, int KL = 0>
 __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict__ frames, int F, int64_t hw,
                                                        int64_t ntiles, const uint32_t *model,
                                                        uint8_t *__restrict__ mask, int64_t vb, int64_t vg,
-                                                       unsigned int *timeout_flag, const uint16_t *kept = nullptr) {
+                                                       unsigned int *timeout_flag, const uint16_t *kept = nullptr,
+                                                       const uint8_t *const *ftab = nullptr,
+                                                       uint8_t *const *mtab = nullptr) {
   using C = TiledCfg<D, NW, PPT, S, FPS>;
   constexpr bool LIST = KL > 0;
   constexpr size_t MODEL_BYTES = LIST ? 0 : (size_t)C::MODEL_WORDS * 4;
@@ -514,7 +525,8 @@ __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict
         mbar_expect_tx(bar, (uint32_t)(nf * C::FRAME_BYTES));
         for (int i = 0; i < nf; ++i)
           bulk_g2s(smem_addr(stages + (size_t)s * C::STAGE + (size_t)i * C::FRAME_BYTES),
-                   base + (int64_t)(f0 + i) * hw * 3, C::FRAME_BYTES, bar);
+                   ftab ? ftab[f0 + i] + tile * C::TILE * 3 : base + (int64_t)(f0 + i) * hw * 3, C::FRAME_BYTES,
+                   bar);
         if (++s == S) s = 0, ++round;
       }
       u += nfr;
@@ -576,12 +588,11 @@ __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict
 #pragma unroll
           for (int i = 0; i < FPS; ++i)
             if (i < nf) {
+              uint8_t *md = mtab ? mtab[f0 + i] + p_tile : mask + (int64_t)(f0 + i) * hw + p_tile;
               if constexpr (LIST)
-                classify_tile_frame_list<D, PPT, KL>(stage + (size_t)i * C::FRAME_BYTES, lst,
-                                                     mask + (int64_t)(f0 + i) * hw + p_tile);
+                classify_tile_frame_list<D, PPT, KL>(stage + (size_t)i * C::FRAME_BYTES, lst, md);
               else
-                classify_tile_frame<D, NW, PPT, S, FPS>(stage + (size_t)i * C::FRAME_BYTES, mrow,
-                                                        mask + (int64_t)(f0 + i) * hw + p_tile);
+                classify_tile_frame<D, NW, PPT, S, FPS>(stage + (size_t)i * C::FRAME_BYTES, mrow, md);
             }
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_addr(&empty[s]));

@@ -9,6 +9,7 @@
 // the classes' branches run concurrently.
 #include <algorithm>
 #include <cstring>
+#include <unordered_map>
 #include <vector>
 
 #include "build_bodies.cuh"
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(256) g_block_tb(const GSeg *__restrict__ g, in
     const int64_t c = u / tiles;
     const int f0 = (int)(c * s.aux2);
     classify_block_tb_body<D, 4>(s.in, s.F, s.H, s.W, s.block, s.bw, s.aux3, s.model, s.mask, u - c * tiles, f0,
-                                 f0 + s.aux2);
+                                 f0 + s.aux2, s.ftab, s.mtab);
   }
 }
 
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1) g_pixel_ws_cls(const GSeg *__
   int64_t vb;
   const GSeg &s = seg_of(g, n, vb);
   classify_pixel_ws_body<D, NW, PPT, S, FPS>(s.in, s.F, s.hw, s.units, s.model, s.mask, vb, s.vg,
-                                             &g_grouped_timeout);
+                                             &g_grouped_timeout, nullptr, s.ftab, s.mtab);
 }
 
 template <int D, int KM>
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(128) g_pixel_list(const GSeg *__restrict__ g, 
   int64_t vb;
   const GSeg &s = seg_of(g, n, vb);
   for (int64_t t = vb * 4 + (threadIdx.x >> 5); t < s.units; t += s.vg * 4)
-    classify_pixel_list_body<D, 8, KL>(s.in, s.F, s.hw, s.kept, s.mask, t);
+    classify_pixel_list_body<D, 8, KL>(s.in, s.F, s.hw, s.kept, s.mask, t, s.ftab, s.mtab);
 }
 
 // ---- serving ticks ------------------------------------------------------------------
@@ -344,6 +345,7 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
   auto base = [](const GStreamIn &x, const uint8_t *src) {
     GSeg s;
     memset(&s, 0, sizeof s);
+    s.tab = -1;
     s.in = src, s.mask = x.mask, s.model = x.model, s.occ = x.occ, s.kept = x.kept;
     s.hw = (int64_t)x.H * x.W;
     s.N = x.N, s.F = x.F, s.H = x.H, s.W = x.W, s.block = x.block, s.T = x.T;
@@ -516,9 +518,11 @@ static ocq_status finish_plan(std::vector<GLaunch> &L) {
   return OCQ_OK;
 }
 
-ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunch> &out, std::vector<int> &single) {
+ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunch> &out, std::vector<int> &single,
+                             std::vector<const void *> &ptrs) {
   out.clear();
   single.clear();
+  ptrs.clear();
   std::vector<GLaunch> L;
   auto launch = [&](int kind, int a, int b) -> GLaunch & {
     for (GLaunch &x : L)
@@ -528,39 +532,59 @@ ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunc
     L.push_back(x);
     return L.back();
   };
+  // a camera's frames of the tick, in order (a camera has one model)
+  std::vector<std::vector<int>> of;
+  std::unordered_map<const ocq_model *, int> cam_of;
   for (int i = 0; i < (int)in.size(); ++i) {
-    const GFrameIn &f = in[i];
+    auto it = cam_of.emplace(in[i].model, (int)of.size()).first;
+    if (it->second == (int)of.size()) of.emplace_back();
+    std::vector<int> &fr = of[it->second];
+    if ((int)fr.size() != in[i].j) return OCQ_EINVAL;  // frames of a camera come in order
+    fr.push_back(i);
+  }
+  for (const std::vector<int> &fr : of) {
+    const GFrameIn &f = in[fr[0]];
     const ocq_model *m = f.model;
     const int d = m->depth;
     const int64_t hw = (int64_t)m->H * m->W;
-    const uintptr_t al = reinterpret_cast<uintptr_t>(f.frame) | reinterpret_cast<uintptr_t>(f.mask);
+    uintptr_t al = 0;
+    for (int i : fr) al |= reinterpret_cast<uintptr_t>(in[i].frame) | reinterpret_cast<uintptr_t>(in[i].mask);
     GSeg c;
     memset(&c, 0, sizeof c);
     c.in = f.frame, c.mask = f.mask, c.model = m->bits, c.kept = m->kept, c.hw = hw;
-    c.N = m->N, c.F = 1, c.H = m->H, c.W = m->W, c.block = m->block, c.T = m->T;
+    c.N = m->N, c.F = (int)fr.size(), c.H = m->H, c.W = m->W, c.block = m->block, c.T = m->T;
     c.bw = m->block > 0 ? (m->W + m->block - 1) / m->block : 1;
-    bool grouped = false;
-    if (m->kind == OCQ_REGION_FRAME && d <= 6) {
-      c.units = hw;
-      launch(GK_CLS_FRAME, d, 0).segs.push_back(c);
-      grouped = true;
-    } else if (m->kind == OCQ_REGION_BLOCK && d <= 5 && m->block % 4 == 0 && m->W % 4 == 0 && (al & 3) == 0) {
+    c.tab = (int64_t)ptrs.size();
+    int kind = -1, a = 0, b = 0;
+    if (m->kind == OCQ_REGION_BLOCK && d <= 5 && m->block % 4 == 0 && m->W % 4 == 0 && (al & 3) == 0) {
       c.aux3 = (m->W + 127) / 128;
       c.aux = (int64_t)((m->H + m->block - 1) / m->block) * c.aux3 * m->block;  // tiles
-      c.aux2 = 1, c.units = c.aux;
-      launch(GK_BLOCK_TB, d, 0).segs.push_back(c);
-      grouped = true;
+      c.aux2 = c.F, c.units = c.aux;
+      kind = GK_BLOCK_TB, a = d;
     } else if (m->kind == OCQ_REGION_PIXEL && d <= 3 && m->bits && hw % 1024 == 0 && (al & 15) == 0) {
       c.units = hw / 1024;
-      launch(GK_PIX_WS_CLS, d, 0).segs.push_back(c);
-      grouped = true;
+      kind = GK_PIX_WS_CLS, a = d;
     } else if (m->kind == OCQ_REGION_PIXEL && (d == 4 || d == 5) && m->kept && m->kept_len > 0 && hw % 4 == 0 &&
                (al & 3) == 0) {
       c.units = (hw + 127) / 128;
-      launch(GK_PIX_LIST, d, m->kept_len).segs.push_back(c);
-      grouped = true;
+      kind = GK_PIX_LIST, a = d, b = m->kept_len;
     }
-    if (!grouped) single.push_back(i);
+    if (kind >= 0) {
+      for (int i : fr) ptrs.push_back(in[i].frame);
+      for (int i : fr) ptrs.push_back(in[i].mask);
+      launch(kind, a, b).segs.push_back(c);
+      continue;
+    }
+    for (int i : fr) {  // one segment per frame (whole frames: a frame's pixels are contiguous)
+      const GFrameIn &g = in[i];
+      if (m->kind == OCQ_REGION_FRAME && d <= 6) {
+        GSeg e = c;
+        e.in = g.frame, e.mask = g.mask, e.F = 1, e.tab = -1, e.units = hw;
+        launch(GK_CLS_FRAME, d, 0).segs.push_back(e);
+      } else {
+        single.push_back(i);
+      }
+    }
   }
   // the window: codes, or bitsets then the counts (after every classify)
   for (const GFrameIn &f : in) {
@@ -568,6 +592,7 @@ ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunc
     const int64_t hw = (int64_t)m->H * m->W;
     GSeg w;
     memset(&w, 0, sizeof w);
+    w.tab = -1;
     w.in = f.frame, w.hw = hw, w.N = f.N, w.F = 1;
     if (f.win == 2) {
       w.kept = reinterpret_cast<uint16_t *>(f.ring) + f.slot * hw;
@@ -584,6 +609,7 @@ ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunc
     if (f.win != 1 || f.j != 0) continue;
     GSeg k;
     memset(&k, 0, sizeof k);
+    k.tab = -1;
     k.model = reinterpret_cast<uint32_t *>(f.ring), k.occ = f.fresh, k.kept = f.counts;
     k.units = wpr32(f.model->depth), k.aux = f.slot, k.N = f.N, k.F = f.m;
     k.aux2 = f.model->depth == 1 ? 8 : 32;

@@ -23,6 +23,13 @@ struct GSeg {
   int64_t aux;        // occupancy: CTAs per frame; block classify: tiles
   int32_t N, F, H, W, block, bw, T, P;
   int32_t aux2, aux3;  // block classify: frames per chunk, 128-pixel segments per row
+  // serving ticks: frame f of the segment and its mask at ftab[f] and mtab[f]
+  // (device tables; null: in + f*hw*3 and mask + f*hw).  While planning, tab
+  // is the index of the segment's first entry in the tick's pointer list
+  // (frames, then masks), or -1.
+  const uint8_t *const *ftab;
+  uint8_t *const *mtab;
+  int64_t tab;
 };
 
 // Kernel kinds (one launch per kind and template arguments a, b).
@@ -91,7 +98,11 @@ struct GFrameIn {
 };
 // Plans a tick: grouped classify launches, then window launches.  Frames no
 // grouped classify body takes are listed in `single` (classified one by one).
-ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunch> &out, std::vector<int> &single);
+// A camera's frames of the tick share one classify segment (its model read
+// once for all of them) where the body takes frame tables: `ptrs` receives the
+// tables (each segment's frames, then its masks; GSeg::tab indexes them).
+ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunch> &out, std::vector<int> &single,
+                             std::vector<const void *> &ptrs);
 // Enqueues one planned launch (segments already on the device) on `st`.
 ocq_status grouped_launch(const GLaunch &L, cudaStream_t st);
 // True (and cleared) if a bounded wait of a grouped body gave up.

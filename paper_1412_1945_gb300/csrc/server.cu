@@ -105,8 +105,17 @@ struct ocq_server {
   // grouped launches.
   cudaStream_t tick = nullptr;
   cudaEvent_t tick_ev = nullptr;
-  GSeg *d_segs = nullptr;
-  size_t segs_cap = 0;
+  uint8_t *d_tick = nullptr;  // a tick's segments and frame tables on the device
+  size_t tick_cap = 0;
+  // page-locked staging of the uploads (a ring, so that a tick's copy never
+  // waits for the previous one's)
+  struct Stage {
+    uint8_t *host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+  };
+  Stage stage[4];
+  int stage_next = 0;
   // frames of cameras whose M_0 is still being built: held on the host (a tick
   // would otherwise wait for the build and hold back every other camera)
   struct Held {
@@ -117,6 +126,7 @@ struct ocq_server {
     double arrival;
   };
   std::vector<Held> held;
+  double batch_delay = 0.0;  // seconds a tick frame may wait for others (ocq_server_set_batch_delay)
 };
 
 // Cameras whose frames run in ticks (windows the grouped tick kernels serve).
@@ -427,23 +437,47 @@ static ocq_status run_tick(ocq_server *s, const std::vector<int> &idx, const int
     if (f.j == 0) f.m = taken[done->frames[&f - &fin[0]].camera];
   std::vector<GLaunch> L;
   std::vector<int> single;
-  if (rc == OCQ_OK) rc = grouped_plan_tick(fin, L, single);
+  std::vector<const void *> ptrs;
+  if (rc == OCQ_OK) rc = grouped_plan_tick(fin, L, single, ptrs);
   size_t nseg = 0;
   for (const GLaunch &x : L) nseg += x.segs.size();
-  if (rc == OCQ_OK && nseg > s->segs_cap) {  // stream-ordered: earlier ticks' kernels are done with it
-    if (s->d_segs) cudaFreeAsync(s->d_segs, s->tick);
-    s->d_segs = nullptr;
-    s->segs_cap = std::max(nseg, 2 * s->segs_cap);
-    rc = cuda_status(malloc_async((void **)&s->d_segs, s->segs_cap * sizeof(GSeg), s->tick), "tick segments");
+  const size_t seg_bytes = nseg * sizeof(GSeg), bytes = seg_bytes + ptrs.size() * sizeof(void *);
+  if (rc == OCQ_OK && bytes > s->tick_cap) {  // stream-ordered: earlier ticks' kernels are done with it
+    if (s->d_tick) cudaFreeAsync(s->d_tick, s->tick);
+    s->d_tick = nullptr;
+    s->tick_cap = std::max(bytes, 2 * s->tick_cap);
+    rc = cuda_status(malloc_async((void **)&s->d_tick, s->tick_cap, s->tick), "tick segments");
   }
-  std::vector<GSeg> host;
-  host.reserve(nseg);
-  for (GLaunch &x : L) host.insert(host.end(), x.segs.begin(), x.segs.end());
-  if (rc == OCQ_OK && nseg)
-    rc = cuda_status(cudaMemcpyAsync(s->d_segs, host.data(), nseg * sizeof(GSeg), cudaMemcpyHostToDevice, s->tick),
-                     "upload tick segments");
+  if (rc == OCQ_OK && bytes) {
+    ocq_server::Stage &sg = s->stage[s->stage_next];
+    s->stage_next = (s->stage_next + 1) % 4;
+    if (sg.done) rc = cuda_status(cudaEventSynchronize(sg.done), "tick staging");  // that upload has ended
+    if (rc == OCQ_OK && sg.cap < bytes) {
+      if (sg.host) cudaFreeHost(sg.host);
+      sg.host = nullptr, sg.cap = 0;
+      rc = cuda_status(cudaHostAlloc((void **)&sg.host, 2 * bytes, cudaHostAllocDefault), "tick staging");
+      if (rc == OCQ_OK) sg.cap = 2 * bytes;
+    }
+    if (rc == OCQ_OK && !sg.done) rc = cuda_status(cudaEventCreateWithFlags(&sg.done, cudaEventDisableTiming), "tick staging");
+    if (rc == OCQ_OK) {
+      GSeg *hs = reinterpret_cast<GSeg *>(sg.host);
+      const uint8_t *const *dtab = reinterpret_cast<const uint8_t *const *>(s->d_tick + seg_bytes);
+      for (const GLaunch &x : L)
+        for (GSeg g : x.segs) {
+          if (g.tab >= 0) {
+            g.ftab = dtab + g.tab;
+            g.mtab = const_cast<uint8_t *const *>(reinterpret_cast<const uint8_t *const *>(dtab + g.tab + g.F));
+          }
+          *hs++ = g;
+        }
+      if (!ptrs.empty()) memcpy(sg.host + seg_bytes, ptrs.data(), ptrs.size() * sizeof(void *));
+      rc = cuda_status(cudaMemcpyAsync(s->d_tick, sg.host, bytes, cudaMemcpyHostToDevice, s->tick),
+                       "upload tick segments");
+      if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(sg.done, s->tick), "tick staging");
+    }
+  }
   size_t at = 0;
-  for (GLaunch &x : L) x.dev = s->d_segs + at, at += x.segs.size();
+  for (GLaunch &x : L) x.dev = reinterpret_cast<GSeg *>(s->d_tick) + at, at += x.segs.size();
   for (size_t k = 0; k < single.size() && rc == OCQ_OK; ++k)
     rc = ocq_classify(fin[single[k]].model, fin[single[k]].frame, 1, fin[single[k]].mask, s->tick);
   size_t li = 0;
@@ -516,6 +550,7 @@ static ocq_status flush(ocq_server *s, bool wait, int n = 0, const int *cameras 
   std::vector<uint64_t> tg;
   std::vector<double> ar;
   std::vector<ocq_server::Held> keep;
+  double oldest = 1e300;
   for (const ocq_server::Held &h : s->held) {
     Camera &c = s->cams[h.camera];
     if (!seen[h.camera]) {
@@ -523,6 +558,11 @@ static ocq_status flush(ocq_server *s, bool wait, int n = 0, const int *cameras 
       if (wait && !c.m0_joined) cudaEventSynchronize(c.merged);
       ready[h.camera] = m0_ready(c);
     }
+    if (ready[h.camera]) oldest = std::min(oldest, h.arrival);
+  }
+  // batching window: the frames wait until the oldest ready one is old enough
+  if (!wait && s->batch_delay > 0.0 && now_s() - oldest < s->batch_delay) return OCQ_OK;
+  for (const ocq_server::Held &h : s->held) {
     if (!ready[h.camera]) {
       keep.push_back(h);
       continue;
@@ -579,12 +619,25 @@ ocq_status ocq_server_submit_many(ocq_server *s, int n, const int *cameras, cons
   return n ? submit_many(s, n, cameras, frames, masks, tags) : OCQ_OK;
 }
 
+ocq_status ocq_server_set_batch_delay(ocq_server *s, double seconds) {
+  if (!s || !(seconds >= 0.0 && seconds <= 1.0)) {
+    set_error("ocq_server_set_batch_delay: bad arguments");
+    return OCQ_EINVAL;
+  }
+  s->batch_delay = seconds;
+  if (!s->held.empty()) {
+    PoolScope scope(s->pool);
+    return flush(s, false);
+  }
+  return OCQ_OK;
+}
+
 ocq_status ocq_server_poll(ocq_server *s, ocq_completion *out, int max, int *n) {
   if (!s || !n || max < 0 || (max > 0 && !out)) {
     set_error("ocq_server_poll: bad arguments");
     return OCQ_EINVAL;
   }
-  if (!s->held.empty()) {  // cameras whose M_0 is now built
+  if (!s->held.empty()) {  // cameras whose M_0 is now built, frames whose batching window ended
     PoolScope scope(s->pool);
     ocq_status rc = flush(s, false);
     if (rc != OCQ_OK) return rc;
@@ -797,11 +850,15 @@ void ocq_server_destroy(ocq_server *s) {
   for (int i = 0; i < s->max_cameras; ++i)
     if (s->cams[i].live) ocq_server_release(s, i);
   if (s->tick) {
-    if (s->d_segs) cudaFreeAsync(s->d_segs, s->tick);
+    if (s->d_tick) cudaFreeAsync(s->d_tick, s->tick);
     cudaStreamSynchronize(s->tick);
     cudaStreamDestroy(s->tick);
   }
   if (s->tick_ev) cudaEventDestroy(s->tick_ev);
+  for (ocq_server::Stage &sg : s->stage) {  // the tick stream is synchronised: every upload has ended
+    if (sg.host) cudaFreeHost(sg.host);
+    if (sg.done) cudaEventDestroy(sg.done);
+  }
   if (s->pool) cudaMemPoolDestroy(s->pool);  // every camera's memory was freed and its stream synchronised
   delete s;
 }

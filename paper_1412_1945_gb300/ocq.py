@@ -112,6 +112,7 @@ SIGNATURES = {
     "ocq_server_submit_many": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                       ctypes.POINTER(ctypes.c_uint64)]),
     "ocq_server_poll": (_i32, [_vp, ctypes.POINTER(ocq_completion), _i32, ctypes.POINTER(_i32)]),
+    "ocq_server_set_batch_delay": (_i32, [_vp, ctypes.c_double]),
     "ocq_server_release": (_i32, [_vp, _i32]),
     "ocq_server_camera_model": (_i32, [_vp, _i32, ctypes.POINTER(_vp)]),
     "ocq_server_usage": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_i64)]),
@@ -526,6 +527,45 @@ def ocq_server_submit_many(server, cameras, frames, masks, tags):
     mk = (_vp * n)(*[_p(m) for m in masks])
     tg = (ctypes.c_uint64 * n)(*tags)
     _check(load().ocq_server_submit_many(server.handle, n, cam, fr, mk, tg))
+
+
+def ocq_server_submit_arrays(server, cameras, frame_ptrs, mask_ptrs, tags):
+    """ocq_server_submit_many from numpy arrays (int32 cameras, uint64 device
+    addresses of frames and masks, uint64 tags), passed without a copy."""
+    import numpy as np
+
+    cam = np.ascontiguousarray(cameras, dtype=np.int32)
+    fr = np.ascontiguousarray(frame_ptrs, dtype=np.uint64)
+    mk = np.ascontiguousarray(mask_ptrs, dtype=np.uint64)
+    tg = np.ascontiguousarray(tags, dtype=np.uint64)
+    n = cam.shape[0]
+    if not (fr.shape[0] == mk.shape[0] == tg.shape[0] == n):
+        raise ValueError("cameras, frames, masks and tags must have the same length")
+    if n == 0:
+        return
+    _check(load().ocq_server_submit_many(server.handle, n, cam.ctypes.data_as(ctypes.POINTER(_i32)),
+                                         ctypes.cast(fr.ctypes.data, ctypes.POINTER(_vp)),
+                                         ctypes.cast(mk.ctypes.data, ctypes.POINTER(_vp)),
+                                         tg.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+
+
+def ocq_server_poll_array(server, max_n=65536):
+    """ocq_server_poll into a numpy structured array (fields camera, frame,
+    tag, arrival_s, done_s)."""
+    import numpy as np
+
+    dt = np.dtype([("camera", np.int32), ("reserved", np.int32), ("frame", np.int64), ("tag", np.uint64),
+                   ("arrival_s", np.float64), ("done_s", np.float64)])
+    assert dt.itemsize == ctypes.sizeof(ocq_completion)
+    buf = np.empty(max_n, dtype=dt)
+    n = ctypes.c_int()
+    _check(load().ocq_server_poll(server.handle, ctypes.cast(buf.ctypes.data, ctypes.POINTER(ocq_completion)),
+                                  max_n, ctypes.byref(n)))
+    return buf[:n.value]
+
+
+def ocq_server_set_batch_delay(server, seconds: float):
+    _check(load().ocq_server_set_batch_delay(server.handle, float(seconds)))
 
 
 def ocq_server_poll(server, max_n=4096):

@@ -129,3 +129,56 @@ def test_batched_submits_follow_the_window_semantics(cuda_ready, chunks):
             assert (model == oracle.build_model(hosts[i][k * K:k * K + N], d, T, region, block)).all(), i
     finally:
         srv.destroy()
+
+
+def test_batching_window_holds_frames_and_keeps_the_semantics(cuda_ready):
+    """With a batching window the frames of tick cameras wait on the host
+    (nothing completes before the window ends), then run in ticks that hold
+    several frames per camera; masks and final models still follow the window
+    semantics."""
+    import time
+
+    import torch
+
+    O = cuda_ready.ocq
+    cams = [c for c in CAMERAS if c[10] in (1, 2)]
+    srv = O.ocq_server_create(1 << 30, len(cams))
+    hosts, devs, masks, ids = [], [], [], []
+    try:
+        for i, cam in enumerate(cams):
+            scene, H, W, region, block, d, T, N, K, F, form = cam
+            host = ocq_synth.fill_host(ocq_synth.make_scene(scene, H, W, N, F, 7500 + i), 0, N + F)
+            hosts.append(host)
+            devs.append(torch.from_numpy(host).cuda())
+            masks.append(torch.full((F, H, W), 9, dtype=torch.uint8, device="cuda"))
+        torch.cuda.synchronize()
+        for i, cam in enumerate(cams):
+            scene, H, W, region, block, d, T, N, K, F, form = cam
+            ids.append(O.ocq_server_admit(srv, H, W, region, block, d, T, N, K, devs[i][:N].contiguous()))
+            assert ids[-1] is not None
+        O.ocq_server_sync(srv)  # every M_0 built: frames are held only by the window
+        O.ocq_server_set_batch_delay(srv, 1.0)
+        order = [(i, t) for t in range(max(c[9] for c in cams)) for i, c in enumerate(cams) if t < c[9]]
+        t0 = time.monotonic()
+        for i, t in order:
+            O.ocq_server_submit(srv, ids[i], devs[i][cams[i][7] + t], masks[i][t], tag=1000 * i + t)
+        early = O.ocq_server_poll(srv, 100000)
+        if time.monotonic() - t0 < 0.5:
+            assert early == []
+        O.ocq_server_set_batch_delay(srv, 0.002)
+        done = list(early)
+        deadline = time.monotonic() + 20.0
+        while len(done) < len(order) and time.monotonic() < deadline:
+            time.sleep(0.003)
+            done += O.ocq_server_poll(srv, 100000)
+        O.ocq_server_sync(srv)
+        done += O.ocq_server_poll(srv, 100000)
+        assert len(done) == len(order)
+        for i, cam in enumerate(cams):
+            scene, H, W, region, block, d, T, N, K, F, form = cam
+            assert (masks[i].cpu().numpy() == _window_oracle(hosts[i], cam)).all(), i
+            model = cuda_ready.export_model(O.ocq_server_camera_model(srv, ids[i])).cpu().numpy().view(np.uint64)
+            k = F // K
+            assert (model == oracle.build_model(hosts[i][k * K:k * K + N], d, T, region, block)).all(), i
+    finally:
+        srv.destroy()
