@@ -735,16 +735,16 @@ def batched_measure(ocq, dev, reps):
 
 
 def _serve_run(O, streams, bufs, fps, budget, n_cameras, frames_per_camera, pool, mask_slots, speed,
-               time_limit_s, batch_delay_s=0.0):
+               time_limit_s, batch_delay_s=0.0, ticks_in_flight=2):
     """One serving run of the camera set with every join and arrival time
     divided by ``speed`` (speed 1 = real time).  Waiting cameras are admitted
     first-fit against the HBM budget as slots and memory free up; a camera
     admitted late has its arrivals shifted by the delay.  Each pass of the
     loop submits every frame that has arrived (one ocq_server_submit_many)
     and polls; latency = completion time - scheduled arrival (host steady
-    clock), so host lag and queueing count against it.  With ``batch_delay_s``
-    > 0 the server holds tick frames that long for others
-    (ocq_server_set_batch_delay); the wait counts in the latency.  The loop's
+    clock), so host lag and queueing count against it.  ``batch_delay_s`` and
+    ``ticks_in_flight`` set the server's batching (ocq_server_set_batching);
+    a frame's wait on the host counts in its latency.  The loop's
     per-frame work is numpy over all cameras (pointer tables built before the
     clock starts), so the harness does not bound the rate it measures."""
     import numpy as np
@@ -762,8 +762,12 @@ def _serve_run(O, streams, bufs, fps, budget, n_cameras, frames_per_camera, pool
     nxt = np.zeros(C, dtype=np.int64)
     completed = np.zeros(C, dtype=np.int64)
 
+    import gc
+
     srv = O.ocq_server_create(budget, n_cameras)
-    O.ocq_server_set_batch_delay(srv, batch_delay_s)
+    O.ocq_server_set_batching(srv, batch_delay_s, ticks_in_flight)
+    gc_was = gc.isenabled()
+    gc.disable()  # no collector pause inside the timed loop
     joins = sorted(range(C), key=lambda i: streams[i].join_s)
     jn = 0
     waiting = []
@@ -834,6 +838,8 @@ def _serve_run(O, streams, bufs, fps, budget, n_cameras, frames_per_camera, pool
         O.ocq_server_sync(srv)
     finally:
         srv.destroy()
+        if gc_was:
+            gc.enable()
     lat = np.concatenate(lat_parts) if lat_parts else np.zeros(0)
     cams = np.concatenate(cam_parts) if cam_parts else np.zeros(0, dtype=np.int64)
     by_kind = {}
@@ -884,8 +890,8 @@ def _serve_plain(O, streams, bufs, frames_per_camera, pool, mask_slots, window):
 
 
 def serving_measure(ocq, dev, time_limit_s, budget_frac=0.7, n_cameras=256, frames_per_camera=90, pool=4,
-                    mask_slots=8, deadline_ms=33.0, speeds=(8, 11, 16, 23, 32, 45, 64, 90, 128),
-                    batch_delays_ms=(0.0, 4.0)):
+                    mask_slots=8, deadline_ms=33.0, speeds=(8, 11, 16, 23, 32, 45, 54, 64, 76, 90, 108, 128),
+                    batchings=((0.0, 0), (0.0, 2), (4.0, 2))):
     """The 256-camera serving preset: cameras join as a Poisson process
     (25.6/s) and then send frames as a Poisson process at 30 fps.  Every
     camera's N training frames and a pool of ``pool`` test frames (cycled) are
@@ -894,7 +900,7 @@ def serving_measure(ocq, dev, time_limit_s, budget_frac=0.7, n_cameras=256, fram
 
     * real time (speed 1): latency at the preset's offered load;
     * capacity: the same arrival process compressed ``speed`` times, for each
-      batching window in ``batch_delays_ms`` and each speed in ``speeds``
+      batching (delay ms, ticks in flight) in ``batchings`` and each speed in ``speeds``
       until a run's p99 passes ``deadline_ms`` (one frame period at 30 fps) or
       frames are left over; the fastest run that kept the deadline gives the
       capacity (Mpixel/s of completed frames over wall time);
@@ -920,16 +926,19 @@ def serving_measure(ocq, dev, time_limit_s, budget_frac=0.7, n_cameras=256, fram
     free, _ = torch.cuda.mem_get_info(dev)
     budget = int(free * budget_frac)
     args = (O, streams, bufs, fps, budget, n_cameras, frames_per_camera, pool, mask_slots)
+    # warm-up (the kernels' first launches, the server's staging), not reported
+    _serve_run(O, streams[:64], bufs[:64], fps[:64], budget, 64, frames_per_camera, pool, mask_slots, 64.0,
+               time_limit_s)
     rt = _serve_run(*args, 1.0, time_limit_s)
     sweep, best = [], None
     offered_1 = sum(s.wl.H * s.wl.W * frames_per_camera for s in streams) / max(
         s.join_s + s.arrivals[-1] - s.join_s for s in streams)
-    for bd in batch_delays_ms:
+    for bd, tif in batchings:
         for sp in speeds:
-            r = _serve_run(*args, float(sp), time_limit_s, bd / 1e3)
+            r = _serve_run(*args, float(sp), time_limit_s, bd / 1e3, tif)
             ok = r["frames_done"] == n_cameras * frames_per_camera and r["p99_ms"] is not None and \
                 r["p99_ms"] <= deadline_ms
-            sweep.append({"batch_delay_ms": bd, "speed": sp, "offered_mpixel_s": round(offered_1 * sp / 1e6, 1),
+            sweep.append({"batch_delay_ms": bd, "ticks_in_flight": tif, "speed": sp, "offered_mpixel_s": round(offered_1 * sp / 1e6, 1),
                           "mpixel_s": r["mpixel_s"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
                           "frames_done": r["frames_done"], "wall_s": round(r["wall"], 3), "kept_deadline": ok})
             if ok:
@@ -955,6 +964,7 @@ def serving_measure(ocq, dev, time_limit_s, budget_frac=0.7, n_cameras=256, fram
            "window_N": 30, "remerge_every_K": 30, "T": 10, "frames_prerendered": True,
            "capacity": {"deadline_ms": deadline_ms, "sweep": sweep,
                         "batch_delay_ms": best["batch_delay_ms"] if best else None,
+                        "ticks_in_flight": best["ticks_in_flight"] if best else None,
                         "capacity_mpixel_s": best["mpixel_s"] if best else None,
                         "p50_ms": best["p50_ms"] if best else None, "p99_ms": best["p99_ms"] if best else None,
                         "plain_per_frame_calls": plain,

@@ -372,14 +372,18 @@ ocq_status ocq_server_submit(ocq_server *server, int camera, const uint8_t *fram
  * one the window semantics give, whatever the grouping.  Non-blocking. */
 ocq_status ocq_server_submit_many(ocq_server *server, int n, const int *cameras, const uint8_t *const *frames,
                                   uint8_t *const *masks, const uint64_t *tags);
-/* Batching window of the ticks: frames of cameras served in ticks wait on the
- * host until the oldest of them has waited `seconds` (checked at every submit
- * and poll; release, snapshot and sync run them at once), so that a tick
- * classifies several frames of a camera against one read of its model (a
- * per-pixel model row is 16-64 B per pixel against a frame's 3 B).  0 (the
- * default) runs them at the next submit.  seconds in [0, 1]; a caller that
- * sets it polls at least that often.  No counterpart in the paper. */
-ocq_status ocq_server_set_batch_delay(ocq_server *server, double seconds);
+/* Batching of the ticks.  A tick classifies all of a camera's frames in it
+ * against one read of the camera's model (a per-pixel model row is 16-64 B per
+ * pixel against a frame's 3 B), so larger ticks move fewer bytes per frame.
+ * Frames of cameras served in ticks wait on the host
+ *   - until the oldest of them has waited `seconds` (0, the default: no wait),
+ *   - and while `ticks_in_flight` ticks are enqueued and unfinished (0: no
+ *     limit; the default 2 lets one tick run while the next is queued, so that
+ *     under load the frames that arrive meanwhile form one larger tick);
+ * both are checked at every submit and poll (release, snapshot and sync run
+ * held frames at once), so a caller polls regularly.  seconds in [0, 1].  No
+ * counterpart in the paper. */
+ocq_status ocq_server_set_batching(ocq_server *server, double seconds, int ticks_in_flight);
 /* Up to max completed frames, oldest first; *n receives the count (runs the
  * held frames whose batching window ended). */
 ocq_status ocq_server_poll(ocq_server *server, ocq_completion *out, int max, int *n);

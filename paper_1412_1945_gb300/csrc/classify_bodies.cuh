@@ -157,13 +157,15 @@ __device__ __forceinline__ void classify_pixel_tb_body(const uint8_t *__restrict
 // while the current PF are looked up (two register buffers).
 // ftab/mtab (device tables, or null): frame f and its mask at ftab[f] and
 // mtab[f] instead of frames + f*H*W*3 and mask + f*H*W (frames gathered from
-// several buffers, as a serving tick's).
+// several buffers, as a serving tick's).  ctab (or null): frame f's u16 leaf
+// codes are written at ctab[f] too (a serving window's slot), 8-byte aligned.
 template <int D, int PF>
 __device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict__ frames, int F, int H, int W,
                                                        int b, int bw, int nseg, const uint32_t *model,
                                                        uint8_t *__restrict__ mask, int64_t t, int fb = 0,
                                                        int fe = -1, const uint8_t *const *ftab = nullptr,
-                                                       uint8_t *const *mtab = nullptr) {
+                                                       uint8_t *const *mtab = nullptr,
+                                                       uint16_t *const *ctab = nullptr) {
   constexpr int64_t WPR = D == 1 ? 1 : (int64_t)1 << (3 * D - 5);
   if (fe < 0 || fe > F) fe = F;
   const int lane = threadIdx.x & 31;
@@ -195,13 +197,16 @@ __device__ __forceinline__ void classify_block_tb_body(const uint8_t *__restrict
       uint32_t m[3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) m[i] = (w[j][i] >> (8 - D)) & byte_mask(D);
-      uint32_t bg[4];
+      uint32_t bg[4], cq[4];
       static_for<0, 4>([&](auto kc) {
         constexpr int kk = decltype(kc)::value;
         const uint32_t c = planar_from_masked<D>(quad_pixel<kk>(m));
+        cq[kk] = c;
         bg[kk] = (uint32_t)row[c >> 3] >> (c & 7);
       });
       st_stream4(fdst(f0 + j), pack_mask4(bg[0], bg[1], bg[2], bg[3]));
+      if (ctab)
+        *reinterpret_cast<uint2 *>(ctab[f0 + j] + pq) = make_uint2(cq[0] | (cq[1] << 16), cq[2] | (cq[3] << 16));
     }
   };
   uint32_t wa[PF][3], wb[PF][3];
@@ -245,12 +250,13 @@ __device__ __forceinline__ bool list_holds(const uint32_t (&l)[KL], uint32_t t) 
 // build): as classify_pixel_tb_body, but a lookup compares the pixel's leaf
 // with its location's kept leaves held in registers instead of gathering a
 // byte of a 512 B / 4 KB row.
-// ftab/mtab as in classify_block_tb_body.
+// ftab/mtab/ctab as in classify_block_tb_body.
 template <int D, int PF, int KL>
 __device__ __forceinline__ void classify_pixel_list_body(const uint8_t *__restrict__ frames, int F, int64_t hw,
                                                          const uint16_t *kept, uint8_t *__restrict__ mask,
                                                          int64_t tile, const uint8_t *const *ftab = nullptr,
-                                                         uint8_t *const *mtab = nullptr) {
+                                                         uint8_t *const *mtab = nullptr,
+                                                         uint16_t *const *ctab = nullptr) {
   const int lane = threadIdx.x & 31;
   const int64_t pq = tile * 128 + 4 * lane;
   if (pq >= hw) return;
@@ -279,6 +285,14 @@ __device__ __forceinline__ void classify_pixel_list_body(const uint8_t *__restri
         bg[k] = list_holds<KL>(lst[k], quad_pixel<k>(m)) ? 1u : 0u;
       });
       st_stream4(mtab ? mtab[f0 + j] + pq : dst + (int64_t)(f0 + j) * hw, pack_mask4(bg[0], bg[1], bg[2], bg[3]));
+      if (ctab) {
+        uint32_t cq[4];
+        static_for<0, 4>([&](auto kc) {
+          constexpr int k = decltype(kc)::value;
+          cq[k] = planar_from_masked<D>(quad_pixel<k>(m));
+        });
+        *reinterpret_cast<uint2 *>(ctab[f0 + j] + pq) = make_uint2(cq[0] | (cq[1] << 16), cq[2] | (cq[3] << 16));
+      }
     }
   }
 }
@@ -427,23 +441,31 @@ __device__ __forceinline__ void store_tile_mask(uint8_t *__restrict__ dst, const
 }
 
 // Classifies one frame of the tile from shared memory: thread (warp, lane)
-// handles pixels (warp*32 + lane)*PPT + j of the tile.
+// handles pixels (warp*32 + lane)*PPT + j of the tile.  cdst (or null): the
+// tile's u16 leaf codes of this frame are written there too (16-byte aligned).
 template <int D, int NW, int PPT, int S, int FPS>
 __device__ __forceinline__ void classify_tile_frame(const uint8_t *__restrict__ src, const uint32_t *__restrict__ mrow,
-                                                    uint8_t *__restrict__ dst) {
+                                                    uint8_t *__restrict__ dst, uint16_t *__restrict__ cdst = nullptr) {
   using C = TiledCfg<D, NW, PPT, S, FPS>;
-  uint32_t fbit[PPT];
+  uint32_t fbit[PPT], q[PPT];
   uint32_t w[12];
   tile_frame_words<D, PPT>(src, w);
   // mrow points at word 0 of pixel j=0 for this lane; pixel j's word q>>5 is at
   // mrow[(j*WPR + (q>>5))*32]
   static_for<0, PPT>([&](auto jc) {
     constexpr int j = decltype(jc)::value;
-    const uint32_t q = planar_from_masked<D>(group_pixel<j>(w));
-    const uint32_t v = mrow[(j * C::WPR + (q >> 5)) * 32];
-    fbit[j] = __funnelshift_r(v, v, q);
+    q[j] = planar_from_masked<D>(group_pixel<j>(w));
+    const uint32_t v = mrow[(j * C::WPR + (q[j] >> 5)) * 32];
+    fbit[j] = __funnelshift_r(v, v, q[j]);
   });
   store_tile_mask<PPT>(dst, fbit);
+  if (cdst) {
+    uint4 *c4 = reinterpret_cast<uint4 *>(cdst + threadIdx.x * PPT);
+#pragma unroll
+    for (int h = 0; h < PPT / 8; ++h)
+      c4[h] = make_uint4(q[8 * h] | (q[8 * h + 1] << 16), q[8 * h + 2] | (q[8 * h + 3] << 16),
+                         q[8 * h + 4] | (q[8 * h + 5] << 16), q[8 * h + 6] | (q[8 * h + 7] << 16));
+  }
 }
 
 // As classify_tile_frame for depth 4-5 models with a kept-leaf index: pixel
@@ -473,14 +495,15 @@ __device__ __forceinline__ void classify_tile_frame_list(const uint8_t *__restri
 // no rows in shared memory; each classifying thread holds the kept-leaf lists
 // of its PPT locations in registers (read from `kept` at a tile change) and
 // compares.
-// ftab/mtab as in classify_block_tb_body.
+// ftab/mtab/ctab as in classify_block_tb_body (ctab only without KL).
 template <int D, int NW, int PPT, int S, int FPS, int KL = 0>
 __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict__ frames, int F, int64_t hw,
                                                        int64_t ntiles, const uint32_t *model,
                                                        uint8_t *__restrict__ mask, int64_t vb, int64_t vg,
                                                        unsigned int *timeout_flag, const uint16_t *kept = nullptr,
                                                        const uint8_t *const *ftab = nullptr,
-                                                       uint8_t *const *mtab = nullptr) {
+                                                       uint8_t *const *mtab = nullptr,
+                                                       uint16_t *const *ctab = nullptr) {
   using C = TiledCfg<D, NW, PPT, S, FPS>;
   constexpr bool LIST = KL > 0;
   constexpr size_t MODEL_BYTES = LIST ? 0 : (size_t)C::MODEL_WORDS * 4;
@@ -592,7 +615,8 @@ __device__ __forceinline__ void classify_pixel_ws_body(const uint8_t *__restrict
               if constexpr (LIST)
                 classify_tile_frame_list<D, PPT, KL>(stage + (size_t)i * C::FRAME_BYTES, lst, md);
               else
-                classify_tile_frame<D, NW, PPT, S, FPS>(stage + (size_t)i * C::FRAME_BYTES, mrow, md);
+                classify_tile_frame<D, NW, PPT, S, FPS>(stage + (size_t)i * C::FRAME_BYTES, mrow, md,
+                                                        ctab ? ctab[f0 + i] + p_tile : nullptr);
             }
           __syncwarp();
           if (lane == 0) mbar_arrive(smem_addr(&empty[s]));

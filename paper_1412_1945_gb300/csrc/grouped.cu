@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) g_block_tb(const GSeg *__restrict__ g, in
     const int64_t c = u / tiles;
     const int f0 = (int)(c * s.aux2);
     classify_block_tb_body<D, 4>(s.in, s.F, s.H, s.W, s.block, s.bw, s.aux3, s.model, s.mask, u - c * tiles, f0,
-                                 f0 + s.aux2, s.ftab, s.mtab);
+                                 f0 + s.aux2, s.ftab, s.mtab, s.ctab);
   }
 }
 
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(NW * 32 + 32, 1) g_pixel_ws_cls(const GSeg *__
   int64_t vb;
   const GSeg &s = seg_of(g, n, vb);
   classify_pixel_ws_body<D, NW, PPT, S, FPS>(s.in, s.F, s.hw, s.units, s.model, s.mask, vb, s.vg,
-                                             &g_grouped_timeout, nullptr, s.ftab, s.mtab);
+                                             &g_grouped_timeout, nullptr, s.ftab, s.mtab, s.ctab);
 }
 
 template <int D, int KM>
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(128) g_pixel_list(const GSeg *__restrict__ g, 
   int64_t vb;
   const GSeg &s = seg_of(g, n, vb);
   for (int64_t t = vb * 4 + (threadIdx.x >> 5); t < s.units; t += s.vg * 4)
-    classify_pixel_list_body<D, 8, KL>(s.in, s.F, s.hw, s.kept, s.mask, t, s.ftab, s.mtab);
+    classify_pixel_list_body<D, 8, KL>(s.in, s.F, s.hw, s.kept, s.mask, t, s.ftab, s.mtab, s.ctab);
 }
 
 // ---- serving ticks ------------------------------------------------------------------
@@ -534,6 +534,7 @@ ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunc
   };
   // a camera's frames of the tick, in order (a camera has one model)
   std::vector<std::vector<int>> of;
+  std::vector<char> coded(in.size(), 0);
   std::unordered_map<const ocq_model *, int> cam_of;
   for (int i = 0; i < (int)in.size(); ++i) {
     auto it = cam_of.emplace(in[i].model, (int)of.size()).first;
@@ -572,6 +573,13 @@ ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunc
     if (kind >= 0) {
       for (int i : fr) ptrs.push_back(in[i].frame);
       for (int i : fr) ptrs.push_back(in[i].mask);
+      if (f.win == 2) {  // the classify writes the frames' codes into their window slots
+        c.codes = 1;
+        for (int i : fr) {
+          ptrs.push_back(reinterpret_cast<uint16_t *>(in[i].ring) + in[i].slot * hw);
+          coded[i] = 1;
+        }
+      }
       launch(kind, a, b).segs.push_back(c);
       continue;
     }
@@ -586,8 +594,11 @@ ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunc
       }
     }
   }
-  // the window: codes, or bitsets then the counts (after every classify)
-  for (const GFrameIn &f : in) {
+  // the window: codes (where the classify did not write them), or bitsets
+  // then the counts (after every classify)
+  for (size_t i = 0; i < in.size(); ++i) {
+    const GFrameIn &f = in[i];
+    if (coded[i]) continue;
     const ocq_model *m = f.model;
     const int64_t hw = (int64_t)m->H * m->W;
     GSeg w;

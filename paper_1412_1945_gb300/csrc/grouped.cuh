@@ -29,7 +29,10 @@ struct GSeg {
   // (frames, then masks), or -1.
   const uint8_t *const *ftab;
   uint8_t *const *mtab;
+  uint16_t *const *ctab;  // frame f's leaf codes into ctab[f] too (a code window's slot), or null
   int64_t tab;
+  int32_t codes;  // planning: the segment's table also lists code slots (after the masks)
+  int32_t pad;
 };
 
 // Kernel kinds (one launch per kind and template arguments a, b).
@@ -100,7 +103,9 @@ struct GFrameIn {
 // grouped classify body takes are listed in `single` (classified one by one).
 // A camera's frames of the tick share one classify segment (its model read
 // once for all of them) where the body takes frame tables: `ptrs` receives the
-// tables (each segment's frames, then its masks; GSeg::tab indexes them).
+// tables (each segment's frames, its masks, then for code windows the slots
+// its leaf codes go to: that classify writes them, no separate code pass;
+// GSeg::tab indexes them).
 ocq_status grouped_plan_tick(const std::vector<GFrameIn> &in, std::vector<GLaunch> &out, std::vector<int> &single,
                              std::vector<const void *> &ptrs);
 // Enqueues one planned launch (segments already on the device) on `st`.

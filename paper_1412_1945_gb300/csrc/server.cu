@@ -116,6 +116,7 @@ struct ocq_server {
   };
   Stage stage[4];
   int stage_next = 0;
+  std::vector<uint8_t *> retired;  // outgrown staging, freed with the server (freeing syncs the device)
   // frames of cameras whose M_0 is still being built: held on the host (a tick
   // would otherwise wait for the build and hold back every other camera)
   struct Held {
@@ -126,7 +127,13 @@ struct ocq_server {
     double arrival;
   };
   std::vector<Held> held;
-  double batch_delay = 0.0;  // seconds a tick frame may wait for others (ocq_server_set_batch_delay)
+  // batching (ocq_server_set_batching): seconds a tick frame may wait for
+  // others; ticks enqueued and not yet finished (end events, oldest first),
+  // beyond which frames wait on the host and join the next, larger tick
+  double batch_delay = 0.0;
+  int max_in_flight = 2;
+  std::deque<cudaEvent_t> in_flight;
+  std::vector<cudaEvent_t> spare_events;
 };
 
 // Cameras whose frames run in ticks (windows the grouped tick kernels serve).
@@ -453,10 +460,11 @@ static ocq_status run_tick(ocq_server *s, const std::vector<int> &idx, const int
     s->stage_next = (s->stage_next + 1) % 4;
     if (sg.done) rc = cuda_status(cudaEventSynchronize(sg.done), "tick staging");  // that upload has ended
     if (rc == OCQ_OK && sg.cap < bytes) {
-      if (sg.host) cudaFreeHost(sg.host);
+      if (sg.host) s->retired.push_back(sg.host);
       sg.host = nullptr, sg.cap = 0;
-      rc = cuda_status(cudaHostAlloc((void **)&sg.host, 2 * bytes, cudaHostAllocDefault), "tick staging");
-      if (rc == OCQ_OK) sg.cap = 2 * bytes;
+      const size_t cap = std::max<size_t>(2 * bytes, 256 * 1024);
+      rc = cuda_status(cudaHostAlloc((void **)&sg.host, cap, cudaHostAllocDefault), "tick staging");
+      if (rc == OCQ_OK) sg.cap = cap;
     }
     if (rc == OCQ_OK && !sg.done) rc = cuda_status(cudaEventCreateWithFlags(&sg.done, cudaEventDisableTiming), "tick staging");
     if (rc == OCQ_OK) {
@@ -466,7 +474,9 @@ static ocq_status run_tick(ocq_server *s, const std::vector<int> &idx, const int
         for (GSeg g : x.segs) {
           if (g.tab >= 0) {
             g.ftab = dtab + g.tab;
-            g.mtab = const_cast<uint8_t *const *>(reinterpret_cast<const uint8_t *const *>(dtab + g.tab + g.F));
+            g.mtab = const_cast<uint8_t *const *>(dtab + g.tab + g.F);
+            if (g.codes)
+              g.ctab = reinterpret_cast<uint16_t *const *>(const_cast<uint8_t *const *>(dtab + g.tab + 2 * g.F));
           }
           *hs++ = g;
         }
@@ -500,6 +510,17 @@ static ocq_status run_tick(ocq_server *s, const std::vector<int> &idx, const int
       rc = launch_window_threshold(c.counts, c.d.depth, (uint32_t)c.d.T, c.model->bits, s->tick);
     else
       rc = launch_remerge_codes(reinterpret_cast<uint16_t *>(c.ring), c.d.N, c.model, s->tick);
+  }
+  if (rc == OCQ_OK) {  // the tick's end, for the in-flight limit
+    cudaEvent_t e = nullptr;
+    if (!s->spare_events.empty()) {
+      e = s->spare_events.back();
+      s->spare_events.pop_back();
+    } else {
+      rc = cuda_status(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "tick end");
+    }
+    if (rc == OCQ_OK) rc = cuda_status(cudaEventRecord(e, s->tick), "tick end");
+    if (e) s->in_flight.push_back(e);
   }
   delete done;
   return rc;
@@ -562,6 +583,12 @@ static ocq_status flush(ocq_server *s, bool wait, int n = 0, const int *cameras 
   }
   // batching window: the frames wait until the oldest ready one is old enough
   if (!wait && s->batch_delay > 0.0 && now_s() - oldest < s->batch_delay) return OCQ_OK;
+  // and while the GPU still has max_in_flight ticks to run
+  while (!s->in_flight.empty() && cudaEventQuery(s->in_flight.front()) == cudaSuccess) {
+    s->spare_events.push_back(s->in_flight.front());
+    s->in_flight.pop_front();
+  }
+  if (!wait && s->max_in_flight > 0 && (int)s->in_flight.size() >= s->max_in_flight) return OCQ_OK;
   for (const ocq_server::Held &h : s->held) {
     if (!ready[h.camera]) {
       keep.push_back(h);
@@ -619,12 +646,13 @@ ocq_status ocq_server_submit_many(ocq_server *s, int n, const int *cameras, cons
   return n ? submit_many(s, n, cameras, frames, masks, tags) : OCQ_OK;
 }
 
-ocq_status ocq_server_set_batch_delay(ocq_server *s, double seconds) {
-  if (!s || !(seconds >= 0.0 && seconds <= 1.0)) {
-    set_error("ocq_server_set_batch_delay: bad arguments");
+ocq_status ocq_server_set_batching(ocq_server *s, double seconds, int ticks_in_flight) {
+  if (!s || !(seconds >= 0.0 && seconds <= 1.0) || ticks_in_flight < 0) {
+    set_error("ocq_server_set_batching: bad arguments");
     return OCQ_EINVAL;
   }
   s->batch_delay = seconds;
+  s->max_in_flight = ticks_in_flight;
   if (!s->held.empty()) {
     PoolScope scope(s->pool);
     return flush(s, false);
@@ -855,6 +883,9 @@ void ocq_server_destroy(ocq_server *s) {
     cudaStreamDestroy(s->tick);
   }
   if (s->tick_ev) cudaEventDestroy(s->tick_ev);
+  for (uint8_t *h : s->retired) cudaFreeHost(h);
+  for (cudaEvent_t e : s->in_flight) cudaEventDestroy(e);
+  for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
   for (ocq_server::Stage &sg : s->stage) {  // the tick stream is synchronised: every upload has ended
     if (sg.host) cudaFreeHost(sg.host);
     if (sg.done) cudaEventDestroy(sg.done);

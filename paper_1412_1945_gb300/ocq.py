@@ -112,7 +112,7 @@ SIGNATURES = {
     "ocq_server_submit_many": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                       ctypes.POINTER(ctypes.c_uint64)]),
     "ocq_server_poll": (_i32, [_vp, ctypes.POINTER(ocq_completion), _i32, ctypes.POINTER(_i32)]),
-    "ocq_server_set_batch_delay": (_i32, [_vp, ctypes.c_double]),
+    "ocq_server_set_batching": (_i32, [_vp, ctypes.c_double, _i32]),
     "ocq_server_release": (_i32, [_vp, _i32]),
     "ocq_server_camera_model": (_i32, [_vp, _i32, ctypes.POINTER(_vp)]),
     "ocq_server_usage": (_i32, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz), ctypes.POINTER(_i64)]),
@@ -564,8 +564,8 @@ def ocq_server_poll_array(server, max_n=65536):
     return buf[:n.value]
 
 
-def ocq_server_set_batch_delay(server, seconds: float):
-    _check(load().ocq_server_set_batch_delay(server.handle, float(seconds)))
+def ocq_server_set_batching(server, seconds: float = 0.0, ticks_in_flight: int = 2):
+    _check(load().ocq_server_set_batching(server.handle, float(seconds), int(ticks_in_flight)))
 
 
 def ocq_server_poll(server, max_n=4096):

@@ -157,7 +157,7 @@ def test_batching_window_holds_frames_and_keeps_the_semantics(cuda_ready):
             ids.append(O.ocq_server_admit(srv, H, W, region, block, d, T, N, K, devs[i][:N].contiguous()))
             assert ids[-1] is not None
         O.ocq_server_sync(srv)  # every M_0 built: frames are held only by the window
-        O.ocq_server_set_batch_delay(srv, 1.0)
+        O.ocq_server_set_batching(srv, 1.0, 2)
         order = [(i, t) for t in range(max(c[9] for c in cams)) for i, c in enumerate(cams) if t < c[9]]
         t0 = time.monotonic()
         for i, t in order:
@@ -165,7 +165,7 @@ def test_batching_window_holds_frames_and_keeps_the_semantics(cuda_ready):
         early = O.ocq_server_poll(srv, 100000)
         if time.monotonic() - t0 < 0.5:
             assert early == []
-        O.ocq_server_set_batch_delay(srv, 0.002)
+        O.ocq_server_set_batching(srv, 0.002, 2)
         done = list(early)
         deadline = time.monotonic() + 20.0
         while len(done) < len(order) and time.monotonic() < deadline:
