@@ -309,6 +309,36 @@ def test_every_tuning_variant(ocq, torch, H, W):
                     O.ocq_tune_select(kernel, saved)
 
 
+@pytest.mark.parametrize("H,W", [(32, 64), (20, 52)])
+def test_pixel_build_variants_many_distinct_leaves(ocq, torch, H, W):
+    """Every per-pixel build variant at depth <= 3 when locations hold many
+    distinct leaves: uniform noise in half the locations (as many distinct
+    leaves as frames, past the candidate build's counters), scene content in
+    the other half; several tiles and a ragged rest; N = 60 and N = 127."""
+    O = ocq.ocq
+    kern = O.OCQ_TUNE_BUILD_PIXEL
+    saved = O.ocq_tune_selected(kern)
+    try:
+        for N in (60, 127):
+            sc = ocq_synth.make_scene("bimodal", H, W, N, 3, seed=40 + N + W)
+            frames = ocq_synth.fill_host(sc, 0, N + 3)
+            g = np.random.default_rng(N * 7 + W)
+            noise = g.integers(0, 256, size=frames.shape, dtype=np.uint8)
+            sel = g.random((H, W)) < 0.5
+            frames = np.where(sel[None, :, :, None], noise, frames)
+            train, test = frames[:N], frames[N:]
+            for d in (2, 3):
+                for T in (1, 3, 10, N):
+                    ow, om = oracle.run(train, d, T, PIXEL, 0, test)
+                    for v in range(O.ocq_tune_count(kern)):
+                        O.ocq_tune_select(kern, v)
+                        words, mask = gpu_model_and_mask(ocq, torch, train, test, d, T, PIXEL, 0)
+                        assert (words == ow).all(), (N, d, T, v)
+                        assert (mask == om).all(), (N, d, T, v)
+    finally:
+        O.ocq_tune_select(kern, saved)
+
+
 @pytest.mark.parametrize("b", [8, 16, 32, 64])
 @pytest.mark.parametrize("d", [1, 3, 4, 5])
 def test_block_tiled_classify(ocq, torch, b, d):
