@@ -576,7 +576,7 @@ def run_ours(args):
     if not args.no_next:
         result["next"] = next_measure(ocq, wl, sc, train, test, mask, stream, dev, peak)
     if not args.no_batched:
-        result["batched"] = batched_measure(ocq, dev, args.batched_reps)
+        result["batched"] = batched_measure(ocq, dev, args.batched_reps, peak)
     if not args.no_serving:
         result["serving"] = serving_measure(ocq, dev, args.serving_seconds)
     if not args.no_configs and world == 1:
@@ -664,7 +664,7 @@ def next_measure(ocq, wl, sc, train, test, mask, stream, dev, peak, reps=5):
     }
 
 
-def batched_measure(ocq, dev, reps):
+def batched_measure(ocq, dev, reps, peak_gbs):
     """The 64-stream preset (uneven resolutions, depths and regions): plain
     per-stream ocq_build_model + ocq_classify calls on one stream, against the
     batched form: one graph replay per run, the graph holding either one
@@ -678,6 +678,7 @@ def batched_measure(ocq, dev, reps):
     O = ocq.ocq
     descs = []
     px = 0
+    alg_bytes = 0  # frames and masks once, each stream's model written once and read once
     for wl in configs.batched_streams():
         sc = ocq_synth.make_scene(wl.scene_kind, wl.H, wl.W, wl.N, wl.F, wl.seed, wl.stream)
         tr = torch.empty((wl.N, wl.H, wl.W, 3), dtype=torch.uint8, device=dev)
@@ -687,6 +688,10 @@ def batched_measure(ocq, dev, reps):
         descs.append(dict(train=tr, test=te, mask=torch.empty((wl.F, wl.H, wl.W), dtype=torch.uint8, device=dev),
                           N=wl.N, H=wl.H, W=wl.W, kind=wl.region, block=wl.block, depth=wl.depth, T=wl.T, F=wl.F))
         px += (wl.N + wl.F) * wl.H * wl.W
+        hw = wl.H * wl.W
+        listed = wl.region == 2 and wl.depth in (4, 5) and wl.N // wl.T <= 8  # kept-leaf list model
+        model = hw * 16 if listed else O.ocq_model_footprint(wl.H, wl.W, wl.region, wl.block, wl.depth)
+        alg_bytes += wl.N * hw * 3 + wl.F * hw * 4 + model
     stream = torch.cuda.current_stream()
 
     def plain():
@@ -731,7 +736,13 @@ def batched_measure(ocq, dev, reps):
             "ratio": round(plain_ms / batched_ms, 3), "form": names[chosen],
             "form_ms": {names[k]: round(v, 3) for k, v in sorted(form_ms.items())},
             "autotune_s": round(tune_s, 2), "work_units_per_item": tiles, "items": n_items,
-            "graph_launches_per_run": 1}
+            "graph_launches_per_run": 1,
+            # the ">= 3x plain" target of this preset against the bytes it must move
+            "roofline_ms": round(alg_bytes / peak_gbs / 1e6, 3), "algorithmic_bytes": alg_bytes,
+            "roofline_frac": round(alg_bytes / peak_gbs / 1e6 / batched_ms, 3),
+            "target_3x_plain_ms": round(plain_ms / 3, 3),
+            "target_3x_met": plain_ms / batched_ms >= 3.0,
+            "target_3x_reachable": plain_ms / 3 >= alg_bytes / peak_gbs / 1e6}
 
 
 def _serve_run(O, streams, bufs, fps, budget, n_cameras, frames_per_camera, pool, mask_slots, speed,
