@@ -708,10 +708,10 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
       const int k = d.N / d.T;
       h.km = k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : k <= 8 ? 8 : 0;
       h.kl = (d.depth == 4 || d.depth == 5) && h.km > 0 ? (h.km < 2 ? 2 : h.km) : 0;
-      // a list model (no rows) where every classify item can read the index
-      list_only[s] = h.kl > 0 && h.tb && list_model_applies(h.kind, d.depth, d.N, d.T);
       h.tb = d.F > 0 && h.hw % 4 == 0 &&
              ((reinterpret_cast<uintptr_t>(d.test) | reinterpret_cast<uintptr_t>(d.mask)) & 3) == 0;
+      // a list model (no rows) where every classify item can read the index
+      list_only[s] = h.kl > 0 && h.tb && list_model_applies(h.kind, d.depth, d.N, d.T);
     }
     if (h.kind == OCQ_REGION_BLOCK && h.block % 4 == 0 && d.W % 4 == 0 && d.F > 0 &&
         ((reinterpret_cast<uintptr_t>(d.test) | reinterpret_cast<uintptr_t>(d.mask)) & 3) == 0) {
