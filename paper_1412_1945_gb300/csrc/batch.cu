@@ -546,9 +546,9 @@ static ocq_status enqueue_branches(ocq_batch *b, cudaStream_t cs) {
 }
 
 // Grouped form: one launch per kernel body and template over all streams it
-// covers (grouped.cu), chained per class of streams (whole frame, blocks,
-// pixels at depth <= 3, pixels at depth 4-5) on one branch each; streams
-// outside those bodies run their plain kernels on branches of their own.
+// covers (grouped.cu), chained on one branch (each class's builds before its
+// classification); streams outside those bodies run their plain kernels on
+// branches of their own.
 static ocq_status plan_grouped(ocq_batch *b) {
   if (b->gplanned) return OCQ_OK;
   std::vector<GStreamIn> in;

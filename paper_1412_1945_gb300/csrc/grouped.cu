@@ -315,30 +315,11 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
   fallback.clear();
   // launch key -> index in `out`, created in the order the phases run
   std::vector<GLaunch> L;
-  // each class's streams dealt to kGroupSplit branches, largest first
-  std::vector<int> share(in.size(), 0);
-  {
-    std::vector<int> order(in.size());
-    for (size_t i = 0; i < in.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-      return (int64_t)in[x].H * in[x].W * (in[x].N + in[x].F) > (int64_t)in[y].H * in[y].W * (in[y].N + in[y].F);
-    });
-    int dealt[GB_COUNT] = {0, 0, 0, 0};
-    for (int i : order) {
-      const GStreamIn &x = in[i];
-      const int cls = x.kind == OCQ_REGION_FRAME ? GB_FRAME
-                      : x.kind == OCQ_REGION_BLOCK ? GB_BLOCK
-                      : x.depth <= 3 ? GB_PIXEL : GB_PIXEL_DEEP;
-      share[i] = dealt[cls]++ % kGroupSplit;
-    }
-  }
-  int cur = 0;  // the stream being planned
-  auto launch = [&](int kind, int a, int b, int cls) -> GLaunch & {
-    const int branch = cls * kGroupSplit + share[cur];
+  auto launch = [&](int kind, int a, int b) -> GLaunch & {
     for (GLaunch &x : L)
-      if (x.kind == kind && x.a == a && x.b == b && x.branch == branch) return x;
+      if (x.kind == kind && x.a == a && x.b == b) return x;
     GLaunch x;
-    x.kind = kind, x.a = a, x.b = b, x.branch = branch;
+    x.kind = kind, x.a = a, x.b = b, x.branch = 0;
     L.push_back(x);
     return L.back();
   };
@@ -357,7 +338,6 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
   };
   const int64_t sms = sm_count();
   for (int i = 0; i < (int)in.size(); ++i) {
-    cur = i;
     const GStreamIn &x = in[i];
     const int64_t hw = (int64_t)x.H * x.W;
     const int d = x.depth;
@@ -369,14 +349,14 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
       }
       GSeg o = base(x, x.train);
       o.aux = cdiv64(hw, kGroupOccChunk), o.vg = o.aux * x.N;
-      launch(GK_OCC, d, 0, GB_FRAME).segs.push_back(o);
+      launch(GK_OCC, d, 0).segs.push_back(o);
       GSeg m = base(x, x.train);
       m.units = wpr32(d), m.vg = std::max<int64_t>(1, std::min<int64_t>(64, cdiv64(m.units, 256)));
-      launch(GK_MERGE, 0, 0, GB_FRAME).segs.push_back(m);
+      launch(GK_MERGE, 0, 0).segs.push_back(m);
       if (x.F > 0) {
         GSeg c = base(x, x.test);
         c.units = (int64_t)x.F * hw;
-        launch(GK_CLS_FRAME, d, 0, GB_FRAME).segs.push_back(c);
+        launch(GK_CLS_FRAME, d, 0).segs.push_back(c);
       }
     } else if (x.kind == OCQ_REGION_BLOCK) {
       const bool cls_ok = x.F == 0 || (x.block % 4 == 0 && x.W % 4 == 0 && (tm & 3) == 0);
@@ -390,15 +370,15 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
       GSeg bld = base(x, x.train);
       if (fs) {
         bld.units = x.block == 8 && d == 5 ? cdiv64(x.H, 8) * (x.W / 8) : cdiv64(x.H, 16) * cdiv64(x.W, 16);
-        launch(GK_BLOCK_FS, d, x.block, GB_BLOCK).segs.push_back(bld);
+        launch(GK_BLOCK_FS, d, x.block).segs.push_back(bld);
       } else if (tile) {
         bld.units = cdiv64(x.H, 16) * cdiv64(x.W, 16);
-        launch(GK_BLOCK_TILE, d, x.block, GB_BLOCK).segs.push_back(bld);
+        launch(GK_BLOCK_TILE, d, x.block).segs.push_back(bld);
       } else {
         const int npx = x.block * x.block;
         const int ppl = npx <= 32 ? 1 : npx <= 64 ? 2 : npx <= 128 ? 4 : 8;
         bld.units = region_count(x.H, x.W, OCQ_REGION_BLOCK, x.block);
-        launch(GK_BLOCK_WARP, d, ppl, GB_BLOCK).segs.push_back(bld);
+        launch(GK_BLOCK_WARP, d, ppl).segs.push_back(bld);
       }
       if (x.F > 0) {
         GSeg c = base(x, x.test);
@@ -412,28 +392,28 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
         const int fchunk = (x.F + chunks - 1) / chunks;
         chunks = (x.F + fchunk - 1) / fchunk;
         c.aux = tiles, c.aux2 = fchunk, c.units = tiles * chunks;
-        launch(GK_BLOCK_TB, d, 0, GB_BLOCK).segs.push_back(c);
+        launch(GK_BLOCK_TB, d, 0).segs.push_back(c);
       }
     } else {
       const uintptr_t all = tm | reinterpret_cast<uintptr_t>(x.train);
       if (d <= 3 && x.N <= 255 && x.T <= 255 && hw % 1024 == 0 && (all & 15) == 0 && x.model) {
         GSeg bld = base(x, x.train);
         bld.units = hw / 128;
-        launch(GK_PIX_WS_BUILD, d, 0, GB_PIXEL).segs.push_back(bld);
+        launch(GK_PIX_WS_BUILD, d, 0).segs.push_back(bld);
         if (x.F > 0) {
           GSeg c = base(x, x.test);
           c.units = hw / 1024;
-          launch(GK_PIX_WS_CLS, d, 0, GB_PIXEL).segs.push_back(c);
+          launch(GK_PIX_WS_CLS, d, 0).segs.push_back(c);
         }
       } else if ((d == 4 || d == 5) && x.N <= 255 && x.km > 0 && x.kl > 0 && x.kept &&
                  (x.F == 0 || (hw % 4 == 0 && (tm & 3) == 0))) {
         GSeg bld = base(x, x.train);
         bld.vg = cdiv64(hw, 128);
-        launch(GK_PIX_MG, d, x.km, GB_PIXEL_DEEP).segs.push_back(bld);
+        launch(GK_PIX_MG, d, x.km).segs.push_back(bld);
         if (x.F > 0) {
           GSeg c = base(x, x.test);
           c.units = cdiv64(hw, 128);
-          launch(GK_PIX_LIST, d, x.kl, GB_PIXEL_DEEP).segs.push_back(c);
+          launch(GK_PIX_LIST, d, x.kl).segs.push_back(c);
         }
       } else {
         fallback.push_back(i);

@@ -52,14 +52,14 @@ enum GroupKind : int {
   GK_COUNT         // serving window: a camera's new leaf bitsets into its ring and counts
 };
 
-// Classes of streams; each class's streams are dealt, largest first, to
-// kGroupSplit branches of the batch graph: branch = class * kGroupSplit +
-// share.  One branch per class measured fastest (two per class, so that one
-// half's classification could run beside the other half's builds: 9.6 ms
-// against 7.7 ms on the 64-stream preset).
-enum GroupBranch : int { GB_FRAME = 0, GB_BLOCK, GB_PIXEL, GB_PIXEL_DEEP, GB_COUNT };
-constexpr int kGroupSplit = 1;
-constexpr int kGroupBranches = GB_COUNT * kGroupSplit;
+// The grouped launches chain on one branch of the batch graph, in GroupKind
+// order (so each class's builds come before its classification).  The
+// classes (whole frame, blocks, pixels d <= 3, pixels d = 4-5) on concurrent
+// branches measured slower and uneven from run to run (7.7-9.8 ms against
+// 7.1 ms on the 64-stream preset): the large grouped kernels of different
+// classes contend for the SMs.  Streams no grouped body takes run their plain
+// kernels on branches of their own.
+constexpr int kGroupBranches = 1;
 
 struct GLaunch {
   int kind = 0, a = 0, b = 0, branch = 0;
