@@ -36,7 +36,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="CPU-baseline budget (oracle)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -573,11 +573,13 @@ def run_ours(args):
     # on some hosts: the copies are bound by the host link)
     if not args.no_e2e:
         result["e2e"] = e2e_measure(ocq, wl, train, test, mask, stream, args, dist, dev, world)
-    if not args.no_next:
+    # the per-GPU sections (one GPU's batched, serving and NEXT figures) run at
+    # N = 1; a run over N GPUs reports the replicated step and e2e
+    if not args.no_next and world == 1:
         result["next"] = next_measure(ocq, wl, sc, train, test, mask, stream, dev, peak)
-    if not args.no_batched:
+    if not args.no_batched and world == 1:
         result["batched"] = batched_measure(ocq, dev, args.batched_reps, peak)
-    if not args.no_serving:
+    if not args.no_serving and world == 1:
         result["serving"] = serving_measure(ocq, dev, args.serving_seconds)
     if not args.no_configs and world == 1:
         result["configs"] = presets_section(ocq, dev, peak, min(5.0, args.cpu_seconds),
