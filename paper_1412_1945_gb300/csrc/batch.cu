@@ -36,6 +36,7 @@ enum : int32_t {
   OP_BUILD_BLOCK,      // build_block_body         (blocks, depth <= 5, b > 16)
   OP_BUILD_BLOCK_WARP, // build_block_warp_body    (blocks, depth <= 5, b <= 16): regions [vb, aux)
   OP_BUILD_PIXEL_MG,   // build_pixel_mg_body      (pixels): 32-pixel tiles [vb, aux)
+  OP_BUILD_BLOCK_TILE, // build_block_tile_body    (blocks, direct tables): 16x16 tiles [vb, aux)
   OP_CLS_FRAME,        // classify_frame_body      (whole frame, depth <= 6)
   OP_CLS_PIXEL_TB,     // classify_pixel_tb_body   (pixels, H*W % 4 == 0): 128-pixel tiles [vb, aux)
   OP_CLS_BLOCK_TB,     // classify_block_tb_body   (blocks, b % 4 == 0, W % 4 == 0): tiles [vb, aux)
@@ -58,6 +59,7 @@ struct BStream {
   int32_t nseg;        // block classify (L1 body): 128-pixel segments per pixel row
   int32_t stage;       // pixel classify, depth <= 3: rows staged in shared memory (else L1)
   int32_t kl;          // pixel regions, depth 4-5, candidates: kept-leaf list length (0: no index)
+  int32_t tile;        // block build over 16x16 warp tiles with direct tables (build_block_tile_body)
   uint16_t *kept;      // kept-leaf index (kl > 0): written by the build, read by the classify
 };
 
@@ -116,6 +118,30 @@ __device__ __noinline__ void block_warp_dispatch(const BStream &S, int64_t r0, i
     case 3: block_warp_item_d<3>(S, r0, r1, smem); break;
     case 4: block_warp_item_d<4>(S, r0, r1, smem); break;
     default: block_warp_item_d<5>(S, r0, r1, smem); break;
+  }
+}
+
+// Warp tiles: warp w of the CTA takes tiles t0 + w, t0 + w + 8, ... < t1 with
+// its own table (zeroed here: the shared memory held other items' data).
+template <int D, int B>
+__device__ __noinline__ void block_tile_item(const BStream &S, int64_t t0, int64_t t1, uint8_t *smem) {
+  using C = BlockTileCfg<D, B>;
+  static_assert(C::DIRECT, "the persistent kernel hosts the direct-table tiles only");
+  uint8_t *wsm = smem + (threadIdx.x >> 5) * C::WARP_SMEM;
+  for (int i = threadIdx.x & 31; i < C::WARP_SMEM / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
+  __syncwarp();
+  build_block_tile_body<D, B, C::PF>(S.train, S.N, S.H, S.W, S.bw, (uint32_t)S.T, S.model, t0 + (threadIdx.x >> 5),
+                                     t1, kBatchThreads / 32, wsm);
+}
+
+__device__ __noinline__ void block_tile_dispatch(const BStream &S, int64_t t0, int64_t t1, uint8_t *smem) {
+  if (S.block == 8) {
+    if (S.depth == 2) block_tile_item<2, 8>(S, t0, t1, smem);
+    else block_tile_item<3, 8>(S, t0, t1, smem);
+  } else {
+    if (S.depth == 2) block_tile_item<2, 16>(S, t0, t1, smem);
+    else if (S.depth == 3) block_tile_item<3, 16>(S, t0, t1, smem);
+    else block_tile_item<4, 16>(S, t0, t1, smem);
   }
 }
 
@@ -235,6 +261,9 @@ __device__ void run_item(const BStream &S, const BItem &it, uint8_t *smem) {
     case OP_BUILD_PIXEL_MG:
       pixel_mg_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux, smem);
       return;
+    case OP_BUILD_BLOCK_TILE:
+      block_tile_dispatch(S, it.vb, it.aux, smem);
+      return;
     case OP_CLS_PIXEL_TB:
       if (S.kl)
         pixel_list_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux);
@@ -295,6 +324,13 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BStream *
   }
 }
 
+// A warp's table bytes of the direct-table tile build (depth <= 3, or 4 with
+// 16 x 16 blocks).
+static size_t block_tile_warp_smem(int d, int b) {
+  if (b == 8) return d == 2 ? BlockTileCfg<2, 8>::WARP_SMEM : BlockTileCfg<3, 8>::WARP_SMEM;
+  return d == 2 ? BlockTileCfg<2, 16>::WARP_SMEM : d == 3 ? BlockTileCfg<3, 16>::WARP_SMEM : BlockTileCfg<4, 16>::WARP_SMEM;
+}
+
 // Shared memory one item of stream S needs (bytes).
 static size_t item_smem(const BStream &h) {
   const int d = h.depth;
@@ -302,7 +338,9 @@ static size_t item_smem(const BStream &h) {
   if (h.kind == OCQ_REGION_FRAME) {
     if (d <= 6) need = std::max<size_t>(need, (size_t)h.wpr * 4 * (d <= 4 ? 32 : 1));  // occ row / replicated row
   } else if (h.kind == OCQ_REGION_BLOCK) {
-    if (h.ppl > 0)
+    if (h.tile)
+      need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * block_tile_warp_smem(d, h.block));
+    else if (h.ppl > 0)
       need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * std::min(1 << (3 * d), 1024) * 4);
     else
       need = std::max<size_t>(need, (size_t)h.wpr * (h.P + 2) * 4);
@@ -415,7 +453,12 @@ static ocq_status plan_items(ocq_batch *b) {
                    [&](int x, int y) { return hs[x].hw * hs[x].N > hs[y].hw * hs[y].N; });
   for (int s : order) {
     BStream &st = hs[s];
-    if (st.kind == OCQ_REGION_BLOCK && st.ppl > 0) {
+    if (st.kind == OCQ_REGION_BLOCK && st.tile) {
+      constexpr int64_t kTilesPerItem = 32;  // 4 per warp
+      const int64_t tiles = cdiv(st.H, 16) * cdiv(st.W, 16);
+      for (int64_t t = 0; t < tiles; t += kTilesPerItem, ++st.n_build)
+        push(OP_BUILD_BLOCK_TILE, s, t, 0, std::min(tiles, t + kTilesPerItem));
+    } else if (st.kind == OCQ_REGION_BLOCK && st.ppl > 0) {
       constexpr int64_t kRegionsPerItem = 40;
       for (int64_t r = 0; r < st.R; r += kRegionsPerItem, ++st.n_build)
         push(OP_BUILD_BLOCK_WARP, s, r, 0, std::min(st.R, r + kRegionsPerItem));
@@ -721,6 +764,11 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
     if (h.kind == OCQ_REGION_BLOCK && block_warp_ok(d.N, d.H, d.W, h.block)) {
       const int npx = h.block * h.block;
       h.ppl = npx <= 32 ? 1 : npx <= 64 ? 2 : npx <= 128 ? 4 : 8;
+    }
+    {
+      SharedGpuScope shared;  // the form the batched plain kernels take
+      h.tile = h.kind == OCQ_REGION_BLOCK && (d.depth <= 3 || (d.depth == 4 && h.block == 16)) &&
+               block_tile_ok(d.N, d.H, d.W, h.block, d.depth, d.train);
     }
     b->hs.push_back(h);
     model_off[s] = bytes;

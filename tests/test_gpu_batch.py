@@ -46,6 +46,8 @@ SMALL_MIX = [
     (0, "bimodal", 12, 20, 30, 3, PIXEL, 0, 5, 2),  # floor(N/T) = 15 > 8: rows, no index
     (0, "bimodal", 16, 1024, 6, 4, PIXEL, 0, 1, 2),
     (0, "clusters", 31, 33, 11, 3, FRAME, 0, 1, 11),
+    (0, "sway", 40, 64, 9, 6, BLOCK, 8, 3, 4),      # W % 8 == 0: warp tiles (the persistent kernel's too)
+    (0, "clusters", 48, 80, 8, 5, BLOCK, 16, 4, 3),  # 16 x 16 at depth 4: direct-table tiles
 ]
 
 
