@@ -1,19 +1,20 @@
 // Batched form: many camera streams of uneven size, depth and region kind are
-// built (S1-S3, Sec. 3, Alg. 1-2) and classified (S4, Alg. 3) in ONE
-// persistent kernel launch, replayed from a CUDA graph.
+// built (S1-S3, Sec. 3, Alg. 1-2) and classified (S4, Alg. 3) by ONE replay
+// of a CUDA graph holding one of three forms: a persistent kernel over a work
+// list, the streams' plain kernels as concurrent branches, or grouped
+// launches per kernel body (grouped.cu).
 //
-// The work list holds the CTAs of the plain per-stream kernels as "virtual
-// CTAs" (vb of vg): each item runs the same device body the plain kernel runs
-// (build_bodies.cuh, classify_bodies.cuh), so every stream's result is the
-// plain path's result bit for bit, and each item is as efficient as a CTA of
-// the plain kernel.  Persistent CTAs (160 threads: four compute warps and a
-// copy warp for the bodies that stream frames) take items in list order from
-// an atomic counter.  Per stream, a merge waits for the stream's occupancy
-// items and classification for its build items; every waited-on item precedes
-// the waiter in the list, so it was taken by a running CTA, and each wait is
-// bounded (1 s) and records a timeout instead of spinning forever.  The
-// classification work per item (in 1024-pixel frame tiles) is chosen per
-// region kind by the autotuner (ocq_batch_autotune).
+// The persistent work list holds the CTAs of the plain per-stream kernels as
+// "virtual CTAs" (vb of vg) or warp ranges: each item runs a device body the
+// plain kernels run (build_bodies.cuh, classify_bodies.cuh), so every stream's
+// result is the plain path's result bit for bit.  Persistent CTAs of 256
+// threads take items in list order from an atomic counter.  Per stream, a
+// merge waits for the stream's occupancy items and classification for its
+// build items; every waited-on item precedes the waiter in the list, so it was
+// taken by a running CTA, and each wait is bounded (1 s) and records a timeout
+// instead of spinning forever.  The classification work per item (in
+// 1024-pixel frame tiles) is chosen per region kind by the autotuner
+// (ocq_batch_autotune), which also picks the fastest of the three forms.
 #include <algorithm>
 #include <cstring>
 #include <map>
