@@ -7,21 +7,21 @@
 //   * after classification frame t enters a ring of the last N frames;
 //   * when (t+1) % K == 0 the ring is merged again: M_(t+1)/K = merge(ring).
 // So M_k is the merged model of global frames [kK, kK+N-1] (training frames
-// first).  A camera's per-frame work (classify, ring copy) is ordered on its
-// own high-priority CUDA stream and its builds on a low-priority one, joined
-// by events: a re-merge starts once the window's last frame is in the ring,
-// and the camera's next frame waits for it.  Cameras run concurrently, so work
-// of frames that arrive while others are on the GPU overlaps on the device,
-// and one camera's long re-merge yields the SMs to other cameras' frames.
-// The window keeps what the merge needs of those frames, not the frames
-// (window.cu): whole-frame cameras a ring of N leaf bitsets plus resident
-// per-leaf counts, updated as each frame enters (re-merge = a threshold pass);
-// pixel and block cameras of depth <= 5 a ring of per-pixel u16 leaf codes
-// (re-merge = counting the codes, no frame is read again).  Both re-merge the
-// model in place on the camera stream, after the frames that read the old one.
+// first).  The window keeps what the merge needs of those frames, not the
+// frames (window.cu): whole-frame cameras a ring of N leaf bitsets plus
+// resident per-leaf counts, updated as each frame enters (re-merge = a
+// threshold pass); pixel and block cameras of depth <= 5 a ring of per-pixel
+// u16 leaf codes (re-merge = counting the codes, no frame is read again).
+// Frames of those cameras run in ticks on the server's high-priority stream
+// (continuous batching): a tick classifies every camera's frames that arrived
+// by grouped launches, a camera's frames of the tick against one read of its
+// model (the classify also writes a code window's slots), then enters the
+// frames into their windows and re-merges in place the cameras whose period
+// ends; ticks follow in stream order, so frame t always meets M_floor(t/K).
 // Cameras outside those forms (deeper, N > 255, blocks wider than 16, or a
-// whole-frame bitset larger than a frame) keep the N frames and rebuild with
-// ocq_build_model on a low-priority stream.
+// whole-frame bitset larger than a frame) keep the N frames, classify frame by
+// frame on their own high-priority stream and rebuild with ocq_build_model on
+// a low-priority one, joined by events.
 // Admission reserves a camera's footprint (window, model, build scratch; the
 // frame ring also a second model) against an HBM budget and returns OCQ_EBUSY
 // when it does not fit; released cameras return their share.  A frame's
