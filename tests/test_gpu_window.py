@@ -182,3 +182,45 @@ def test_batching_window_holds_frames_and_keeps_the_semantics(cuda_ready):
             assert (model == oracle.build_model(hosts[i][k * K:k * K + N], d, T, region, block)).all(), i
     finally:
         srv.destroy()
+
+
+def test_array_submits_and_polls(cuda_ready):
+    """The numpy-array bindings (device addresses in uint64 arrays, completions
+    as a structured array) submit and report the same frames as the list
+    forms: every frame once, its tag back, masks under the window semantics."""
+    import time
+
+    import torch
+
+    O = cuda_ready.ocq
+    cams = [CAMERAS[3], CAMERAS[6], CAMERAS[0]]  # block codes, pixel codes, whole-frame bitsets
+    srv = O.ocq_server_create(1 << 30, len(cams))
+    hosts, devs, masks, ids = [], [], [], []
+    try:
+        for i, cam in enumerate(cams):
+            scene, H, W, region, block, d, T, N, K, F, form = cam
+            host = ocq_synth.fill_host(ocq_synth.make_scene(scene, H, W, N, F, 7700 + i), 0, N + F)
+            hosts.append(host)
+            devs.append(torch.from_numpy(host).cuda())
+            masks.append(torch.full((F, H, W), 9, dtype=torch.uint8, device="cuda"))
+        torch.cuda.synchronize()
+        for i, cam in enumerate(cams):
+            scene, H, W, region, block, d, T, N, K, F, form = cam
+            ids.append(O.ocq_server_admit(srv, H, W, region, block, d, T, N, K, devs[i][:N].contiguous()))
+        order = [(i, t) for t in range(max(c[9] for c in cams)) for i, c in enumerate(cams) if t < c[9]]
+        O.ocq_server_submit_arrays(srv, np.array([ids[i] for i, _ in order], dtype=np.int32),
+                                   np.array([devs[i][cams[i][7] + t].data_ptr() for i, t in order], dtype=np.uint64),
+                                   np.array([masks[i][t].data_ptr() for i, t in order], dtype=np.uint64),
+                                   np.array([1000 * i + t for i, t in order], dtype=np.uint64))
+        got = []
+        deadline = time.monotonic() + 20.0
+        while sum(len(g) for g in got) < len(order) and time.monotonic() < deadline:
+            got.append(O.ocq_server_poll_array(srv))
+            time.sleep(0.002)
+        done = np.concatenate(got)
+        assert sorted(done["tag"].tolist()) == sorted(1000 * i + t for i, t in order)
+        assert (done["done_s"] >= done["arrival_s"]).all()
+        for i, cam in enumerate(cams):
+            assert (masks[i].cpu().numpy() == _window_oracle(hosts[i], cam)).all(), i
+    finally:
+        srv.destroy()
