@@ -460,19 +460,22 @@ void ocq_server_destroy(ocq_server *server);
  *                            frames: warps over 16 x 16 pixel tiles (four 8 x 8 or
  *                            one 16 x 16 region, 8 pixels per lane; direct leaf
  *                            tables at depth <= 3, two-level prefix tables
- *                            deeper), or the N frames split over the 8 warps of a
- *                            CTA (shared u8 counters per region, a leaf bitset per
- *                            warp for the frame it counts); every other block
- *                            build runs one warp per region.  1 (default) picks
- *                            by shape and size: frames split for 16 x 16 at depth
- *                            5, 8 x 8 at depth 4, 8 x 8 at depth 5 up to 16384
- *                            regions and any frame of fewer than 1024 tiles;
- *                            tiles for depth <= 3 and 16 x 16 at depth 4; one warp
- *                            per region for 8 x 8 at depth 5 above 16384
- *                            regions.  0 one warp per region always; 2 frames
- *                            split wherever they apply; 3 tiles wherever they
- *                            apply (8 x 8 at depth 5: one warp per region);
- *                            params = {variant, 0, ...}
+ *                            deeper); the N frames split over the 8 warps of a CTA
+ *                            (shared u8 counters per region, a leaf bitset per
+ *                            warp for the frame it counts); for 8 x 8 at depth 5
+ *                            one region per warp with two-level prefix tables;
+ *                            every other block build runs one warp per region
+ *                            with a hashed leaf table.  1 (default) picks by
+ *                            shape and size: the region tables for 8 x 8 at depth
+ *                            5 (frames split below 1024 tiles); frames split for
+ *                            16 x 16 at depth 5, 8 x 8 at depth 4 and any frame of
+ *                            fewer than 1024 tiles; tiles for depth <= 3 and
+ *                            16 x 16 at depth 4; inside the batched forms tiles
+ *                            and region tables only.  0 one warp per region
+ *                            always; 2 frames split wherever they apply; 3 tiles
+ *                            wherever they apply (8 x 8 at depth 5: one warp per
+ *                            region); 4 the region tables for 8 x 8 at depth 5
+ *                            (else one warp per region); params = {variant, 0, ...}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5

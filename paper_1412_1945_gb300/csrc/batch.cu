@@ -38,6 +38,7 @@ enum : int32_t {
   OP_BUILD_BLOCK_WARP, // build_block_warp_body    (blocks, depth <= 5, b <= 16): regions [vb, aux)
   OP_BUILD_PIXEL_MG,   // build_pixel_mg_body      (pixels): 32-pixel tiles [vb, aux)
   OP_BUILD_BLOCK_TILE, // build_block_tile_body    (blocks, direct tables): 16x16 tiles [vb, aux)
+  OP_BUILD_BLOCK_R8,   // build_block_r8_body      (8x8 blocks, depth 5): regions [vb, aux)
   OP_CLS_FRAME,        // classify_frame_body      (whole frame, depth <= 6)
   OP_CLS_PIXEL_TB,     // classify_pixel_tb_body   (pixels, H*W % 4 == 0): 128-pixel tiles [vb, aux)
   OP_CLS_BLOCK_TB,     // classify_block_tb_body   (blocks, b % 4 == 0, W % 4 == 0): tiles [vb, aux)
@@ -61,6 +62,7 @@ struct BStream {
   int32_t stage;       // pixel classify, depth <= 3: rows staged in shared memory (else L1)
   int32_t kl;          // pixel regions, depth 4-5, candidates: kept-leaf list length (0: no index)
   int32_t tile;        // block build over 16x16 warp tiles with direct tables (build_block_tile_body)
+  int32_t r8;          // block build, 8x8 at depth 5, one region per warp, two-level tables
   uint16_t *kept;      // kept-leaf index (kl > 0): written by the build, read by the classify
 };
 
@@ -133,6 +135,14 @@ __device__ __noinline__ void block_tile_item(const BStream &S, int64_t t0, int64
   __syncwarp();
   build_block_tile_body<D, B, C::PF>(S.train, S.N, S.H, S.W, S.bw, (uint32_t)S.T, S.model, t0 + (threadIdx.x >> 5),
                                      t1, kBatchThreads / 32, wsm);
+}
+
+__device__ __noinline__ void block_r8_item(const BStream &S, int64_t r0, int64_t r1, uint8_t *smem) {
+  uint8_t *wsm = smem + (threadIdx.x >> 5) * BlockR8Cfg::WARP_SMEM;
+  for (int i = threadIdx.x & 31; i < BlockR8Cfg::WARP_SMEM / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
+  __syncwarp();
+  build_block_r8_body(S.train, S.N, S.H, S.W, S.bw, (uint32_t)S.T, S.model, r0 + (threadIdx.x >> 5), r1,
+                      kBatchThreads / 32, wsm);
 }
 
 __device__ __noinline__ void block_tile_dispatch(const BStream &S, int64_t t0, int64_t t1, uint8_t *smem) {
@@ -265,6 +275,9 @@ __device__ void run_item(const BStream &S, const BItem &it, uint8_t *smem) {
     case OP_BUILD_BLOCK_TILE:
       block_tile_dispatch(S, it.vb, it.aux, smem);
       return;
+    case OP_BUILD_BLOCK_R8:
+      block_r8_item(S, it.vb, it.aux, smem);
+      return;
     case OP_CLS_PIXEL_TB:
       if (S.kl)
         pixel_list_dispatch(S, it.vb + (threadIdx.x >> 5), it.aux);
@@ -339,7 +352,9 @@ static size_t item_smem(const BStream &h) {
   if (h.kind == OCQ_REGION_FRAME) {
     if (d <= 6) need = std::max<size_t>(need, (size_t)h.wpr * 4 * (d <= 4 ? 32 : 1));  // occ row / replicated row
   } else if (h.kind == OCQ_REGION_BLOCK) {
-    if (h.tile)
+    if (h.r8)
+      need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * BlockR8Cfg::WARP_SMEM);
+    else if (h.tile)
       need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * block_tile_warp_smem(d, h.block));
     else if (h.ppl > 0)
       need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * std::min(1 << (3 * d), 1024) * 4);
@@ -454,7 +469,11 @@ static ocq_status plan_items(ocq_batch *b) {
                    [&](int x, int y) { return hs[x].hw * hs[x].N > hs[y].hw * hs[y].N; });
   for (int s : order) {
     BStream &st = hs[s];
-    if (st.kind == OCQ_REGION_BLOCK && st.tile) {
+    if (st.kind == OCQ_REGION_BLOCK && st.r8) {
+      constexpr int64_t kRegionsPerItem = 64;  // 8 per warp
+      for (int64_t r = 0; r < st.R; r += kRegionsPerItem, ++st.n_build)
+        push(OP_BUILD_BLOCK_R8, s, r, 0, std::min(st.R, r + kRegionsPerItem));
+    } else if (st.kind == OCQ_REGION_BLOCK && st.tile) {
       constexpr int64_t kTilesPerItem = 32;  // 4 per warp
       const int64_t tiles = cdiv(st.H, 16) * cdiv(st.W, 16);
       for (int64_t t = 0; t < tiles; t += kTilesPerItem, ++st.n_build)
@@ -770,6 +789,7 @@ ocq_status ocq_batch_create(const ocq_stream_desc *streams, int n, void *stream,
       SharedGpuScope shared;  // the form the batched plain kernels take
       h.tile = h.kind == OCQ_REGION_BLOCK && (d.depth <= 3 || (d.depth == 4 && h.block == 16)) &&
                block_tile_ok(d.N, d.H, d.W, h.block, d.depth, d.train);
+      h.r8 = h.kind == OCQ_REGION_BLOCK && block_r8_ok(d.N, d.H, d.W, h.block, d.depth, d.train);
     }
     b->hs.push_back(h);
     model_off[s] = bytes;

@@ -88,6 +88,18 @@ __global__ void __launch_bounds__(BlockTileCfg<D, B>::WPC * 32, BlockTileCfg<D, 
                                   (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), ntiles, nw, wsm);
 }
 
+__global__ void __launch_bounds__(256, 4) build_block_r8_kernel(const uint8_t *__restrict__ frames, int N, int H, int W,
+                                                             int bw, uint32_t T, uint32_t *__restrict__ model,
+                                                             int64_t R) {
+  extern __shared__ __align__(16) uint8_t r8_smem[];
+  constexpr int WB = BlockR8Cfg::WARP_SMEM;
+  uint8_t *wsm = r8_smem + (threadIdx.x >> 5) * WB;
+  for (int i = threadIdx.x & 31; i < WB / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
+  __syncwarp();
+  build_block_r8_body(frames, N, H, W, bw, T, model, (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), R,
+                      (int64_t)gridDim.x * 8, wsm);
+}
+
 template <int D, int B>
 __global__ void __launch_bounds__(256, BlockFsCfg<D, B>::MINB) build_block_fs_kernel(const uint8_t *__restrict__ frames, int N, int H, int W,
                                                                int bw, uint32_t T, uint32_t *__restrict__ model,
@@ -641,23 +653,27 @@ static ocq_status launch_block_warp_ppl(const uint8_t *frames, int N, ocq_model 
 
 // Block builds for b in {8, 16} (depth 2-5, N <= 255, W % 8 == 0, 8-byte
 // aligned frames, frame offsets within 32 bits): warps over 16 x 16 pixel
-// tiles, or the frames split over the 8 warps of a CTA.  Form 1 (the default)
-// picks by shape and size, from CUDA-event times of 30-frame builds at
-// 320x240 .. 1920x1080 (cluster and sway scenes):
+// tiles, the frames split over the 8 warps of a CTA, or (8 x 8 at depth 5)
+// one region per warp with two-level tables.  Form 1 (the default) picks by
+// shape and size, from CUDA-event times of 30-frame builds at 320x240 ..
+// 1920x1080 (cluster and sway scenes):
+//   * 8 x 8 at depth 5: the two-level region tables (1080p 0.168 / 0.198 ms
+//     against 0.224 / 0.274 ms one warp per region; 720p 0.106 against 0.133
+//     frames split), frames split below 1024 tiles (320x240: 0.025 against
+//     0.036 ms);
 //   * frames split: 16 x 16 at depth 5 (1080p 0.19 against 0.25 ms for the
-//     tiles), 8 x 8 at depth 4 (1080p 0.15 against 0.17 ms), 8 x 8 at depth 5
-//     up to 16384 regions (720p 0.13 against 0.145 ms one warp per region;
-//     at 1080p one warp per region is 0.22 against 0.27 ms on the cluster
-//     scene), and every frame of fewer than 1024 tiles (320x240: 1.2-2.5x),
-//     where the tiles leave most SMs idle;
+//     tiles), 8 x 8 at depth 4 (1080p 0.15 against 0.17 ms), and every frame
+//     of fewer than 1024 tiles (320x240: 1.2-2.5x), where the tiles leave most
+//     SMs idle;
 //   * warp tiles: depth <= 3, and 16 x 16 at depth 4 (1080p 0.12 against
-//     0.14 ms);
-//   * one warp per region: 8 x 8 at depth 5 above 16384 regions.
+//     0.14 ms).
 // Where other streams' kernels share the GPU (the batched forms), form 1
-// takes the forms that do the least work per region instead: tiles, and one
-// warp per region for 8 x 8 at depth 5 (64-stream mix, 8 x 8 depth 4 class:
-// 0.32 against 0.36 ms in the graph of branches).
-// Forms 0, 2 and 3 force one warp per region, frames split and tiles.
+// takes the forms that do the least work per region instead: the tiles, and
+// the region tables for 8 x 8 at depth 5 (64-stream mix, 8 x 8 d = 4 class in
+// the graph of branches: frames split 0.36, tiles 0.32 ms).
+// Forms 0, 2, 3 and 4 force one warp per region, frames split, tiles (8 x 8
+// at depth 5: one warp per region) and the region tables (8 x 8 at depth 5
+// only).
 static int g_block_form = 1;
 static thread_local bool t_shared_gpu = false;
 SharedGpuScope::SharedGpuScope() : prev(t_shared_gpu) { t_shared_gpu = true; }
@@ -666,15 +682,16 @@ static bool block_shape_ok(int N, int H, int W, int b, int depth, const void *fr
   return (b == 8 || b == 16) && depth >= 2 && depth <= 5 && N <= 255 && W % 8 == 0 &&
          (reinterpret_cast<uintptr_t>(frames) & 7) == 0 && (int64_t)H * W * 3 <= (int64_t)UINT32_MAX;
 }
-enum BlockBuildKind { BB_WARP = 0, BB_TILE, BB_FS };
+enum BlockBuildKind { BB_WARP = 0, BB_TILE, BB_FS, BB_R8 };
 static BlockBuildKind block_build_kind(int N, int H, int W, int b, int depth, const void *frames) {
   if (g_block_form == 0 || !block_shape_ok(N, H, W, b, depth, frames)) return BB_WARP;
   if (g_block_form == 2) return BB_FS;
-  if (g_block_form == 3 || t_shared_gpu) return b == 8 && depth == 5 ? BB_WARP : BB_TILE;
+  if (g_block_form == 4) return b == 8 && depth == 5 ? BB_R8 : BB_WARP;
+  if (g_block_form == 3) return b == 8 && depth == 5 ? BB_WARP : BB_TILE;
   const int64_t tiles = (int64_t)((H + 15) / 16) * ((W + 15) / 16);
-  const int64_t regions = (int64_t)((H + b - 1) / b) * ((W + b - 1) / b);
+  if (b == 8 && depth == 5) return !t_shared_gpu && tiles < 1024 ? BB_FS : BB_R8;
+  if (t_shared_gpu) return BB_TILE;
   if (tiles < 1024 || (b == 16 && depth == 5) || (b == 8 && depth == 4)) return BB_FS;
-  if (b == 8 && depth == 5) return regions <= 16384 ? BB_FS : BB_WARP;
   return BB_TILE;
 }
 bool block_tile_ok(int N, int H, int W, int b, int depth, const void *frames) {
@@ -683,12 +700,36 @@ bool block_tile_ok(int N, int H, int W, int b, int depth, const void *frames) {
 bool block_fs_ok(int N, int H, int W, int b, int depth, const void *frames) {
   return block_build_kind(N, H, W, b, depth, frames) == BB_FS;
 }
-int block_build_form_count() { return 4; }
+bool block_r8_ok(int N, int H, int W, int b, int depth, const void *frames) {
+  return block_build_kind(N, H, W, b, depth, frames) == BB_R8;
+}
+int block_build_form_count() { return 5; }
 int block_build_form_selected() { return g_block_form; }
 bool block_build_form_select(int v) {
-  if (v < 0 || v > 3) return false;
+  if (v < 0 || v > 4) return false;
   g_block_form = v;
   return true;
+}
+
+static ocq_status launch_block_r8(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  constexpr size_t smem = (size_t)8 * BlockR8Cfg::WARP_SMEM;
+  static int cap = 0;
+  if (!cap) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(build_block_r8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, build_block_r8_kernel, 256, smem);
+    cap = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+  }
+  const int bw = m->W / 8;
+  const int64_t R = (int64_t)((m->H + 7) / 8) * bw;
+  const int64_t ctas = (R + 7) / 8;
+  build_block_r8_kernel<<<(unsigned)(ctas < cap ? ctas : cap), 256, smem, st>>>(frames, N, m->H, m->W, bw,
+                                                                               (uint32_t)m->T, m->bits, R);
+  count_launch();
+  return cuda_status(cudaGetLastError(), "build_block_r8_kernel");
 }
 
 template <int D, int B>
@@ -1057,6 +1098,8 @@ ocq_status launch_build(const uint8_t *frames, int N, ocq_model *m, cudaStream_t
   const int d = m->depth;
   m->kept_len = 0;  // until a candidate build writes the kept-leaf index
   if (m->kind == OCQ_REGION_FRAME || (m->kind == OCQ_REGION_BLOCK && d >= 6)) return build_dense(frames, N, m, st);
+  if (m->kind == OCQ_REGION_BLOCK && block_r8_ok(N, m->H, m->W, m->block, d, frames))
+    return launch_block_r8(frames, N, m, st);
   if (m->kind == OCQ_REGION_BLOCK && block_fs_ok(N, m->H, m->W, m->block, d, frames)) {
     switch (d) {
       case 2: return launch_block_fs_b<2>(frames, N, m, st);

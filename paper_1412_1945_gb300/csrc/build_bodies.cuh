@@ -1014,6 +1014,192 @@ __device__ __forceinline__ void build_block_fs_body(const uint8_t *__restrict__ 
   }
 }
 
+// ---- 8 x 8 block regions at depth 5: one region per warp, two-level tables --
+// A warp counts one 8 x 8 region at a time, 2 pixels per lane (lane l: row
+// l / 4, columns 2 (l % 4) and 2 (l % 4) + 1, read as the two words holding
+// their 6 bytes).  The region's leaves are counted in the warp tiles'
+// two-level tables (a depth-3 prefix directory, then a 64-entry sub-table per
+// prefix claimed from a pool of NP; u16 entries (frame + 1, count), rewritten
+// only while their frame field is older, so same-frame lanes store the same
+// value): no probing, unlike the hashed one-warp-per-region table.  A region
+// whose prefixes exhaust the pool is recounted by the chunked direct passes.
+struct BlockR8Cfg {
+  static constexpr int D = 5;
+  static constexpr int NPRE = 512;
+  static constexpr int SUB = 64, SUBS = SUB + 2;
+  static constexpr int NP = 32;
+  static constexpr int DIR_BYTES = NPRE * 2;
+  static constexpr int POOL_BYTES = (NP * SUBS * 2 + 15) & ~15;
+  static constexpr int OWNER_BYTES = (NP * 2 + 15) & ~15;
+  static constexpr int TABLE_BYTES = DIR_BYTES + POOL_BYTES + OWNER_BYTES + 16;  // + pool count
+  static constexpr int WARP_SMEM = TABLE_BYTES + 16;                              // + overflow flag
+  static constexpr int WPR = 1024;
+  static constexpr int PF = 4;
+  static_assert(TABLE_BYTES >= 4096, "the recount passes use a 4 KB table");
+};
+
+// Warp w of the caller handles regions r = r_first, r_first + r_step, ... <
+// r_end (row-major, bw = W / 8 per row).  Needs W % 8 == 0, 4-byte aligned
+// frames, N <= 255, H*W*3 < 2^32.  wsm: this warp's WARP_SMEM bytes (16-byte
+// aligned), zero on entry and on return.
+__device__ __forceinline__ void build_block_r8_body(const uint8_t *__restrict__ frames, int N, int H, int W, int bw,
+                                                    uint32_t T, uint32_t *__restrict__ model, int64_t r_first,
+                                                    int64_t r_end, int64_t r_step, uint8_t *wsm) {
+  using C = BlockR8Cfg;
+  constexpr int D = C::D, E = D - 3;
+  const int lane = threadIdx.x & 31;
+  const int ly = lane >> 2, lj = lane & 3;
+  const int64_t fstride = (int64_t)H * W * 3;
+  uint16_t *dir = reinterpret_cast<uint16_t *>(wsm);
+  uint16_t *pool = reinterpret_cast<uint16_t *>(wsm + C::DIR_BYTES);
+  uint16_t *owner = reinterpret_cast<uint16_t *>(wsm + C::DIR_BYTES + C::POOL_BYTES);
+  uint32_t *pcount = reinterpret_cast<uint32_t *>(wsm + C::DIR_BYTES + C::POOL_BYTES + C::OWNER_BYTES);
+  uint32_t *flag = reinterpret_cast<uint32_t *>(wsm + C::TABLE_BYTES);
+  // byte selectors of the lane's two pixels within its two words
+  const uint32_t sel = (uint32_t)((6 * lj) & 3);
+  const uint32_t s0 = sel | ((sel + 1) << 4) | ((sel + 2) << 8), s1 = s0 + 0x333u;
+  for (int64_t r = r_first; r < r_end; r += r_step) {
+    const int by = (int)(r / bw), bx = (int)(r - (int64_t)by * bw);
+    const int y = by * 8 + ly;
+    const bool active = y < H;
+    const int64_t pofs = ((int64_t)y * W + bx * 8 + 2 * lj) * 3;
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(frames + (pofs & ~(int64_t)3));
+    bool skip = !active;
+    auto load = [&](uint32_t (&v)[C::PF][2], int f0) {
+#pragma unroll
+      for (int j = 0; j < C::PF; ++j)
+        if (active && f0 + j < N) {
+          const uint32_t *s = src + (int64_t)(f0 + j) * (fstride >> 2);
+          v[j][0] = __ldg(s), v[j][1] = __ldg(s + 1);
+        }
+    };
+    auto count = [&](const uint32_t (&v)[C::PF][2], int f0) {
+#pragma unroll
+      for (int j = 0; j < C::PF; ++j) {
+        if (f0 + j >= N) break;
+        const uint32_t fh = (uint32_t)(f0 + j + 1) << 8;
+        uint32_t pre[2], suf[2], sub[2];
+        uint32_t deferred = 0;
+        if (!skip) {
+          const uint32_t m0 = (v[j][0] >> (8 - D)) & byte_mask(D), m1 = (v[j][1] >> (8 - D)) & byte_mask(D);
+          const uint32_t px[2] = {__byte_perm(m0, m1, s0), __byte_perm(m0, m1, s1)};
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            pre[k] = __dp4a((px[k] >> E) & byte_mask(3), 1u | (8u << 8) | (64u << 16), 0u);
+            suf[k] = __dp4a(px[k] & byte_mask(E), 1u | ((1u << E) << 8) | ((1u << (2 * E)) << 16), 0u);
+          }
+          volatile uint16_t *vd = dir;
+#pragma unroll
+          for (int k = 0; k < 2; ++k) sub[k] = vd[pre[k]];
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+            if (sub[k] == 0u || sub[k] == 0xFFFFu) {
+              // claim the prefix's sub-table (0: another lane is claiming it,
+              // or the pool ran out and the region is recounted)
+              sub[k] = 0u;
+              const unsigned short old = atomicCAS(reinterpret_cast<unsigned short *>(dir + pre[k]),
+                                                   (unsigned short)0, (unsigned short)0xFFFF);
+              if (old == 0) {
+                const uint32_t jt = atomicAdd(pcount, 1u);
+                if (jt < (uint32_t)C::NP) {
+                  owner[jt] = (uint16_t)pre[k];
+                  *reinterpret_cast<volatile uint16_t *>(dir + pre[k]) = (uint16_t)(jt + 1);
+                  sub[k] = jt + 1;
+                } else {
+                  atomicOr(flag, 1u);
+                }
+              } else if (old != 0xFFFF) {
+                sub[k] = old;
+              }
+              if (!sub[k]) deferred |= 1u << k;
+            }
+          volatile uint16_t *vp = pool;
+          uint32_t e[2];
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+            if (!((deferred >> k) & 1u)) e[k] = vp[(sub[k] - 1u) * C::SUBS + suf[k]];
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+            if (!((deferred >> k) & 1u) && e[k] < fh)
+              vp[(sub[k] - 1u) * C::SUBS + suf[k]] = (uint16_t)(fh | ((e[k] + 1u) & 0xFFu));
+        }
+        __syncwarp();
+        if (__any_sync(0xFFFFFFFFu, deferred != 0u)) {  // their prefixes are set now (or the pool ran out)
+          if (deferred && !*(volatile uint32_t *)flag) {
+            volatile uint16_t *vd = dir;
+            volatile uint16_t *vp = pool;
+#pragma unroll
+            for (int k = 0; k < 2; ++k)
+              if ((deferred >> k) & 1u) {
+                const uint32_t sb = vd[pre[k]];
+                if (sb == 0u || sb == 0xFFFFu) continue;  // unreachable unless the region overflowed
+                const uint32_t ee = vp[(sb - 1u) * C::SUBS + suf[k]];
+                if (ee < fh) vp[(sb - 1u) * C::SUBS + suf[k]] = (uint16_t)(fh | ((ee + 1u) & 0xFFu));
+              }
+          }
+          __syncwarp();
+        }
+        skip = skip || *(volatile uint32_t *)flag != 0u;
+      }
+    };
+    {
+      uint32_t va[C::PF][2], vb[C::PF][2];
+      load(va, 0);
+      for (int f0 = 0; f0 < N; f0 += 2 * C::PF) {
+        load(vb, f0 + C::PF);
+        count(va, f0);
+        if (f0 + C::PF >= N) break;
+        load(va, f0 + 2 * C::PF);
+        count(vb, f0 + C::PF);
+      }
+    }
+    __syncwarp();
+    // Emit: the row zeroed, then the kept leaves' bits; the tables cleared.
+    uint32_t *row = model + r * C::WPR;
+    const bool ovf = *(volatile uint32_t *)flag != 0u;
+    {
+      uint4 *r4 = reinterpret_cast<uint4 *>(row);
+      for (int i = lane; i < C::WPR / 4; i += 32) r4[i] = make_uint4(0, 0, 0, 0);
+    }
+    __syncwarp();
+    const uint32_t used = min(*(volatile uint32_t *)pcount, (uint32_t)C::NP);
+    for (uint32_t i = lane; i < used * C::SUB; i += 32) {
+      const uint32_t jt = i / C::SUB, sx = i - jt * C::SUB;
+      const uint32_t e = pool[jt * C::SUBS + sx];
+      if (e) {
+        pool[jt * C::SUBS + sx] = 0;
+        if (!ovf && (e & 0xFFu) >= T) {
+          const uint32_t q = tile_compose<D>(owner[jt], sx);
+          atomicOr(&row[q >> 5], 1u << (q & 31));
+        }
+      }
+    }
+    {
+      uint4 *z = reinterpret_cast<uint4 *>(wsm);  // the directory
+      for (int i = lane; i < C::DIR_BYTES / 16; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+    }
+    if (lane == 0) *pcount = 0u;
+    __syncwarp();
+    if (ovf) {  // chunked direct passes over 1024-leaf slices (table = the first 4 KB of wsm, zero now)
+      uint32_t *tab = reinterpret_cast<uint32_t *>(wsm);
+      const int x0 = bx * 8, h = min(8, H - by * 8), npx = h * 8;
+      uint32_t off[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int i = lane + 32 * k;
+        off[k] = i < npx ? (uint32_t)(((int64_t)(by * 8 + i / 8) * W + x0 + i % 8) * 3) : 0u;
+      }
+      for (int c = 0; c < WarpTableCfg<D>::NC / WarpTableCfg<D>::S; ++c) {
+        __syncwarp();
+        warp_region_pass<D, 2, 4, true>(frames, N, fstride, off, npx, tab, c);
+        warp_emit<D>(tab, row, T);
+      }
+      if (lane == 0) *flag = 0u;
+      __syncwarp();
+    }
+  }
+}
+
 // ---- pixel regions, depth <= 3 -------------------------------------------------
 // Thread t of a 128-thread CTA owns pixel location p and a private column of
 // counter words cnt[k * 128 + t] (4 u8 or 2 u16 counters per word).

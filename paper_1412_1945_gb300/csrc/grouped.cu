@@ -98,6 +98,18 @@ __global__ void __launch_bounds__(256, BlockFsCfg<D, B>::MINB) g_block_fs(const 
   build_block_fs_body<D, B>(s.in, s.N, s.H, s.W, s.bw, (uint32_t)s.T, s.model, s.units, vb, s.vg, gf_smem);
 }
 
+__global__ void __launch_bounds__(256, 4) g_block_r8(const GSeg *__restrict__ g, int n) {
+  extern __shared__ __align__(16) uint8_t gr_smem[];
+  constexpr int WB = BlockR8Cfg::WARP_SMEM;
+  uint8_t *wsm = gr_smem + (threadIdx.x >> 5) * WB;
+  for (int i = threadIdx.x & 31; i < WB / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
+  __syncwarp();
+  int64_t vb;
+  const GSeg &s = seg_of(g, n, vb);
+  build_block_r8_body(s.in, s.N, s.H, s.W, s.bw, (uint32_t)s.T, s.model, vb * 8 + (threadIdx.x >> 5), s.units,
+                      s.vg * 8, wsm);
+}
+
 // items u = chunk * tiles + tile over frames [chunk * fchunk, + fchunk)
 template <int D>
 __global__ void __launch_bounds__(256) g_block_tb(const GSeg *__restrict__ g, int n) {
@@ -244,6 +256,10 @@ static KInfo kinfo_d(int kind, int b) {
         if (b == 8) k.fn = g_block_fs<D, 8>, k.smem = BlockFsCfg<D, 8>::SMEM;
       }
       break;
+    case GK_BLOCK_R8:
+      if constexpr (D == 5)
+        if (b == 8) k.fn = g_block_r8, k.smem = (size_t)8 * BlockR8Cfg::WARP_SMEM;
+      break;
     case GK_BLOCK_WARP:
       if constexpr (D <= 5) {
         k.smem = (size_t)8 * WarpTableCfg<D>::S * 4;
@@ -360,15 +376,19 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
       }
     } else if (x.kind == OCQ_REGION_BLOCK) {
       const bool cls_ok = x.F == 0 || (x.block % 4 == 0 && x.W % 4 == 0 && (tm & 3) == 0);
-      const bool fs = block_fs_ok(x.N, x.H, x.W, x.block, d, x.train);
-      const bool tile = !fs && block_tile_ok(x.N, x.H, x.W, x.block, d, x.train);
-      const bool warp = !fs && !tile && d <= 5 && block_warp_ok(x.N, x.H, x.W, x.block);
-      if (!cls_ok || (!fs && !tile && !warp)) {
+      const bool r8 = block_r8_ok(x.N, x.H, x.W, x.block, d, x.train);
+      const bool fs = !r8 && block_fs_ok(x.N, x.H, x.W, x.block, d, x.train);
+      const bool tile = !r8 && !fs && block_tile_ok(x.N, x.H, x.W, x.block, d, x.train);
+      const bool warp = !r8 && !fs && !tile && d <= 5 && block_warp_ok(x.N, x.H, x.W, x.block);
+      if (!cls_ok || (!r8 && !fs && !tile && !warp)) {
         fallback.push_back(i);
         continue;
       }
       GSeg bld = base(x, x.train);
-      if (fs) {
+      if (r8) {
+        bld.units = cdiv64(x.H, 8) * (x.W / 8);
+        launch(GK_BLOCK_R8, d, 8).segs.push_back(bld);
+      } else if (fs) {
         bld.units = x.block == 8 && d == 5 ? cdiv64(x.H, 8) * (x.W / 8) : cdiv64(x.H, 16) * cdiv64(x.W, 16);
         launch(GK_BLOCK_FS, d, x.block).segs.push_back(bld);
       } else if (tile) {
@@ -449,6 +469,7 @@ ocq_status grouped_plan(const std::vector<GStreamIn> &in, std::vector<GLaunch> &
         case GK_CLS_FRAME: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 16 * 256), cap)); break;
         case GK_BLOCK_TILE: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, x.threads / 32), cap)); break;
         case GK_BLOCK_FS: s.vg = std::max<int64_t>(1, std::min<int64_t>(s.units, cap)); break;
+        case GK_BLOCK_R8: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 8), cap)); break;
         case GK_BLOCK_WARP:
         case GK_BLOCK_TB: s.vg = std::max<int64_t>(1, std::min<int64_t>(cdiv64(s.units, 8), cap)); break;
         case GK_PIX_WS_BUILD: s.vg = std::max<int64_t>(1, std::min<int64_t>(s.units, cap)); break;

@@ -43,6 +43,7 @@ enum GroupKind : int {
   GK_BLOCK_TILE,   // block build over 16 x 16 warp tiles, a = depth, b = block size
   GK_BLOCK_WARP,   // block build, one warp per region, a = depth, b = pixels per lane
   GK_BLOCK_FS,     // block build, frames split over a CTA's warps, a = depth, b = block size
+  GK_BLOCK_R8,     // block build, 8 x 8 at depth 5, one region per warp, two-level tables
   GK_BLOCK_TB,     // block classify, warps walking frames, a = depth
   GK_PIX_WS_BUILD, // per-pixel build, depth <= 3, counters + copy warp, a = depth
   GK_PIX_WS_CLS,   // per-pixel classify, depth <= 3, rows staged + copy warp, a = depth

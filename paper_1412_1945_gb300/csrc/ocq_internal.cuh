@@ -203,6 +203,7 @@ bool block_warp_ok(int N, int H, int W, int b);
 // and its selection (1: used where it applies; 0: one warp per region).
 bool block_tile_ok(int N, int H, int W, int b, int depth, const void *frames);
 bool block_fs_ok(int N, int H, int W, int b, int depth, const void *frames);
+bool block_r8_ok(int N, int H, int W, int b, int depth, const void *frames);
 // While one is alive on this thread, the default block build form picks for
 // work per region rather than for filling the GPU (the batched forms, where
 // other streams' kernels run beside it).
