@@ -1042,14 +1042,18 @@ struct BlockR8Cfg {
 // r_end (row-major, bw = W / 8 per row).  Needs W % 8 == 0, 4-byte aligned
 // frames, N <= 255, H*W*3 < 2^32.  wsm: this warp's WARP_SMEM bytes (16-byte
 // aligned), zero on entry and on return.
-__device__ __forceinline__ void build_block_r8_body(const uint8_t *__restrict__ frames, int N, int H, int W, int bw,
+// SRC = uint16_t: `frames` holds depth-5 planar leaf codes, u16 [N][H*W] (a
+// serving window's per-frame occupancy); a lane's two pixels are one word.
+template <typename SRC = uint8_t>
+__device__ __forceinline__ void build_block_r8_body(const SRC *__restrict__ frames, int N, int H, int W, int bw,
                                                     uint32_t T, uint32_t *__restrict__ model, int64_t r_first,
                                                     int64_t r_end, int64_t r_step, uint8_t *wsm) {
   using C = BlockR8Cfg;
+  constexpr bool CODES = std::is_same<SRC, uint16_t>::value;
   constexpr int D = C::D, E = D - 3;
   const int lane = threadIdx.x & 31;
   const int ly = lane >> 2, lj = lane & 3;
-  const int64_t fstride = (int64_t)H * W * 3;
+  const int64_t fstride = (int64_t)H * W * (CODES ? 1 : 3);  // in SRC elements
   uint16_t *dir = reinterpret_cast<uint16_t *>(wsm);
   uint16_t *pool = reinterpret_cast<uint16_t *>(wsm + C::DIR_BYTES);
   uint16_t *owner = reinterpret_cast<uint16_t *>(wsm + C::DIR_BYTES + C::POOL_BYTES);
@@ -1062,15 +1066,19 @@ __device__ __forceinline__ void build_block_r8_body(const uint8_t *__restrict__ 
     const int by = (int)(r / bw), bx = (int)(r - (int64_t)by * bw);
     const int y = by * 8 + ly;
     const bool active = y < H;
-    const int64_t pofs = ((int64_t)y * W + bx * 8 + 2 * lj) * 3;
-    const uint32_t *src = reinterpret_cast<const uint32_t *>(frames + (pofs & ~(int64_t)3));
+    const int64_t pix = (int64_t)y * W + bx * 8 + 2 * lj;
+    const int64_t pofs = CODES ? pix * 2 : pix * 3;  // bytes
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(frames) +
+                                                             (pofs & ~(int64_t)3));
+    const int64_t fwords = fstride * (int64_t)sizeof(SRC) / 4;  // words per frame (H*W*3 or 2*H*W bytes, W % 8 == 0)
     bool skip = !active;
     auto load = [&](uint32_t (&v)[C::PF][2], int f0) {
 #pragma unroll
       for (int j = 0; j < C::PF; ++j)
         if (active && f0 + j < N) {
-          const uint32_t *s = src + (int64_t)(f0 + j) * (fstride >> 2);
-          v[j][0] = __ldg(s), v[j][1] = __ldg(s + 1);
+          const uint32_t *s = src + (int64_t)(f0 + j) * fwords;
+          v[j][0] = __ldg(s);
+          if constexpr (!CODES) v[j][1] = __ldg(s + 1);
         }
     };
     auto count = [&](const uint32_t (&v)[C::PF][2], int f0) {
@@ -1081,12 +1089,21 @@ __device__ __forceinline__ void build_block_r8_body(const uint8_t *__restrict__ 
         uint32_t pre[2], suf[2], sub[2];
         uint32_t deferred = 0;
         if (!skip) {
-          const uint32_t m0 = (v[j][0] >> (8 - D)) & byte_mask(D), m1 = (v[j][1] >> (8 - D)) & byte_mask(D);
-          const uint32_t px[2] = {__byte_perm(m0, m1, s0), __byte_perm(m0, m1, s1)};
+          if constexpr (CODES) {  // q = r | g << 5 | b << 10: prefix = top 3 bits, suffix = low 2 of each
+            const uint32_t q[2] = {v[j][0] & 0xFFFFu, v[j][0] >> 16};
 #pragma unroll
-          for (int k = 0; k < 2; ++k) {
-            pre[k] = __dp4a((px[k] >> E) & byte_mask(3), 1u | (8u << 8) | (64u << 16), 0u);
-            suf[k] = __dp4a(px[k] & byte_mask(E), 1u | ((1u << E) << 8) | ((1u << (2 * E)) << 16), 0u);
+            for (int k = 0; k < 2; ++k) {
+              pre[k] = ((q[k] >> E) & 7u) | ((q[k] >> (D + E - 3)) & 0x38u) | ((q[k] >> (2 * D + E - 6)) & 0x1C0u);
+              suf[k] = (q[k] & 3u) | ((q[k] >> (D - E)) & 0xCu) | ((q[k] >> (2 * D - 2 * E)) & 0x30u);
+            }
+          } else {
+            const uint32_t m0 = (v[j][0] >> (8 - D)) & byte_mask(D), m1 = (v[j][1] >> (8 - D)) & byte_mask(D);
+            const uint32_t px[2] = {__byte_perm(m0, m1, s0), __byte_perm(m0, m1, s1)};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              pre[k] = __dp4a((px[k] >> E) & byte_mask(3), 1u | (8u << 8) | (64u << 16), 0u);
+              suf[k] = __dp4a(px[k] & byte_mask(E), 1u | ((1u << E) << 8) | ((1u << (2 * E)) << 16), 0u);
+            }
           }
           volatile uint16_t *vd = dir;
 #pragma unroll
@@ -1187,11 +1204,11 @@ __device__ __forceinline__ void build_block_r8_body(const uint8_t *__restrict__ 
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int i = lane + 32 * k;
-        off[k] = i < npx ? (uint32_t)(((int64_t)(by * 8 + i / 8) * W + x0 + i % 8) * 3) : 0u;
+        off[k] = i < npx ? (uint32_t)(((int64_t)(by * 8 + i / 8) * W + x0 + i % 8) * (CODES ? 1 : 3)) : 0u;
       }
       for (int c = 0; c < WarpTableCfg<D>::NC / WarpTableCfg<D>::S; ++c) {
         __syncwarp();
-        warp_region_pass<D, 2, 4, true>(frames, N, fstride, off, npx, tab, c);
+        warp_region_pass<D, 2, 4, true, SRC>(frames, N, fstride, off, npx, tab, c);
         warp_emit<D>(tab, row, T);
       }
       if (lane == 0) *flag = 0u;

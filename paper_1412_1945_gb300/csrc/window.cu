@@ -162,6 +162,20 @@ __global__ void __launch_bounds__(256) remerge_block_codes_kernel(const uint16_t
                                    (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), R, nw, tab);
 }
 
+// 8 x 8 blocks at depth 5: one region per warp with two-level tables over the
+// window's code planes (build_block_r8_body reading codes).
+__global__ void __launch_bounds__(256, 4) remerge_block_r8_kernel(const uint16_t *__restrict__ ring, int N, int H,
+                                                                int W, int bw, uint32_t T,
+                                                                uint32_t *__restrict__ model, int64_t R) {
+  extern __shared__ __align__(16) uint8_t rr_smem[];
+  constexpr int WB = BlockR8Cfg::WARP_SMEM;
+  uint8_t *wsm = rr_smem + (threadIdx.x >> 5) * WB;
+  for (int i = threadIdx.x & 31; i < WB / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
+  __syncwarp();
+  build_block_r8_body<uint16_t>(ring, N, H, W, bw, T, model, (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), R,
+                                (int64_t)gridDim.x * 8, wsm);
+}
+
 static unsigned window_grid(int64_t work, int threads, int per_sm) {
   int64_t b = (work + threads - 1) / threads;
   const int64_t cap = (int64_t)sm_count() * per_sm;
@@ -250,6 +264,22 @@ static ocq_status launch_remerge_block_ppl(const uint16_t *ring, int N, ocq_mode
 
 template <int D>
 static ocq_status launch_remerge_block(const uint16_t *ring, int N, ocq_model *m, cudaStream_t st) {
+  if (D == 5 && m->block == 8 && m->W % 8 == 0 && (reinterpret_cast<uintptr_t>(ring) & 3) == 0) {
+    constexpr size_t smem = (size_t)8 * BlockR8Cfg::WARP_SMEM;
+    static int cap = 0;
+    if (!cap) {
+      cudaFuncSetAttribute(remerge_block_r8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int per = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, remerge_block_r8_kernel, 256, smem);
+      cap = sm_count() * (per > 0 ? per : 1);
+    }
+    const int bw = m->W / 8;
+    const int64_t ctas = (m->R + 7) / 8;
+    remerge_block_r8_kernel<<<(unsigned)(ctas < cap ? ctas : cap), 256, smem, st>>>(ring, N, m->H, m->W, bw,
+                                                                                   (uint32_t)m->T, m->bits, m->R);
+    count_launch();
+    return cuda_status(cudaGetLastError(), "remerge_block_r8_kernel");
+  }
   const int npx = m->block * m->block;
   if (npx <= 32) return launch_remerge_block_ppl<D, 1>(ring, N, m, st);
   if (npx <= 64) return launch_remerge_block_ppl<D, 2>(ring, N, m, st);

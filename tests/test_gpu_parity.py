@@ -407,6 +407,29 @@ def test_block_build_tiles(ocq, torch, b, d):
         O.ocq_tune_select(kern, saved)
 
 
+@pytest.mark.parametrize("b,d", [(8, 3), (8, 4), (8, 5), (16, 4), (16, 5)])
+def test_block_build_one_and_two_frames(ocq, torch, b, d):
+    """Every block build form with N = 1 and N = 2 (T = 1 keeps every leaf of
+    the frames, T = N only the leaves of both), on several regions with a
+    ragged bottom row of blocks."""
+    O = ocq.ocq
+    kern = O.OCQ_TUNE_BUILD_BLOCK
+    saved = O.ocq_tune_selected(kern)
+    try:
+        H, W = 3 * b + 5, 48
+        sc = ocq_synth.make_scene("sway", H, W, 2, 3, seed=950 + 7 * b + d)
+        frames = ocq_synth.fill_host(sc, 0, 5)
+        for N in (1, 2):
+            for T in sorted({1, N}):
+                ow, om = oracle.run(frames[:N], d, T, BLOCK, b, frames[2:])
+                for form in range(O.ocq_tune_count(kern)):
+                    O.ocq_tune_select(kern, form)
+                    words, mask = gpu_model_and_mask(ocq, torch, frames[:N], frames[2:], d, T, BLOCK, b)
+                    assert (words == ow).all() and (mask == om).all(), (N, T, form)
+    finally:
+        O.ocq_tune_select(kern, saved)
+
+
 @pytest.mark.parametrize("N", [254, 255, 256])
 def test_block_build_frame_count_limits(ocq, torch, N):
     """The warp tables and the frame-split counters keep counts in 8 bits:

@@ -224,3 +224,37 @@ def test_array_submits_and_polls(cuda_ready):
             assert (masks[i].cpu().numpy() == _window_oracle(hosts[i], cam)).all(), i
     finally:
         srv.destroy()
+
+
+def test_block_code_window_many_leaves(cuda_ready):
+    """8 x 8 blocks at depth 5 re-merged from their code window when regions
+    hold more depth-3 prefixes than the region tables' pool (uniform noise in
+    half the frames' pixels, so those regions are recounted by the chunked
+    passes), with a ragged bottom row of blocks; masks and the final model
+    under the window semantics."""
+    import torch
+
+    O = cuda_ready.ocq
+    H, W, N, K, T, F = 21, 32, 9, 3, 2, 10
+    cam = ("sway", H, W, BLOCK, 8, 5, T, N, K, F, 2)
+    g = np.random.default_rng(77)
+    host = ocq_synth.fill_host(ocq_synth.make_scene("sway", H, W, N, F, 7900), 0, N + F)
+    noise = g.integers(0, 256, size=host.shape, dtype=np.uint8)
+    host = np.where((g.random((N + F, H, W)) < 0.5)[..., None], noise, host)
+    dev = torch.from_numpy(host).cuda()
+    masks = torch.full((F, H, W), 9, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    srv = O.ocq_server_create(1 << 28, 1)
+    try:
+        c = O.ocq_server_admit(srv, H, W, BLOCK, 8, 5, T, N, K, dev[:N].contiguous())
+        assert c is not None
+        for t in range(F):
+            O.ocq_server_submit(srv, c, dev[N + t], masks[t], tag=t)
+        O.ocq_server_sync(srv)
+        model = cuda_ready.export_model(O.ocq_server_camera_model(srv, c)).cpu().numpy().view(np.uint64)
+        O.ocq_server_release(srv, c)
+    finally:
+        srv.destroy()
+    assert (masks.cpu().numpy() == _window_oracle(host, cam)).all()
+    k = F // K
+    assert (model == oracle.build_model(host[k * K:k * K + N], 5, T, BLOCK, 8)).all()
