@@ -474,8 +474,9 @@ void ocq_server_destroy(ocq_server *server);
  *                            and region tables only.  0 one warp per region
  *                            always; 2 frames split wherever they apply; 3 tiles
  *                            wherever they apply (8 x 8 at depth 5: one warp per
- *                            region); 4 the region tables for 8 x 8 at depth 5
- *                            (else one warp per region); params = {variant, 0, ...}
+ *                            region); 4 the region tables for 8 x 8 at depth 4
+ *                            or 5 (else one warp per region); params =
+ *                            {variant, 0, ...}
  * ocq_tune_count: number of variants (-1 for an unknown kernel).
  * ocq_tune_select: process-wide choice used by later calls (not thread-safe
  * against concurrent calls of the same kernel).  ocq_tune_describe writes 5

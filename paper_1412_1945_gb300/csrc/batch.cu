@@ -137,12 +137,13 @@ __device__ __noinline__ void block_tile_item(const BStream &S, int64_t t0, int64
                                      t1, kBatchThreads / 32, wsm);
 }
 
+template <int D>
 __device__ __noinline__ void block_r8_item(const BStream &S, int64_t r0, int64_t r1, uint8_t *smem) {
-  uint8_t *wsm = smem + (threadIdx.x >> 5) * BlockR8Cfg::WARP_SMEM;
-  for (int i = threadIdx.x & 31; i < BlockR8Cfg::WARP_SMEM / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
+  uint8_t *wsm = smem + (threadIdx.x >> 5) * BlockR8CfgD<D>::WARP_SMEM;
+  for (int i = threadIdx.x & 31; i < BlockR8CfgD<D>::WARP_SMEM / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
   __syncwarp();
-  build_block_r8_body(S.train, S.N, S.H, S.W, S.bw, (uint32_t)S.T, S.model, r0 + (threadIdx.x >> 5), r1,
-                      kBatchThreads / 32, wsm);
+  build_block_r8_body<D>(S.train, S.N, S.H, S.W, S.bw, (uint32_t)S.T, S.model, r0 + (threadIdx.x >> 5), r1,
+                         kBatchThreads / 32, wsm);
 }
 
 __device__ __noinline__ void block_tile_dispatch(const BStream &S, int64_t t0, int64_t t1, uint8_t *smem) {
@@ -276,7 +277,10 @@ __device__ void run_item(const BStream &S, const BItem &it, uint8_t *smem) {
       block_tile_dispatch(S, it.vb, it.aux, smem);
       return;
     case OP_BUILD_BLOCK_R8:
-      block_r8_item(S, it.vb, it.aux, smem);
+      if (S.depth == 4)
+        block_r8_item<4>(S, it.vb, it.aux, smem);
+      else
+        block_r8_item<5>(S, it.vb, it.aux, smem);
       return;
     case OP_CLS_PIXEL_TB:
       if (S.kl)
@@ -353,7 +357,8 @@ static size_t item_smem(const BStream &h) {
     if (d <= 6) need = std::max<size_t>(need, (size_t)h.wpr * 4 * (d <= 4 ? 32 : 1));  // occ row / replicated row
   } else if (h.kind == OCQ_REGION_BLOCK) {
     if (h.r8)
-      need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * BlockR8Cfg::WARP_SMEM);
+      need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) *
+                                        (d == 4 ? BlockR8CfgD<4>::WARP_SMEM : BlockR8CfgD<5>::WARP_SMEM));
     else if (h.tile)
       need = std::max<size_t>(need, (size_t)(kBatchThreads / 32) * block_tile_warp_smem(d, h.block));
     else if (h.ppl > 0)

@@ -88,16 +88,17 @@ __global__ void __launch_bounds__(BlockTileCfg<D, B>::WPC * 32, BlockTileCfg<D, 
                                   (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), ntiles, nw, wsm);
 }
 
+template <int D>
 __global__ void __launch_bounds__(256, 4) build_block_r8_kernel(const uint8_t *__restrict__ frames, int N, int H, int W,
                                                              int bw, uint32_t T, uint32_t *__restrict__ model,
                                                              int64_t R) {
   extern __shared__ __align__(16) uint8_t r8_smem[];
-  constexpr int WB = BlockR8Cfg::WARP_SMEM;
+  constexpr int WB = BlockR8CfgD<D>::WARP_SMEM;
   uint8_t *wsm = r8_smem + (threadIdx.x >> 5) * WB;
   for (int i = threadIdx.x & 31; i < WB / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
   __syncwarp();
-  build_block_r8_body(frames, N, H, W, bw, T, model, (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), R,
-                      (int64_t)gridDim.x * 8, wsm);
+  build_block_r8_body<D>(frames, N, H, W, bw, T, model, (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), R,
+                         (int64_t)gridDim.x * 8, wsm);
 }
 
 template <int D, int B>
@@ -672,8 +673,9 @@ static ocq_status launch_block_warp_ppl(const uint8_t *frames, int N, ocq_model 
 // the region tables for 8 x 8 at depth 5 (64-stream mix, 8 x 8 d = 4 class in
 // the graph of branches: frames split 0.36, tiles 0.32 ms).
 // Forms 0, 2, 3 and 4 force one warp per region, frames split, tiles (8 x 8
-// at depth 5: one warp per region) and the region tables (8 x 8 at depth 5
-// only).
+// at depth 5: one warp per region) and the region tables (8 x 8 at depth 4
+// or 5; at depth 4 they measured 0.17-0.18 ms at 1080p, no faster than the tiles and
+// behind the frames split, so the default does not take them there).
 static int g_block_form = 1;
 static thread_local bool t_shared_gpu = false;
 SharedGpuScope::SharedGpuScope() : prev(t_shared_gpu) { t_shared_gpu = true; }
@@ -686,7 +688,7 @@ enum BlockBuildKind { BB_WARP = 0, BB_TILE, BB_FS, BB_R8 };
 static BlockBuildKind block_build_kind(int N, int H, int W, int b, int depth, const void *frames) {
   if (g_block_form == 0 || !block_shape_ok(N, H, W, b, depth, frames)) return BB_WARP;
   if (g_block_form == 2) return BB_FS;
-  if (g_block_form == 4) return b == 8 && depth == 5 ? BB_R8 : BB_WARP;
+  if (g_block_form == 4) return b == 8 && depth >= 4 ? BB_R8 : BB_WARP;
   if (g_block_form == 3) return b == 8 && depth == 5 ? BB_WARP : BB_TILE;
   const int64_t tiles = (int64_t)((H + 15) / 16) * ((W + 15) / 16);
   if (b == 8 && depth == 5) return !t_shared_gpu && tiles < 1024 ? BB_FS : BB_R8;
@@ -711,25 +713,29 @@ bool block_build_form_select(int v) {
   return true;
 }
 
-static ocq_status launch_block_r8(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
-  constexpr size_t smem = (size_t)8 * BlockR8Cfg::WARP_SMEM;
+template <int D>
+static ocq_status launch_block_r8_d(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  constexpr size_t smem = (size_t)8 * BlockR8CfgD<D>::WARP_SMEM;
+  auto kern = build_block_r8_kernel<D>;
   static int cap = 0;
   if (!cap) {
-    if (smem > 48 * 1024)
-      cudaFuncSetAttribute(build_block_r8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, build_block_r8_kernel, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 256, smem);
     cap = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
   }
   const int bw = m->W / 8;
   const int64_t R = (int64_t)((m->H + 7) / 8) * bw;
   const int64_t ctas = (R + 7) / 8;
-  build_block_r8_kernel<<<(unsigned)(ctas < cap ? ctas : cap), 256, smem, st>>>(frames, N, m->H, m->W, bw,
-                                                                               (uint32_t)m->T, m->bits, R);
+  kern<<<(unsigned)(ctas < cap ? ctas : cap), 256, smem, st>>>(frames, N, m->H, m->W, bw, (uint32_t)m->T, m->bits, R);
   count_launch();
   return cuda_status(cudaGetLastError(), "build_block_r8_kernel");
+}
+
+static ocq_status launch_block_r8(const uint8_t *frames, int N, ocq_model *m, cudaStream_t st) {
+  return m->depth == 4 ? launch_block_r8_d<4>(frames, N, m, st) : launch_block_r8_d<5>(frames, N, m, st);
 }
 
 template <int D, int B>

@@ -1023,20 +1023,23 @@ __device__ __forceinline__ void build_block_fs_body(const uint8_t *__restrict__ 
 // only while their frame field is older, so same-frame lanes store the same
 // value): no probing, unlike the hashed one-warp-per-region table.  A region
 // whose prefixes exhaust the pool is recounted by the chunked direct passes.
-struct BlockR8Cfg {
-  static constexpr int D = 5;
+template <int D>
+struct BlockR8CfgD {
+  static_assert(D == 4 || D == 5, "two-level region tables at depth 4 or 5");
+  static constexpr int E = D - 3;
   static constexpr int NPRE = 512;
-  static constexpr int SUB = 64, SUBS = SUB + 2;
-  static constexpr int NP = 32;
+  static constexpr int SUB = 1 << (3 * E), SUBS = SUB + 2;
+  static constexpr int NP = D == 5 ? 32 : 128;
   static constexpr int DIR_BYTES = NPRE * 2;
   static constexpr int POOL_BYTES = (NP * SUBS * 2 + 15) & ~15;
   static constexpr int OWNER_BYTES = (NP * 2 + 15) & ~15;
-  static constexpr int TABLE_BYTES = DIR_BYTES + POOL_BYTES + OWNER_BYTES + 16;  // + pool count
-  static constexpr int WARP_SMEM = TABLE_BYTES + 16;                              // + overflow flag
-  static constexpr int WPR = 1024;
+  static constexpr int USED = DIR_BYTES + POOL_BYTES + OWNER_BYTES + 16;  // + pool count
+  static constexpr int TABLE_BYTES = USED > 4096 ? USED : 4096;          // the recount passes use 4 KB
+  static constexpr int WARP_SMEM = TABLE_BYTES + 16;                     // + overflow flag
+  static constexpr int WPR = 1 << (3 * D - 5);
   static constexpr int PF = 4;
-  static_assert(TABLE_BYTES >= 4096, "the recount passes use a 4 KB table");
 };
+using BlockR8Cfg = BlockR8CfgD<5>;
 
 // Warp w of the caller handles regions r = r_first, r_first + r_step, ... <
 // r_end (row-major, bw = W / 8 per row).  Needs W % 8 == 0, 4-byte aligned
@@ -1044,13 +1047,14 @@ struct BlockR8Cfg {
 // aligned), zero on entry and on return.
 // SRC = uint16_t: `frames` holds depth-5 planar leaf codes, u16 [N][H*W] (a
 // serving window's per-frame occupancy); a lane's two pixels are one word.
-template <typename SRC = uint8_t>
+template <int D = 5, typename SRC = uint8_t>
 __device__ __forceinline__ void build_block_r8_body(const SRC *__restrict__ frames, int N, int H, int W, int bw,
                                                     uint32_t T, uint32_t *__restrict__ model, int64_t r_first,
                                                     int64_t r_end, int64_t r_step, uint8_t *wsm) {
-  using C = BlockR8Cfg;
+  using C = BlockR8CfgD<D>;
   constexpr bool CODES = std::is_same<SRC, uint16_t>::value;
-  constexpr int D = C::D, E = D - 3;
+  constexpr int E = C::E;
+  constexpr uint32_t SM = (1u << E) - 1u;
   const int lane = threadIdx.x & 31;
   const int ly = lane >> 2, lj = lane & 3;
   const int64_t fstride = (int64_t)H * W * (CODES ? 1 : 3);  // in SRC elements
@@ -1070,7 +1074,7 @@ __device__ __forceinline__ void build_block_r8_body(const SRC *__restrict__ fram
     const int64_t pofs = CODES ? pix * 2 : pix * 3;  // bytes
     const uint32_t *src = reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(frames) +
                                                              (pofs & ~(int64_t)3));
-    const int64_t fwords = fstride * (int64_t)sizeof(SRC) / 4;  // words per frame (H*W*3 or 2*H*W bytes, W % 8 == 0)
+    const int64_t fwords = CODES ? fstride >> 1 : fstride >> 2;  // words per frame (2*H*W or H*W*3 bytes, W % 8 == 0)
     bool skip = !active;
     auto load = [&](uint32_t (&v)[C::PF][2], int f0) {
 #pragma unroll
@@ -1094,7 +1098,7 @@ __device__ __forceinline__ void build_block_r8_body(const SRC *__restrict__ fram
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
               pre[k] = ((q[k] >> E) & 7u) | ((q[k] >> (D + E - 3)) & 0x38u) | ((q[k] >> (2 * D + E - 6)) & 0x1C0u);
-              suf[k] = (q[k] & 3u) | ((q[k] >> (D - E)) & 0xCu) | ((q[k] >> (2 * D - 2 * E)) & 0x30u);
+              suf[k] = (q[k] & SM) | ((q[k] >> (D - E)) & (SM << E)) | ((q[k] >> (2 * D - 2 * E)) & (SM << (2 * E)));
             }
           } else {
             const uint32_t m0 = (v[j][0] >> (8 - D)) & byte_mask(D), m1 = (v[j][1] >> (8 - D)) & byte_mask(D);
@@ -1197,8 +1201,13 @@ __device__ __forceinline__ void build_block_r8_body(const SRC *__restrict__ fram
     }
     if (lane == 0) *pcount = 0u;
     __syncwarp();
-    if (ovf) {  // chunked direct passes over 1024-leaf slices (table = the first 4 KB of wsm, zero now)
+    if (ovf) {  // chunked direct passes over 1024-leaf slices (table = the first 4 KB of wsm)
       uint32_t *tab = reinterpret_cast<uint32_t *>(wsm);
+      {  // at depth 4 the sub-tables' owners lie in those 4 KB too
+        uint4 *z = reinterpret_cast<uint4 *>(wsm);
+        for (int i = lane; i < 4096 / 16; i += 32) z[i] = make_uint4(0, 0, 0, 0);
+      }
+      __syncwarp();
       const int x0 = bx * 8, h = min(8, H - by * 8), npx = h * 8;
       uint32_t off[2];
 #pragma unroll

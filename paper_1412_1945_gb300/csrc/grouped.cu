@@ -98,16 +98,17 @@ __global__ void __launch_bounds__(256, BlockFsCfg<D, B>::MINB) g_block_fs(const 
   build_block_fs_body<D, B>(s.in, s.N, s.H, s.W, s.bw, (uint32_t)s.T, s.model, s.units, vb, s.vg, gf_smem);
 }
 
+template <int D>
 __global__ void __launch_bounds__(256, 4) g_block_r8(const GSeg *__restrict__ g, int n) {
   extern __shared__ __align__(16) uint8_t gr_smem[];
-  constexpr int WB = BlockR8Cfg::WARP_SMEM;
+  constexpr int WB = BlockR8CfgD<D>::WARP_SMEM;
   uint8_t *wsm = gr_smem + (threadIdx.x >> 5) * WB;
   for (int i = threadIdx.x & 31; i < WB / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
   __syncwarp();
   int64_t vb;
   const GSeg &s = seg_of(g, n, vb);
-  build_block_r8_body(s.in, s.N, s.H, s.W, s.bw, (uint32_t)s.T, s.model, vb * 8 + (threadIdx.x >> 5), s.units,
-                      s.vg * 8, wsm);
+  build_block_r8_body<D>(s.in, s.N, s.H, s.W, s.bw, (uint32_t)s.T, s.model, vb * 8 + (threadIdx.x >> 5), s.units,
+                         s.vg * 8, wsm);
 }
 
 // items u = chunk * tiles + tile over frames [chunk * fchunk, + fchunk)
@@ -257,8 +258,8 @@ static KInfo kinfo_d(int kind, int b) {
       }
       break;
     case GK_BLOCK_R8:
-      if constexpr (D == 5)
-        if (b == 8) k.fn = g_block_r8, k.smem = (size_t)8 * BlockR8Cfg::WARP_SMEM;
+      if constexpr (D == 4 || D == 5)
+        if (b == 8) k.fn = g_block_r8<D>, k.smem = (size_t)8 * BlockR8CfgD<D>::WARP_SMEM;
       break;
     case GK_BLOCK_WARP:
       if constexpr (D <= 5) {

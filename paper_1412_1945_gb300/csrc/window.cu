@@ -172,8 +172,8 @@ __global__ void __launch_bounds__(256, 4) remerge_block_r8_kernel(const uint16_t
   uint8_t *wsm = rr_smem + (threadIdx.x >> 5) * WB;
   for (int i = threadIdx.x & 31; i < WB / 4; i += 32) reinterpret_cast<uint32_t *>(wsm)[i] = 0u;
   __syncwarp();
-  build_block_r8_body<uint16_t>(ring, N, H, W, bw, T, model, (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), R,
-                                (int64_t)gridDim.x * 8, wsm);
+  build_block_r8_body<5, uint16_t>(ring, N, H, W, bw, T, model, (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5), R,
+                                   (int64_t)gridDim.x * 8, wsm);
 }
 
 static unsigned window_grid(int64_t work, int threads, int per_sm) {
